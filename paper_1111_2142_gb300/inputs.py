@@ -1,0 +1,143 @@
+"""Seeded synthetic initial conditions, in numpy FP64.
+
+This module holds no LW-ACM arithmetic: it only builds initial fields
+(d = rho - 1, u) that both the CUDA library and the FP64 oracle are fed with.
+Shapes are (ny, nx) for 2D and (nz, ny, nx) for 3D, x fastest.
+
+Workloads:
+  * 2D Taylor-Green vortex with its consistent pressure (closed-form solution of
+    the incompressible Navier-Stokes equations; pressure p = rho/3, so
+    d = 3 (p - p0)).
+  * 3D Taylor-Green vortex u = u0 sin cos cos, v = -u0 cos sin cos, w = 0 with
+    p - p0 = (u0^2/16)(cos 2kx + cos 2ky)(cos 2kz + 2).
+  * band-limited random divergence-free fields (2D stream function, 3D curl of a
+    vector potential), Hermitian so the fields are real, scaled to a target rms.
+  * the batched ensemble of independent 2D domains (side lengths log-uniform,
+    viscosities uniform).
+  * smooth random fields for parity tests on ragged shapes.
+"""
+from __future__ import annotations
+
+import numpy as np
+
+
+def tgv2d(nx: int, ny: int | None = None, u0: float = 0.01):
+    """2D Taylor-Green vortex at t = 0 on integer nodes x = i (k = 2 pi / n)."""
+    ny = nx if ny is None else ny
+    kx, ky = 2 * np.pi / nx, 2 * np.pi / ny
+    x = np.arange(nx)[None, :]
+    y = np.arange(ny)[:, None]
+    ux = u0 * np.sin(kx * x) * np.cos(ky * y)
+    uy = -u0 * (kx / ky) * np.cos(kx * x) * np.sin(ky * y)
+    p = (u0 * u0 / 4.0) * (np.cos(2 * kx * x) + (kx / ky) ** 2 * np.cos(2 * ky * y))
+    d = 3.0 * p
+    return d.astype(np.float64), ux.astype(np.float64), uy.astype(np.float64)
+
+
+def tgv3d(n: int, u0: float = 0.02, ny: int | None = None, nz: int | None = None):
+    """Classical 3D Taylor-Green vortex at t = 0 (cubic n^3 unless ny/nz given)."""
+    ny = n if ny is None else ny
+    nz = n if nz is None else nz
+    kx, ky, kz = 2 * np.pi / n, 2 * np.pi / ny, 2 * np.pi / nz
+    x = np.arange(n)[None, None, :]
+    y = np.arange(ny)[None, :, None]
+    z = np.arange(nz)[:, None, None]
+    sx, cx = np.sin(kx * x), np.cos(kx * x)
+    sy, cy = np.sin(ky * y), np.cos(ky * y)
+    cz = np.cos(kz * z)
+    ux = u0 * sx * cy * cz
+    uy = -u0 * cx * sy * cz
+    uz = np.zeros((nz, ny, n))
+    p = (u0 * u0 / 16.0) * (np.cos(2 * kx * x) + np.cos(2 * ky * y)) * (np.cos(2 * kz * z) + 2.0)
+    d = 3.0 * p * np.ones((nz, ny, n))
+    return (d.astype(np.float64), ux.astype(np.float64), uy.astype(np.float64),
+            uz.astype(np.float64))
+
+
+def _band_coeffs(rng, shape_k, kmin, kmax, mags):
+    amp = rng.standard_normal(shape_k) + 1j * rng.standard_normal(shape_k)
+    mask = (mags >= kmin) & (mags <= kmax)
+    return amp * mask
+
+
+def random_divfree_2d(nx: int, ny: int, rms: float = 0.02, kmin: float = 1, kmax: float = 4,
+                      seed: int = 0):
+    """u = (d psi/dy, -d psi/dx) from a random stream function with integer
+    wave numbers kmin <= |m| <= kmax; spectral derivatives, real output."""
+    rng = np.random.default_rng(seed)
+    mx = np.fft.fftfreq(nx, d=1.0 / nx)[None, :]
+    my = np.fft.fftfreq(ny, d=1.0 / ny)[:, None]
+    mags = np.sqrt(mx ** 2 + my ** 2)
+    psi_hat = _band_coeffs(rng, (ny, nx), kmin, kmax, mags)
+    kx = 2j * np.pi * mx / nx
+    ky = 2j * np.pi * my / ny
+    ux = np.real(np.fft.ifft2(ky * psi_hat))
+    uy = np.real(np.fft.ifft2(-kx * psi_hat))
+    s = np.sqrt(np.mean(ux ** 2 + uy ** 2))
+    if s > 0:
+        ux, uy = ux * (rms / s), uy * (rms / s)
+    d = np.zeros((ny, nx))
+    return d, np.ascontiguousarray(ux), np.ascontiguousarray(uy)
+
+
+def random_divfree_3d(nx: int, ny: int, nz: int, rms: float = 0.03, kmin: float = 1,
+                      kmax: float = 8, seed: int = 0):
+    """u = curl A for a random band-limited vector potential A."""
+    rng = np.random.default_rng(seed)
+    mx = np.fft.fftfreq(nx, d=1.0 / nx)[None, None, :]
+    my = np.fft.fftfreq(ny, d=1.0 / ny)[None, :, None]
+    mz = np.fft.fftfreq(nz, d=1.0 / nz)[:, None, None]
+    mags = np.sqrt(mx ** 2 + my ** 2 + mz ** 2)
+    shp = (nz, ny, nx)
+    A = [_band_coeffs(rng, shp, kmin, kmax, mags) for _ in range(3)]
+    kx = 2j * np.pi * mx / nx
+    ky = 2j * np.pi * my / ny
+    kz = 2j * np.pi * mz / nz
+    ux = np.real(np.fft.ifftn(ky * A[2] - kz * A[1]))
+    uy = np.real(np.fft.ifftn(kz * A[0] - kx * A[2]))
+    uz = np.real(np.fft.ifftn(kx * A[1] - ky * A[0]))
+    s = np.sqrt(np.mean(ux ** 2 + uy ** 2 + uz ** 2))
+    if s > 0:
+        ux, uy, uz = ux * (rms / s), uy * (rms / s), uz * (rms / s)
+    return (np.zeros(shp), np.ascontiguousarray(ux), np.ascontiguousarray(uy),
+            np.ascontiguousarray(uz))
+
+
+def smooth_random(shape, seed: int = 0, u_amp: float = 0.03, d_amp: float = 0.01, ncomp=None):
+    """Smooth random (d, u...) fields on any (ragged) shape: a few low Fourier
+    modes with random phases per component; not divergence-free."""
+    rng = np.random.default_rng(seed)
+    ncomp = len(shape) if ncomp is None else ncomp
+    grids = np.meshgrid(*[np.arange(n) for n in shape], indexing="ij")
+    out = []
+    for amp in [d_amp] + [u_amp] * ncomp:
+        f = np.zeros(shape)
+        for _ in range(4):
+            ph = rng.uniform(0, 2 * np.pi)
+            arg = ph
+            for g, n in zip(grids, shape):
+                arg = arg + 2 * np.pi * rng.integers(-2, 3) * g / n
+            f += rng.uniform(-1, 1) * np.cos(arg)
+        f += 0.1 * rng.uniform(-1, 1, size=shape)
+        out.append(amp * f / max(np.max(np.abs(f)), 1e-30))
+    return tuple(np.ascontiguousarray(a) for a in out)
+
+
+def ensemble_2d(n_domains: int = 256, seed: int = 1, smin: int = 32, smax: int = 512,
+                nu_lo: float = 0.002, nu_hi: float = 0.05, rms: float = 0.02,
+                kmin: float = 1, kmax: float = 4):
+    """Independent periodic D2Q9 domains: side lengths log-uniform on [smin, smax]
+    (rounded), nu uniform, initial u band-limited divergence-free with d = 0.
+
+    Returns a list of dicts {nx, ny, nu, d, ux, uy}.
+    """
+    rng = np.random.default_rng(seed)
+    nx = np.rint(np.exp(rng.uniform(np.log(smin), np.log(smax), n_domains))).astype(int)
+    ny = np.rint(np.exp(rng.uniform(np.log(smin), np.log(smax), n_domains))).astype(int)
+    nus = rng.uniform(nu_lo, nu_hi, n_domains)
+    seeds = rng.integers(0, 2 ** 31 - 1, n_domains)
+    doms = []
+    for b in range(n_domains):
+        d, ux, uy = random_divfree_2d(int(nx[b]), int(ny[b]), rms, kmin, kmax, int(seeds[b]))
+        doms.append(dict(nx=int(nx[b]), ny=int(ny[b]), nu=float(nus[b]), d=d, ux=ux, uy=uy))
+    return doms
