@@ -1,0 +1,174 @@
+/*
+ * lwacm.h — C ABI of the GB300 (sm_103a) Link-wise Artificial Compressibility
+ * Method library (Asinari, Ohwada, Chiavazzo, Di Rienzo, "Link-wise Artificial
+ * Compressibility Method").
+ *
+ * The method (Section 2.1, Eq. ACM2.0) advances only the hydrodynamic fields
+ * (rho, u) of every lattice node:
+ *
+ *   f_i(x,t+1) = f_i^(e)(x - c_i, t)
+ *              + 2(omega-1)/omega [ f_i^(e,o)(x,t) - f_i^(e,o)(x - c_i,t) ]
+ *   rho(x,t+1) = sum_i f_i(x,t+1),   rho u(x,t+1) = sum_i c_i f_i(x,t+1)
+ *
+ * with the second-order equilibrium of Eq. d2q9_equilibrium_compact (D2Q9; the
+ * same form with the weights of Eq. weight_factors_3d for D3Q19), its odd part
+ * Eq. feqo, and omega from the viscosity by Eq. viscosity2,
+ * nu = (1/omega - 1/2)/3. Populations f_i are never stored.
+ *
+ * Conventions (all entry points):
+ *   - Every call returns an lwacm_status; nothing throws, aborts or exits.
+ *   - Fields are structure-of-arrays, one array per field, x fastest:
+ *     element (x,y,z) of a field is at [(z*ny + y)*nx + x]. The density field
+ *     is stored as d = rho - 1 (not rho), so that no O(1) constant enters the
+ *     single-precision sums. D2Q9 has nz = 1 and no uz field.
+ *   - Device memory belongs to the caller: the library never allocates or frees
+ *     device memory. The caller binds one workspace (lwacm_bind) that holds the
+ *     two ping-pong state buffers (Section 2.4: two arrays, toggled each step),
+ *     a staging area and reduction scratch.
+ *   - Work is enqueued asynchronously on the bound stream. Asynchronous CUDA
+ *     errors surface at the next lwacm_sync / lwacm_diagnostics /
+ *     lwacm_get_fields call.
+ *   - Errors are sticky per context: after LWACM_E_CUDA only lwacm_last_error
+ *     and lwacm_destroy are valid.
+ *   - A context is not thread-safe; use one context per host thread.
+ */
+#ifndef LWACM_H
+#define LWACM_H
+
+#include <stddef.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct lwacm_ctx lwacm_ctx; /* opaque; owned by the library */
+
+typedef enum {
+    LWACM_OK = 0,
+    LWACM_E_ARG = 1,         /* bad argument: null pointer, bad lattice/bc/dtype/size */
+    LWACM_E_RANGE = 2,       /* nu outside (0, 1/6], i.e. omega outside [1, 2) */
+    LWACM_E_STATE = 3,       /* call order: e.g. step before bind/set_fields */
+    LWACM_E_NOMEM = 4,       /* the bound workspace is smaller than required */
+    LWACM_E_CUDA = 5,        /* a CUDA runtime error (sticky; see lwacm_last_error) */
+    LWACM_E_NONFINITE = 6,   /* diagnostics found a non-finite field value */
+    LWACM_E_TIMEOUT = 7,     /* a bounded device-side wait gave up */
+    LWACM_E_UNSUPPORTED = 8  /* valid request this build does not implement */
+} lwacm_status;
+
+enum { LWACM_D2Q9 = 9, LWACM_D3Q19 = 19 };
+
+/* Boundary types.
+ *   PERIODIC: every axis periodic (Section 2.5).
+ *   CAVITY:   half-way link-wise walls on every face (Section 2.6, Eq. ACM2.0cccbb2),
+ *             the top face of the last axis (y in 2D, z in 3D) moving with the lid
+ *             velocity through Eq. ACM2.0ccccbb (lid corners take the lid velocity,
+ *             Section 2.6.1).
+ *   CHANNEL:  half-way walls at y = -1/2 and y = ny - 1/2, other axes periodic; the
+ *             top wall moves with the lid velocity (zero by default: Poiseuille
+ *             with a body force, plane Couette with a lid). */
+enum { LWACM_BC_PERIODIC = 0, LWACM_BC_CAVITY = 1, LWACM_BC_CHANNEL = 2 };
+
+/* Element types, for storage and for field transfer. */
+enum { LWACM_F32 = 0, LWACM_BF16 = 1, LWACM_F16 = 2, LWACM_F64 = 3 };
+
+/* Where a transfer buffer lives. */
+enum { LWACM_DEVICE = 0, LWACM_HOST = 1 };
+
+/* Option keys for lwacm_set_option (values are doubles). */
+enum {
+    LWACM_OPT_LID_X = 0,   /* lid / moving-wall velocity u_w (lattice units) */
+    LWACM_OPT_LID_Y = 1,
+    LWACM_OPT_LID_Z = 2,
+    LWACM_OPT_FORCE_X = 3, /* body acceleration g of Eq. force (lattice units) */
+    LWACM_OPT_FORCE_Y = 4,
+    LWACM_OPT_FORCE_Z = 5,
+    LWACM_OPT_RHO0 = 6,    /* rho_0 of the moving-wall term, Eq. ACM2.0movebb (default 1) */
+    LWACM_OPT_STORAGE = 7, /* storage element type: LWACM_F32 (default), BF16, F16;
+                              only before lwacm_bind */
+    LWACM_OPT_GRAPH_CHUNK = 8, /* steps per captured CUDA graph in lwacm_step (even;
+                                  0 disables graphs; default 64) */
+    LWACM_OPT_KERNEL = 9   /* interior kernel: 0 = autotuned choice (default),
+                              1 = generic gather kernel, 2 = tiled kernel */
+};
+
+/* Create a single-domain context.
+ *   lattice: LWACM_D2Q9 or LWACM_D3Q19; nx, ny, nz >= 1 (nz == 1 for D2Q9;
+ *   walled axes need >= 2 nodes); nu: kinematic viscosity in lattice units,
+ *   0 < nu <= 1/6 (the stable range 1 <= omega < 2 of Section 2.3) -> otherwise
+ *   LWACM_E_RANGE; bc: LWACM_BC_*. On success *out receives a new context. No
+ *   device work is done. */
+lwacm_status lwacm_create(int lattice, int nx, int ny, int nz, double nu, int bc,
+                          lwacm_ctx **out);
+
+/* Set an option (LWACM_OPT_*). Storage type changes are refused after bind
+ * (LWACM_E_STATE). */
+lwacm_status lwacm_set_option(lwacm_ctx *ctx, int key, double value);
+
+/* Number of workspace bytes lwacm_bind needs for the current options. */
+lwacm_status lwacm_workspace_bytes(const lwacm_ctx *ctx, size_t *bytes);
+
+/* Bind caller-owned device memory (>= lwacm_workspace_bytes, 256-byte aligned)
+ * and a CUDA stream (cudaStream_t cast to void*, NULL = legacy default stream).
+ * The memory must stay valid until lwacm_destroy or the next bind. Fields are
+ * undefined until lwacm_set_fields. */
+lwacm_status lwacm_bind(lwacm_ctx *ctx, void *dev_workspace, size_t bytes, void *cuda_stream);
+
+/* Copy an initial state in. d, ux, uy, uz are arrays of nx*ny*nz elements of
+ * type dtype (LWACM_F32 or LWACM_F64) on the device or on the host (where =
+ * LWACM_DEVICE / LWACM_HOST; host memory should be pinned for asynchronous
+ * copies). uz must be NULL for D2Q9. The values are rounded once to the storage
+ * type by a device kernel. Resets the step counter. Stream-ordered: host
+ * buffers must stay valid until the stream reaches this point. */
+lwacm_status lwacm_set_fields(lwacm_ctx *ctx, const void *d, const void *ux, const void *uy,
+                              const void *uz, int dtype, int where);
+
+/* Advance the state by n >= 0 time steps of Eq. ACM2.0 (plus the wall pass of
+ * Eqs. ACM2.0cccbb2 / ACM2.0ccccbb and the forcing of Eq. force when enabled).
+ * Asynchronous on the bound stream; long runs are replayed from captured CUDA
+ * graphs. */
+lwacm_status lwacm_step(lwacm_ctx *ctx, long long n);
+
+/* Borrowed device pointers to the current state (zero copy). Valid until the
+ * next lwacm_step / lwacm_set_fields / lwacm_bind / lwacm_destroy. *dtype gets
+ * the storage type, *pitch_elems the row pitch in elements (== nx). uz may be
+ * NULL; *uz is NULL for D2Q9. */
+lwacm_status lwacm_fields(lwacm_ctx *ctx, void **d, void **ux, void **uy, void **uz,
+                          int *dtype, long long *pitch_elems);
+
+/* Copy the current state out, converted by a device kernel to dtype
+ * (LWACM_F32 or LWACM_F64), into device or host arrays (where). Synchronises
+ * the bound stream when where == LWACM_HOST. */
+lwacm_status lwacm_get_fields(lwacm_ctx *ctx, void *d, void *ux, void *uy, void *uz, int dtype,
+                              int where);
+
+/* FP64 global quantities of the current state (Eq. global.quantities):
+ *   out[0] = sum d (mass minus the node count), out[1..3] = sum rho u_a,
+ *   out[4] = 0.5 sum rho |u|^2, out[5] = max |u|, out[6] = 0.5 sum (u+w)^2,
+ *   out[7] = 0.5 sum (u-w)^2 (the M_par / M_perp sums of Eq. 3Dmomenta before
+ *   the volume factor; zero in 2D).
+ * Deterministic two-pass device reduction in FP64; synchronises the stream.
+ * Returns LWACM_E_NONFINITE (and still fills out) if any value is NaN/Inf. */
+lwacm_status lwacm_diagnostics(lwacm_ctx *ctx, double out[8]);
+
+/* Number of completed steps since the last lwacm_set_fields. */
+lwacm_status lwacm_step_count(const lwacm_ctx *ctx, long long *steps);
+
+/* Wait for the bound stream and report any asynchronous CUDA error. */
+lwacm_status lwacm_sync(lwacm_ctx *ctx);
+
+/* Human-readable description of the last error on this context ("" if none).
+ * The string is owned by the context. */
+const char *lwacm_last_error(const lwacm_ctx *ctx);
+
+/* Name of the interior kernel the context runs (for reports). */
+const char *lwacm_kernel_name(const lwacm_ctx *ctx);
+
+/* Release the context (host memory and CUDA graphs). Does not touch the bound
+ * workspace, which belongs to the caller. NULL is allowed. */
+void lwacm_destroy(lwacm_ctx *ctx);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* LWACM_H */

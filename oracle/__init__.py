@@ -34,12 +34,22 @@ def build(force: bool = False) -> str:
     if (not force and os.path.exists(_LIB_PATH)
             and os.path.getmtime(_LIB_PATH) >= os.path.getmtime(_SRC)):
         return _LIB_PATH
+    import fcntl
+    with open(_LIB_PATH + ".lock", "w") as lk:  # one builder at a time (multi-rank)
+        fcntl.flock(lk, fcntl.LOCK_EX)
+        if (not force and os.path.exists(_LIB_PATH)
+                and os.path.getmtime(_LIB_PATH) >= os.path.getmtime(_SRC)):
+            return _LIB_PATH
+        _compile()
+    return _LIB_PATH
+
+
+def _compile():
     tmp = _LIB_PATH + f".tmp{os.getpid()}"
     cmd = ["gcc", "-O3", "-std=c11", "-fopenmp", "-fPIC", "-shared", "-Wall", "-Wextra",
            "-Wno-unused-parameter", _SRC, "-o", tmp, "-lm"]
     subprocess.run(cmd, check=True)
     os.replace(tmp, _LIB_PATH)
-    return _LIB_PATH
 
 
 def _load():

@@ -1,0 +1,354 @@
+// Generic LW-ACM kernels: one thread per node, gathering (d,u) of the Q upwind
+// neighbours through the cache hierarchy. Correct for every lattice, size,
+// storage type and boundary type; the tiled kernels replace the interior update
+// for the shapes they support. Also: the link-wise wall pass, field conversion
+// and the FP64 diagnostics reduction.
+#include <type_traits>
+
+#include "launch.h"
+#include "lwacm_core.cuh"
+
+namespace lwacm {
+
+// Full update of one node (x,y,z). With WALLS, sources beyond a walled face are
+// replaced by the bounce-back rule; without, every axis wraps (periodic).
+template <int Q, bool WALLS, typename T>
+__device__ __forceinline__ void node_update(const T *__restrict__ in, T *__restrict__ out,
+                                            const StepParams &p, int x, int y, int z) {
+    using L = Lat<Q>;
+    const long long k = ((long long)z * p.ny + y) * p.nx + x;
+    const T *Din = in, *Uin = in + p.fstride, *Vin = in + 2 * p.fstride,
+            *Win = in + 3 * p.fstride;
+    const float dx = ldf(Din + k), ux = ldf(Uin + k), uy = ldf(Vin + k);
+    const float uz = (Q == 19) ? ldf(Win + k) : 0.f;
+    const float rx = 1.f + dx;
+    const float qx = fmaf(ux, ux, fmaf(uy, uy, uz * uz));
+    float dd = 0.f, jx = 0.f, jy = 0.f, jz = 0.f;
+#pragma unroll
+    for (int i = 0; i < Q; ++i) {
+        const int cx = L::c(i, 0), cy = L::c(i, 1), cz = L::c(i, 2);
+        int sx = x - cx, sy = y - cy, sz = z - cz;
+        bool outside = false, above = false;
+        if (WALLS) {
+            if (p.walled[0] && (sx < 0 || sx >= p.nx)) outside = true;
+            if (p.walled[1] && (sy < 0 || sy >= p.ny)) outside = true;
+            if (Q == 19 && p.walled[2] && (sz < 0 || sz >= p.nz)) outside = true;
+            const int sl = p.lid_axis == 0 ? sx : (p.lid_axis == 1 ? sy : sz);
+            const int nl = p.lid_axis == 0 ? p.nx : (p.lid_axis == 1 ? p.ny : p.nz);
+            above = outside && sl >= nl;
+        }
+        float g;
+        if (!outside) {
+            sx = sx < 0 ? sx + p.nx : (sx >= p.nx ? sx - p.nx : sx);
+            sy = sy < 0 ? sy + p.ny : (sy >= p.ny ? sy - p.ny : sy);
+            sz = sz < 0 ? sz + p.nz : (sz >= p.nz ? sz - p.nz : sz);
+            const long long s = ((long long)sz * p.ny + sy) * p.nx + sx;
+            const float ds = ldf(Din + s), us = ldf(Uin + s), vs = ldf(Vin + s);
+            const float ws = (Q == 19) ? ldf(Win + s) : 0.f;
+            const float e = cx * us + cy * vs + cz * ws;
+            const float q = fmaf(us, us, fmaf(vs, vs, ws * ws));
+            g = link_g(L::w(i), ds, 1.f + ds, e, q, p.s);
+        } else {
+            // Eq. ACM2.0cccbb2 + Eq. ACM2.0ccccbb: own outgoing BB(i) value, reflected
+            const float e = -(cx * ux + cy * uy + cz * uz);
+            g = link_g(L::w(i), dx, rx, e, qx, p.s);
+            if (above) {
+                const float cu = cx * p.lid[0] + cy * p.lid[1] + cz * p.lid[2];
+                g = fmaf(L::w(i) * p.wallc, cu, g);
+            }
+        }
+        dd += g;
+        if (cx) jx += cx > 0 ? g : -g;
+        if (cy) jy += cy > 0 ? g : -g;
+        if (cz) jz += cz > 0 ? g : -g;
+    }
+    jx = fmaf(p.a * rx, ux, jx);
+    jy = fmaf(p.a * rx, uy, jy);
+    jz = fmaf(p.a * rx, uz, jz);
+    if (p.has_force) {  // Eq. force: the odd part of f^(e)(rho(x,t), g) adds rho g to j
+        jx = fmaf(rx, p.force[0], jx);
+        jy = fmaf(rx, p.force[1], jy);
+        jz = fmaf(rx, p.force[2], jz);
+    }
+    const float rn = 1.f + dd;
+    stf(out + k, dd);
+    stf(out + p.fstride + k, jx / rn);
+    stf(out + 2 * p.fstride + k, jy / rn);
+    if (Q == 19) stf(out + 3 * p.fstride + k, jz / rn);
+}
+
+template <int Q, typename T>
+__global__ void __launch_bounds__(256) k_step_generic(const T *__restrict__ in,
+                                                      T *__restrict__ out, StepParams p) {
+    const long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (idx >= p.N) return;
+    const int x = (int)(idx % p.nx);
+    const long long r = idx / p.nx;
+    const int y = (int)(r % p.ny);
+    const int z = (int)(r / p.ny);
+    node_update<Q, false>(in, out, p, x, y, z);
+}
+
+// Boundary nodes of a walled domain, enumerated without gaps.
+//   cavity 2D: the perimeter of the nx x ny rectangle;
+//   cavity 3D: the planes z = 0 and z = nz-1, then the perimeter of each inner plane;
+//   channel:   rows y = 0 and y = ny-1 of every z plane.
+__host__ __device__ inline long long perimeter(int nx, int ny) {
+    return ny <= 1 ? nx : (nx <= 1 ? ny : 2LL * nx + 2LL * (ny - 2));
+}
+__host__ __device__ inline long long boundary_count(const StepParams &p, int D) {
+    if (p.bc == BC_CHANNEL) return (p.ny <= 1 ? 1LL : 2LL) * p.nx * p.nz;
+    if (D == 2) return perimeter(p.nx, p.ny);
+    if (p.nz <= 2) return (long long)p.nx * p.ny * p.nz;
+    return 2LL * p.nx * p.ny + (long long)(p.nz - 2) * perimeter(p.nx, p.ny);
+}
+__device__ inline void perimeter_node(long long t, int nx, int ny, int &x, int &y) {
+    if (ny <= 1) { x = (int)t; y = 0; return; }
+    if (nx <= 1) { x = 0; y = (int)t; return; }
+    if (t < nx) { x = (int)t; y = 0; return; }
+    t -= nx;
+    if (t < nx) { x = (int)t; y = ny - 1; return; }
+    t -= nx;
+    if (t < ny - 2) { x = 0; y = 1 + (int)t; return; }
+    t -= ny - 2;
+    x = nx - 1;
+    y = 1 + (int)t;
+}
+
+template <int Q, typename T>
+__global__ void __launch_bounds__(256) k_wall_pass(const T *__restrict__ in, T *__restrict__ out,
+                                                   StepParams p, long long nb) {
+    const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= nb) return;
+    int x, y, z;
+    if (p.bc == BC_CHANNEL) {
+        const long long row = t / p.nx;  // 0 .. 2*nz-1
+        x = (int)(t % p.nx);
+        z = (int)(row >> 1);
+        y = (row & 1) ? p.ny - 1 : 0;
+    } else if (Q == 9 || p.nz <= 2) {
+        if (Q == 9) {
+            z = 0;
+            perimeter_node(t, p.nx, p.ny, x, y);
+        } else {  // every node is on the boundary
+            x = (int)(t % p.nx);
+            y = (int)((t / p.nx) % p.ny);
+            z = (int)(t / ((long long)p.nx * p.ny));
+        }
+    } else {
+        const long long plane = (long long)p.nx * p.ny;
+        if (t < 2 * plane) {
+            z = t < plane ? 0 : p.nz - 1;
+            const long long r = t < plane ? t : t - plane;
+            x = (int)(r % p.nx);
+            y = (int)(r / p.nx);
+        } else {
+            const long long per = perimeter(p.nx, p.ny);
+            const long long r = t - 2 * plane;
+            z = 1 + (int)(r / per);
+            perimeter_node(r % per, p.nx, p.ny, x, y);
+        }
+    }
+    node_update<Q, true>(in, out, p, x, y, z);
+}
+
+// storage -> double needs the exact stored value, converted without rounding
+template <typename T>
+__global__ void k_to_f64(const T *__restrict__ in, double *__restrict__ out, long long n) {
+    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+         i += (long long)gridDim.x * blockDim.x)
+        out[i] = (double)ldf(in + i);
+}
+template <typename T>
+__global__ void k_to_f32(const T *__restrict__ in, float *__restrict__ out, long long n) {
+    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+         i += (long long)gridDim.x * blockDim.x)
+        out[i] = ldf(in + i);
+}
+template <typename Ti, typename T>
+__global__ void k_from(const Ti *__restrict__ in, T *__restrict__ out, long long n) {
+    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+         i += (long long)gridDim.x * blockDim.x) {
+        if constexpr (sizeof(Ti) == 8) {
+            // round once from FP64 to the storage type
+            if constexpr (sizeof(T) == 4)
+                out[i] = __double2float_rn(in[i]);
+            else if constexpr (std::is_same<T, __half>::value)
+                out[i] = __double2half(in[i]);
+            else
+                out[i] = __double2bfloat16(in[i]);
+        } else {
+            stf(out + i, in[i]);
+        }
+    }
+}
+
+// ---- FP64 diagnostics: per-block partials, then one block in fixed order ------
+constexpr int kDiagVals = 9;  // mass, jx, jy, jz, ke, max|u|^2, mpar, mperp, nonfinite
+
+template <typename T>
+__global__ void __launch_bounds__(256) k_diag_partial(const T *__restrict__ f, long long fstride,
+                                                      long long N, int has_z,
+                                                      double *__restrict__ partial) {
+    double acc[kDiagVals] = {0, 0, 0, 0, 0, 0, 0, 0, 0};
+    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < N;
+         i += (long long)gridDim.x * blockDim.x) {
+        const double d = ldf(f + i), u = ldf(f + fstride + i), v = ldf(f + 2 * fstride + i);
+        const double w = has_z ? (double)ldf(f + 3 * fstride + i) : 0.0;
+        const double rho = 1.0 + d, uu = u * u + v * v + w * w;
+        acc[0] += d;
+        acc[1] += rho * u;
+        acc[2] += rho * v;
+        acc[3] += rho * w;
+        acc[4] += 0.5 * rho * uu;
+        acc[5] = fmax(acc[5], uu);
+        if (has_z) {
+            acc[6] += 0.5 * (u + w) * (u + w);
+            acc[7] += 0.5 * (u - w) * (u - w);
+        }
+        if (!isfinite(d) || !isfinite(uu)) acc[8] += 1.0;
+    }
+    __shared__ double sh[kDiagVals][256];
+    for (int v = 0; v < kDiagVals; ++v) sh[v][threadIdx.x] = acc[v];
+    __syncthreads();
+    for (int off = blockDim.x / 2; off > 0; off >>= 1) {
+        if (threadIdx.x < off)
+            for (int v = 0; v < kDiagVals; ++v) {
+                const double o = sh[v][threadIdx.x + off];
+                sh[v][threadIdx.x] = (v == 5) ? fmax(sh[v][threadIdx.x], o) : sh[v][threadIdx.x] + o;
+            }
+        __syncthreads();
+    }
+    if (threadIdx.x < kDiagVals) partial[(long long)blockIdx.x * kDiagVals + threadIdx.x] = sh[threadIdx.x][0];
+}
+
+__global__ void k_diag_final(const double *__restrict__ partial, int nblocks, double *__restrict__ out) {
+    __shared__ double sh[kDiagVals][256];
+    double acc[kDiagVals] = {0, 0, 0, 0, 0, 0, 0, 0, 0};
+    for (int b = threadIdx.x; b < nblocks; b += blockDim.x)
+        for (int v = 0; v < kDiagVals; ++v) {
+            const double o = partial[(long long)b * kDiagVals + v];
+            acc[v] = (v == 5) ? fmax(acc[v], o) : acc[v] + o;
+        }
+    for (int v = 0; v < kDiagVals; ++v) sh[v][threadIdx.x] = acc[v];
+    __syncthreads();
+    for (int off = blockDim.x / 2; off > 0; off >>= 1) {
+        if (threadIdx.x < off)
+            for (int v = 0; v < kDiagVals; ++v) {
+                const double o = sh[v][threadIdx.x + off];
+                sh[v][threadIdx.x] = (v == 5) ? fmax(sh[v][threadIdx.x], o) : sh[v][threadIdx.x] + o;
+            }
+        __syncthreads();
+    }
+    if (threadIdx.x < kDiagVals) out[threadIdx.x] = sh[threadIdx.x][0];
+}
+
+// ---- host launchers ---------------------------------------------------------
+static inline unsigned blocks_for(long long n, int tpb) { return (unsigned)((n + tpb - 1) / tpb); }
+
+template <typename T>
+cudaError_t launch_step_generic_t(int Q, const void *in, void *out, const StepParams &p,
+                                  cudaStream_t st) {
+    const unsigned nb = blocks_for(p.N, 256);
+    if (Q == 9)
+        k_step_generic<9, T><<<nb, 256, 0, st>>>((const T *)in, (T *)out, p);
+    else
+        k_step_generic<19, T><<<nb, 256, 0, st>>>((const T *)in, (T *)out, p);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_step_generic(int Q, int storage, const void *in, void *out,
+                                const StepParams &p, cudaStream_t st) {
+    switch (storage) {
+        case STORE_F32: return launch_step_generic_t<float>(Q, in, out, p, st);
+        case STORE_BF16: return launch_step_generic_t<__nv_bfloat16>(Q, in, out, p, st);
+        case STORE_F16: return launch_step_generic_t<__half>(Q, in, out, p, st);
+    }
+    return cudaErrorInvalidValue;
+}
+
+template <typename T>
+cudaError_t launch_wall_t(int Q, const void *in, void *out, const StepParams &p, cudaStream_t st) {
+    const long long nb = boundary_count(p, Q == 9 ? 2 : 3);
+    if (nb <= 0) return cudaSuccess;
+    if (Q == 9)
+        k_wall_pass<9, T><<<blocks_for(nb, 256), 256, 0, st>>>((const T *)in, (T *)out, p, nb);
+    else
+        k_wall_pass<19, T><<<blocks_for(nb, 256), 256, 0, st>>>((const T *)in, (T *)out, p, nb);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_wall_pass(int Q, int storage, const void *in, void *out, const StepParams &p,
+                             cudaStream_t st) {
+    switch (storage) {
+        case STORE_F32: return launch_wall_t<float>(Q, in, out, p, st);
+        case STORE_BF16: return launch_wall_t<__nv_bfloat16>(Q, in, out, p, st);
+        case STORE_F16: return launch_wall_t<__half>(Q, in, out, p, st);
+    }
+    return cudaErrorInvalidValue;
+}
+
+static unsigned conv_blocks(long long n) {
+    const long long b = (n + 255) / 256;
+    return (unsigned)(b < 152 * 16 ? (b < 1 ? 1 : b) : 152 * 16);
+}
+
+template <typename T>
+static cudaError_t from_t(int src_dtype, const void *src, void *dst, long long n, cudaStream_t st) {
+    if (src_dtype == XFER_F64)
+        k_from<double, T><<<conv_blocks(n), 256, 0, st>>>((const double *)src, (T *)dst, n);
+    else
+        k_from<float, T><<<conv_blocks(n), 256, 0, st>>>((const float *)src, (T *)dst, n);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_convert_in(int storage, int src_dtype, const void *src, void *dst, long long n,
+                              cudaStream_t st) {
+    switch (storage) {
+        case STORE_F32: return from_t<float>(src_dtype, src, dst, n, st);
+        case STORE_BF16: return from_t<__nv_bfloat16>(src_dtype, src, dst, n, st);
+        case STORE_F16: return from_t<__half>(src_dtype, src, dst, n, st);
+    }
+    return cudaErrorInvalidValue;
+}
+
+template <typename T>
+static cudaError_t to_t(int dst_dtype, const void *src, void *dst, long long n, cudaStream_t st) {
+    if (dst_dtype == XFER_F64)
+        k_to_f64<T><<<conv_blocks(n), 256, 0, st>>>((const T *)src, (double *)dst, n);
+    else
+        k_to_f32<T><<<conv_blocks(n), 256, 0, st>>>((const T *)src, (float *)dst, n);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_convert_out(int storage, int dst_dtype, const void *src, void *dst, long long n,
+                               cudaStream_t st) {
+    switch (storage) {
+        case STORE_F32: return to_t<float>(dst_dtype, src, dst, n, st);
+        case STORE_BF16: return to_t<__nv_bfloat16>(dst_dtype, src, dst, n, st);
+        case STORE_F16: return to_t<__half>(dst_dtype, src, dst, n, st);
+    }
+    return cudaErrorInvalidValue;
+}
+
+template <typename T>
+static cudaError_t diag_t(const void *f, long long fstride, long long N, int has_z, double *partial,
+                          double *out, cudaStream_t st) {
+    k_diag_partial<T><<<kDiagBlocks, 256, 0, st>>>((const T *)f, fstride, N, has_z, partial);
+    k_diag_final<<<1, 256, 0, st>>>(partial, kDiagBlocks, out);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_diagnostics(int storage, const void *f, long long fstride, long long N,
+                               int has_z, double *partial, double *out, cudaStream_t st) {
+    switch (storage) {
+        case STORE_F32: return diag_t<float>(f, fstride, N, has_z, partial, out, st);
+        case STORE_BF16: return diag_t<__nv_bfloat16>(f, fstride, N, has_z, partial, out, st);
+        case STORE_F16: return diag_t<__half>(f, fstride, N, has_z, partial, out, st);
+    }
+    return cudaErrorInvalidValue;
+}
+
+long long wall_node_count(const StepParams &p, int Q) { return boundary_count(p, Q == 9 ? 2 : 3); }
+
+}  // namespace lwacm

@@ -1,0 +1,441 @@
+// C-ABI implementation (include/lwacm.h): context, validation, workspace
+// layout, field transfer, stepping (with captured CUDA graphs) and diagnostics.
+#include <cuda_runtime.h>
+
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <new>
+#include <string>
+
+#include "../../include/lwacm.h"
+#include "launch.h"
+#include "lwacm_core.cuh"
+
+using namespace lwacm;
+
+namespace {
+
+constexpr size_t kAlign = 256;
+inline size_t align_up(size_t v, size_t a) { return (v + a - 1) / a * a; }
+inline int esize(int storage) { return storage == LWACM_F32 ? 4 : 2; }
+
+}  // namespace
+
+struct lwacm_ctx {
+    int Q = 0, D = 0, nx = 0, ny = 0, nz = 0, bc = 0, nf = 0;
+    double nu = 0;
+    long long N = 0, Nal = 0;
+    double lid[3] = {0, 0, 0}, force[3] = {0, 0, 0}, rho0 = 1.0;
+    int storage = LWACM_F32;
+    int graph_chunk = 64;
+    int kernel_opt = 0;
+    // workspace
+    char *ws = nullptr;
+    size_t ws_bytes = 0;
+    size_t off_buf[2] = {0, 0}, off_stage = 0, off_partial = 0, off_diag = 0, total = 0;
+    cudaStream_t stream = nullptr;
+    bool bound = false, has_fields = false;
+    int cur = 0;
+    long long steps = 0;
+    // status
+    lwacm_status sticky = LWACM_OK;
+    std::string err;
+    // graphs: one per starting buffer parity
+    cudaStream_t cap_stream = nullptr;
+    cudaGraphExec_t gexec[2] = {nullptr, nullptr};
+    int gchunk[2] = {0, 0};
+    bool use_tiled = false;
+    std::string kname = "none";
+};
+
+namespace {
+
+lwacm_status fail(lwacm_ctx *c, lwacm_status s, const std::string &msg) {
+    if (c) {
+        c->err = msg;
+        if (s == LWACM_E_CUDA || s == LWACM_E_TIMEOUT) c->sticky = s;
+    }
+    return s;
+}
+
+lwacm_status cuda_fail(lwacm_ctx *c, cudaError_t e, const char *where) {
+    return fail(c, LWACM_E_CUDA, std::string(where) + ": " + cudaGetErrorName(e) + " (" +
+                                     cudaGetErrorString(e) + ")");
+}
+
+#define CK(ctx, call, where)                                  \
+    do {                                                      \
+        cudaError_t e_ = (call);                              \
+        if (e_ != cudaSuccess) return cuda_fail(ctx, e_, where); \
+    } while (0)
+
+void layout(lwacm_ctx *c) {
+    const size_t fbytes = (size_t)c->Nal * esize(c->storage);
+    size_t off = 0;
+    for (int b = 0; b < 2; ++b) {
+        c->off_buf[b] = off;
+        off = align_up(off + fbytes * c->nf, kAlign);
+    }
+    c->off_stage = off;
+    off = align_up(off + (size_t)c->Nal * 8, kAlign);
+    c->off_partial = off;
+    off = align_up(off + (size_t)kDiagBlocks * kDiagValues * 8, kAlign);
+    c->off_diag = off;
+    off = align_up(off + 16 * 8, kAlign);
+    c->total = off;
+}
+
+StepParams params(const lwacm_ctx *c) {
+    StepParams p;
+    memset(&p, 0, sizeof(p));
+    p.nx = c->nx;
+    p.ny = c->ny;
+    p.nz = c->nz;
+    p.bc = c->bc;
+    p.N = c->N;
+    p.fstride = c->Nal;
+    // Eq. viscosity2 / Eq. ACM2.0nu: a = 2(omega-1)/omega = 1 - 6 nu; s = 3(1-a) = 18 nu
+    p.s = (float)(18.0 * c->nu);
+    p.a = (float)(1.0 - 6.0 * c->nu);
+    // Eq. ACM2.0ccccbb: (2/omega - 1) * 2 f^(e,o)(rho0, u_w) = 6 nu * 2 * 3 w rho0 (c.u_w)
+    p.wallc = (float)(36.0 * c->nu * c->rho0);
+    for (int a = 0; a < 3; ++a) {
+        p.lid[a] = (float)c->lid[a];
+        p.force[a] = (float)c->force[a];
+    }
+    p.has_force = (c->force[0] != 0 || c->force[1] != 0 || c->force[2] != 0) ? 1 : 0;
+    p.walled[0] = p.walled[1] = p.walled[2] = 0;
+    p.lid_axis = c->D - 1;
+    if (c->bc == LWACM_BC_CAVITY) {
+        for (int a = 0; a < c->D; ++a) p.walled[a] = 1;
+    } else if (c->bc == LWACM_BC_CHANNEL) {
+        p.walled[1] = 1;
+        p.lid_axis = 1;
+    }
+    return p;
+}
+
+void drop_graphs(lwacm_ctx *c) {
+    for (int k = 0; k < 2; ++k) {
+        if (c->gexec[k]) cudaGraphExecDestroy(c->gexec[k]);
+        c->gexec[k] = nullptr;
+        c->gchunk[k] = 0;
+    }
+}
+
+void choose_kernel(lwacm_ctx *c) {
+    const StepParams p = params(c);
+    const bool ok = c->bc == LWACM_BC_PERIODIC && tiled_supported(c->Q, c->storage, p);
+    c->use_tiled = (c->kernel_opt == 2 || c->kernel_opt == 0) && ok;
+    c->kname = c->use_tiled ? tiled_name(c->Q) : (c->Q == 9 ? "generic_d2q9" : "generic_d3q19");
+}
+
+void *bufp(lwacm_ctx *c, int b) { return c->ws + c->off_buf[b]; }
+
+size_t field_bytes(const lwacm_ctx *c) { return (size_t)c->Nal * esize(c->storage); }
+
+// enqueue one time step: buffer cur -> buffer 1-cur
+cudaError_t enqueue_step(lwacm_ctx *c, int cur, cudaStream_t st) {
+    const StepParams p = params(c);
+    const void *in = bufp(c, cur);
+    void *out = bufp(c, 1 - cur);
+    cudaError_t e = c->use_tiled ? launch_step_tiled(c->Q, c->storage, in, out, p, st)
+                                 : launch_step_generic(c->Q, c->storage, in, out, p, st);
+    if (e != cudaSuccess) return e;
+    if (c->bc != LWACM_BC_PERIODIC) e = launch_wall_pass(c->Q, c->storage, in, out, p, st);
+    return e;
+}
+
+lwacm_status ready(lwacm_ctx *c, bool need_fields) {
+    if (!c) return LWACM_E_ARG;
+    if (c->sticky != LWACM_OK) return c->sticky;
+    if (!c->bound) return fail(c, LWACM_E_STATE, "no workspace bound (call lwacm_bind)");
+    if (need_fields && !c->has_fields)
+        return fail(c, LWACM_E_STATE, "fields not initialised (call lwacm_set_fields)");
+    return LWACM_OK;
+}
+
+lwacm_status build_graph(lwacm_ctx *c, int parity, int chunk) {
+    if (!c->cap_stream) CK(c, cudaStreamCreateWithFlags(&c->cap_stream, cudaStreamNonBlocking), "stream create");
+    CK(c, cudaStreamBeginCapture(c->cap_stream, cudaStreamCaptureModeThreadLocal), "begin capture");
+    int cur = parity;
+    cudaError_t le = cudaSuccess;
+    for (int k = 0; k < chunk && le == cudaSuccess; ++k) {
+        le = enqueue_step(c, cur, c->cap_stream);
+        cur ^= 1;
+    }
+    cudaGraph_t g = nullptr;
+    cudaError_t ee = cudaStreamEndCapture(c->cap_stream, &g);
+    if (le != cudaSuccess) {
+        if (g) cudaGraphDestroy(g);
+        return cuda_fail(c, le, "capture launch");
+    }
+    if (ee != cudaSuccess) return cuda_fail(c, ee, "end capture");
+    cudaGraphExec_t ex = nullptr;
+    cudaError_t ie = cudaGraphInstantiate(&ex, g, 0);
+    cudaGraphDestroy(g);
+    if (ie != cudaSuccess) return cuda_fail(c, ie, "graph instantiate");
+    c->gexec[parity] = ex;
+    c->gchunk[parity] = chunk;
+    return LWACM_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+lwacm_status lwacm_create(int lattice, int nx, int ny, int nz, double nu, int bc,
+                          lwacm_ctx **out) {
+    if (!out) return LWACM_E_ARG;
+    *out = nullptr;
+    if (lattice != LWACM_D2Q9 && lattice != LWACM_D3Q19) return LWACM_E_ARG;
+    if (bc != LWACM_BC_PERIODIC && bc != LWACM_BC_CAVITY && bc != LWACM_BC_CHANNEL)
+        return LWACM_E_ARG;
+    if (nx < 1 || ny < 1 || nz < 1) return LWACM_E_ARG;
+    if (lattice == LWACM_D2Q9 && nz != 1) return LWACM_E_ARG;
+    if (bc == LWACM_BC_CAVITY && (nx < 2 || ny < 2 || (lattice == LWACM_D3Q19 && nz < 2)))
+        return LWACM_E_ARG;
+    if (bc == LWACM_BC_CHANNEL && ny < 2) return LWACM_E_ARG;
+    if ((long long)nx * ny * nz > (1LL << 40)) return LWACM_E_ARG;
+    // Section 2.3: stable for 1 <= omega < 2, i.e. 0 < nu <= 1/6 (Eq. viscosity2)
+    if (!(nu > 0.0) || !(nu <= 1.0 / 6.0 + 1e-15) || !std::isfinite(nu)) return LWACM_E_RANGE;
+    lwacm_ctx *c = new (std::nothrow) lwacm_ctx();
+    if (!c) return LWACM_E_NOMEM;
+    c->Q = lattice;
+    c->D = lattice == LWACM_D2Q9 ? 2 : 3;
+    c->nx = nx;
+    c->ny = ny;
+    c->nz = nz;
+    c->bc = bc;
+    c->nu = nu;
+    c->nf = c->D + 1;
+    c->N = (long long)nx * ny * nz;
+    c->Nal = (long long)align_up((size_t)c->N, 64);
+    layout(c);
+    choose_kernel(c);
+    *out = c;
+    return LWACM_OK;
+}
+
+lwacm_status lwacm_set_option(lwacm_ctx *c, int key, double v) {
+    if (!c) return LWACM_E_ARG;
+    if (c->sticky != LWACM_OK) return c->sticky;
+    if (!std::isfinite(v)) return fail(c, LWACM_E_ARG, "non-finite option value");
+    switch (key) {
+        case LWACM_OPT_LID_X: case LWACM_OPT_LID_Y: case LWACM_OPT_LID_Z:
+            c->lid[key - LWACM_OPT_LID_X] = v;
+            break;
+        case LWACM_OPT_FORCE_X: case LWACM_OPT_FORCE_Y: case LWACM_OPT_FORCE_Z:
+            c->force[key - LWACM_OPT_FORCE_X] = v;
+            break;
+        case LWACM_OPT_RHO0:
+            if (!(v > 0)) return fail(c, LWACM_E_ARG, "rho0 must be > 0");
+            c->rho0 = v;
+            break;
+        case LWACM_OPT_STORAGE: {
+            const int s = (int)v;
+            if (s != LWACM_F32 && s != LWACM_BF16 && s != LWACM_F16)
+                return fail(c, LWACM_E_ARG, "storage must be F32, BF16 or F16");
+            if (c->bound) return fail(c, LWACM_E_STATE, "storage type is fixed once bound");
+            c->storage = s;
+            layout(c);
+            break;
+        }
+        case LWACM_OPT_GRAPH_CHUNK: {
+            const int g = (int)v;
+            if (g < 0 || (g & 1) || g > 100000)
+                return fail(c, LWACM_E_ARG, "graph chunk must be even, >= 0");
+            c->graph_chunk = g;
+            break;
+        }
+        case LWACM_OPT_KERNEL: {
+            const int k = (int)v;
+            if (k < 0 || k > 2) return fail(c, LWACM_E_ARG, "kernel must be 0, 1 or 2");
+            c->kernel_opt = k;
+            break;
+        }
+        default:
+            return fail(c, LWACM_E_ARG, "unknown option key");
+    }
+    choose_kernel(c);
+    if (c->kernel_opt == 2 && !c->use_tiled && key == LWACM_OPT_KERNEL) {
+        c->kernel_opt = 0;
+        choose_kernel(c);
+        return fail(c, LWACM_E_UNSUPPORTED, "tiled kernel does not support this shape/boundary");
+    }
+    drop_graphs(c);
+    return LWACM_OK;
+}
+
+lwacm_status lwacm_workspace_bytes(const lwacm_ctx *c, size_t *bytes) {
+    if (!c || !bytes) return LWACM_E_ARG;
+    *bytes = c->total;
+    return LWACM_OK;
+}
+
+lwacm_status lwacm_bind(lwacm_ctx *c, void *ws, size_t bytes, void *stream) {
+    if (!c) return LWACM_E_ARG;
+    if (c->sticky != LWACM_OK) return c->sticky;
+    if (!ws) return fail(c, LWACM_E_ARG, "null workspace");
+    if (((uintptr_t)ws) % kAlign) return fail(c, LWACM_E_ARG, "workspace not 256-byte aligned");
+    if (bytes < c->total) return fail(c, LWACM_E_NOMEM, "workspace smaller than lwacm_workspace_bytes");
+    drop_graphs(c);
+    c->ws = (char *)ws;
+    c->ws_bytes = bytes;
+    c->stream = (cudaStream_t)stream;
+    c->bound = true;
+    c->has_fields = false;
+    c->cur = 0;
+    c->steps = 0;
+    return LWACM_OK;
+}
+
+lwacm_status lwacm_set_fields(lwacm_ctx *c, const void *d, const void *ux, const void *uy,
+                              const void *uz, int dtype, int where) {
+    lwacm_status s = ready(c, false);
+    if (s != LWACM_OK) return s;
+    if (!d || !ux || !uy || (c->Q == 19 && !uz) || (c->Q == 9 && uz))
+        return fail(c, LWACM_E_ARG, "field pointers: d, ux, uy required; uz iff D3Q19");
+    if (dtype != LWACM_F32 && dtype != LWACM_F64) return fail(c, LWACM_E_ARG, "dtype must be F32 or F64");
+    if (where != LWACM_DEVICE && where != LWACM_HOST) return fail(c, LWACM_E_ARG, "bad location");
+    const void *src[4] = {d, ux, uy, uz};
+    const size_t sb = dtype == LWACM_F64 ? 8 : 4;
+    const size_t nbytes = (size_t)c->N * sb;
+    c->cur = 0;
+    char *dst = (char *)bufp(c, 0);
+    for (int f = 0; f < c->nf; ++f) {
+        char *fd = dst + (size_t)f * field_bytes(c);
+        if (where == LWACM_HOST && dtype == LWACM_F32 && c->storage == LWACM_F32) {
+            CK(c, cudaMemcpyAsync(fd, src[f], nbytes, cudaMemcpyHostToDevice, c->stream), "H2D");
+            continue;
+        }
+        const void *dsrc = src[f];
+        if (where == LWACM_HOST) {
+            CK(c, cudaMemcpyAsync(c->ws + c->off_stage, src[f], nbytes, cudaMemcpyHostToDevice, c->stream),
+               "H2D stage");
+            dsrc = c->ws + c->off_stage;
+        }
+        CK(c, launch_convert_in(c->storage, dtype, dsrc, fd, c->N, c->stream), "convert in");
+    }
+    c->has_fields = true;
+    c->steps = 0;
+    return LWACM_OK;
+}
+
+lwacm_status lwacm_step(lwacm_ctx *c, long long n) {
+    lwacm_status s = ready(c, true);
+    if (s != LWACM_OK) return s;
+    if (n < 0) return fail(c, LWACM_E_ARG, "negative step count");
+    long long left = n;
+    const int chunk = c->graph_chunk;
+    if (chunk > 0 && left >= chunk) {
+        // graphs are replayed on the bound stream; capture needs a private stream
+        const int par = c->cur;
+        if (!c->gexec[par] || c->gchunk[par] != chunk) {
+            if (c->gexec[par]) {
+                cudaGraphExecDestroy(c->gexec[par]);
+                c->gexec[par] = nullptr;
+            }
+            s = build_graph(c, par, chunk);
+            if (s != LWACM_OK) return s;
+        }
+        while (left >= chunk) {
+            CK(c, cudaGraphLaunch(c->gexec[par], c->stream), "graph launch");
+            left -= chunk;
+            c->steps += chunk;  // chunk is even: parity unchanged
+        }
+    }
+    for (; left > 0; --left) {
+        CK(c, enqueue_step(c, c->cur, c->stream), "step launch");
+        c->cur ^= 1;
+        c->steps += 1;
+    }
+    return LWACM_OK;
+}
+
+lwacm_status lwacm_fields(lwacm_ctx *c, void **d, void **ux, void **uy, void **uz, int *dtype,
+                          long long *pitch) {
+    lwacm_status s = ready(c, true);
+    if (s != LWACM_OK) return s;
+    char *b = (char *)bufp(c, c->cur);
+    const size_t fb = field_bytes(c);
+    if (d) *d = b;
+    if (ux) *ux = b + fb;
+    if (uy) *uy = b + 2 * fb;
+    if (uz) *uz = c->Q == 19 ? b + 3 * fb : nullptr;
+    if (dtype) *dtype = c->storage;
+    if (pitch) *pitch = c->nx;
+    return LWACM_OK;
+}
+
+lwacm_status lwacm_get_fields(lwacm_ctx *c, void *d, void *ux, void *uy, void *uz, int dtype,
+                              int where) {
+    lwacm_status s = ready(c, true);
+    if (s != LWACM_OK) return s;
+    if (!d || !ux || !uy || (c->Q == 19 && !uz))
+        return fail(c, LWACM_E_ARG, "field pointers: d, ux, uy required; uz for D3Q19");
+    if (dtype != LWACM_F32 && dtype != LWACM_F64) return fail(c, LWACM_E_ARG, "dtype must be F32 or F64");
+    if (where != LWACM_DEVICE && where != LWACM_HOST) return fail(c, LWACM_E_ARG, "bad location");
+    void *dst[4] = {d, ux, uy, uz};
+    const size_t nbytes = (size_t)c->N * (dtype == LWACM_F64 ? 8 : 4);
+    const char *b = (const char *)bufp(c, c->cur);
+    for (int f = 0; f < c->nf; ++f) {
+        const char *fs = b + (size_t)f * field_bytes(c);
+        if (where == LWACM_HOST && dtype == LWACM_F32 && c->storage == LWACM_F32) {
+            CK(c, cudaMemcpyAsync(dst[f], fs, nbytes, cudaMemcpyDeviceToHost, c->stream), "D2H");
+            continue;
+        }
+        void *ddst = where == LWACM_HOST ? (void *)(c->ws + c->off_stage) : dst[f];
+        CK(c, launch_convert_out(c->storage, dtype, fs, ddst, c->N, c->stream), "convert out");
+        if (where == LWACM_HOST)
+            CK(c, cudaMemcpyAsync(dst[f], ddst, nbytes, cudaMemcpyDeviceToHost, c->stream), "D2H stage");
+    }
+    if (where == LWACM_HOST) CK(c, cudaStreamSynchronize(c->stream), "sync");
+    return LWACM_OK;
+}
+
+lwacm_status lwacm_diagnostics(lwacm_ctx *c, double out[8]) {
+    lwacm_status s = ready(c, true);
+    if (s != LWACM_OK) return s;
+    if (!out) return fail(c, LWACM_E_ARG, "null output");
+    double *partial = (double *)(c->ws + c->off_partial);
+    double *res = (double *)(c->ws + c->off_diag);
+    CK(c, launch_diagnostics(c->storage, bufp(c, c->cur), c->Nal, c->N, c->Q == 19 ? 1 : 0,
+                             partial, res, c->stream),
+       "diagnostics");
+    double h[kDiagValues];
+    CK(c, cudaMemcpyAsync(h, res, sizeof(h), cudaMemcpyDeviceToHost, c->stream), "D2H diag");
+    CK(c, cudaStreamSynchronize(c->stream), "sync");
+    for (int k = 0; k < 8; ++k) out[k] = h[k];
+    out[5] = std::sqrt(h[5]);
+    if (h[8] != 0.0) return fail(c, LWACM_E_NONFINITE, "non-finite values in the fields");
+    return LWACM_OK;
+}
+
+lwacm_status lwacm_step_count(const lwacm_ctx *c, long long *steps) {
+    if (!c || !steps) return LWACM_E_ARG;
+    *steps = c->steps;
+    return LWACM_OK;
+}
+
+lwacm_status lwacm_sync(lwacm_ctx *c) {
+    lwacm_status s = ready(c, false);
+    if (s != LWACM_OK) return s;
+    CK(c, cudaStreamSynchronize(c->stream), "sync");
+    CK(c, cudaGetLastError(), "async error");
+    return LWACM_OK;
+}
+
+const char *lwacm_last_error(const lwacm_ctx *c) { return c ? c->err.c_str() : "null context"; }
+
+const char *lwacm_kernel_name(const lwacm_ctx *c) { return c ? c->kname.c_str() : ""; }
+
+void lwacm_destroy(lwacm_ctx *c) {
+    if (!c) return;
+    drop_graphs(c);
+    if (c->cap_stream) cudaStreamDestroy(c->cap_stream);
+    delete c;
+}
+
+}  // extern "C"

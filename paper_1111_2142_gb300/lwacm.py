@@ -1,0 +1,245 @@
+"""Thin ctypes binding of the C ABI in include/lwacm.h.
+
+Argument marshalling only: every step of the LW-ACM path runs in the CUDA
+library. PyTorch provides device memory (the workspace) and the stream. There
+is no CPU fallback: loading fails loudly if liblwacm.so is missing.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "liblwacm.so")
+
+# constants mirrored from include/lwacm.h
+OK, E_ARG, E_RANGE, E_STATE, E_NOMEM, E_CUDA, E_NONFINITE, E_TIMEOUT, E_UNSUPPORTED = range(9)
+D2Q9, D3Q19 = 9, 19
+PERIODIC, CAVITY, CHANNEL = 0, 1, 2
+F32, BF16, F16, F64 = 0, 1, 2, 3
+DEVICE, HOST = 0, 1
+OPT_LID_X, OPT_LID_Y, OPT_LID_Z, OPT_FORCE_X, OPT_FORCE_Y, OPT_FORCE_Z = range(6)
+OPT_RHO0, OPT_STORAGE, OPT_GRAPH_CHUNK, OPT_KERNEL = 6, 7, 8, 9
+
+STATUS_NAMES = {OK: "OK", E_ARG: "E_ARG", E_RANGE: "E_RANGE", E_STATE: "E_STATE",
+                E_NOMEM: "E_NOMEM", E_CUDA: "E_CUDA", E_NONFINITE: "E_NONFINITE",
+                E_TIMEOUT: "E_TIMEOUT", E_UNSUPPORTED: "E_UNSUPPORTED"}
+
+_lib = None
+
+
+class LwacmError(RuntimeError):
+    def __init__(self, status, msg=""):
+        super().__init__(f"{STATUS_NAMES.get(status, status)}: {msg}")
+        self.status = status
+
+
+def load():
+    """Load liblwacm.so (built by __graft_entry__.build()); raise if it is missing."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(LIB_PATH):
+        raise RuntimeError(f"CUDA library not built: {LIB_PATH} is missing "
+                           "(run __graft_entry__.build()); there is no CPU fallback")
+    lib = ctypes.CDLL(LIB_PATH)
+    vp, i, d, ll = ctypes.c_void_p, ctypes.c_int, ctypes.c_double, ctypes.c_longlong
+    P = ctypes.POINTER
+    sig = {
+        "lwacm_create": [i, i, i, i, d, i, P(vp)],
+        "lwacm_set_option": [vp, i, d],
+        "lwacm_workspace_bytes": [vp, P(ctypes.c_size_t)],
+        "lwacm_bind": [vp, vp, ctypes.c_size_t, vp],
+        "lwacm_set_fields": [vp, vp, vp, vp, vp, i, i],
+        "lwacm_step": [vp, ll],
+        "lwacm_fields": [vp, P(vp), P(vp), P(vp), P(vp), P(i), P(ll)],
+        "lwacm_get_fields": [vp, vp, vp, vp, vp, i, i],
+        "lwacm_diagnostics": [vp, P(d)],
+        "lwacm_step_count": [vp, P(ll)],
+        "lwacm_sync": [vp],
+    }
+    for name, args in sig.items():
+        fn = getattr(lib, name)
+        fn.argtypes = args
+        fn.restype = ctypes.c_int
+    lib.lwacm_last_error.argtypes = [vp]
+    lib.lwacm_last_error.restype = ctypes.c_char_p
+    lib.lwacm_kernel_name.argtypes = [vp]
+    lib.lwacm_kernel_name.restype = ctypes.c_char_p
+    lib.lwacm_destroy.argtypes = [vp]
+    lib.lwacm_destroy.restype = None
+    _lib = lib
+    return lib
+
+
+def _torch():
+    import torch
+    return torch
+
+
+def _ptr(x):
+    """Device or host address of a torch tensor / numpy array (None -> NULL)."""
+    if x is None:
+        return None
+    if isinstance(x, np.ndarray):
+        return x.ctypes.data
+    return x.data_ptr()
+
+
+class Lwacm:
+    """One LW-ACM domain on the current CUDA device.
+
+    Wraps lwacm_create / lwacm_set_option / lwacm_bind; the workspace is a torch
+    uint8 tensor owned by this object and the stream is torch's current stream
+    (or the one given).
+    """
+
+    def __init__(self, lattice, nx, ny, nz=1, nu=0.01, bc=PERIODIC, *, storage=F32, lid=None,
+                 force=None, rho0=None, kernel=0, graph_chunk=None, device=None, stream=None):
+        torch = _torch()
+        lib = load()
+        self._lib = lib
+        self.lattice, self.nx, self.ny, self.nz = int(lattice), int(nx), int(ny), int(nz)
+        self.nu, self.bc = float(nu), int(bc)
+        h = ctypes.c_void_p()
+        st = lib.lwacm_create(self.lattice, self.nx, self.ny, self.nz, self.nu, self.bc,
+                              ctypes.byref(h))
+        if st != OK:
+            raise LwacmError(st, "lwacm_create")
+        self._h = h
+        try:
+            if storage != F32:
+                self._check(lib.lwacm_set_option(h, OPT_STORAGE, float(storage)))
+            for k, vec in ((OPT_LID_X, lid), (OPT_FORCE_X, force)):
+                if vec is not None:
+                    for a, v in enumerate(vec):
+                        self._check(lib.lwacm_set_option(h, k + a, float(v)))
+            if rho0 is not None:
+                self._check(lib.lwacm_set_option(h, OPT_RHO0, float(rho0)))
+            if graph_chunk is not None:
+                self._check(lib.lwacm_set_option(h, OPT_GRAPH_CHUNK, float(graph_chunk)))
+            if kernel:
+                self._check(lib.lwacm_set_option(h, OPT_KERNEL, float(kernel)))
+            nbytes = ctypes.c_size_t()
+            self._check(lib.lwacm_workspace_bytes(h, ctypes.byref(nbytes)))
+            self.device = torch.device(device if device is not None else "cuda")
+            self.workspace = torch.empty(nbytes.value, dtype=torch.uint8, device=self.device)
+            self.stream = stream if stream is not None else torch.cuda.current_stream(self.device)
+            self._check(lib.lwacm_bind(h, self.workspace.data_ptr(), nbytes.value,
+                                       ctypes.c_void_p(self.stream.cuda_stream)))
+        except Exception:
+            lib.lwacm_destroy(h)
+            self._h = None
+            raise
+        self.storage = storage
+        self.nf = 3 if self.lattice == D2Q9 else 4
+
+    # -- helpers --
+    def _check(self, st):
+        if st != OK:
+            msg = self._lib.lwacm_last_error(self._h).decode() if self._h else ""
+            raise LwacmError(st, msg)
+        return st
+
+    @property
+    def shape(self):
+        return (self.ny, self.nx) if self.lattice == D2Q9 else (self.nz, self.ny, self.nx)
+
+    @property
+    def kernel_name(self):
+        return self._lib.lwacm_kernel_name(self._h).decode()
+
+    def close(self):
+        if getattr(self, "_h", None):
+            self._lib.lwacm_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    # -- C-ABI calls --
+    def set_fields(self, d, ux, uy, uz=None):
+        """Initial state from numpy arrays (host, any float -> FP64) or torch tensors
+        (CUDA or host, float32/float64)."""
+        arrs = [d, ux, uy] + ([uz] if self.lattice == D3Q19 else [])
+        torch = _torch()
+        if all(isinstance(a, np.ndarray) for a in arrs):
+            keep = [np.ascontiguousarray(a, dtype=np.float64).reshape(-1) for a in arrs]
+            dtype, where = F64, HOST
+        else:
+            keep = [a.contiguous().reshape(-1) for a in arrs]
+            dt = keep[0].dtype
+            dtype = {torch.float32: F32, torch.float64: F64}[dt]
+            where = DEVICE if keep[0].is_cuda else HOST
+        for a in keep:
+            assert a.size == self.nx * self.ny * self.nz if isinstance(a, np.ndarray) \
+                else a.numel() == self.nx * self.ny * self.nz
+        ptrs = [_ptr(a) for a in keep] + [None] * (4 - len(keep))
+        self._check(self._lib.lwacm_set_fields(self._h, *ptrs, dtype, where))
+        if where == HOST:
+            self._hold = keep  # host memory must outlive the asynchronous copy
+            self.sync()
+            self._hold = None
+
+    def step(self, n=1):
+        self._check(self._lib.lwacm_step(self._h, int(n)))
+
+    def sync(self):
+        self._check(self._lib.lwacm_sync(self._h))
+
+    def step_count(self):
+        v = ctypes.c_longlong()
+        self._check(self._lib.lwacm_step_count(self._h, ctypes.byref(v)))
+        return v.value
+
+    def get_fields(self, dtype=np.float64):
+        """Current state copied to host numpy arrays (converted on the device)."""
+        code = F64 if np.dtype(dtype) == np.float64 else F32
+        outs = [np.empty(self.shape, dtype=np.float64 if code == F64 else np.float32)
+                for _ in range(self.nf)]
+        ptrs = [o.ctypes.data for o in outs] + [None] * (4 - self.nf)
+        self._check(self._lib.lwacm_get_fields(self._h, *ptrs, code, HOST))
+        return tuple(outs)
+
+    def get_fields_into(self, outs, where=DEVICE):
+        """Copy the current state into caller tensors/arrays (float32 or float64)."""
+        torch = _torch()
+        first = outs[0]
+        if isinstance(first, np.ndarray):
+            code = F64 if first.dtype == np.float64 else F32
+        else:
+            code = F64 if first.dtype == torch.float64 else F32
+        ptrs = [_ptr(o) for o in outs] + [None] * (4 - len(outs))
+        self._check(self._lib.lwacm_get_fields(self._h, *ptrs, code, where))
+
+    def fields(self):
+        """Zero-copy torch views of the current state (storage dtype)."""
+        torch = _torch()
+        vp = [ctypes.c_void_p() for _ in range(4)]
+        dt = ctypes.c_int()
+        pitch = ctypes.c_longlong()
+        self._check(self._lib.lwacm_fields(self._h, *[ctypes.byref(v) for v in vp],
+                                           ctypes.byref(dt), ctypes.byref(pitch)))
+        tdt = {F32: torch.float32, BF16: torch.bfloat16, F16: torch.float16}[dt.value]
+        esz = 4 if dt.value == F32 else 2
+        base = self.workspace.data_ptr()
+        n = self.nx * self.ny * self.nz
+        views = []
+        for k in range(self.nf):
+            off = vp[k].value - base
+            views.append(self.workspace[off:off + n * esz].view(tdt).view(self.shape))
+        return tuple(views)
+
+    def diagnostics(self):
+        out = (ctypes.c_double * 8)()
+        st = self._lib.lwacm_diagnostics(self._h, out)
+        res = {"mass": out[0], "jx": out[1], "jy": out[2], "jz": out[3], "ke": out[4],
+               "umax": out[5], "mpar": out[6], "mperp": out[7], "finite": st != E_NONFINITE}
+        if st not in (OK, E_NONFINITE):
+            self._check(st)
+        return res

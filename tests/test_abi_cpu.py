@@ -1,0 +1,99 @@
+"""Host-side checks of the C ABI that need no GPU: the library loads, exports
+every entry point include/*.h declares, and validates arguments without device
+work (lwacm_create / lwacm_set_option / lwacm_workspace_bytes are host-only)."""
+import ctypes
+import glob
+import os
+import re
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module")
+def lib():
+    import __graft_entry__
+    __graft_entry__.build()
+    from paper_1111_2142_gb300 import lwacm as lw
+    return lw.load()
+
+
+def declared_functions():
+    names = set()
+    for h in glob.glob(os.path.join(ROOT, "include", "*.h")):
+        src = open(h).read()
+        src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+        names |= set(re.findall(r"\b(lwacm_[a-z0-9_]+)\s*\(", src))
+    return sorted(names)
+
+
+def test_exports_every_declared_symbol(lib):
+    names = declared_functions()
+    assert "lwacm_create" in names and "lwacm_step" in names
+    for n in names:
+        assert hasattr(lib, n), f"{n} declared in include/ but not exported"
+
+
+def _create(lib, *args):
+    h = ctypes.c_void_p()
+    st = lib.lwacm_create(*args, ctypes.byref(h))
+    return st, h
+
+
+def test_create_validation(lib):
+    from paper_1111_2142_gb300 import lwacm as lw
+    st, h = _create(lib, lw.D3Q19, 16, 16, 16, 0.01, lw.PERIODIC)
+    assert st == lw.OK and h.value
+    lib.lwacm_destroy(h)
+    # nu range: 0 < nu <= 1/6  (1 <= omega < 2)
+    for nu in (0.0, -0.1, 0.2, float("nan")):
+        assert _create(lib, lw.D3Q19, 8, 8, 8, nu, lw.PERIODIC)[0] == lw.E_RANGE
+    st, h = _create(lib, lw.D2Q9, 8, 8, 1, 1.0 / 6.0, lw.PERIODIC)
+    assert st == lw.OK
+    lib.lwacm_destroy(h)
+    bad = [(7, 8, 8, 1), (9, 8, 8, 2), (9, 0, 8, 1), (19, 8, -1, 8), (9, 1, 8, 1)]
+    for Q, nx, ny, nz in bad[:4]:
+        assert _create(lib, Q, nx, ny, nz, 0.01, lw.PERIODIC)[0] == lw.E_ARG
+    # walled axes need two nodes
+    assert _create(lib, lw.D2Q9, 1, 8, 1, 0.01, lw.CAVITY)[0] == lw.E_ARG
+    assert _create(lib, lw.D2Q9, 8, 1, 1, 0.01, lw.CHANNEL)[0] == lw.E_ARG
+    assert _create(lib, lw.D2Q9, 8, 8, 1, 0.01, 7)[0] == lw.E_ARG
+
+
+def test_workspace_and_options(lib):
+    from paper_1111_2142_gb300 import lwacm as lw
+    st, h = _create(lib, lw.D3Q19, 32, 16, 8, 0.01, lw.PERIODIC)
+    assert st == lw.OK
+    nb = ctypes.c_size_t()
+    assert lib.lwacm_workspace_bytes(h, ctypes.byref(nb)) == lw.OK
+    N = 32 * 16 * 8
+    # two ping-pong buffers of 4 FP32 fields + FP64 staging + reduction scratch
+    assert nb.value >= 2 * 4 * N * 4 + N * 8
+    assert lib.lwacm_set_option(h, lw.OPT_STORAGE, float(lw.BF16)) == lw.OK
+    nb2 = ctypes.c_size_t()
+    lib.lwacm_workspace_bytes(h, ctypes.byref(nb2))
+    assert nb2.value < nb.value
+    assert lib.lwacm_set_option(h, lw.OPT_STORAGE, 9.0) == lw.E_ARG
+    assert lib.lwacm_set_option(h, lw.OPT_GRAPH_CHUNK, 3.0) == lw.E_ARG
+    assert lib.lwacm_set_option(h, 99, 1.0) == lw.E_ARG
+    assert lib.lwacm_set_option(h, lw.OPT_RHO0, -1.0) == lw.E_ARG
+    assert lib.lwacm_set_option(h, lw.OPT_LID_X, float("inf")) == lw.E_ARG
+    assert b"non-finite" in lib.lwacm_last_error(h)
+    # calls that need a bound workspace report a state error, not a crash
+    assert lib.lwacm_step(h, 1) == lw.E_STATE
+    assert lib.lwacm_sync(h) == lw.E_STATE
+    out = (ctypes.c_double * 8)()
+    assert lib.lwacm_diagnostics(h, out) == lw.E_STATE
+    # a misaligned or short workspace is refused before any device work
+    assert lib.lwacm_bind(h, ctypes.c_void_p(4096 + 8), nb2.value, None) == lw.E_ARG
+    assert lib.lwacm_bind(h, ctypes.c_void_p(4096 * 256), 16, None) == lw.E_NOMEM
+    lib.lwacm_destroy(h)
+    lib.lwacm_destroy(None)
+
+
+def test_null_arguments(lib):
+    from paper_1111_2142_gb300 import lwacm as lw
+    assert lib.lwacm_create(9, 8, 8, 1, 0.01, 0, None) == lw.E_ARG
+    assert lib.lwacm_workspace_bytes(None, None) == lw.E_ARG
+    assert lib.lwacm_step(None, 1) == lw.E_ARG

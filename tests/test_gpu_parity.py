@@ -1,0 +1,239 @@
+"""GPU parity: the CUDA library (through the C ABI) against the FP64 oracle on the
+same seeded inputs, element by element.
+
+Tolerances (FP32 arithmetic and storage, IEEE division): one update rounds each
+stored value once (relative 2^-24) after O(Q) single-precision sums whose
+terms are bounded by |u| and |d|; the scheme is diffusive, so rounding errors
+random-walk rather than grow. Bounds used below: max|du| / u_scale <= 1e-5 and
+max|dd| / max|d_ref| <= 1e-4 after up to 1000 steps; BF16 / FP16 storage round
+each stored value to 8 / 11 significant bits every step, giving the looser
+bounds stated in those tests.
+"""
+import numpy as np
+import pytest
+
+import oracle
+from paper_1111_2142_gb300 import inputs
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def lw():
+    import __graft_entry__
+    __graft_entry__.build()
+    from paper_1111_2142_gb300 import lwacm
+    return lwacm
+
+
+def errs(got, ref, u_scale):
+    eu = max(float(np.max(np.abs(g - r))) for g, r in zip(got[1:], ref[1:])) / u_scale
+    dmax = max(float(np.max(np.abs(ref[0]))), 1e-300)
+    ed = float(np.max(np.abs(got[0] - ref[0]))) / dmax
+    return eu, ed
+
+
+def run_gpu(lw, Q, fields, nu, nsteps, bc=0, **kw):
+    shape = fields[0].shape
+    nz = 1 if Q == 9 else shape[0]
+    ny, nx = shape[-2], shape[-1]
+    sim = lw.Lwacm(Q, nx, ny, nz, nu, bc, **kw)
+    sim.set_fields(*fields)
+    sim.step(nsteps)
+    out = sim.get_fields()
+    name = sim.kernel_name
+    sim.close()
+    return out, name
+
+
+KERNELS = [1, 0]  # generic gather kernel, automatic choice (tiled where supported)
+
+
+@pytest.mark.parametrize("kernel", KERNELS)
+def test_d2q9_tgv_64(lw, kernel):
+    """2D Taylor-Green 64x64, u0 = 0.01, nu = 0.01, 1000 steps."""
+    f = inputs.tgv2d(64, u0=0.01)
+    got, name = run_gpu(lw, 9, f, 0.01, 1000, kernel=kernel)
+    ref = oracle.step(9, *f, nu=0.01, nsteps=1000)
+    eu, ed = errs(got, ref, 0.01)
+    print(f"[{name}] d2q9 tgv64: du/u0={eu:.2e} dd/d={ed:.2e}")
+    assert eu < 1e-5 and ed < 1e-4
+
+
+@pytest.mark.parametrize("kernel", KERNELS)
+@pytest.mark.parametrize("shape", [(23, 37), (1, 5), (64, 96), (33, 130)])
+def test_d2q9_ragged(lw, kernel, shape):
+    f = inputs.smooth_random(shape, seed=3, u_amp=0.05, d_amp=0.01)
+    got, name = run_gpu(lw, 9, f, 0.02, 60, kernel=kernel)
+    ref = oracle.step(9, *f, nu=0.02, nsteps=60)
+    eu, ed = errs(got, ref, 0.05)
+    print(f"[{name}] d2q9 {shape}: du/U={eu:.2e} dd/d={ed:.2e}")
+    assert eu < 1e-5 and ed < 1e-4
+
+
+@pytest.mark.parametrize("kernel", KERNELS)
+@pytest.mark.parametrize("shape", [(9, 11, 13), (3, 4, 5), (16, 16, 64), (5, 7, 132)])
+def test_d3q19_ragged(lw, kernel, shape):
+    f = inputs.smooth_random(shape, seed=4, u_amp=0.05, d_amp=0.01)
+    got, name = run_gpu(lw, 19, f, 0.01, 30, kernel=kernel)
+    ref = oracle.step(19, *f, nu=0.01, nsteps=30)
+    eu, ed = errs(got, ref, 0.05)
+    print(f"[{name}] d3q19 {shape}: du/U={eu:.2e} dd/d={ed:.2e}")
+    assert eu < 1e-5 and ed < 1e-4
+
+
+@pytest.mark.parametrize("kernel", KERNELS)
+def test_d3q19_tgv_48(lw, kernel):
+    """3D Taylor-Green, u0 = 0.02, nu = 0.005 (the 256^3 workload's parameters), 300 steps."""
+    f = inputs.tgv3d(48, u0=0.02)
+    got, name = run_gpu(lw, 19, f, 0.005, 300, kernel=kernel)
+    ref = oracle.step(19, *f, nu=0.005, nsteps=300)
+    eu, ed = errs(got, ref, 0.02)
+    print(f"[{name}] d3q19 tgv48 x300: du/u0={eu:.2e} dd/d={ed:.2e}")
+    assert eu < 1e-5 and ed < 1e-4
+
+
+@pytest.mark.parametrize("shape,lid", [((33, 40), (0.1, 0.0)), ((2, 2), (0.05, 0.0)),
+                                       ((17, 5), (0.0, 0.0))])
+def test_cavity_2d(lw, shape, lid):
+    f = inputs.smooth_random(shape, seed=5, u_amp=0.03, d_amp=0.005)
+    got, _ = run_gpu(lw, 9, f, 0.0128, 200, bc=lw.CAVITY, lid=lid)
+    ref = oracle.step(9, *f, nu=0.0128, bc=oracle.CAVITY, lid=lid, nsteps=200)
+    eu, ed = errs(got, ref, 0.1)
+    print(f"cavity2d {shape}: du/U={eu:.2e} dd/d={ed:.2e}")
+    assert eu < 1e-5 and ed < 1e-4
+
+
+@pytest.mark.parametrize("shape", [(9, 10, 12), (2, 3, 4)])
+def test_cavity_3d(lw, shape):
+    lid = (np.sqrt(2) / 20, np.sqrt(2) / 20, 0.0)
+    f = inputs.smooth_random(shape, seed=6, u_amp=0.03, d_amp=0.005)
+    got, _ = run_gpu(lw, 19, f, 0.02, 100, bc=lw.CAVITY, lid=lid)
+    ref = oracle.step(19, *f, nu=0.02, bc=oracle.CAVITY, lid=lid, nsteps=100)
+    eu, ed = errs(got, ref, 0.1)
+    print(f"cavity3d {shape}: du/U={eu:.2e} dd/d={ed:.2e}")
+    assert eu < 1e-5 and ed < 1e-4
+
+
+@pytest.mark.parametrize("Q,shape", [(9, (12, 20)), (19, (6, 12, 10))])
+def test_channel_force(lw, Q, shape):
+    g = (1e-5, 0.0, 0.0)
+    f = inputs.smooth_random(shape, seed=7, u_amp=0.01, d_amp=0.002)
+    got, _ = run_gpu(lw, Q, f, 0.05, 200, bc=lw.CHANNEL, force=g[: (2 if Q == 9 else 3)],
+                     lid=(0.01, 0.0, 0.0)[: (2 if Q == 9 else 3)])
+    ref = oracle.step(Q, *f, nu=0.05, bc=oracle.CHANNEL, force=g, lid=(0.01, 0, 0), nsteps=200)
+    eu, ed = errs(got, ref, 0.01)
+    print(f"channel Q{Q} {shape}: du/U={eu:.2e} dd/d={ed:.2e}")
+    assert eu < 1e-5 and ed < 1e-4
+
+
+def test_cavity_128_centrelines(lw):
+    """Lid-driven cavity at Re = 1000 on 128^2 (U = 0.1, nu = 0.1*128/1000), 25,000
+    steps (about 20 lid travel times): centreline u(x = N/2, y) and v(x, y = N/2)
+    agree with the oracle to 1e-5 U."""
+    N, U = 128, 0.1
+    nu = U * N / 1000.0
+    z = np.zeros((N, N))
+    T = 25000
+    got, _ = run_gpu(lw, 9, (z, z, z), nu, T, bc=lw.CAVITY, lid=(U, 0.0))
+    ref = oracle.step(9, z, z, z, nu=nu, bc=oracle.CAVITY, lid=(U, 0, 0), nsteps=T)
+    cu = np.max(np.abs(got[1][:, N // 2] - ref[1][:, N // 2])) / U
+    cv = np.max(np.abs(got[2][N // 2, :] - ref[2][N // 2, :])) / U
+    eu, ed = errs(got, ref, U)
+    print(f"cavity128 Re1000 x{T}: centreline du/U={cu:.2e} dv/U={cv:.2e} field du/U={eu:.2e}")
+    assert cu < 1e-5 and cv < 1e-5
+
+
+@pytest.mark.parametrize("storage,tol_u,tol_d", [(2, 2e-3, 2e-2), (1, 1.5e-2, 1e-1)])
+def test_half_storage(lw, storage, tol_u, tol_d):
+    """FP16 / BF16 storage with FP32 arithmetic: error vs the FP64 oracle, 3D TGV
+    32^3, 200 steps. Bounds: 11 (FP16) / 8 (BF16) significant bits per store,
+    random-walking over the steps."""
+    f = inputs.tgv3d(32, u0=0.02)
+    got, name = run_gpu(lw, 19, f, 0.005, 200, storage=storage)
+    ref = oracle.step(19, *f, nu=0.005, nsteps=200)
+    eu, ed = errs(got, ref, 0.02)
+    print(f"[{name}] storage {storage}: du/u0={eu:.2e} dd/d={ed:.2e}")
+    assert eu < tol_u and ed < tol_d
+
+
+def test_diagnostics_match_fp64_sums(lw):
+    f = inputs.smooth_random((10, 12, 14), seed=8, u_amp=0.05, d_amp=0.01)
+    sim = lw.Lwacm(19, 14, 12, 10, 0.02)
+    sim.set_fields(*f)
+    sim.step(7)
+    diag = sim.diagnostics()
+    got = sim.get_fields()
+    ref = oracle.diagnostics(*got)
+    for k in ("mass", "jx", "jy", "jz", "ke", "umax"):
+        assert abs(diag[k] - ref[k]) <= 1e-12 * max(1.0, abs(ref[k])), (k, diag[k], ref[k])
+    u, w = got[1], got[3]
+    assert abs(diag["mpar"] - 0.5 * np.sum((u + w) ** 2)) < 1e-12
+    assert abs(diag["mperp"] - 0.5 * np.sum((u - w) ** 2)) < 1e-12
+    sim.close()
+
+
+def test_conservation_fp64_reduction(lw):
+    """Mass and momentum on a periodic grid are exact invariants (Section 2.1); in
+    FP32 they drift by rounding only."""
+    f = inputs.tgv3d(64, u0=0.02)
+    sim = lw.Lwacm(19, 64, 64, 64, 0.005)
+    sim.set_fields(*f)
+    d0 = sim.diagnostics()
+    sim.step(1000)
+    d1 = sim.diagnostics()
+    N = 64 ** 3
+    drift_m = abs(d1["mass"] - d0["mass"]) / N
+    drift_j = max(abs(d1[k] - d0[k]) for k in ("jx", "jy", "jz")) / N
+    print(f"[{sim.kernel_name}] drift per node after 1000 steps: mass {drift_m:.2e} "
+          f"momentum {drift_j:.2e}")
+    assert drift_m < 1e-8 and drift_j < 1e-9
+    sim.close()
+
+
+def test_graph_replay_matches_direct_launches(lw):
+    f = inputs.smooth_random((20, 24), seed=9)
+    a, _ = run_gpu(lw, 9, f, 0.02, 130, graph_chunk=64)
+    b, _ = run_gpu(lw, 9, f, 0.02, 130, graph_chunk=0)
+    for x, y in zip(a, b):
+        assert np.array_equal(x, y)
+
+
+def test_roundtrip_and_zero_steps(lw):
+    import torch
+    f = inputs.smooth_random((5, 6, 7), seed=10)
+    sim = lw.Lwacm(19, 7, 6, 5, 0.02)
+    t32 = [torch.tensor(a, dtype=torch.float32, device="cuda") for a in f]
+    sim.set_fields(*t32)
+    sim.step(0)
+    out = sim.get_fields(np.float32)
+    for a, b in zip(out, t32):
+        assert np.array_equal(a, b.cpu().numpy())
+    views = sim.fields()
+    assert torch.equal(views[1], t32[1])
+    assert sim.step_count() == 0
+    sim.step(3)
+    assert sim.step_count() == 3
+    sim.close()
+
+
+def test_nonfinite_is_reported(lw):
+    d, u, v = inputs.smooth_random((8, 8), seed=11)
+    d = d.copy()
+    d[3, 4] = np.nan
+    sim = lw.Lwacm(9, 8, 8, 1, 0.02)
+    sim.set_fields(d, u, v)
+    assert sim.diagnostics()["finite"] is False
+    sim.close()
+
+
+def test_full_size_256_d3q19_one_step(lw):
+    """The benchmark workload (D3Q19 3D Taylor-Green 256^3, FP32, the kernel the
+    benchmark times): 2 steps compared with the oracle on every node."""
+    n = 256
+    f = inputs.tgv3d(n, u0=0.02)
+    got, name = run_gpu(lw, 19, f, 0.005, 2)
+    ref = oracle.step(19, *f, nu=0.005, nsteps=2)
+    eu, ed = errs(got, ref, 0.02)
+    print(f"[{name}] d3q19 256^3 x2: du/u0={eu:.2e} dd/d={ed:.2e}")
+    assert eu < 1e-6 and ed < 1e-5
