@@ -2,7 +2,7 @@
 // ny a multiple of 8: the moment form of Eq. ACM2.0 (see lwacm_core.cuh) with
 // every field read from HBM once and written once per step.
 //
-// CTA = 8 row warps + 2 halo warps. Row warp w owns the full x-row y0 + w of the
+// CTA = 8 row warps. Row warp w owns the full x-row y0 + w of the
 // current z-plane, lane l the VX consecutive nodes x = l*VX .. l*VX+VX-1, so the
 // periodic x-neighbours of a row are reached with warp shuffles (lane 31 wraps to
 // lane 0). The CTA marches along z through its chunk [z0, z1); per plane each
@@ -11,7 +11,7 @@
 //   * links with c_y = 0 stay in the warp: register moves, one shuffle per link
 //     at lane boundaries;
 //   * links with c_y = +-1 go through shared memory to the warp of the next /
-//     previous row (double-buffered, one barrier per plane); the two halo warps
+//     previous row (double-buffered, one barrier per plane); warps 0 and 7 also
 //     compute the c_y = +1 values of row y0-1 and the c_y = -1 values of row y0+8;
 //   * links with c_z = +-1 land in the accumulators of planes z+-1, which live in
 //     registers: three planes of (d, jx, jy, jz) rotate as the CTA marches.
@@ -26,7 +26,7 @@ namespace lwacm {
 namespace {
 
 constexpr int ROWS = 8;
-constexpr int NWARPS = ROWS + 2;
+constexpr int NWARPS = ROWS;  // warps 0 and ROWS-1 also compute the halo rows
 constexpr int NTHREADS = NWARPS * 32;
 constexpr unsigned FULL = 0xffffffffu;
 
@@ -170,20 +170,21 @@ __device__ __forceinline__ void ld_slot(const float *slot, float (&o)[VX], int l
 }
 
 template <int VX, int PM, int P0, int PP>
-__device__ __forceinline__ void plane_step(float (&acc)[3][VX][4], float (&F)[4][VX], int pz,
-                                           int z0, int z1, const TiledParams &p, int lane,
-                                           int warp, int yrow, const float *__restrict__ in,
+__device__ __forceinline__ void plane_step(float (&acc)[3][VX][4], float (&F)[4][VX],
+                                           float (&Fh)[4][VX], int pz, int z0, int z1,
+                                           const TiledParams &p, int lane, int warp, int yrow,
+                                           int hrow, const float *__restrict__ in,
                                            float *__restrict__ out, float *xs) {
     using G = Geo<VX>;
     float *buf = xs + (pz & 1) * G::BUF;  // pz may be -1: & 1 still alternates
     float *up = buf, *dn = buf + G::DIR;
     const long long rowoff = (long long)yrow * p.nx + lane * VX;
+    const long long hrowoff = (long long)hrow * p.nx + lane * VX;
     const long long plane = (long long)p.nx * p.ny;
 
-    NodeConst<VX> nc;
-    node_consts(nc, F, p.s18);
-
-    if (warp < ROWS) {
+    {
+        NodeConst<VX> nc;
+        node_consts(nc, F, p.s18);
         // ---- rest link, post-combine term a rho u, z-links -------------------
 #pragma unroll
         for (int i = 0; i < VX; ++i) {
@@ -238,23 +239,23 @@ __device__ __forceinline__ void plane_step(float (&acc)[3][VX][4], float (&F)[4]
                 st_slot(dn + k * G::SLOT + (warp - 1) * G::RL, gm, lane);
             }
         }
-    } else if (warp == ROWS) {  // bottom halo row y0-1: its c_y = +1 values feed row 0
+    }
+    // ---- halo rows: bottom (y0-1) feeds row 0, top (y0+ROWS) feeds row ROWS-1 --
+    if (warp == 0 || warp == ROWS - 1) {
+        NodeConst<VX> hc;
+        node_consts(hc, Fh, p.s18);
 #pragma unroll
         for (int k = 0; k < 5; ++k) {
             float gp[VX], gm[VX];
 #pragma unroll
-            for (int i = 0; i < VX; ++i) pair_g(nc, i, ypair_e(nc, k, i), k != 0, p.c4, gp[i], gm[i]);
-            xshift(gp, ypair_cx(k), lane);
-            st_slot(up + k * G::SLOT, gp, lane);
-        }
-    } else {  // top halo row y0+ROWS: its c_y = -1 values feed row ROWS-1
-#pragma unroll
-        for (int k = 0; k < 5; ++k) {
-            float gp[VX], gm[VX];
-#pragma unroll
-            for (int i = 0; i < VX; ++i) pair_g(nc, i, ypair_e(nc, k, i), k != 0, p.c4, gp[i], gm[i]);
-            xshift(gm, -ypair_cx(k), lane);
-            st_slot(dn + k * G::SLOT + (ROWS - 1) * G::RL, gm, lane);
+            for (int i = 0; i < VX; ++i) pair_g(hc, i, ypair_e(hc, k, i), k != 0, p.c4, gp[i], gm[i]);
+            if (warp == 0) {  // c_y = +1 values of row y0-1
+                xshift(gp, ypair_cx(k), lane);
+                st_slot(up + k * G::SLOT, gp, lane);
+            } else {  // c_y = -1 values of row y0+ROWS
+                xshift(gm, -ypair_cx(k), lane);
+                st_slot(dn + k * G::SLOT + (ROWS - 1) * G::RL, gm, lane);
+            }
         }
     }
 
@@ -263,10 +264,12 @@ __device__ __forceinline__ void plane_step(float (&acc)[3][VX][4], float (&F)[4]
         int zn = pz + 1;
         zn = zn >= p.nz ? zn - p.nz : zn;
         load_plane<VX>(F, in + (long long)zn * plane + rowoff, p.fstride);
+        if (warp == 0 || warp == ROWS - 1)
+            load_plane<VX>(Fh, in + (long long)zn * plane + hrowoff, p.fstride);
     }
     __syncthreads();
 
-    if (warp < ROWS) {
+    {
         // ---- receive row-crossing links ---------------------------------------
 #pragma unroll
         for (int k = 0; k < 5; ++k) {
@@ -308,21 +311,23 @@ __device__ __forceinline__ void plane_step(float (&acc)[3][VX][4], float (&F)[4]
     }
 }
 
-// No __launch_bounds__: its register cap assumes 128-thread granularity (168 for
-// 320 threads); the kernel needs about 200 registers, and 10 warps x 200 fit the
-// 64K-register file. launch_vx checks the occupancy before the first launch.
+// 8 warps: up to 255 registers per thread; launch_vx checks the occupancy
+// before the first launch.
 template <int VX>
-__global__ void k_d3q19_tiled(const float *__restrict__ in, float *__restrict__ out, TiledParams p) {
+__global__ void __launch_bounds__(NTHREADS, 1) k_d3q19_tiled(const float *__restrict__ in, float *__restrict__ out, TiledParams p) {
     extern __shared__ float4 smem4[];
     float *xs = reinterpret_cast<float *>(smem4);
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const int y0 = blockIdx.x * ROWS;
     const int z0 = blockIdx.y * p.zc;
     const int z1 = min(z0 + p.zc, p.nz);
-    int yrow = warp < ROWS ? y0 + warp : (warp == ROWS ? y0 - 1 : y0 + ROWS);
-    yrow = yrow < 0 ? yrow + p.ny : (yrow >= p.ny ? yrow - p.ny : yrow);
+    const int yrow = y0 + warp;
+    // halo row of warps 0 / ROWS-1 (periodic in y); unused by the other warps
+    int hrow = warp == 0 ? y0 - 1 : y0 + ROWS;
+    hrow = hrow < 0 ? hrow + p.ny : (hrow >= p.ny ? hrow - p.ny : hrow);
     const long long plane = (long long)p.nx * p.ny;
     const long long rowoff = (long long)yrow * p.nx + lane * VX;
+    const long long hrowoff = (long long)hrow * p.nx + lane * VX;
 
     float acc[3][VX][4];
 #pragma unroll
@@ -331,19 +336,21 @@ __global__ void k_d3q19_tiled(const float *__restrict__ in, float *__restrict__ 
         for (int i = 0; i < VX; ++i)
 #pragma unroll
             for (int c = 0; c < 4; ++c) acc[a][i][c] = 0.f;
-    float F[4][VX];
+    float F[4][VX], Fh[4][VX];
     {
         int zs = z0 - 1;
         zs = zs < 0 ? zs + p.nz : zs;
         load_plane<VX>(F, in + (long long)zs * plane + rowoff, p.fstride);
+        if (warp == 0 || warp == ROWS - 1)
+            load_plane<VX>(Fh, in + (long long)zs * plane + hrowoff, p.fstride);
     }
     // source planes z0-1 .. z1; receiver plane pz-1 completes at source plane pz
     for (int pz = z0 - 1; pz <= z1; pz += 3) {
-        plane_step<VX, 0, 1, 2>(acc, F, pz, z0, z1, p, lane, warp, yrow, in, out, xs);
+        plane_step<VX, 0, 1, 2>(acc, F, Fh, pz, z0, z1, p, lane, warp, yrow, hrow, in, out, xs);
         if (pz + 1 <= z1)
-            plane_step<VX, 1, 2, 0>(acc, F, pz + 1, z0, z1, p, lane, warp, yrow, in, out, xs);
+            plane_step<VX, 1, 2, 0>(acc, F, Fh, pz + 1, z0, z1, p, lane, warp, yrow, hrow, in, out, xs);
         if (pz + 2 <= z1)
-            plane_step<VX, 2, 0, 1>(acc, F, pz + 2, z0, z1, p, lane, warp, yrow, in, out, xs);
+            plane_step<VX, 2, 0, 1>(acc, F, Fh, pz + 2, z0, z1, p, lane, warp, yrow, hrow, in, out, xs);
     }
 }
 
