@@ -1,24 +1,31 @@
-// Tiled interior kernel for D3Q19 on periodic domains with nx = 32*VX (VX = 4, 8),
-// ny a multiple of 8: the moment form of Eq. ACM2.0 (see lwacm_core.cuh) with
-// every field read from HBM once and written once per step.
+// Tiled interior kernel for D3Q19 on periodic domains with nx = 32*VX (VX = 4, 8)
+// and ny a multiple of 8: the moment form of Eq. ACM2.0 (see lwacm_core.cuh), every
+// field read from HBM once and written once per step.
 //
-// CTA = 8 row warps. Row warp w owns the full x-row y0 + w of the
-// current z-plane, lane l the VX consecutive nodes x = l*VX .. l*VX+VX-1, so the
-// periodic x-neighbours of a row are reached with warp shuffles (lane 31 wraps to
-// lane 0). The CTA marches along z through its chunk [z0, z1); per plane each
-// node computes its 19 outgoing values g_i once (pre-combine, Eq. ACM2.0b(a)) and
-// they are streamed (Eq. ACM2.0b(b)) to their receivers:
-//   * links with c_y = 0 stay in the warp: register moves, one shuffle per link
-//     at lane boundaries;
-//   * links with c_y = +-1 go through shared memory to the warp of the next /
-//     previous row (double-buffered, one barrier per plane); warps 0 and 7 also
-//     compute the c_y = +1 values of row y0-1 and the c_y = -1 values of row y0+8;
-//   * links with c_z = +-1 land in the accumulators of planes z+-1, which live in
-//     registers: three planes of (d, jx, jy, jz) rotate as the CTA marches.
-// Plane z-1 is complete once plane z has been processed; it is post-combined
-// (Eq. ACM2.0b(c): + a rho u), divided by rho (moments, Section 2.1) and stored.
-// The next plane's fields are loaded into registers while the current plane's
-// exchange and stores proceed.
+// Persistent CTAs (one per SM) of 8 warps. The (y-column, z) plane-rows of the
+// lattice (a y-column is 8 consecutive rows) are split into equal contiguous
+// ranges, one per CTA; a CTA marches along z through its range, one source plane
+// per task. Per plane:
+//   * TMA (cp.async.bulk, mbarrier completion, two-stage ring) copies the ten rows
+//     y0-1 .. y0+8 of the four fields into shared memory two tasks ahead;
+//   * warp w owns row y0+w, lane l the VX consecutive nodes x = l*VX + i; each node
+//     computes its outgoing values g_i once (pre-combine, Eq. ACM2.0b(a)) and
+//     streams them (Eq. ACM2.0b(b)): links with c_y = 0 stay in the warp (register
+//     moves, one shuffle at lane edges, periodic in x through lane 31 -> 0); links
+//     with c_y = +-1 are summed per receiver into four values and passed through
+//     shared memory to the next / previous row (double-buffered, one CTA barrier
+//     per plane); warps 0 and 7 also compute those values for the halo rows
+//     y0-1 and y0+8;
+//   * links with c_z = +-1 land in register accumulators of planes z+-1 (three
+//     planes of (d, jx, jy, jz) rotate); plane z-1 is then complete, post-combined
+//     (+ a rho u, Eq. ACM2.0b(c)), divided by rho (moments, Section 2.1) and
+//     stored with 16-byte stores.
+// The first and last plane of a run (the z-halo) only evaluate the five links that
+// point into the run.
+// Every wait on an mbarrier is bounded; on timeout the CTA sets an error word,
+// waits (bounded) for its own copies in flight and exits.
+#include <stdint.h>
+
 #include "launch.h"
 #include "lwacm_core.cuh"
 
@@ -26,50 +33,110 @@ namespace lwacm {
 namespace {
 
 constexpr int ROWS = 8;
-constexpr int NWARPS = ROWS;  // warps 0 and ROWS-1 also compute the halo rows
-constexpr int NTHREADS = NWARPS * 32;
+constexpr int NTHREADS = ROWS * 32;
+constexpr int TROWS = ROWS + 2;  // staged rows: y0-1, y0 .. y0+7, y0+8
+constexpr int NSLOT = 4;         // values passed per receiver and direction
 constexpr unsigned FULL = 0xffffffffu;
 
 struct TiledParams {
-    int nx, ny, nz, zc;
+    int nx, ny, nz;
+    long long work;      // (ny / ROWS) * nz plane-rows
     long long fstride;
-    float s18;   // s / 18 = nu
-    float c4;    // 1 / (4 nu): turns rho nu e into the rho e / 4 of the 9/2 (c.u)^2 term
-    float a_s;   // a / nu: turns rho nu into a rho
+    float s18;           // s / 18 = nu
+    float c4;            // 1 / (4 nu)
+    float a_s;           // a / nu
+    int *err;            // error word (timeout)
 };
 
 template <int VX>
 struct Geo {
-    static constexpr int RL = 32 * VX;        // row length in floats
-    static constexpr int SLOT = ROWS * RL;     // one link slot, all receiver rows
-    static constexpr int DIR = 5 * SLOT;       // five links per direction
-    static constexpr int BUF = 2 * DIR;        // up + down
-    static constexpr size_t BYTES = 2 * BUF * sizeof(float);  // double-buffered
+    static constexpr int RL = 32 * VX;                   // row length (floats)
+    static constexpr int XSLOT = ROWS * RL;              // one slot, all receiver rows
+    static constexpr int XDIR = NSLOT * XSLOT;
+    static constexpr int XBUF = 2 * XDIR;                // up + down
+    static constexpr int STAGE = 4 * TROWS * RL;         // 4 fields x 10 rows
+    static constexpr size_t XBYTES = 2 * (size_t)XBUF * 4;   // double-buffered exchange
+    static constexpr size_t SBYTES = 2 * (size_t)STAGE * 4;  // two TMA stages
+    static constexpr size_t BYTES = XBYTES + SBYTES + 64;    // + mbarriers
+    static constexpr uint32_t TX = STAGE * 4;                // bytes per stage
 };
 
-// position of node i of lane l inside a row slot: 4-float groups of all lanes
-// are contiguous, so float4 accesses of a warp are bank-conflict free
-__device__ __forceinline__ int spos(int l, int h) { return h * 128 + l * 4; }
+// ---- PTX wrappers: mbarrier and 1-D bulk copy ---------------------------------
+__device__ __forceinline__ uint32_t sa(const void *p) { return (uint32_t)__cvta_generic_to_shared(p); }
 
-template <int VX>
-__device__ __forceinline__ void load_plane(float (&F)[4][VX], const float *__restrict__ base,
-                                           long long fstride) {
-#pragma unroll
-    for (int f = 0; f < 4; ++f)
-#pragma unroll
-        for (int h = 0; h < VX / 4; ++h) {
-            const float4 t = __ldg(reinterpret_cast<const float4 *>(base + f * fstride) + h);
-            F[f][4 * h + 0] = t.x;
-            F[f][4 * h + 1] = t.y;
-            F[f][4 * h + 2] = t.z;
-            F[f][4 * h + 3] = t.w;
-        }
+__device__ __forceinline__ void mbar_init(uint64_t *bar, uint32_t count) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(sa(bar)), "r"(count) : "memory");
+}
+__device__ __forceinline__ void mbar_expect_tx(uint64_t *bar, uint32_t bytes) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(sa(bar)), "r"(bytes)
+                 : "memory");
+}
+__device__ __forceinline__ bool mbar_test(uint64_t *bar, uint32_t parity) {
+    uint32_t ok;
+    asm volatile(
+        "{\n .reg .pred p;\n mbarrier.test_wait.parity.shared::cta.b64 p, [%1], %2;\n"
+        " selp.u32 %0, 1, 0, p;\n}\n"
+        : "=r"(ok)
+        : "r"(sa(bar)), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+// bounded wait: at most 2^22 polls with back-off (well under a second)
+__device__ __forceinline__ bool mbar_wait(uint64_t *bar, uint32_t parity) {
+    for (int it = 0; it < (1 << 22); ++it) {
+        if (mbar_test(bar, parity)) return true;
+        if (it > 32) __nanosleep(100);
+    }
+    return false;
+}
+__device__ __forceinline__ void bulk_g2s(void *dst, const void *src, uint32_t bytes, uint64_t *bar) {
+    asm volatile(
+        "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+            sa(dst)),
+        "l"(src), "r"(bytes), "r"(sa(bar))
+        : "memory");
 }
 
+// ---- task iteration -------------------------------------------------------------
+// A CTA's range [lo, hi) of plane-rows (index = col * nz + z) splits into runs of
+// consecutive z in one column. A run [za, zb) is processed as source planes
+// za-1 (FIRST), za .. zb-1 (MID), zb (LAST).
+enum { FIRST = 0, MID = 1, LAST = 2 };
+
+struct TaskIter {
+    long long idx, hi;
+    int nz, col, za, zb, pz;
+    __device__ void start_run() {
+        col = (int)(idx / nz);
+        za = (int)(idx % nz);
+        const long long rest = hi - idx;
+        zb = za + (int)(rest < (long long)(nz - za) ? rest : (long long)(nz - za));
+        pz = za - 1;
+    }
+    __device__ TaskIter(long long lo, long long hi_, int nz_) : idx(lo), hi(hi_), nz(nz_) {
+        col = za = zb = pz = 0;
+        if (idx < hi) start_run();
+    }
+    __device__ bool valid() const { return idx < hi; }
+    __device__ int mode() const { return pz < za ? FIRST : (pz < zb ? MID : LAST); }
+    __device__ void next() {
+        if (pz < zb) {
+            ++pz;
+        } else {
+            idx += zb - za;
+            if (idx < hi) start_run();
+        }
+    }
+};
+
+// position of node group h (4 nodes) of lane l inside an exchange row: the 4-float
+// groups of all lanes are contiguous, so warp float4 accesses are conflict-free
+__device__ __forceinline__ int spos(int l, int h) { return h * 128 + l * 4; }
+
 // deposit the value g of link c = (cx,cy,cz) into a receiver's (d, jx, jy, jz).
-// Links with c_z = +1 feed the plane ahead, which receives nothing else before it
-// becomes the current plane: its jz equals its d then and is copied at that
-// point, so those deposits skip jz.
+// Values arriving along c_z = +1 links feed the plane ahead, which receives
+// nothing else before it becomes the current plane; its jz then equals its d and
+// is copied at that point, so those deposits skip jz.
 __device__ __forceinline__ void dep(float (&a)[4], float g, int cx, int cy, int cz) {
     a[0] += g;
     if (cx > 0) a[1] += g;
@@ -79,39 +146,45 @@ __device__ __forceinline__ void dep(float (&a)[4], float g, int cx, int cy, int 
     if (cz < 0) a[3] -= g;
 }
 
-// plane slot for a link with z-component cz, given the rotating indices
 template <int PM, int P0, int PP>
 __device__ __forceinline__ constexpr int pl(int cz) { return cz > 0 ? PP : (cz < 0 ? PM : P0); }
 
-// The five (c, -c) pairs whose c has c_y = +1; c = (cx, 1, cz), diag = |c|^2 == 2.
-__device__ __forceinline__ constexpr int ypair_cx(int k) { return k == 1 ? 1 : (k == 2 ? -1 : 0); }
-__device__ __forceinline__ constexpr int ypair_cz(int k) { return k == 3 ? 1 : (k == 4 ? -1 : 0); }
-
 // per-node constants: velocity, K/18 with K = d - 3/2 rho |u|^2, and rho nu
-// (= rho s / 18). A link value is then w/(1/18) * (K1 + A1 e (1 + e / (4 nu)))
-// = w [d + rho (s e + 9/2 e^2 - 3/2 |u|^2)] with e = c.u.
+// (= rho s / 18); a link value is w/(1/18) (K1 + A1 e (1 + e/(4 nu))) with e = c.u,
+// i.e. w [d + rho (s e + 9/2 e^2 - 3/2 |u|^2)].
 template <int VX>
 struct NodeConst {
     float U[VX], V[VX], W[VX], K1[VX], A1[VX];
 };
 
+// row: staged field-0 row; rstride: distance between fields in the stage
 template <int VX>
-__device__ __forceinline__ void node_consts(NodeConst<VX> &nc, const float (&F)[4][VX], float s18) {
+__device__ __forceinline__ void node_consts(NodeConst<VX> &nc, const float *row, int rstride,
+                                            int lane, float s18) {
 #pragma unroll
-    for (int i = 0; i < VX; ++i) {
-        const float d = F[0][i], u = F[1][i], v = F[2][i], w = F[3][i];
-        const float rho = 1.f + d;
-        const float q = fmaf(u, u, fmaf(v, v, w * w));
-        const float K = fmaf(-1.5f * rho, q, d);  // d - 3/2 rho |u|^2
-        nc.U[i] = u;
-        nc.V[i] = v;
-        nc.W[i] = w;
-        nc.K1[i] = K * (1.f / 18.f);
-        nc.A1[i] = rho * s18;  // rho s / 18
+    for (int h = 0; h < VX / 4; ++h) {
+        const float4 d4 = *reinterpret_cast<const float4 *>(row + lane * VX + 4 * h);
+        const float4 u4 = *reinterpret_cast<const float4 *>(row + rstride + lane * VX + 4 * h);
+        const float4 v4 = *reinterpret_cast<const float4 *>(row + 2 * rstride + lane * VX + 4 * h);
+        const float4 w4 = *reinterpret_cast<const float4 *>(row + 3 * rstride + lane * VX + 4 * h);
+        const float dd[4] = {d4.x, d4.y, d4.z, d4.w}, uu[4] = {u4.x, u4.y, u4.z, u4.w};
+        const float vv[4] = {v4.x, v4.y, v4.z, v4.w}, ww[4] = {w4.x, w4.y, w4.z, w4.w};
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+            const int i = 4 * h + j;
+            const float rho = 1.f + dd[j];
+            const float q = fmaf(uu[j], uu[j], fmaf(vv[j], vv[j], ww[j] * ww[j]));
+            const float K = fmaf(-1.5f * rho, q, dd[j]);
+            nc.U[i] = uu[j];
+            nc.V[i] = vv[j];
+            nc.W[i] = ww[j];
+            nc.K1[i] = K * (1.f / 18.f);
+            nc.A1[i] = rho * s18;
+        }
     }
 }
 
-// g for the pair (c, -c) at node i: axis links weight 1/18, diagonals 1/36
+// values of the pair (c, -c) at node i: axis links weight 1/18, diagonals 1/36
 template <int VX>
 __device__ __forceinline__ void pair_g(const NodeConst<VX> &nc, int i, float e, bool diag,
                                        float c4, float &gp, float &gm) {
@@ -127,6 +200,7 @@ __device__ __forceinline__ void pair_g(const NodeConst<VX> &nc, int i, float e, 
     }
 }
 
+// the five (c, -c) pairs with c_y(c) = +1: c = (cx, 1, cz)
 template <int VX>
 __device__ __forceinline__ float ypair_e(const NodeConst<VX> &nc, int k, int i) {
     const float u = nc.U[i], v = nc.V[i], w = nc.W[i];
@@ -156,7 +230,6 @@ __device__ __forceinline__ void st_slot(float *slot, const float (&o)[VX], int l
         *reinterpret_cast<float4 *>(slot + spos(lane, h)) =
             make_float4(o[4 * h], o[4 * h + 1], o[4 * h + 2], o[4 * h + 3]);
 }
-
 template <int VX>
 __device__ __forceinline__ void ld_slot(const float *slot, float (&o)[VX], int lane) {
 #pragma unroll
@@ -169,133 +242,234 @@ __device__ __forceinline__ void ld_slot(const float *slot, float (&o)[VX], int l
     }
 }
 
-template <int VX, int PM, int P0, int PP>
-__device__ __forceinline__ void plane_step(float (&acc)[3][VX][4], float (&F)[4][VX],
-                                           float (&Fh)[4][VX], int pz, int z0, int z1,
-                                           const TiledParams &p, int lane, int warp, int yrow,
-                                           int hrow, const float *__restrict__ in,
-                                           float *__restrict__ out, float *xs) {
+// Row-crossing values of one row for the receivers above (UP, c_y = +1) or below
+// (c_y = -1), four per receiver x:
+//   slot 0: sum of the three c_z = 0 links  (d, and +-jy)
+//   slot 1: their x-momentum                (jx)
+//   slot 2: the c_z = +1 link               (plane ahead)
+//   slot 3: the c_z = -1 link               (plane behind)
+// MODE FIRST needs slot 2 only, LAST slot 3 only.
+template <int VX, int MODE, bool UP>
+__device__ __forceinline__ void send_row(const NodeConst<VX> &nc, float c4, float *xdir, int row,
+                                         int lane) {
     using G = Geo<VX>;
-    float *buf = xs + (pz & 1) * G::BUF;  // pz may be -1: & 1 still alternates
-    float *up = buf, *dn = buf + G::DIR;
-    const long long rowoff = (long long)yrow * p.nx + lane * VX;
-    const long long hrowoff = (long long)hrow * p.nx + lane * VX;
-    const long long plane = (long long)p.nx * p.ny;
+    float *base = xdir + row * G::RL;
+    if (MODE == MID) {
+        float s0[VX], s1[VX];
+        {  // k = 0: c = (0,1,0), -c = (0,-1,0)
+            float gp[VX], gm[VX];
+#pragma unroll
+            for (int i = 0; i < VX; ++i) pair_g(nc, i, ypair_e(nc, 0, i), false, c4, gp[i], gm[i]);
+#pragma unroll
+            for (int i = 0; i < VX; ++i) s0[i] = UP ? gp[i] : gm[i];
+        }
+        {  // k = 1: c = (1,1,0) [up: receiver x <- x-1]; -c = (-1,-1,0) [down: x <- x+1]
+            float gp[VX], gm[VX];
+#pragma unroll
+            for (int i = 0; i < VX; ++i) pair_g(nc, i, ypair_e(nc, 1, i), true, c4, gp[i], gm[i]);
+            if (UP) {
+                xshift(gp, 1, lane);
+#pragma unroll
+                for (int i = 0; i < VX; ++i) {
+                    s0[i] += gp[i];
+                    s1[i] = gp[i];
+                }
+            } else {
+                xshift(gm, -1, lane);
+#pragma unroll
+                for (int i = 0; i < VX; ++i) {
+                    s0[i] += gm[i];
+                    s1[i] = -gm[i];
+                }
+            }
+        }
+        {  // k = 2: c = (-1,1,0) [up: x <- x+1]; -c = (1,-1,0) [down: x <- x-1]
+            float gp[VX], gm[VX];
+#pragma unroll
+            for (int i = 0; i < VX; ++i) pair_g(nc, i, ypair_e(nc, 2, i), true, c4, gp[i], gm[i]);
+            if (UP) {
+                xshift(gp, -1, lane);
+#pragma unroll
+                for (int i = 0; i < VX; ++i) {
+                    s0[i] += gp[i];
+                    s1[i] -= gp[i];
+                }
+            } else {
+                xshift(gm, 1, lane);
+#pragma unroll
+                for (int i = 0; i < VX; ++i) {
+                    s0[i] += gm[i];
+                    s1[i] += gm[i];
+                }
+            }
+        }
+        st_slot(base + 0 * G::XSLOT, s0, lane);
+        st_slot(base + 1 * G::XSLOT, s1, lane);
+    }
+    // k = 3: c = (0,1,1), -c = (0,-1,-1); k = 4: c = (0,1,-1), -c = (0,-1,1)
+    if (MODE != LAST) {  // slot 2 (c_z = +1): up -> c of k = 3; down -> -c of k = 4
+        float gp[VX], gm[VX];
+        const int k = UP ? 3 : 4;
+#pragma unroll
+        for (int i = 0; i < VX; ++i) pair_g(nc, i, ypair_e(nc, k, i), true, c4, gp[i], gm[i]);
+        st_slot(base + 2 * G::XSLOT, UP ? gp : gm, lane);
+    }
+    if (MODE != FIRST) {  // slot 3 (c_z = -1): up -> c of k = 4; down -> -c of k = 3
+        float gp[VX], gm[VX];
+        const int k = UP ? 4 : 3;
+#pragma unroll
+        for (int i = 0; i < VX; ++i) pair_g(nc, i, ypair_e(nc, k, i), true, c4, gp[i], gm[i]);
+        st_slot(base + 3 * G::XSLOT, UP ? gp : gm, lane);
+    }
+}
 
+// Phase A of a task: values of the staged source plane -> own accumulators and
+// the exchange buffer.
+template <int VX, int MODE, int PM, int P0, int PP>
+__device__ __forceinline__ void phase_a(float (&acc)[3][VX][4], const float *stg, float *xbuf,
+                                        const TiledParams &p, int lane, int warp) {
+    using G = Geo<VX>;
+    float *up = xbuf, *dn = xbuf + G::XDIR;
     {
         NodeConst<VX> nc;
-        node_consts(nc, F, p.s18);
-        // ---- rest link, post-combine term a rho u, z-links -------------------
+        node_consts(nc, stg + (warp + 1) * G::RL, TROWS * G::RL, lane, p.s18);
 #pragma unroll
         for (int i = 0; i < VX; ++i) {
-            // the receiver plane's z-momentum so far equals its density sum: every
-            // value it received came along a c_z = +1 link (see plane rotation)
-            acc[P0][i][3] = acc[P0][i][0];
-            acc[P0][i][0] += 6.f * nc.K1[i];  // w_0 K = K/3
-            const float ar = p.a_s * nc.A1[i];  // a rho
-            acc[P0][i][1] = fmaf(ar, nc.U[i], acc[P0][i][1]);
-            acc[P0][i][2] = fmaf(ar, nc.V[i], acc[P0][i][2]);
-            acc[P0][i][3] = fmaf(ar, nc.W[i], acc[P0][i][3]);
             float gp, gm;
             pair_g(nc, i, nc.W[i], false, p.c4, gp, gm);  // (0,0,+1) / (0,0,-1)
-            acc[PP][i][0] += gp;  // c = (0,0,+1): jz of plane PP is implied by d
-            dep(acc[PM][i], gm, 0, 0, -1);
+            if (MODE == MID) {
+                acc[P0][i][3] = acc[P0][i][0];  // jz so far = d so far (c_z = +1 arrivals)
+                acc[P0][i][0] += 6.f * nc.K1[i];  // rest link: w_0 K = K/3
+                const float ar = p.a_s * nc.A1[i];  // a rho (post-combine)
+                acc[P0][i][1] = fmaf(ar, nc.U[i], acc[P0][i][1]);
+                acc[P0][i][2] = fmaf(ar, nc.V[i], acc[P0][i][2]);
+                acc[P0][i][3] = fmaf(ar, nc.W[i], acc[P0][i][3]);
+            }
+            if (MODE != LAST) acc[PP][i][0] += gp;
+            if (MODE != FIRST) dep(acc[PM][i], gm, 0, 0, -1);
         }
-        // ---- in-row links c = (1,0,cz) / -c --------------------------------
+        // in-row pairs c = (1,0,cz) / -c = (-1,0,-cz)
 #pragma unroll
         for (int cz = -1; cz <= 1; ++cz) {
+            // c lands in plane cz, -c in plane -cz: FIRST keeps only the plane ahead,
+            // LAST only the plane behind
+            const bool need_p = MODE == MID || (MODE == FIRST ? cz > 0 : cz < 0);
+            const bool need_m = MODE == MID || (MODE == FIRST ? cz < 0 : cz > 0);
+            if (!need_p && !need_m) continue;
             float eP = 0.f, eM = 0.f;
 #pragma unroll
             for (int i = 0; i < VX; ++i) {
                 float gp, gm;
                 const float e = cz == 0 ? nc.U[i] : (cz > 0 ? nc.U[i] + nc.W[i] : nc.U[i] - nc.W[i]);
                 pair_g(nc, i, e, cz != 0, p.c4, gp, gm);
-                if (i + 1 < VX)
-                    dep(acc[pl<PM, P0, PP>(cz)][i + 1], gp, 1, 0, cz);
-                else
-                    eP = gp;
-                if (i > 0)
-                    dep(acc[pl<PM, P0, PP>(-cz)][i - 1], gm, -1, 0, -cz);
-                else
-                    eM = gm;
+                if (need_p) {
+                    if (i + 1 < VX)
+                        dep(acc[pl<PM, P0, PP>(cz)][i + 1], gp, 1, 0, cz);
+                    else
+                        eP = gp;
+                }
+                if (need_m) {
+                    if (i > 0)
+                        dep(acc[pl<PM, P0, PP>(-cz)][i - 1], gm, -1, 0, -cz);
+                    else
+                        eM = gm;
+                }
             }
-            const float rP = __shfl_sync(FULL, eP, (lane + 31) & 31);
-            const float rM = __shfl_sync(FULL, eM, (lane + 1) & 31);
-            dep(acc[pl<PM, P0, PP>(cz)][0], rP, 1, 0, cz);
-            dep(acc[pl<PM, P0, PP>(-cz)][VX - 1], rM, -1, 0, -cz);
-        }
-        // ---- row-crossing links: to shared memory ---------------------------
-#pragma unroll
-        for (int k = 0; k < 5; ++k) {
-            float gp[VX], gm[VX];
-#pragma unroll
-            for (int i = 0; i < VX; ++i) pair_g(nc, i, ypair_e(nc, k, i), k != 0, p.c4, gp[i], gm[i]);
-            if (warp + 1 < ROWS) {  // c (c_y = +1) to the next row, receiver x <- source x - cx
-                xshift(gp, ypair_cx(k), lane);
-                st_slot(up + k * G::SLOT + (warp + 1) * G::RL, gp, lane);
+            if (need_p) {
+                const float rP = __shfl_sync(FULL, eP, (lane + 31) & 31);
+                dep(acc[pl<PM, P0, PP>(cz)][0], rP, 1, 0, cz);
             }
-            if (warp > 0) {  // -c (c_y = -1) to the previous row, receiver x <- source x + cx
-                xshift(gm, -ypair_cx(k), lane);
-                st_slot(dn + k * G::SLOT + (warp - 1) * G::RL, gm, lane);
+            if (need_m) {
+                const float rM = __shfl_sync(FULL, eM, (lane + 1) & 31);
+                dep(acc[pl<PM, P0, PP>(-cz)][VX - 1], rM, -1, 0, -cz);
             }
         }
+        if (warp + 1 < ROWS) send_row<VX, MODE, true>(nc, p.c4, up, warp + 1, lane);
+        if (warp > 0) send_row<VX, MODE, false>(nc, p.c4, dn, warp - 1, lane);
     }
-    // ---- halo rows: bottom (y0-1) feeds row 0, top (y0+ROWS) feeds row ROWS-1 --
-    if (warp == 0 || warp == ROWS - 1) {
+    // halo rows: y0-1 (staged row 0) feeds row 0, y0+8 (staged row 9) feeds row 7
+    if (warp == 0) {
         NodeConst<VX> hc;
-        node_consts(hc, Fh, p.s18);
+        node_consts(hc, stg, TROWS * G::RL, lane, p.s18);
+        send_row<VX, MODE, true>(hc, p.c4, up, 0, lane);
+    } else if (warp == ROWS - 1) {
+        NodeConst<VX> hc;
+        node_consts(hc, stg + (TROWS - 1) * G::RL, TROWS * G::RL, lane, p.s18);
+        send_row<VX, MODE, false>(hc, p.c4, dn, ROWS - 1, lane);
+    }
+}
+
+// Phase B: receive the row-crossing values; plane zfin (>= 0) is then complete and
+// is stored.
+template <int VX, int MODE, int PM, int P0, int PP>
+__device__ __forceinline__ void phase_b(float (&acc)[3][VX][4], const float *xbuf, float *out,
+                                        const TiledParams &p, int lane, int warp, int col,
+                                        int zfin) {
+    using G = Geo<VX>;
+    const float *up = xbuf + warp * G::RL, *dn = xbuf + G::XDIR + warp * G::RL;
+    float o[VX];
+    if (MODE == MID) {
+        ld_slot(up, o, lane);  // from below, c_z = 0: d, +jy
 #pragma unroll
-        for (int k = 0; k < 5; ++k) {
-            float gp[VX], gm[VX];
+        for (int i = 0; i < VX; ++i) {
+            acc[P0][i][0] += o[i];
+            acc[P0][i][2] += o[i];
+        }
+        ld_slot(up + G::XSLOT, o, lane);
 #pragma unroll
-            for (int i = 0; i < VX; ++i) pair_g(hc, i, ypair_e(hc, k, i), k != 0, p.c4, gp[i], gm[i]);
-            if (warp == 0) {  // c_y = +1 values of row y0-1
-                xshift(gp, ypair_cx(k), lane);
-                st_slot(up + k * G::SLOT, gp, lane);
-            } else {  // c_y = -1 values of row y0+ROWS
-                xshift(gm, -ypair_cx(k), lane);
-                st_slot(dn + k * G::SLOT + (ROWS - 1) * G::RL, gm, lane);
-            }
+        for (int i = 0; i < VX; ++i) acc[P0][i][1] += o[i];
+        ld_slot(dn, o, lane);  // from above, c_z = 0: d, -jy
+#pragma unroll
+        for (int i = 0; i < VX; ++i) {
+            acc[P0][i][0] += o[i];
+            acc[P0][i][2] -= o[i];
+        }
+        ld_slot(dn + G::XSLOT, o, lane);
+#pragma unroll
+        for (int i = 0; i < VX; ++i) acc[P0][i][1] += o[i];
+    }
+    if (MODE != LAST) {  // c_z = +1 arrivals for the plane ahead (jz implied by d)
+        ld_slot(up + 2 * G::XSLOT, o, lane);
+#pragma unroll
+        for (int i = 0; i < VX; ++i) {
+            acc[PP][i][0] += o[i];
+            acc[PP][i][2] += o[i];
+        }
+        ld_slot(dn + 2 * G::XSLOT, o, lane);
+#pragma unroll
+        for (int i = 0; i < VX; ++i) {
+            acc[PP][i][0] += o[i];
+            acc[PP][i][2] -= o[i];
         }
     }
-
-    // ---- prefetch the next plane while the exchange completes -------------
-    if (pz + 1 <= z1) {
-        int zn = pz + 1;
-        zn = zn >= p.nz ? zn - p.nz : zn;
-        load_plane<VX>(F, in + (long long)zn * plane + rowoff, p.fstride);
-        if (warp == 0 || warp == ROWS - 1)
-            load_plane<VX>(Fh, in + (long long)zn * plane + hrowoff, p.fstride);
-    }
-    __syncthreads();
-
-    {
-        // ---- receive row-crossing links ---------------------------------------
+    if (MODE != FIRST) {  // c_z = -1 arrivals complete the plane behind
+        ld_slot(up + 3 * G::XSLOT, o, lane);
 #pragma unroll
-        for (int k = 0; k < 5; ++k) {
-            float o[VX];
-            const int cx = ypair_cx(k), cz = ypair_cz(k);
-            ld_slot(up + k * G::SLOT + warp * G::RL, o, lane);
-#pragma unroll
-            for (int i = 0; i < VX; ++i) dep(acc[pl<PM, P0, PP>(cz)][i], o[i], cx, 1, cz);
-            ld_slot(dn + k * G::SLOT + warp * G::RL, o, lane);
-#pragma unroll
-            for (int i = 0; i < VX; ++i) dep(acc[pl<PM, P0, PP>(-cz)][i], o[i], -cx, -1, -cz);
+        for (int i = 0; i < VX; ++i) {
+            acc[PM][i][0] += o[i];
+            acc[PM][i][2] += o[i];
+            acc[PM][i][3] -= o[i];
         }
-        // ---- plane pz-1 is complete: moments, store, reset ---------------------
-        const int zr = pz - 1;
-        if (zr >= z0 && zr < z1) {
-            float *o = out + (long long)zr * plane + rowoff;
+        ld_slot(dn + 3 * G::XSLOT, o, lane);
+#pragma unroll
+        for (int i = 0; i < VX; ++i) {
+            acc[PM][i][0] += o[i];
+            acc[PM][i][2] -= o[i];
+            acc[PM][i][3] -= o[i];
+        }
+        if (zfin >= 0) {
+            const long long rowoff = ((long long)zfin * p.ny + col * ROWS + warp) * p.nx + lane * VX;
+            float *op = out + rowoff;
             float r[VX];
 #pragma unroll
             for (int i = 0; i < VX; ++i) r[i] = __frcp_rn(1.f + acc[PM][i][0]);
 #pragma unroll
             for (int h = 0; h < VX / 4; ++h) {
-#define LW_ST(F, C, SC)                                                                          \
-    reinterpret_cast<float4 *>(o + (F) * p.fstride)[h] =                                         \
-        make_float4(acc[PM][4 * h][C] * (SC ? r[4 * h] : 1.f),                                   \
-                    acc[PM][4 * h + 1][C] * (SC ? r[4 * h + 1] : 1.f),                           \
-                    acc[PM][4 * h + 2][C] * (SC ? r[4 * h + 2] : 1.f),                           \
+#define LW_ST(F, C, SC)                                                                         \
+    reinterpret_cast<float4 *>(op + (F) * p.fstride)[h] =                                       \
+        make_float4(acc[PM][4 * h][C] * (SC ? r[4 * h] : 1.f),                                  \
+                    acc[PM][4 * h + 1][C] * (SC ? r[4 * h + 1] : 1.f),                          \
+                    acc[PM][4 * h + 2][C] * (SC ? r[4 * h + 2] : 1.f),                          \
                     acc[PM][4 * h + 3][C] * (SC ? r[4 * h + 3] : 1.f))
                 LW_ST(0, 0, false);
                 LW_ST(1, 1, true);
@@ -311,23 +485,60 @@ __device__ __forceinline__ void plane_step(float (&acc)[3][VX][4], float (&F)[4]
     }
 }
 
-// 8 warps: up to 255 registers per thread; launch_vx checks the occupancy
-// before the first launch.
+// issue the TMA copies of the ten staged rows of source plane z of column col
 template <int VX>
-__global__ void __launch_bounds__(NTHREADS, 1) k_d3q19_tiled(const float *__restrict__ in, float *__restrict__ out, TiledParams p) {
+__device__ __forceinline__ void issue_plane(const float *in, const TiledParams &p, int col, int z,
+                                            float *stage, uint64_t *bar) {
+    using G = Geo<VX>;
+    const int zl = z < 0 ? z + p.nz : (z >= p.nz ? z - p.nz : z);
+    const int y0 = col * ROWS;
+    const long long plane = (long long)p.nx * p.ny;
+    mbar_expect_tx(bar, G::TX);
+    const uint32_t rb = (uint32_t)(G::RL * 4);
+#pragma unroll
+    for (int f = 0; f < 4; ++f) {
+        const float *src = in + f * p.fstride + (long long)zl * plane;
+        float *dst = stage + f * TROWS * G::RL;
+        if (y0 >= 1 && y0 + ROWS < p.ny) {
+            bulk_g2s(dst, src + (long long)(y0 - 1) * p.nx, TROWS * rb, bar);
+        } else {
+            const int yb = y0 - 1 < 0 ? y0 - 1 + p.ny : y0 - 1;
+            const int yt = y0 + ROWS >= p.ny ? y0 + ROWS - p.ny : y0 + ROWS;
+            bulk_g2s(dst, src + (long long)yb * p.nx, rb, bar);
+            bulk_g2s(dst + G::RL, src + (long long)y0 * p.nx, ROWS * rb, bar);
+            bulk_g2s(dst + (TROWS - 1) * G::RL, src + (long long)yt * p.nx, rb, bar);
+        }
+    }
+}
+
+template <int VX>
+__global__ void __launch_bounds__(NTHREADS, 1)
+    k_d3q19_tiled(const float *__restrict__ in, float *__restrict__ out, TiledParams p) {
+    using G = Geo<VX>;
     extern __shared__ float4 smem4[];
     float *xs = reinterpret_cast<float *>(smem4);
+    float *stg = xs + 2 * G::XBUF;
+    uint64_t *bars = reinterpret_cast<uint64_t *>(stg + 2 * G::STAGE);
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    const int y0 = blockIdx.x * ROWS;
-    const int z0 = blockIdx.y * p.zc;
-    const int z1 = min(z0 + p.zc, p.nz);
-    const int yrow = y0 + warp;
-    // halo row of warps 0 / ROWS-1 (periodic in y); unused by the other warps
-    int hrow = warp == 0 ? y0 - 1 : y0 + ROWS;
-    hrow = hrow < 0 ? hrow + p.ny : (hrow >= p.ny ? hrow - p.ny : hrow);
-    const long long plane = (long long)p.nx * p.ny;
-    const long long rowoff = (long long)yrow * p.nx + lane * VX;
-    const long long hrowoff = (long long)hrow * p.nx + lane * VX;
+    const long long lo = p.work * blockIdx.x / gridDim.x;
+    const long long hi = p.work * (blockIdx.x + 1) / gridDim.x;
+    if (lo >= hi) return;  // uniform per CTA
+
+    if (threadIdx.x == 0) {
+        mbar_init(&bars[0], 1);
+        mbar_init(&bars[1], 1);
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    __syncthreads();
+
+    TaskIter it(lo, hi, p.nz);
+    TaskIter pf = it;  // load cursor: two tasks ahead of `it` after the prologue
+    int issued = 0;    // loads issued so far (uniform)
+    for (int k = 0; k < 2 && pf.valid(); ++k) {
+        if (threadIdx.x == 0) issue_plane<VX>(in, p, pf.col, pf.pz, stg + k * G::STAGE, &bars[k]);
+        ++issued;
+        pf.next();
+    }
 
     float acc[3][VX][4];
 #pragma unroll
@@ -336,71 +547,100 @@ __global__ void __launch_bounds__(NTHREADS, 1) k_d3q19_tiled(const float *__rest
         for (int i = 0; i < VX; ++i)
 #pragma unroll
             for (int c = 0; c < 4; ++c) acc[a][i][c] = 0.f;
-    float F[4][VX], Fh[4][VX];
-    {
-        int zs = z0 - 1;
-        zs = zs < 0 ? zs + p.nz : zs;
-        load_plane<VX>(F, in + (long long)zs * plane + rowoff, p.fstride);
-        if (warp == 0 || warp == ROWS - 1)
-            load_plane<VX>(Fh, in + (long long)zs * plane + hrowoff, p.fstride);
-    }
-    // source planes z0-1 .. z1; receiver plane pz-1 completes at source plane pz
-    for (int pz = z0 - 1; pz <= z1; pz += 3) {
-        plane_step<VX, 0, 1, 2>(acc, F, Fh, pz, z0, z1, p, lane, warp, yrow, hrow, in, out, xs);
-        if (pz + 1 <= z1)
-            plane_step<VX, 1, 2, 0>(acc, F, Fh, pz + 1, z0, z1, p, lane, warp, yrow, hrow, in, out, xs);
-        if (pz + 2 <= z1)
-            plane_step<VX, 2, 0, 1>(acc, F, Fh, pz + 2, z0, z1, p, lane, warp, yrow, hrow, in, out, xs);
-    }
-}
 
-int chunk_for(const StepParams &p) {
-    // CTAs = (ny/8) x ceil(nz/zc): aim for a whole number of waves at one CTA
-    // per SM with chunks of >= 8 planes.
-    static int sms = 0;
-    if (sms == 0) {
-        int dev = 0, n = 0;
-        if (cudaGetDevice(&dev) == cudaSuccess &&
-            cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev) == cudaSuccess && n > 0)
-            sms = n;
-        else
-            sms = 152;
-    }
-    const int ycta = p.ny / ROWS;
-    int best = p.nz, best_score = -1;
-    for (int zc = 8; zc <= p.nz; ++zc) {
-        const int nch = (p.nz + zc - 1) / zc;
-        const long long ctas = (long long)ycta * nch;
-        const long long waves = (ctas + sms - 1) / sms;
-        // efficiency: useful work / (waves * sms * zc) with a 2-plane halo cost
-        const double eff = (double)ycta * p.nz / ((double)waves * sms * (zc + 0.6));
-        const int score = (int)(eff * 1e6);
-        if (score > best_score) {
-            best_score = score;
-            best = zc;
+    for (int tc = 0; it.valid(); ++tc) {
+        const int s = tc & 1;
+        const float *stage = stg + s * G::STAGE;
+        float *xbuf = xs + s * G::XBUF;
+        const bool ok = mbar_wait(&bars[s], (uint32_t)((tc >> 1) & 1));
+        const int mode = it.mode();
+        const int k = it.pz - it.za;  // position of a MID plane within its run
+        const int len = it.zb - it.za;
+        if (ok) {
+            if (mode == FIRST) {
+                // a new run: the previous run leaves its plane-ahead partial sums behind
+#pragma unroll
+                for (int a = 0; a < 3; ++a)
+#pragma unroll
+                    for (int i = 0; i < VX; ++i)
+#pragma unroll
+                        for (int c = 0; c < 4; ++c) acc[a][i][c] = 0.f;
+                phase_a<VX, FIRST, 0, 1, 2>(acc, stage, xbuf, p, lane, warp);
+            } else if (mode == MID) {
+                switch (k % 3) {
+                    case 0: phase_a<VX, MID, 1, 2, 0>(acc, stage, xbuf, p, lane, warp); break;
+                    case 1: phase_a<VX, MID, 2, 0, 1>(acc, stage, xbuf, p, lane, warp); break;
+                    default: phase_a<VX, MID, 0, 1, 2>(acc, stage, xbuf, p, lane, warp); break;
+                }
+            } else {
+                switch ((len + 1) % 3) {
+                    case 0: phase_a<VX, LAST, 0, 1, 2>(acc, stage, xbuf, p, lane, warp); break;
+                    case 1: phase_a<VX, LAST, 1, 2, 0>(acc, stage, xbuf, p, lane, warp); break;
+                    default: phase_a<VX, LAST, 2, 0, 1>(acc, stage, xbuf, p, lane, warp); break;
+                }
+            }
         }
+        if (__syncthreads_or(ok ? 0 : 1)) {
+            // a copy never arrived: flag it, let the copies in flight land, stop
+            if (threadIdx.x == 0) {
+                atomicExch(p.err, 1);
+                for (int t = tc + 1; t < issued; ++t) mbar_wait(&bars[t & 1], (uint32_t)((t >> 1) & 1));
+            }
+            return;
+        }
+        // every warp has consumed this stage: refill it two tasks ahead
+        if (pf.valid()) {
+            if (threadIdx.x == 0) {
+                asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+                issue_plane<VX>(in, p, pf.col, pf.pz, stg + s * G::STAGE, &bars[s]);
+            }
+            ++issued;
+            pf.next();
+        }
+        if (mode == FIRST) {
+            phase_b<VX, FIRST, 0, 1, 2>(acc, xbuf, out, p, lane, warp, it.col, -1);
+        } else if (mode == MID) {
+            const int zfin = k > 0 ? it.pz - 1 : -1;
+            switch (k % 3) {
+                case 0: phase_b<VX, MID, 1, 2, 0>(acc, xbuf, out, p, lane, warp, it.col, zfin); break;
+                case 1: phase_b<VX, MID, 2, 0, 1>(acc, xbuf, out, p, lane, warp, it.col, zfin); break;
+                default: phase_b<VX, MID, 0, 1, 2>(acc, xbuf, out, p, lane, warp, it.col, zfin); break;
+            }
+        } else {
+            // the plane behind (zb - 1) completes the run
+            const int zfin = it.zb - 1;
+            switch ((len + 1) % 3) {
+                case 0: phase_b<VX, LAST, 0, 1, 2>(acc, xbuf, out, p, lane, warp, it.col, zfin); break;
+                case 1: phase_b<VX, LAST, 1, 2, 0>(acc, xbuf, out, p, lane, warp, it.col, zfin); break;
+                default: phase_b<VX, LAST, 2, 0, 1>(acc, xbuf, out, p, lane, warp, it.col, zfin); break;
+            }
+        }
+        it.next();
     }
-    return best;
 }
 
-}  // namespace
-
-// One-time set-up per kernel instance: opt in to the shared-memory size and
-// check that one CTA fits on an SM (registers + shared memory).
 template <int VX>
-static cudaError_t prepare_vx() {
-    static int state = 0;  // 0 unknown, 1 ok, -1 does not fit
+static cudaError_t prepare_vx(int *ctas) {
+    static int state = 0, nctas = 0;
     if (state == 0) {
         cudaError_t e = cudaFuncSetAttribute(k_d3q19_tiled<VX>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                              (int)Geo<VX>::BYTES);
         if (e != cudaSuccess) return e;
-        int nb = 0;
+        int nb = 0, dev = 0, sms = 0;
         e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_d3q19_tiled<VX>, NTHREADS, Geo<VX>::BYTES);
         if (e != cudaSuccess) return e;
+        e = cudaGetDevice(&dev);
+        if (e != cudaSuccess) return e;
+        e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+        if (e != cudaSuccess) return e;
         state = nb >= 1 ? 1 : -1;
+        nctas = nb * sms;
     }
+    if (ctas) *ctas = nctas;
     return state == 1 ? cudaSuccess : cudaErrorNotSupported;
 }
+
+}  // namespace
 
 bool tiled_supported(int Q, int storage, const StepParams &p) {
     if (Q != 19 || storage != STORE_F32) return false;
@@ -408,28 +648,31 @@ bool tiled_supported(int Q, int storage, const StepParams &p) {
     if (!(p.nx == 128 || p.nx == 256)) return false;
     if (p.ny % ROWS != 0 || p.ny < ROWS) return false;
     if (p.nz < 1) return false;
-    if (p.fstride % 4 != 0) return false;  // float4 rows
+    if (p.fstride % 4 != 0) return false;  // 16-byte rows for the bulk copies
+    if (!p.err) return false;
     int dev = 0;
-    if (cudaGetDevice(&dev) != cudaSuccess) return false;  // no device: cannot run it anyway
-    return (p.nx == 256 ? prepare_vx<8>() : prepare_vx<4>()) == cudaSuccess;
+    if (cudaGetDevice(&dev) != cudaSuccess) return false;
+    return (p.nx == 256 ? prepare_vx<8>(nullptr) : prepare_vx<4>(nullptr)) == cudaSuccess;
 }
 
 template <int VX>
 static cudaError_t launch_vx(const void *in, void *out, const StepParams &sp, cudaStream_t st) {
-    cudaError_t e = prepare_vx<VX>();
+    int ctas = 0;
+    cudaError_t e = prepare_vx<VX>(&ctas);
     if (e != cudaSuccess) return e;
     TiledParams p;
     p.nx = sp.nx;
     p.ny = sp.ny;
     p.nz = sp.nz;
+    p.work = (long long)(sp.ny / ROWS) * sp.nz;
     p.fstride = sp.fstride;
     const double nu = (double)sp.s / 18.0;
     p.s18 = (float)nu;
     p.c4 = (float)(1.0 / (4.0 * nu));
     p.a_s = (float)((double)sp.a / nu);
-    p.zc = chunk_for(sp);
-    dim3 grid(sp.ny / ROWS, (sp.nz + p.zc - 1) / p.zc);
-    k_d3q19_tiled<VX><<<grid, NTHREADS, Geo<VX>::BYTES, st>>>((const float *)in, (float *)out, p);
+    p.err = sp.err;
+    const long long grid = ctas < p.work ? ctas : p.work;
+    k_d3q19_tiled<VX><<<(unsigned)grid, NTHREADS, Geo<VX>::BYTES, st>>>((const float *)in, (float *)out, p);
     return cudaGetLastError();
 }
 
@@ -440,6 +683,6 @@ cudaError_t launch_step_tiled(int Q, int storage, const void *in, void *out, con
     return launch_vx<4>(in, out, p, st);
 }
 
-const char *tiled_name(int Q) { return Q == 9 ? "tiled_d2q9" : "tiled_d3q19_zmarch"; }
+const char *tiled_name(int Q) { return Q == 9 ? "tiled_d2q9" : "tiled_d3q19_tma"; }
 
 }  // namespace lwacm

@@ -33,4 +33,9 @@ cudaError_t launch_step_tiled(int Q, int storage, const void *in, void *out, con
                               cudaStream_t st);
 const char *tiled_name(int Q);
 
+// Register-prefetch z-marching variant of the D3Q19 kernel (same shapes).
+bool zmarch_supported(int Q, int storage, const StepParams &p);
+cudaError_t launch_step_zmarch(int Q, int storage, const void *in, void *out, const StepParams &p,
+                               cudaStream_t st);
+
 }  // namespace lwacm

@@ -33,7 +33,7 @@ struct lwacm_ctx {
     // workspace
     char *ws = nullptr;
     size_t ws_bytes = 0;
-    size_t off_buf[2] = {0, 0}, off_stage = 0, off_partial = 0, off_diag = 0, total = 0;
+    size_t off_buf[2] = {0, 0}, off_stage = 0, off_partial = 0, off_diag = 0, off_err = 0, total = 0;
     cudaStream_t stream = nullptr;
     bool bound = false, has_fields = false;
     int cur = 0;
@@ -45,7 +45,7 @@ struct lwacm_ctx {
     cudaStream_t cap_stream = nullptr;
     cudaGraphExec_t gexec[2] = {nullptr, nullptr};
     int gchunk[2] = {0, 0};
-    bool use_tiled = false;
+    int kernel = 1;  // 1 generic, 2 tiled (TMA), 3 z-march (register prefetch)
     std::string kname = "none";
 };
 
@@ -83,6 +83,8 @@ void layout(lwacm_ctx *c) {
     off = align_up(off + (size_t)kDiagBlocks * kDiagValues * 8, kAlign);
     c->off_diag = off;
     off = align_up(off + 16 * 8, kAlign);
+    c->off_err = off;
+    off = align_up(off + 16, kAlign);
     c->total = off;
 }
 
@@ -105,6 +107,7 @@ StepParams params(const lwacm_ctx *c) {
         p.force[a] = (float)c->force[a];
     }
     p.has_force = (c->force[0] != 0 || c->force[1] != 0 || c->force[2] != 0) ? 1 : 0;
+    p.err = c->ws ? (int *)(c->ws + c->off_err) : nullptr;
     p.walled[0] = p.walled[1] = p.walled[2] = 0;
     p.lid_axis = c->D - 1;
     if (c->bc == LWACM_BC_CAVITY) {
@@ -124,11 +127,27 @@ void drop_graphs(lwacm_ctx *c) {
     }
 }
 
-void choose_kernel(lwacm_ctx *c) {
+// Interior kernel: the explicit choice if it supports the shape, else (automatic)
+// the tiled TMA kernel, then the register-prefetch z-march kernel, then the
+// generic gather kernel, which supports everything. Returns false when an
+// explicit choice is not supported. Kernels that need the device are only
+// considered once a workspace is bound.
+bool choose_kernel(lwacm_ctx *c) {
     const StepParams p = params(c);
-    const bool ok = c->bc == LWACM_BC_PERIODIC && tiled_supported(c->Q, c->storage, p);
-    c->use_tiled = (c->kernel_opt == 2 || c->kernel_opt == 0) && ok;
-    c->kname = c->use_tiled ? tiled_name(c->Q) : (c->Q == 9 ? "generic_d2q9" : "generic_d3q19");
+    const bool dev = c->bound;
+    const bool t_ok = dev && tiled_supported(c->Q, c->storage, p);
+    const bool z_ok = dev && zmarch_supported(c->Q, c->storage, p);
+    bool ok = true;
+    switch (c->kernel_opt) {
+        case 1: c->kernel = 1; break;
+        case 2: c->kernel = t_ok ? 2 : 1; ok = t_ok || !dev; break;
+        case 3: c->kernel = z_ok ? 3 : 1; ok = z_ok || !dev; break;
+        default: c->kernel = t_ok ? 2 : (z_ok ? 3 : 1); break;
+    }
+    static const char *gname[2] = {"generic_d2q9", "generic_d3q19"};
+    c->kname = c->kernel == 2 ? tiled_name(c->Q)
+                              : (c->kernel == 3 ? "zmarch_d3q19" : gname[c->Q == 19 ? 1 : 0]);
+    return ok;
 }
 
 void *bufp(lwacm_ctx *c, int b) { return c->ws + c->off_buf[b]; }
@@ -140,8 +159,9 @@ cudaError_t enqueue_step(lwacm_ctx *c, int cur, cudaStream_t st) {
     const StepParams p = params(c);
     const void *in = bufp(c, cur);
     void *out = bufp(c, 1 - cur);
-    cudaError_t e = c->use_tiled ? launch_step_tiled(c->Q, c->storage, in, out, p, st)
-                                 : launch_step_generic(c->Q, c->storage, in, out, p, st);
+    cudaError_t e = c->kernel == 2   ? launch_step_tiled(c->Q, c->storage, in, out, p, st)
+                    : c->kernel == 3 ? launch_step_zmarch(c->Q, c->storage, in, out, p, st)
+                                     : launch_step_generic(c->Q, c->storage, in, out, p, st);
     if (e != cudaSuccess) return e;
     if (c->bc != LWACM_BC_PERIODIC) e = launch_wall_pass(c->Q, c->storage, in, out, p, st);
     return e;
@@ -251,19 +271,20 @@ lwacm_status lwacm_set_option(lwacm_ctx *c, int key, double v) {
         }
         case LWACM_OPT_KERNEL: {
             const int k = (int)v;
-            if (k < 0 || k > 2) return fail(c, LWACM_E_ARG, "kernel must be 0, 1 or 2");
+            if (k < 0 || k > 3) return fail(c, LWACM_E_ARG, "kernel must be 0, 1, 2 or 3");
+            const int old = c->kernel_opt;
             c->kernel_opt = k;
+            if (!choose_kernel(c)) {
+                c->kernel_opt = old;
+                choose_kernel(c);
+                return fail(c, LWACM_E_UNSUPPORTED, "this kernel does not support the shape/boundary/storage");
+            }
             break;
         }
         default:
             return fail(c, LWACM_E_ARG, "unknown option key");
     }
     choose_kernel(c);
-    if (c->kernel_opt == 2 && !c->use_tiled && key == LWACM_OPT_KERNEL) {
-        c->kernel_opt = 0;
-        choose_kernel(c);
-        return fail(c, LWACM_E_UNSUPPORTED, "tiled kernel does not support this shape/boundary");
-    }
     drop_graphs(c);
     return LWACM_OK;
 }
@@ -288,6 +309,12 @@ lwacm_status lwacm_bind(lwacm_ctx *c, void *ws, size_t bytes, void *stream) {
     c->has_fields = false;
     c->cur = 0;
     c->steps = 0;
+    CK(c, cudaMemsetAsync(c->ws + c->off_err, 0, 16, c->stream), "clear error word");
+    if (!choose_kernel(c)) {
+        c->kernel_opt = 0;
+        choose_kernel(c);
+        return fail(c, LWACM_E_UNSUPPORTED, "the requested kernel does not support the shape/boundary/storage");
+    }
     return LWACM_OK;
 }
 
@@ -422,8 +449,12 @@ lwacm_status lwacm_step_count(const lwacm_ctx *c, long long *steps) {
 lwacm_status lwacm_sync(lwacm_ctx *c) {
     lwacm_status s = ready(c, false);
     if (s != LWACM_OK) return s;
+    int err = 0;
+    CK(c, cudaMemcpyAsync(&err, c->ws + c->off_err, sizeof(int), cudaMemcpyDeviceToHost, c->stream),
+       "read error word");
     CK(c, cudaStreamSynchronize(c->stream), "sync");
     CK(c, cudaGetLastError(), "async error");
+    if (err) return fail(c, LWACM_E_TIMEOUT, "a device-side wait gave up (data copy did not arrive)");
     return LWACM_OK;
 }
 

@@ -90,6 +90,7 @@ struct StepParams {
     int has_force;
     int walled[3];      // 1 = half-way walls on both ends of this axis
     int lid_axis;       // axis whose top wall moves with the lid velocity
+    int *err;           // device error word (bounded waits that gave up set it)
 };
 
 // g_i at a node with fields (d, u), for a link with integer velocity (cx,cy,cz)
