@@ -40,7 +40,8 @@ constexpr unsigned FULL = 0xffffffffu;
 
 struct TiledParams {
     int nx, ny, nz;
-    long long work;      // (ny / ROWS) * nz plane-rows
+    int ycols;           // ny / ROWS
+    int zc, nitems;      // planes per chunk, ycols * ceil(nz / zc)
     long long fstride;
     float s18;           // s / 18 = nu
     float c4;            // 1 / (4 nu)
@@ -98,33 +99,36 @@ __device__ __forceinline__ void bulk_g2s(void *dst, const void *src, uint32_t by
 }
 
 // ---- task iteration -------------------------------------------------------------
-// A CTA's range [lo, hi) of plane-rows (index = col * nz + z) splits into runs of
-// consecutive z in one column. A run [za, zb) is processed as source planes
-// za-1 (FIRST), za .. zb-1 (MID), zb (LAST).
+// Work items are (column, z-chunk) pairs, numbered chunk-major (item = chunk * ycols
+// + col) so that the CTAs working on neighbouring columns march through the same
+// planes together and share their halo rows in L2. CTA b takes items b, b + G,
+// b + 2G, ... (G = grid size). An item is a run [za, zb) of planes of one column,
+// processed as source planes za-1 (FIRST), za .. zb-1 (MID), zb (LAST).
 enum { FIRST = 0, MID = 1, LAST = 2 };
 
 struct TaskIter {
-    long long idx, hi;
-    int nz, col, za, zb, pz;
+    int item, nitems, stride, ycols, zc, nz;
+    int col, za, zb, pz;
     __device__ void start_run() {
-        col = (int)(idx / nz);
-        za = (int)(idx % nz);
-        const long long rest = hi - idx;
-        zb = za + (int)(rest < (long long)(nz - za) ? rest : (long long)(nz - za));
+        col = item % ycols;
+        const int ch = item / ycols;
+        za = ch * zc;
+        zb = za + zc < nz ? za + zc : nz;
         pz = za - 1;
     }
-    __device__ TaskIter(long long lo, long long hi_, int nz_) : idx(lo), hi(hi_), nz(nz_) {
+    __device__ TaskIter(int first, int nitems_, int stride_, int ycols_, int zc_, int nz_)
+        : item(first), nitems(nitems_), stride(stride_), ycols(ycols_), zc(zc_), nz(nz_) {
         col = za = zb = pz = 0;
-        if (idx < hi) start_run();
+        if (item < nitems) start_run();
     }
-    __device__ bool valid() const { return idx < hi; }
+    __device__ bool valid() const { return item < nitems; }
     __device__ int mode() const { return pz < za ? FIRST : (pz < zb ? MID : LAST); }
     __device__ void next() {
         if (pz < zb) {
             ++pz;
         } else {
-            idx += zb - za;
-            if (idx < hi) start_run();
+            item += stride;
+            if (item < nitems) start_run();
         }
     }
 };
@@ -511,6 +515,21 @@ __device__ __forceinline__ void issue_plane(const float *in, const TiledParams &
     }
 }
 
+// After a MID plane, plane z-1 has been stored and zeroed: shift the window so
+// that index 0 is again the plane behind, 1 the current plane, 2 the plane ahead.
+template <int VX>
+__device__ __forceinline__ void rotate(float (&acc)[3][VX][4]) {
+#pragma unroll
+    for (int i = 0; i < VX; ++i) {
+#pragma unroll
+        for (int c = 0; c < 4; ++c) acc[0][i][c] = acc[1][i][c];
+#pragma unroll
+        for (int c = 0; c < 3; ++c) acc[1][i][c] = acc[2][i][c];  // jz of the plane ahead is implied
+#pragma unroll
+        for (int c = 0; c < 4; ++c) acc[2][i][c] = 0.f;
+    }
+}
+
 template <int VX>
 __global__ void __launch_bounds__(NTHREADS, 1)
     k_d3q19_tiled(const float *__restrict__ in, float *__restrict__ out, TiledParams p) {
@@ -520,9 +539,7 @@ __global__ void __launch_bounds__(NTHREADS, 1)
     float *stg = xs + 2 * G::XBUF;
     uint64_t *bars = reinterpret_cast<uint64_t *>(stg + 2 * G::STAGE);
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    const long long lo = p.work * blockIdx.x / gridDim.x;
-    const long long hi = p.work * (blockIdx.x + 1) / gridDim.x;
-    if (lo >= hi) return;  // uniform per CTA
+    if ((int)blockIdx.x >= p.nitems) return;  // uniform per CTA
 
     if (threadIdx.x == 0) {
         mbar_init(&bars[0], 1);
@@ -531,7 +548,7 @@ __global__ void __launch_bounds__(NTHREADS, 1)
     }
     __syncthreads();
 
-    TaskIter it(lo, hi, p.nz);
+    TaskIter it(blockIdx.x, p.nitems, gridDim.x, p.ycols, p.zc, p.nz);
     TaskIter pf = it;  // load cursor: two tasks ahead of `it` after the prologue
     int issued = 0;    // loads issued so far (uniform)
     for (int k = 0; k < 2 && pf.valid(); ++k) {
@@ -540,6 +557,7 @@ __global__ void __launch_bounds__(NTHREADS, 1)
         pf.next();
     }
 
+    // accumulators: [0] plane behind, [1] current plane, [2] plane ahead
     float acc[3][VX][4];
 #pragma unroll
     for (int a = 0; a < 3; ++a)
@@ -554,31 +572,13 @@ __global__ void __launch_bounds__(NTHREADS, 1)
         float *xbuf = xs + s * G::XBUF;
         const bool ok = mbar_wait(&bars[s], (uint32_t)((tc >> 1) & 1));
         const int mode = it.mode();
-        const int k = it.pz - it.za;  // position of a MID plane within its run
-        const int len = it.zb - it.za;
         if (ok) {
-            if (mode == FIRST) {
-                // a new run: the previous run leaves its plane-ahead partial sums behind
-#pragma unroll
-                for (int a = 0; a < 3; ++a)
-#pragma unroll
-                    for (int i = 0; i < VX; ++i)
-#pragma unroll
-                        for (int c = 0; c < 4; ++c) acc[a][i][c] = 0.f;
+            if (mode == MID)
+                phase_a<VX, MID, 0, 1, 2>(acc, stage, xbuf, p, lane, warp);
+            else if (mode == FIRST)
                 phase_a<VX, FIRST, 0, 1, 2>(acc, stage, xbuf, p, lane, warp);
-            } else if (mode == MID) {
-                switch (k % 3) {
-                    case 0: phase_a<VX, MID, 1, 2, 0>(acc, stage, xbuf, p, lane, warp); break;
-                    case 1: phase_a<VX, MID, 2, 0, 1>(acc, stage, xbuf, p, lane, warp); break;
-                    default: phase_a<VX, MID, 0, 1, 2>(acc, stage, xbuf, p, lane, warp); break;
-                }
-            } else {
-                switch ((len + 1) % 3) {
-                    case 0: phase_a<VX, LAST, 0, 1, 2>(acc, stage, xbuf, p, lane, warp); break;
-                    case 1: phase_a<VX, LAST, 1, 2, 0>(acc, stage, xbuf, p, lane, warp); break;
-                    default: phase_a<VX, LAST, 2, 0, 1>(acc, stage, xbuf, p, lane, warp); break;
-                }
-            }
+            else
+                phase_a<VX, LAST, 0, 1, 2>(acc, stage, xbuf, p, lane, warp);
         }
         if (__syncthreads_or(ok ? 0 : 1)) {
             // a copy never arrived: flag it, let the copies in flight land, stop
@@ -597,23 +597,23 @@ __global__ void __launch_bounds__(NTHREADS, 1)
             ++issued;
             pf.next();
         }
-        if (mode == FIRST) {
+        if (mode == MID) {
+            phase_b<VX, MID, 0, 1, 2>(acc, xbuf, out, p, lane, warp, it.col,
+                                      it.pz > it.za ? it.pz - 1 : -1);
+            rotate(acc);
+        } else if (mode == FIRST) {
             phase_b<VX, FIRST, 0, 1, 2>(acc, xbuf, out, p, lane, warp, it.col, -1);
-        } else if (mode == MID) {
-            const int zfin = k > 0 ? it.pz - 1 : -1;
-            switch (k % 3) {
-                case 0: phase_b<VX, MID, 1, 2, 0>(acc, xbuf, out, p, lane, warp, it.col, zfin); break;
-                case 1: phase_b<VX, MID, 2, 0, 1>(acc, xbuf, out, p, lane, warp, it.col, zfin); break;
-                default: phase_b<VX, MID, 0, 1, 2>(acc, xbuf, out, p, lane, warp, it.col, zfin); break;
-            }
+            rotate(acc);  // plane za becomes the current plane
         } else {
-            // the plane behind (zb - 1) completes the run
-            const int zfin = it.zb - 1;
-            switch ((len + 1) % 3) {
-                case 0: phase_b<VX, LAST, 0, 1, 2>(acc, xbuf, out, p, lane, warp, it.col, zfin); break;
-                case 1: phase_b<VX, LAST, 1, 2, 0>(acc, xbuf, out, p, lane, warp, it.col, zfin); break;
-                default: phase_b<VX, LAST, 2, 0, 1>(acc, xbuf, out, p, lane, warp, it.col, zfin); break;
-            }
+            // LAST: the plane behind (zb - 1) completes the run; clear the plane
+            // ahead's partial sums before the next run
+            phase_b<VX, LAST, 0, 1, 2>(acc, xbuf, out, p, lane, warp, it.col, it.zb - 1);
+#pragma unroll
+            for (int a = 1; a < 3; ++a)
+#pragma unroll
+                for (int i = 0; i < VX; ++i)
+#pragma unroll
+                    for (int c = 0; c < 4; ++c) acc[a][i][c] = 0.f;
         }
         it.next();
     }
@@ -640,6 +640,25 @@ static cudaError_t prepare_vx(int *ctas) {
     return state == 1 ? cudaSuccess : cudaErrorNotSupported;
 }
 
+// Planes per chunk: minimise the per-CTA critical path, i.e. the number of items
+// per CTA times (planes per chunk + the two z-halo planes at about 0.35 of a
+// plane each), over chunks of 4 .. nz planes.
+int chunk_planes(int ycols, int nz, int ctas) {
+    if (ctas < 1) ctas = 1;
+    int best = nz;
+    double best_t = 1e300;
+    for (int zc = (nz < 4 ? nz : 4); zc <= nz; ++zc) {
+        const long long items = (long long)ycols * ((nz + zc - 1) / zc);
+        const long long per = (items + ctas - 1) / ctas;
+        const double t = (double)per * (zc + 0.7);
+        if (t < best_t - 1e-9) {
+            best_t = t;
+            best = zc;
+        }
+    }
+    return best;
+}
+
 }  // namespace
 
 bool tiled_supported(int Q, int storage, const StepParams &p) {
@@ -664,14 +683,16 @@ static cudaError_t launch_vx(const void *in, void *out, const StepParams &sp, cu
     p.nx = sp.nx;
     p.ny = sp.ny;
     p.nz = sp.nz;
-    p.work = (long long)(sp.ny / ROWS) * sp.nz;
+    p.ycols = sp.ny / ROWS;
+    p.zc = chunk_planes(p.ycols, sp.nz, ctas);
+    p.nitems = p.ycols * ((sp.nz + p.zc - 1) / p.zc);
     p.fstride = sp.fstride;
     const double nu = (double)sp.s / 18.0;
     p.s18 = (float)nu;
     p.c4 = (float)(1.0 / (4.0 * nu));
     p.a_s = (float)((double)sp.a / nu);
     p.err = sp.err;
-    const long long grid = ctas < p.work ? ctas : p.work;
+    const int grid = ctas < p.nitems ? ctas : p.nitems;
     k_d3q19_tiled<VX><<<(unsigned)grid, NTHREADS, Geo<VX>::BYTES, st>>>((const float *)in, (float *)out, p);
     return cudaGetLastError();
 }
