@@ -167,6 +167,34 @@ const char *lwacm_kernel_name(const lwacm_ctx *ctx);
  * workspace, which belongs to the caller. NULL is allowed. */
 void lwacm_destroy(lwacm_ctx *ctx);
 
+/* Allocation-free diagnostics (the paper has no counterpart; this is a service
+ * of the library).
+ *
+ * For callers that cannot allocate device memory or bind a workspace: code
+ * running where cudaMalloc is forbidden or unavailable, or a tool that only sees
+ * the field arrays of a running simulation. Computes the same eight FP64 global
+ * quantities as lwacm_diagnostics, plus out_dev[8] = the number of nodes with a
+ * non-finite value, from caller-owned device arrays d, ux, uy (and uz, or NULL for
+ * 2D) of n nodes of type dtype (LWACM_F32, LWACM_BF16 or LWACM_F16), into the
+ * caller-owned device array out_dev (9 doubles). Stream-ordered on `stream`
+ * (cudaStream_t; NULL = legacy default stream); it does not synchronise.
+ *
+ * It allocates nothing: the per-block partial sums live in a fixed device array
+ * of 72 KiB inside this library (held on every GPU that loads the library until
+ * the process exits), which limits n to LWACM_NOALLOC_MAX_N nodes; larger n
+ * returns LWACM_E_RANGE without launching anything. The first call on each
+ * device looks up that array's device address (with the device current), so
+ * make the first call on a device before any stream capture. All calls share
+ * the array: calls whose kernels overlap on the GPU (different streams, or
+ * different host threads) race on it and must be ordered by the caller. Every
+ * slot a call reads is written by that same call, so no clearing is needed.
+ * Errors: LWACM_E_ARG (null pointer, n < 1, bad dtype), LWACM_E_RANGE,
+ * LWACM_E_CUDA (launch failure). */
+#define LWACM_NOALLOC_MAX_N 33554432LL
+lwacm_status lwacm_diagnostics_noalloc(const void *d, const void *ux, const void *uy,
+                                       const void *uz, long long n, int dtype, double *out_dev,
+                                       void *stream);
+
 #ifdef __cplusplus
 }
 #endif
