@@ -150,6 +150,37 @@ lwacm_status lwacm_get_fields(lwacm_ctx *ctx, void *d, void *ux, void *uy, void 
  * Returns LWACM_E_NONFINITE (and still fills out) if any value is NaN/Inf. */
 lwacm_status lwacm_diagnostics(lwacm_ctx *ctx, double out[8]);
 
+/* ---- Adjoint (reverse-mode derivative of T steps) -----------------------------
+ * The derivative of a scalar loss L of the state after T steps with respect to
+ * the initial state (d, u) and to nu, by the chain rule through the moment form
+ * of Eq. ACM2.0 (nu enters through a = 1 - 6 nu, Eq. ACM2.0nu, and the 18 nu of
+ * the pre-combined values). Periodic domains with FP32 storage (and optional
+ * forcing); other setups return LWACM_E_UNSUPPORTED. Memory is the caller's:
+ * ceil(T/S) checkpoints of the state plus S+1 segment states and three lambda
+ * states, S = stride (0 = ceil(sqrt(T))). */
+
+/* Bytes of adjoint workspace lwacm_forward_record needs for T steps. */
+lwacm_status lwacm_adjoint_workspace_bytes(const lwacm_ctx *ctx, long long T, int stride,
+                                           size_t *bytes);
+
+/* Advance the current state by T steps (as lwacm_step) while keeping a checkpoint
+ * every S steps in the caller's device workspace (256-byte aligned, >=
+ * lwacm_adjoint_workspace_bytes). The context then holds the state after T steps
+ * and remembers the run for lwacm_backward; the workspace must stay valid until
+ * then. */
+lwacm_status lwacm_forward_record(lwacm_ctx *ctx, long long T, int stride, void *dev_workspace,
+                                  size_t bytes);
+
+/* Given lambda_T = dL/d(d, ux, uy[, uz]) at the end of the recorded run (device
+ * arrays of nx*ny*nz elements of dtype LWACM_F32 or LWACM_F64; luz NULL in 2D),
+ * write dL/d(d, ux, uy[, uz]) at its start into the device arrays gd, gux, guy,
+ * guz (same dtype) and dL/dnu into *g_nu (host). Recomputes each segment from its
+ * checkpoint and runs the adjoint step backwards through it; FP32 arithmetic,
+ * FP64 accumulation of dL/dnu. Synchronises the bound stream. */
+lwacm_status lwacm_backward(lwacm_ctx *ctx, const void *ld, const void *lux, const void *luy,
+                            const void *luz, int dtype, void *gd, void *gux, void *guy, void *guz,
+                            double *g_nu);
+
 /* Number of completed steps since the last lwacm_set_fields. */
 lwacm_status lwacm_step_count(const lwacm_ctx *ctx, long long *steps);
 

@@ -33,6 +33,13 @@ cudaError_t launch_step_tiled(int Q, int storage, const void *in, void *out, con
                               cudaStream_t st);
 const char *tiled_name(int Q);
 
+// Adjoint of one step (periodic; kernels_adjoint.cu): lambda_t from lambda_t1, the
+// states at t and t+1; dj is scratch for (Dbar, Jbar); adds dL/dnu to *nu_total.
+int adjoint_partials();
+cudaError_t launch_adjoint_step(int Q, const float *state_t, const float *state_t1, const float *lam_t1,
+                                float *dj, float *lam_t, const StepParams &p, double *nu_partial,
+                                double *nu_total, cudaStream_t st);
+
 // Register-prefetch z-marching variant of the D3Q19 kernel (same shapes).
 bool zmarch_supported(int Q, int storage, const StepParams &p);
 cudaError_t launch_step_zmarch(int Q, int storage, const void *in, void *out, const StepParams &p,

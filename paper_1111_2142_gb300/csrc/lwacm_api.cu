@@ -2,6 +2,7 @@
 // layout, field transfer, stepping (with captured CUDA graphs) and diagnostics.
 #include <cuda_runtime.h>
 
+#include <algorithm>
 #include <cmath>
 #include <cstdio>
 #include <cstring>
@@ -47,6 +48,11 @@ struct lwacm_ctx {
     int gchunk[2] = {0, 0};
     int kernel = 1;  // 1 generic, 2 tiled (TMA), 3 z-march (register prefetch)
     std::string kname = "none";
+    // recorded forward run for lwacm_backward
+    char *adj = nullptr;
+    size_t adj_bytes = 0;
+    long long rec_T = -1;
+    int rec_S = 0;
 };
 
 namespace {
@@ -155,17 +161,49 @@ void *bufp(lwacm_ctx *c, int b) { return c->ws + c->off_buf[b]; }
 
 size_t field_bytes(const lwacm_ctx *c) { return (size_t)c->Nal * esize(c->storage); }
 
-// enqueue one time step: buffer cur -> buffer 1-cur
-cudaError_t enqueue_step(lwacm_ctx *c, int cur, cudaStream_t st) {
+// enqueue one time step from state `in` to state `out` (each nf fields x Nal)
+cudaError_t step_between(lwacm_ctx *c, const void *in, void *out, cudaStream_t st) {
     const StepParams p = params(c);
-    const void *in = bufp(c, cur);
-    void *out = bufp(c, 1 - cur);
     cudaError_t e = c->kernel == 2   ? launch_step_tiled(c->Q, c->storage, in, out, p, st)
                     : c->kernel == 3 ? launch_step_zmarch(c->Q, c->storage, in, out, p, st)
                                      : launch_step_generic(c->Q, c->storage, in, out, p, st);
     if (e != cudaSuccess) return e;
     if (c->bc != LWACM_BC_PERIODIC) e = launch_wall_pass(c->Q, c->storage, in, out, p, st);
     return e;
+}
+
+// enqueue one time step: buffer cur -> buffer 1-cur
+cudaError_t enqueue_step(lwacm_ctx *c, int cur, cudaStream_t st) {
+    return step_between(c, bufp(c, cur), bufp(c, 1 - cur), st);
+}
+
+// adjoint workspace: K checkpoints, S+1 segment states, 2 lambda states, (Dbar, Jbar),
+// dL/dnu partials and total
+struct AdjLayout {
+    long long K = 0;
+    int S = 0;
+    size_t state = 0, ckpt = 0, seg = 0, lam = 0, dj = 0, part = 0, total = 0, bytes = 0;
+};
+AdjLayout adj_layout(const lwacm_ctx *c, long long T, int stride) {
+    AdjLayout L;
+    L.S = stride > 0 ? stride : (int)std::ceil(std::sqrt((double)(T > 0 ? T : 1)));
+    L.K = T > 0 ? (T + L.S - 1) / L.S : 1;
+    L.state = align_up((size_t)c->Nal * 4 * c->nf, kAlign);
+    size_t off = 0;
+    L.ckpt = off;
+    off += L.state * (size_t)L.K;
+    L.seg = off;
+    off += L.state * (size_t)(L.S + 1);
+    L.lam = off;
+    off += L.state * 2;
+    L.dj = off;
+    off += L.state;
+    L.part = off;
+    off = align_up(off + (size_t)adjoint_partials() * 8, kAlign);
+    L.total = off;
+    off = align_up(off + 64, kAlign);
+    L.bytes = off;
+    return L;
 }
 
 lwacm_status ready(lwacm_ctx *c, bool need_fields) {
@@ -438,6 +476,96 @@ lwacm_status lwacm_diagnostics(lwacm_ctx *c, double out[8]) {
     for (int k = 0; k < 8; ++k) out[k] = h[k];
     out[5] = std::sqrt(h[5]);
     if (h[8] != 0.0) return fail(c, LWACM_E_NONFINITE, "non-finite values in the fields");
+    return LWACM_OK;
+}
+
+lwacm_status lwacm_adjoint_workspace_bytes(const lwacm_ctx *c, long long T, int stride,
+                                           size_t *bytes) {
+    if (!c || !bytes || T < 0 || stride < 0) return LWACM_E_ARG;
+    *bytes = adj_layout(c, T, stride).bytes;
+    return LWACM_OK;
+}
+
+lwacm_status lwacm_forward_record(lwacm_ctx *c, long long T, int stride, void *ws, size_t bytes) {
+    lwacm_status s = ready(c, true);
+    if (s != LWACM_OK) return s;
+    if (T < 0 || stride < 0 || !ws) return fail(c, LWACM_E_ARG, "T >= 0, stride >= 0, workspace required");
+    if (((uintptr_t)ws) % kAlign) return fail(c, LWACM_E_ARG, "adjoint workspace not 256-byte aligned");
+    if (c->storage != LWACM_F32 || c->bc != LWACM_BC_PERIODIC)
+        return fail(c, LWACM_E_UNSUPPORTED, "the adjoint needs FP32 storage and a periodic domain");
+    const AdjLayout L = adj_layout(c, T, stride);
+    if (bytes < L.bytes) return fail(c, LWACM_E_NOMEM, "adjoint workspace smaller than lwacm_adjoint_workspace_bytes");
+    c->adj = (char *)ws;
+    c->adj_bytes = bytes;
+    const size_t sb = (size_t)c->Nal * 4 * c->nf;
+    for (long long k = 0; k < L.K; ++k) {
+        CK(c, cudaMemcpyAsync(c->adj + L.ckpt + k * L.state, bufp(c, c->cur), sb, cudaMemcpyDeviceToDevice,
+                              c->stream),
+           "checkpoint copy");
+        const long long n = std::min<long long>(L.S, T - k * L.S);
+        if (n > 0) {
+            s = lwacm_step(c, n);
+            if (s != LWACM_OK) return s;
+        }
+    }
+    c->rec_T = T;
+    c->rec_S = L.S;
+    return LWACM_OK;
+}
+
+lwacm_status lwacm_backward(lwacm_ctx *c, const void *ld, const void *lux, const void *luy,
+                            const void *luz, int dtype, void *gd, void *gux, void *guy, void *guz,
+                            double *g_nu) {
+    lwacm_status s = ready(c, false);
+    if (s != LWACM_OK) return s;
+    if (c->rec_T < 0 || !c->adj) return fail(c, LWACM_E_STATE, "no recorded run (call lwacm_forward_record)");
+    if (!ld || !lux || !luy || !gd || !gux || !guy || !g_nu || (c->Q == 19 && (!luz || !guz)))
+        return fail(c, LWACM_E_ARG, "null argument");
+    if (dtype != LWACM_F32 && dtype != LWACM_F64) return fail(c, LWACM_E_ARG, "dtype must be F32 or F64");
+    const long long T = c->rec_T;
+    const AdjLayout L = adj_layout(c, T, c->rec_S);
+    const size_t sb = (size_t)c->Nal * 4 * c->nf;
+    const size_t fb = (size_t)c->Nal * 4;
+    char *A = c->adj;
+    float *lam[2] = {(float *)(A + L.lam), (float *)(A + L.lam + L.state)};
+    float *dj = (float *)(A + L.dj);
+    double *part = (double *)(A + L.part), *total = (double *)(A + L.total);
+    const void *lin[4] = {ld, lux, luy, luz};
+    for (int f = 0; f < c->nf; ++f)
+        CK(c, launch_convert_in(STORE_F32, dtype, lin[f], (char *)lam[0] + f * fb, c->N, c->stream), "lambda in");
+    CK(c, cudaMemsetAsync(total, 0, sizeof(double), c->stream), "clear dnu");
+    const StepParams p = params(c);
+    int cur = 0;
+    for (long long k = L.K - 1; k >= 0; --k) {
+        const long long t0 = k * L.S;
+        const long long len = std::min<long long>(L.S, T - t0);
+        char *seg = A + L.seg;
+        CK(c, cudaMemcpyAsync(seg, A + L.ckpt + k * L.state, sb, cudaMemcpyDeviceToDevice, c->stream),
+           "segment restore");
+        for (long long j = 0; j < len; ++j)
+            CK(c, step_between(c, seg + j * L.state, seg + (j + 1) * L.state, c->stream), "segment recompute");
+        for (long long j = len - 1; j >= 0; --j) {
+            CK(c, launch_adjoint_step(c->Q, (const float *)(seg + j * L.state),
+                                      (const float *)(seg + (j + 1) * L.state), lam[cur], dj, lam[1 - cur], p,
+                                      part, total, c->stream),
+               "adjoint step");
+            cur ^= 1;
+        }
+    }
+    void *gout[4] = {gd, gux, guy, guz};
+    for (int f = 0; f < c->nf; ++f) {
+        if (dtype == LWACM_F32)
+            CK(c, cudaMemcpyAsync(gout[f], (char *)lam[cur] + f * fb, (size_t)c->N * 4, cudaMemcpyDeviceToDevice,
+                                  c->stream),
+               "gradient out");
+        else
+            CK(c, launch_convert_out(STORE_F32, LWACM_F64, (char *)lam[cur] + f * fb, gout[f], c->N, c->stream),
+               "gradient out");
+    }
+    double h = 0.0;
+    CK(c, cudaMemcpyAsync(&h, total, sizeof(double), cudaMemcpyDeviceToHost, c->stream), "dnu out");
+    CK(c, cudaStreamSynchronize(c->stream), "sync");
+    *g_nu = h;
     return LWACM_OK;
 }
 

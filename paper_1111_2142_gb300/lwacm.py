@@ -59,6 +59,10 @@ def load():
         "lwacm_diagnostics": [vp, P(d)],
         "lwacm_step_count": [vp, P(ll)],
         "lwacm_sync": [vp],
+        "lwacm_adjoint_workspace_bytes": [vp, ll, i, P(ctypes.c_size_t)],
+        "lwacm_forward_record": [vp, ll, i, vp, ctypes.c_size_t],
+        "lwacm_backward": [vp, vp, vp, vp, vp, i, vp, vp, vp, vp, P(d)],
+        "lwacm_diagnostics_noalloc": [vp, vp, vp, vp, ll, i, vp, vp],
     }
     for name, args in sig.items():
         fn = getattr(lib, name)
@@ -235,6 +239,32 @@ class Lwacm:
             views.append(self.workspace[off:off + n * esz].view(tdt).view(self.shape))
         return tuple(views)
 
+    # -- adjoint --
+    def forward_record(self, T, stride=0):
+        """Advance T steps keeping sqrt(T) checkpoints (lwacm_forward_record); the
+        adjoint workspace is a torch tensor owned by this object."""
+        torch = _torch()
+        nb = ctypes.c_size_t()
+        self._check(self._lib.lwacm_adjoint_workspace_bytes(self._h, int(T), int(stride),
+                                                             ctypes.byref(nb)))
+        if getattr(self, "adj_workspace", None) is None or self.adj_workspace.numel() < nb.value:
+            self.adj_workspace = torch.empty(nb.value, dtype=torch.uint8, device=self.device)
+        self._check(self._lib.lwacm_forward_record(self._h, int(T), int(stride),
+                                                   self.adj_workspace.data_ptr(), nb.value))
+
+    def backward(self, lam):
+        """lam: dL/d(d, ux, uy[, uz]) at the end of the recorded run (CUDA tensors,
+        float32 or float64). Returns (grads at the start, dL/dnu)."""
+        torch = _torch()
+        lam = [t.contiguous() for t in lam]
+        code = F64 if lam[0].dtype == torch.float64 else F32
+        outs = [torch.empty_like(t) for t in lam]
+        ptrs_in = [t.data_ptr() for t in lam] + [None] * (4 - len(lam))
+        ptrs_out = [t.data_ptr() for t in outs] + [None] * (4 - len(outs))
+        g_nu = ctypes.c_double()
+        self._check(self._lib.lwacm_backward(self._h, *ptrs_in, code, *ptrs_out, ctypes.byref(g_nu)))
+        return tuple(outs), g_nu.value
+
     def diagnostics(self):
         out = (ctypes.c_double * 8)()
         st = self._lib.lwacm_diagnostics(self._h, out)
@@ -243,3 +273,50 @@ class Lwacm:
         if st not in (OK, E_NONFINITE):
             self._check(st)
         return res
+
+
+def _make_function():
+    torch = _torch()
+
+    class LwacmRun(torch.autograd.Function):
+        """T LW-ACM steps as a differentiable function of the initial fields and nu.
+
+        forward(sim, T, stride, nu, d0, ux0, uy0[, uz0]) -> (d, ux, uy[, uz]) after T
+        steps (CUDA float32 tensors); backward uses the hand-written adjoint kernels
+        with sqrt(T) checkpointing (lwacm_forward_record / lwacm_backward). `nu` is a
+        0-d tensor equal to the simulation's viscosity; its gradient is dL/dnu.
+        """
+
+        @staticmethod
+        def forward(ctx, sim, T, stride, nu, *fields):
+            sim.set_fields(*[f.detach().to(torch.float32) for f in fields])
+            sim.forward_record(int(T), int(stride))
+            outs = [torch.empty(sim.shape, dtype=torch.float32, device=sim.device)
+                    for _ in range(sim.nf)]
+            sim.get_fields_into(outs, DEVICE)
+            ctx.sim = sim
+            ctx.nu_dtype = nu.dtype if torch.is_tensor(nu) else torch.float64
+            return tuple(outs)
+
+        @staticmethod
+        def backward(ctx, *grads):
+            sim = ctx.sim
+            lam = [g if g is not None else torch.zeros(sim.shape, device=sim.device)
+                   for g in grads]
+            lam = [g.to(torch.float32).contiguous() for g in lam]
+            gfields, g_nu = sim.backward(lam)
+            return (None, None, None, torch.tensor(g_nu, dtype=ctx.nu_dtype), *gfields)
+
+    return LwacmRun
+
+
+_LwacmRun = None
+
+
+def run(sim, T, nu, *fields, stride=0):
+    """Differentiable T-step run: returns the fields after T steps; gradients flow
+    to `fields` and to the 0-d tensor `nu` (which must equal the sim's viscosity)."""
+    global _LwacmRun
+    if _LwacmRun is None:
+        _LwacmRun = _make_function()
+    return _LwacmRun.apply(sim, T, stride, nu, *fields)
