@@ -112,14 +112,22 @@ def test_autograd_function(lw):
 def test_adjoint_central_differences_128(lw):
     """The adjoint workload: D3Q19 128^3 periodic, initial velocity divergence-free
     (wave numbers 1-8, rms 0.03, seed 2), target from seed 3, nu = 0.01, T = 500.
-    Directional derivatives along random unit-rms directions (seed 4) from the
-    adjoint vs FP32 central differences of the loss (accumulated in FP64), step
-    h = 1e-2 * rms(u0); and dJ/dnu vs a central difference in nu. Bound 1e-4
-    relative (the FP32 forward's rounding noise divided by h is below it)."""
+    * Directional derivatives along 32 random unit-rms directions (seed 4) from the
+      adjoint vs FP32 central differences of the GPU loss (accumulated in FP64),
+      step h = 3e-2 * rms(u0). Error measure: |fd - an| / |an| over the vector of
+      the 32 directional derivatives (a single direction nearly orthogonal to the
+      gradient has a tiny |an|, and its ratio measures the FP32 noise, not the
+      adjoint): bound 1e-4.
+    * dJ/dnu vs a central difference of the FP64 oracle's loss in nu (h = 1e-5):
+      a change of nu changes every rounding of an FP32 run, so an FP32 difference
+      in nu is too noisy to check against; the FP64 one is exact to ~1e-8. The GPU
+      value carries the FP32 forward's and adjoint's rounding: bound 5e-4 relative.
+    """
     import torch
     n, T, nu = 128, 500, 0.01
     st = inputs.random_divfree_3d(n, n, n, rms=0.03, kmax=8, seed=2)
-    tgt = [torch.tensor(a, device="cuda") for a in inputs.random_divfree_3d(n, n, n, rms=0.03, kmax=8, seed=3)[1:]]
+    tgt_np = inputs.random_divfree_3d(n, n, n, rms=0.03, kmax=8, seed=3)[1:]
+    tgt = [torch.tensor(a, device="cuda") for a in tgt_np]
     sim = lw.Lwacm(19, n, n, n, nu)
     f32 = [torch.tensor(a, dtype=torch.float32, device="cuda") for a in st]
 
@@ -128,7 +136,7 @@ def test_adjoint_central_differences_128(lw):
         sim_.step(T)
         outs = [torch.empty((n, n, n), dtype=torch.float32, device="cuda") for _ in range(4)]
         sim_.get_fields_into(outs)
-        return sum(0.5 * ((o.double() - t) ** 2).sum().item() for o, t in zip(outs[1:], tgt)), outs
+        return sum(0.5 * ((o.double() - t) ** 2).sum().item() for o, t in zip(outs[1:], tgt))
 
     sim.set_fields(*f32)
     sim.forward_record(T)
@@ -136,24 +144,26 @@ def test_adjoint_central_differences_128(lw):
     sim.get_fields_into(outs)
     lam = [torch.zeros_like(outs[0])] + [(o.double() - t).float() for o, t in zip(outs[1:], tgt)]
     g, gnu = sim.backward(lam)
-    rng = np.random.default_rng(4)
-    h = 1e-2 * 0.03
-    rel = []
-    for _ in range(4):
-        dirs = [torch.tensor(rng.standard_normal((n, n, n)), dtype=torch.float32, device="cuda")
-                for _ in range(3)]
-        an = sum((gi.double() * di.double()).sum().item() for gi, di in zip(g[1:], dirs))
-        lp, _ = loss_of([f32[0]] + [a + h * di for a, di in zip(f32[1:], dirs)], sim)
-        lm, _ = loss_of([f32[0]] + [a - h * di for a, di in zip(f32[1:], dirs)], sim)
-        fd = (lp - lm) / (2 * h)
-        rel.append(abs(fd - an) / abs(an))
-    hn = 1e-4
-    sp = lw.Lwacm(19, n, n, n, nu + hn)
-    sm = lw.Lwacm(19, n, n, n, nu - hn)
-    fdn = (loss_of(f32, sp)[0] - loss_of(f32, sm)[0]) / (2 * hn)
-    print(f"adjoint 128^3 T=500: directional rel errors {['%.1e' % r for r in rel]}, "
-          f"dnu {gnu:.6e} vs FD {fdn:.6e}")
-    assert max(rel) < 1e-4
-    assert abs(gnu - fdn) <= 1e-3 * abs(fdn)
-    for s in (sim, sp, sm):
-        s.close()
+    gen = torch.Generator(device="cuda").manual_seed(4)
+    h = 3e-2 * 0.03
+    ans, fds = [], []
+    for _ in range(32):
+        dirs = [torch.randn((n, n, n), generator=gen, device="cuda") for _ in range(3)]
+        ans.append(sum((gi.double() * di.double()).sum().item() for gi, di in zip(g[1:], dirs)))
+        lp = loss_of([f32[0]] + [a + h * di for a, di in zip(f32[1:], dirs)], sim)
+        lm = loss_of([f32[0]] + [a - h * di for a, di in zip(f32[1:], dirs)], sim)
+        fds.append((lp - lm) / (2 * h))
+    sim.close()
+    ans, fds = np.array(ans), np.array(fds)
+    agg = float(np.linalg.norm(fds - ans) / np.linalg.norm(ans))
+
+    def oracle_loss(nu_):
+        out = oracle.step(19, *st, nu=nu_, nsteps=T)
+        return 0.5 * sum(float(np.sum((o - t) ** 2)) for o, t in zip(out[1:], tgt_np))
+    hn = 1e-5
+    fdn = (oracle_loss(nu + hn) - oracle_loss(nu - hn)) / (2 * hn)
+    print(f"adjoint 128^3 T=500: 32 directions, |fd - an|/|an| = {agg:.1e} (per direction: "
+          f"median {np.median(np.abs(fds - ans) / np.abs(ans)):.1e}); "
+          f"dJ/dnu {gnu:.6e} vs FP64 difference {fdn:.6e} (rel {abs(gnu - fdn) / abs(fdn):.1e})")
+    assert agg < 1e-4
+    assert abs(gnu - fdn) <= 5e-4 * abs(fdn)
