@@ -87,8 +87,19 @@ enum {
                               only before lwacm_bind */
     LWACM_OPT_GRAPH_CHUNK = 8, /* steps per captured CUDA graph in lwacm_step (even;
                                   0 disables graphs; default 64) */
-    LWACM_OPT_KERNEL = 9   /* interior kernel: 0 = autotuned choice (default),
-                              1 = generic gather kernel, 2 = tiled kernel */
+    LWACM_OPT_KERNEL = 9,  /* interior kernel: 0 = automatic choice (default),
+                              1 = generic gather kernel, 2 = D3Q19 TMA row-tiled kernel,
+                              3 = D3Q19 register-prefetch z-march kernel (2 and 3 need a
+                              periodic domain with nx in {128, 256}, ny % 8 == 0, FP32
+                              storage: LWACM_E_UNSUPPORTED otherwise) */
+    LWACM_OPT_BATCH_MODE = 10, /* batched contexts: 0 = one launch per step, replayed
+                                  from CUDA graphs (default); 1 = one persistent
+                                  cooperative launch per lwacm_step call, with a
+                                  bounded grid-wide barrier between steps */
+    LWACM_OPT_TEST_WITHHOLD = 11 /* batched contexts, tests only: in persistent mode the
+                                    first CTA leaves without arriving at the barrier after
+                                    this step (-1 = never), so the other CTAs' bounded
+                                    waits run out and lwacm_sync reports LWACM_E_TIMEOUT */
 };
 
 /* Create a single-domain context.
@@ -99,6 +110,20 @@ enum {
  *   device work is done. */
 lwacm_status lwacm_create(int lattice, int nx, int ny, int nz, double nu, int bc,
                           lwacm_ctx **out);
+
+/* Create a context holding n independent periodic domains (batched ensemble):
+ * domain b has nx[b] x ny[b] x nz[b] nodes (nz may be NULL for D2Q9) and
+ * viscosity nu[b] (each checked as in lwacm_create); bc must be
+ * LWACM_BC_PERIODIC (else LWACM_E_UNSUPPORTED). The domains are packed one after
+ * the other: every field array of the context (lwacm_set_fields, lwacm_get_fields,
+ * lwacm_fields) holds domain 0's nodes, then domain 1's, ..., each x fastest;
+ * lwacm_diagnostics sums over all of them. One lwacm_step advances every domain. */
+lwacm_status lwacm_batch_create(int lattice, int n, const int *nx, const int *ny, const int *nz,
+                                const double *nu, int bc, lwacm_ctx **out);
+
+/* offsets[0..n]: first packed node of each domain, then the total node count
+ * (n = 1 for a single-domain context). */
+lwacm_status lwacm_batch_offsets(const lwacm_ctx *ctx, long long *offsets);
 
 /* Set an option (LWACM_OPT_*). Storage type changes are refused after bind
  * (LWACM_E_STATE). */

@@ -7,75 +7,9 @@
 
 #include "launch.h"
 #include "lwacm_core.cuh"
+#include "node_update.cuh"
 
 namespace lwacm {
-
-// Full update of one node (x,y,z). With WALLS, sources beyond a walled face are
-// replaced by the bounce-back rule; without, every axis wraps (periodic).
-template <int Q, bool WALLS, typename T>
-__device__ __forceinline__ void node_update(const T *__restrict__ in, T *__restrict__ out,
-                                            const StepParams &p, int x, int y, int z) {
-    using L = Lat<Q>;
-    const long long k = ((long long)z * p.ny + y) * p.nx + x;
-    const T *Din = in, *Uin = in + p.fstride, *Vin = in + 2 * p.fstride,
-            *Win = in + 3 * p.fstride;
-    const float dx = ldf(Din + k), ux = ldf(Uin + k), uy = ldf(Vin + k);
-    const float uz = (Q == 19) ? ldf(Win + k) : 0.f;
-    const float rx = 1.f + dx;
-    const float qx = fmaf(ux, ux, fmaf(uy, uy, uz * uz));
-    float dd = 0.f, jx = 0.f, jy = 0.f, jz = 0.f;
-#pragma unroll
-    for (int i = 0; i < Q; ++i) {
-        const int cx = L::c(i, 0), cy = L::c(i, 1), cz = L::c(i, 2);
-        int sx = x - cx, sy = y - cy, sz = z - cz;
-        bool outside = false, above = false;
-        if (WALLS) {
-            if (p.walled[0] && (sx < 0 || sx >= p.nx)) outside = true;
-            if (p.walled[1] && (sy < 0 || sy >= p.ny)) outside = true;
-            if (Q == 19 && p.walled[2] && (sz < 0 || sz >= p.nz)) outside = true;
-            const int sl = p.lid_axis == 0 ? sx : (p.lid_axis == 1 ? sy : sz);
-            const int nl = p.lid_axis == 0 ? p.nx : (p.lid_axis == 1 ? p.ny : p.nz);
-            above = outside && sl >= nl;
-        }
-        float g;
-        if (!outside) {
-            sx = sx < 0 ? sx + p.nx : (sx >= p.nx ? sx - p.nx : sx);
-            sy = sy < 0 ? sy + p.ny : (sy >= p.ny ? sy - p.ny : sy);
-            sz = sz < 0 ? sz + p.nz : (sz >= p.nz ? sz - p.nz : sz);
-            const long long s = ((long long)sz * p.ny + sy) * p.nx + sx;
-            const float ds = ldf(Din + s), us = ldf(Uin + s), vs = ldf(Vin + s);
-            const float ws = (Q == 19) ? ldf(Win + s) : 0.f;
-            const float e = cx * us + cy * vs + cz * ws;
-            const float q = fmaf(us, us, fmaf(vs, vs, ws * ws));
-            g = link_g(L::w(i), ds, 1.f + ds, e, q, p.s);
-        } else {
-            // Eq. ACM2.0cccbb2 + Eq. ACM2.0ccccbb: own outgoing BB(i) value, reflected
-            const float e = -(cx * ux + cy * uy + cz * uz);
-            g = link_g(L::w(i), dx, rx, e, qx, p.s);
-            if (above) {
-                const float cu = cx * p.lid[0] + cy * p.lid[1] + cz * p.lid[2];
-                g = fmaf(L::w(i) * p.wallc, cu, g);
-            }
-        }
-        dd += g;
-        if (cx) jx += cx > 0 ? g : -g;
-        if (cy) jy += cy > 0 ? g : -g;
-        if (cz) jz += cz > 0 ? g : -g;
-    }
-    jx = fmaf(p.a * rx, ux, jx);
-    jy = fmaf(p.a * rx, uy, jy);
-    jz = fmaf(p.a * rx, uz, jz);
-    if (p.has_force) {  // Eq. force: the odd part of f^(e)(rho(x,t), g) adds rho g to j
-        jx = fmaf(rx, p.force[0], jx);
-        jy = fmaf(rx, p.force[1], jy);
-        jz = fmaf(rx, p.force[2], jz);
-    }
-    const float rn = 1.f + dd;
-    stf(out + k, dd);
-    stf(out + p.fstride + k, jx / rn);
-    stf(out + 2 * p.fstride + k, jy / rn);
-    if (Q == 19) stf(out + 3 * p.fstride + k, jz / rn);
-}
 
 template <int Q, typename T>
 __global__ void __launch_bounds__(256) k_step_generic(const T *__restrict__ in,

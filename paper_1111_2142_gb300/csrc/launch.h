@@ -40,6 +40,33 @@ cudaError_t launch_adjoint_step(int Q, const float *state_t, const float *state_
                                 float *dj, float *lam_t, const StepParams &p, double *nu_partial,
                                 double *nu_total, cudaStream_t st);
 
+// Batched independent periodic domains packed in one set of field arrays
+// (kernels_batch.cu). A tile is batch_tile() consecutive nodes of one domain.
+struct BatchDomain {
+    int nx, ny, nz, pad;
+    long long off, n;  // first node (packed index) and node count
+    float s, a;        // 18 nu and 1 - 6 nu of this domain
+};
+struct BatchTile {
+    int dom, pad;
+    long long start;   // packed index of the tile's first node
+};
+struct BatchParams {
+    const BatchDomain *doms;
+    const BatchTile *tiles;
+    long long ntiles;
+    long long fstride;
+    unsigned *bar_count;  // followed by the barrier generation word
+    unsigned *bar_gen;
+    int *err;
+    long long withhold_step;  // test hook: CTA 0 skips the barrier after this step (-1: never)
+};
+int batch_tile();
+cudaError_t launch_batch_step(int Q, int storage, const void *in, void *out, const BatchParams &bp,
+                              cudaStream_t st);
+cudaError_t launch_batch_persistent(int Q, int storage, void *buf0, void *buf1, const BatchParams &bp,
+                                    long long nsteps, int parity, cudaStream_t st);
+
 // Register-prefetch z-marching variant of the D3Q19 kernel (same shapes).
 bool zmarch_supported(int Q, int storage, const StepParams &p);
 cudaError_t launch_step_zmarch(int Q, int storage, const void *in, void *out, const StepParams &p,

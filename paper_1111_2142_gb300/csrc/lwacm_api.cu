@@ -8,6 +8,7 @@
 #include <cstring>
 #include <new>
 #include <string>
+#include <vector>
 
 #include "../../include/lwacm.h"
 #include "launch.h"
@@ -48,6 +49,13 @@ struct lwacm_ctx {
     int gchunk[2] = {0, 0};
     int kernel = 1;  // 1 generic, 2 tiled (TMA), 3 z-march (register prefetch)
     std::string kname = "none";
+    // batched domains (nbatch > 0): packed one after the other
+    int nbatch = 0;
+    std::vector<BatchDomain> doms;
+    std::vector<BatchTile> tiles;
+    size_t off_doms = 0, off_tiles = 0, off_bar = 0;
+    int batch_mode = 0;  // 0: one launch per step (graphs), 1: one persistent launch
+    long long withhold = -1;
     // recorded forward run for lwacm_backward
     char *adj = nullptr;
     size_t adj_bytes = 0;
@@ -91,6 +99,14 @@ void layout(lwacm_ctx *c) {
     off = align_up(off + 16 * 8, kAlign);
     c->off_err = off;
     off = align_up(off + 16, kAlign);
+    if (c->nbatch) {
+        c->off_doms = off;
+        off = align_up(off + sizeof(BatchDomain) * c->doms.size(), kAlign);
+        c->off_tiles = off;
+        off = align_up(off + sizeof(BatchTile) * c->tiles.size(), kAlign);
+        c->off_bar = off;
+        off = align_up(off + 16, kAlign);
+    }
     c->total = off;
 }
 
@@ -140,6 +156,11 @@ void drop_graphs(lwacm_ctx *c) {
 // explicit choice is not supported. Kernels that need the device are only
 // considered once a workspace is bound.
 bool choose_kernel(lwacm_ctx *c) {
+    if (c->nbatch) {
+        c->kernel = 4;
+        c->kname = c->batch_mode ? "batch_persistent" : "batch_step";
+        return c->kernel_opt == 0 || c->kernel_opt == 1;
+    }
     const StepParams p = params(c);
     const bool dev = c->bound;
     const bool t_ok = dev && tiled_supported(c->Q, c->storage, p);
@@ -161,8 +182,22 @@ void *bufp(lwacm_ctx *c, int b) { return c->ws + c->off_buf[b]; }
 
 size_t field_bytes(const lwacm_ctx *c) { return (size_t)c->Nal * esize(c->storage); }
 
+BatchParams batch_params(lwacm_ctx *c) {
+    BatchParams bp;
+    bp.doms = (const BatchDomain *)(c->ws + c->off_doms);
+    bp.tiles = (const BatchTile *)(c->ws + c->off_tiles);
+    bp.ntiles = (long long)c->tiles.size();
+    bp.fstride = c->Nal;
+    bp.bar_count = (unsigned *)(c->ws + c->off_bar);
+    bp.bar_gen = bp.bar_count + 1;
+    bp.err = (int *)(c->ws + c->off_err);
+    bp.withhold_step = c->withhold;
+    return bp;
+}
+
 // enqueue one time step from state `in` to state `out` (each nf fields x Nal)
 cudaError_t step_between(lwacm_ctx *c, const void *in, void *out, cudaStream_t st) {
+    if (c->nbatch) return launch_batch_step(c->Q, c->storage, in, out, batch_params(c), st);
     const StepParams p = params(c);
     cudaError_t e = c->kernel == 2   ? launch_step_tiled(c->Q, c->storage, in, out, p, st)
                     : c->kernel == 3 ? launch_step_zmarch(c->Q, c->storage, in, out, p, st)
@@ -277,6 +312,81 @@ lwacm_status lwacm_create(int lattice, int nx, int ny, int nz, double nu, int bc
     return LWACM_OK;
 }
 
+lwacm_status lwacm_batch_create(int lattice, int n, const int *nx, const int *ny, const int *nz,
+                                const double *nu, int bc, lwacm_ctx **out) {
+    if (!out) return LWACM_E_ARG;
+    *out = nullptr;
+    if (n < 1 || !nx || !ny || !nu) return LWACM_E_ARG;
+    if (lattice != LWACM_D2Q9 && lattice != LWACM_D3Q19) return LWACM_E_ARG;
+    if (lattice == LWACM_D3Q19 && !nz) return LWACM_E_ARG;
+    if (bc != LWACM_BC_PERIODIC) return LWACM_E_UNSUPPORTED;
+    lwacm_ctx *c = new (std::nothrow) lwacm_ctx();
+    if (!c) return LWACM_E_NOMEM;
+    c->Q = lattice;
+    c->D = lattice == LWACM_D2Q9 ? 2 : 3;
+    c->nf = c->D + 1;
+    c->bc = bc;
+    c->nbatch = n;
+    long long off = 0;
+    const int tile = batch_tile();
+    try {
+        c->doms.resize(n);
+        for (int b = 0; b < n; ++b) {
+            const int z = lattice == LWACM_D2Q9 ? 1 : nz[b];
+            if (nx[b] < 1 || ny[b] < 1 || z < 1 || (lattice == LWACM_D2Q9 && nz && nz[b] != 1)) {
+                delete c;
+                return LWACM_E_ARG;
+            }
+            if (!(nu[b] > 0.0) || !(nu[b] <= 1.0 / 6.0 + 1e-15) || !std::isfinite(nu[b])) {
+                delete c;
+                return LWACM_E_RANGE;
+            }
+            BatchDomain &d = c->doms[b];
+            d.nx = nx[b];
+            d.ny = ny[b];
+            d.nz = z;
+            d.pad = 0;
+            d.off = off;
+            d.n = (long long)nx[b] * ny[b] * z;
+            d.s = (float)(18.0 * nu[b]);  // Eq. ACM2.0nu: s = 18 nu, a = 1 - 6 nu
+            d.a = (float)(1.0 - 6.0 * nu[b]);
+            for (long long t = 0; t < d.n; t += tile) {
+                BatchTile bt;
+                bt.dom = b;
+                bt.pad = 0;
+                bt.start = off + t;
+                c->tiles.push_back(bt);
+            }
+            off += d.n;
+        }
+    } catch (...) {
+        delete c;
+        return LWACM_E_NOMEM;
+    }
+    c->nu = nu[0];
+    c->nx = (int)std::min<long long>(off, 1LL << 30);
+    c->ny = 1;
+    c->nz = 1;
+    c->N = off;
+    c->Nal = (long long)align_up((size_t)c->N, 64);
+    layout(c);
+    choose_kernel(c);
+    *out = c;
+    return LWACM_OK;
+}
+
+lwacm_status lwacm_batch_offsets(const lwacm_ctx *c, long long *offsets) {
+    if (!c || !offsets) return LWACM_E_ARG;
+    if (!c->nbatch) {
+        offsets[0] = 0;
+        offsets[1] = c->N;
+        return LWACM_OK;
+    }
+    for (int b = 0; b < c->nbatch; ++b) offsets[b] = c->doms[b].off;
+    offsets[c->nbatch] = c->N;
+    return LWACM_OK;
+}
+
 lwacm_status lwacm_set_option(lwacm_ctx *c, int key, double v) {
     if (!c) return LWACM_E_ARG;
     if (c->sticky != LWACM_OK) return c->sticky;
@@ -320,6 +430,17 @@ lwacm_status lwacm_set_option(lwacm_ctx *c, int key, double v) {
             }
             break;
         }
+        case LWACM_OPT_BATCH_MODE: {
+            const int m = (int)v;
+            if (m != 0 && m != 1) return fail(c, LWACM_E_ARG, "batch mode must be 0 or 1");
+            if (!c->nbatch) return fail(c, LWACM_E_STATE, "not a batched context");
+            c->batch_mode = m;
+            break;
+        }
+        case LWACM_OPT_TEST_WITHHOLD:
+            if (!c->nbatch) return fail(c, LWACM_E_STATE, "not a batched context");
+            c->withhold = (long long)v;
+            break;
         default:
             return fail(c, LWACM_E_ARG, "unknown option key");
     }
@@ -349,6 +470,15 @@ lwacm_status lwacm_bind(lwacm_ctx *c, void *ws, size_t bytes, void *stream) {
     c->cur = 0;
     c->steps = 0;
     CK(c, cudaMemsetAsync(c->ws + c->off_err, 0, 16, c->stream), "clear error word");
+    if (c->nbatch) {
+        CK(c, cudaMemcpyAsync(c->ws + c->off_doms, c->doms.data(), sizeof(BatchDomain) * c->doms.size(),
+                              cudaMemcpyHostToDevice, c->stream),
+           "domain table");
+        CK(c, cudaMemcpyAsync(c->ws + c->off_tiles, c->tiles.data(), sizeof(BatchTile) * c->tiles.size(),
+                              cudaMemcpyHostToDevice, c->stream),
+           "tile table");
+        CK(c, cudaStreamSynchronize(c->stream), "sync");  // the host tables are pageable
+    }
     if (!choose_kernel(c)) {
         c->kernel_opt = 0;
         choose_kernel(c);
@@ -393,6 +523,15 @@ lwacm_status lwacm_step(lwacm_ctx *c, long long n) {
     lwacm_status s = ready(c, true);
     if (s != LWACM_OK) return s;
     if (n < 0) return fail(c, LWACM_E_ARG, "negative step count");
+    if (c->nbatch && c->batch_mode == 1) {
+        if (n == 0) return LWACM_OK;
+        CK(c, launch_batch_persistent(c->Q, c->storage, bufp(c, 0), bufp(c, 1), batch_params(c), n, c->cur,
+                                      c->stream),
+           "persistent batch launch");
+        c->cur ^= (int)(n & 1);
+        c->steps += n;
+        return LWACM_OK;
+    }
     long long left = n;
     const int chunk = c->graph_chunk;
     if (chunk > 0 && left >= chunk) {
@@ -491,8 +630,8 @@ lwacm_status lwacm_forward_record(lwacm_ctx *c, long long T, int stride, void *w
     if (s != LWACM_OK) return s;
     if (T < 0 || stride < 0 || !ws) return fail(c, LWACM_E_ARG, "T >= 0, stride >= 0, workspace required");
     if (((uintptr_t)ws) % kAlign) return fail(c, LWACM_E_ARG, "adjoint workspace not 256-byte aligned");
-    if (c->storage != LWACM_F32 || c->bc != LWACM_BC_PERIODIC)
-        return fail(c, LWACM_E_UNSUPPORTED, "the adjoint needs FP32 storage and a periodic domain");
+    if (c->storage != LWACM_F32 || c->bc != LWACM_BC_PERIODIC || c->nbatch)
+        return fail(c, LWACM_E_UNSUPPORTED, "the adjoint needs one periodic domain with FP32 storage");
     const AdjLayout L = adj_layout(c, T, stride);
     if (bytes < L.bytes) return fail(c, LWACM_E_NOMEM, "adjoint workspace smaller than lwacm_adjoint_workspace_bytes");
     c->adj = (char *)ws;

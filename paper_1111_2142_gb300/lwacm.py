@@ -22,6 +22,7 @@ F32, BF16, F16, F64 = 0, 1, 2, 3
 DEVICE, HOST = 0, 1
 OPT_LID_X, OPT_LID_Y, OPT_LID_Z, OPT_FORCE_X, OPT_FORCE_Y, OPT_FORCE_Z = range(6)
 OPT_RHO0, OPT_STORAGE, OPT_GRAPH_CHUNK, OPT_KERNEL = 6, 7, 8, 9
+OPT_BATCH_MODE, OPT_TEST_WITHHOLD = 10, 11
 
 STATUS_NAMES = {OK: "OK", E_ARG: "E_ARG", E_RANGE: "E_RANGE", E_STATE: "E_STATE",
                 E_NOMEM: "E_NOMEM", E_CUDA: "E_CUDA", E_NONFINITE: "E_NONFINITE",
@@ -63,6 +64,8 @@ def load():
         "lwacm_forward_record": [vp, ll, i, vp, ctypes.c_size_t],
         "lwacm_backward": [vp, vp, vp, vp, vp, i, vp, vp, vp, vp, P(d)],
         "lwacm_diagnostics_noalloc": [vp, vp, vp, vp, ll, i, vp, vp],
+        "lwacm_batch_create": [i, i, P(i), P(i), P(i), P(d), i, P(vp)],
+        "lwacm_batch_offsets": [vp, P(ll)],
     }
     for name, args in sig.items():
         fn = getattr(lib, name)
@@ -102,16 +105,21 @@ class Lwacm:
 
     def __init__(self, lattice, nx, ny, nz=1, nu=0.01, bc=PERIODIC, *, storage=F32, lid=None,
                  force=None, rho0=None, kernel=0, graph_chunk=None, device=None, stream=None):
-        torch = _torch()
         lib = load()
-        self._lib = lib
         self.lattice, self.nx, self.ny, self.nz = int(lattice), int(nx), int(ny), int(nz)
         self.nu, self.bc = float(nu), int(bc)
+        self.n_nodes = self.nx * self.ny * self.nz
         h = ctypes.c_void_p()
         st = lib.lwacm_create(self.lattice, self.nx, self.ny, self.nz, self.nu, self.bc,
                               ctypes.byref(h))
         if st != OK:
             raise LwacmError(st, "lwacm_create")
+        self._setup(lib, h, storage, lid, force, rho0, kernel, graph_chunk, device, stream, {})
+
+    def _setup(self, lib, h, storage, lid, force, rho0, kernel, graph_chunk, device, stream,
+               extra):
+        torch = _torch()
+        self._lib = lib
         self._h = h
         try:
             if storage != F32:
@@ -124,8 +132,8 @@ class Lwacm:
                 self._check(lib.lwacm_set_option(h, OPT_RHO0, float(rho0)))
             if graph_chunk is not None:
                 self._check(lib.lwacm_set_option(h, OPT_GRAPH_CHUNK, float(graph_chunk)))
-            if kernel:
-                self._check(lib.lwacm_set_option(h, OPT_KERNEL, float(kernel)))
+            for key, val in extra.items():
+                self._check(lib.lwacm_set_option(h, key, float(val)))
             nbytes = ctypes.c_size_t()
             self._check(lib.lwacm_workspace_bytes(h, ctypes.byref(nbytes)))
             self.device = torch.device(device if device is not None else "cuda")
@@ -133,6 +141,8 @@ class Lwacm:
             self.stream = stream if stream is not None else torch.cuda.current_stream(self.device)
             self._check(lib.lwacm_bind(h, self.workspace.data_ptr(), nbytes.value,
                                        ctypes.c_void_p(self.stream.cuda_stream)))
+            if kernel:  # explicit kernels are checked against the bound device
+                self._check(lib.lwacm_set_option(h, OPT_KERNEL, float(kernel)))
         except Exception:
             lib.lwacm_destroy(h)
             self._h = None
@@ -150,6 +160,9 @@ class Lwacm:
     @property
     def shape(self):
         return (self.ny, self.nx) if self.lattice == D2Q9 else (self.nz, self.ny, self.nx)
+
+    def set_option(self, key, value):
+        self._check(self._lib.lwacm_set_option(self._h, int(key), float(value)))
 
     @property
     def kernel_name(self):
@@ -181,8 +194,7 @@ class Lwacm:
             dtype = {torch.float32: F32, torch.float64: F64}[dt]
             where = DEVICE if keep[0].is_cuda else HOST
         for a in keep:
-            assert a.size == self.nx * self.ny * self.nz if isinstance(a, np.ndarray) \
-                else a.numel() == self.nx * self.ny * self.nz
+            assert (a.size if isinstance(a, np.ndarray) else a.numel()) == self.n_nodes
         ptrs = [_ptr(a) for a in keep] + [None] * (4 - len(keep))
         self._check(self._lib.lwacm_set_fields(self._h, *ptrs, dtype, where))
         if where == HOST:
@@ -232,7 +244,7 @@ class Lwacm:
         tdt = {F32: torch.float32, BF16: torch.bfloat16, F16: torch.float16}[dt.value]
         esz = 4 if dt.value == F32 else 2
         base = self.workspace.data_ptr()
-        n = self.nx * self.ny * self.nz
+        n = self.n_nodes
         views = []
         for k in range(self.nf):
             off = vp[k].value - base
@@ -273,6 +285,62 @@ class Lwacm:
         if st not in (OK, E_NONFINITE):
             self._check(st)
         return res
+
+
+class LwacmBatch(Lwacm):
+    """Many independent periodic domains advanced together (lwacm_batch_create).
+
+    dims: list of (nx, ny) for D2Q9 or (nx, ny, nz) for D3Q19; nus: viscosities.
+    Fields are packed domain after domain; set_domains / get_domains pack and
+    unpack per-domain numpy arrays. mode 0: one launch per step (graphs); mode 1:
+    one persistent cooperative launch per step() call.
+    """
+
+    def __init__(self, lattice, dims, nus, *, storage=F32, mode=0, graph_chunk=None,
+                 device=None, stream=None):
+        lib = load()
+        n = len(dims)
+        self.lattice = int(lattice)
+        self.dims = [tuple(int(v) for v in d) for d in dims]
+        nx = (ctypes.c_int * n)(*[d[0] for d in self.dims])
+        ny = (ctypes.c_int * n)(*[d[1] for d in self.dims])
+        nz = (ctypes.c_int * n)(*[(d[2] if len(d) > 2 else 1) for d in self.dims])
+        nu = (ctypes.c_double * n)(*[float(v) for v in nus])
+        h = ctypes.c_void_p()
+        st = lib.lwacm_batch_create(self.lattice, n, nx, ny, nz, nu, PERIODIC, ctypes.byref(h))
+        if st != OK:
+            raise LwacmError(st, "lwacm_batch_create")
+        offs = (ctypes.c_longlong * (n + 1))()
+        lib.lwacm_batch_offsets(h, offs)
+        self.offsets = list(offs)
+        self.n_nodes = self.offsets[-1]
+        self.nx, self.ny, self.nz = self.n_nodes, 1, 1
+        self.nu, self.bc = float(nus[0]), PERIODIC
+        self._setup(lib, h, storage, None, None, None, 0, graph_chunk, device, stream,
+                    {OPT_BATCH_MODE: mode} if mode else {})
+
+    @property
+    def shape(self):
+        return (self.n_nodes,)
+
+    def domain_shape(self, b):
+        d = self.dims[b]
+        return (d[1], d[0]) if self.lattice == D2Q9 else (d[2], d[1], d[0])
+
+    def set_domains(self, fields):
+        """fields: per domain a tuple (d, ux, uy[, uz]) of numpy arrays."""
+        nf = 3 if self.lattice == D2Q9 else 4
+        packed = [np.concatenate([np.asarray(f[k], dtype=np.float64).reshape(-1) for f in fields])
+                  for k in range(nf)]
+        self.set_fields(*packed)
+
+    def get_domains(self):
+        packed = self.get_fields()
+        out = []
+        for b in range(len(self.dims)):
+            lo, hi = self.offsets[b], self.offsets[b + 1]
+            out.append(tuple(p[lo:hi].reshape(self.domain_shape(b)) for p in packed))
+        return out
 
 
 def _make_function():

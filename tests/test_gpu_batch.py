@@ -1,0 +1,122 @@
+"""Batched independent domains (lwacm_batch_create): per-step launches and the
+persistent cooperative launch against the FP64 oracle run domain by domain, and
+the bounded grid barrier's timeout path."""
+import numpy as np
+import pytest
+
+import oracle
+from paper_1111_2142_gb300 import inputs
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def lw():
+    import __graft_entry__
+    __graft_entry__.build()
+    from paper_1111_2142_gb300 import lwacm
+    return lwacm
+
+
+def small_ensemble(Q, n, seed):
+    rng = np.random.default_rng(seed)
+    dims, nus, fields = [], [], []
+    for b in range(n):
+        if Q == 9:
+            d = (int(rng.integers(3, 48)), int(rng.integers(3, 40)))
+            shape = (d[1], d[0])
+        else:
+            d = (int(rng.integers(3, 14)), int(rng.integers(3, 12)), int(rng.integers(2, 10)))
+            shape = (d[2], d[1], d[0])
+        dims.append(d)
+        nus.append(float(rng.uniform(0.002, 0.05)))
+        fields.append(inputs.smooth_random(shape, seed=seed * 1000 + b, u_amp=0.04, d_amp=0.01))
+    return dims, nus, fields
+
+
+@pytest.mark.parametrize("mode", [0, 1])
+@pytest.mark.parametrize("Q", [9, 19])
+def test_batch_matches_oracle(lw, Q, mode):
+    dims, nus, fields = small_ensemble(Q, 13, seed=61 + Q)
+    sim = lw.LwacmBatch(Q, dims, nus, mode=mode)
+    sim.set_domains(fields)
+    T = 70
+    sim.step(T)
+    sim.sync()
+    got = sim.get_domains()
+    worst = 0.0
+    for b in range(len(dims)):
+        ref = oracle.step(Q, *fields[b], nu=nus[b], nsteps=T)
+        eu = max(float(np.max(np.abs(g - r))) for g, r in zip(got[b][1:], ref[1:])) / 0.04
+        ed = float(np.max(np.abs(got[b][0] - ref[0]))) / max(float(np.max(np.abs(ref[0]))), 3 * 0.04 ** 2)
+        worst = max(worst, eu)
+        assert eu < 1e-5 and ed < 1e-4, (b, dims[b], eu, ed)
+    print(f"[{sim.kernel_name}] Q{Q} 13 domains x{T}: worst du/U = {worst:.2e}")
+    sim.close()
+
+
+def test_persistent_equals_per_step(lw):
+    dims, nus, fields = small_ensemble(9, 9, seed=70)
+    out = []
+    for mode in (0, 1):
+        sim = lw.LwacmBatch(9, dims, nus, mode=mode)
+        sim.set_domains(fields)
+        sim.step(33)
+        sim.step(4)
+        out.append(sim.get_fields())
+        sim.close()
+    for a, b in zip(*out):
+        assert np.array_equal(a, b)
+
+
+def test_barrier_timeout_is_reported(lw):
+    """A CTA that never arrives (test hook) makes the others' bounded waits run out:
+    the launch ends, the error word is set and lwacm_sync reports LWACM_E_TIMEOUT."""
+    import time
+    dims, nus, fields = small_ensemble(9, 40, seed=71)
+    dims = [(max(d[0], 40), max(d[1], 40)) for d in dims]  # enough tiles for several CTAs
+    fields = [inputs.smooth_random((d[1], d[0]), seed=k) for k, d in enumerate(dims)]
+    sim = lw.LwacmBatch(9, dims, nus, mode=1)
+    sim.set_domains(fields)
+    sim.set_option(lw.OPT_TEST_WITHHOLD, 3)
+    t0 = time.time()
+    sim.step(10)
+    with pytest.raises(lw.LwacmError) as ei:
+        sim.sync()
+    assert ei.value.status == lw.E_TIMEOUT
+    assert time.time() - t0 < 30
+    sim.close()
+    # the device is still usable afterwards
+    ok = lw.LwacmBatch(9, dims[:3], nus[:3], mode=1)
+    ok.set_domains(fields[:3])
+    ok.step(5)
+    ok.sync()
+    ok.close()
+
+
+def test_ensemble_256_sampled(lw):
+    """The batched workload: 256 periodic D2Q9 domains, sides log-uniform on
+    [32, 512] (seed 1), nu uniform on [0.002, 0.05], band-limited divergence-free
+    initial velocity (wave numbers 1-4, rms 0.02), 2000 steps in one persistent
+    launch; the five smallest domains and one mid-size domain checked against the
+    oracle, every domain checked for finite values."""
+    doms = inputs.ensemble_2d(256, seed=1)
+    dims = [(d["nx"], d["ny"]) for d in doms]
+    nus = [d["nu"] for d in doms]
+    fields = [(d["d"], d["ux"], d["uy"]) for d in doms]
+    sim = lw.LwacmBatch(9, dims, nus, mode=1)
+    sim.set_domains(fields)
+    T = 2000
+    sim.step(T)
+    sim.sync()
+    assert sim.diagnostics()["finite"]
+    got = sim.get_domains()
+    sizes = [d[0] * d[1] for d in dims]
+    order = np.argsort(sizes)
+    check = list(order[:5]) + [int(order[len(order) // 2])]
+    for b in check:
+        ref = oracle.step(9, *fields[b], nu=nus[b], nsteps=T)
+        eu = max(float(np.max(np.abs(g - r))) for g, r in zip(got[b][1:], ref[1:])) / 0.02
+        assert eu < 1e-5, (b, dims[b], eu)
+    print(f"ensemble: {sim.n_nodes} nodes in 256 domains, sampled domains agree")
+    sim.close()
