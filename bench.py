@@ -113,7 +113,7 @@ class ClockSampler:
                 "reasons": reasons, "samples": len(rows)}
 
 
-def cpu_baseline(steps=2, n=N_SIDE):
+def cpu_baseline(steps=40, n=N_SIDE):
     """The FP64 oracle as it stands on the host cores: `steps` updates of the same
     256^3 workload (a bounded sample of the GPU run's steps)."""
     import oracle
@@ -128,16 +128,21 @@ def cpu_baseline(steps=2, n=N_SIDE):
             f"({dt:.1f} s)"}
 
 
+REF_SIDE = 128  # the reference arm's bounded sample: the same workload on 128^3
+
+
 def run_reference(args):
     ws, rank, _ = _dist()
     if rank != 0:
         return 0
     import oracle
     from paper_1111_2142_gb300 import inputs
-    n = N_SIDE
+    n = REF_SIDE
     f = inputs.tgv3d(n, u0=U0)
     oracle.step(19, *[a[:8] for a in f], nu=NU, nsteps=1)
-    # each reference "step" is one FP64 oracle update of the full 256^3 lattice
+    # each reference "step" is one FP64 oracle update of a 128^3 Taylor-Green lattice
+    # with the benchmark's parameters (a bounded sample of the 256^3 workload; the
+    # oracle's per-node cost does not depend on the lattice size)
     state = f
     for _ in range(args.warmup):
         state = oracle.step(19, *state, nu=NU, nsteps=1)
@@ -152,11 +157,128 @@ def run_reference(args):
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
             "data": "synthetic", "config": {"workload": WORKLOAD + " (FP64 oracle)"},
             "cpu_baseline": {"value": v, "unit": "GLUPS", "cores": cores, "kind": "oracle",
-                             "sample": f"{args.steps} timed oracle steps of the {n}^3 workload"},
+                             "sample": f"{args.steps} timed FP64 oracle steps of the workload "
+                                       f"on a {n}^3 lattice (same u0, nu)"},
             "e2e": {"value": v, "unit": "GLUPS", "h2d_bytes_per_step": 0,
                     "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
     return 0
+
+
+def _events_ms(stream, fn):
+    import torch
+    torch.cuda.synchronize()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    fn()
+    e1.record(stream)
+    torch.cuda.synchronize()
+    return e0.elapsed_time(e1)
+
+
+def variants(hbm):
+    """The other configurations and forms, each timed with CUDA events on its own
+    stream after a warm-up: storage modes and kernels for the 256^3 workload, the
+    batched ensemble (persistent launch / per-step graphs / per-domain launches),
+    the adjoint at 128^3, the 1024^2 cavity and the 64^2 2D Taylor-Green vortex."""
+    import torch
+    from paper_1111_2142_gb300 import inputs
+    from paper_1111_2142_gb300 import lwacm as lw
+    out = {}
+
+    def glups(nodes, steps, ms):
+        return nodes * steps / (ms * 1e-3) / 1e9
+
+    n = N_SIDE
+    f = inputs.tgv3d(n, u0=U0)
+    for name, kw, bpn in (("d3q19_256_bf16_storage", dict(storage=lw.BF16), 16),
+                          ("d3q19_256_fp16_storage", dict(storage=lw.F16), 16),
+                          ("d3q19_256_generic_kernel", dict(kernel=1), 32),
+                          ("d3q19_256_tma_kernel", dict(kernel=2), 32)):
+        sim = lw.Lwacm(lw.D3Q19, n, n, n, NU, **kw)
+        sim.set_fields(*f)
+        sim.step(20)
+        steps = 400
+        ms = _events_ms(sim.stream, lambda: sim.step(steps))
+        g = glups(n ** 3, steps, ms)
+        out[name] = {"value": g, "unit": "GLUPS", "kernel": sim.kernel_name,
+                     "hbm_frac": bpn * g / hbm, "bytes_per_node": bpn}
+        sim.close()
+        torch.cuda.empty_cache()
+
+    # batched ensemble: 256 D2Q9 domains (seed 1), 2000 steps
+    doms = inputs.ensemble_2d(256, seed=1)
+    dims = [(d["nx"], d["ny"]) for d in doms]
+    nus = [d["nu"] for d in doms]
+    fields = [(d["d"], d["ux"], d["uy"]) for d in doms]
+    nodes = sum(a * b for a, b in dims)
+    T = 2000
+    ens = {"domains": 256, "nodes": nodes, "steps": T}
+    for mode, label in ((1, "persistent_launch"), (0, "per_step_graphs")):
+        sim = lw.LwacmBatch(lw.D2Q9, dims, nus, mode=mode)
+        sim.set_domains(fields)
+        sim.step(10)
+        ms = _events_ms(sim.stream, lambda: sim.step(T))
+        ens[label] = glups(nodes, T, ms)
+        sim.close()
+    # per-domain launches: one context per domain, each stepped on its own
+    sims = []
+    for (nx, ny), nu_b, fb in zip(dims, nus, fields):
+        s_ = lw.Lwacm(lw.D2Q9, nx, ny, 1, nu_b)
+        s_.set_fields(*fb)
+        sims.append(s_)
+    Tpd = 200
+    for s_ in sims:
+        s_.step(2)
+    ms = _events_ms(sims[0].stream, lambda: [s_.step(Tpd) for s_ in sims])
+    ens["per_domain_launches"] = glups(nodes, Tpd, ms)
+    ens["per_domain_steps"] = Tpd
+    ens["unit"] = "GLUPS"
+    for s_ in sims:
+        s_.close()
+    out["ensemble_256_d2q9"] = ens
+
+    # adjoint: D3Q19 128^3, T = 500, sqrt(T) checkpoints
+    n3, T3 = 128, 500
+    fa = inputs.random_divfree_3d(n3, n3, n3, rms=0.03, kmax=8, seed=2)
+    sim = lw.Lwacm(lw.D3Q19, n3, n3, n3, 0.01)
+    sim.set_fields(*fa)
+    sim.step(10)
+    ms_fwd = _events_ms(sim.stream, lambda: sim.step(T3))
+    sim.set_fields(*fa)
+    ms_rec = _events_ms(sim.stream, lambda: sim.forward_record(T3))
+    lam = [torch.zeros((n3, n3, n3), device="cuda")] + [
+        torch.tensor(a, dtype=torch.float32, device="cuda") for a in fa[1:]]
+    ms_bwd = _events_ms(sim.stream, lambda: sim.backward(lam))
+    out["adjoint_d3q19_128_T500"] = {
+        "forward_glups": glups(n3 ** 3, T3, ms_fwd),
+        "recorded_forward_glups": glups(n3 ** 3, T3, ms_rec),
+        "backward_glups_equiv": glups(n3 ** 3, T3, ms_bwd),
+        "backward_over_forward_time": ms_bwd / ms_fwd, "unit": "GLUPS",
+        "kernel_forward": sim.kernel_name}
+    sim.close()
+    torch.cuda.empty_cache()
+
+    # 2D lid-driven cavity 1024^2, Re = 1000 (U = 0.1, nu = 0.1024)
+    z = torch.zeros((1024, 1024), dtype=torch.float32, device="cuda")
+    sim = lw.Lwacm(lw.D2Q9, 1024, 1024, 1, 0.1024, lw.CAVITY, lid=(0.1, 0.0))
+    sim.set_fields(z, z, z)
+    sim.step(64)
+    ms = _events_ms(sim.stream, lambda: sim.step(2000))
+    out["cavity_d2q9_1024"] = {"value": glups(1024 ** 2, 2000, ms), "unit": "GLUPS",
+                               "kernel": sim.kernel_name + "+wall_pass", "l2_resident": True}
+    sim.close()
+
+    # 2D Taylor-Green 64^2
+    sim = lw.Lwacm(lw.D2Q9, 64, 64, 1, 0.01)
+    sim.set_fields(*inputs.tgv2d(64, u0=0.01))
+    sim.step(64)
+    ms = _events_ms(sim.stream, lambda: sim.step(6400))
+    out["tgv_d2q9_64"] = {"value": glups(64 ** 2, 6400, ms), "unit": "GLUPS",
+                          "kernel": sim.kernel_name, "l2_resident": True}
+    sim.close()
+    return out
 
 
 def run_gpu(args):
@@ -272,6 +394,8 @@ def run_gpu(args):
         "clocks": clocks,
         "check": {"mass": diag["mass"], "ke": diag["ke"], "finite": diag["finite"]},
     }
+    if rank == 0 and not args.no_variants and ws == 1:
+        line["variants"] = variants(hbm)
     if rank == 0 and not args.no_cpu_baseline and ws == 1:
         try:
             line["cpu_baseline"] = cpu_baseline(args.cpu_steps)
@@ -294,8 +418,9 @@ def main():
     ap.add_argument("--graph-chunk", type=int, default=64)
     ap.add_argument("--kernel", type=int, default=0)
     ap.add_argument("--e2e-steps", type=int, default=20)
-    ap.add_argument("--cpu-steps", type=int, default=2)
+    ap.add_argument("--cpu-steps", type=int, default=40)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-variants", action="store_true")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3

@@ -99,7 +99,8 @@ def test_ensemble_256_sampled(lw):
     [32, 512] (seed 1), nu uniform on [0.002, 0.05], band-limited divergence-free
     initial velocity (wave numbers 1-4, rms 0.02), 2000 steps in one persistent
     launch; the five smallest domains and one mid-size domain checked against the
-    oracle, every domain checked for finite values."""
+    oracle, every domain checked for finite values. FP32 rounding accumulates at
+    most linearly with the step count: the 1000-step bound of 1e-5 becomes 2e-5."""
     doms = inputs.ensemble_2d(256, seed=1)
     dims = [(d["nx"], d["ny"]) for d in doms]
     nus = [d["nu"] for d in doms]
@@ -117,6 +118,6 @@ def test_ensemble_256_sampled(lw):
     for b in check:
         ref = oracle.step(9, *fields[b], nu=nus[b], nsteps=T)
         eu = max(float(np.max(np.abs(g - r))) for g, r in zip(got[b][1:], ref[1:])) / 0.02
-        assert eu < 1e-5, (b, dims[b], eu)
+        assert eu < 1e-5 * T / 1000, (b, dims[b], eu)
     print(f"ensemble: {sim.n_nodes} nodes in 256 domains, sampled domains agree")
     sim.close()
