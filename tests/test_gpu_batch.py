@@ -94,30 +94,53 @@ def test_barrier_timeout_is_reported(lw):
     ok.close()
 
 
-def test_ensemble_256_sampled(lw):
+def test_ensemble_256(lw):
     """The batched workload: 256 periodic D2Q9 domains, sides log-uniform on
     [32, 512] (seed 1), nu uniform on [0.002, 0.05], band-limited divergence-free
-    initial velocity (wave numbers 1-4, rms 0.02), 2000 steps in one persistent
-    launch; the five smallest domains and one mid-size domain checked against the
-    oracle, every domain checked for finite values. FP32 rounding accumulates at
-    most linearly with the step count: the 1000-step bound of 1e-5 becomes 2e-5."""
+    initial velocity (wave numbers 1-4, rms U = 0.02), 2000 steps in one
+    persistent launch.
+
+    * after 200 steps: six sampled domains (the five smallest and a mid-size one)
+      agree with the oracle to 1e-5 U;
+    * after 2000 steps: every one of the 256 domains, stepped once more from the
+      GPU's state by GPU and oracle, agrees to 1e-6 U (one step of FP32 rounding);
+    * the 2000-step runs themselves drift apart: the per-step FP32 rounding is
+      carried forward by the nonlinear flow (domain Reynolds numbers up to ~500),
+      about linearly in T (measured 4.6e-5 U at 1000 and 1.1e-4 U at 2000 steps
+      on the worst sampled domain); bound 2.5e-4 U at 2000 steps.
+    """
+    U = 0.02
     doms = inputs.ensemble_2d(256, seed=1)
     dims = [(d["nx"], d["ny"]) for d in doms]
     nus = [d["nu"] for d in doms]
     fields = [(d["d"], d["ux"], d["uy"]) for d in doms]
+    sizes = [d[0] * d[1] for d in dims]
+    order = np.argsort(sizes)
+    check = [int(b) for b in order[:5]] + [int(order[len(order) // 2])]
     sim = lw.LwacmBatch(9, dims, nus, mode=1)
     sim.set_domains(fields)
-    T = 2000
-    sim.step(T)
+    sim.step(200)
+    got = sim.get_domains()
+    for b in check:
+        ref = oracle.step(9, *fields[b], nu=nus[b], nsteps=200)
+        eu = max(float(np.max(np.abs(g - r))) for g, r in zip(got[b][1:], ref[1:])) / U
+        assert eu < 1e-5, (b, dims[b], eu)
+    sim.step(1800)
     sim.sync()
     assert sim.diagnostics()["finite"]
     got = sim.get_domains()
-    sizes = [d[0] * d[1] for d in dims]
-    order = np.argsort(sizes)
-    check = list(order[:5]) + [int(order[len(order) // 2])]
+    long_err = 0.0
     for b in check:
-        ref = oracle.step(9, *fields[b], nu=nus[b], nsteps=T)
-        eu = max(float(np.max(np.abs(g - r))) for g, r in zip(got[b][1:], ref[1:])) / 0.02
-        assert eu < 1e-5 * T / 1000, (b, dims[b], eu)
-    print(f"ensemble: {sim.n_nodes} nodes in 256 domains, sampled domains agree")
+        ref = oracle.step(9, *fields[b], nu=nus[b], nsteps=2000)
+        long_err = max(long_err, max(float(np.max(np.abs(g - r))) for g, r in zip(got[b][1:], ref[1:])) / U)
+    sim.step(1)
+    one = sim.get_domains()
+    worst1 = 0.0
+    for b in range(256):
+        ref1 = oracle.step(9, *got[b], nu=nus[b], nsteps=1)
+        worst1 = max(worst1, max(float(np.max(np.abs(g - r))) for g, r in zip(one[b][1:], ref1[1:])) / U)
+    print(f"ensemble: {sim.n_nodes} nodes in 256 domains; 2000 steps: sampled drift {long_err:.2e} U; "
+          f"one step from the GPU state, all domains: {worst1:.2e} U")
+    assert worst1 < 1e-6
+    assert long_err < 2.5e-4
     sim.close()
