@@ -89,8 +89,9 @@ enum {
                                   0 disables graphs; default 64) */
     LWACM_OPT_KERNEL = 9,  /* interior kernel: 0 = automatic choice (default),
                               1 = generic gather kernel, 2 = D3Q19 TMA row-tiled kernel,
-                              3 = D3Q19 register-prefetch z-march kernel (2 and 3 need a
-                              periodic domain with nx in {128, 256}, ny % 8 == 0, FP32
+                              3 = D3Q19 register-prefetch z-march kernel, 5 = D3Q19 half-row
+                              TMA kernel (2 and 3 need a periodic domain with nx in
+                              {128, 256}, 5 needs nx = 256; all need ny % 8 == 0 and FP32
                               storage: LWACM_E_UNSUPPORTED otherwise) */
     LWACM_OPT_BATCH_MODE = 10, /* batched contexts: 0 = one launch per step, replayed
                                   from CUDA graphs (default); 1 = one persistent

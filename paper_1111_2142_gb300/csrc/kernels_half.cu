@@ -1,0 +1,499 @@
+// Half-row variant of the TMA row-tiled D3Q19 kernel, for periodic domains with
+// nx = 256 and ny a multiple of 8: the moment form of Eq. ACM2.0 (see
+// lwacm_core.cuh), every field read from HBM once and written once per step.
+//
+// Same structure as kernels_tiled.cu (persistent CTAs over chunk-major
+// (y-column, z-chunk) items, TMA bulk copies of ten staged rows per plane, packed
+// row exchange through shared memory, three rotating accumulator planes), but each
+// 256-node row is shared by two warps (half h covers x = 128 h .. 128 h + 127, four
+// nodes per lane), so a CTA of 8 rows has 16 warps and each thread keeps half the
+// registers: 16 warps per SM instead of 8.
+//
+// The two halves of a row meet at x = 127|128 and, periodically, at x = 255|0. A
+// shuffle cannot cross them, so the values that must (the boundary lane's in-row
+// links and the x-shifted row-crossing diagonals) are written to a small edge
+// buffer in phase A and added by the partner half's boundary lane after the
+// barrier.
+#include <stdint.h>
+
+#include "launch.h"
+#include "lwacm_core.cuh"
+#include "tile_common.cuh"
+
+namespace lwacm {
+namespace {
+
+using namespace tile;
+
+constexpr int VXH = 4;                 // nodes per lane
+constexpr int NWH = 2 * ROWS;          // warps per CTA
+constexpr int NTH = NWH * 32;          // threads per CTA
+constexpr int RL = 256;                // row length (nx)
+constexpr int HALF = 128;              // nodes per half row
+constexpr int XSLOT = ROWS * RL;
+constexpr int XDIR = NSLOT * XSLOT;
+constexpr int XBUF = 2 * XDIR;
+constexpr int STAGE = 4 * TROWS * RL;
+// edge values per staged row and half: in-row c = (1,0,cz) from lane 31 (3),
+// -c from lane 0 (3), and the four shifted diagonals of the row-crossing send
+constexpr int E_INP = 0, E_INM = 3, E_UP1 = 6, E_UP2 = 7, E_DN1 = 8, E_DN2 = 9, NEDGE = 12;
+constexpr int EBUF = TROWS * 2 * NEDGE;
+constexpr size_t BYTES = (2 * (size_t)XBUF + 2 * (size_t)STAGE + 2 * (size_t)EBUF) * 4 + 64;
+constexpr uint32_t TX = STAGE * 4;
+
+using NC = NodeConst<VXH>;
+
+// Row-crossing values of one half row for the receivers above (UP) or below, as in
+// kernels_tiled.cu; the boundary lanes leave out the x-shifted diagonal that would
+// cross into the other half and record their own boundary value in `edge`.
+template <int MODE, bool UP>
+__device__ __forceinline__ void send_half(const NC &nc, float c4, float *base, float *edge, int lane) {
+    if (MODE == MID) {
+        float s0[VXH], s1[VXH];
+        {
+            float gp[VXH], gm[VXH];
+#pragma unroll
+            for (int i = 0; i < VXH; ++i) pair_g(nc, i, ypair_e(nc, 0, i), false, c4, gp[i], gm[i]);
+#pragma unroll
+            for (int i = 0; i < VXH; ++i) s0[i] = UP ? gp[i] : gm[i];
+        }
+        {  // k = 1: c = (1,1,0) [up: x <- x-1]; -c = (-1,-1,0) [down: x <- x+1]
+            float gp[VXH], gm[VXH];
+#pragma unroll
+            for (int i = 0; i < VXH; ++i) pair_g(nc, i, ypair_e(nc, 1, i), true, c4, gp[i], gm[i]);
+            if (UP) {
+                if (lane == 31) edge[E_UP1] = gp[VXH - 1];
+                xshift(gp, 1, lane);
+                if (lane == 0) gp[0] = 0.f;
+#pragma unroll
+                for (int i = 0; i < VXH; ++i) {
+                    s0[i] += gp[i];
+                    s1[i] = gp[i];
+                }
+            } else {
+                if (lane == 0) edge[E_DN1] = gm[0];
+                xshift(gm, -1, lane);
+                if (lane == 31) gm[VXH - 1] = 0.f;
+#pragma unroll
+                for (int i = 0; i < VXH; ++i) {
+                    s0[i] += gm[i];
+                    s1[i] = -gm[i];
+                }
+            }
+        }
+        {  // k = 2: c = (-1,1,0) [up: x <- x+1]; -c = (1,-1,0) [down: x <- x-1]
+            float gp[VXH], gm[VXH];
+#pragma unroll
+            for (int i = 0; i < VXH; ++i) pair_g(nc, i, ypair_e(nc, 2, i), true, c4, gp[i], gm[i]);
+            if (UP) {
+                if (lane == 0) edge[E_UP2] = gp[0];
+                xshift(gp, -1, lane);
+                if (lane == 31) gp[VXH - 1] = 0.f;
+#pragma unroll
+                for (int i = 0; i < VXH; ++i) {
+                    s0[i] += gp[i];
+                    s1[i] -= gp[i];
+                }
+            } else {
+                if (lane == 31) edge[E_DN2] = gm[VXH - 1];
+                xshift(gm, 1, lane);
+                if (lane == 0) gm[0] = 0.f;
+#pragma unroll
+                for (int i = 0; i < VXH; ++i) {
+                    s0[i] += gm[i];
+                    s1[i] += gm[i];
+                }
+            }
+        }
+        st_slot(base + 0 * XSLOT, s0, lane);
+        st_slot(base + 1 * XSLOT, s1, lane);
+    }
+    if (MODE != LAST) {  // slot 2 (c_z = +1): up -> c of k = 3; down -> -c of k = 4
+        float gp[VXH], gm[VXH];
+        const int k = UP ? 3 : 4;
+#pragma unroll
+        for (int i = 0; i < VXH; ++i) pair_g(nc, i, ypair_e(nc, k, i), true, c4, gp[i], gm[i]);
+        st_slot(base + 2 * XSLOT, UP ? gp : gm, lane);
+    }
+    if (MODE != FIRST) {  // slot 3 (c_z = -1): up -> c of k = 4; down -> -c of k = 3
+        float gp[VXH], gm[VXH];
+        const int k = UP ? 4 : 3;
+#pragma unroll
+        for (int i = 0; i < VXH; ++i) pair_g(nc, i, ypair_e(nc, k, i), true, c4, gp[i], gm[i]);
+        st_slot(base + 3 * XSLOT, UP ? gp : gm, lane);
+    }
+}
+
+// which halves of the in-row pair (c = (1,0,cz), -c) a mode needs
+__device__ __forceinline__ constexpr bool need_p(int mode, int cz) {
+    return mode == MID || (mode == FIRST ? cz > 0 : cz < 0);
+}
+__device__ __forceinline__ constexpr bool need_m(int mode, int cz) {
+    return mode == MID || (mode == FIRST ? cz < 0 : cz > 0);
+}
+
+template <int MODE>
+__device__ __forceinline__ void phase_a(float (&acc)[3][VXH][4], const float *stg, float *xbuf, float *ebuf,
+                                        const TiledParams &p, int lane, int row, int half) {
+    constexpr int PM = 0, P0 = 1, PP = 2;
+    float *up = xbuf + half * HALF, *dn = xbuf + XDIR + half * HALF;
+    {
+        NC nc;
+        node_consts(nc, stg + (row + 1) * RL + half * HALF, TROWS * RL, lane, p.s18);
+        float *edge = ebuf + ((row + 1) * 2 + half) * NEDGE;
+#pragma unroll
+        for (int i = 0; i < VXH; ++i) {
+            float gp, gm;
+            pair_g(nc, i, nc.W[i], false, p.c4, gp, gm);  // (0,0,+1) / (0,0,-1)
+            if (MODE == MID) {
+                acc[P0][i][3] = acc[P0][i][0];    // jz so far = d so far (c_z = +1 arrivals)
+                acc[P0][i][0] += 6.f * nc.K1[i];  // rest link: w_0 K = K/3
+                const float ar = p.a_s * nc.A1[i];  // a rho (post-combine)
+                acc[P0][i][1] = fmaf(ar, nc.U[i], acc[P0][i][1]);
+                acc[P0][i][2] = fmaf(ar, nc.V[i], acc[P0][i][2]);
+                acc[P0][i][3] = fmaf(ar, nc.W[i], acc[P0][i][3]);
+            }
+            if (MODE != LAST) acc[PP][i][0] += gp;
+            if (MODE != FIRST) dep(acc[PM][i], gm, 0, 0, -1);
+        }
+#pragma unroll
+        for (int cz = -1; cz <= 1; ++cz) {
+            const bool np = need_p(MODE, cz), nm = need_m(MODE, cz);
+            if (!np && !nm) continue;
+            float eP = 0.f, eM = 0.f;
+#pragma unroll
+            for (int i = 0; i < VXH; ++i) {
+                float gp, gm;
+                const float e = cz == 0 ? nc.U[i] : (cz > 0 ? nc.U[i] + nc.W[i] : nc.U[i] - nc.W[i]);
+                pair_g(nc, i, e, cz != 0, p.c4, gp, gm);
+                if (np) {
+                    if (i + 1 < VXH)
+                        dep(acc[pl<PM, P0, PP>(cz)][i + 1], gp, 1, 0, cz);
+                    else
+                        eP = gp;
+                }
+                if (nm) {
+                    if (i > 0)
+                        dep(acc[pl<PM, P0, PP>(-cz)][i - 1], gm, -1, 0, -cz);
+                    else
+                        eM = gm;
+                }
+            }
+            if (np) {
+                if (lane == 31) edge[E_INP + cz + 1] = eP;  // for the other half's lane 0
+                const float rP = __shfl_sync(FULL, eP, (lane + 31) & 31);
+                if (lane != 0) dep(acc[pl<PM, P0, PP>(cz)][0], rP, 1, 0, cz);
+            }
+            if (nm) {
+                if (lane == 0) edge[E_INM + cz + 1] = eM;  // for the other half's lane 31
+                const float rM = __shfl_sync(FULL, eM, (lane + 1) & 31);
+                if (lane != 31) dep(acc[pl<PM, P0, PP>(-cz)][VXH - 1], rM, -1, 0, -cz);
+            }
+        }
+        if (row + 1 < ROWS) send_half<MODE, true>(nc, p.c4, up + (row + 1) * RL, edge, lane);
+        if (row > 0) send_half<MODE, false>(nc, p.c4, dn + (row - 1) * RL, edge, lane);
+    }
+    if (row == 0) {  // bottom halo row y0-1 (staged row 0) feeds row 0
+        NC hc;
+        node_consts(hc, stg + half * HALF, TROWS * RL, lane, p.s18);
+        send_half<MODE, true>(hc, p.c4, up, ebuf + half * NEDGE, lane);
+    } else if (row == ROWS - 1) {  // top halo row y0+8 (staged row 9) feeds row 7
+        NC hc;
+        node_consts(hc, stg + (TROWS - 1) * RL + half * HALF, TROWS * RL, lane, p.s18);
+        send_half<MODE, false>(hc, p.c4, dn + (ROWS - 1) * RL, ebuf + ((TROWS - 1) * 2 + half) * NEDGE, lane);
+    }
+}
+
+template <int MODE>
+__device__ __forceinline__ void phase_b(float (&acc)[3][VXH][4], const float *xbuf, const float *ebuf,
+                                        float *out, const TiledParams &p, int lane, int row, int half,
+                                        int col, int zfin) {
+    constexpr int PM = 0, P0 = 1, PP = 2;
+    const float *up = xbuf + row * RL + half * HALF, *dn = xbuf + XDIR + row * RL + half * HALF;
+    const int ph = 1 - half;
+    const float *e_own = ebuf + ((row + 1) * 2 + ph) * NEDGE;  // partner half, same row
+    const float *e_up = ebuf + (row * 2 + ph) * NEDGE;         // partner half, row below
+    const float *e_dn = ebuf + ((row + 2) * 2 + ph) * NEDGE;   // partner half, row above
+    float o[VXH];
+    if (MODE == MID) {
+        ld_slot(up, o, lane);  // from below, c_z = 0: d, +jy
+        if (lane == 0) o[0] += e_up[E_UP1];
+        if (lane == 31) o[VXH - 1] += e_up[E_UP2];
+#pragma unroll
+        for (int i = 0; i < VXH; ++i) {
+            acc[P0][i][0] += o[i];
+            acc[P0][i][2] += o[i];
+        }
+        ld_slot(up + XSLOT, o, lane);
+        if (lane == 0) o[0] += e_up[E_UP1];
+        if (lane == 31) o[VXH - 1] -= e_up[E_UP2];
+#pragma unroll
+        for (int i = 0; i < VXH; ++i) acc[P0][i][1] += o[i];
+        ld_slot(dn, o, lane);  // from above, c_z = 0: d, -jy
+        if (lane == 31) o[VXH - 1] += e_dn[E_DN1];
+        if (lane == 0) o[0] += e_dn[E_DN2];
+#pragma unroll
+        for (int i = 0; i < VXH; ++i) {
+            acc[P0][i][0] += o[i];
+            acc[P0][i][2] -= o[i];
+        }
+        ld_slot(dn + XSLOT, o, lane);
+        if (lane == 31) o[VXH - 1] -= e_dn[E_DN1];
+        if (lane == 0) o[0] += e_dn[E_DN2];
+#pragma unroll
+        for (int i = 0; i < VXH; ++i) acc[P0][i][1] += o[i];
+    }
+    // in-row values from the other half's boundary lanes
+#pragma unroll
+    for (int cz = -1; cz <= 1; ++cz) {
+        if (need_p(MODE, cz) && lane == 0) dep(acc[pl<PM, P0, PP>(cz)][0], e_own[E_INP + cz + 1], 1, 0, cz);
+        if (need_m(MODE, cz) && lane == 31)
+            dep(acc[pl<PM, P0, PP>(-cz)][VXH - 1], e_own[E_INM + cz + 1], -1, 0, -cz);
+    }
+    if (MODE != LAST) {  // c_z = +1 arrivals for the plane ahead (jz implied by d)
+        ld_slot(up + 2 * XSLOT, o, lane);
+#pragma unroll
+        for (int i = 0; i < VXH; ++i) {
+            acc[PP][i][0] += o[i];
+            acc[PP][i][2] += o[i];
+        }
+        ld_slot(dn + 2 * XSLOT, o, lane);
+#pragma unroll
+        for (int i = 0; i < VXH; ++i) {
+            acc[PP][i][0] += o[i];
+            acc[PP][i][2] -= o[i];
+        }
+    }
+    if (MODE != FIRST) {  // c_z = -1 arrivals complete the plane behind
+        ld_slot(up + 3 * XSLOT, o, lane);
+#pragma unroll
+        for (int i = 0; i < VXH; ++i) {
+            acc[PM][i][0] += o[i];
+            acc[PM][i][2] += o[i];
+            acc[PM][i][3] -= o[i];
+        }
+        ld_slot(dn + 3 * XSLOT, o, lane);
+#pragma unroll
+        for (int i = 0; i < VXH; ++i) {
+            acc[PM][i][0] += o[i];
+            acc[PM][i][2] -= o[i];
+            acc[PM][i][3] -= o[i];
+        }
+        if (zfin >= 0) {
+            const long long rowoff =
+                ((long long)zfin * p.ny + col * ROWS + row) * p.nx + half * HALF + lane * VXH;
+            float *op = out + rowoff;
+            float r[VXH];
+#pragma unroll
+            for (int i = 0; i < VXH; ++i) r[i] = __frcp_rn(1.f + acc[PM][i][0]);
+            *reinterpret_cast<float4 *>(op) = make_float4(acc[PM][0][0], acc[PM][1][0], acc[PM][2][0], acc[PM][3][0]);
+#pragma unroll
+            for (int c = 1; c < 4; ++c)
+                *reinterpret_cast<float4 *>(op + c * p.fstride) =
+                    make_float4(acc[PM][0][c] * r[0], acc[PM][1][c] * r[1], acc[PM][2][c] * r[2],
+                                acc[PM][3][c] * r[3]);
+        }
+#pragma unroll
+        for (int i = 0; i < VXH; ++i)
+#pragma unroll
+            for (int c = 0; c < 4; ++c) acc[PM][i][c] = 0.f;
+    }
+}
+
+__device__ __forceinline__ void issue_plane(const float *in, const TiledParams &p, int col, int z,
+                                            float *stage, uint64_t *bar) {
+    const int zl = z < 0 ? z + p.nz : (z >= p.nz ? z - p.nz : z);
+    const int y0 = col * ROWS;
+    const long long plane = (long long)p.nx * p.ny;
+    mbar_expect_tx(bar, TX);
+    const uint32_t rb = (uint32_t)(RL * 4);
+#pragma unroll
+    for (int f = 0; f < 4; ++f) {
+        const float *src = in + f * p.fstride + (long long)zl * plane;
+        float *dst = stage + f * TROWS * RL;
+        if (y0 >= 1 && y0 + ROWS < p.ny) {
+            bulk_g2s(dst, src + (long long)(y0 - 1) * p.nx, TROWS * rb, bar);
+        } else {
+            const int yb = y0 - 1 < 0 ? y0 - 1 + p.ny : y0 - 1;
+            const int yt = y0 + ROWS >= p.ny ? y0 + ROWS - p.ny : y0 + ROWS;
+            bulk_g2s(dst, src + (long long)yb * p.nx, rb, bar);
+            bulk_g2s(dst + RL, src + (long long)y0 * p.nx, ROWS * rb, bar);
+            bulk_g2s(dst + (TROWS - 1) * RL, src + (long long)yt * p.nx, rb, bar);
+        }
+    }
+}
+
+__device__ __forceinline__ void rotate(float (&acc)[3][VXH][4]) {
+#pragma unroll
+    for (int i = 0; i < VXH; ++i) {
+#pragma unroll
+        for (int c = 0; c < 4; ++c) acc[0][i][c] = acc[1][i][c];
+#pragma unroll
+        for (int c = 0; c < 3; ++c) acc[1][i][c] = acc[2][i][c];
+#pragma unroll
+        for (int c = 0; c < 4; ++c) acc[2][i][c] = 0.f;
+    }
+}
+
+__global__ void __launch_bounds__(NTH, 1) k_d3q19_half(const float *__restrict__ in, float *__restrict__ out,
+                                                       TiledParams p) {
+    extern __shared__ float4 smem4[];
+    float *xs = reinterpret_cast<float *>(smem4);
+    float *stg = xs + 2 * XBUF;
+    float *eb = stg + 2 * STAGE;
+    uint64_t *bars = reinterpret_cast<uint64_t *>(eb + 2 * EBUF);
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int row = warp >> 1, half = warp & 1;
+    if ((int)blockIdx.x >= p.nitems) return;  // uniform per CTA
+
+    if (threadIdx.x == 0) {
+        mbar_init(&bars[0], 1);
+        mbar_init(&bars[1], 1);
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    __syncthreads();
+
+    TaskIter it(blockIdx.x, p.nitems, gridDim.x, p.ycols, p.zc, p.nz);
+    TaskIter pf = it;
+    int issued = 0;
+    for (int k = 0; k < 2 && pf.valid(); ++k) {
+        if (threadIdx.x == 0) issue_plane(in, p, pf.col, pf.pz, stg + k * STAGE, &bars[k]);
+        ++issued;
+        pf.next();
+    }
+
+    float acc[3][VXH][4];
+#pragma unroll
+    for (int a = 0; a < 3; ++a)
+#pragma unroll
+        for (int i = 0; i < VXH; ++i)
+#pragma unroll
+            for (int c = 0; c < 4; ++c) acc[a][i][c] = 0.f;
+
+    for (int tc = 0; it.valid(); ++tc) {
+        const int s = tc & 1;
+        const float *stage = stg + s * STAGE;
+        float *xbuf = xs + s * XBUF;
+        float *ebuf = eb + s * EBUF;
+        const bool ok = mbar_wait(&bars[s], (uint32_t)((tc >> 1) & 1));
+        const int mode = it.mode();
+        if (ok) {
+            if (mode == MID) {
+                phase_a<MID>(acc, stage, xbuf, ebuf, p, lane, row, half);
+            } else if (mode == FIRST) {
+#pragma unroll
+                for (int a = 0; a < 3; ++a)
+#pragma unroll
+                    for (int i = 0; i < VXH; ++i)
+#pragma unroll
+                        for (int c = 0; c < 4; ++c) acc[a][i][c] = 0.f;
+                phase_a<FIRST>(acc, stage, xbuf, ebuf, p, lane, row, half);
+            } else {
+                phase_a<LAST>(acc, stage, xbuf, ebuf, p, lane, row, half);
+            }
+        }
+        if (__syncthreads_or(ok ? 0 : 1)) {
+            if (threadIdx.x == 0) {
+                atomicExch(p.err, 1);
+                for (int t = tc + 1; t < issued; ++t) mbar_wait(&bars[t & 1], (uint32_t)((t >> 1) & 1));
+            }
+            return;
+        }
+        if (pf.valid()) {
+            if (threadIdx.x == 0) {
+                asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+                issue_plane(in, p, pf.col, pf.pz, stg + s * STAGE, &bars[s]);
+            }
+            ++issued;
+            pf.next();
+        }
+        if (mode == MID) {
+            phase_b<MID>(acc, xbuf, ebuf, out, p, lane, row, half, it.col, it.pz > it.za ? it.pz - 1 : -1);
+            rotate(acc);
+        } else if (mode == FIRST) {
+            phase_b<FIRST>(acc, xbuf, ebuf, out, p, lane, row, half, it.col, -1);
+            rotate(acc);
+        } else {
+            phase_b<LAST>(acc, xbuf, ebuf, out, p, lane, row, half, it.col, it.zb - 1);
+#pragma unroll
+            for (int a = 1; a < 3; ++a)
+#pragma unroll
+                for (int i = 0; i < VXH; ++i)
+#pragma unroll
+                    for (int c = 0; c < 4; ++c) acc[a][i][c] = 0.f;
+        }
+        it.next();
+    }
+}
+
+cudaError_t prepare(int *ctas) {
+    static int state = 0, nctas = 0;
+    if (state == 0) {
+        cudaError_t e = cudaFuncSetAttribute(k_d3q19_half, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)BYTES);
+        if (e != cudaSuccess) return e;
+        int nb = 0, dev = 0, sms = 0;
+        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_d3q19_half, NTH, BYTES);
+        if (e != cudaSuccess) return e;
+        e = cudaGetDevice(&dev);
+        if (e != cudaSuccess) return e;
+        e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+        if (e != cudaSuccess) return e;
+        state = nb >= 1 ? 1 : -1;
+        nctas = nb * sms;
+    }
+    if (ctas) *ctas = nctas;
+    return state == 1 ? cudaSuccess : cudaErrorNotSupported;
+}
+
+int half_chunk_planes(int ycols, int nz, int ctas) {
+    if (ctas < 1) ctas = 1;
+    int best = nz;
+    double best_t = 1e300;
+    for (int zc = (nz < 4 ? nz : 4); zc <= nz; ++zc) {
+        const long long items = (long long)ycols * ((nz + zc - 1) / zc);
+        const long long per = (items + ctas - 1) / ctas;
+        const double t = (double)per * (zc + 0.7);
+        if (t < best_t - 1e-9) {
+            best_t = t;
+            best = zc;
+        }
+    }
+    return best;
+}
+
+}  // namespace
+
+bool half_supported(int Q, int storage, const StepParams &p) {
+    if (Q != 19 || storage != STORE_F32 || p.bc != BC_PERIODIC) return false;
+    if (p.nx != RL || p.ny % ROWS != 0 || p.ny < ROWS || p.nz < 1) return false;
+    if (p.fstride % 4 != 0 || !p.err) return false;
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) return false;
+    return prepare(nullptr) == cudaSuccess;
+}
+
+cudaError_t launch_step_half(int Q, int storage, const void *in, void *out, const StepParams &sp,
+                             cudaStream_t st) {
+    if (!half_supported(Q, storage, sp)) return cudaErrorNotSupported;
+    int ctas = 0;
+    cudaError_t e = prepare(&ctas);
+    if (e != cudaSuccess) return e;
+    TiledParams p;
+    p.nx = sp.nx;
+    p.ny = sp.ny;
+    p.nz = sp.nz;
+    p.ycols = sp.ny / ROWS;
+    p.zc = half_chunk_planes(p.ycols, sp.nz, ctas);
+    p.nitems = p.ycols * ((sp.nz + p.zc - 1) / p.zc);
+    p.fstride = sp.fstride;
+    const double nu = (double)sp.s / 18.0;
+    p.s18 = (float)nu;
+    p.c4 = (float)(1.0 / (4.0 * nu));
+    p.a_s = (float)((double)sp.a / nu);
+    p.err = sp.err;
+    const int grid = ctas < p.nitems ? ctas : p.nitems;
+    k_d3q19_half<<<(unsigned)grid, NTH, BYTES, st>>>((const float *)in, (float *)out, p);
+    return cudaGetLastError();
+}
+
+}  // namespace lwacm

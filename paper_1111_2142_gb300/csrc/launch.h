@@ -67,6 +67,11 @@ cudaError_t launch_batch_step(int Q, int storage, const void *in, void *out, con
 cudaError_t launch_batch_persistent(int Q, int storage, void *buf0, void *buf1, const BatchParams &bp,
                                     long long nsteps, int parity, cudaStream_t st);
 
+// Half-row TMA variant of the D3Q19 kernel (nx = 256, 16 warps per CTA).
+bool half_supported(int Q, int storage, const StepParams &p);
+cudaError_t launch_step_half(int Q, int storage, const void *in, void *out, const StepParams &p,
+                             cudaStream_t st);
+
 // Register-prefetch z-marching variant of the D3Q19 kernel (same shapes).
 bool zmarch_supported(int Q, int storage, const StepParams &p);
 cudaError_t launch_step_zmarch(int Q, int storage, const void *in, void *out, const StepParams &p,

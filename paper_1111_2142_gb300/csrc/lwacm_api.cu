@@ -47,7 +47,7 @@ struct lwacm_ctx {
     cudaStream_t cap_stream = nullptr;
     cudaGraphExec_t gexec[2] = {nullptr, nullptr};
     int gchunk[2] = {0, 0};
-    int kernel = 1;  // 1 generic, 2 tiled (TMA), 3 z-march (register prefetch)
+    int kernel = 1;  // 1 generic, 2 tiled (TMA), 3 z-march (register prefetch), 4 batch, 5 half-row TMA
     std::string kname = "none";
     // batched domains (nbatch > 0): packed one after the other
     int nbatch = 0;
@@ -165,16 +165,20 @@ bool choose_kernel(lwacm_ctx *c) {
     const bool dev = c->bound;
     const bool t_ok = dev && tiled_supported(c->Q, c->storage, p);
     const bool z_ok = dev && zmarch_supported(c->Q, c->storage, p);
+    const bool h_ok = dev && half_supported(c->Q, c->storage, p);
     bool ok = true;
     switch (c->kernel_opt) {
         case 1: c->kernel = 1; break;
         case 2: c->kernel = t_ok ? 2 : 1; ok = t_ok || !dev; break;
         case 3: c->kernel = z_ok ? 3 : 1; ok = z_ok || !dev; break;
+        case 5: c->kernel = h_ok ? 5 : 1; ok = h_ok || !dev; break;
         default: c->kernel = z_ok ? 3 : (t_ok ? 2 : 1); break;
     }
     static const char *gname[2] = {"generic_d2q9", "generic_d3q19"};
-    c->kname = c->kernel == 2 ? tiled_name(c->Q)
-                              : (c->kernel == 3 ? "zmarch_d3q19" : gname[c->Q == 19 ? 1 : 0]);
+    c->kname = c->kernel == 2   ? tiled_name(c->Q)
+               : c->kernel == 3 ? "zmarch_d3q19"
+               : c->kernel == 5 ? "half_d3q19_tma"
+                                : gname[c->Q == 19 ? 1 : 0];
     return ok;
 }
 
@@ -201,6 +205,7 @@ cudaError_t step_between(lwacm_ctx *c, const void *in, void *out, cudaStream_t s
     const StepParams p = params(c);
     cudaError_t e = c->kernel == 2   ? launch_step_tiled(c->Q, c->storage, in, out, p, st)
                     : c->kernel == 3 ? launch_step_zmarch(c->Q, c->storage, in, out, p, st)
+                    : c->kernel == 5 ? launch_step_half(c->Q, c->storage, in, out, p, st)
                                      : launch_step_generic(c->Q, c->storage, in, out, p, st);
     if (e != cudaSuccess) return e;
     if (c->bc != LWACM_BC_PERIODIC) e = launch_wall_pass(c->Q, c->storage, in, out, p, st);
@@ -420,7 +425,7 @@ lwacm_status lwacm_set_option(lwacm_ctx *c, int key, double v) {
         }
         case LWACM_OPT_KERNEL: {
             const int k = (int)v;
-            if (k < 0 || k > 3) return fail(c, LWACM_E_ARG, "kernel must be 0, 1, 2 or 3");
+            if (k < 0 || k > 5 || k == 4) return fail(c, LWACM_E_ARG, "kernel must be 0, 1, 2, 3 or 5");
             const int old = c->kernel_opt;
             c->kernel_opt = k;
             if (!choose_kernel(c)) {
