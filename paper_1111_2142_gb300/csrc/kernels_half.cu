@@ -62,18 +62,18 @@ __device__ __forceinline__ void send_half(const NC &nc, float c4, float *base, f
 #pragma unroll
             for (int i = 0; i < VXH; ++i) pair_g(nc, i, ypair_e(nc, 1, i), true, c4, gp[i], gm[i]);
             if (UP) {
-                if (lane == 31) edge[E_UP1] = gp[VXH - 1];
+                st_shared_if(edge + E_UP1, gp[VXH - 1], lane == 31);
                 xshift(gp, 1, lane);
-                if (lane == 0) gp[0] = 0.f;
+                gp[0] = lane == 0 ? 0.f : gp[0];
 #pragma unroll
                 for (int i = 0; i < VXH; ++i) {
                     s0[i] += gp[i];
                     s1[i] = gp[i];
                 }
             } else {
-                if (lane == 0) edge[E_DN1] = gm[0];
+                st_shared_if(edge + E_DN1, gm[0], lane == 0);
                 xshift(gm, -1, lane);
-                if (lane == 31) gm[VXH - 1] = 0.f;
+                gm[VXH - 1] = lane == 31 ? 0.f : gm[VXH - 1];
 #pragma unroll
                 for (int i = 0; i < VXH; ++i) {
                     s0[i] += gm[i];
@@ -86,18 +86,18 @@ __device__ __forceinline__ void send_half(const NC &nc, float c4, float *base, f
 #pragma unroll
             for (int i = 0; i < VXH; ++i) pair_g(nc, i, ypair_e(nc, 2, i), true, c4, gp[i], gm[i]);
             if (UP) {
-                if (lane == 0) edge[E_UP2] = gp[0];
+                st_shared_if(edge + E_UP2, gp[0], lane == 0);
                 xshift(gp, -1, lane);
-                if (lane == 31) gp[VXH - 1] = 0.f;
+                gp[VXH - 1] = lane == 31 ? 0.f : gp[VXH - 1];
 #pragma unroll
                 for (int i = 0; i < VXH; ++i) {
                     s0[i] += gp[i];
                     s1[i] -= gp[i];
                 }
             } else {
-                if (lane == 31) edge[E_DN2] = gm[VXH - 1];
+                st_shared_if(edge + E_DN2, gm[VXH - 1], lane == 31);
                 xshift(gm, 1, lane);
-                if (lane == 0) gm[0] = 0.f;
+                gm[0] = lane == 0 ? 0.f : gm[0];
 #pragma unroll
                 for (int i = 0; i < VXH; ++i) {
                     s0[i] += gm[i];
@@ -180,14 +180,16 @@ __device__ __forceinline__ void phase_a(float (&acc)[3][VXH][4], const float *st
                 }
             }
             if (np) {
-                if (lane == 31) edge[E_INP + cz + 1] = eP;  // for the other half's lane 0
-                const float rP = __shfl_sync(FULL, eP, (lane + 31) & 31);
-                if (lane != 0) dep(acc[pl<PM, P0, PP>(cz)][0], rP, 1, 0, cz);
+                st_shared_if(edge + E_INP + cz + 1, eP, lane == 31);  // for the other half's lane 0
+                float rP = __shfl_sync(FULL, eP, (lane + 31) & 31);
+                rP = lane == 0 ? 0.f : rP;  // lane 0's comes from the other half (phase B)
+                dep(acc[pl<PM, P0, PP>(cz)][0], rP, 1, 0, cz);
             }
             if (nm) {
-                if (lane == 0) edge[E_INM + cz + 1] = eM;  // for the other half's lane 31
-                const float rM = __shfl_sync(FULL, eM, (lane + 1) & 31);
-                if (lane != 31) dep(acc[pl<PM, P0, PP>(-cz)][VXH - 1], rM, -1, 0, -cz);
+                st_shared_if(edge + E_INM + cz + 1, eM, lane == 0);  // for the other half's lane 31
+                float rM = __shfl_sync(FULL, eM, (lane + 1) & 31);
+                rM = lane == 31 ? 0.f : rM;
+                dep(acc[pl<PM, P0, PP>(-cz)][VXH - 1], rM, -1, 0, -cz);
             }
         }
         if (row + 1 < ROWS) send_half<MODE, true>(nc, p.c4, up + (row + 1) * RL, edge, lane);
@@ -216,39 +218,46 @@ __device__ __forceinline__ void phase_b(float (&acc)[3][VXH][4], const float *xb
     const float *e_dn = ebuf + ((row + 2) * 2 + ph) * NEDGE;   // partner half, row above
     float o[VXH];
     if (MODE == MID) {
+        const float u1 = e_up[E_UP1], u2 = e_up[E_UP2], d1 = e_dn[E_DN1], d2 = e_dn[E_DN2];
+        const bool l0 = lane == 0, l31 = lane == 31;
         ld_slot(up, o, lane);  // from below, c_z = 0: d, +jy
-        if (lane == 0) o[0] += e_up[E_UP1];
-        if (lane == 31) o[VXH - 1] += e_up[E_UP2];
+        o[0] += l0 ? u1 : 0.f;
+        o[VXH - 1] += l31 ? u2 : 0.f;
 #pragma unroll
         for (int i = 0; i < VXH; ++i) {
             acc[P0][i][0] += o[i];
             acc[P0][i][2] += o[i];
         }
         ld_slot(up + XSLOT, o, lane);
-        if (lane == 0) o[0] += e_up[E_UP1];
-        if (lane == 31) o[VXH - 1] -= e_up[E_UP2];
+        o[0] += l0 ? u1 : 0.f;
+        o[VXH - 1] -= l31 ? u2 : 0.f;
 #pragma unroll
         for (int i = 0; i < VXH; ++i) acc[P0][i][1] += o[i];
         ld_slot(dn, o, lane);  // from above, c_z = 0: d, -jy
-        if (lane == 31) o[VXH - 1] += e_dn[E_DN1];
-        if (lane == 0) o[0] += e_dn[E_DN2];
+        o[VXH - 1] += l31 ? d1 : 0.f;
+        o[0] += l0 ? d2 : 0.f;
 #pragma unroll
         for (int i = 0; i < VXH; ++i) {
             acc[P0][i][0] += o[i];
             acc[P0][i][2] -= o[i];
         }
         ld_slot(dn + XSLOT, o, lane);
-        if (lane == 31) o[VXH - 1] -= e_dn[E_DN1];
-        if (lane == 0) o[0] += e_dn[E_DN2];
+        o[VXH - 1] -= l31 ? d1 : 0.f;
+        o[0] += l0 ? d2 : 0.f;
 #pragma unroll
         for (int i = 0; i < VXH; ++i) acc[P0][i][1] += o[i];
     }
     // in-row values from the other half's boundary lanes
 #pragma unroll
     for (int cz = -1; cz <= 1; ++cz) {
-        if (need_p(MODE, cz) && lane == 0) dep(acc[pl<PM, P0, PP>(cz)][0], e_own[E_INP + cz + 1], 1, 0, cz);
-        if (need_m(MODE, cz) && lane == 31)
-            dep(acc[pl<PM, P0, PP>(-cz)][VXH - 1], e_own[E_INM + cz + 1], -1, 0, -cz);
+        if (need_p(MODE, cz)) {
+            const float v = e_own[E_INP + cz + 1];
+            dep(acc[pl<PM, P0, PP>(cz)][0], lane == 0 ? v : 0.f, 1, 0, cz);
+        }
+        if (need_m(MODE, cz)) {
+            const float v = e_own[E_INM + cz + 1];
+            dep(acc[pl<PM, P0, PP>(-cz)][VXH - 1], lane == 31 ? v : 0.f, -1, 0, -cz);
+        }
     }
     if (MODE != LAST) {  // c_z = +1 arrivals for the plane ahead (jz implied by d)
         ld_slot(up + 2 * XSLOT, o, lane);
@@ -285,7 +294,7 @@ __device__ __forceinline__ void phase_b(float (&acc)[3][VXH][4], const float *xb
             float *op = out + rowoff;
             float r[VXH];
 #pragma unroll
-            for (int i = 0; i < VXH; ++i) r[i] = __frcp_rn(1.f + acc[PM][i][0]);
+            for (int i = 0; i < VXH; ++i) r[i] = rcp_nr(1.f + acc[PM][i][0]);
             *reinterpret_cast<float4 *>(op) = make_float4(acc[PM][0][0], acc[PM][1][0], acc[PM][2][0], acc[PM][3][0]);
 #pragma unroll
             for (int c = 1; c < 4; ++c)
