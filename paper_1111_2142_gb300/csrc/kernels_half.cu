@@ -43,42 +43,43 @@ constexpr uint32_t TX = STAGE * 4;
 
 using NC = NodeConst<VXH>;
 
-// Row-crossing values of one half row for the receivers above (UP) or below, as in
-// kernels_tiled.cu; the boundary lanes leave out the x-shifted diagonal that would
-// cross into the other half and record their own boundary value in `edge`.
-template <int MODE, bool UP>
-__device__ __forceinline__ void send_half(const NC &nc, float c4, float *base, float *edge, int lane) {
+// Row-crossing values of one half row, computed once per link pair and sent to
+// the receivers above (up, c_y = +1; when UP) and below (down, c_y = -1; when DN),
+// four values per receiver x and direction as in kernels_tiled.cu:
+//   slot 0: sum of the three c_z = 0 links (d, +-jy), slot 1: their x-momentum,
+//   slot 2: the c_z = +1 link, slot 3: the c_z = -1 link.
+// The boundary lanes leave out the x-shifted diagonal that would cross into the
+// other half and record their own boundary value in `edge`.
+template <int MODE>
+__device__ __forceinline__ void send_rows(const NC &nc, float c4, float *ubase, float *dbase, bool UP,
+                                          bool DN, float *edge, int lane) {
+    const bool l0 = lane == 0, l31 = lane == 31;
     if (MODE == MID) {
-        float s0[VXH], s1[VXH];
-        {
-            float gp[VXH], gm[VXH];
+        float u0[VXH], u1[VXH], d0[VXH], d1[VXH];
+        {  // k = 0: c = (0,1,0), -c = (0,-1,0)
 #pragma unroll
-            for (int i = 0; i < VXH; ++i) pair_g(nc, i, ypair_e(nc, 0, i), false, c4, gp[i], gm[i]);
-#pragma unroll
-            for (int i = 0; i < VXH; ++i) s0[i] = UP ? gp[i] : gm[i];
+            for (int i = 0; i < VXH; ++i) pair_g(nc, i, ypair_e(nc, 0, i), false, c4, u0[i], d0[i]);
         }
-        {  // k = 1: c = (1,1,0) [up: x <- x-1]; -c = (-1,-1,0) [down: x <- x+1]
+        {  // k = 1: c = (1,1,0) [up: receiver x <- x-1]; -c = (-1,-1,0) [down: x <- x+1]
             float gp[VXH], gm[VXH];
 #pragma unroll
             for (int i = 0; i < VXH; ++i) pair_g(nc, i, ypair_e(nc, 1, i), true, c4, gp[i], gm[i]);
             if (UP) {
-                st_shared_if(edge + E_UP1, gp[VXH - 1], lane == 31);
+                st_shared_if(edge + E_UP1, gp[VXH - 1], l31);
                 xshift(gp, 1, lane);
-                gp[0] = lane == 0 ? 0.f : gp[0];
-#pragma unroll
-                for (int i = 0; i < VXH; ++i) {
-                    s0[i] += gp[i];
-                    s1[i] = gp[i];
-                }
-            } else {
-                st_shared_if(edge + E_DN1, gm[0], lane == 0);
+                gp[0] = l0 ? 0.f : gp[0];
+            }
+            if (DN) {
+                st_shared_if(edge + E_DN1, gm[0], l0);
                 xshift(gm, -1, lane);
-                gm[VXH - 1] = lane == 31 ? 0.f : gm[VXH - 1];
+                gm[VXH - 1] = l31 ? 0.f : gm[VXH - 1];
+            }
 #pragma unroll
-                for (int i = 0; i < VXH; ++i) {
-                    s0[i] += gm[i];
-                    s1[i] = -gm[i];
-                }
+            for (int i = 0; i < VXH; ++i) {
+                u0[i] += gp[i];
+                u1[i] = gp[i];
+                d0[i] += gm[i];
+                d1[i] = -gm[i];
             }
         }
         {  // k = 2: c = (-1,1,0) [up: x <- x+1]; -c = (1,-1,0) [down: x <- x-1]
@@ -86,41 +87,48 @@ __device__ __forceinline__ void send_half(const NC &nc, float c4, float *base, f
 #pragma unroll
             for (int i = 0; i < VXH; ++i) pair_g(nc, i, ypair_e(nc, 2, i), true, c4, gp[i], gm[i]);
             if (UP) {
-                st_shared_if(edge + E_UP2, gp[0], lane == 0);
+                st_shared_if(edge + E_UP2, gp[0], l0);
                 xshift(gp, -1, lane);
-                gp[VXH - 1] = lane == 31 ? 0.f : gp[VXH - 1];
-#pragma unroll
-                for (int i = 0; i < VXH; ++i) {
-                    s0[i] += gp[i];
-                    s1[i] -= gp[i];
-                }
-            } else {
-                st_shared_if(edge + E_DN2, gm[VXH - 1], lane == 31);
+                gp[VXH - 1] = l31 ? 0.f : gp[VXH - 1];
+            }
+            if (DN) {
+                st_shared_if(edge + E_DN2, gm[VXH - 1], l31);
                 xshift(gm, 1, lane);
-                gm[0] = lane == 0 ? 0.f : gm[0];
+                gm[0] = l0 ? 0.f : gm[0];
+            }
 #pragma unroll
-                for (int i = 0; i < VXH; ++i) {
-                    s0[i] += gm[i];
-                    s1[i] += gm[i];
-                }
+            for (int i = 0; i < VXH; ++i) {
+                u0[i] += gp[i];
+                u1[i] -= gp[i];
+                d0[i] += gm[i];
+                d1[i] += gm[i];
             }
         }
-        st_slot(base + 0 * XSLOT, s0, lane);
-        st_slot(base + 1 * XSLOT, s1, lane);
+        if (UP) {
+            st_slot(ubase + 0 * XSLOT, u0, lane);
+            st_slot(ubase + 1 * XSLOT, u1, lane);
+        }
+        if (DN) {
+            st_slot(dbase + 0 * XSLOT, d0, lane);
+            st_slot(dbase + 1 * XSLOT, d1, lane);
+        }
     }
-    if (MODE != LAST) {  // slot 2 (c_z = +1): up -> c of k = 3; down -> -c of k = 4
+    // k = 3: c = (0,1,1), -c = (0,-1,-1); k = 4: c = (0,1,-1), -c = (0,-1,1)
+    // slot 2 (c_z = +1): up <- c of k = 3, down <- -c of k = 4
+    // slot 3 (c_z = -1): up <- c of k = 4, down <- -c of k = 3
+    {
         float gp[VXH], gm[VXH];
-        const int k = UP ? 3 : 4;
 #pragma unroll
-        for (int i = 0; i < VXH; ++i) pair_g(nc, i, ypair_e(nc, k, i), true, c4, gp[i], gm[i]);
-        st_slot(base + 2 * XSLOT, UP ? gp : gm, lane);
+        for (int i = 0; i < VXH; ++i) pair_g(nc, i, ypair_e(nc, 3, i), true, c4, gp[i], gm[i]);
+        if (UP && MODE != LAST) st_slot(ubase + 2 * XSLOT, gp, lane);
+        if (DN && MODE != FIRST) st_slot(dbase + 3 * XSLOT, gm, lane);
     }
-    if (MODE != FIRST) {  // slot 3 (c_z = -1): up -> c of k = 4; down -> -c of k = 3
+    {
         float gp[VXH], gm[VXH];
-        const int k = UP ? 4 : 3;
 #pragma unroll
-        for (int i = 0; i < VXH; ++i) pair_g(nc, i, ypair_e(nc, k, i), true, c4, gp[i], gm[i]);
-        st_slot(base + 3 * XSLOT, UP ? gp : gm, lane);
+        for (int i = 0; i < VXH; ++i) pair_g(nc, i, ypair_e(nc, 4, i), true, c4, gp[i], gm[i]);
+        if (UP && MODE != FIRST) st_slot(ubase + 3 * XSLOT, gp, lane);
+        if (DN && MODE != LAST) st_slot(dbase + 2 * XSLOT, gm, lane);
     }
 }
 
@@ -192,17 +200,17 @@ __device__ __forceinline__ void phase_a(float (&acc)[3][VXH][4], const float *st
                 dep(acc[pl<PM, P0, PP>(-cz)][VXH - 1], rM, -1, 0, -cz);
             }
         }
-        if (row + 1 < ROWS) send_half<MODE, true>(nc, p.c4, up + (row + 1) * RL, edge, lane);
-        if (row > 0) send_half<MODE, false>(nc, p.c4, dn + (row - 1) * RL, edge, lane);
+        send_rows<MODE>(nc, p.c4, up + (row + 1) * RL, dn + (row - 1) * RL, row + 1 < ROWS, row > 0, edge, lane);
     }
     if (row == 0) {  // bottom halo row y0-1 (staged row 0) feeds row 0
         NC hc;
         node_consts(hc, stg + half * HALF, TROWS * RL, lane, p.s18);
-        send_half<MODE, true>(hc, p.c4, up, ebuf + half * NEDGE, lane);
+        send_rows<MODE>(hc, p.c4, up, nullptr, true, false, ebuf + half * NEDGE, lane);
     } else if (row == ROWS - 1) {  // top halo row y0+8 (staged row 9) feeds row 7
         NC hc;
         node_consts(hc, stg + (TROWS - 1) * RL + half * HALF, TROWS * RL, lane, p.s18);
-        send_half<MODE, false>(hc, p.c4, dn + (ROWS - 1) * RL, ebuf + ((TROWS - 1) * 2 + half) * NEDGE, lane);
+        send_rows<MODE>(hc, p.c4, nullptr, dn + (ROWS - 1) * RL, false, true,
+                        ebuf + ((TROWS - 1) * 2 + half) * NEDGE, lane);
     }
 }
 
