@@ -174,6 +174,26 @@ def _events_ms(stream, fn):
     return e0.elapsed_time(e1)
 
 
+KERNEL_SOURCES = {
+    "half_d3q19_tma": ("kernels_half.cu", "tile_common.cuh", "lwacm_core.cuh"),
+    "zmarch_d3q19": ("kernels_zmarch.cu", "tile_common.cuh", "lwacm_core.cuh"),
+}
+
+
+def _kernel_source_hash(kname):
+    """SHA-256 over the CUDA sources of an interior kernel: stored ncu traffic is
+    used only while it matches the kernel as built."""
+    import hashlib
+    files = KERNEL_SOURCES.get(kname)
+    if not files:
+        return None
+    h = hashlib.sha256()
+    for fn in files:
+        with open(os.path.join(ROOT, "paper_1111_2142_gb300", "csrc", fn), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()
+
+
 def variants(hbm):
     """The other configurations and forms, each timed with CUDA events on its own
     stream after a warm-up: storage modes and kernels for the 256^3 workload, the
@@ -192,7 +212,8 @@ def variants(hbm):
     for name, kw, bpn in (("d3q19_256_bf16_storage", dict(storage=lw.BF16), 16),
                           ("d3q19_256_fp16_storage", dict(storage=lw.F16), 16),
                           ("d3q19_256_generic_kernel", dict(kernel=1), 32),
-                          ("d3q19_256_tma_kernel", dict(kernel=2), 32)):
+                          ("d3q19_256_tma_kernel", dict(kernel=2), 32),
+                          ("d3q19_256_zmarch_kernel", dict(kernel=3), 32)):
         sim = lw.Lwacm(lw.D3Q19, n, n, n, NU, **kw)
         sim.set_fields(*f)
         sim.step(20)
@@ -338,7 +359,8 @@ def run_gpu(args):
         try:
             with open(tf) as fh:
                 tj = json.load(fh)
-            if tj.get("kernel") == sim.kernel_name:
+            if tj.get("kernel") == sim.kernel_name and tj.get("source_sha256") == _kernel_source_hash(
+                    sim.kernel_name):
                 traffic = tj.get("bytes_per_launch")
         except Exception:
             traffic = None

@@ -1,5 +1,5 @@
 // Half-row variant of the TMA row-tiled D3Q19 kernel, for periodic domains with
-// nx = 256 and ny a multiple of 8: the moment form of Eq. ACM2.0 (see
+// nx = 256 (or 128) and ny a multiple of 8: the moment form of Eq. ACM2.0 (see
 // lwacm_core.cuh), every field read from HBM once and written once per step.
 //
 // Same structure as kernels_tiled.cu (persistent CTAs over chunk-major
@@ -14,6 +14,10 @@
 // links and the x-shifted row-crossing diagonals) are written to a small edge
 // buffer in phase A and added by the partner half's boundary lane after the
 // barrier.
+//
+// nx = 128 uses the same code with one warp per row (NH = 1): the warp's shuffles
+// wrap x periodically by themselves, there is no edge buffer, and two CTAs of 8
+// warps share an SM.
 #include <stdint.h>
 
 #include "launch.h"
@@ -26,20 +30,25 @@ namespace {
 using namespace tile;
 
 constexpr int VXH = 4;                 // nodes per lane
-constexpr int NWH = 2 * ROWS;          // warps per CTA
-constexpr int NTH = NWH * 32;          // threads per CTA
-constexpr int RL = 256;                // row length (nx)
-constexpr int HALF = 128;              // nodes per half row
-constexpr int XSLOT = ROWS * RL;
-constexpr int XDIR = NSLOT * XSLOT;
-constexpr int XBUF = 2 * XDIR;
-constexpr int STAGE = 4 * TROWS * RL;
+constexpr int HALF = 128;              // nodes per warp row segment
 // edge values per staged row and half: in-row c = (1,0,cz) from lane 31 (3),
 // -c from lane 0 (3), and the four shifted diagonals of the row-crossing send
 constexpr int E_INP = 0, E_INM = 3, E_UP1 = 6, E_UP2 = 7, E_DN1 = 8, E_DN2 = 9, NEDGE = 12;
-constexpr int EBUF = TROWS * 2 * NEDGE;
-constexpr size_t BYTES = (2 * (size_t)XBUF + 2 * (size_t)STAGE + 2 * (size_t)EBUF) * 4 + 64;
-constexpr uint32_t TX = STAGE * 4;
+
+// NH warps share a row of nx = 128 NH nodes (NH = 1: one warp per row, its lanes
+// wrap periodically by themselves; NH = 2: two halves with the edge exchange)
+template <int NH>
+struct HG {
+    static constexpr int NTH = ROWS * NH * 32;  // threads per CTA
+    static constexpr int RL = HALF * NH;        // row length (nx)
+    static constexpr int XSLOT = ROWS * RL;
+    static constexpr int XDIR = NSLOT * XSLOT;
+    static constexpr int XBUF = 2 * XDIR;
+    static constexpr int STAGE = 4 * TROWS * RL;
+    static constexpr int EBUF = NH == 2 ? TROWS * 2 * NEDGE : 0;
+    static constexpr size_t BYTES = (2 * (size_t)XBUF + 2 * (size_t)STAGE + 2 * (size_t)EBUF) * 4 + 64;
+    static constexpr uint32_t TX = STAGE * 4;
+};
 
 using NC = NodeConst<VXH>;
 
@@ -50,10 +59,11 @@ using NC = NodeConst<VXH>;
 //   slot 2: the c_z = +1 link, slot 3: the c_z = -1 link.
 // The boundary lanes leave out the x-shifted diagonal that would cross into the
 // other half and record their own boundary value in `edge`.
-template <int MODE>
+template <int NH, int MODE>
 __device__ __forceinline__ void send_rows(const NC &nc, float c4, float *ubase, float *dbase, bool UP,
                                           bool DN, float *edge, int lane) {
-    const bool l0 = lane == 0, l31 = lane == 31;
+    constexpr int XSLOT = HG<NH>::XSLOT;
+    const bool l0 = lane == 0 && NH == 2, l31 = lane == 31 && NH == 2;
     if (MODE == MID) {
         float u0[VXH], u1[VXH], d0[VXH], d1[VXH];
         {  // k = 0: c = (0,1,0), -c = (0,-1,0)
@@ -65,12 +75,12 @@ __device__ __forceinline__ void send_rows(const NC &nc, float c4, float *ubase, 
 #pragma unroll
             for (int i = 0; i < VXH; ++i) pair_g(nc, i, ypair_e(nc, 1, i), true, c4, gp[i], gm[i]);
             if (UP) {
-                st_shared_if(edge + E_UP1, gp[VXH - 1], l31);
+                if (NH == 2) st_shared_if(edge + E_UP1, gp[VXH - 1], l31);
                 xshift(gp, 1, lane);
                 gp[0] = l0 ? 0.f : gp[0];
             }
             if (DN) {
-                st_shared_if(edge + E_DN1, gm[0], l0);
+                if (NH == 2) st_shared_if(edge + E_DN1, gm[0], l0);
                 xshift(gm, -1, lane);
                 gm[VXH - 1] = l31 ? 0.f : gm[VXH - 1];
             }
@@ -87,12 +97,12 @@ __device__ __forceinline__ void send_rows(const NC &nc, float c4, float *ubase, 
 #pragma unroll
             for (int i = 0; i < VXH; ++i) pair_g(nc, i, ypair_e(nc, 2, i), true, c4, gp[i], gm[i]);
             if (UP) {
-                st_shared_if(edge + E_UP2, gp[0], l0);
+                if (NH == 2) st_shared_if(edge + E_UP2, gp[0], l0);
                 xshift(gp, -1, lane);
                 gp[VXH - 1] = l31 ? 0.f : gp[VXH - 1];
             }
             if (DN) {
-                st_shared_if(edge + E_DN2, gm[VXH - 1], l31);
+                if (NH == 2) st_shared_if(edge + E_DN2, gm[VXH - 1], l31);
                 xshift(gm, 1, lane);
                 gm[0] = l0 ? 0.f : gm[0];
             }
@@ -140,15 +150,16 @@ __device__ __forceinline__ constexpr bool need_m(int mode, int cz) {
     return mode == MID || (mode == FIRST ? cz < 0 : cz > 0);
 }
 
-template <int MODE>
+template <int NH, int MODE>
 __device__ __forceinline__ void phase_a(float (&acc)[3][VXH][4], const float *stg, float *xbuf, float *ebuf,
                                         const TiledParams &p, int lane, int row, int half) {
     constexpr int PM = 0, P0 = 1, PP = 2;
+    constexpr int RL = HG<NH>::RL, XDIR = HG<NH>::XDIR;
     float *up = xbuf + half * HALF, *dn = xbuf + XDIR + half * HALF;
     {
         NC nc;
         node_consts(nc, stg + (row + 1) * RL + half * HALF, TROWS * RL, lane, p.s18);
-        float *edge = ebuf + ((row + 1) * 2 + half) * NEDGE;
+        float *edge = NH == 2 ? ebuf + ((row + 1) * 2 + half) * NEDGE : nullptr;
 #pragma unroll
         for (int i = 0; i < VXH; ++i) {
             float gp, gm;
@@ -188,37 +199,39 @@ __device__ __forceinline__ void phase_a(float (&acc)[3][VXH][4], const float *st
                 }
             }
             if (np) {
-                st_shared_if(edge + E_INP + cz + 1, eP, lane == 31);  // for the other half's lane 0
+                if (NH == 2) st_shared_if(edge + E_INP + cz + 1, eP, lane == 31);  // for the other half's lane 0
                 float rP = __shfl_sync(FULL, eP, (lane + 31) & 31);
-                rP = lane == 0 ? 0.f : rP;  // lane 0's comes from the other half (phase B)
+                if (NH == 2) rP = lane == 0 ? 0.f : rP;  // lane 0's comes from the other half (phase B)
                 dep(acc[pl<PM, P0, PP>(cz)][0], rP, 1, 0, cz);
             }
             if (nm) {
-                st_shared_if(edge + E_INM + cz + 1, eM, lane == 0);  // for the other half's lane 31
+                if (NH == 2) st_shared_if(edge + E_INM + cz + 1, eM, lane == 0);  // for the other half's lane 31
                 float rM = __shfl_sync(FULL, eM, (lane + 1) & 31);
-                rM = lane == 31 ? 0.f : rM;
+                if (NH == 2) rM = lane == 31 ? 0.f : rM;
                 dep(acc[pl<PM, P0, PP>(-cz)][VXH - 1], rM, -1, 0, -cz);
             }
         }
-        send_rows<MODE>(nc, p.c4, up + (row + 1) * RL, dn + (row - 1) * RL, row + 1 < ROWS, row > 0, edge, lane);
+        send_rows<NH, MODE>(nc, p.c4, up + (row + 1) * RL, dn + (row - 1) * RL, row + 1 < ROWS, row > 0,
+                            edge, lane);
     }
     if (row == 0) {  // bottom halo row y0-1 (staged row 0) feeds row 0
         NC hc;
         node_consts(hc, stg + half * HALF, TROWS * RL, lane, p.s18);
-        send_rows<MODE>(hc, p.c4, up, nullptr, true, false, ebuf + half * NEDGE, lane);
+        send_rows<NH, MODE>(hc, p.c4, up, nullptr, true, false, NH == 2 ? ebuf + half * NEDGE : nullptr, lane);
     } else if (row == ROWS - 1) {  // top halo row y0+8 (staged row 9) feeds row 7
         NC hc;
         node_consts(hc, stg + (TROWS - 1) * RL + half * HALF, TROWS * RL, lane, p.s18);
-        send_rows<MODE>(hc, p.c4, nullptr, dn + (ROWS - 1) * RL, false, true,
-                        ebuf + ((TROWS - 1) * 2 + half) * NEDGE, lane);
+        send_rows<NH, MODE>(hc, p.c4, nullptr, dn + (ROWS - 1) * RL, false, true,
+                            NH == 2 ? ebuf + ((TROWS - 1) * 2 + half) * NEDGE : nullptr, lane);
     }
 }
 
-template <int MODE>
+template <int NH, int MODE>
 __device__ __forceinline__ void phase_b(float (&acc)[3][VXH][4], const float *xbuf, const float *ebuf,
                                         float *out, const TiledParams &p, int lane, int row, int half,
                                         int col, int zfin) {
     constexpr int PM = 0, P0 = 1, PP = 2;
+    constexpr int RL = HG<NH>::RL, XDIR = HG<NH>::XDIR, XSLOT = HG<NH>::XSLOT;
     const float *up = xbuf + row * RL + half * HALF, *dn = xbuf + XDIR + row * RL + half * HALF;
     const int ph = 1 - half;
     const float *e_own = ebuf + ((row + 1) * 2 + ph) * NEDGE;  // partner half, same row
@@ -226,8 +239,9 @@ __device__ __forceinline__ void phase_b(float (&acc)[3][VXH][4], const float *xb
     const float *e_dn = ebuf + ((row + 2) * 2 + ph) * NEDGE;   // partner half, row above
     float o[VXH];
     if (MODE == MID) {
-        const float u1 = e_up[E_UP1], u2 = e_up[E_UP2], d1 = e_dn[E_DN1], d2 = e_dn[E_DN2];
-        const bool l0 = lane == 0, l31 = lane == 31;
+        const float u1 = NH == 2 ? e_up[E_UP1] : 0.f, u2 = NH == 2 ? e_up[E_UP2] : 0.f;
+        const float d1 = NH == 2 ? e_dn[E_DN1] : 0.f, d2 = NH == 2 ? e_dn[E_DN2] : 0.f;
+        const bool l0 = lane == 0 && NH == 2, l31 = lane == 31 && NH == 2;
         ld_slot(up, o, lane);  // from below, c_z = 0: d, +jy
         o[0] += l0 ? u1 : 0.f;
         o[VXH - 1] += l31 ? u2 : 0.f;
@@ -256,15 +270,17 @@ __device__ __forceinline__ void phase_b(float (&acc)[3][VXH][4], const float *xb
         for (int i = 0; i < VXH; ++i) acc[P0][i][1] += o[i];
     }
     // in-row values from the other half's boundary lanes
+    if (NH == 2) {
 #pragma unroll
-    for (int cz = -1; cz <= 1; ++cz) {
-        if (need_p(MODE, cz)) {
-            const float v = e_own[E_INP + cz + 1];
-            dep(acc[pl<PM, P0, PP>(cz)][0], lane == 0 ? v : 0.f, 1, 0, cz);
-        }
-        if (need_m(MODE, cz)) {
-            const float v = e_own[E_INM + cz + 1];
-            dep(acc[pl<PM, P0, PP>(-cz)][VXH - 1], lane == 31 ? v : 0.f, -1, 0, -cz);
+        for (int cz = -1; cz <= 1; ++cz) {
+            if (need_p(MODE, cz)) {
+                const float v = e_own[E_INP + cz + 1];
+                dep(acc[pl<PM, P0, PP>(cz)][0], lane == 0 ? v : 0.f, 1, 0, cz);
+            }
+            if (need_m(MODE, cz)) {
+                const float v = e_own[E_INM + cz + 1];
+                dep(acc[pl<PM, P0, PP>(-cz)][VXH - 1], lane == 31 ? v : 0.f, -1, 0, -cz);
+            }
         }
     }
     if (MODE != LAST) {  // c_z = +1 arrivals for the plane ahead (jz implied by d)
@@ -317,8 +333,11 @@ __device__ __forceinline__ void phase_b(float (&acc)[3][VXH][4], const float *xb
     }
 }
 
+template <int NH>
 __device__ __forceinline__ void issue_plane(const float *in, const TiledParams &p, int col, int z,
                                             float *stage, uint64_t *bar) {
+    constexpr int RL = HG<NH>::RL;
+    constexpr uint32_t TX = HG<NH>::TX;
     const int zl = z < 0 ? z + p.nz : (z >= p.nz ? z - p.nz : z);
     const int y0 = col * ROWS;
     const long long plane = (long long)p.nx * p.ny;
@@ -352,15 +371,17 @@ __device__ __forceinline__ void rotate(float (&acc)[3][VXH][4]) {
     }
 }
 
-__global__ void __launch_bounds__(NTH, 1) k_d3q19_half(const float *__restrict__ in, float *__restrict__ out,
-                                                       TiledParams p) {
+template <int NH>
+__global__ void __launch_bounds__(HG<NH>::NTH, 2 / NH) k_d3q19_half(const float *__restrict__ in,
+                                                                   float *__restrict__ out, TiledParams p) {
+    constexpr int XBUF = HG<NH>::XBUF, STAGE = HG<NH>::STAGE, EBUF = HG<NH>::EBUF;
     extern __shared__ float4 smem4[];
     float *xs = reinterpret_cast<float *>(smem4);
     float *stg = xs + 2 * XBUF;
     float *eb = stg + 2 * STAGE;
     uint64_t *bars = reinterpret_cast<uint64_t *>(eb + 2 * EBUF);
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    const int row = warp >> 1, half = warp & 1;
+    const int row = NH == 2 ? warp >> 1 : warp, half = NH == 2 ? (warp & 1) : 0;
     if ((int)blockIdx.x >= p.nitems) return;  // uniform per CTA
 
     if (threadIdx.x == 0) {
@@ -374,7 +395,7 @@ __global__ void __launch_bounds__(NTH, 1) k_d3q19_half(const float *__restrict__
     TaskIter pf = it;
     int issued = 0;
     for (int k = 0; k < 2 && pf.valid(); ++k) {
-        if (threadIdx.x == 0) issue_plane(in, p, pf.col, pf.pz, stg + k * STAGE, &bars[k]);
+        if (threadIdx.x == 0) issue_plane<NH>(in, p, pf.col, pf.pz, stg + k * STAGE, &bars[k]);
         ++issued;
         pf.next();
     }
@@ -396,7 +417,7 @@ __global__ void __launch_bounds__(NTH, 1) k_d3q19_half(const float *__restrict__
         const int mode = it.mode();
         if (ok) {
             if (mode == MID) {
-                phase_a<MID>(acc, stage, xbuf, ebuf, p, lane, row, half);
+                phase_a<NH, MID>(acc, stage, xbuf, ebuf, p, lane, row, half);
             } else if (mode == FIRST) {
 #pragma unroll
                 for (int a = 0; a < 3; ++a)
@@ -404,9 +425,9 @@ __global__ void __launch_bounds__(NTH, 1) k_d3q19_half(const float *__restrict__
                     for (int i = 0; i < VXH; ++i)
 #pragma unroll
                         for (int c = 0; c < 4; ++c) acc[a][i][c] = 0.f;
-                phase_a<FIRST>(acc, stage, xbuf, ebuf, p, lane, row, half);
+                phase_a<NH, FIRST>(acc, stage, xbuf, ebuf, p, lane, row, half);
             } else {
-                phase_a<LAST>(acc, stage, xbuf, ebuf, p, lane, row, half);
+                phase_a<NH, LAST>(acc, stage, xbuf, ebuf, p, lane, row, half);
             }
         }
         if (__syncthreads_or(ok ? 0 : 1)) {
@@ -419,19 +440,19 @@ __global__ void __launch_bounds__(NTH, 1) k_d3q19_half(const float *__restrict__
         if (pf.valid()) {
             if (threadIdx.x == 0) {
                 asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-                issue_plane(in, p, pf.col, pf.pz, stg + s * STAGE, &bars[s]);
+                issue_plane<NH>(in, p, pf.col, pf.pz, stg + s * STAGE, &bars[s]);
             }
             ++issued;
             pf.next();
         }
         if (mode == MID) {
-            phase_b<MID>(acc, xbuf, ebuf, out, p, lane, row, half, it.col, it.pz > it.za ? it.pz - 1 : -1);
+            phase_b<NH, MID>(acc, xbuf, ebuf, out, p, lane, row, half, it.col, it.pz > it.za ? it.pz - 1 : -1);
             rotate(acc);
         } else if (mode == FIRST) {
-            phase_b<FIRST>(acc, xbuf, ebuf, out, p, lane, row, half, it.col, -1);
+            phase_b<NH, FIRST>(acc, xbuf, ebuf, out, p, lane, row, half, it.col, -1);
             rotate(acc);
         } else {
-            phase_b<LAST>(acc, xbuf, ebuf, out, p, lane, row, half, it.col, it.zb - 1);
+            phase_b<NH, LAST>(acc, xbuf, ebuf, out, p, lane, row, half, it.col, it.zb - 1);
 #pragma unroll
             for (int a = 1; a < 3; ++a)
 #pragma unroll
@@ -443,13 +464,15 @@ __global__ void __launch_bounds__(NTH, 1) k_d3q19_half(const float *__restrict__
     }
 }
 
+template <int NH>
 cudaError_t prepare(int *ctas) {
     static int state = 0, nctas = 0;
     if (state == 0) {
-        cudaError_t e = cudaFuncSetAttribute(k_d3q19_half, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)BYTES);
+        cudaError_t e = cudaFuncSetAttribute(k_d3q19_half<NH>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                             (int)HG<NH>::BYTES);
         if (e != cudaSuccess) return e;
         int nb = 0, dev = 0, sms = 0;
-        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_d3q19_half, NTH, BYTES);
+        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_d3q19_half<NH>, HG<NH>::NTH, HG<NH>::BYTES);
         if (e != cudaSuccess) return e;
         e = cudaGetDevice(&dev);
         if (e != cudaSuccess) return e;
@@ -482,18 +505,17 @@ int half_chunk_planes(int ycols, int nz, int ctas) {
 
 bool half_supported(int Q, int storage, const StepParams &p) {
     if (Q != 19 || storage != STORE_F32 || p.bc != BC_PERIODIC) return false;
-    if (p.nx != RL || p.ny % ROWS != 0 || p.ny < ROWS || p.nz < 1) return false;
+    if ((p.nx != 128 && p.nx != 256) || p.ny % ROWS != 0 || p.ny < ROWS || p.nz < 1) return false;
     if (p.fstride % 4 != 0 || !p.err) return false;
     int dev = 0;
     if (cudaGetDevice(&dev) != cudaSuccess) return false;
-    return prepare(nullptr) == cudaSuccess;
+    return (p.nx == 256 ? prepare<2>(nullptr) : prepare<1>(nullptr)) == cudaSuccess;
 }
 
-cudaError_t launch_step_half(int Q, int storage, const void *in, void *out, const StepParams &sp,
-                             cudaStream_t st) {
-    if (!half_supported(Q, storage, sp)) return cudaErrorNotSupported;
+template <int NH>
+static cudaError_t launch_nh(const void *in, void *out, const StepParams &sp, cudaStream_t st) {
     int ctas = 0;
-    cudaError_t e = prepare(&ctas);
+    cudaError_t e = prepare<NH>(&ctas);
     if (e != cudaSuccess) return e;
     TiledParams p;
     p.nx = sp.nx;
@@ -509,8 +531,14 @@ cudaError_t launch_step_half(int Q, int storage, const void *in, void *out, cons
     p.a_s = (float)((double)sp.a / nu);
     p.err = sp.err;
     const int grid = ctas < p.nitems ? ctas : p.nitems;
-    k_d3q19_half<<<(unsigned)grid, NTH, BYTES, st>>>((const float *)in, (float *)out, p);
+    k_d3q19_half<NH><<<(unsigned)grid, HG<NH>::NTH, HG<NH>::BYTES, st>>>((const float *)in, (float *)out, p);
     return cudaGetLastError();
+}
+
+cudaError_t launch_step_half(int Q, int storage, const void *in, void *out, const StepParams &sp,
+                             cudaStream_t st) {
+    if (!half_supported(Q, storage, sp)) return cudaErrorNotSupported;
+    return sp.nx == 256 ? launch_nh<2>(in, out, sp, st) : launch_nh<1>(in, out, sp, st);
 }
 
 }  // namespace lwacm

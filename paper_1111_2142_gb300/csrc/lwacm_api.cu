@@ -172,7 +172,7 @@ bool choose_kernel(lwacm_ctx *c) {
         case 2: c->kernel = t_ok ? 2 : 1; ok = t_ok || !dev; break;
         case 3: c->kernel = z_ok ? 3 : 1; ok = z_ok || !dev; break;
         case 5: c->kernel = h_ok ? 5 : 1; ok = h_ok || !dev; break;
-        default: c->kernel = z_ok ? 3 : (t_ok ? 2 : 1); break;
+        default: c->kernel = h_ok ? 5 : (z_ok ? 3 : (t_ok ? 2 : 1)); break;
     }
     static const char *gname[2] = {"generic_d2q9", "generic_d3q19"};
     c->kname = c->kernel == 2   ? tiled_name(c->Q)

@@ -89,10 +89,9 @@ def test_d3q19_ragged(lw, kernel, shape):
                                    (2, 8, 256), (37, 8, 128), (300, 16, 128), (41, 24, 256)])
 def test_d3q19_tiled_kernel(lw, kernel, shape):
     """The row-tiled D3Q19 kernels (rows of 128 / 256 nodes, ny a multiple of 8),
-    forced on: the TMA persistent kernel (2) and the register-prefetch z-march
-    kernel (3); shapes cover runs that cross columns, one plane, ragged chunks."""
-    if kernel == 5 and shape[2] != 256:
-        pytest.skip("the half-row kernel needs nx = 256")
+    forced on: the TMA persistent kernel (2), the register-prefetch z-march
+    kernel (3) and the half-row TMA kernel (5: two warps per 256-node row, one per
+    128-node row); shapes cover runs that cross columns, one plane, ragged chunks."""
     f = inputs.smooth_random(shape, seed=12, u_amp=0.05, d_amp=0.01)
     got, name = run_gpu(lw, 19, f, 0.01, 25, kernel=kernel)
     assert name.startswith({2: "tiled", 3: "zmarch", 5: "half"}[kernel])
