@@ -35,6 +35,7 @@ if ROOT not in sys.path:
 N_SIDE = 256
 U0, NU = 0.02, 0.005
 BYTES_PER_NODE = 32  # FP32 (d, ux, uy, uz): read once, written once
+FLOPS_PER_NODE = 146  # FP32 operations of the moment form per D3Q19 node update (FMA = 2)
 WORKLOAD = "D3Q19 3D Taylor-Green 256^3 periodic, u0=0.02, nu=0.005, FP32 fields (d=rho-1, ux, uy, uz)"
 METRIC = "GLUPS, D3Q19 256^3 FP32 LW-ACM update"
 
@@ -365,6 +366,13 @@ def run_gpu(args):
         except Exception:
             traffic = None
 
+    # the FP32 compute roof, measured on this GPU (register-only FMA chains)
+    try:
+        fp32_tflops, fp32_ms = lw.measure_fp32_peak(4096, sim.stream)
+    except Exception:
+        fp32_tflops, fp32_ms = None, None
+    fp32_achieved = FLOPS_PER_NODE * N / (ms_step * 1e-3) / 1e12
+
     # end-to-end through the C ABI with pinned host buffers
     e2e_steps = max(3, min(args.e2e_steps, args.steps))
     host_in = [torch.from_numpy(a.astype(np.float32)).pin_memory() for a in f]
@@ -406,7 +414,11 @@ def run_gpu(args):
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s",
                      "frac": achieved / hbm, "traffic": traffic,
                      "peak_source": f"{src} hbm_gbs (copy test)",
-                     "bytes_per_node": BYTES_PER_NODE},
+                     "bytes_per_node": BYTES_PER_NODE,
+                     "fp32": {"flops_per_node": FLOPS_PER_NODE, "achieved": fp32_achieved,
+                              "peak": fp32_tflops, "unit": "TFLOP/s",
+                              "frac": fp32_achieved / fp32_tflops if fp32_tflops else None,
+                              "peak_source": "measured: FMA-chain kernel (lwacm_measure_fp32_peak)"}},
         "e2e": {"value": e2e_glups, "unit": "GLUPS", "h2d_bytes_per_step": field_bytes,
                 "d2h_bytes_per_step": field_bytes, "steps": e2e_steps},
         "gpu_launches": args.steps,

@@ -66,6 +66,7 @@ def load():
         "lwacm_diagnostics_noalloc": [vp, vp, vp, vp, ll, i, vp, vp],
         "lwacm_batch_create": [i, i, P(i), P(i), P(i), P(d), i, P(vp)],
         "lwacm_batch_offsets": [vp, P(ll)],
+        "lwacm_measure_fp32_peak": [ll, vp, P(d), P(d)],
     }
     for name, args in sig.items():
         fn = getattr(lib, name)
@@ -341,6 +342,21 @@ class LwacmBatch(Lwacm):
             lo, hi = self.offsets[b], self.offsets[b + 1]
             out.append(tuple(p[lo:hi].reshape(self.domain_shape(b)) for p in packed))
         return out
+
+
+def measure_fp32_peak(iters=4096, stream=None):
+    """Measured FP32 FMA throughput of the current device: (TFLOP/s, ms of the
+    timed launch). Runs the library's register-only FMA-chain kernel on `stream`
+    (a torch.cuda.Stream, or the current stream) and waits for it."""
+    torch = _torch()
+    lib = load()
+    st = stream if stream is not None else torch.cuda.current_stream()
+    tf, ms = ctypes.c_double(), ctypes.c_double()
+    rc = lib.lwacm_measure_fp32_peak(int(iters), ctypes.c_void_p(st.cuda_stream), ctypes.byref(tf),
+                                     ctypes.byref(ms))
+    if rc != OK:
+        raise LwacmError(rc, "lwacm_measure_fp32_peak failed")
+    return tf.value, ms.value
 
 
 def _make_function():

@@ -97,3 +97,13 @@ def test_null_arguments(lib):
     assert lib.lwacm_create(9, 8, 8, 1, 0.01, 0, None) == lw.E_ARG
     assert lib.lwacm_workspace_bytes(None, None) == lw.E_ARG
     assert lib.lwacm_step(None, 1) == lw.E_ARG
+
+
+def test_measure_fp32_peak_validation(lib):
+    """The FMA-throughput probe rejects bad arguments before touching the device."""
+    from paper_1111_2142_gb300 import lwacm as lw
+    tf, ms = ctypes.c_double(), ctypes.c_double()
+    assert lib.lwacm_measure_fp32_peak(0, None, ctypes.byref(tf), ctypes.byref(ms)) == lw.E_ARG
+    assert lib.lwacm_measure_fp32_peak((1 << 20) + 1, None, ctypes.byref(tf), ctypes.byref(ms)) == lw.E_ARG
+    assert lib.lwacm_measure_fp32_peak(16, None, None, ctypes.byref(ms)) == lw.E_ARG
+    assert lib.lwacm_measure_fp32_peak(16, None, ctypes.byref(tf), None) == lw.E_ARG
