@@ -246,23 +246,27 @@ int lwo_max_threads(void) {
 
 static double omega_of_nu(double nu) { return 2.0 / (6.0 * nu + 1.0); } /* Eq. viscosity2 */
 
-/* Advance (d,ux,uy[,uz]) in place by nsteps of Eq. ACM2.0. rho0 enters only the
- * moving-wall term. lid / force may be NULL (zero). Returns 0 or a negative code. */
-int lwo_step(int Q, int nx, int ny, int nz, double nu, int bc, double rho0, const double *lid,
-             const double *force, long nsteps, double *d, double *ux, double *uy, double *uz,
-             int nthreads) {
+/* Advance (d,ux,uy[,uz]) in place by nsteps of Eq. ACM2.0, with the external
+ * acceleration g of Eq. force either one constant vector (force, or NULL) or, when
+ * gx is not NULL, a per-node field (gx, gy[, gz]) held fixed over the nsteps. */
+static int run_steps(int Q, int nx, int ny, int nz, double nu, int bc, double rho0,
+                     const double *lid, const double *force, const double *gx, const double *gy,
+                     const double *gz, long nsteps, double *d, double *ux, double *uy, double *uz,
+                     int nthreads) {
     lwo_lattice L;
     lwo_geom G;
     if (make_lattice(Q, &L)) return -1;
     if (make_geom(&L, nx, ny, nz, bc, &G)) return -2;
     if (!(nu > 0.0)) return -4;
     if (Q == 19 && !uz) return -5;
+    if (gx && !gy) return -3;
     set_threads(nthreads);
     const double omega = omega_of_nu(nu);
     const double zero[3] = {0.0, 0.0, 0.0};
     const double *lid_ = lid ? lid : zero;
     const double *frc = force ? force : zero;
-    const int has_force = force && (force[0] != 0.0 || force[1] != 0.0 || force[2] != 0.0);
+    const int has_force =
+        gx != NULL || (force && (force[0] != 0.0 || force[1] != 0.0 || force[2] != 0.0));
     const long N = (long)nx * ny * nz;
     const int nf = (Q == 19) ? 4 : 3;
     double *buf = (double *)malloc(sizeof(double) * N * nf);
@@ -276,8 +280,15 @@ int lwo_step(int Q, int nx, int ny, int nz, double nu, int bc, double rho0, cons
                 for (int xx = 0; xx < nx; ++xx) {
                     const int x[3] = {xx, y, z};
                     const long k = ((long)z * ny + y) * nx + xx;
-                    double r, u[3];
-                    node_update(&L, &G, omega, rho0, lid_, frc, has_force, x, src[0], src[1],
+                    double r, u[3], gk[3];
+                    const double *g = frc;
+                    if (gx) {
+                        gk[0] = gx[k];
+                        gk[1] = gy[k];
+                        gk[2] = gz ? gz[k] : 0.0;
+                        g = gk;
+                    }
+                    node_update(&L, &G, omega, rho0, lid_, g, has_force, x, src[0], src[1],
                                 src[2], src[3], &r, u);
                     dst[0][k] = r - 1.0;
                     dst[1][k] = u[0];
@@ -298,7 +309,27 @@ int lwo_step(int Q, int nx, int ny, int nz, double nu, int bc, double rho0, cons
     return 0;
 }
 
-/* Lattice tables for tests: c (Q x 3), w (Q), bb (Q). */
+/* Advance (d,ux,uy[,uz]) in place by nsteps of Eq. ACM2.0. rho0 enters only the
+ * moving-wall term. lid / force may be NULL (zero). Returns 0 or a negative code. */
+int lwo_step(int Q, int nx, int ny, int nz, double nu, int bc, double rho0, const double *lid,
+             const double *force, long nsteps, double *d, double *ux, double *uy, double *uz,
+             int nthreads) {
+    return run_steps(Q, nx, ny, nz, nu, bc, rho0, lid, force, NULL, NULL, NULL, nsteps, d, ux, uy,
+                     uz, nthreads);
+}
+
+/* As lwo_step, with a per-node acceleration field g(x) = (gx, gy[, gz]) (Eq. force
+ * written for a space-dependent g), held fixed over the nsteps; a time-dependent
+ * g(x,t) is applied by one call per step with g evaluated at time t. gz may be
+ * NULL (zero). */
+int lwo_step_force_field(int Q, int nx, int ny, int nz, double nu, int bc, double rho0,
+                         const double *lid, const double *gx, const double *gy, const double *gz,
+                         long nsteps, double *d, double *ux, double *uy, double *uz, int nthreads) {
+    if (!gx || !gy) return -3;
+    return run_steps(Q, nx, ny, nz, nu, bc, rho0, lid, NULL, gx, gy, gz, nsteps, d, ux, uy, uz,
+                     nthreads);
+}
+
 int lwo_lattice_tables(int Q, int *c, double *w, int *bb) {
     lwo_lattice L;
     if (make_lattice(Q, &L)) return -1;

@@ -67,6 +67,7 @@ def load():
         "lwacm_batch_create": [i, i, P(i), P(i), P(i), P(d), i, P(vp)],
         "lwacm_batch_offsets": [vp, P(ll)],
         "lwacm_measure_fp32_peak": [ll, vp, P(d), P(d)],
+        "lwacm_selftest_reciprocal": [vp, vp, ll, vp],
     }
     for name, args in sig.items():
         fn = getattr(lib, name)

@@ -107,3 +107,9 @@ def test_measure_fp32_peak_validation(lib):
     assert lib.lwacm_measure_fp32_peak((1 << 20) + 1, None, ctypes.byref(tf), ctypes.byref(ms)) == lw.E_ARG
     assert lib.lwacm_measure_fp32_peak(16, None, None, ctypes.byref(ms)) == lw.E_ARG
     assert lib.lwacm_measure_fp32_peak(16, None, ctypes.byref(tf), None) == lw.E_ARG
+
+
+def test_selftest_reciprocal_validation(lib):
+    from paper_1111_2142_gb300 import lwacm as lw
+    assert lib.lwacm_selftest_reciprocal(None, None, 4, None) == lw.E_ARG
+    assert lib.lwacm_selftest_reciprocal(ctypes.c_void_p(16), ctypes.c_void_p(16), 0, None) == lw.E_ARG
