@@ -90,17 +90,21 @@ enum {
     LWACM_OPT_KERNEL = 9,  /* interior kernel: 0 = automatic choice (default),
                               1 = generic gather kernel, 2 = D3Q19 TMA row-tiled kernel,
                               3 = D3Q19 register-prefetch z-march kernel, 5 = D3Q19 half-row
-                              TMA kernel (2 and 3 need a periodic domain with nx in
-                              {128, 256}, 5 needs nx = 256; all need ny % 8 == 0 and FP32
-                              storage: LWACM_E_UNSUPPORTED otherwise) */
+                              TMA kernel (2, 3 and 5 need a periodic domain without
+                              forcing, nx in {128, 256}, ny % 8 == 0 and FP32 storage:
+                              LWACM_E_UNSUPPORTED otherwise). The automatic choice takes
+                              5, else 3, else 2, else 1. */
     LWACM_OPT_BATCH_MODE = 10, /* batched contexts: 0 = one launch per step, replayed
                                   from CUDA graphs (default); 1 = one persistent
                                   cooperative launch per lwacm_step call, with a
                                   bounded grid-wide barrier between steps */
-    LWACM_OPT_TEST_WITHHOLD = 11 /* batched contexts, tests only: in persistent mode the
-                                    first CTA leaves without arriving at the barrier after
-                                    this step (-1 = never), so the other CTAs' bounded
-                                    waits run out and lwacm_sync reports LWACM_E_TIMEOUT */
+    LWACM_OPT_TEST_WITHHOLD = 11, /* batched contexts, tests only: in persistent mode the
+                                     first CTA leaves without arriving at the barrier after
+                                     this step (-1 = never), so the other CTAs' bounded
+                                     waits run out and lwacm_sync reports LWACM_E_TIMEOUT */
+    LWACM_OPT_FORCE_FIELD = 12    /* 1 = reserve room in the workspace for a per-node
+                                     acceleration field (lwacm_set_force_field); only
+                                     before lwacm_bind; single-domain contexts only */
 };
 
 /* Create a single-domain context.
@@ -147,6 +151,24 @@ lwacm_status lwacm_bind(lwacm_ctx *ctx, void *dev_workspace, size_t bytes, void 
  * buffers must stay valid until the stream reaches this point. */
 lwacm_status lwacm_set_fields(lwacm_ctx *ctx, const void *d, const void *ux, const void *uy,
                               const void *uz, int dtype, int where);
+
+/* Per-node body acceleration g(x) of Eq. force (Section 2.1), for a force that
+ * varies in space (and, by calling this between steps, in time: Eq. force uses g
+ * at the time level t of the state it updates, so set g(x, t) before the step
+ * from t to t+1). gx, gy (and gz for D3Q19; NULL for D2Q9) are arrays of
+ * nx*ny*nz elements of type dtype (LWACM_F32 or LWACM_F64) on the device or
+ * host (where); they are copied (FP64 rounded once to FP32) into the workspace
+ * room reserved by LWACM_OPT_FORCE_FIELD and used by every following step until
+ * the next call. The step adds rho(x,t) g(x) to the momentum, on top of any
+ * constant LWACM_OPT_FORCE_* vector. All three pointers NULL switches the field
+ * off. Stream-ordered on the bound stream (host buffers must stay valid until
+ * the stream reaches this point; FP32 host arrays should be pinned). The row-tiled
+ * kernels have no forcing term, so a context with forcing runs the generic
+ * kernel. The adjoint (lwacm_forward_record) refuses a context whose field is on
+ * (LWACM_E_UNSUPPORTED).
+ * Errors: LWACM_E_STATE (nothing reserved, or not bound), LWACM_E_ARG. */
+lwacm_status lwacm_set_force_field(lwacm_ctx *ctx, const void *gx, const void *gy, const void *gz,
+                                   int dtype, int where);
 
 /* Advance the state by n >= 0 time steps of Eq. ACM2.0 (plus the wall pass of
  * Eqs. ACM2.0cccbb2 / ACM2.0ccccbb and the forcing of Eq. force when enabled).

@@ -17,7 +17,9 @@
  *   - omega from nu by Eq. viscosity2, nu = (1/omega - 1/2)/3;
  *   - half-way link-wise walls, Eq. ACM2.0cccbb2, with the moving-wall term of
  *     Eq. ACM2.0ccccbb (Section 2.6, rules of the 2D cavity in Section 2.6.1);
- *   - external forcing, Eq. force;
+ *   - external forcing, Eq. force, with a constant acceleration or a per-node
+ *     field g(x) (lwo_step_force_field; a time-dependent g is applied by one call
+ *     per step);
  *   - an equilibrium-initialised BGK lattice Boltzmann comparator (the LKS limit
  *     omega = 1 named in Section 2.2);
  *   - the D2Q9 finite-difference formulas Eqs. FDjx, FDjy, FDpressure (Appendix C);

@@ -44,6 +44,7 @@ __device__ __forceinline__ void tile_update(const T *__restrict__ in, T *__restr
     p.a = dm.a;
     p.wallc = 0.f;
     p.has_force = 0;
+    p.gfield = nullptr;
     p.lid_axis = 0;
     p.err = nullptr;
     for (int c = 0; c < 3; ++c) {

@@ -505,6 +505,7 @@ int half_chunk_planes(int ycols, int nz, int ctas) {
 
 bool half_supported(int Q, int storage, const StepParams &p) {
     if (Q != 19 || storage != STORE_F32 || p.bc != BC_PERIODIC) return false;
+    if (p.has_force || p.gfield) return false;  // no forcing term in this kernel
     if ((p.nx != 128 && p.nx != 256) || p.ny % ROWS != 0 || p.ny < ROWS || p.nz < 1) return false;
     if (p.fstride % 4 != 0 || !p.err) return false;
     int dev = 0;

@@ -36,6 +36,9 @@ struct lwacm_ctx {
     char *ws = nullptr;
     size_t ws_bytes = 0;
     size_t off_buf[2] = {0, 0}, off_stage = 0, off_partial = 0, off_diag = 0, off_err = 0, total = 0;
+    // per-node force field (LWACM_OPT_FORCE_FIELD): D FP32 fields in the workspace
+    bool ff_reserved = false, ff_active = false;
+    size_t off_ff = 0;
     cudaStream_t stream = nullptr;
     bool bound = false, has_fields = false;
     int cur = 0;
@@ -99,6 +102,10 @@ void layout(lwacm_ctx *c) {
     off = align_up(off + 16 * 8, kAlign);
     c->off_err = off;
     off = align_up(off + 16, kAlign);
+    if (c->ff_reserved) {
+        c->off_ff = off;
+        off = align_up(off + (size_t)c->Nal * 4 * c->D, kAlign);
+    }
     if (c->nbatch) {
         c->off_doms = off;
         off = align_up(off + sizeof(BatchDomain) * c->doms.size(), kAlign);
@@ -129,6 +136,7 @@ StepParams params(const lwacm_ctx *c) {
         p.force[a] = (float)c->force[a];
     }
     p.has_force = (c->force[0] != 0 || c->force[1] != 0 || c->force[2] != 0) ? 1 : 0;
+    p.gfield = (c->ff_active && c->ws) ? (const float *)(c->ws + c->off_ff) : nullptr;
     p.err = c->ws ? (int *)(c->ws + c->off_err) : nullptr;
     p.walled[0] = p.walled[1] = p.walled[2] = 0;
     p.lid_axis = c->D - 1;
@@ -442,6 +450,16 @@ lwacm_status lwacm_set_option(lwacm_ctx *c, int key, double v) {
             c->batch_mode = m;
             break;
         }
+        case LWACM_OPT_FORCE_FIELD: {
+            const int r = (int)v;
+            if (r != 0 && r != 1) return fail(c, LWACM_E_ARG, "force field option must be 0 or 1");
+            if (c->nbatch) return fail(c, LWACM_E_UNSUPPORTED, "no force field in batched contexts");
+            if (c->bound) return fail(c, LWACM_E_STATE, "the force field is reserved before lwacm_bind");
+            c->ff_reserved = r != 0;
+            c->ff_active = false;
+            layout(c);
+            break;
+        }
         case LWACM_OPT_TEST_WITHHOLD:
             if (!c->nbatch) return fail(c, LWACM_E_STATE, "not a batched context");
             c->withhold = (long long)v;
@@ -521,6 +539,51 @@ lwacm_status lwacm_set_fields(lwacm_ctx *c, const void *d, const void *ux, const
     }
     c->has_fields = true;
     c->steps = 0;
+    return LWACM_OK;
+}
+
+lwacm_status lwacm_set_force_field(lwacm_ctx *c, const void *gx, const void *gy, const void *gz, int dtype,
+                                   int where) {
+    lwacm_status s = ready(c, false);
+    if (s != LWACM_OK) return s;
+    if (!c->ff_reserved) return fail(c, LWACM_E_STATE, "no force field reserved (LWACM_OPT_FORCE_FIELD before bind)");
+    if (!gx && !gy && !gz) {
+        if (c->ff_active) {
+            c->ff_active = false;
+            choose_kernel(c);
+            drop_graphs(c);
+        }
+        return LWACM_OK;
+    }
+    if (!gx || !gy || (c->Q == 19 && !gz) || (c->Q == 9 && gz))
+        return fail(c, LWACM_E_ARG, "force field pointers: gx, gy required; gz iff D3Q19");
+    if (dtype != LWACM_F32 && dtype != LWACM_F64) return fail(c, LWACM_E_ARG, "dtype must be F32 or F64");
+    if (where != LWACM_DEVICE && where != LWACM_HOST) return fail(c, LWACM_E_ARG, "bad location");
+    const void *src[3] = {gx, gy, gz};
+    const size_t sb = dtype == LWACM_F64 ? 8 : 4;
+    const size_t nbytes = (size_t)c->N * sb;
+    for (int a = 0; a < c->D; ++a) {
+        char *dst = c->ws + c->off_ff + (size_t)a * c->Nal * 4;
+        if (dtype == LWACM_F32) {
+            CK(c, cudaMemcpyAsync(dst, src[a], nbytes,
+                                  where == LWACM_HOST ? cudaMemcpyHostToDevice : cudaMemcpyDeviceToDevice,
+                                  c->stream),
+               "force field copy");
+            continue;
+        }
+        const void *dsrc = src[a];
+        if (where == LWACM_HOST) {
+            CK(c, cudaMemcpyAsync(c->ws + c->off_stage, src[a], nbytes, cudaMemcpyHostToDevice, c->stream),
+               "H2D stage");
+            dsrc = c->ws + c->off_stage;
+        }
+        CK(c, launch_convert_in(STORE_F32, LWACM_F64, dsrc, dst, c->N, c->stream), "force field convert");
+    }
+    if (!c->ff_active) {
+        c->ff_active = true;
+        choose_kernel(c);
+        drop_graphs(c);
+    }
     return LWACM_OK;
 }
 
@@ -637,6 +700,7 @@ lwacm_status lwacm_forward_record(lwacm_ctx *c, long long T, int stride, void *w
     if (((uintptr_t)ws) % kAlign) return fail(c, LWACM_E_ARG, "adjoint workspace not 256-byte aligned");
     if (c->storage != LWACM_F32 || c->bc != LWACM_BC_PERIODIC || c->nbatch)
         return fail(c, LWACM_E_UNSUPPORTED, "the adjoint needs one periodic domain with FP32 storage");
+    if (c->ff_active) return fail(c, LWACM_E_UNSUPPORTED, "the adjoint does not take a force field");
     const AdjLayout L = adj_layout(c, T, stride);
     if (bytes < L.bytes) return fail(c, LWACM_E_NOMEM, "adjoint workspace smaller than lwacm_adjoint_workspace_bytes");
     c->adj = (char *)ws;

@@ -88,6 +88,7 @@ struct StepParams {
     float lid[3];       // u_w of the moving wall
     float force[3];     // g of Eq. force
     int has_force;
+    const float *gfield;  // per-node g of Eq. force (D FP32 fields, stride fstride) or null
     int walled[3];      // 1 = half-way walls on both ends of this axis
     int lid_axis;       // axis whose top wall moves with the lid velocity
     int *err;           // device error word (bounded waits that gave up set it)

@@ -66,6 +66,11 @@ __device__ __forceinline__ void node_update(const T *__restrict__ in, T *__restr
         jy = fmaf(rx, p.force[1], jy);
         jz = fmaf(rx, p.force[2], jz);
     }
+    if (p.gfield) {  // Eq. force with a space-dependent g(x,t), supplied per step
+        jx = fmaf(rx, __ldg(p.gfield + k), jx);
+        jy = fmaf(rx, __ldg(p.gfield + p.fstride + k), jy);
+        if (Q == 19) jz = fmaf(rx, __ldg(p.gfield + 2 * p.fstride + k), jz);
+    }
     const float rn = 1.f + dd;
     stf(out + k, dd);
     stf(out + p.fstride + k, jx / rn);

@@ -15,6 +15,8 @@ Workloads:
   * the batched ensemble of independent 2D domains (side lengths log-uniform,
     viscosities uniform).
   * smooth random fields for parity tests on ragged shapes.
+  * the generalized (time-periodic, forced) Taylor-Green vortex of Section 3.2:
+    its exact solution and its external acceleration, in lattice units.
 """
 from __future__ import annotations
 
@@ -141,3 +143,50 @@ def ensemble_2d(n_domains: int = 256, seed: int = 1, smin: int = 32, smax: int =
         d, ux, uy = random_divfree_2d(int(nx[b]), int(ny[b]), rms, kmin, kmax, int(seeds[b]))
         doms.append(dict(nx=int(nx[b]), ny=int(ny[b]), nu=float(nus[b]), d=d, ux=ux, uy=uy))
     return doms
+
+
+# Generalized Taylor-Green vortex (Section 3.2, Eqs. external-force and
+# exactsolution): domain [0, 2 pi]^2, periodic, drift (u0, v0) = (0.3, 0.6),
+# nu = 0.1, diffusive scaling dx = eps, dt = eps^2 (Section 2.3, Table of units).
+GTG_U0, GTG_V0, GTG_NU = 0.3, 0.6, 0.1
+
+
+def gtg_grid(n: int):
+    """Node coordinates x_i = i eps, eps = 2 pi / n, as (X, Y) of shape (n, n)."""
+    eps = 2.0 * np.pi / n
+    x = np.arange(n) * eps
+    X, Y = np.meshgrid(x, x, indexing="xy")
+    return eps, X, Y
+
+
+def gtg_exact(n: int, t: float):
+    """Exact (u, v, p) in physical units at time t on the n x n grid."""
+    _, X, Y = gtg_grid(n)
+    a, b = X - GTG_U0 * t, Y - GTG_V0 * t
+    u = GTG_U0 + np.sin(a) * np.cos(b) * np.cos(t)
+    v = GTG_V0 - np.cos(a) * np.sin(b) * np.cos(t)
+    p = 0.25 * (np.cos(2 * a) + np.cos(2 * b)) * np.cos(t) ** 2
+    return u, v, p
+
+
+def gtg_state(n: int, t: float = 0.0):
+    """Lattice fields (d, ux, uy) of the exact solution at time t: u_lattice =
+    eps u, p = rho/3 with (p - p0)/eps^2 the physical pressure, so d = 3 eps^2 p."""
+    eps = 2.0 * np.pi / n
+    u, v, p = gtg_exact(n, t)
+    return 3.0 * eps ** 2 * p, eps * u, eps * v
+
+
+def gtg_force(n: int, t: float):
+    """Lattice acceleration (gx, gy) = eps^3 g_bar(t) (Section 2.1: g = eps^3 g_bar
+    under diffusive scaling), g_bar of Eq. external-force."""
+    eps, X, Y = gtg_grid(n)
+    a, b = X - GTG_U0 * t, Y - GTG_V0 * t
+    amp = 2.0 * GTG_NU * np.cos(t) - np.sin(t)
+    return eps ** 3 * np.sin(a) * np.cos(b) * amp, -eps ** 3 * np.cos(a) * np.sin(b) * amp
+
+
+def gtg_steps(n: int, t_end: float = 60.0) -> int:
+    """Number of steps of size eps^2 nearest to t_end."""
+    eps = 2.0 * np.pi / n
+    return int(round(t_end / eps ** 2))

@@ -22,7 +22,7 @@ F32, BF16, F16, F64 = 0, 1, 2, 3
 DEVICE, HOST = 0, 1
 OPT_LID_X, OPT_LID_Y, OPT_LID_Z, OPT_FORCE_X, OPT_FORCE_Y, OPT_FORCE_Z = range(6)
 OPT_RHO0, OPT_STORAGE, OPT_GRAPH_CHUNK, OPT_KERNEL = 6, 7, 8, 9
-OPT_BATCH_MODE, OPT_TEST_WITHHOLD = 10, 11
+OPT_BATCH_MODE, OPT_TEST_WITHHOLD, OPT_FORCE_FIELD = 10, 11, 12
 
 STATUS_NAMES = {OK: "OK", E_ARG: "E_ARG", E_RANGE: "E_RANGE", E_STATE: "E_STATE",
                 E_NOMEM: "E_NOMEM", E_CUDA: "E_CUDA", E_NONFINITE: "E_NONFINITE",
@@ -68,6 +68,7 @@ def load():
         "lwacm_batch_offsets": [vp, P(ll)],
         "lwacm_measure_fp32_peak": [ll, vp, P(d), P(d)],
         "lwacm_selftest_reciprocal": [vp, vp, ll, vp],
+        "lwacm_set_force_field": [vp, vp, vp, vp, i, i],
     }
     for name, args in sig.items():
         fn = getattr(lib, name)
@@ -106,7 +107,8 @@ class Lwacm:
     """
 
     def __init__(self, lattice, nx, ny, nz=1, nu=0.01, bc=PERIODIC, *, storage=F32, lid=None,
-                 force=None, rho0=None, kernel=0, graph_chunk=None, device=None, stream=None):
+                 force=None, rho0=None, kernel=0, graph_chunk=None, device=None, stream=None,
+                 force_field=False):
         lib = load()
         self.lattice, self.nx, self.ny, self.nz = int(lattice), int(nx), int(ny), int(nz)
         self.nu, self.bc = float(nu), int(bc)
@@ -116,7 +118,8 @@ class Lwacm:
                               ctypes.byref(h))
         if st != OK:
             raise LwacmError(st, "lwacm_create")
-        self._setup(lib, h, storage, lid, force, rho0, kernel, graph_chunk, device, stream, {})
+        self._setup(lib, h, storage, lid, force, rho0, kernel, graph_chunk, device, stream,
+                    {OPT_FORCE_FIELD: 1} if force_field else {})
 
     def _setup(self, lib, h, storage, lid, force, rho0, kernel, graph_chunk, device, stream,
                extra):
@@ -203,6 +206,34 @@ class Lwacm:
             self._hold = keep  # host memory must outlive the asynchronous copy
             self.sync()
             self._hold = None
+
+    def set_force_field(self, gx, gy, gz=None):
+        """Per-node acceleration g(x) of Eq. force for the following steps (needs
+        force_field=True at construction): torch tensors (CUDA or host, float32 /
+        float64) or numpy arrays; set_force_field(None, None) switches it off."""
+        if gx is None and gy is None and gz is None:
+            self._check(self._lib.lwacm_set_force_field(self._h, None, None, None, F32, DEVICE))
+            return
+        arrs = [gx, gy] + ([gz] if self.lattice == D3Q19 else [])
+        if all(isinstance(a, np.ndarray) for a in arrs):
+            keep = [np.ascontiguousarray(a, dtype=np.float64).reshape(-1) for a in arrs]
+            dtype, where = F64, HOST
+        else:
+            torch = _torch()
+            keep = [a.contiguous().reshape(-1) for a in arrs]
+            dtype = {torch.float32: F32, torch.float64: F64}[keep[0].dtype]
+            where = DEVICE if keep[0].is_cuda else HOST
+        for a in keep:
+            assert (a.size if isinstance(a, np.ndarray) else a.numel()) == self.n_nodes
+        ptrs = [_ptr(a) for a in keep] + [None] * (3 - len(keep))
+        self._check(self._lib.lwacm_set_force_field(self._h, *ptrs, dtype, where))
+        if where == HOST:
+            self._hold = keep  # host memory must outlive the asynchronous copy
+            self.sync()
+            self._hold = None
+        else:
+            for a in keep:  # the copy runs on the library's stream
+                a.record_stream(self.stream)
 
     def step(self, n=1):
         self._check(self._lib.lwacm_step(self._h, int(n)))

@@ -113,3 +113,30 @@ def test_selftest_reciprocal_validation(lib):
     from paper_1111_2142_gb300 import lwacm as lw
     assert lib.lwacm_selftest_reciprocal(None, None, 4, None) == lw.E_ARG
     assert lib.lwacm_selftest_reciprocal(ctypes.c_void_p(16), ctypes.c_void_p(16), 0, None) == lw.E_ARG
+
+
+def test_force_field_option(lib):
+    """The force-field room is reserved before bind and grows the workspace by D
+    FP32 fields; batched contexts refuse it; setting a field needs a bound context."""
+    from paper_1111_2142_gb300 import lwacm as lw
+    st, h = _create(lib, 19, 16, 8, 4, 0.02, 0)
+    assert st == lw.OK
+    n0 = ctypes.c_size_t()
+    assert lib.lwacm_workspace_bytes(h, ctypes.byref(n0)) == lw.OK
+    assert lib.lwacm_set_option(h, lw.OPT_FORCE_FIELD, 2.0) == lw.E_ARG
+    assert lib.lwacm_set_option(h, lw.OPT_FORCE_FIELD, 1.0) == lw.OK
+    n1 = ctypes.c_size_t()
+    assert lib.lwacm_workspace_bytes(h, ctypes.byref(n1)) == lw.OK
+    assert n1.value - n0.value >= 3 * 16 * 8 * 4 * 4
+    assert lib.lwacm_set_force_field(h, None, None, None, lw.F32, lw.DEVICE) == lw.E_STATE
+    assert lib.lwacm_set_option(h, lw.OPT_FORCE_FIELD, 0.0) == lw.OK
+    n2 = ctypes.c_size_t()
+    assert lib.lwacm_workspace_bytes(h, ctypes.byref(n2)) == lw.OK and n2.value == n0.value
+    lib.lwacm_destroy(h)
+    hb = ctypes.c_void_p()
+    nx = (ctypes.c_int * 2)(8, 9)
+    ny = (ctypes.c_int * 2)(8, 7)
+    nu = (ctypes.c_double * 2)(0.01, 0.02)
+    assert lib.lwacm_batch_create(9, 2, nx, ny, None, nu, 0, ctypes.byref(hb)) == lw.OK
+    assert lib.lwacm_set_option(hb, lw.OPT_FORCE_FIELD, 1.0) == lw.E_UNSUPPORTED
+    lib.lwacm_destroy(hb)

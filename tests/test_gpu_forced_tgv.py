@@ -1,0 +1,129 @@
+"""Forcing with a space- and time-dependent acceleration (Eq. force) on the GPU:
+the generalized Taylor-Green vortex of Section 3.2 against the FP64 oracle and
+against the paper's Table gtg, and one-step parity of the force-field path.
+
+The L1 readings are the ones stated in tests/test_oracle_forced_tgv.py."""
+import os
+import sys
+
+import numpy as np
+import pytest
+
+import oracle
+from paper_1111_2142_gb300 import inputs
+
+sys.path.insert(0, os.path.dirname(__file__))
+from test_oracle_forced_tgv import gtg_l1, paper_table  # noqa: E402
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def lw():
+    import __graft_entry__
+    __graft_entry__.build()
+    from paper_1111_2142_gb300 import lwacm
+    return lwacm
+
+
+def run_gpu_gtg(lw, n):
+    """Every step: g(x, t) evaluated on the device in FP64 at the state's time
+    level, copied in with lwacm_set_force_field, then one step."""
+    import torch
+    eps = 2.0 * np.pi / n
+    sim = lw.Lwacm(lw.D2Q9, n, n, 1, inputs.GTG_NU, force_field=True)
+    sim.set_fields(*inputs.gtg_state(n, 0.0))
+    x = torch.arange(n, dtype=torch.float64, device="cuda") * eps
+    Y, X = torch.meshgrid(x, x, indexing="ij")
+    steps = inputs.gtg_steps(n)
+    with torch.cuda.stream(sim.stream):
+        for k in range(steps):
+            t = k * eps ** 2
+            a, b = X - inputs.GTG_U0 * t, Y - inputs.GTG_V0 * t
+            amp = eps ** 3 * (2.0 * inputs.GTG_NU * np.cos(t) - np.sin(t))
+            sim.set_force_field(torch.sin(a) * torch.cos(b) * amp, -torch.cos(a) * torch.sin(b) * amp)
+            sim.step(1)
+    name = sim.kernel_name
+    got = sim.get_fields()
+    sim.close()
+    return got, steps * eps ** 2, name
+
+
+def test_generalized_tgv(lw):
+    """N = 32 and 64: every node against the FP64 oracle after 1556 / 6225 steps
+    (FP32 rounding of a viscous, forced flow: bound 2e-5 of the velocity scale
+    eps (|u0| + 1)); N = 32, 64, 128: L1 errors against Table gtg. The table's
+    eps = pi/64 values fall off second order (ratio 3.1 against 3.9 one level
+    up), the oracle's do not, so at N = 128 the band is wider."""
+    paper = paper_table()
+    for n in (32, 64, 128):
+        got, t_end, name = run_gpu_gtg(lw, n)
+        assert name.startswith("generic")
+        l1 = gtg_l1(n, *got, t_end)
+        for k, nm in enumerate("uvp"):
+            r = l1[k] / paper[n][k]
+            print(f"[{name}] GTG N={n}: L1[{nm}] {l1[k]:.5e} paper {paper[n][k]:.5e} ratio {r:.3f}")
+            lo = 0.8 if n < 128 else 0.65
+            assert lo < r < 1.05, (n, nm, r)
+        if n <= 64:
+            eps = 2.0 * np.pi / n
+            d, ux, uy = inputs.gtg_state(n, 0.0)
+            for k in range(inputs.gtg_steps(n)):
+                d, ux, uy = oracle.step_force_field(9, d, ux, uy, nu=inputs.GTG_NU,
+                                                    g=inputs.gtg_force(n, k * eps ** 2))
+            uscale = eps * (1.0 + abs(inputs.GTG_V0))
+            eu = max(float(np.max(np.abs(g - r))) for g, r in zip(got[1:], (ux, uy))) / uscale
+            ed = float(np.max(np.abs(got[0] - d))) / float(np.max(np.abs(d)))
+            print(f"GTG N={n}: GPU vs oracle du/U = {eu:.2e}, dd/max|d| = {ed:.2e}")
+            assert eu < 2e-5 and ed < 2e-4
+
+
+@pytest.mark.parametrize("Q,shape,bc", [(9, (19, 23), 0), (9, (16, 21), 2), (19, (6, 8, 128), 0),
+                                        (19, (5, 7, 9), 1)])
+def test_force_field_one_step(lw, Q, shape, bc):
+    """One step with a random force field (plus a constant force) from a random
+    state: GPU == oracle to FP32 rounding, periodic, channel and cavity."""
+    rng = np.random.default_rng(11)
+    f = inputs.smooth_random(shape, seed=21, u_amp=0.04, d_amp=0.01)
+    D = 2 if Q == 9 else 3
+    g = tuple(rng.normal(size=shape) * 2e-4 for _ in range(D))
+    g0 = (1e-4, -5e-5, 2e-5) if D == 3 else (1e-4, -5e-5)
+    dims = (shape[1], shape[0], 1) if Q == 9 else (shape[2], shape[1], shape[0])
+    lid = (0.05, 0.0) if (bc == 1 and Q == 9) else ((0.05, 0.0, 0.0) if bc == 1 else None)
+    sim = lw.Lwacm(Q, *dims, 0.02, bc, force_field=True, force=g0, lid=lid)
+    sim.set_fields(*f)
+    sim.set_force_field(*g)
+    assert sim.kernel_name.startswith("generic")
+    sim.step(2)
+    got = sim.get_fields()
+    ref = f
+    gsum = tuple(gi + g0[a] for a, gi in enumerate(g))
+    for _ in range(2):
+        ref = oracle.step_force_field(Q, *ref, nu=0.02, g=gsum, bc=bc,
+                                      lid=(0.05, 0.0, 0.0) if bc == 1 else None)
+    eu = max(float(np.max(np.abs(a - b))) for a, b in zip(got[1:], ref[1:])) / 0.04
+    ed = float(np.max(np.abs(got[0] - ref[0]))) / max(float(np.max(np.abs(ref[0]))), 3 * 0.04 ** 2)
+    print(f"force field Q{Q} {shape} bc={bc}: du/U={eu:.2e} dd/d={ed:.2e}")
+    assert eu < 1e-6 and ed < 1e-5
+    # switching the field off again returns to the fastest kernel for the shape
+    sim.set_force_field(None, None, None)
+    sim.close()
+
+
+def test_forcing_keeps_tiled_kernels_off(lw):
+    """The row-tiled kernels have no forcing term: a periodic 256-wide D3Q19 box
+    with a constant force runs the generic kernel and matches the oracle."""
+    shape = (3, 8, 256)
+    f = inputs.smooth_random(shape, seed=31, u_amp=0.03, d_amp=0.01)
+    sim = lw.Lwacm(lw.D3Q19, 256, 8, 3, 0.02, force=(1e-4, 0.0, -1e-4))
+    assert sim.kernel_name.startswith("generic")
+    sim.set_fields(*f)
+    sim.step(5)
+    got = sim.get_fields()
+    ref = oracle.step(19, *f, nu=0.02, force=(1e-4, 0.0, -1e-4), nsteps=5)
+    eu = max(float(np.max(np.abs(a - b))) for a, b in zip(got[1:], ref[1:])) / 0.03
+    assert eu < 1e-5
+    sim.close()
+    plain = lw.Lwacm(lw.D3Q19, 256, 8, 3, 0.02)
+    assert plain.kernel_name.startswith("half")
+    plain.close()
