@@ -50,9 +50,11 @@ def run_gpu_gtg(lw, n):
 
 
 def test_generalized_tgv(lw):
-    """N = 32 and 64: every node against the FP64 oracle after 1556 / 6225 steps
-    (FP32 rounding of a viscous, forced flow: bound 2e-5 of the velocity scale
-    eps (|u0| + 1)); N = 32, 64, 128: L1 errors against Table gtg. The table's
+    """N = 32 and 64: every node against the FP64 oracle after 1556 / 6225 steps.
+    The FP32 run drifts from the FP64 one about linearly in the step count (the
+    forcing is re-rounded to FP32 every step and the flow never decays): measured
+    3.2e-6 and 1.5e-5 of the velocity scale eps (|v0| + 1), i.e. ~2.5e-9 per step;
+    bound 4e-9 per step. N = 32, 64, 128: L1 errors against Table gtg. The table's
     eps = pi/64 values fall off second order (ratio 3.1 against 3.9 one level
     up), the oracle's do not, so at N = 128 the band is wider."""
     paper = paper_table()
@@ -74,8 +76,9 @@ def test_generalized_tgv(lw):
             uscale = eps * (1.0 + abs(inputs.GTG_V0))
             eu = max(float(np.max(np.abs(g - r))) for g, r in zip(got[1:], (ux, uy))) / uscale
             ed = float(np.max(np.abs(got[0] - d))) / float(np.max(np.abs(d)))
-            print(f"GTG N={n}: GPU vs oracle du/U = {eu:.2e}, dd/max|d| = {ed:.2e}")
-            assert eu < 2e-5 and ed < 2e-4
+            steps = inputs.gtg_steps(n)
+            print(f"GTG N={n}: GPU vs oracle du/U = {eu:.2e}, dd/max|d| = {ed:.2e} after {steps} steps")
+            assert eu < 4e-9 * steps and ed < 4e-9 * steps
 
 
 @pytest.mark.parametrize("Q,shape,bc", [(9, (19, 23), 0), (9, (16, 21), 2), (19, (6, 8, 128), 0),
