@@ -91,9 +91,10 @@ enum {
                               1 = generic gather kernel, 2 = D3Q19 TMA row-tiled kernel,
                               3 = D3Q19 register-prefetch z-march kernel, 5 = D3Q19 half-row
                               TMA kernel (2, 3 and 5 need a periodic domain without
-                              forcing, nx in {128, 256}, ny % 8 == 0 and FP32 storage:
-                              LWACM_E_UNSUPPORTED otherwise). The automatic choice takes
-                              5, else 3, else 2, else 1. */
+                              forcing, nx in {128, 256} and ny % 8 == 0; 2 and 3 need FP32
+                              storage, 5 takes FP32, BF16 and FP16: LWACM_E_UNSUPPORTED
+                              otherwise). The automatic choice takes 5, else 3, else 2,
+                              else 1. */
     LWACM_OPT_BATCH_MODE = 10, /* batched contexts: 0 = one launch per step, replayed
                                   from CUDA graphs (default); 1 = one persistent
                                   cooperative launch per lwacm_step call, with a

@@ -36,18 +36,20 @@ constexpr int HALF = 128;              // nodes per warp row segment
 constexpr int E_INP = 0, E_INM = 3, E_UP1 = 6, E_UP2 = 7, E_DN1 = 8, E_DN2 = 9, NEDGE = 12;
 
 // NH warps share a row of nx = 128 NH nodes (NH = 1: one warp per row, its lanes
-// wrap periodically by themselves; NH = 2: two halves with the edge exchange)
-template <int NH>
+// wrap periodically by themselves; NH = 2: two halves with the edge exchange).
+// T: storage type of the fields (FP32, or BF16 / FP16 widened to FP32 on load).
+template <int NH, typename T = float>
 struct HG {
     static constexpr int NTH = ROWS * NH * 32;  // threads per CTA
     static constexpr int RL = HALF * NH;        // row length (nx)
     static constexpr int XSLOT = ROWS * RL;
     static constexpr int XDIR = NSLOT * XSLOT;
-    static constexpr int XBUF = 2 * XDIR;
-    static constexpr int STAGE = 4 * TROWS * RL;
+    static constexpr int XBUF = 2 * XDIR;        // floats
+    static constexpr int STAGE = 4 * TROWS * RL;  // elements of T
     static constexpr int EBUF = NH == 2 ? TROWS * 2 * NEDGE : 0;
-    static constexpr size_t BYTES = (2 * (size_t)XBUF + 2 * (size_t)STAGE + 2 * (size_t)EBUF) * 4 + 64;
-    static constexpr uint32_t TX = STAGE * 4;
+    static constexpr size_t BYTES =
+        (2 * (size_t)XBUF + 2 * (size_t)EBUF) * 4 + 2 * (size_t)STAGE * sizeof(T) + 64;
+    static constexpr uint32_t TX = STAGE * sizeof(T);
 };
 
 using NC = NodeConst<VXH>;
@@ -150,8 +152,8 @@ __device__ __forceinline__ constexpr bool need_m(int mode, int cz) {
     return mode == MID || (mode == FIRST ? cz < 0 : cz > 0);
 }
 
-template <int NH, int MODE>
-__device__ __forceinline__ void phase_a(float (&acc)[3][VXH][4], const float *stg, float *xbuf, float *ebuf,
+template <int NH, int MODE, typename T>
+__device__ __forceinline__ void phase_a(float (&acc)[3][VXH][4], const T *stg, float *xbuf, float *ebuf,
                                         const TiledParams &p, int lane, int row, int half) {
     constexpr int PM = 0, P0 = 1, PP = 2;
     constexpr int RL = HG<NH>::RL, XDIR = HG<NH>::XDIR;
@@ -226,9 +228,9 @@ __device__ __forceinline__ void phase_a(float (&acc)[3][VXH][4], const float *st
     }
 }
 
-template <int NH, int MODE>
+template <int NH, int MODE, typename T>
 __device__ __forceinline__ void phase_b(float (&acc)[3][VXH][4], const float *xbuf, const float *ebuf,
-                                        float *out, const TiledParams &p, int lane, int row, int half,
+                                        T *out, const TiledParams &p, int lane, int row, int half,
                                         int col, int zfin) {
     constexpr int PM = 0, P0 = 1, PP = 2;
     constexpr int RL = HG<NH>::RL, XDIR = HG<NH>::XDIR, XSLOT = HG<NH>::XSLOT;
@@ -315,16 +317,15 @@ __device__ __forceinline__ void phase_b(float (&acc)[3][VXH][4], const float *xb
         if (zfin >= 0) {
             const long long rowoff =
                 ((long long)zfin * p.ny + col * ROWS + row) * p.nx + half * HALF + lane * VXH;
-            float *op = out + rowoff;
+            T *op = out + rowoff;
             float r[VXH];
 #pragma unroll
             for (int i = 0; i < VXH; ++i) r[i] = rcp_nr(1.f + acc[PM][i][0]);
-            *reinterpret_cast<float4 *>(op) = make_float4(acc[PM][0][0], acc[PM][1][0], acc[PM][2][0], acc[PM][3][0]);
+            st4(op, acc[PM][0][0], acc[PM][1][0], acc[PM][2][0], acc[PM][3][0]);
 #pragma unroll
             for (int c = 1; c < 4; ++c)
-                *reinterpret_cast<float4 *>(op + c * p.fstride) =
-                    make_float4(acc[PM][0][c] * r[0], acc[PM][1][c] * r[1], acc[PM][2][c] * r[2],
-                                acc[PM][3][c] * r[3]);
+                st4(op + c * p.fstride, acc[PM][0][c] * r[0], acc[PM][1][c] * r[1], acc[PM][2][c] * r[2],
+                    acc[PM][3][c] * r[3]);
         }
 #pragma unroll
         for (int i = 0; i < VXH; ++i)
@@ -333,20 +334,20 @@ __device__ __forceinline__ void phase_b(float (&acc)[3][VXH][4], const float *xb
     }
 }
 
-template <int NH>
-__device__ __forceinline__ void issue_plane(const float *in, const TiledParams &p, int col, int z,
-                                            float *stage, uint64_t *bar) {
-    constexpr int RL = HG<NH>::RL;
-    constexpr uint32_t TX = HG<NH>::TX;
+template <int NH, typename T>
+__device__ __forceinline__ void issue_plane(const T *in, const TiledParams &p, int col, int z, T *stage,
+                                            uint64_t *bar) {
+    constexpr int RL = HG<NH, T>::RL;
+    constexpr uint32_t TX = HG<NH, T>::TX;
     const int zl = z < 0 ? z + p.nz : (z >= p.nz ? z - p.nz : z);
     const int y0 = col * ROWS;
     const long long plane = (long long)p.nx * p.ny;
     mbar_expect_tx(bar, TX);
-    const uint32_t rb = (uint32_t)(RL * 4);
+    const uint32_t rb = (uint32_t)(RL * sizeof(T));
 #pragma unroll
     for (int f = 0; f < 4; ++f) {
-        const float *src = in + f * p.fstride + (long long)zl * plane;
-        float *dst = stage + f * TROWS * RL;
+        const T *src = in + f * p.fstride + (long long)zl * plane;
+        T *dst = stage + f * TROWS * RL;
         if (y0 >= 1 && y0 + ROWS < p.ny) {
             bulk_g2s(dst, src + (long long)(y0 - 1) * p.nx, TROWS * rb, bar);
         } else {
@@ -371,14 +372,14 @@ __device__ __forceinline__ void rotate(float (&acc)[3][VXH][4]) {
     }
 }
 
-template <int NH>
-__global__ void __launch_bounds__(HG<NH>::NTH, 2 / NH) k_d3q19_half(const float *__restrict__ in,
-                                                                   float *__restrict__ out, TiledParams p) {
-    constexpr int XBUF = HG<NH>::XBUF, STAGE = HG<NH>::STAGE, EBUF = HG<NH>::EBUF;
+template <int NH, typename T>
+__global__ void __launch_bounds__(HG<NH>::NTH, 2 / NH) k_d3q19_half(const T *__restrict__ in,
+                                                                   T *__restrict__ out, TiledParams p) {
+    constexpr int XBUF = HG<NH, T>::XBUF, STAGE = HG<NH, T>::STAGE, EBUF = HG<NH, T>::EBUF;
     extern __shared__ float4 smem4[];
     float *xs = reinterpret_cast<float *>(smem4);
-    float *stg = xs + 2 * XBUF;
-    float *eb = stg + 2 * STAGE;
+    T *stg = reinterpret_cast<T *>(xs + 2 * XBUF);
+    float *eb = reinterpret_cast<float *>(stg + 2 * STAGE);
     uint64_t *bars = reinterpret_cast<uint64_t *>(eb + 2 * EBUF);
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const int row = NH == 2 ? warp >> 1 : warp, half = NH == 2 ? (warp & 1) : 0;
@@ -395,7 +396,7 @@ __global__ void __launch_bounds__(HG<NH>::NTH, 2 / NH) k_d3q19_half(const float 
     TaskIter pf = it;
     int issued = 0;
     for (int k = 0; k < 2 && pf.valid(); ++k) {
-        if (threadIdx.x == 0) issue_plane<NH>(in, p, pf.col, pf.pz, stg + k * STAGE, &bars[k]);
+        if (threadIdx.x == 0) issue_plane<NH, T>(in, p, pf.col, pf.pz, stg + k * STAGE, &bars[k]);
         ++issued;
         pf.next();
     }
@@ -410,7 +411,7 @@ __global__ void __launch_bounds__(HG<NH>::NTH, 2 / NH) k_d3q19_half(const float 
 
     for (int tc = 0; it.valid(); ++tc) {
         const int s = tc & 1;
-        const float *stage = stg + s * STAGE;
+        const T *stage = stg + s * STAGE;
         float *xbuf = xs + s * XBUF;
         float *ebuf = eb + s * EBUF;
         const bool ok = mbar_wait(&bars[s], (uint32_t)((tc >> 1) & 1));
@@ -440,7 +441,7 @@ __global__ void __launch_bounds__(HG<NH>::NTH, 2 / NH) k_d3q19_half(const float 
         if (pf.valid()) {
             if (threadIdx.x == 0) {
                 asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-                issue_plane<NH>(in, p, pf.col, pf.pz, stg + s * STAGE, &bars[s]);
+                issue_plane<NH, T>(in, p, pf.col, pf.pz, stg + s * STAGE, &bars[s]);
             }
             ++issued;
             pf.next();
@@ -464,15 +465,16 @@ __global__ void __launch_bounds__(HG<NH>::NTH, 2 / NH) k_d3q19_half(const float 
     }
 }
 
-template <int NH>
+template <int NH, typename T>
 cudaError_t prepare(int *ctas) {
     static int state = 0, nctas = 0;
     if (state == 0) {
-        cudaError_t e = cudaFuncSetAttribute(k_d3q19_half<NH>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                             (int)HG<NH>::BYTES);
+        cudaError_t e = cudaFuncSetAttribute(k_d3q19_half<NH, T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                             (int)HG<NH, T>::BYTES);
         if (e != cudaSuccess) return e;
         int nb = 0, dev = 0, sms = 0;
-        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_d3q19_half<NH>, HG<NH>::NTH, HG<NH>::BYTES);
+        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_d3q19_half<NH, T>, HG<NH, T>::NTH,
+                                                          HG<NH, T>::BYTES);
         if (e != cudaSuccess) return e;
         e = cudaGetDevice(&dev);
         if (e != cudaSuccess) return e;
@@ -503,20 +505,31 @@ int half_chunk_planes(int ycols, int nz, int ctas) {
 
 }  // namespace
 
-bool half_supported(int Q, int storage, const StepParams &p) {
-    if (Q != 19 || storage != STORE_F32 || p.bc != BC_PERIODIC) return false;
-    if (p.has_force || p.gfield) return false;  // no forcing term in this kernel
-    if ((p.nx != 128 && p.nx != 256) || p.ny % ROWS != 0 || p.ny < ROWS || p.nz < 1) return false;
-    if (p.fstride % 4 != 0 || !p.err) return false;
-    int dev = 0;
-    if (cudaGetDevice(&dev) != cudaSuccess) return false;
-    return (p.nx == 256 ? prepare<2>(nullptr) : prepare<1>(nullptr)) == cudaSuccess;
+template <int NH>
+static cudaError_t prepare_storage(int storage) {
+    switch (storage) {
+        case STORE_F32: return prepare<NH, float>(nullptr);
+        case STORE_BF16: return prepare<NH, __nv_bfloat16>(nullptr);
+        case STORE_F16: return prepare<NH, __half>(nullptr);
+    }
+    return cudaErrorInvalidValue;
 }
 
-template <int NH>
+bool half_supported(int Q, int storage, const StepParams &p) {
+    if (Q != 19 || p.bc != BC_PERIODIC) return false;
+    if (storage != STORE_F32 && storage != STORE_BF16 && storage != STORE_F16) return false;
+    if (p.has_force || p.gfield) return false;  // no forcing term in this kernel
+    if ((p.nx != 128 && p.nx != 256) || p.ny % ROWS != 0 || p.ny < ROWS || p.nz < 1) return false;
+    if (p.fstride % 8 != 0 || !p.err) return false;  // 16-byte field starts for 2-byte storage
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) return false;
+    return (p.nx == 256 ? prepare_storage<2>(storage) : prepare_storage<1>(storage)) == cudaSuccess;
+}
+
+template <int NH, typename T>
 static cudaError_t launch_nh(const void *in, void *out, const StepParams &sp, cudaStream_t st) {
     int ctas = 0;
-    cudaError_t e = prepare<NH>(&ctas);
+    cudaError_t e = prepare<NH, T>(&ctas);
     if (e != cudaSuccess) return e;
     TiledParams p;
     p.nx = sp.nx;
@@ -532,14 +545,21 @@ static cudaError_t launch_nh(const void *in, void *out, const StepParams &sp, cu
     p.a_s = (float)((double)sp.a / nu);
     p.err = sp.err;
     const int grid = ctas < p.nitems ? ctas : p.nitems;
-    k_d3q19_half<NH><<<(unsigned)grid, HG<NH>::NTH, HG<NH>::BYTES, st>>>((const float *)in, (float *)out, p);
+    k_d3q19_half<NH, T><<<(unsigned)grid, HG<NH, T>::NTH, HG<NH, T>::BYTES, st>>>((const T *)in, (T *)out, p);
     return cudaGetLastError();
 }
 
 cudaError_t launch_step_half(int Q, int storage, const void *in, void *out, const StepParams &sp,
                              cudaStream_t st) {
     if (!half_supported(Q, storage, sp)) return cudaErrorNotSupported;
-    return sp.nx == 256 ? launch_nh<2>(in, out, sp, st) : launch_nh<1>(in, out, sp, st);
+    const bool w = sp.nx == 256;
+    switch (storage) {
+        case STORE_F32: return w ? launch_nh<2, float>(in, out, sp, st) : launch_nh<1, float>(in, out, sp, st);
+        case STORE_BF16:
+            return w ? launch_nh<2, __nv_bfloat16>(in, out, sp, st) : launch_nh<1, __nv_bfloat16>(in, out, sp, st);
+        case STORE_F16: return w ? launch_nh<2, __half>(in, out, sp, st) : launch_nh<1, __half>(in, out, sp, st);
+    }
+    return cudaErrorInvalidValue;
 }
 
 }  // namespace lwacm

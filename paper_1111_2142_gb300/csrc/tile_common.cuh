@@ -5,6 +5,7 @@
 #pragma once
 
 #include <stdint.h>
+#include <string.h>
 
 #include "lwacm_core.cuh"
 
@@ -141,16 +142,51 @@ struct NodeConst {
     float U[VX], V[VX], W[VX], K1[VX], A1[VX];
 };
 
-// row: staged field-0 row; rstride: distance between fields in the stage
-template <int VX>
-__device__ __forceinline__ void node_consts(NodeConst<VX> &nc, const float *row, int rstride,
-                                            int lane, float s18) {
+// four consecutive stored values as floats (FP32, or BF16 / FP16 storage: a
+// bfloat16 is the upper half of an FP32, so widening it is exact)
+__device__ __forceinline__ float4 ld4(const float *p) { return *reinterpret_cast<const float4 *>(p); }
+__device__ __forceinline__ float4 ld4(const __nv_bfloat16 *p) {
+    const uint2 r = *reinterpret_cast<const uint2 *>(p);
+    return make_float4(__uint_as_float(r.x << 16), __uint_as_float(r.x & 0xffff0000u),
+                       __uint_as_float(r.y << 16), __uint_as_float(r.y & 0xffff0000u));
+}
+__device__ __forceinline__ float4 ld4(const __half *p) {
+    const uint2 r = *reinterpret_cast<const uint2 *>(p);
+    __half2 a, b;
+    memcpy(&a, &r.x, 4);
+    memcpy(&b, &r.y, 4);
+    const float2 fa = __half22float2(a), fb = __half22float2(b);
+    return make_float4(fa.x, fa.y, fb.x, fb.y);
+}
+// store four floats rounded (to nearest even) to the storage type
+__device__ __forceinline__ void st4(float *p, float a, float b, float c, float d) {
+    *reinterpret_cast<float4 *>(p) = make_float4(a, b, c, d);
+}
+__device__ __forceinline__ void st4(__nv_bfloat16 *p, float a, float b, float c, float d) {
+    const __nv_bfloat162 x = __floats2bfloat162_rn(a, b), y = __floats2bfloat162_rn(c, d);
+    uint2 r;
+    memcpy(&r.x, &x, 4);
+    memcpy(&r.y, &y, 4);
+    *reinterpret_cast<uint2 *>(p) = r;
+}
+__device__ __forceinline__ void st4(__half *p, float a, float b, float c, float d) {
+    const __half2 x = __floats2half2_rn(a, b), y = __floats2half2_rn(c, d);
+    uint2 r;
+    memcpy(&r.x, &x, 4);
+    memcpy(&r.y, &y, 4);
+    *reinterpret_cast<uint2 *>(p) = r;
+}
+
+// row: staged field-0 row; rstride: distance (in elements) between fields in the stage
+template <int VX, typename T>
+__device__ __forceinline__ void node_consts(NodeConst<VX> &nc, const T *row, int rstride, int lane,
+                                            float s18) {
 #pragma unroll
     for (int h = 0; h < VX / 4; ++h) {
-        const float4 d4 = *reinterpret_cast<const float4 *>(row + lane * VX + 4 * h);
-        const float4 u4 = *reinterpret_cast<const float4 *>(row + rstride + lane * VX + 4 * h);
-        const float4 v4 = *reinterpret_cast<const float4 *>(row + 2 * rstride + lane * VX + 4 * h);
-        const float4 w4 = *reinterpret_cast<const float4 *>(row + 3 * rstride + lane * VX + 4 * h);
+        const float4 d4 = ld4(row + lane * VX + 4 * h);
+        const float4 u4 = ld4(row + rstride + lane * VX + 4 * h);
+        const float4 v4 = ld4(row + 2 * rstride + lane * VX + 4 * h);
+        const float4 w4 = ld4(row + 3 * rstride + lane * VX + 4 * h);
         const float dd[4] = {d4.x, d4.y, d4.z, d4.w}, uu[4] = {u4.x, u4.y, u4.z, u4.w};
         const float vv[4] = {v4.x, v4.y, v4.z, v4.w}, ww[4] = {w4.x, w4.y, w4.z, w4.w};
 #pragma unroll

@@ -193,12 +193,24 @@ def round_storage(a, storage):
 HALF_ULP = {2: 2.0 ** -11, 1: 2.0 ** -8}
 
 
+# (nx, ny, nz): the generic kernel (32^3) and the half-row kernel with 256- and
+# 128-node rows
+HALF_SHAPES = [(32, 32, 32), (256, 16, 8), (128, 24, 5)]
+
+
+def _tgv_box(shape):
+    nx, ny, nz = shape
+    return inputs.tgv3d(nx, u0=0.02, ny=ny, nz=nz)
+
+
+@pytest.mark.parametrize("shape", HALF_SHAPES)
 @pytest.mark.parametrize("storage", [2, 1])
-def test_half_storage_one_step(lw, storage):
+def test_half_storage_one_step(lw, storage, shape):
     """FP16 / BF16 storage, FP32 arithmetic: from the same rounded state one step
     differs from the FP64 oracle by the final rounding to the storage type only."""
-    f = [round_storage(a, storage) for a in inputs.tgv3d(32, u0=0.02)]
+    f = [round_storage(a, storage) for a in _tgv_box(shape)]
     got, name = run_gpu(lw, 19, f, 0.005, 1, storage=storage)
+    assert name.startswith("generic" if shape[0] == 32 else "half")
     ref = oracle.step(19, *f, nu=0.005, nsteps=1)
     for g, r in zip(got, ref):
         # floors: FP16 subnormals (|v| < 2^-14) have a fixed spacing of 2^-24; values
@@ -208,14 +220,15 @@ def test_half_storage_one_step(lw, storage):
         assert np.all(np.abs(g - r) <= tol), (name, float(np.max(np.abs(g - r) / (np.abs(r) + 1e-30))))
 
 
+@pytest.mark.parametrize("shape", HALF_SHAPES)
 @pytest.mark.parametrize("storage", [2, 1])
-def test_half_storage_error_vs_oracle(lw, storage):
+def test_half_storage_error_vs_oracle(lw, storage, shape):
     """FP16 / BF16 storage over 200 steps of the 3D Taylor-Green vortex (u0 = 0.02,
     nu = 0.005): each step re-rounds every stored value by at most half an ulp,
     so |du| / u0 <= T * half-ulp (linear accumulation bound); the measured error
     is printed for the record."""
     T = 200
-    f = inputs.tgv3d(32, u0=0.02)
+    f = _tgv_box(shape)
     got, name = run_gpu(lw, 19, f, 0.005, T, storage=storage)
     ref = oracle.step(19, *f, nu=0.005, nsteps=T)
     eu, ed = errs(got, ref, 0.02)
