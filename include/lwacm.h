@@ -192,9 +192,10 @@ lwacm_status lwacm_get_fields(lwacm_ctx *ctx, void *d, void *ux, void *uy, void 
 
 /* FP64 global quantities of the current state (Eq. global.quantities):
  *   out[0] = sum d (mass minus the node count), out[1..3] = sum rho u_a,
- *   out[4] = 0.5 sum rho |u|^2, out[5] = max |u|, out[6] = 0.5 sum (u+w)^2,
- *   out[7] = 0.5 sum (u-w)^2 (the M_par / M_perp sums of Eq. 3Dmomenta before
- *   the volume factor; zero in 2D).
+ *   out[4] = 0.5 sum rho |u|^2, out[5] = max |u|, out[6] = 0.5 sum (ux+uy)^2,
+ *   out[7] = 0.5 sum (ux-uy)^2 (the M_par / M_perp sums of Eq. 3Dmomenta before
+ *   the volume factor, for a lid moving along the x = y diagonal of the top z
+ *   plane; zero in 2D).
  * Deterministic two-pass device reduction in FP64; synchronises the stream.
  * Returns LWACM_E_NONFINITE (and still fills out) if any value is NaN/Inf. */
 lwacm_status lwacm_diagnostics(lwacm_ctx *ctx, double out[8]);

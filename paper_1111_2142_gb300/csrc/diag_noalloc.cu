@@ -54,8 +54,10 @@ __global__ void __launch_bounds__(kThreads) k_partials(const T *__restrict__ d, 
         acc[4] += 0.5 * rho * uu;
         acc[5] = fmax(acc[5], uu);
         if (uz) {
-            acc[6] += 0.5 * (u + w) * (u + w);
-            acc[7] += 0.5 * (u - w) * (u - w);
+            // Eq. 3Dmomenta, read for a lid moving along the x = y diagonal of the
+            // top z plane: components parallel / perpendicular to the lid (times sqrt 2)
+            acc[6] += 0.5 * (u + v) * (u + v);
+            acc[7] += 0.5 * (u - v) * (u - v);
         }
         if (!isfinite(dd) || !isfinite(uu)) acc[8] += 1.0;
     }

@@ -247,9 +247,9 @@ def test_diagnostics_match_fp64_sums(lw):
     ref = oracle.diagnostics(*got)
     for k in ("mass", "jx", "jy", "jz", "ke", "umax"):
         assert abs(diag[k] - ref[k]) <= 1e-12 * max(1.0, abs(ref[k])), (k, diag[k], ref[k])
-    u, w = got[1], got[3]
-    assert abs(diag["mpar"] - 0.5 * np.sum((u + w) ** 2)) < 1e-12
-    assert abs(diag["mperp"] - 0.5 * np.sum((u - w) ** 2)) < 1e-12
+    u, v = got[1], got[2]
+    assert abs(diag["mpar"] - 0.5 * np.sum((u + v) ** 2)) < 1e-12
+    assert abs(diag["mperp"] - 0.5 * np.sum((u - v) ** 2)) < 1e-12
     sim.close()
 
 
