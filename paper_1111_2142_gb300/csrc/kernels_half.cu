@@ -70,12 +70,12 @@ __device__ __forceinline__ void send_rows(const NC &nc, float c4, float *ubase, 
         float u0[VXH], u1[VXH], d0[VXH], d1[VXH];
         {  // k = 0: c = (0,1,0), -c = (0,-1,0)
 #pragma unroll
-            for (int i = 0; i < VXH; ++i) pair_g(nc, i, ypair_e(nc, 0, i), false, c4, u0[i], d0[i]);
+            for (int i = 0; i < VXH; ++i) pair_g(nc, i, ypair_e(nc, 0, i), false, u0[i], d0[i]);
         }
         {  // k = 1: c = (1,1,0) [up: receiver x <- x-1]; -c = (-1,-1,0) [down: x <- x+1]
             float gp[VXH], gm[VXH];
 #pragma unroll
-            for (int i = 0; i < VXH; ++i) pair_g(nc, i, ypair_e(nc, 1, i), true, c4, gp[i], gm[i]);
+            for (int i = 0; i < VXH; ++i) pair_g(nc, i, ypair_e(nc, 1, i), true, gp[i], gm[i]);
             if (UP) {
                 if (NH == 2) st_shared_if(edge + E_UP1, gp[VXH - 1], l31);
                 xshift(gp, 1, lane);
@@ -97,7 +97,7 @@ __device__ __forceinline__ void send_rows(const NC &nc, float c4, float *ubase, 
         {  // k = 2: c = (-1,1,0) [up: x <- x+1]; -c = (1,-1,0) [down: x <- x-1]
             float gp[VXH], gm[VXH];
 #pragma unroll
-            for (int i = 0; i < VXH; ++i) pair_g(nc, i, ypair_e(nc, 2, i), true, c4, gp[i], gm[i]);
+            for (int i = 0; i < VXH; ++i) pair_g(nc, i, ypair_e(nc, 2, i), true, gp[i], gm[i]);
             if (UP) {
                 if (NH == 2) st_shared_if(edge + E_UP2, gp[0], l0);
                 xshift(gp, -1, lane);
@@ -131,14 +131,14 @@ __device__ __forceinline__ void send_rows(const NC &nc, float c4, float *ubase, 
     {
         float gp[VXH], gm[VXH];
 #pragma unroll
-        for (int i = 0; i < VXH; ++i) pair_g(nc, i, ypair_e(nc, 3, i), true, c4, gp[i], gm[i]);
+        for (int i = 0; i < VXH; ++i) pair_g(nc, i, ypair_e(nc, 3, i), true, gp[i], gm[i]);
         if (UP && MODE != LAST) st_slot(ubase + 2 * XSLOT, gp, lane);
         if (DN && MODE != FIRST) st_slot(dbase + 3 * XSLOT, gm, lane);
     }
     {
         float gp[VXH], gm[VXH];
 #pragma unroll
-        for (int i = 0; i < VXH; ++i) pair_g(nc, i, ypair_e(nc, 4, i), true, c4, gp[i], gm[i]);
+        for (int i = 0; i < VXH; ++i) pair_g(nc, i, ypair_e(nc, 4, i), true, gp[i], gm[i]);
         if (UP && MODE != FIRST) st_slot(ubase + 3 * XSLOT, gp, lane);
         if (DN && MODE != LAST) st_slot(dbase + 2 * XSLOT, gm, lane);
     }
@@ -165,7 +165,7 @@ __device__ __forceinline__ void phase_a(float (&acc)[3][VXH][4], const T *stg, f
 #pragma unroll
         for (int i = 0; i < VXH; ++i) {
             float gp, gm;
-            pair_g(nc, i, nc.W[i], false, p.c4, gp, gm);  // (0,0,+1) / (0,0,-1)
+            pair_g(nc, i, nc.W[i], false, gp, gm);  // (0,0,+1) / (0,0,-1)
             if (MODE == MID) {
                 acc[P0][i][3] = acc[P0][i][0];    // jz so far = d so far (c_z = +1 arrivals)
                 acc[P0][i][0] += 6.f * nc.K1[i];  // rest link: w_0 K = K/3
@@ -186,7 +186,7 @@ __device__ __forceinline__ void phase_a(float (&acc)[3][VXH][4], const T *stg, f
             for (int i = 0; i < VXH; ++i) {
                 float gp, gm;
                 const float e = cz == 0 ? nc.U[i] : (cz > 0 ? nc.U[i] + nc.W[i] : nc.U[i] - nc.W[i]);
-                pair_g(nc, i, e, cz != 0, p.c4, gp, gm);
+                pair_g(nc, i, e, cz != 0, gp, gm);
                 if (np) {
                     if (i + 1 < VXH)
                         dep(acc[pl<PM, P0, PP>(cz)][i + 1], gp, 1, 0, cz);

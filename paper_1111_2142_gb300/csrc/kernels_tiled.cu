@@ -68,14 +68,14 @@ __device__ __forceinline__ void send_row(const NodeConst<VX> &nc, float c4, floa
         {  // k = 0: c = (0,1,0), -c = (0,-1,0)
             float gp[VX], gm[VX];
 #pragma unroll
-            for (int i = 0; i < VX; ++i) pair_g(nc, i, ypair_e(nc, 0, i), false, c4, gp[i], gm[i]);
+            for (int i = 0; i < VX; ++i) pair_g(nc, i, ypair_e(nc, 0, i), false, gp[i], gm[i]);
 #pragma unroll
             for (int i = 0; i < VX; ++i) s0[i] = UP ? gp[i] : gm[i];
         }
         {  // k = 1: c = (1,1,0) [up: receiver x <- x-1]; -c = (-1,-1,0) [down: x <- x+1]
             float gp[VX], gm[VX];
 #pragma unroll
-            for (int i = 0; i < VX; ++i) pair_g(nc, i, ypair_e(nc, 1, i), true, c4, gp[i], gm[i]);
+            for (int i = 0; i < VX; ++i) pair_g(nc, i, ypair_e(nc, 1, i), true, gp[i], gm[i]);
             if (UP) {
                 xshift(gp, 1, lane);
 #pragma unroll
@@ -95,7 +95,7 @@ __device__ __forceinline__ void send_row(const NodeConst<VX> &nc, float c4, floa
         {  // k = 2: c = (-1,1,0) [up: x <- x+1]; -c = (1,-1,0) [down: x <- x-1]
             float gp[VX], gm[VX];
 #pragma unroll
-            for (int i = 0; i < VX; ++i) pair_g(nc, i, ypair_e(nc, 2, i), true, c4, gp[i], gm[i]);
+            for (int i = 0; i < VX; ++i) pair_g(nc, i, ypair_e(nc, 2, i), true, gp[i], gm[i]);
             if (UP) {
                 xshift(gp, -1, lane);
 #pragma unroll
@@ -120,14 +120,14 @@ __device__ __forceinline__ void send_row(const NodeConst<VX> &nc, float c4, floa
         float gp[VX], gm[VX];
         const int k = UP ? 3 : 4;
 #pragma unroll
-        for (int i = 0; i < VX; ++i) pair_g(nc, i, ypair_e(nc, k, i), true, c4, gp[i], gm[i]);
+        for (int i = 0; i < VX; ++i) pair_g(nc, i, ypair_e(nc, k, i), true, gp[i], gm[i]);
         st_slot(base + 2 * G::XSLOT, UP ? gp : gm, lane);
     }
     if (MODE != FIRST) {  // slot 3 (c_z = -1): up -> c of k = 4; down -> -c of k = 3
         float gp[VX], gm[VX];
         const int k = UP ? 4 : 3;
 #pragma unroll
-        for (int i = 0; i < VX; ++i) pair_g(nc, i, ypair_e(nc, k, i), true, c4, gp[i], gm[i]);
+        for (int i = 0; i < VX; ++i) pair_g(nc, i, ypair_e(nc, k, i), true, gp[i], gm[i]);
         st_slot(base + 3 * G::XSLOT, UP ? gp : gm, lane);
     }
 }
@@ -145,7 +145,7 @@ __device__ __forceinline__ void phase_a(float (&acc)[3][VX][4], const float *stg
 #pragma unroll
         for (int i = 0; i < VX; ++i) {
             float gp, gm;
-            pair_g(nc, i, nc.W[i], false, p.c4, gp, gm);  // (0,0,+1) / (0,0,-1)
+            pair_g(nc, i, nc.W[i], false, gp, gm);  // (0,0,+1) / (0,0,-1)
             if (MODE == MID) {
                 acc[P0][i][3] = acc[P0][i][0];  // jz so far = d so far (c_z = +1 arrivals)
                 acc[P0][i][0] += 6.f * nc.K1[i];  // rest link: w_0 K = K/3
@@ -170,7 +170,7 @@ __device__ __forceinline__ void phase_a(float (&acc)[3][VX][4], const float *stg
             for (int i = 0; i < VX; ++i) {
                 float gp, gm;
                 const float e = cz == 0 ? nc.U[i] : (cz > 0 ? nc.U[i] + nc.W[i] : nc.U[i] - nc.W[i]);
-                pair_g(nc, i, e, cz != 0, p.c4, gp, gm);
+                pair_g(nc, i, e, cz != 0, gp, gm);
                 if (need_p) {
                     if (i + 1 < VX)
                         dep(acc[pl<PM, P0, PP>(cz)][i + 1], gp, 1, 0, cz);

@@ -134,12 +134,14 @@ __device__ __forceinline__ void dep(float (&a)[4], float g, int cx, int cy, int 
 template <int PM, int P0, int PP>
 __device__ __forceinline__ constexpr int pl(int cz) { return cz > 0 ? PP : (cz < 0 ? PM : P0); }
 
-// per-node constants: velocity, K/18 with K = d - 3/2 rho |u|^2, and rho nu
-// (= rho s / 18); a link value is w/(1/18) (K1 + A1 e (1 + e/(4 nu))) with e = c.u,
-// i.e. w [d + rho (s e + 9/2 e^2 - 3/2 |u|^2)].
+// per-node constants: velocity and, with K = d - 3/2 rho |u|^2, the three
+// coefficients of a link value w [d + rho (s e + 9/2 e^2 - 3/2 |u|^2)] =
+// w K + w rho s e + w 9/2 rho e^2 (e = c.u) for the axis weight w = 1/18
+// (K1 = K/18, A1 = rho s/18 = rho nu, B1 = rho/4) and the diagonal weight
+// 1/36 (K2, A2, B2: half of those).
 template <int VX>
 struct NodeConst {
-    float U[VX], V[VX], W[VX], K1[VX], A1[VX];
+    float U[VX], V[VX], W[VX], K1[VX], A1[VX], B1[VX], K2[VX], A2[VX], B2[VX];
 };
 
 // four consecutive stored values as floats (FP32, or BF16 / FP16 storage: a
@@ -200,24 +202,23 @@ __device__ __forceinline__ void node_consts(NodeConst<VX> &nc, const T *row, int
             nc.W[i] = ww[j];
             nc.K1[i] = K * (1.f / 18.f);
             nc.A1[i] = rho * s18;
+            nc.B1[i] = 0.25f * rho;
+            nc.K2[i] = K * (1.f / 36.f);
+            nc.A2[i] = rho * (0.5f * s18);
+            nc.B2[i] = 0.125f * rho;
         }
     }
 }
 
-// values of the pair (c, -c) at node i: axis links weight 1/18, diagonals 1/36
+// values of the pair (c, -c) at node i (e = c.u): the even part w (K + 9/2 rho e^2)
+// plus or minus the odd part w rho s e; axis links weight 1/18, diagonals 1/36
 template <int VX>
-__device__ __forceinline__ void pair_g(const NodeConst<VX> &nc, int i, float e, bool diag,
-                                       float c4, float &gp, float &gm) {
-    const float od = nc.A1[i] * e;                // rho s e / 18
-    const float cm = fmaf(od * c4, e, nc.K1[i]);  // (K + 9/2 rho e^2) / 18
-    if (diag) {
-        const float ho = 0.5f * od;
-        gp = fmaf(0.5f, cm, ho);
-        gm = fmaf(0.5f, cm, -ho);
-    } else {
-        gp = cm + od;
-        gm = cm - od;
-    }
+__device__ __forceinline__ void pair_g(const NodeConst<VX> &nc, int i, float e, bool diag, float &gp,
+                                       float &gm) {
+    const float A = diag ? nc.A2[i] : nc.A1[i];
+    const float cm = fmaf((diag ? nc.B2[i] : nc.B1[i]) * e, e, diag ? nc.K2[i] : nc.K1[i]);
+    gp = fmaf(A, e, cm);
+    gm = fmaf(-A, e, cm);
 }
 
 // the five (c, -c) pairs with c_y(c) = +1: c = (cx, 1, cz)
