@@ -38,22 +38,22 @@ __device__ __forceinline__ void mbar_expect_tx(uint64_t *bar, uint32_t bytes) {
     asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(sa(bar)), "r"(bytes)
                  : "memory");
 }
-// bounded wait: each try_wait suspends the thread in hardware until the phase
-// completes or about 1 us passes (no busy polling); at most 2^19 tries, so a
-// phase that never completes is given up well under a second
-__device__ __forceinline__ bool mbar_try(uint64_t *bar, uint32_t parity) {
+__device__ __forceinline__ bool mbar_test(uint64_t *bar, uint32_t parity) {
     uint32_t ok;
     asm volatile(
-        "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2, %3;\n"
+        "{\n .reg .pred p;\n mbarrier.test_wait.parity.shared::cta.b64 p, [%1], %2;\n"
         " selp.u32 %0, 1, 0, p;\n}\n"
         : "=r"(ok)
-        : "r"(sa(bar)), "r"(parity), "r"(1000u)
+        : "r"(sa(bar)), "r"(parity)
         : "memory");
     return ok != 0;
 }
+// bounded wait: at most 2^22 polls with back-off (well under a second)
 __device__ __forceinline__ bool mbar_wait(uint64_t *bar, uint32_t parity) {
-    for (int it = 0; it < (1 << 19); ++it)
-        if (mbar_try(bar, parity)) return true;
+    for (int it = 0; it < (1 << 22); ++it) {
+        if (mbar_test(bar, parity)) return true;
+        if (it > 32) __nanosleep(100);
+    }
     return false;
 }
 __device__ __forceinline__ void bulk_g2s(void *dst, const void *src, uint32_t bytes, uint64_t *bar) {
