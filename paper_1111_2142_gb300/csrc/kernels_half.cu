@@ -52,7 +52,103 @@ struct HG {
     static constexpr uint32_t TX = STAGE * sizeof(T);
 };
 
-using NC = NodeConst<VXH>;
+// ---- packed arithmetic ----------------------------------------------------------
+// The four nodes of a lane are held as two pairs, (0,1) and (2,3), in float2
+// registers, so that the same operation on two nodes issues as one packed FP32x2
+// instruction (half the issue slots of two scalar ones, same rounding).
+using F2 = float2;
+__device__ __forceinline__ F2 b2(float v) { return make_float2(v, v); }
+__device__ __forceinline__ F2 add2(F2 a, F2 b) { return __fadd2_rn(a, b); }
+__device__ __forceinline__ F2 sub2(F2 a, F2 b) { return __fadd2_rn(a, make_float2(-b.x, -b.y)); }
+__device__ __forceinline__ F2 mul2(F2 a, F2 b) { return __fmul2_rn(a, b); }
+__device__ __forceinline__ F2 fma2(F2 a, F2 b, F2 c) { return __ffma2_rn(a, b, c); }
+__device__ __forceinline__ F2 neg2(F2 a) { return make_float2(-a.x, -a.y); }
+
+// node i of a lane inside a pair array
+__device__ __forceinline__ float ndv(const F2 (&v)[2], int i) { return (i & 1) ? v[i >> 1].y : v[i >> 1].x; }
+
+// per-node constants of the moment form (see tile_common.cuh, NodeConst), per pair
+struct NC2 {
+    F2 U[2], V[2], W[2], K1[2], A1[2], B1[2], K2[2], A2[2], B2[2];
+};
+
+template <typename T>
+__device__ __forceinline__ void node_consts2(NC2 &nc, const T *row, int rstride, int lane, float s18) {
+    const float4 d4 = ld4(row + lane * VXH), u4 = ld4(row + rstride + lane * VXH);
+    const float4 v4 = ld4(row + 2 * rstride + lane * VXH), w4 = ld4(row + 3 * rstride + lane * VXH);
+    const F2 dd[2] = {make_float2(d4.x, d4.y), make_float2(d4.z, d4.w)};
+    nc.U[0] = make_float2(u4.x, u4.y);
+    nc.U[1] = make_float2(u4.z, u4.w);
+    nc.V[0] = make_float2(v4.x, v4.y);
+    nc.V[1] = make_float2(v4.z, v4.w);
+    nc.W[0] = make_float2(w4.x, w4.y);
+    nc.W[1] = make_float2(w4.z, w4.w);
+#pragma unroll
+    for (int j = 0; j < 2; ++j) {
+        const F2 rho = add2(dd[j], b2(1.f));
+        const F2 q = fma2(nc.U[j], nc.U[j], fma2(nc.V[j], nc.V[j], mul2(nc.W[j], nc.W[j])));
+        const F2 K = fma2(mul2(b2(-1.5f), rho), q, dd[j]);  // d - 3/2 rho |u|^2
+        nc.K1[j] = mul2(K, b2(1.f / 18.f));
+        nc.A1[j] = mul2(rho, b2(s18));
+        nc.B1[j] = mul2(rho, b2(0.25f));
+        nc.K2[j] = mul2(K, b2(1.f / 36.f));
+        nc.A2[j] = mul2(rho, b2(0.5f * s18));
+        nc.B2[j] = mul2(rho, b2(0.125f));
+    }
+}
+
+// values of the link pair (c, -c) at the two nodes of pair j, e = c.u
+__device__ __forceinline__ void pair2(const NC2 &nc, int j, F2 e, bool diag, F2 &gp, F2 &gm) {
+    const F2 A = diag ? nc.A2[j] : nc.A1[j], B = diag ? nc.B2[j] : nc.B1[j], K = diag ? nc.K2[j] : nc.K1[j];
+    const float cx = fmaf(B.x * e.x, e.x, K.x), cy = fmaf(B.y * e.y, e.y, K.y);
+    gp = make_float2(fmaf(A.x, e.x, cx), fmaf(A.y, e.y, cy));
+    gm = make_float2(fmaf(-A.x, e.x, cx), fmaf(-A.y, e.y, cy));
+}
+
+// c.u of the five pairs with c_y = +1: c = (0,1,0), (1,1,0), (-1,1,0), (0,1,1), (0,1,-1)
+__device__ __forceinline__ F2 ye2(const NC2 &nc, int k, int j) {
+    return k == 0 ? nc.V[j]
+                  : (k == 1 ? add2(nc.U[j], nc.V[j])
+                            : (k == 2 ? sub2(nc.V[j], nc.U[j])
+                                      : (k == 3 ? add2(nc.V[j], nc.W[j]) : sub2(nc.V[j], nc.W[j]))));
+}
+
+// shift a lane-distributed row by +1 (g[x] <- g[x-1]) or -1 (g[x] <- g[x+1]);
+// the node crossing the lane boundary comes from the neighbouring lane
+__device__ __forceinline__ void shift2(F2 (&g)[2], int dir, int lane) {
+    if (dir > 0) {
+        const float e = __shfl_sync(FULL, g[1].y, (lane + 31) & 31);
+        g[1] = make_float2(g[0].y, g[1].x);
+        g[0] = make_float2(e, g[0].x);
+    } else {
+        const float e = __shfl_sync(FULL, g[0].x, (lane + 1) & 31);
+        g[0] = make_float2(g[0].y, g[1].x);
+        g[1] = make_float2(g[1].y, e);
+    }
+}
+
+__device__ __forceinline__ void st_slot2(float *slot, const F2 (&o)[2], int lane) {
+    *reinterpret_cast<float4 *>(slot + spos(lane, 0)) = make_float4(o[0].x, o[0].y, o[1].x, o[1].y);
+}
+__device__ __forceinline__ void ld_slot2(const float *slot, F2 (&o)[2], int lane) {
+    const float4 t = *reinterpret_cast<const float4 *>(slot + spos(lane, 0));
+    o[0] = make_float2(t.x, t.y);
+    o[1] = make_float2(t.z, t.w);
+}
+
+// deposit one node's link value g of c = (cx, cy, cz) into a receiver's (d, jx, jy, jz)
+// (as dep() in tile_common.cuh; c_z = +1 arrivals skip jz)
+__device__ __forceinline__ float &ac(F2 (&a)[2][4], int i, int c) {
+    return (i & 1) ? a[i >> 1][c].y : a[i >> 1][c].x;
+}
+__device__ __forceinline__ void dep1(F2 (&a)[2][4], int i, float g, int cx, int cy, int cz) {
+    ac(a, i, 0) += g;
+    if (cx > 0) ac(a, i, 1) += g;
+    if (cx < 0) ac(a, i, 1) -= g;
+    if (cy > 0) ac(a, i, 2) += g;
+    if (cy < 0) ac(a, i, 2) -= g;
+    if (cz < 0) ac(a, i, 3) -= g;
+}
 
 // Row-crossing values of one half row, computed once per link pair and sent to
 // the receivers above (up, c_y = +1; when UP) and below (down, c_y = -1; when DN),
@@ -62,85 +158,83 @@ using NC = NodeConst<VXH>;
 // The boundary lanes leave out the x-shifted diagonal that would cross into the
 // other half and record their own boundary value in `edge`.
 template <int NH, int MODE>
-__device__ __forceinline__ void send_rows(const NC &nc, float c4, float *ubase, float *dbase, bool UP,
-                                          bool DN, float *edge, int lane) {
+__device__ __forceinline__ void send_rows(const NC2 &nc, float *ubase, float *dbase, bool UP, bool DN,
+                                          float *edge, int lane) {
     constexpr int XSLOT = HG<NH>::XSLOT;
     const bool l0 = lane == 0 && NH == 2, l31 = lane == 31 && NH == 2;
     if (MODE == MID) {
-        float u0[VXH], u1[VXH], d0[VXH], d1[VXH];
-        {  // k = 0: c = (0,1,0), -c = (0,-1,0)
+        F2 u0[2], u1[2], d0[2], d1[2];
 #pragma unroll
-            for (int i = 0; i < VXH; ++i) pair_g(nc, i, ypair_e(nc, 0, i), false, u0[i], d0[i]);
-        }
+        for (int j = 0; j < 2; ++j) pair2(nc, j, ye2(nc, 0, j), false, u0[j], d0[j]);  // c = (0,1,0)
         {  // k = 1: c = (1,1,0) [up: receiver x <- x-1]; -c = (-1,-1,0) [down: x <- x+1]
-            float gp[VXH], gm[VXH];
+            F2 gp[2], gm[2];
 #pragma unroll
-            for (int i = 0; i < VXH; ++i) pair_g(nc, i, ypair_e(nc, 1, i), true, gp[i], gm[i]);
+            for (int j = 0; j < 2; ++j) pair2(nc, j, ye2(nc, 1, j), true, gp[j], gm[j]);
             if (UP) {
-                if (NH == 2) st_shared_if(edge + E_UP1, gp[VXH - 1], l31);
-                xshift(gp, 1, lane);
-                gp[0] = l0 ? 0.f : gp[0];
+                if (NH == 2) st_shared_if(edge + E_UP1, gp[1].y, l31);
+                shift2(gp, 1, lane);
+                gp[0].x = l0 ? 0.f : gp[0].x;
             }
             if (DN) {
-                if (NH == 2) st_shared_if(edge + E_DN1, gm[0], l0);
-                xshift(gm, -1, lane);
-                gm[VXH - 1] = l31 ? 0.f : gm[VXH - 1];
+                if (NH == 2) st_shared_if(edge + E_DN1, gm[0].x, l0);
+                shift2(gm, -1, lane);
+                gm[1].y = l31 ? 0.f : gm[1].y;
             }
 #pragma unroll
-            for (int i = 0; i < VXH; ++i) {
-                u0[i] += gp[i];
-                u1[i] = gp[i];
-                d0[i] += gm[i];
-                d1[i] = -gm[i];
+            for (int j = 0; j < 2; ++j) {
+                u0[j] = add2(u0[j], gp[j]);
+                u1[j] = gp[j];
+                d0[j] = add2(d0[j], gm[j]);
+                d1[j] = neg2(gm[j]);
             }
         }
         {  // k = 2: c = (-1,1,0) [up: x <- x+1]; -c = (1,-1,0) [down: x <- x-1]
-            float gp[VXH], gm[VXH];
+            F2 gp[2], gm[2];
 #pragma unroll
-            for (int i = 0; i < VXH; ++i) pair_g(nc, i, ypair_e(nc, 2, i), true, gp[i], gm[i]);
+            for (int j = 0; j < 2; ++j) pair2(nc, j, ye2(nc, 2, j), true, gp[j], gm[j]);
             if (UP) {
-                if (NH == 2) st_shared_if(edge + E_UP2, gp[0], l0);
-                xshift(gp, -1, lane);
-                gp[VXH - 1] = l31 ? 0.f : gp[VXH - 1];
+                if (NH == 2) st_shared_if(edge + E_UP2, gp[0].x, l0);
+                shift2(gp, -1, lane);
+                gp[1].y = l31 ? 0.f : gp[1].y;
             }
             if (DN) {
-                if (NH == 2) st_shared_if(edge + E_DN2, gm[VXH - 1], l31);
-                xshift(gm, 1, lane);
-                gm[0] = l0 ? 0.f : gm[0];
+                if (NH == 2) st_shared_if(edge + E_DN2, gm[1].y, l31);
+                shift2(gm, 1, lane);
+                gm[0].x = l0 ? 0.f : gm[0].x;
             }
 #pragma unroll
-            for (int i = 0; i < VXH; ++i) {
-                u0[i] += gp[i];
-                u1[i] -= gp[i];
-                d0[i] += gm[i];
-                d1[i] += gm[i];
+            for (int j = 0; j < 2; ++j) {
+                u0[j] = add2(u0[j], gp[j]);
+                u1[j] = sub2(u1[j], gp[j]);
+                d0[j] = add2(d0[j], gm[j]);
+                d1[j] = add2(d1[j], gm[j]);
             }
         }
         if (UP) {
-            st_slot(ubase + 0 * XSLOT, u0, lane);
-            st_slot(ubase + 1 * XSLOT, u1, lane);
+            st_slot2(ubase + 0 * XSLOT, u0, lane);
+            st_slot2(ubase + 1 * XSLOT, u1, lane);
         }
         if (DN) {
-            st_slot(dbase + 0 * XSLOT, d0, lane);
-            st_slot(dbase + 1 * XSLOT, d1, lane);
+            st_slot2(dbase + 0 * XSLOT, d0, lane);
+            st_slot2(dbase + 1 * XSLOT, d1, lane);
         }
     }
     // k = 3: c = (0,1,1), -c = (0,-1,-1); k = 4: c = (0,1,-1), -c = (0,-1,1)
     // slot 2 (c_z = +1): up <- c of k = 3, down <- -c of k = 4
     // slot 3 (c_z = -1): up <- c of k = 4, down <- -c of k = 3
     {
-        float gp[VXH], gm[VXH];
+        F2 gp[2], gm[2];
 #pragma unroll
-        for (int i = 0; i < VXH; ++i) pair_g(nc, i, ypair_e(nc, 3, i), true, gp[i], gm[i]);
-        if (UP && MODE != LAST) st_slot(ubase + 2 * XSLOT, gp, lane);
-        if (DN && MODE != FIRST) st_slot(dbase + 3 * XSLOT, gm, lane);
+        for (int j = 0; j < 2; ++j) pair2(nc, j, ye2(nc, 3, j), true, gp[j], gm[j]);
+        if (UP && MODE != LAST) st_slot2(ubase + 2 * XSLOT, gp, lane);
+        if (DN && MODE != FIRST) st_slot2(dbase + 3 * XSLOT, gm, lane);
     }
     {
-        float gp[VXH], gm[VXH];
+        F2 gp[2], gm[2];
 #pragma unroll
-        for (int i = 0; i < VXH; ++i) pair_g(nc, i, ypair_e(nc, 4, i), true, gp[i], gm[i]);
-        if (UP && MODE != FIRST) st_slot(ubase + 3 * XSLOT, gp, lane);
-        if (DN && MODE != LAST) st_slot(dbase + 2 * XSLOT, gm, lane);
+        for (int j = 0; j < 2; ++j) pair2(nc, j, ye2(nc, 4, j), true, gp[j], gm[j]);
+        if (UP && MODE != FIRST) st_slot2(ubase + 3 * XSLOT, gp, lane);
+        if (DN && MODE != LAST) st_slot2(dbase + 2 * XSLOT, gm, lane);
     }
 }
 
@@ -152,86 +246,82 @@ __device__ __forceinline__ constexpr bool need_m(int mode, int cz) {
     return mode == MID || (mode == FIRST ? cz < 0 : cz > 0);
 }
 
+using Acc = F2[3][2][4];  // [plane behind / current / ahead][node pair][d, jx, jy, jz]
+
 template <int NH, int MODE, typename T>
-__device__ __forceinline__ void phase_a(float (&acc)[3][VXH][4], const T *stg, float *xbuf, float *ebuf,
-                                        const TiledParams &p, int lane, int row, int half) {
+__device__ __forceinline__ void phase_a(Acc &acc, const T *stg, float *xbuf, float *ebuf, const TiledParams &p,
+                                        int lane, int row, int half) {
     constexpr int PM = 0, P0 = 1, PP = 2;
     constexpr int RL = HG<NH>::RL, XDIR = HG<NH>::XDIR;
     float *up = xbuf + half * HALF, *dn = xbuf + XDIR + half * HALF;
     {
-        NC nc;
-        node_consts(nc, stg + (row + 1) * RL + half * HALF, TROWS * RL, lane, p.s18);
+        NC2 nc;
+        node_consts2(nc, stg + (row + 1) * RL + half * HALF, TROWS * RL, lane, p.s18);
         float *edge = NH == 2 ? ebuf + ((row + 1) * 2 + half) * NEDGE : nullptr;
 #pragma unroll
-        for (int i = 0; i < VXH; ++i) {
-            float gp, gm;
-            pair_g(nc, i, nc.W[i], false, gp, gm);  // (0,0,+1) / (0,0,-1)
+        for (int j = 0; j < 2; ++j) {
+            F2 gp, gm;
+            pair2(nc, j, nc.W[j], false, gp, gm);  // (0,0,+1) / (0,0,-1)
             if (MODE == MID) {
-                acc[P0][i][3] = acc[P0][i][0];    // jz so far = d so far (c_z = +1 arrivals)
-                acc[P0][i][0] += 6.f * nc.K1[i];  // rest link: w_0 K = K/3
-                const float ar = p.a_s * nc.A1[i];  // a rho (post-combine)
-                acc[P0][i][1] = fmaf(ar, nc.U[i], acc[P0][i][1]);
-                acc[P0][i][2] = fmaf(ar, nc.V[i], acc[P0][i][2]);
-                acc[P0][i][3] = fmaf(ar, nc.W[i], acc[P0][i][3]);
+                acc[P0][j][3] = acc[P0][j][0];                       // jz so far = d so far
+                acc[P0][j][0] = fma2(b2(6.f), nc.K1[j], acc[P0][j][0]);  // rest link: w_0 K = K/3
+                const F2 ar = mul2(b2(p.a_s), nc.A1[j]);             // a rho (post-combine)
+                acc[P0][j][1] = fma2(ar, nc.U[j], acc[P0][j][1]);
+                acc[P0][j][2] = fma2(ar, nc.V[j], acc[P0][j][2]);
+                acc[P0][j][3] = fma2(ar, nc.W[j], acc[P0][j][3]);
             }
-            if (MODE != LAST) acc[PP][i][0] += gp;
-            if (MODE != FIRST) dep(acc[PM][i], gm, 0, 0, -1);
+            if (MODE != LAST) acc[PP][j][0] = add2(acc[PP][j][0], gp);
+            if (MODE != FIRST) {
+                acc[PM][j][0] = add2(acc[PM][j][0], gm);
+                acc[PM][j][3] = sub2(acc[PM][j][3], gm);
+            }
         }
 #pragma unroll
         for (int cz = -1; cz <= 1; ++cz) {
             const bool np = need_p(MODE, cz), nm = need_m(MODE, cz);
             if (!np && !nm) continue;
-            float eP = 0.f, eM = 0.f;
+            F2 gp[2], gm[2];
 #pragma unroll
-            for (int i = 0; i < VXH; ++i) {
-                float gp, gm;
-                const float e = cz == 0 ? nc.U[i] : (cz > 0 ? nc.U[i] + nc.W[i] : nc.U[i] - nc.W[i]);
-                pair_g(nc, i, e, cz != 0, gp, gm);
-                if (np) {
-                    if (i + 1 < VXH)
-                        dep(acc[pl<PM, P0, PP>(cz)][i + 1], gp, 1, 0, cz);
-                    else
-                        eP = gp;
-                }
-                if (nm) {
-                    if (i > 0)
-                        dep(acc[pl<PM, P0, PP>(-cz)][i - 1], gm, -1, 0, -cz);
-                    else
-                        eM = gm;
-                }
+            for (int j = 0; j < 2; ++j) {
+                const F2 e = cz == 0 ? nc.U[j] : (cz > 0 ? add2(nc.U[j], nc.W[j]) : sub2(nc.U[j], nc.W[j]));
+                pair2(nc, j, e, cz != 0, gp[j], gm[j]);
             }
-            if (np) {
+            if (np) {  // c = (1,0,cz): node i feeds node i+1
+#pragma unroll
+                for (int i = 0; i + 1 < VXH; ++i) dep1(acc[pl<PM, P0, PP>(cz)], i + 1, ndv(gp, i), 1, 0, cz);
+                const float eP = gp[1].y;
                 if (NH == 2) st_shared_if(edge + E_INP + cz + 1, eP, lane == 31);  // for the other half's lane 0
                 float rP = __shfl_sync(FULL, eP, (lane + 31) & 31);
                 if (NH == 2) rP = lane == 0 ? 0.f : rP;  // lane 0's comes from the other half (phase B)
-                dep(acc[pl<PM, P0, PP>(cz)][0], rP, 1, 0, cz);
+                dep1(acc[pl<PM, P0, PP>(cz)], 0, rP, 1, 0, cz);
             }
-            if (nm) {
+            if (nm) {  // -c: node i feeds node i-1
+#pragma unroll
+                for (int i = 1; i < VXH; ++i) dep1(acc[pl<PM, P0, PP>(-cz)], i - 1, ndv(gm, i), -1, 0, -cz);
+                const float eM = gm[0].x;
                 if (NH == 2) st_shared_if(edge + E_INM + cz + 1, eM, lane == 0);  // for the other half's lane 31
                 float rM = __shfl_sync(FULL, eM, (lane + 1) & 31);
                 if (NH == 2) rM = lane == 31 ? 0.f : rM;
-                dep(acc[pl<PM, P0, PP>(-cz)][VXH - 1], rM, -1, 0, -cz);
+                dep1(acc[pl<PM, P0, PP>(-cz)], VXH - 1, rM, -1, 0, -cz);
             }
         }
-        send_rows<NH, MODE>(nc, p.c4, up + (row + 1) * RL, dn + (row - 1) * RL, row + 1 < ROWS, row > 0,
-                            edge, lane);
+        send_rows<NH, MODE>(nc, up + (row + 1) * RL, dn + (row - 1) * RL, row + 1 < ROWS, row > 0, edge, lane);
     }
     if (row == 0) {  // bottom halo row y0-1 (staged row 0) feeds row 0
-        NC hc;
-        node_consts(hc, stg + half * HALF, TROWS * RL, lane, p.s18);
-        send_rows<NH, MODE>(hc, p.c4, up, nullptr, true, false, NH == 2 ? ebuf + half * NEDGE : nullptr, lane);
+        NC2 hc;
+        node_consts2(hc, stg + half * HALF, TROWS * RL, lane, p.s18);
+        send_rows<NH, MODE>(hc, up, nullptr, true, false, NH == 2 ? ebuf + half * NEDGE : nullptr, lane);
     } else if (row == ROWS - 1) {  // top halo row y0+8 (staged row 9) feeds row 7
-        NC hc;
-        node_consts(hc, stg + (TROWS - 1) * RL + half * HALF, TROWS * RL, lane, p.s18);
-        send_rows<NH, MODE>(hc, p.c4, nullptr, dn + (ROWS - 1) * RL, false, true,
+        NC2 hc;
+        node_consts2(hc, stg + (TROWS - 1) * RL + half * HALF, TROWS * RL, lane, p.s18);
+        send_rows<NH, MODE>(hc, nullptr, dn + (ROWS - 1) * RL, false, true,
                             NH == 2 ? ebuf + ((TROWS - 1) * 2 + half) * NEDGE : nullptr, lane);
     }
 }
 
 template <int NH, int MODE, typename T>
-__device__ __forceinline__ void phase_b(float (&acc)[3][VXH][4], const float *xbuf, const float *ebuf,
-                                        T *out, const TiledParams &p, int lane, int row, int half,
-                                        int col, int zfin) {
+__device__ __forceinline__ void phase_b(Acc &acc, const float *xbuf, const float *ebuf, T *out,
+                                        const TiledParams &p, int lane, int row, int half, int col, int zfin) {
     constexpr int PM = 0, P0 = 1, PP = 2;
     constexpr int RL = HG<NH>::RL, XDIR = HG<NH>::XDIR, XSLOT = HG<NH>::XSLOT;
     const float *up = xbuf + row * RL + half * HALF, *dn = xbuf + XDIR + row * RL + half * HALF;
@@ -239,37 +329,37 @@ __device__ __forceinline__ void phase_b(float (&acc)[3][VXH][4], const float *xb
     const float *e_own = ebuf + ((row + 1) * 2 + ph) * NEDGE;  // partner half, same row
     const float *e_up = ebuf + (row * 2 + ph) * NEDGE;         // partner half, row below
     const float *e_dn = ebuf + ((row + 2) * 2 + ph) * NEDGE;   // partner half, row above
-    float o[VXH];
+    F2 o[2];
     if (MODE == MID) {
         const float u1 = NH == 2 ? e_up[E_UP1] : 0.f, u2 = NH == 2 ? e_up[E_UP2] : 0.f;
         const float d1 = NH == 2 ? e_dn[E_DN1] : 0.f, d2 = NH == 2 ? e_dn[E_DN2] : 0.f;
         const bool l0 = lane == 0 && NH == 2, l31 = lane == 31 && NH == 2;
-        ld_slot(up, o, lane);  // from below, c_z = 0: d, +jy
-        o[0] += l0 ? u1 : 0.f;
-        o[VXH - 1] += l31 ? u2 : 0.f;
+        ld_slot2(up, o, lane);  // from below, c_z = 0: d, +jy
+        o[0].x += l0 ? u1 : 0.f;
+        o[1].y += l31 ? u2 : 0.f;
 #pragma unroll
-        for (int i = 0; i < VXH; ++i) {
-            acc[P0][i][0] += o[i];
-            acc[P0][i][2] += o[i];
+        for (int j = 0; j < 2; ++j) {
+            acc[P0][j][0] = add2(acc[P0][j][0], o[j]);
+            acc[P0][j][2] = add2(acc[P0][j][2], o[j]);
         }
-        ld_slot(up + XSLOT, o, lane);
-        o[0] += l0 ? u1 : 0.f;
-        o[VXH - 1] -= l31 ? u2 : 0.f;
+        ld_slot2(up + XSLOT, o, lane);
+        o[0].x += l0 ? u1 : 0.f;
+        o[1].y -= l31 ? u2 : 0.f;
 #pragma unroll
-        for (int i = 0; i < VXH; ++i) acc[P0][i][1] += o[i];
-        ld_slot(dn, o, lane);  // from above, c_z = 0: d, -jy
-        o[VXH - 1] += l31 ? d1 : 0.f;
-        o[0] += l0 ? d2 : 0.f;
+        for (int j = 0; j < 2; ++j) acc[P0][j][1] = add2(acc[P0][j][1], o[j]);
+        ld_slot2(dn, o, lane);  // from above, c_z = 0: d, -jy
+        o[1].y += l31 ? d1 : 0.f;
+        o[0].x += l0 ? d2 : 0.f;
 #pragma unroll
-        for (int i = 0; i < VXH; ++i) {
-            acc[P0][i][0] += o[i];
-            acc[P0][i][2] -= o[i];
+        for (int j = 0; j < 2; ++j) {
+            acc[P0][j][0] = add2(acc[P0][j][0], o[j]);
+            acc[P0][j][2] = sub2(acc[P0][j][2], o[j]);
         }
-        ld_slot(dn + XSLOT, o, lane);
-        o[VXH - 1] -= l31 ? d1 : 0.f;
-        o[0] += l0 ? d2 : 0.f;
+        ld_slot2(dn + XSLOT, o, lane);
+        o[1].y -= l31 ? d1 : 0.f;
+        o[0].x += l0 ? d2 : 0.f;
 #pragma unroll
-        for (int i = 0; i < VXH; ++i) acc[P0][i][1] += o[i];
+        for (int j = 0; j < 2; ++j) acc[P0][j][1] = add2(acc[P0][j][1], o[j]);
     }
     // in-row values from the other half's boundary lanes
     if (NH == 2) {
@@ -277,60 +367,66 @@ __device__ __forceinline__ void phase_b(float (&acc)[3][VXH][4], const float *xb
         for (int cz = -1; cz <= 1; ++cz) {
             if (need_p(MODE, cz)) {
                 const float v = e_own[E_INP + cz + 1];
-                dep(acc[pl<PM, P0, PP>(cz)][0], lane == 0 ? v : 0.f, 1, 0, cz);
+                dep1(acc[pl<PM, P0, PP>(cz)], 0, lane == 0 ? v : 0.f, 1, 0, cz);
             }
             if (need_m(MODE, cz)) {
                 const float v = e_own[E_INM + cz + 1];
-                dep(acc[pl<PM, P0, PP>(-cz)][VXH - 1], lane == 31 ? v : 0.f, -1, 0, -cz);
+                dep1(acc[pl<PM, P0, PP>(-cz)], VXH - 1, lane == 31 ? v : 0.f, -1, 0, -cz);
             }
         }
     }
     if (MODE != LAST) {  // c_z = +1 arrivals for the plane ahead (jz implied by d)
-        ld_slot(up + 2 * XSLOT, o, lane);
+        ld_slot2(up + 2 * XSLOT, o, lane);
 #pragma unroll
-        for (int i = 0; i < VXH; ++i) {
-            acc[PP][i][0] += o[i];
-            acc[PP][i][2] += o[i];
+        for (int j = 0; j < 2; ++j) {
+            acc[PP][j][0] = add2(acc[PP][j][0], o[j]);
+            acc[PP][j][2] = add2(acc[PP][j][2], o[j]);
         }
-        ld_slot(dn + 2 * XSLOT, o, lane);
+        ld_slot2(dn + 2 * XSLOT, o, lane);
 #pragma unroll
-        for (int i = 0; i < VXH; ++i) {
-            acc[PP][i][0] += o[i];
-            acc[PP][i][2] -= o[i];
+        for (int j = 0; j < 2; ++j) {
+            acc[PP][j][0] = add2(acc[PP][j][0], o[j]);
+            acc[PP][j][2] = sub2(acc[PP][j][2], o[j]);
         }
     }
     if (MODE != FIRST) {  // c_z = -1 arrivals complete the plane behind
-        ld_slot(up + 3 * XSLOT, o, lane);
+        ld_slot2(up + 3 * XSLOT, o, lane);
 #pragma unroll
-        for (int i = 0; i < VXH; ++i) {
-            acc[PM][i][0] += o[i];
-            acc[PM][i][2] += o[i];
-            acc[PM][i][3] -= o[i];
+        for (int j = 0; j < 2; ++j) {
+            acc[PM][j][0] = add2(acc[PM][j][0], o[j]);
+            acc[PM][j][2] = add2(acc[PM][j][2], o[j]);
+            acc[PM][j][3] = sub2(acc[PM][j][3], o[j]);
         }
-        ld_slot(dn + 3 * XSLOT, o, lane);
+        ld_slot2(dn + 3 * XSLOT, o, lane);
 #pragma unroll
-        for (int i = 0; i < VXH; ++i) {
-            acc[PM][i][0] += o[i];
-            acc[PM][i][2] -= o[i];
-            acc[PM][i][3] -= o[i];
+        for (int j = 0; j < 2; ++j) {
+            acc[PM][j][0] = add2(acc[PM][j][0], o[j]);
+            acc[PM][j][2] = sub2(acc[PM][j][2], o[j]);
+            acc[PM][j][3] = sub2(acc[PM][j][3], o[j]);
         }
         if (zfin >= 0) {
             const long long rowoff =
                 ((long long)zfin * p.ny + col * ROWS + row) * p.nx + half * HALF + lane * VXH;
             T *op = out + rowoff;
-            float r[VXH];
+            F2 r[2];
 #pragma unroll
-            for (int i = 0; i < VXH; ++i) r[i] = rcp_nr(1.f + acc[PM][i][0]);
-            st4(op, acc[PM][0][0], acc[PM][1][0], acc[PM][2][0], acc[PM][3][0]);
+            for (int j = 0; j < 2; ++j) {
+                // 1/rho: hardware approximation refined by one Newton-Raphson step
+                const F2 x = add2(b2(1.f), acc[PM][j][0]);
+                const F2 r0 = make_float2(__fdividef(1.0f, x.x), __fdividef(1.0f, x.y));
+                r[j] = fma2(r0, fma2(neg2(x), r0, b2(1.f)), r0);
+            }
+            st4(op, acc[PM][0][0].x, acc[PM][0][0].y, acc[PM][1][0].x, acc[PM][1][0].y);
 #pragma unroll
-            for (int c = 1; c < 4; ++c)
-                st4(op + c * p.fstride, acc[PM][0][c] * r[0], acc[PM][1][c] * r[1], acc[PM][2][c] * r[2],
-                    acc[PM][3][c] * r[3]);
+            for (int c = 1; c < 4; ++c) {
+                const F2 v0 = mul2(acc[PM][0][c], r[0]), v1 = mul2(acc[PM][1][c], r[1]);
+                st4(op + c * p.fstride, v0.x, v0.y, v1.x, v1.y);
+            }
         }
 #pragma unroll
-        for (int i = 0; i < VXH; ++i)
+        for (int j = 0; j < 2; ++j)
 #pragma unroll
-            for (int c = 0; c < 4; ++c) acc[PM][i][c] = 0.f;
+            for (int c = 0; c < 4; ++c) acc[PM][j][c] = b2(0.f);
     }
 }
 
@@ -360,15 +456,15 @@ __device__ __forceinline__ void issue_plane(const T *in, const TiledParams &p, i
     }
 }
 
-__device__ __forceinline__ void rotate(float (&acc)[3][VXH][4]) {
+__device__ __forceinline__ void rotate(Acc &acc) {
 #pragma unroll
-    for (int i = 0; i < VXH; ++i) {
+    for (int j = 0; j < 2; ++j) {
 #pragma unroll
-        for (int c = 0; c < 4; ++c) acc[0][i][c] = acc[1][i][c];
+        for (int c = 0; c < 4; ++c) acc[0][j][c] = acc[1][j][c];
 #pragma unroll
-        for (int c = 0; c < 3; ++c) acc[1][i][c] = acc[2][i][c];
+        for (int c = 0; c < 3; ++c) acc[1][j][c] = acc[2][j][c];
 #pragma unroll
-        for (int c = 0; c < 4; ++c) acc[2][i][c] = 0.f;
+        for (int c = 0; c < 4; ++c) acc[2][j][c] = b2(0.f);
     }
 }
 
@@ -401,13 +497,13 @@ __global__ void __launch_bounds__(HG<NH>::NTH, 2 / NH) k_d3q19_half(const T *__r
         pf.next();
     }
 
-    float acc[3][VXH][4];
+    Acc acc;
 #pragma unroll
     for (int a = 0; a < 3; ++a)
 #pragma unroll
-        for (int i = 0; i < VXH; ++i)
+        for (int j = 0; j < 2; ++j)
 #pragma unroll
-            for (int c = 0; c < 4; ++c) acc[a][i][c] = 0.f;
+            for (int c = 0; c < 4; ++c) acc[a][j][c] = b2(0.f);
 
     for (int tc = 0; it.valid(); ++tc) {
         const int s = tc & 1;
@@ -423,9 +519,9 @@ __global__ void __launch_bounds__(HG<NH>::NTH, 2 / NH) k_d3q19_half(const T *__r
 #pragma unroll
                 for (int a = 0; a < 3; ++a)
 #pragma unroll
-                    for (int i = 0; i < VXH; ++i)
+                    for (int j = 0; j < 2; ++j)
 #pragma unroll
-                        for (int c = 0; c < 4; ++c) acc[a][i][c] = 0.f;
+                        for (int c = 0; c < 4; ++c) acc[a][j][c] = b2(0.f);
                 phase_a<NH, FIRST>(acc, stage, xbuf, ebuf, p, lane, row, half);
             } else {
                 phase_a<NH, LAST>(acc, stage, xbuf, ebuf, p, lane, row, half);
@@ -457,9 +553,9 @@ __global__ void __launch_bounds__(HG<NH>::NTH, 2 / NH) k_d3q19_half(const T *__r
 #pragma unroll
             for (int a = 1; a < 3; ++a)
 #pragma unroll
-                for (int i = 0; i < VXH; ++i)
+                for (int j = 0; j < 2; ++j)
 #pragma unroll
-                    for (int c = 0; c < 4; ++c) acc[a][i][c] = 0.f;
+                    for (int c = 0; c < 4; ++c) acc[a][j][c] = b2(0.f);
         }
         it.next();
     }
