@@ -103,9 +103,16 @@ enum {
                                      first CTA leaves without arriving at the barrier after
                                      this step (-1 = never), so the other CTAs' bounded
                                      waits run out and lwacm_sync reports LWACM_E_TIMEOUT */
-    LWACM_OPT_FORCE_FIELD = 12    /* 1 = reserve room in the workspace for a per-node
+    LWACM_OPT_FORCE_FIELD = 12,   /* 1 = reserve room in the workspace for a per-node
                                      acceleration field (lwacm_set_force_field); only
                                      before lwacm_bind; single-domain contexts only */
+    LWACM_OPT_BATCH_TILE = 13     /* batched contexts: how the domains are cut into CTA
+                                     tiles. 0 (default) = runs of 256 consecutive nodes,
+                                     one thread per node, every lattice; 1..6 = 2D tiles
+                                     of 30x6, 30x14, 62x6, 30x30, 62x14, 126x6 nodes, D2Q9
+                                     only (LWACM_E_UNSUPPORTED otherwise), with the link
+                                     values computed once per node and exchanged in
+                                     shared memory. Any time; lwacm_autotune picks one. */
 };
 
 /* Create a single-domain context.

@@ -13,6 +13,14 @@
 //                       bounded number of times; a CTA that gives up sets the
 //                       device error word to 2 and returns, so a missing arrival
 //                       ends the launch instead of hanging it.
+//
+// D2Q9 domains can instead be cut into 2D tiles of TW x TH nodes (shape chosen per
+// context, by option or by the autotuner). A CTA of (TW+2) x (TH+2) threads takes
+// one tile plus a one-node frame: every thread loads its node, computes the
+// node's eight moving link values once (pre-combining, Eq. ACM2.0b(a)) and leaves
+// them in shared memory; after a barrier each interior thread gathers the eight
+// values arriving from its neighbours (streaming, Eq. ACM2.0b(b)) and forms the new
+// moments (post-combining, Eq. ACM2.0b(c)).
 #include <cooperative_groups.h>
 
 #include "launch.h"
@@ -57,6 +65,70 @@ __device__ __forceinline__ void tile_update(const T *__restrict__ in, T *__restr
     const int y = (int)(r % dm.ny);
     const int z = (int)(r / dm.ny);
     node_update<Q, false>(in + dm.off, out + dm.off, p, x, y, z);
+}
+
+// ---- 2D tiles (D2Q9) -------------------------------------------------------------
+// link order of Lat<9>: 1 (1,0) 2 (-1,0) 3 (0,1) 4 (0,-1) 5 (1,1) 6 (-1,-1) 7 (1,-1) 8 (-1,1)
+constexpr int kShapes[][2] = {{0, 0}, {30, 6}, {30, 14}, {62, 6}, {30, 30}, {62, 14}, {126, 6}};
+constexpr int kNumShapes = sizeof(kShapes) / sizeof(kShapes[0]);
+
+template <int TW, int TH, typename T>
+__device__ __forceinline__ void tile2_update(const T *__restrict__ in, T *__restrict__ out, const BatchParams &bp,
+                                             long long t, float (*G)[(TW + 2) * (TH + 2)]) {
+    constexpr int W = TW + 2;
+    const BatchTile2 tile = bp.tiles2[t];
+    const BatchDomain dm = bp.doms[tile.dom];
+    const int tx = threadIdx.x % W, ty = threadIdx.x / W;
+    int x = tile.x0 + tx - 1, y = tile.y0 + ty - 1;
+    x %= dm.nx;
+    if (x < 0) x += dm.nx;
+    y %= dm.ny;
+    if (y < 0) y += dm.ny;
+    const long long k = dm.off + (long long)y * dm.nx + x;
+    const float d = ldf(in + k), u = ldf(in + bp.fstride + k), v = ldf(in + 2 * bp.fstride + k);
+    const float rho = 1.f + d;
+    const float K = fmaf(-1.5f * rho, fmaf(u, u, v * v), d);  // d - 3/2 rho |u|^2
+    const float nu = dm.s * (1.f / 18.f);
+    {
+        // pair (c, -c) with e = c.u: w (K + 9/2 rho e^2) +- w rho s e
+        const float a9 = rho * nu * 2.f, b9 = rho * 0.5f, k9 = K * (1.f / 9.f);        // axis, w = 1/9
+        const float a36 = rho * nu * 0.5f, b36 = rho * 0.125f, k36 = K * (1.f / 36.f);  // diagonal, w = 1/36
+        const float e[4] = {u, v, u + v, u - v};
+#pragma unroll
+        for (int p = 0; p < 4; ++p) {
+            const bool dg = p >= 2;
+            const float cm = fmaf((dg ? b36 : b9) * e[p], e[p], dg ? k36 : k9);
+            const float A = dg ? a36 : a9;
+            G[2 * p][threadIdx.x] = fmaf(A, e[p], cm);
+            G[2 * p + 1][threadIdx.x] = fmaf(-A, e[p], cm);
+        }
+    }
+    __syncthreads();
+    const int xi = tile.x0 + tx - 1, yi = tile.y0 + ty - 1;
+    if (tx >= 1 && tx <= TW && ty >= 1 && ty <= TH && xi < dm.nx && yi < dm.ny) {
+        const int tid = (int)threadIdx.x;
+        // value arriving along c from the neighbour at (tx - cx, ty - cy)
+#define LW_IN(i, cx, cy) G[(i) - 1][tid - (cx) - (cy) * W]
+        const float g1 = LW_IN(1, 1, 0), g2 = LW_IN(2, -1, 0), g3 = LW_IN(3, 0, 1), g4 = LW_IN(4, 0, -1);
+        const float g5 = LW_IN(5, 1, 1), g6 = LW_IN(6, -1, -1), g7 = LW_IN(7, 1, -1), g8 = LW_IN(8, -1, 1);
+#undef LW_IN
+        const float dd = fmaf(4.f / 9.f, K, ((g1 + g2) + (g3 + g4)) + ((g5 + g6) + (g7 + g8)));
+        const float ar = dm.a * rho;
+        const float jx = fmaf(ar, u, (g1 - g2) + ((g5 - g6) + (g7 - g8)));
+        const float jy = fmaf(ar, v, (g3 - g4) + ((g5 - g6) - (g7 - g8)));
+        const float rn = 1.f + dd;
+        stf(out + k, dd);
+        stf(out + bp.fstride + k, jx / rn);
+        stf(out + 2 * bp.fstride + k, jy / rn);
+    }
+    __syncthreads();  // G is rewritten by the next tile
+}
+
+template <int TW, int TH, typename T>
+__global__ void __launch_bounds__((TW + 2) * (TH + 2)) k_batch_tiles(const T *__restrict__ in, T *__restrict__ out,
+                                                                    BatchParams bp) {
+    __shared__ float G[8][(TW + 2) * (TH + 2)];
+    for (long long t = blockIdx.x; t < bp.ntiles; t += gridDim.x) tile2_update<TW, TH, T>(in, out, bp, t, G);
 }
 
 template <int Q, typename T>
@@ -112,6 +184,83 @@ __global__ void __launch_bounds__(kTile) k_batch_persistent(T *buf0, T *buf1, Ba
     }
 }
 
+template <int TW, int TH, typename T>
+__global__ void __launch_bounds__((TW + 2) * (TH + 2)) k_batch_tiles_persistent(T *buf0, T *buf1, BatchParams bp,
+                                                                               long long nsteps, int parity) {
+    __shared__ float G[8][(TW + 2) * (TH + 2)];
+    for (long long s = 0; s < nsteps; ++s) {
+        const int cur = (int)((parity + s) & 1);
+        const T *in = cur ? buf1 : buf0;
+        T *out = cur ? buf0 : buf1;
+        for (long long t = blockIdx.x; t < bp.ntiles; t += gridDim.x) tile2_update<TW, TH, T>(in, out, bp, t, G);
+        if (s + 1 < nsteps) {
+            if (bp.withhold_step == s && blockIdx.x == 0) return;
+            if (!grid_barrier(bp, (unsigned)(s + 1))) return;
+        }
+    }
+}
+
+// occupancy-limited grid of a kernel: CTAs per SM x SMs, cached per kernel
+template <typename K>
+static int max_grid(K kern, int threads, int *cache) {
+    if (*cache == 0) {
+        int dev = 0, sms = 0, per = 0;
+        if (cudaGetDevice(&dev) != cudaSuccess ||
+            cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess ||
+            cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, kern, threads, 0) != cudaSuccess)
+            return 0;
+        *cache = per * sms;
+    }
+    return *cache;
+}
+
+template <int TW, int TH, typename T>
+cudaError_t tiles_t(const void *in, void *out, void *b0, void *b1, const BatchParams &bp, long long nsteps,
+                    int parity, bool persistent, cudaStream_t st) {
+    constexpr int NT = (TW + 2) * (TH + 2);
+    if (!persistent) {
+        static int cap = 0;
+        const int g = max_grid(k_batch_tiles<TW, TH, T>, NT, &cap);
+        if (g < 1) return cudaErrorNotSupported;
+        const long long grid = bp.ntiles < 4LL * g ? bp.ntiles : 4LL * g;
+        k_batch_tiles<TW, TH, T><<<(unsigned)grid, NT, 0, st>>>((const T *)in, (T *)out, bp);
+        return cudaGetLastError();
+    }
+    static int cap = 0;
+    const int g = max_grid(k_batch_tiles_persistent<TW, TH, T>, NT, &cap);
+    if (g < 1) return cudaErrorNotSupported;
+    const long long grid = bp.ntiles < g ? bp.ntiles : g;
+    T *p0 = (T *)b0, *p1 = (T *)b1;
+    BatchParams q = bp;
+    void *args[] = {&p0, &p1, &q, &nsteps, &parity};
+    return cudaLaunchCooperativeKernel((const void *)k_batch_tiles_persistent<TW, TH, T>, dim3((unsigned)grid),
+                                       dim3(NT), args, 0, st);
+}
+
+template <typename T>
+cudaError_t tiles_dispatch(const void *in, void *out, void *b0, void *b1, const BatchParams &bp, long long nsteps,
+                           int parity, bool persistent, cudaStream_t st) {
+    switch (bp.shape) {
+        case 1: return tiles_t<30, 6, T>(in, out, b0, b1, bp, nsteps, parity, persistent, st);
+        case 2: return tiles_t<30, 14, T>(in, out, b0, b1, bp, nsteps, parity, persistent, st);
+        case 3: return tiles_t<62, 6, T>(in, out, b0, b1, bp, nsteps, parity, persistent, st);
+        case 4: return tiles_t<30, 30, T>(in, out, b0, b1, bp, nsteps, parity, persistent, st);
+        case 5: return tiles_t<62, 14, T>(in, out, b0, b1, bp, nsteps, parity, persistent, st);
+        case 6: return tiles_t<126, 6, T>(in, out, b0, b1, bp, nsteps, parity, persistent, st);
+    }
+    return cudaErrorInvalidValue;
+}
+
+cudaError_t tiles_storage(int storage, const void *in, void *out, void *b0, void *b1, const BatchParams &bp,
+                          long long nsteps, int parity, bool persistent, cudaStream_t st) {
+    switch (storage) {
+        case STORE_F32: return tiles_dispatch<float>(in, out, b0, b1, bp, nsteps, parity, persistent, st);
+        case STORE_BF16: return tiles_dispatch<__nv_bfloat16>(in, out, b0, b1, bp, nsteps, parity, persistent, st);
+        case STORE_F16: return tiles_dispatch<__half>(in, out, b0, b1, bp, nsteps, parity, persistent, st);
+    }
+    return cudaErrorInvalidValue;
+}
+
 template <int Q, typename T>
 cudaError_t persistent_t(void *b0, void *b1, const BatchParams &bp, long long nsteps, int parity,
                          cudaStream_t st) {
@@ -156,9 +305,24 @@ cudaError_t step_t(int Q, const void *in, void *out, const BatchParams &bp, cuda
 }  // namespace
 
 int batch_tile() { return kTile; }
+int batch_shapes() { return kNumShapes; }
+void batch_shape(int k, int *tw, int *th) {
+    const int i = k >= 0 && k < kNumShapes ? k : 0;
+    *tw = kShapes[i][0];
+    *th = kShapes[i][1];
+}
+bool batch_shape_supported(int Q, int storage, int k) {
+    if (k == 0) return true;
+    return Q == 9 && k > 0 && k < kNumShapes &&
+           (storage == STORE_F32 || storage == STORE_BF16 || storage == STORE_F16);
+}
 
 cudaError_t launch_batch_step(int Q, int storage, const void *in, void *out, const BatchParams &bp,
                               cudaStream_t st) {
+    if (bp.shape > 0) {
+        if (!batch_shape_supported(Q, storage, bp.shape)) return cudaErrorInvalidValue;
+        return tiles_storage(storage, in, out, nullptr, nullptr, bp, 1, 0, false, st);
+    }
     switch (storage) {
         case STORE_F32: return step_t<float>(Q, in, out, bp, st);
         case STORE_BF16: return step_t<__nv_bfloat16>(Q, in, out, bp, st);
@@ -171,6 +335,10 @@ cudaError_t launch_batch_persistent(int Q, int storage, void *buf0, void *buf1, 
                                     long long nsteps, int parity, cudaStream_t st) {
     cudaError_t e = cudaMemsetAsync(bp.bar_count, 0, 2 * sizeof(unsigned), st);  // count, generation
     if (e != cudaSuccess) return e;
+    if (bp.shape > 0) {
+        if (!batch_shape_supported(Q, storage, bp.shape)) return cudaErrorInvalidValue;
+        return tiles_storage(storage, nullptr, nullptr, buf0, buf1, bp, nsteps, parity, true, st);
+    }
     if (Q == 9) {
         switch (storage) {
             case STORE_F32: return persistent_t<9, float>(buf0, buf1, bp, nsteps, parity, st);

@@ -51,9 +51,16 @@ struct BatchTile {
     int dom, pad;
     long long start;   // packed index of the tile's first node
 };
+// 2D tile of a D2Q9 domain: interior nodes [x0, x0 + TW) x [y0, y0 + TH) (clipped
+// to the domain), for the tile shapes of batch_shape()
+struct BatchTile2 {
+    int dom, x0, y0, pad;
+};
 struct BatchParams {
     const BatchDomain *doms;
     const BatchTile *tiles;
+    const BatchTile2 *tiles2;  // same storage as tiles, used when shape > 0
+    int shape;                 // 0: 1D tiles of batch_tile() nodes; k > 0: 2D shape k
     long long ntiles;
     long long fstride;
     unsigned *bar_count;  // followed by the barrier generation word
@@ -62,6 +69,11 @@ struct BatchParams {
     long long withhold_step;  // test hook: CTA 0 skips the barrier after this step (-1: never)
 };
 int batch_tile();
+// 2D tile shapes of the D2Q9 batched kernel (interior width x height); shape 0 is
+// the 1D tiling. batch_shapes() is the number of shapes including 0.
+int batch_shapes();
+void batch_shape(int k, int *tw, int *th);
+bool batch_shape_supported(int Q, int storage, int k);
 cudaError_t launch_batch_step(int Q, int storage, const void *in, void *out, const BatchParams &bp,
                               cudaStream_t st);
 cudaError_t launch_batch_persistent(int Q, int storage, void *buf0, void *buf1, const BatchParams &bp,

@@ -55,7 +55,10 @@ struct lwacm_ctx {
     // batched domains (nbatch > 0): packed one after the other
     int nbatch = 0;
     std::vector<BatchDomain> doms;
-    std::vector<BatchTile> tiles;
+    std::vector<BatchTile> tiles;    // 1D tiles (shape 0)
+    std::vector<BatchTile2> tiles2;  // 2D tiles of the current shape (shape > 0)
+    int batch_shape = 0;
+    size_t tiles_cap = 0;  // table entries reserved in the workspace (largest over the shapes)
     size_t off_doms = 0, off_tiles = 0, off_bar = 0;
     int batch_mode = 0;  // 0: one launch per step (graphs), 1: one persistent launch
     long long withhold = -1;
@@ -110,7 +113,7 @@ void layout(lwacm_ctx *c) {
         c->off_doms = off;
         off = align_up(off + sizeof(BatchDomain) * c->doms.size(), kAlign);
         c->off_tiles = off;
-        off = align_up(off + sizeof(BatchTile) * c->tiles.size(), kAlign);
+        off = align_up(off + 16 * c->tiles_cap, kAlign);
         c->off_bar = off;
         off = align_up(off + 16, kAlign);
     }
@@ -166,7 +169,13 @@ void drop_graphs(lwacm_ctx *c) {
 bool choose_kernel(lwacm_ctx *c) {
     if (c->nbatch) {
         c->kernel = 4;
-        c->kname = c->batch_mode ? "batch_persistent" : "batch_step";
+        static const char *names[2][8] = {
+            {"batch_step", "batch_tiles30x6_step", "batch_tiles30x14_step", "batch_tiles62x6_step",
+             "batch_tiles30x30_step", "batch_tiles62x14_step", "batch_tiles126x6_step", "batch_step"},
+            {"batch_persistent", "batch_tiles30x6_persistent", "batch_tiles30x14_persistent",
+             "batch_tiles62x6_persistent", "batch_tiles30x30_persistent", "batch_tiles62x14_persistent",
+             "batch_tiles126x6_persistent", "batch_persistent"}};
+        c->kname = names[c->batch_mode ? 1 : 0][c->batch_shape & 7];
         return c->kernel_opt == 0 || c->kernel_opt == 1;
     }
     const StepParams p = params(c);
@@ -194,11 +203,39 @@ void *bufp(lwacm_ctx *c, int b) { return c->ws + c->off_buf[b]; }
 
 size_t field_bytes(const lwacm_ctx *c) { return (size_t)c->Nal * esize(c->storage); }
 
+// 2D tiles of shape k over every domain (D2Q9): row-major within a domain
+void build_tiles2(const lwacm_ctx *c, int k, std::vector<BatchTile2> &out) {
+    out.clear();
+    int tw = 0, th = 0;
+    batch_shape(k, &tw, &th);
+    for (int b = 0; b < c->nbatch; ++b)
+        for (int y = 0; y < c->doms[b].ny; y += th)
+            for (int x = 0; x < c->doms[b].nx; x += tw) out.push_back(BatchTile2{b, x, y, 0});
+}
+
+// upload the tile table of the current shape (host tables are pageable: synchronise)
+lwacm_status upload_tiles(lwacm_ctx *c) {
+    if (c->batch_shape > 0) {
+        build_tiles2(c, c->batch_shape, c->tiles2);
+        CK(c, cudaMemcpyAsync(c->ws + c->off_tiles, c->tiles2.data(), sizeof(BatchTile2) * c->tiles2.size(),
+                              cudaMemcpyHostToDevice, c->stream),
+           "tile table");
+    } else {
+        CK(c, cudaMemcpyAsync(c->ws + c->off_tiles, c->tiles.data(), sizeof(BatchTile) * c->tiles.size(),
+                              cudaMemcpyHostToDevice, c->stream),
+           "tile table");
+    }
+    CK(c, cudaStreamSynchronize(c->stream), "sync");
+    return LWACM_OK;
+}
+
 BatchParams batch_params(lwacm_ctx *c) {
     BatchParams bp;
     bp.doms = (const BatchDomain *)(c->ws + c->off_doms);
     bp.tiles = (const BatchTile *)(c->ws + c->off_tiles);
-    bp.ntiles = (long long)c->tiles.size();
+    bp.tiles2 = (const BatchTile2 *)(c->ws + c->off_tiles);
+    bp.shape = c->batch_shape;
+    bp.ntiles = (long long)(c->batch_shape > 0 ? c->tiles2.size() : c->tiles.size());
     bp.fstride = c->Nal;
     bp.bar_count = (unsigned *)(c->ws + c->off_bar);
     bp.bar_gen = bp.bar_count + 1;
@@ -376,6 +413,19 @@ lwacm_status lwacm_batch_create(int lattice, int n, const int *nx, const int *ny
         delete c;
         return LWACM_E_NOMEM;
     }
+    try {
+        c->tiles_cap = c->tiles.size();
+        if (lattice == LWACM_D2Q9) {
+            std::vector<BatchTile2> t2;
+            for (int k = 1; k < batch_shapes(); ++k) {
+                build_tiles2(c, k, t2);
+                c->tiles_cap = std::max(c->tiles_cap, t2.size());
+            }
+        }
+    } catch (...) {
+        delete c;
+        return LWACM_E_NOMEM;
+    }
     c->nu = nu[0];
     c->nx = (int)std::min<long long>(off, 1LL << 30);
     c->ny = 1;
@@ -450,6 +500,19 @@ lwacm_status lwacm_set_option(lwacm_ctx *c, int key, double v) {
             c->batch_mode = m;
             break;
         }
+        case LWACM_OPT_BATCH_TILE: {
+            const int k = (int)v;
+            if (!c->nbatch) return fail(c, LWACM_E_STATE, "not a batched context");
+            if (k < 0 || k >= batch_shapes() || (double)k != v) return fail(c, LWACM_E_ARG, "unknown tile shape");
+            if (!batch_shape_supported(c->Q, c->storage, k))
+                return fail(c, LWACM_E_UNSUPPORTED, "2D tile shapes are for D2Q9 ensembles");
+            c->batch_shape = k;
+            if (c->bound) {
+                const lwacm_status ts = upload_tiles(c);
+                if (ts != LWACM_OK) return ts;
+            }
+            break;
+        }
         case LWACM_OPT_FORCE_FIELD: {
             const int r = (int)v;
             if (r != 0 && r != 1) return fail(c, LWACM_E_ARG, "force field option must be 0 or 1");
@@ -497,10 +560,9 @@ lwacm_status lwacm_bind(lwacm_ctx *c, void *ws, size_t bytes, void *stream) {
         CK(c, cudaMemcpyAsync(c->ws + c->off_doms, c->doms.data(), sizeof(BatchDomain) * c->doms.size(),
                               cudaMemcpyHostToDevice, c->stream),
            "domain table");
-        CK(c, cudaMemcpyAsync(c->ws + c->off_tiles, c->tiles.data(), sizeof(BatchTile) * c->tiles.size(),
-                              cudaMemcpyHostToDevice, c->stream),
-           "tile table");
         CK(c, cudaStreamSynchronize(c->stream), "sync");  // the host tables are pageable
+        const lwacm_status ts = upload_tiles(c);
+        if (ts != LWACM_OK) return ts;
     }
     if (!choose_kernel(c)) {
         c->kernel_opt = 0;

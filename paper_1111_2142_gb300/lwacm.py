@@ -22,7 +22,9 @@ F32, BF16, F16, F64 = 0, 1, 2, 3
 DEVICE, HOST = 0, 1
 OPT_LID_X, OPT_LID_Y, OPT_LID_Z, OPT_FORCE_X, OPT_FORCE_Y, OPT_FORCE_Z = range(6)
 OPT_RHO0, OPT_STORAGE, OPT_GRAPH_CHUNK, OPT_KERNEL = 6, 7, 8, 9
-OPT_BATCH_MODE, OPT_TEST_WITHHOLD, OPT_FORCE_FIELD = 10, 11, 12
+OPT_BATCH_MODE, OPT_TEST_WITHHOLD, OPT_FORCE_FIELD, OPT_BATCH_TILE = 10, 11, 12, 13
+# 2D tile shapes of the D2Q9 batched kernel (LWACM_OPT_BATCH_TILE 1..6); 0 = 1D runs
+BATCH_TILE_SHAPES = {0: None, 1: (30, 6), 2: (30, 14), 3: (62, 6), 4: (30, 30), 5: (62, 14), 6: (126, 6)}
 
 STATUS_NAMES = {OK: "OK", E_ARG: "E_ARG", E_RANGE: "E_RANGE", E_STATE: "E_STATE",
                 E_NOMEM: "E_NOMEM", E_CUDA: "E_CUDA", E_NONFINITE: "E_NONFINITE",
@@ -326,10 +328,11 @@ class LwacmBatch(Lwacm):
     dims: list of (nx, ny) for D2Q9 or (nx, ny, nz) for D3Q19; nus: viscosities.
     Fields are packed domain after domain; set_domains / get_domains pack and
     unpack per-domain numpy arrays. mode 0: one launch per step (graphs); mode 1:
-    one persistent cooperative launch per step() call.
+    one persistent cooperative launch per step() call. tile: LWACM_OPT_BATCH_TILE
+    (0 = runs of 256 nodes; 1..6 = the 2D shapes of BATCH_TILE_SHAPES, D2Q9).
     """
 
-    def __init__(self, lattice, dims, nus, *, storage=F32, mode=0, graph_chunk=None,
+    def __init__(self, lattice, dims, nus, *, storage=F32, mode=0, tile=0, graph_chunk=None,
                  device=None, stream=None):
         lib = load()
         n = len(dims)
@@ -349,8 +352,12 @@ class LwacmBatch(Lwacm):
         self.n_nodes = self.offsets[-1]
         self.nx, self.ny, self.nz = self.n_nodes, 1, 1
         self.nu, self.bc = float(nus[0]), PERIODIC
-        self._setup(lib, h, storage, None, None, None, 0, graph_chunk, device, stream,
-                    {OPT_BATCH_MODE: mode} if mode else {})
+        extra = {}
+        if mode:
+            extra[OPT_BATCH_MODE] = mode
+        if tile:
+            extra[OPT_BATCH_TILE] = tile
+        self._setup(lib, h, storage, None, None, None, 0, graph_chunk, device, stream, extra)
 
     @property
     def shape(self):

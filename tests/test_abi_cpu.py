@@ -140,3 +140,29 @@ def test_force_field_option(lib):
     assert lib.lwacm_batch_create(9, 2, nx, ny, None, nu, 0, ctypes.byref(hb)) == lw.OK
     assert lib.lwacm_set_option(hb, lw.OPT_FORCE_FIELD, 1.0) == lw.E_UNSUPPORTED
     lib.lwacm_destroy(hb)
+
+
+def test_batch_tile_option(lib):
+    """2D tile shapes: D2Q9 ensembles only; unknown shapes refused."""
+    from paper_1111_2142_gb300 import lwacm as lw
+    nx = (ctypes.c_int * 2)(40, 9)
+    ny = (ctypes.c_int * 2)(17, 70)
+    nz = (ctypes.c_int * 2)(3, 2)
+    nu = (ctypes.c_double * 2)(0.01, 0.02)
+    h = ctypes.c_void_p()
+    assert lib.lwacm_batch_create(9, 2, nx, ny, None, nu, 0, ctypes.byref(h)) == lw.OK
+    for k in range(7):
+        assert lib.lwacm_set_option(h, lw.OPT_BATCH_TILE, float(k)) == lw.OK
+    assert lib.lwacm_set_option(h, lw.OPT_BATCH_TILE, 7.0) == lw.E_ARG
+    assert lib.lwacm_set_option(h, lw.OPT_BATCH_TILE, 1.5) == lw.E_ARG
+    assert lib.lwacm_kernel_name(h).decode() == "batch_tiles126x6_step"
+    lib.lwacm_destroy(h)
+    h3 = ctypes.c_void_p()
+    assert lib.lwacm_batch_create(19, 2, nx, ny, nz, nu, 0, ctypes.byref(h3)) == lw.OK
+    assert lib.lwacm_set_option(h3, lw.OPT_BATCH_TILE, 1.0) == lw.E_UNSUPPORTED
+    assert lib.lwacm_set_option(h3, lw.OPT_BATCH_TILE, 0.0) == lw.OK
+    lib.lwacm_destroy(h3)
+    hs = ctypes.c_void_p()
+    assert lib.lwacm_create(9, 8, 8, 1, 0.01, 0, ctypes.byref(hs)) == lw.OK
+    assert lib.lwacm_set_option(hs, lw.OPT_BATCH_TILE, 1.0) == lw.E_STATE
+    lib.lwacm_destroy(hs)

@@ -55,6 +55,48 @@ def test_batch_matches_oracle(lw, Q, mode):
     sim.close()
 
 
+@pytest.mark.parametrize("mode", [0, 1])
+@pytest.mark.parametrize("tile", [1, 2, 3, 4, 5, 6])
+def test_batch_2d_tiles_match_oracle(lw, tile, mode):
+    """D2Q9 ensembles on the 2D-tile kernel (every shape, both launch forms):
+    domains smaller and larger than a tile, ragged edges, against the oracle."""
+    dims, nus, fields = small_ensemble(9, 11, seed=80 + tile)
+    dims[0] = (1, 1)      # one node: every neighbour is itself
+    dims[1] = (131, 3)    # wider than every tile, three rows
+    fields[0] = inputs.smooth_random((1, 1), seed=5, u_amp=0.04, d_amp=0.01)
+    fields[1] = inputs.smooth_random((3, 131), seed=6, u_amp=0.04, d_amp=0.01)
+    sim = lw.LwacmBatch(9, dims, nus, mode=mode, tile=tile)
+    assert "tiles" in sim.kernel_name
+    sim.set_domains(fields)
+    T = 40
+    sim.step(T)
+    got = sim.get_domains()
+    for b in range(len(dims)):
+        ref = oracle.step(9, *fields[b], nu=nus[b], nsteps=T)
+        eu = max(float(np.max(np.abs(g - r))) for g, r in zip(got[b][1:], ref[1:])) / 0.04
+        ed = float(np.max(np.abs(got[b][0] - ref[0]))) / max(float(np.max(np.abs(ref[0]))), 3 * 0.04 ** 2)
+        assert eu < 1e-5 and ed < 1e-4, (tile, mode, b, dims[b], eu, ed)
+    sim.close()
+
+
+def test_tile_shape_switch_mid_run(lw):
+    """Changing the tile shape between steps keeps the state and the results."""
+    dims, nus, fields = small_ensemble(9, 7, seed=90)
+    ref_sim = lw.LwacmBatch(9, dims, nus)
+    ref_sim.set_domains(fields)
+    sim = lw.LwacmBatch(9, dims, nus, tile=2)
+    sim.set_domains(fields)
+    for k, shape in enumerate((2, 0, 5, 1)):
+        sim.set_option(lw.OPT_BATCH_TILE, shape)
+        sim.step(9)
+        ref_sim.step(9)
+    a, b = sim.get_fields(), ref_sim.get_fields()
+    for x, y in zip(a, b):
+        assert float(np.max(np.abs(x - y))) < 1e-6
+    sim.close()
+    ref_sim.close()
+
+
 def test_persistent_equals_per_step(lw):
     dims, nus, fields = small_ensemble(9, 9, seed=70)
     out = []
