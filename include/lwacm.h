@@ -248,6 +248,29 @@ lwacm_status lwacm_sync(lwacm_ctx *ctx);
  * The string is owned by the context. */
 const char *lwacm_last_error(const lwacm_ctx *ctx);
 
+/* Autotuner: measure the kernel configurations that can run this context and
+ * keep the fastest (the paper has no counterpart; Section 2.4 discusses tuning the
+ * implementation to the machine). The candidates are, for a batched context, every
+ * tile layout (LWACM_OPT_BATCH_TILE) the lattice allows times both launch forms
+ * (LWACM_OPT_BATCH_MODE); for a single domain, every interior kernel
+ * (LWACM_OPT_KERNEL 5, 3, 2, 1) that supports it. Each is timed with CUDA events over
+ * trial_steps steps (0 = 256) after a warm-up, from the rest state, on the bound
+ * stream; the call synchronises.
+ *
+ * cache_path (or NULL): a JSON file mapping a problem key (lattice, storage, boundary,
+ * shape or the ensemble's sizes and viscosities, forcing, SM count and compute
+ * capability) to the chosen configuration. On a hit nothing is timed and the
+ * recorded choice is applied; on a miss the measured choice is added (written to a
+ * temporary file renamed over the cache). report (or NULL): receives a one-line JSON
+ * record (key, "cache" or "measured", the choice, every candidate's time), cut to
+ * report_bytes.
+ *
+ * Call after lwacm_bind and before lwacm_set_fields (LWACM_E_STATE otherwise): the
+ * trial steps use the workspace and leave the fields unset. Errors: LWACM_E_ARG,
+ * LWACM_E_STATE, LWACM_E_CUDA, LWACM_E_UNSUPPORTED (no candidate ran). */
+lwacm_status lwacm_autotune(lwacm_ctx *ctx, const char *cache_path, int trial_steps, char *report,
+                            size_t report_bytes);
+
 /* Name of the interior kernel the context runs (for reports). */
 const char *lwacm_kernel_name(const lwacm_ctx *ctx);
 

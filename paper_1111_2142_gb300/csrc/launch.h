@@ -3,6 +3,8 @@
 
 #include <cuda_runtime.h>
 
+#include <string>
+
 namespace lwacm {
 
 struct StepParams;
@@ -78,6 +80,14 @@ cudaError_t launch_batch_step(int Q, int storage, const void *in, void *out, con
                               cudaStream_t st);
 cudaError_t launch_batch_persistent(int Q, int storage, void *buf0, void *buf1, const BatchParams &bp,
                                     long long nsteps, int parity, cudaStream_t st);
+
+// Autotuner cache (tune_cache.cu): the configuration measured fastest for a key.
+struct TuneChoice {
+    int kernel = 0, tile = 0, mode = 0;
+    double us = 0.0;  // microseconds per step when measured
+};
+bool tune_cache_lookup(const char *path, const std::string &key, TuneChoice *out);
+bool tune_cache_store(const char *path, const std::string &key, const TuneChoice &ch);
 
 // Half-row TMA variant of the D3Q19 kernel (nx = 256, 16 warps per CTA).
 bool half_supported(int Q, int storage, const StepParams &p);

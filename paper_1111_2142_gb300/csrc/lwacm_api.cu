@@ -4,6 +4,7 @@
 
 #include <algorithm>
 #include <cmath>
+#include <cstdint>
 #include <cstdio>
 #include <cstring>
 #include <new>
@@ -322,6 +323,80 @@ lwacm_status build_graph(lwacm_ctx *c, int parity, int chunk) {
     if (ie != cudaSuccess) return cuda_fail(c, ie, "graph instantiate");
     c->gexec[parity] = ex;
     c->gchunk[parity] = chunk;
+    return LWACM_OK;
+}
+
+// ---- autotuner helpers --------------------------------------------------------
+struct Cand {
+    int kernel, tile, mode;
+};
+
+// FNV-1a over the bytes of v
+void fnv(uint64_t &h, const void *v, size_t n) {
+    const unsigned char *p = (const unsigned char *)v;
+    for (size_t i = 0; i < n; ++i) {
+        h ^= p[i];
+        h *= 1099511628211ULL;
+    }
+}
+
+// problem key: lattice, storage, boundary, shape (or the ensemble's sizes and
+// viscosities, hashed), forcing, and the device (SM count, compute capability)
+std::string tune_key(const lwacm_ctx *c) {
+    int dev = 0, sms = 0, mj = 0, mn = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    cudaDeviceGetAttribute(&mj, cudaDevAttrComputeCapabilityMajor, dev);
+    cudaDeviceGetAttribute(&mn, cudaDevAttrComputeCapabilityMinor, dev);
+    char buf[256];
+    if (c->nbatch) {
+        uint64_t h = 1469598103934665603ULL;
+        for (const BatchDomain &d : c->doms) {
+            fnv(h, &d.nx, sizeof d.nx);
+            fnv(h, &d.ny, sizeof d.ny);
+            fnv(h, &d.nz, sizeof d.nz);
+            fnv(h, &d.s, sizeof d.s);
+        }
+        std::snprintf(buf, sizeof buf, "lattice=%d;storage=%d;batch=%d;nodes=%lld;domains=%016llx;sm=%d;cc=%d.%d",
+                      c->Q, c->storage, c->nbatch, c->N, (unsigned long long)h, sms, mj, mn);
+    } else {
+        const bool forced = c->force[0] != 0 || c->force[1] != 0 || c->force[2] != 0 || c->ff_active;
+        std::snprintf(buf, sizeof buf, "lattice=%d;storage=%d;bc=%d;nx=%d;ny=%d;nz=%d;force=%d;sm=%d;cc=%d.%d", c->Q,
+                      c->storage, c->bc, c->nx, c->ny, c->nz, forced ? 1 : 0, sms, mj, mn);
+    }
+    return buf;
+}
+
+std::vector<Cand> tune_candidates(const lwacm_ctx *c) {
+    std::vector<Cand> v;
+    if (c->nbatch) {
+        for (int k = 0; k < batch_shapes(); ++k)
+            if (batch_shape_supported(c->Q, c->storage, k))
+                for (int m = 0; m < 2; ++m) v.push_back(Cand{0, k, m});
+    } else {
+        const int ks[4] = {5, 3, 2, 1};
+        for (int k : ks) v.push_back(Cand{k, 0, 0});
+    }
+    return v;
+}
+
+lwacm_status apply_cand(lwacm_ctx *c, const Cand &k) {
+    if (c->nbatch) {
+        lwacm_status s = lwacm_set_option(c, LWACM_OPT_BATCH_TILE, k.tile);
+        if (s == LWACM_OK) s = lwacm_set_option(c, LWACM_OPT_BATCH_MODE, k.mode);
+        return s;
+    }
+    const lwacm_status s = lwacm_set_option(c, LWACM_OPT_KERNEL, k.kernel);
+    if (s != LWACM_OK) return s;
+    return c->kernel == k.kernel ? LWACM_OK : LWACM_E_UNSUPPORTED;
+}
+
+// the rest state (all fields zero) in buffer 0, marked as set
+lwacm_status tune_zero_state(lwacm_ctx *c) {
+    CK(c, cudaMemsetAsync(bufp(c, 0), 0, field_bytes(c) * c->nf, c->stream), "zero state");
+    c->cur = 0;
+    c->has_fields = true;
+    c->steps = 0;
     return LWACM_OK;
 }
 
@@ -854,6 +929,101 @@ lwacm_status lwacm_sync(lwacm_ctx *c) {
     CK(c, cudaStreamSynchronize(c->stream), "sync");
     CK(c, cudaGetLastError(), "async error");
     if (err) return fail(c, LWACM_E_TIMEOUT, "a device-side wait gave up (data copy did not arrive)");
+    return LWACM_OK;
+}
+
+lwacm_status lwacm_autotune(lwacm_ctx *c, const char *cache_path, int trial_steps, char *report,
+                            size_t report_bytes) {
+    lwacm_status s = ready(c, false);
+    if (s != LWACM_OK) return s;
+    if (c->has_fields)
+        return fail(c, LWACM_E_STATE, "autotune runs on a fresh context: after lwacm_bind, before lwacm_set_fields");
+    if (trial_steps < 0 || trial_steps > 100000) return fail(c, LWACM_E_ARG, "trial_steps must be in [0, 100000]");
+    const long long T = trial_steps ? trial_steps : 256;
+    const std::string key = tune_key(c);
+    std::vector<Cand> cands = tune_candidates(c);
+    std::vector<double> times(cands.size(), -1.0);
+    std::vector<std::string> names(cands.size());
+    TuneChoice best;
+    std::string source = "measured";
+    bool stored = false;
+    TuneChoice hit;
+    int best_i = -1;
+    if (cache_path && tune_cache_lookup(cache_path, key, &hit)) {
+        for (size_t i = 0; i < cands.size(); ++i)
+            if (cands[i].kernel == hit.kernel && cands[i].tile == hit.tile && cands[i].mode == hit.mode)
+                best_i = (int)i;
+        if (best_i >= 0 && apply_cand(c, cands[best_i]) == LWACM_OK) {
+            best = hit;
+            source = "cache";
+        } else {
+            best_i = -1;
+        }
+    }
+    if (best_i < 0) {
+        // time every candidate from the rest state (d = 0, u = 0: a fixed point)
+        const int keep_kernel = c->kernel_opt, keep_tile = c->batch_shape, keep_mode = c->batch_mode;
+        cudaEvent_t e0 = nullptr, e1 = nullptr;
+        CK(c, cudaEventCreate(&e0), "event");
+        CK(c, cudaEventCreate(&e1), "event");
+        const long long warm = std::max(8, c->graph_chunk);
+        lwacm_status st = LWACM_OK;
+        for (size_t i = 0; i < cands.size() && st == LWACM_OK; ++i) {
+            if (apply_cand(c, cands[i]) != LWACM_OK) continue;
+            names[i] = c->kname;
+            st = tune_zero_state(c);
+            if (st == LWACM_OK) st = lwacm_step(c, warm);
+            if (st == LWACM_OK) st = lwacm_sync(c);
+            if (st != LWACM_OK) break;
+            cudaEventRecord(e0, c->stream);
+            st = lwacm_step(c, T);
+            cudaEventRecord(e1, c->stream);
+            if (st == LWACM_OK) st = lwacm_sync(c);
+            float ms = 0.f;
+            if (st == LWACM_OK && cudaEventElapsedTime(&ms, e0, e1) == cudaSuccess) {
+                times[i] = 1e3 * ms / (double)T;
+                if (best_i < 0 || times[i] < times[best_i]) best_i = (int)i;
+            }
+        }
+        cudaEventDestroy(e0);
+        cudaEventDestroy(e1);
+        c->has_fields = false;
+        c->steps = 0;
+        c->cur = 0;
+        if (st != LWACM_OK) return st;
+        if (best_i < 0) {
+            c->kernel_opt = keep_kernel;
+            c->batch_shape = keep_tile;
+            c->batch_mode = keep_mode;
+            choose_kernel(c);
+            return fail(c, LWACM_E_UNSUPPORTED, "no candidate configuration ran");
+        }
+        best.kernel = cands[best_i].kernel;
+        best.tile = cands[best_i].tile;
+        best.mode = cands[best_i].mode;
+        best.us = times[best_i];
+        s = apply_cand(c, cands[best_i]);
+        if (s != LWACM_OK) return s;
+        if (cache_path) stored = tune_cache_store(cache_path, key, best);
+    }
+    if (report && report_bytes) {
+        std::string r = "{\"key\": \"" + key + "\", \"source\": \"" + source + "\", \"choice\": {\"name\": \"" +
+                        c->kname + "\", \"kernel\": " + std::to_string(best.kernel) +
+                        ", \"tile\": " + std::to_string(best.tile) + ", \"mode\": " + std::to_string(best.mode) +
+                        ", \"us_per_step\": " + std::to_string(best.us) + "}, \"cache_written\": " +
+                        (stored ? "true" : "false") + ", \"candidates\": [";
+        bool first = true;
+        for (size_t i = 0; i < cands.size(); ++i) {
+            if (times[i] < 0) continue;
+            r += std::string(first ? "" : ", ") + "{\"name\": \"" + names[i] + "\", \"kernel\": " +
+                 std::to_string(cands[i].kernel) + ", \"tile\": " + std::to_string(cands[i].tile) +
+                 ", \"mode\": " + std::to_string(cands[i].mode) + ", \"us_per_step\": " + std::to_string(times[i]) +
+                 "}";
+            first = false;
+        }
+        r += "]}";
+        std::snprintf(report, report_bytes, "%s", r.c_str());
+    }
     return LWACM_OK;
 }
 

@@ -71,6 +71,7 @@ def load():
         "lwacm_measure_fp32_peak": [ll, vp, P(d), P(d)],
         "lwacm_selftest_reciprocal": [vp, vp, ll, vp],
         "lwacm_set_force_field": [vp, vp, vp, vp, i, i],
+        "lwacm_autotune": [vp, ctypes.c_char_p, i, ctypes.c_char_p, ctypes.c_size_t],
     }
     for name, args in sig.items():
         fn = getattr(lib, name)
@@ -236,6 +237,16 @@ class Lwacm:
         else:
             for a in keep:  # the copy runs on the library's stream
                 a.record_stream(self.stream)
+
+    def autotune(self, cache=None, steps=0):
+        """lwacm_autotune: time the candidate kernel configurations and keep the
+        fastest (call before set_fields). cache: path of the JSON cache or None.
+        Returns the report as a dict."""
+        import json
+        buf = ctypes.create_string_buffer(16384)
+        path = None if cache is None else str(cache).encode()
+        self._check(self._lib.lwacm_autotune(self._h, path, int(steps), buf, len(buf)))
+        return json.loads(buf.value.decode())
 
     def step(self, n=1):
         self._check(self._lib.lwacm_step(self._h, int(n)))

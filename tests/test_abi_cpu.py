@@ -166,3 +166,12 @@ def test_batch_tile_option(lib):
     assert lib.lwacm_create(9, 8, 8, 1, 0.01, 0, ctypes.byref(hs)) == lw.OK
     assert lib.lwacm_set_option(hs, lw.OPT_BATCH_TILE, 1.0) == lw.E_STATE
     lib.lwacm_destroy(hs)
+
+
+def test_autotune_needs_a_bound_fresh_context(lib):
+    from paper_1111_2142_gb300 import lwacm as lw
+    assert lib.lwacm_autotune(None, None, 0, None, 0) == lw.E_ARG
+    st, h = _create(lib, 9, 16, 16, 1, 0.02, 0)
+    assert st == lw.OK
+    assert lib.lwacm_autotune(h, None, 0, None, 0) == lw.E_STATE  # not bound
+    lib.lwacm_destroy(h)
