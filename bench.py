@@ -241,6 +241,16 @@ def variants(hbm):
         ms = _events_ms(sim.stream, lambda: sim.step(T))
         ens[label] = glups(nodes, T, ms)
         sim.close()
+    # the autotuner's choice among the tile layouts and launch forms
+    sim = lw.LwacmBatch(lw.D2Q9, dims, nus)
+    rep = sim.autotune(steps=256)
+    sim.set_domains(fields)
+    sim.step(10)
+    ms = _events_ms(sim.stream, lambda: sim.step(T))
+    ens["autotuned"] = {"value": glups(nodes, T, ms), "kernel": sim.kernel_name,
+                        "candidates": {c["name"]: round(nodes / c["us_per_step"] / 1e3, 2)
+                                       for c in rep["candidates"]}}
+    sim.close()
     # per-domain launches: one context per domain, each stepped on its own
     sims = []
     for (nx, ny), nu_b, fb in zip(dims, nus, fields):
