@@ -93,7 +93,9 @@ enum {
                               TMA kernel (2, 3 and 5 need a periodic domain without
                               forcing, nx in {128, 256} and ny % 8 == 0; 2 and 3 need FP32
                               storage, 5 takes FP32, BF16 and FP16: LWACM_E_UNSUPPORTED
-                              otherwise). The automatic choice takes 5, else 3, else 2,
+                              otherwise); 6 = D2Q9 2D-tile kernel (any boundary, no
+                              forcing; tile shape from LWACM_OPT_BATCH_TILE, 30x14 when
+                              0). The automatic choice takes 5, else 3, else 2, else 6,
                               else 1. */
     LWACM_OPT_BATCH_MODE = 10, /* batched contexts: 0 = one launch per step, replayed
                                   from CUDA graphs (default); 1 = one persistent
@@ -106,13 +108,14 @@ enum {
     LWACM_OPT_FORCE_FIELD = 12,   /* 1 = reserve room in the workspace for a per-node
                                      acceleration field (lwacm_set_force_field); only
                                      before lwacm_bind; single-domain contexts only */
-    LWACM_OPT_BATCH_TILE = 13     /* batched contexts: how the domains are cut into CTA
-                                     tiles. 0 (default) = runs of 256 consecutive nodes,
-                                     one thread per node, every lattice; 1..6 = 2D tiles
-                                     of 30x6, 30x14, 62x6, 30x30, 62x14, 126x6 nodes, D2Q9
+    LWACM_OPT_BATCH_TILE = 13     /* how domains are cut into CTA tiles. Batched contexts:
+                                     0 (default) = runs of 256 consecutive nodes, one
+                                     thread per node, every lattice; 1..6 = 2D tiles of
+                                     30x6, 30x14, 62x6, 30x30, 62x14, 126x6 nodes, D2Q9
                                      only (LWACM_E_UNSUPPORTED otherwise), with the link
                                      values computed once per node and exchanged in
-                                     shared memory. Any time; lwacm_autotune picks one. */
+                                     shared memory. Single D2Q9 contexts: the shape of
+                                     kernel 6. Any time; lwacm_autotune picks one. */
 };
 
 /* Create a single-domain context.

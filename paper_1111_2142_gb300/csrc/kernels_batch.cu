@@ -72,23 +72,24 @@ __device__ __forceinline__ void tile_update(const T *__restrict__ in, T *__restr
 constexpr int kShapes[][2] = {{0, 0}, {30, 6}, {30, 14}, {62, 6}, {30, 30}, {62, 14}, {126, 6}};
 constexpr int kNumShapes = sizeof(kShapes) / sizeof(kShapes[0]);
 
+// one TW x TH tile (plus frame) of a periodic D2Q9 domain whose node (0,0) is at
+// packed index base; s, a: 18 nu and 1 - 6 nu of the domain
 template <int TW, int TH, typename T>
-__device__ __forceinline__ void tile2_update(const T *__restrict__ in, T *__restrict__ out, const BatchParams &bp,
-                                             long long t, float (*G)[(TW + 2) * (TH + 2)]) {
+__device__ __forceinline__ void tile2_core(const T *__restrict__ in, T *__restrict__ out, long long base, int nx,
+                                           int ny, long long fstride, float s, float a, int x0, int y0,
+                                           float (*G)[(TW + 2) * (TH + 2)]) {
     constexpr int W = TW + 2;
-    const BatchTile2 tile = bp.tiles2[t];
-    const BatchDomain dm = bp.doms[tile.dom];
     const int tx = threadIdx.x % W, ty = threadIdx.x / W;
-    int x = tile.x0 + tx - 1, y = tile.y0 + ty - 1;
-    x %= dm.nx;
-    if (x < 0) x += dm.nx;
-    y %= dm.ny;
-    if (y < 0) y += dm.ny;
-    const long long k = dm.off + (long long)y * dm.nx + x;
-    const float d = ldf(in + k), u = ldf(in + bp.fstride + k), v = ldf(in + 2 * bp.fstride + k);
+    int x = x0 + tx - 1, y = y0 + ty - 1;
+    x %= nx;
+    if (x < 0) x += nx;
+    y %= ny;
+    if (y < 0) y += ny;
+    const long long k = base + (long long)y * nx + x;
+    const float d = ldf(in + k), u = ldf(in + fstride + k), v = ldf(in + 2 * fstride + k);
     const float rho = 1.f + d;
     const float K = fmaf(-1.5f * rho, fmaf(u, u, v * v), d);  // d - 3/2 rho |u|^2
-    const float nu = dm.s * (1.f / 18.f);
+    const float nu = s * (1.f / 18.f);
     {
         // pair (c, -c) with e = c.u: w (K + 9/2 rho e^2) +- w rho s e
         const float a9 = rho * nu * 2.f, b9 = rho * 0.5f, k9 = K * (1.f / 9.f);        // axis, w = 1/9
@@ -104,24 +105,44 @@ __device__ __forceinline__ void tile2_update(const T *__restrict__ in, T *__rest
         }
     }
     __syncthreads();
-    const int xi = tile.x0 + tx - 1, yi = tile.y0 + ty - 1;
-    if (tx >= 1 && tx <= TW && ty >= 1 && ty <= TH && xi < dm.nx && yi < dm.ny) {
+    const int xi = x0 + tx - 1, yi = y0 + ty - 1;
+    if (tx >= 1 && tx <= TW && ty >= 1 && ty <= TH && xi < nx && yi < ny) {
         const int tid = (int)threadIdx.x;
-        // value arriving along c from the neighbour at (tx - cx, ty - cy)
+        // G[] order: (1,0) (-1,0) (0,1) (0,-1) (1,1) (-1,-1) (1,-1) (-1,1); the value
+        // arriving along c comes from the neighbour at (tx - cx, ty - cy)
 #define LW_IN(i, cx, cy) G[(i) - 1][tid - (cx) - (cy) * W]
         const float g1 = LW_IN(1, 1, 0), g2 = LW_IN(2, -1, 0), g3 = LW_IN(3, 0, 1), g4 = LW_IN(4, 0, -1);
         const float g5 = LW_IN(5, 1, 1), g6 = LW_IN(6, -1, -1), g7 = LW_IN(7, 1, -1), g8 = LW_IN(8, -1, 1);
 #undef LW_IN
         const float dd = fmaf(4.f / 9.f, K, ((g1 + g2) + (g3 + g4)) + ((g5 + g6) + (g7 + g8)));
-        const float ar = dm.a * rho;
+        const float ar = a * rho;
         const float jx = fmaf(ar, u, (g1 - g2) + ((g5 - g6) + (g7 - g8)));
         const float jy = fmaf(ar, v, (g3 - g4) + ((g5 - g6) - (g7 - g8)));
         const float rn = 1.f + dd;
         stf(out + k, dd);
-        stf(out + bp.fstride + k, jx / rn);
-        stf(out + 2 * bp.fstride + k, jy / rn);
+        stf(out + fstride + k, jx / rn);
+        stf(out + 2 * fstride + k, jy / rn);
     }
     __syncthreads();  // G is rewritten by the next tile
+}
+
+template <int TW, int TH, typename T>
+__device__ __forceinline__ void tile2_update(const T *__restrict__ in, T *__restrict__ out, const BatchParams &bp,
+                                             long long t, float (*G)[(TW + 2) * (TH + 2)]) {
+    const BatchTile2 tile = bp.tiles2[t];
+    const BatchDomain dm = bp.doms[tile.dom];
+    tile2_core<TW, TH, T>(in, out, dm.off, dm.nx, dm.ny, bp.fstride, dm.s, dm.a, tile.x0, tile.y0, G);
+}
+
+// one periodic D2Q9 domain (the wall pass, where there are walls, runs after it
+// and replaces the boundary nodes); tiles numbered row-major
+template <int TW, int TH, typename T>
+__global__ void __launch_bounds__((TW + 2) * (TH + 2)) k_d2q9_tiles(const T *__restrict__ in, T *__restrict__ out,
+                                                                   int nx, int ny, long long fstride, float s,
+                                                                   float a, int tilesx, long long ntiles) {
+    __shared__ float G[8][(TW + 2) * (TH + 2)];
+    for (long long t = blockIdx.x; t < ntiles; t += gridDim.x)
+        tile2_core<TW, TH, T>(in, out, 0, nx, ny, fstride, s, a, (int)(t % tilesx) * TW, (int)(t / tilesx) * TH, G);
 }
 
 template <int TW, int TH, typename T>
@@ -261,6 +282,33 @@ cudaError_t tiles_storage(int storage, const void *in, void *out, void *b0, void
     return cudaErrorInvalidValue;
 }
 
+template <int TW, int TH, typename T>
+cudaError_t single_t(const void *in, void *out, const StepParams &p, cudaStream_t st) {
+    constexpr int NT = (TW + 2) * (TH + 2);
+    static int cap = 0;
+    const int g = max_grid(k_d2q9_tiles<TW, TH, T>, NT, &cap);
+    if (g < 1) return cudaErrorNotSupported;
+    const int tilesx = (p.nx + TW - 1) / TW;
+    const long long ntiles = (long long)tilesx * ((p.ny + TH - 1) / TH);
+    const long long grid = ntiles < 4LL * g ? ntiles : 4LL * g;
+    k_d2q9_tiles<TW, TH, T><<<(unsigned)grid, NT, 0, st>>>((const T *)in, (T *)out, p.nx, p.ny, p.fstride, p.s, p.a,
+                                                          tilesx, ntiles);
+    return cudaGetLastError();
+}
+
+template <typename T>
+cudaError_t single_dispatch(int shape, const void *in, void *out, const StepParams &p, cudaStream_t st) {
+    switch (shape) {
+        case 1: return single_t<30, 6, T>(in, out, p, st);
+        case 2: return single_t<30, 14, T>(in, out, p, st);
+        case 3: return single_t<62, 6, T>(in, out, p, st);
+        case 4: return single_t<30, 30, T>(in, out, p, st);
+        case 5: return single_t<62, 14, T>(in, out, p, st);
+        case 6: return single_t<126, 6, T>(in, out, p, st);
+    }
+    return cudaErrorInvalidValue;
+}
+
 template <int Q, typename T>
 cudaError_t persistent_t(void *b0, void *b1, const BatchParams &bp, long long nsteps, int parity,
                          cudaStream_t st) {
@@ -315,6 +363,22 @@ bool batch_shape_supported(int Q, int storage, int k) {
     if (k == 0) return true;
     return Q == 9 && k > 0 && k < kNumShapes &&
            (storage == STORE_F32 || storage == STORE_BF16 || storage == STORE_F16);
+}
+
+bool tiles2d_supported(int Q, int storage, const StepParams &p) {
+    return Q == 9 && p.nz == 1 && !p.has_force && !p.gfield &&
+           (storage == STORE_F32 || storage == STORE_BF16 || storage == STORE_F16);
+}
+
+cudaError_t launch_step_tiles2d(int Q, int storage, int shape, const void *in, void *out, const StepParams &p,
+                                cudaStream_t st) {
+    if (!tiles2d_supported(Q, storage, p) || shape < 1 || shape >= kNumShapes) return cudaErrorInvalidValue;
+    switch (storage) {
+        case STORE_F32: return single_dispatch<float>(shape, in, out, p, st);
+        case STORE_BF16: return single_dispatch<__nv_bfloat16>(shape, in, out, p, st);
+        case STORE_F16: return single_dispatch<__half>(shape, in, out, p, st);
+    }
+    return cudaErrorInvalidValue;
 }
 
 cudaError_t launch_batch_step(int Q, int storage, const void *in, void *out, const BatchParams &bp,

@@ -76,6 +76,11 @@ int batch_tile();
 int batch_shapes();
 void batch_shape(int k, int *tw, int *th);
 bool batch_shape_supported(int Q, int storage, int k);
+// the same 2D-tile update for one D2Q9 domain (any boundary: the wall pass runs
+// after it; no forcing)
+bool tiles2d_supported(int Q, int storage, const StepParams &p);
+cudaError_t launch_step_tiles2d(int Q, int storage, int shape, const void *in, void *out, const StepParams &p,
+                                cudaStream_t st);
 cudaError_t launch_batch_step(int Q, int storage, const void *in, void *out, const BatchParams &bp,
                               cudaStream_t st);
 cudaError_t launch_batch_persistent(int Q, int storage, void *buf0, void *buf1, const BatchParams &bp,

@@ -51,7 +51,8 @@ struct lwacm_ctx {
     cudaStream_t cap_stream = nullptr;
     cudaGraphExec_t gexec[2] = {nullptr, nullptr};
     int gchunk[2] = {0, 0};
-    int kernel = 1;  // 1 generic, 2 tiled (TMA), 3 z-march (register prefetch), 4 batch, 5 half-row TMA
+    int kernel = 1;  // 1 generic, 2 tiled (TMA), 3 z-march (register prefetch), 4 batch, 5 half-row TMA,
+                     // 6 D2Q9 2D tiles
     std::string kname = "none";
     // batched domains (nbatch > 0): packed one after the other
     int nbatch = 0;
@@ -184,18 +185,23 @@ bool choose_kernel(lwacm_ctx *c) {
     const bool t_ok = dev && tiled_supported(c->Q, c->storage, p);
     const bool z_ok = dev && zmarch_supported(c->Q, c->storage, p);
     const bool h_ok = dev && half_supported(c->Q, c->storage, p);
+    const bool s_ok = tiles2d_supported(c->Q, c->storage, p);
     bool ok = true;
     switch (c->kernel_opt) {
         case 1: c->kernel = 1; break;
         case 2: c->kernel = t_ok ? 2 : 1; ok = t_ok || !dev; break;
         case 3: c->kernel = z_ok ? 3 : 1; ok = z_ok || !dev; break;
         case 5: c->kernel = h_ok ? 5 : 1; ok = h_ok || !dev; break;
-        default: c->kernel = h_ok ? 5 : (z_ok ? 3 : (t_ok ? 2 : 1)); break;
+        case 6: c->kernel = s_ok ? 6 : 1; ok = s_ok; break;
+        default: c->kernel = h_ok ? 5 : (z_ok ? 3 : (t_ok ? 2 : (s_ok ? 6 : 1))); break;
     }
     static const char *gname[2] = {"generic_d2q9", "generic_d3q19"};
+    static const char *sname[7] = {"tiles2d_d2q9_30x14", "tiles2d_d2q9_30x6",  "tiles2d_d2q9_30x14", "tiles2d_d2q9_62x6",
+                                   "tiles2d_d2q9_30x30", "tiles2d_d2q9_62x14", "tiles2d_d2q9_126x6"};
     c->kname = c->kernel == 2   ? tiled_name(c->Q)
                : c->kernel == 3 ? "zmarch_d3q19"
                : c->kernel == 5 ? "half_d3q19_tma"
+               : c->kernel == 6 ? sname[c->batch_shape >= 0 && c->batch_shape < 7 ? c->batch_shape : 0]
                                 : gname[c->Q == 19 ? 1 : 0];
     return ok;
 }
@@ -252,6 +258,8 @@ cudaError_t step_between(lwacm_ctx *c, const void *in, void *out, cudaStream_t s
     cudaError_t e = c->kernel == 2   ? launch_step_tiled(c->Q, c->storage, in, out, p, st)
                     : c->kernel == 3 ? launch_step_zmarch(c->Q, c->storage, in, out, p, st)
                     : c->kernel == 5 ? launch_step_half(c->Q, c->storage, in, out, p, st)
+                    : c->kernel == 6 ? launch_step_tiles2d(c->Q, c->storage, c->batch_shape > 0 ? c->batch_shape : 2,
+                                                           in, out, p, st)
                                      : launch_step_generic(c->Q, c->storage, in, out, p, st);
     if (e != cudaSuccess) return e;
     if (c->bc != LWACM_BC_PERIODIC) e = launch_wall_pass(c->Q, c->storage, in, out, p, st);
@@ -376,6 +384,8 @@ std::vector<Cand> tune_candidates(const lwacm_ctx *c) {
     } else {
         const int ks[4] = {5, 3, 2, 1};
         for (int k : ks) v.push_back(Cand{k, 0, 0});
+        if (c->Q == 9)
+            for (int k = 1; k < batch_shapes(); ++k) v.push_back(Cand{6, k, 0});
     }
     return v;
 }
@@ -385,6 +395,10 @@ lwacm_status apply_cand(lwacm_ctx *c, const Cand &k) {
         lwacm_status s = lwacm_set_option(c, LWACM_OPT_BATCH_TILE, k.tile);
         if (s == LWACM_OK) s = lwacm_set_option(c, LWACM_OPT_BATCH_MODE, k.mode);
         return s;
+    }
+    if (k.kernel == 6) {
+        const lwacm_status s = lwacm_set_option(c, LWACM_OPT_BATCH_TILE, k.tile);
+        if (s != LWACM_OK) return s;
     }
     const lwacm_status s = lwacm_set_option(c, LWACM_OPT_KERNEL, k.kernel);
     if (s != LWACM_OK) return s;
@@ -558,7 +572,7 @@ lwacm_status lwacm_set_option(lwacm_ctx *c, int key, double v) {
         }
         case LWACM_OPT_KERNEL: {
             const int k = (int)v;
-            if (k < 0 || k > 5 || k == 4) return fail(c, LWACM_E_ARG, "kernel must be 0, 1, 2, 3 or 5");
+            if (k < 0 || k > 6 || k == 4) return fail(c, LWACM_E_ARG, "kernel must be 0, 1, 2, 3, 5 or 6");
             const int old = c->kernel_opt;
             c->kernel_opt = k;
             if (!choose_kernel(c)) {
@@ -577,12 +591,11 @@ lwacm_status lwacm_set_option(lwacm_ctx *c, int key, double v) {
         }
         case LWACM_OPT_BATCH_TILE: {
             const int k = (int)v;
-            if (!c->nbatch) return fail(c, LWACM_E_STATE, "not a batched context");
             if (k < 0 || k >= batch_shapes() || (double)k != v) return fail(c, LWACM_E_ARG, "unknown tile shape");
             if (!batch_shape_supported(c->Q, c->storage, k))
-                return fail(c, LWACM_E_UNSUPPORTED, "2D tile shapes are for D2Q9 ensembles");
+                return fail(c, LWACM_E_UNSUPPORTED, "2D tile shapes are for the D2Q9 lattice");
             c->batch_shape = k;
-            if (c->bound) {
+            if (c->bound && c->nbatch) {
                 const lwacm_status ts = upload_tiles(c);
                 if (ts != LWACM_OK) return ts;
             }

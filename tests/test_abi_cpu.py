@@ -164,8 +164,15 @@ def test_batch_tile_option(lib):
     lib.lwacm_destroy(h3)
     hs = ctypes.c_void_p()
     assert lib.lwacm_create(9, 8, 8, 1, 0.01, 0, ctypes.byref(hs)) == lw.OK
-    assert lib.lwacm_set_option(hs, lw.OPT_BATCH_TILE, 1.0) == lw.E_STATE
+    assert lib.lwacm_set_option(hs, lw.OPT_BATCH_TILE, 1.0) == lw.OK  # shape of kernel 6
+    assert lib.lwacm_set_option(hs, lw.OPT_KERNEL, 6.0) == lw.OK
+    assert lib.lwacm_kernel_name(hs).decode() == "tiles2d_d2q9_30x6"
     lib.lwacm_destroy(hs)
+    h19 = ctypes.c_void_p()
+    assert lib.lwacm_create(19, 8, 8, 8, 0.01, 0, ctypes.byref(h19)) == lw.OK
+    assert lib.lwacm_set_option(h19, lw.OPT_BATCH_TILE, 1.0) == lw.E_UNSUPPORTED
+    assert lib.lwacm_set_option(h19, lw.OPT_KERNEL, 6.0) == lw.E_UNSUPPORTED
+    lib.lwacm_destroy(h19)
 
 
 def test_autotune_needs_a_bound_fresh_context(lib):

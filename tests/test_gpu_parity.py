@@ -73,6 +73,31 @@ def test_d2q9_ragged(lw, kernel, shape):
     assert eu < 1e-5 and ed < 1e-4
 
 
+@pytest.mark.parametrize("tile", [1, 2, 3, 4, 5, 6])
+@pytest.mark.parametrize("bc", [0, 1, 2])
+def test_d2q9_tiles2d_kernel(lw, tile, bc):
+    """The D2Q9 2D-tile kernel (kernel 6) forced on, every tile shape, periodic,
+    cavity (lid 0.05) and channel (with the wall pass after it): ragged shapes
+    narrower and wider than the tiles."""
+    lid = (0.05, 0.0) if bc == 1 else None
+    for shape in ((23, 37), (1, 5), (33, 130), (64, 64)):
+        if bc and min(shape) < 2:
+            continue
+        f = inputs.smooth_random(shape, seed=13, u_amp=0.05, d_amp=0.01)
+        ny, nx = shape
+        sim = lw.Lwacm(9, nx, ny, 1, 0.02, bc, lid=lid)
+        sim.set_option(lw.OPT_BATCH_TILE, tile)
+        sim.set_option(lw.OPT_KERNEL, 6)
+        assert sim.kernel_name.startswith("tiles2d")
+        sim.set_fields(*f)
+        sim.step(45)
+        got = sim.get_fields()
+        sim.close()
+        ref = oracle.step(9, *f, nu=0.02, nsteps=45, bc=bc, lid=None if lid is None else (0.05, 0.0, 0.0))
+        eu, ed = errs(got, ref, 0.05)
+        assert eu < 1e-5 and ed < 1e-4, (tile, bc, shape, eu, ed)
+
+
 @pytest.mark.parametrize("kernel", KERNELS)
 @pytest.mark.parametrize("shape", [(9, 11, 13), (3, 4, 5), (16, 16, 64), (5, 7, 132)])
 def test_d3q19_ragged(lw, kernel, shape):
