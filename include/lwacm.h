@@ -93,8 +93,8 @@ enum {
                               TMA kernel (2, 3 and 5 need a periodic domain without
                               forcing, nx in {128, 256} and ny % 8 == 0; 2 and 3 need FP32
                               storage, 5 takes FP32, BF16 and FP16: LWACM_E_UNSUPPORTED
-                              otherwise); 6 = D2Q9 2D-tile kernel (any boundary, no
-                              forcing; tile shape from LWACM_OPT_BATCH_TILE, 30x14 when
+                              otherwise); 6 = D2Q9 2D-tile kernel (any boundary, walls
+                              applied in the kernel, no forcing; tile shape from LWACM_OPT_BATCH_TILE, 30x14 when
                               0). The automatic choice takes 5, else 3, else 2, else 6,
                               else 1. */
     LWACM_OPT_BATCH_MODE = 10, /* batched contexts: 0 = one launch per step, replayed

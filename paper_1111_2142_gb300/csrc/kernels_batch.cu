@@ -72,12 +72,23 @@ __device__ __forceinline__ void tile_update(const T *__restrict__ in, T *__restr
 constexpr int kShapes[][2] = {{0, 0}, {30, 6}, {30, 14}, {62, 6}, {30, 30}, {62, 14}, {126, 6}};
 constexpr int kNumShapes = sizeof(kShapes) / sizeof(kShapes[0]);
 
-// one TW x TH tile (plus frame) of a periodic D2Q9 domain whose node (0,0) is at
-// packed index base; s, a: 18 nu and 1 - 6 nu of the domain
-template <int TW, int TH, typename T>
+// walls of a single D2Q9 domain for the tile kernel (half-way walls on the walled
+// axes, Eqs. ACM2.0cccbb2 / ACM2.0ccccbb; the lid moves on the top of lid axis)
+struct Walls2 {
+    int wx, wy;        // 1 = walls on both ends of x / y
+    int lid_axis;      // 0: x, 1: y
+    float wallc;       // 36 nu rho0
+    float lidx, lidy;  // lid velocity
+};
+
+// one TW x TH tile (plus frame) of a D2Q9 domain whose node (0,0) is at packed
+// index base; s, a: 18 nu and 1 - 6 nu of the domain. Without WALLS every axis is
+// periodic; with WALLS a link whose source lies beyond a walled face takes the
+// node's own value of the opposite link plus the moving-wall term.
+template <int TW, int TH, typename T, bool WALLS = false>
 __device__ __forceinline__ void tile2_core(const T *__restrict__ in, T *__restrict__ out, long long base, int nx,
                                            int ny, long long fstride, float s, float a, int x0, int y0,
-                                           float (*G)[(TW + 2) * (TH + 2)]) {
+                                           float (*G)[(TW + 2) * (TH + 2)], const Walls2 &wl = Walls2{}) {
     constexpr int W = TW + 2;
     const int tx = threadIdx.x % W, ty = threadIdx.x / W;
     int x = x0 + tx - 1, y = y0 + ty - 1;
@@ -111,9 +122,34 @@ __device__ __forceinline__ void tile2_core(const T *__restrict__ in, T *__restri
         // G[] order: (1,0) (-1,0) (0,1) (0,-1) (1,1) (-1,-1) (1,-1) (-1,1); the value
         // arriving along c comes from the neighbour at (tx - cx, ty - cy)
 #define LW_IN(i, cx, cy) G[(i) - 1][tid - (cx) - (cy) * W]
-        const float g1 = LW_IN(1, 1, 0), g2 = LW_IN(2, -1, 0), g3 = LW_IN(3, 0, 1), g4 = LW_IN(4, 0, -1);
-        const float g5 = LW_IN(5, 1, 1), g6 = LW_IN(6, -1, -1), g7 = LW_IN(7, 1, -1), g8 = LW_IN(8, -1, 1);
+        float g1 = LW_IN(1, 1, 0), g2 = LW_IN(2, -1, 0), g3 = LW_IN(3, 0, 1), g4 = LW_IN(4, 0, -1);
+        float g5 = LW_IN(5, 1, 1), g6 = LW_IN(6, -1, -1), g7 = LW_IN(7, 1, -1), g8 = LW_IN(8, -1, 1);
 #undef LW_IN
+        if (WALLS) {
+            const bool xl = wl.wx && xi == 0, xh = wl.wx && xi == nx - 1;
+            const bool yl = wl.wy && yi == 0, yh = wl.wy && yi == ny - 1;
+            if (xl || xh || yl || yh) {
+                // link i with c = (cx, cy) from outside: own value along -c, plus the
+                // lid term when the source lies beyond the top of the lid axis
+                auto fix = [&](float &g, int i, int cx, int cy) {
+                    const bool ox = (cx > 0 && xl) || (cx < 0 && xh), oy = (cy > 0 && yl) || (cy < 0 && yh);
+                    if (!(ox || oy)) return;
+                    const int j = (i & 1) ? i + 1 : i - 1;  // opposite link (pairs 1-2, 3-4, 5-6, 7-8)
+                    float v = G[j - 1][tid];
+                    const bool above = wl.lid_axis == 0 ? (cx < 0 && xh) : (cy < 0 && yh);
+                    if (above) v = fmaf((i <= 4 ? 1.f / 9.f : 1.f / 36.f) * wl.wallc, cx * wl.lidx + cy * wl.lidy, v);
+                    g = v;
+                };
+                fix(g1, 1, 1, 0);
+                fix(g2, 2, -1, 0);
+                fix(g3, 3, 0, 1);
+                fix(g4, 4, 0, -1);
+                fix(g5, 5, 1, 1);
+                fix(g6, 6, -1, -1);
+                fix(g7, 7, 1, -1);
+                fix(g8, 8, -1, 1);
+            }
+        }
         const float dd = fmaf(4.f / 9.f, K, ((g1 + g2) + (g3 + g4)) + ((g5 + g6) + (g7 + g8)));
         const float ar = a * rho;
         const float jx = fmaf(ar, u, (g1 - g2) + ((g5 - g6) + (g7 - g8)));
@@ -134,15 +170,15 @@ __device__ __forceinline__ void tile2_update(const T *__restrict__ in, T *__rest
     tile2_core<TW, TH, T>(in, out, dm.off, dm.nx, dm.ny, bp.fstride, dm.s, dm.a, tile.x0, tile.y0, G);
 }
 
-// one periodic D2Q9 domain (the wall pass, where there are walls, runs after it
-// and replaces the boundary nodes); tiles numbered row-major
-template <int TW, int TH, typename T>
+// one D2Q9 domain, walls included (no separate wall pass); tiles numbered row-major
+template <int TW, int TH, typename T, bool WALLS>
 __global__ void __launch_bounds__((TW + 2) * (TH + 2)) k_d2q9_tiles(const T *__restrict__ in, T *__restrict__ out,
                                                                    int nx, int ny, long long fstride, float s,
-                                                                   float a, int tilesx, long long ntiles) {
+                                                                   float a, int tilesx, long long ntiles, Walls2 wl) {
     __shared__ float G[8][(TW + 2) * (TH + 2)];
     for (long long t = blockIdx.x; t < ntiles; t += gridDim.x)
-        tile2_core<TW, TH, T>(in, out, 0, nx, ny, fstride, s, a, (int)(t % tilesx) * TW, (int)(t / tilesx) * TH, G);
+        tile2_core<TW, TH, T, WALLS>(in, out, 0, nx, ny, fstride, s, a, (int)(t % tilesx) * TW,
+                                     (int)(t / tilesx) * TH, G, wl);
 }
 
 template <int TW, int TH, typename T>
@@ -282,18 +318,31 @@ cudaError_t tiles_storage(int storage, const void *in, void *out, void *b0, void
     return cudaErrorInvalidValue;
 }
 
-template <int TW, int TH, typename T>
-cudaError_t single_t(const void *in, void *out, const StepParams &p, cudaStream_t st) {
+template <int TW, int TH, typename T, bool WALLS>
+cudaError_t single_w(const void *in, void *out, const StepParams &p, const Walls2 &wl, cudaStream_t st) {
     constexpr int NT = (TW + 2) * (TH + 2);
     static int cap = 0;
-    const int g = max_grid(k_d2q9_tiles<TW, TH, T>, NT, &cap);
+    const int g = max_grid(k_d2q9_tiles<TW, TH, T, WALLS>, NT, &cap);
     if (g < 1) return cudaErrorNotSupported;
     const int tilesx = (p.nx + TW - 1) / TW;
     const long long ntiles = (long long)tilesx * ((p.ny + TH - 1) / TH);
     const long long grid = ntiles < 4LL * g ? ntiles : 4LL * g;
-    k_d2q9_tiles<TW, TH, T><<<(unsigned)grid, NT, 0, st>>>((const T *)in, (T *)out, p.nx, p.ny, p.fstride, p.s, p.a,
-                                                          tilesx, ntiles);
+    k_d2q9_tiles<TW, TH, T, WALLS><<<(unsigned)grid, NT, 0, st>>>((const T *)in, (T *)out, p.nx, p.ny, p.fstride,
+                                                                 p.s, p.a, tilesx, ntiles, wl);
     return cudaGetLastError();
+}
+
+template <int TW, int TH, typename T>
+cudaError_t single_t(const void *in, void *out, const StepParams &p, cudaStream_t st) {
+    if (p.bc == BC_PERIODIC) return single_w<TW, TH, T, false>(in, out, p, Walls2{}, st);
+    Walls2 wl;
+    wl.wx = p.walled[0];
+    wl.wy = p.walled[1];
+    wl.lid_axis = p.lid_axis;
+    wl.wallc = p.wallc;
+    wl.lidx = p.lid[0];
+    wl.lidy = p.lid[1];
+    return single_w<TW, TH, T, true>(in, out, p, wl, st);
 }
 
 template <typename T>

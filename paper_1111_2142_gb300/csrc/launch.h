@@ -76,8 +76,8 @@ int batch_tile();
 int batch_shapes();
 void batch_shape(int k, int *tw, int *th);
 bool batch_shape_supported(int Q, int storage, int k);
-// the same 2D-tile update for one D2Q9 domain (any boundary: the wall pass runs
-// after it; no forcing)
+// the same 2D-tile update for one D2Q9 domain (any boundary, the wall rule applied
+// in the kernel; no forcing)
 bool tiles2d_supported(int Q, int storage, const StepParams &p);
 cudaError_t launch_step_tiles2d(int Q, int storage, int shape, const void *in, void *out, const StepParams &p,
                                 cudaStream_t st);

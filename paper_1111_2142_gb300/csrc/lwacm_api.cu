@@ -262,7 +262,8 @@ cudaError_t step_between(lwacm_ctx *c, const void *in, void *out, cudaStream_t s
                                                            in, out, p, st)
                                      : launch_step_generic(c->Q, c->storage, in, out, p, st);
     if (e != cudaSuccess) return e;
-    if (c->bc != LWACM_BC_PERIODIC) e = launch_wall_pass(c->Q, c->storage, in, out, p, st);
+    // the 2D-tile kernel applies the wall rule itself
+    if (c->bc != LWACM_BC_PERIODIC && c->kernel != 6) e = launch_wall_pass(c->Q, c->storage, in, out, p, st);
     return e;
 }
 
