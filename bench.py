@@ -296,7 +296,8 @@ def variants(hbm):
     sim.step(64)
     ms = _events_ms(sim.stream, lambda: sim.step(2000))
     out["cavity_d2q9_1024"] = {"value": glups(1024 ** 2, 2000, ms), "unit": "GLUPS",
-                               "kernel": sim.kernel_name + "+wall_pass", "l2_resident": True}
+                               "kernel": sim.kernel_name + ("+wall_pass" if sim.kernel_name.startswith("generic")
+                                                            else ""), "l2_resident": True}
     sim.close()
 
     # 2D Taylor-Green 64^2
