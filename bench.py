@@ -353,12 +353,10 @@ def run_gpu(args):
         ms = ev0.elapsed_time(ev1)
     clocks = clk.summary()
 
-    t_max = ms
-    if dist is not None:
-        t = torch.tensor([ms], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        t_max = float(t.item())
-    glups = ws * args.steps * N / (t_max * 1e-3) / 1e9
+    from paper_1111_2142_gb300.shard import aggregate_throughput
+    units, t_max_s = aggregate_throughput(args.steps * N, ms * 1e-3, device="cuda")
+    t_max = t_max_s * 1e3
+    glups = units / t_max_s / 1e9
     ms_step = t_max / args.steps
     diag = sim.diagnostics()
 
@@ -405,12 +403,8 @@ def run_gpu(args):
         e2e_step()
     torch.cuda.synchronize()
     barrier()
-    e2e_s = time.perf_counter() - t0
-    if dist is not None:
-        t = torch.tensor([e2e_s], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        e2e_s = float(t.item())
-    e2e_glups = ws * e2e_steps * N / e2e_s / 1e9
+    e2e_units, e2e_s = aggregate_throughput(e2e_steps * N, time.perf_counter() - t0, device="cuda")
+    e2e_glups = e2e_units / e2e_s / 1e9
     field_bytes = 4 * N * 4
 
     line = {
