@@ -270,7 +270,7 @@ __device__ __forceinline__ void phase_a(Acc &acc, const T *stg, float *xbuf, flo
                 acc[P0][j][2] = fma2(ar, nc.V[j], acc[P0][j][2]);
                 acc[P0][j][3] = fma2(ar, nc.W[j], acc[P0][j][3]);
             }
-            if (MODE != LAST) acc[PP][j][0] = add2(acc[PP][j][0], gp);
+            if (MODE != LAST) acc[PP][j][0] = gp;  // first value of the plane ahead
             if (MODE != FIRST) {
                 acc[PM][j][0] = add2(acc[PM][j][0], gm);
                 acc[PM][j][3] = sub2(acc[PM][j][3], gm);
@@ -296,13 +296,26 @@ __device__ __forceinline__ void phase_a(Acc &acc, const T *stg, float *xbuf, flo
                 dep1(acc[pl<PM, P0, PP>(cz)], 0, rP, 1, 0, cz);
             }
             if (nm) {  // -c: node i feeds node i-1
+                // for cz = -1 this is the first x-momentum of the plane ahead
 #pragma unroll
-                for (int i = 1; i < VXH; ++i) dep1(acc[pl<PM, P0, PP>(-cz)], i - 1, ndv(gm, i), -1, 0, -cz);
+                for (int i = 1; i < VXH; ++i) {
+                    if (cz < 0) {
+                        ac(acc[PP], i - 1, 0) += ndv(gm, i);
+                        ac(acc[PP], i - 1, 1) = -ndv(gm, i);
+                    } else {
+                        dep1(acc[pl<PM, P0, PP>(-cz)], i - 1, ndv(gm, i), -1, 0, -cz);
+                    }
+                }
                 const float eM = gm[0].x;
                 if (NH == 2) st_shared_if(edge + E_INM + cz + 1, eM, lane == 0);  // for the other half's lane 31
                 float rM = __shfl_sync(FULL, eM, (lane + 1) & 31);
                 if (NH == 2) rM = lane == 31 ? 0.f : rM;
-                dep1(acc[pl<PM, P0, PP>(-cz)], VXH - 1, rM, -1, 0, -cz);
+                if (cz < 0) {
+                    ac(acc[PP], VXH - 1, 0) += rM;
+                    ac(acc[PP], VXH - 1, 1) = -rM;
+                } else {
+                    dep1(acc[pl<PM, P0, PP>(-cz)], VXH - 1, rM, -1, 0, -cz);
+                }
             }
         }
         send_rows<NH, MODE>(nc, up + (row + 1) * RL, dn + (row - 1) * RL, row + 1 < ROWS, row > 0, edge, lane);
@@ -380,7 +393,7 @@ __device__ __forceinline__ void phase_b(Acc &acc, const float *xbuf, const float
 #pragma unroll
         for (int j = 0; j < 2; ++j) {
             acc[PP][j][0] = add2(acc[PP][j][0], o[j]);
-            acc[PP][j][2] = add2(acc[PP][j][2], o[j]);
+            acc[PP][j][2] = o[j];  // first y-momentum of the plane ahead
         }
         ld_slot2(dn + 2 * XSLOT, o, lane);
 #pragma unroll
@@ -423,10 +436,6 @@ __device__ __forceinline__ void phase_b(Acc &acc, const float *xbuf, const float
                 st4(op + c * p.fstride, v0.x, v0.y, v1.x, v1.y);
             }
         }
-#pragma unroll
-        for (int j = 0; j < 2; ++j)
-#pragma unroll
-            for (int c = 0; c < 4; ++c) acc[PM][j][c] = b2(0.f);
     }
 }
 
@@ -456,6 +465,8 @@ __device__ __forceinline__ void issue_plane(const T *in, const TiledParams &p, i
     }
 }
 
+// the plane ahead starts from its first deposits (assignments), so it needs no
+// clearing; a plane behind that holds values of another run is never stored
 __device__ __forceinline__ void rotate(Acc &acc) {
 #pragma unroll
     for (int j = 0; j < 2; ++j) {
@@ -463,8 +474,6 @@ __device__ __forceinline__ void rotate(Acc &acc) {
         for (int c = 0; c < 4; ++c) acc[0][j][c] = acc[1][j][c];
 #pragma unroll
         for (int c = 0; c < 3; ++c) acc[1][j][c] = acc[2][j][c];
-#pragma unroll
-        for (int c = 0; c < 4; ++c) acc[2][j][c] = b2(0.f);
     }
 }
 
@@ -516,12 +525,6 @@ __global__ void __launch_bounds__(HG<NH>::NTH, 2 / NH) k_d3q19_half(const T *__r
             if (mode == MID) {
                 phase_a<NH, MID>(acc, stage, xbuf, ebuf, p, lane, row, half);
             } else if (mode == FIRST) {
-#pragma unroll
-                for (int a = 0; a < 3; ++a)
-#pragma unroll
-                    for (int j = 0; j < 2; ++j)
-#pragma unroll
-                        for (int c = 0; c < 4; ++c) acc[a][j][c] = b2(0.f);
                 phase_a<NH, FIRST>(acc, stage, xbuf, ebuf, p, lane, row, half);
             } else {
                 phase_a<NH, LAST>(acc, stage, xbuf, ebuf, p, lane, row, half);
@@ -550,12 +553,6 @@ __global__ void __launch_bounds__(HG<NH>::NTH, 2 / NH) k_d3q19_half(const T *__r
             rotate(acc);
         } else {
             phase_b<NH, LAST>(acc, xbuf, ebuf, out, p, lane, row, half, it.col, it.zb - 1);
-#pragma unroll
-            for (int a = 1; a < 3; ++a)
-#pragma unroll
-                for (int j = 0; j < 2; ++j)
-#pragma unroll
-                    for (int c = 0; c < 4; ++c) acc[a][j][c] = b2(0.f);
         }
         it.next();
     }
