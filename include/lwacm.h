@@ -108,7 +108,7 @@ enum {
     LWACM_OPT_FORCE_FIELD = 12,   /* 1 = reserve room in the workspace for a per-node
                                      acceleration field (lwacm_set_force_field); only
                                      before lwacm_bind; single-domain contexts only */
-    LWACM_OPT_BATCH_TILE = 13     /* how domains are cut into CTA tiles. Batched contexts:
+    LWACM_OPT_BATCH_TILE = 13,    /* how domains are cut into CTA tiles. Batched contexts:
                                      0 (default) = runs of 256 consecutive nodes, one
                                      thread per node, every lattice; 1..6 = 2D tiles of
                                      30x6, 30x14, 62x6, 30x30, 62x14, 126x6 nodes, D2Q9
@@ -116,6 +116,12 @@ enum {
                                      values computed once per node and exchanged in
                                      shared memory. Single D2Q9 contexts: the shape of
                                      kernel 6. Any time; lwacm_autotune picks one. */
+    LWACM_OPT_NU_P = 14           /* viscosity nu_p of the pressure (density) update,
+                                     i.e. omega_p of Section 2.2 item 3 (Eq. FDcompact c
+                                     relaxed with omega_p, momentum with omega): in (0,
+                                     1/6], or 0 = nu (default). Single periodic domains
+                                     only (LWACM_E_UNSUPPORTED otherwise); runs on the
+                                     generic kernel; the adjoint refuses nu_p != nu. */
 };
 
 /* Create a single-domain context.

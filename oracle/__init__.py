@@ -62,6 +62,7 @@ def _load():
         i, d, l = ctypes.c_int, ctypes.c_double, ctypes.c_long
         lib.lwo_step.argtypes = [i, i, i, i, d, i, d, P, P, l, P, P, P, P, i]
         lib.lwo_step_force_field.argtypes = [i, i, i, i, d, i, d, P, P, P, P, l, P, P, P, P, i]
+        lib.lwo_step_nu_p.argtypes = [i, i, i, i, d, d, P, P, P, P, l, P, P, P, P, i]
         lib.lwo_lattice_tables.argtypes = [i, IP, P, IP]
         lib.lwo_equilibria.argtypes = [i, d, P, P, P]
         lib.lwo_bgk_init.argtypes = [i, i, i, i, P, P, P, P, P]
@@ -140,6 +141,24 @@ def step(Q, d, ux, uy, uz=None, *, nu, bc=PERIODIC, nsteps=1, rho0=1.0, lid=None
     nx, ny, nz = _dims(Q, d)
     rc = lib.lwo_step(Q, nx, ny, nz, float(nu), int(bc), float(rho0), _p(_vec3(lid)),
                       _p(_vec3(force)), int(nsteps), _p(d), _p(ux), _p(uy), _p(uz), int(nthreads))
+    if rc != 0:
+        raise ValueError(f"oracle step failed: {rc}")
+    return (d, ux, uy) if Q == 9 else (d, ux, uy, uz)
+
+
+def step_nu_p(Q, d, ux, uy, uz=None, *, nu, nu_p, force=None, g=None, nsteps=1, nthreads=0):
+    """As step() on a periodic domain, with the pressure (density) update relaxed
+    with nu_p (omega_p of Section 2.2, item 3) and the momentum with nu; force: a
+    constant acceleration, g: a per-node field (gx, gy[, gz])."""
+    lib = _load()
+    d, ux, uy, uz = _f64(d), _f64(ux), _f64(uy), _f64(uz)
+    nx, ny, nz = _dims(Q, d)
+    gx = gy = gz = None
+    if g is not None:
+        gx, gy = _f64(g[0]), _f64(g[1])
+        gz = _f64(g[2]) if len(g) > 2 and g[2] is not None else None
+    rc = lib.lwo_step_nu_p(Q, nx, ny, nz, float(nu), float(nu_p), _p(_vec3(force)), _p(gx), _p(gy), _p(gz),
+                           int(nsteps), _p(d), _p(ux), _p(uy), _p(uz), int(nthreads))
     if rc != 0:
         raise ValueError(f"oracle step failed: {rc}")
     return (d, ux, uy) if Q == 9 else (d, ux, uy, uz)

@@ -17,6 +17,8 @@
  *   - omega from nu by Eq. viscosity2, nu = (1/omega - 1/2)/3;
  *   - half-way link-wise walls, Eq. ACM2.0cccbb2, with the moving-wall term of
  *     Eq. ACM2.0ccccbb (Section 2.6, rules of the 2D cavity in Section 2.6.1);
+ *   - a separate relaxation frequency omega_p for the pressure update (Section
+ *     2.2, item 3), periodic domains (lwo_step_nu_p);
  *   - external forcing, Eq. force, with a constant acceleration or a per-node
  *     field g(x) (lwo_step_force_field; a time-dependent g is applied by one call
  *     per step);
@@ -192,13 +194,17 @@ static void load_u(const double *ux, const double *uy, const double *uz, long k,
     u[2] = uz ? uz[k] : 0.0;
 }
 
-/* One node of Eq. ACM2.0 (with walls and forcing): writes rho(x,t+1), u(x,t+1). */
-static void node_update(const lwo_lattice *L, const lwo_geom *G, double omega, double rho0,
+/* One node of Eq. ACM2.0 (with walls and forcing): writes rho(x,t+1), u(x,t+1).
+ * omega_p: the relaxation frequency of the pressure (density) update (Section 2.2,
+ * item 3: Eq. FDcompact c with omega_p); the density sums populations built with
+ * a_p = 2(omega_p-1)/omega_p, the momentum those built with a (periodic links). */
+static void node_update(const lwo_lattice *L, const lwo_geom *G, double omega, double omega_p, double rho0,
                         const double lid[3], const double force[3], int has_force, const int x[3],
                         const double *d, const double *ux, const double *uy, const double *uz,
                         double *rho_new, double u_new[3]) {
     const long k = ((long)x[2] * G->n[1] + x[1]) * G->n[0] + x[0];
     const double a = 2.0 * (omega - 1.0) / omega;  /* Eq. ACM2.0 */
+    const double ap = 2.0 * (omega_p - 1.0) / omega_p;
     const double bw = 2.0 / omega - 1.0;           /* Eq. ACM2.0ccccbb */
     const double zero[3] = {0.0, 0.0, 0.0};
     double ux_[3];
@@ -208,12 +214,13 @@ static void node_update(const lwo_lattice *L, const lwo_geom *G, double omega, d
     for (int i = 0; i < L->Q; ++i) {
         int above;
         const long s = source_of(G, x, L->c[i], &above);
-        double f;
+        double f, fp;
         if (s >= 0) {
             double us[3];
             load_u(ux, uy, uz, s, us);
             const double rs = 1.0 + d[s];
             f = feq(L, i, rs, us) + a * (feqo(L, i, rx, ux_) - feqo(L, i, rs, us));
+            fp = feq(L, i, rs, us) + ap * (feqo(L, i, rx, ux_) - feqo(L, i, rs, us));
         } else {
             /* link i arrives from outside: Eq. ACM2.0cccbb2 with BB(i) pointing at
              * the wall, plus the moving-wall correction of Eq. ACM2.0ccccbb */
@@ -221,9 +228,13 @@ static void node_update(const lwo_lattice *L, const lwo_geom *G, double omega, d
             const double *uw = above ? lid : zero;
             f = feq(L, j, rx, ux_) + (2.0 - 2.0 / omega) * 2.0 * feqo(L, i, rx, ux_) +
                 bw * 2.0 * feqo(L, i, rho0, uw);
+            fp = f;
         }
-        if (has_force) f += feqo(L, i, rx, force); /* Eq. force */
-        rho += f;
+        if (has_force) {
+            f += feqo(L, i, rx, force); /* Eq. force */
+            fp += feqo(L, i, rx, force);
+        }
+        rho += fp;
         for (int b = 0; b < 3; ++b) m[b] += L->c[i][b] * f;
     }
     *rho_new = rho;
@@ -251,7 +262,7 @@ static double omega_of_nu(double nu) { return 2.0 / (6.0 * nu + 1.0); } /* Eq. v
 /* Advance (d,ux,uy[,uz]) in place by nsteps of Eq. ACM2.0, with the external
  * acceleration g of Eq. force either one constant vector (force, or NULL) or, when
  * gx is not NULL, a per-node field (gx, gy[, gz]) held fixed over the nsteps. */
-static int run_steps(int Q, int nx, int ny, int nz, double nu, int bc, double rho0,
+static int run_steps(int Q, int nx, int ny, int nz, double nu, double nu_p, int bc, double rho0,
                      const double *lid, const double *force, const double *gx, const double *gy,
                      const double *gz, long nsteps, double *d, double *ux, double *uy, double *uz,
                      int nthreads) {
@@ -262,8 +273,10 @@ static int run_steps(int Q, int nx, int ny, int nz, double nu, int bc, double rh
     if (!(nu > 0.0)) return -4;
     if (Q == 19 && !uz) return -5;
     if (gx && !gy) return -3;
+    if (!(nu_p > 0.0)) return -4;
+    if (nu_p != nu && bc != LWO_PERIODIC) return -7; /* omega_p only on periodic domains */
     set_threads(nthreads);
-    const double omega = omega_of_nu(nu);
+    const double omega = omega_of_nu(nu), omega_p = omega_of_nu(nu_p);
     const double zero[3] = {0.0, 0.0, 0.0};
     const double *lid_ = lid ? lid : zero;
     const double *frc = force ? force : zero;
@@ -290,7 +303,7 @@ static int run_steps(int Q, int nx, int ny, int nz, double nu, int bc, double rh
                         gk[2] = gz ? gz[k] : 0.0;
                         g = gk;
                     }
-                    node_update(&L, &G, omega, rho0, lid_, g, has_force, x, src[0], src[1],
+                    node_update(&L, &G, omega, omega_p, rho0, lid_, g, has_force, x, src[0], src[1],
                                 src[2], src[3], &r, u);
                     dst[0][k] = r - 1.0;
                     dst[1][k] = u[0];
@@ -316,7 +329,7 @@ static int run_steps(int Q, int nx, int ny, int nz, double nu, int bc, double rh
 int lwo_step(int Q, int nx, int ny, int nz, double nu, int bc, double rho0, const double *lid,
              const double *force, long nsteps, double *d, double *ux, double *uy, double *uz,
              int nthreads) {
-    return run_steps(Q, nx, ny, nz, nu, bc, rho0, lid, force, NULL, NULL, NULL, nsteps, d, ux, uy,
+    return run_steps(Q, nx, ny, nz, nu, nu, bc, rho0, lid, force, NULL, NULL, NULL, nsteps, d, ux, uy,
                      uz, nthreads);
 }
 
@@ -328,7 +341,17 @@ int lwo_step_force_field(int Q, int nx, int ny, int nz, double nu, int bc, doubl
                          const double *lid, const double *gx, const double *gy, const double *gz,
                          long nsteps, double *d, double *ux, double *uy, double *uz, int nthreads) {
     if (!gx || !gy) return -3;
-    return run_steps(Q, nx, ny, nz, nu, bc, rho0, lid, NULL, gx, gy, gz, nsteps, d, ux, uy, uz,
+    return run_steps(Q, nx, ny, nz, nu, nu, bc, rho0, lid, NULL, gx, gy, gz, nsteps, d, ux, uy, uz,
+                     nthreads);
+}
+
+/* As lwo_step / lwo_step_force_field on a periodic domain, with a separate
+ * viscosity nu_p for the pressure (density) update (omega_p of Section 2.2, item 3).
+ * force (constant) or gx, gy[, gz] (per node) may be NULL. */
+int lwo_step_nu_p(int Q, int nx, int ny, int nz, double nu, double nu_p, const double *force,
+                  const double *gx, const double *gy, const double *gz, long nsteps, double *d, double *ux,
+                  double *uy, double *uz, int nthreads) {
+    return run_steps(Q, nx, ny, nz, nu, nu_p, LWO_PERIODIC, 1.0, NULL, force, gx, gy, gz, nsteps, d, ux, uy, uz,
                      nthreads);
 }
 
@@ -544,7 +567,7 @@ static void adjoint_step(const lwo_lattice *L, const lwo_geom *G, double omega, 
                 const long k = ((long)z * G->n[1] + y) * G->n[0] + xx;
                 /* forward recompute of rho+, u+ at x */
                 double rn, un[3];
-                node_update(L, G, omega, rho0, lid, force, has_force, x, d, ux, uy, uz, &rn, un);
+                node_update(L, G, omega, omega, rho0, lid, force, has_force, x, d, ux, uy, uz, &rn, un);
                 const double lun[3] = {lux_n[k], luy_n[k], luz_n ? luz_n[k] : 0.0};
                 /* u+ = m / rho+, rho+ = 1 + d+ */
                 double mbar[3], rbar = ld_n[k];

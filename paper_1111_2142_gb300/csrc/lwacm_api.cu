@@ -27,7 +27,7 @@ inline int esize(int storage) { return storage == LWACM_F32 ? 4 : 2; }
 
 struct lwacm_ctx {
     int Q = 0, D = 0, nx = 0, ny = 0, nz = 0, bc = 0, nf = 0;
-    double nu = 0;
+    double nu = 0, nu_p = 0;  // nu_p: viscosity of the pressure update (0: nu)
     long long N = 0, Nal = 0;
     double lid[3] = {0, 0, 0}, force[3] = {0, 0, 0}, rho0 = 1.0;
     int storage = LWACM_F32;
@@ -142,6 +142,7 @@ StepParams params(const lwacm_ctx *c) {
     }
     p.has_force = (c->force[0] != 0 || c->force[1] != 0 || c->force[2] != 0) ? 1 : 0;
     p.gfield = (c->ff_active && c->ws) ? (const float *)(c->ws + c->off_ff) : nullptr;
+    p.sdelta = c->nu_p > 0 ? (float)(18.0 * (c->nu_p - c->nu)) : 0.f;
     p.err = c->ws ? (int *)(c->ws + c->off_err) : nullptr;
     p.walled[0] = p.walled[1] = p.walled[2] = 0;
     p.lid_axis = c->D - 1;
@@ -590,6 +591,15 @@ lwacm_status lwacm_set_option(lwacm_ctx *c, int key, double v) {
             c->batch_mode = m;
             break;
         }
+        case LWACM_OPT_NU_P: {
+            if (c->nbatch) return fail(c, LWACM_E_UNSUPPORTED, "no omega_p in batched contexts");
+            if (v != 0 && !(v > 0.0 && v <= 1.0 / 6.0 + 1e-15))
+                return fail(c, LWACM_E_RANGE, "nu_p must be in (0, 1/6] (or 0: same as nu)");
+            if (v != 0 && c->bc != LWACM_BC_PERIODIC)
+                return fail(c, LWACM_E_UNSUPPORTED, "omega_p is for periodic domains");
+            c->nu_p = v;
+            break;
+        }
         case LWACM_OPT_BATCH_TILE: {
             const int k = (int)v;
             if (k < 0 || k >= batch_shapes() || (double)k != v) return fail(c, LWACM_E_ARG, "unknown tile shape");
@@ -852,6 +862,7 @@ lwacm_status lwacm_forward_record(lwacm_ctx *c, long long T, int stride, void *w
     if (c->storage != LWACM_F32 || c->bc != LWACM_BC_PERIODIC || c->nbatch)
         return fail(c, LWACM_E_UNSUPPORTED, "the adjoint needs one periodic domain with FP32 storage");
     if (c->ff_active) return fail(c, LWACM_E_UNSUPPORTED, "the adjoint does not take a force field");
+    if (c->nu_p > 0 && c->nu_p != c->nu) return fail(c, LWACM_E_UNSUPPORTED, "the adjoint needs omega_p = omega");
     const AdjLayout L = adj_layout(c, T, stride);
     if (bytes < L.bytes) return fail(c, LWACM_E_NOMEM, "adjoint workspace smaller than lwacm_adjoint_workspace_bytes");
     c->adj = (char *)ws;

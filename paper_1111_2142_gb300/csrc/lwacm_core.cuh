@@ -89,6 +89,7 @@ struct StepParams {
     float force[3];     // g of Eq. force
     int has_force;
     const float *gfield;  // per-node g of Eq. force (D FP32 fields, stride fstride) or null
+    float sdelta;         // 18 (nu_p - nu): pressure update relaxed with omega_p (0: omega_p = omega)
     int walled[3];      // 1 = half-way walls on both ends of this axis
     int lid_axis;       // axis whose top wall moves with the lid velocity
     int *err;           // device error word (bounded waits that gave up set it)

@@ -8,7 +8,9 @@ namespace lwacm {
 
 // Full update of one node (x,y,z). With WALLS, sources beyond a walled face are
 // replaced by the bounce-back rule; without, every axis wraps (periodic).
-template <int Q, bool WALLS, typename T>
+// With NUP the density sums its link values with s_p = 18 nu_p in place of s
+// (omega_p of Section 2.2, item 3: only the pressure update changes).
+template <int Q, bool WALLS, bool NUP = false, typename T>
 __device__ __forceinline__ void node_update(const T *__restrict__ in, T *__restrict__ out,
                                             const StepParams &p, int x, int y, int z) {
     using L = Lat<Q>;
@@ -19,7 +21,7 @@ __device__ __forceinline__ void node_update(const T *__restrict__ in, T *__restr
     const float uz = (Q == 19) ? ldf(Win + k) : 0.f;
     const float rx = 1.f + dx;
     const float qx = fmaf(ux, ux, fmaf(uy, uy, uz * uz));
-    float dd = 0.f, jx = 0.f, jy = 0.f, jz = 0.f;
+    float dd = 0.f, jx = 0.f, jy = 0.f, jz = 0.f, dsp = 0.f;
 #pragma unroll
     for (int i = 0; i < Q; ++i) {
         const int cx = L::c(i, 0), cy = L::c(i, 1), cz = L::c(i, 2);
@@ -44,6 +46,7 @@ __device__ __forceinline__ void node_update(const T *__restrict__ in, T *__restr
             const float e = cx * us + cy * vs + cz * ws;
             const float q = fmaf(us, us, fmaf(vs, vs, ws * ws));
             g = link_g(L::w(i), ds, 1.f + ds, e, q, p.s);
+            if (NUP) dsp = fmaf(L::w(i) * (1.f + ds), e, dsp);  // sum of w rho e
         } else {
             // Eq. ACM2.0cccbb2 + Eq. ACM2.0ccccbb: own outgoing BB(i) value, reflected
             const float e = -(cx * ux + cy * uy + cz * uz);
@@ -58,6 +61,7 @@ __device__ __forceinline__ void node_update(const T *__restrict__ in, T *__restr
         if (cy) jy += cy > 0 ? g : -g;
         if (cz) jz += cz > 0 ? g : -g;
     }
+    if (NUP) dd = fmaf(p.sdelta, dsp, dd);
     jx = fmaf(p.a * rx, ux, jx);
     jy = fmaf(p.a * rx, uy, jy);
     jz = fmaf(p.a * rx, uz, jz);

@@ -22,7 +22,7 @@ F32, BF16, F16, F64 = 0, 1, 2, 3
 DEVICE, HOST = 0, 1
 OPT_LID_X, OPT_LID_Y, OPT_LID_Z, OPT_FORCE_X, OPT_FORCE_Y, OPT_FORCE_Z = range(6)
 OPT_RHO0, OPT_STORAGE, OPT_GRAPH_CHUNK, OPT_KERNEL = 6, 7, 8, 9
-OPT_BATCH_MODE, OPT_TEST_WITHHOLD, OPT_FORCE_FIELD, OPT_BATCH_TILE = 10, 11, 12, 13
+OPT_BATCH_MODE, OPT_TEST_WITHHOLD, OPT_FORCE_FIELD, OPT_BATCH_TILE, OPT_NU_P = 10, 11, 12, 13, 14
 # 2D tile shapes of the D2Q9 batched kernel (LWACM_OPT_BATCH_TILE 1..6); 0 = 1D runs
 BATCH_TILE_SHAPES = {0: None, 1: (30, 6), 2: (30, 14), 3: (62, 6), 4: (30, 30), 5: (62, 14), 6: (126, 6)}
 

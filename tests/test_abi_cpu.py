@@ -182,3 +182,16 @@ def test_autotune_needs_a_bound_fresh_context(lib):
     assert st == lw.OK
     assert lib.lwacm_autotune(h, None, 0, None, 0) == lw.E_STATE  # not bound
     lib.lwacm_destroy(h)
+
+
+def test_nu_p_option(lib):
+    from paper_1111_2142_gb300 import lwacm as lw
+    st, h = _create(lib, 19, 16, 8, 4, 0.02, 0)
+    assert lib.lwacm_set_option(h, lw.OPT_NU_P, 0.1) == lw.OK
+    assert lib.lwacm_set_option(h, lw.OPT_NU_P, 0.2) == lw.E_RANGE
+    assert lib.lwacm_set_option(h, lw.OPT_NU_P, -0.1) == lw.E_RANGE
+    assert lib.lwacm_set_option(h, lw.OPT_NU_P, 0.0) == lw.OK
+    lib.lwacm_destroy(h)
+    st, hc = _create(lib, 9, 16, 16, 1, 0.02, 1)
+    assert lib.lwacm_set_option(hc, lw.OPT_NU_P, 0.1) == lw.E_UNSUPPORTED
+    lib.lwacm_destroy(hc)

@@ -342,3 +342,23 @@ def test_full_size_256_d3q19_one_step(lw):
     eu, ed = errs(got, ref, 0.02)
     print(f"[{name}] d3q19 256^3 x2: du/u0={eu:.2e} dd/d={ed:.2e}")
     assert eu < 1e-6 and ed < 1e-5
+
+
+@pytest.mark.parametrize("Q,shape", [(9, (23, 37)), (9, (64, 64)), (19, (9, 11, 13)), (19, (8, 16, 128))])
+def test_nu_p_matches_oracle(lw, Q, shape):
+    """omega_p (LWACM_OPT_NU_P): the density sums link values built with 18 nu_p,
+    the momentum with 18 nu; runs on the generic kernel."""
+    f = inputs.smooth_random(shape, seed=17, u_amp=0.05, d_amp=0.01)
+    nz = 1 if Q == 9 else shape[0]
+    ny, nx = shape[-2], shape[-1]
+    sim = lw.Lwacm(Q, nx, ny, nz, 0.01)
+    sim.set_option(lw.OPT_NU_P, 0.12)
+    assert sim.kernel_name.startswith("generic")
+    sim.set_fields(*f)
+    sim.step(40)
+    got = sim.get_fields()
+    sim.close()
+    ref = oracle.step_nu_p(Q, *f, nu=0.01, nu_p=0.12, nsteps=40)
+    eu, ed = errs(got, ref, 0.05)
+    print(f"nu_p Q{Q} {shape}: du/U={eu:.2e} dd/d={ed:.2e}")
+    assert eu < 1e-5 and ed < 1e-4
