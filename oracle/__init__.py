@@ -62,6 +62,7 @@ def _load():
         i, d, l = ctypes.c_int, ctypes.c_double, ctypes.c_long
         lib.lwo_step.argtypes = [i, i, i, i, d, i, d, P, P, l, P, P, P, P, i]
         lib.lwo_step_force_field.argtypes = [i, i, i, i, d, i, d, P, P, P, P, l, P, P, P, P, i]
+        lib.lwo_step_scalar.argtypes = [i, i, i, i, d, d, l, P, P, P, P, P, i]
         lib.lwo_step_nu_p.argtypes = [i, i, i, i, d, d, P, P, P, P, l, P, P, P, P, i]
         lib.lwo_lattice_tables.argtypes = [i, IP, P, IP]
         lib.lwo_equilibria.argtypes = [i, d, P, P, P]
@@ -162,6 +163,20 @@ def step_nu_p(Q, d, ux, uy, uz=None, *, nu, nu_p, force=None, g=None, nsteps=1, 
     if rc != 0:
         raise ValueError(f"oracle step failed: {rc}")
     return (d, ux, uy) if Q == 9 else (d, ux, uy, uz)
+
+
+def step_scalar(Q, d, ux, uy, uz=None, *, T, nu, alpha, nsteps=1, nthreads=0):
+    """Advance the flow (Eq. ACM2.0) and a passive scalar T (Eq. ACM2.0t, thermal
+    diffusivity alpha, advected by the flow velocity at each step's time level) on a
+    periodic domain; returns (d, ux, uy[, uz], T)."""
+    lib = _load()
+    d, ux, uy, uz, T = _f64(d), _f64(ux), _f64(uy), _f64(uz), _f64(T)
+    nx, ny, nz = _dims(Q, d)
+    rc = lib.lwo_step_scalar(Q, nx, ny, nz, float(nu), float(alpha), int(nsteps), _p(d), _p(ux), _p(uy), _p(uz),
+                             _p(T), int(nthreads))
+    if rc != 0:
+        raise ValueError(f"oracle scalar step failed: {rc}")
+    return (d, ux, uy, T) if Q == 9 else (d, ux, uy, uz, T)
 
 
 def step_force_field(Q, d, ux, uy, uz=None, *, nu, g, bc=PERIODIC, nsteps=1, rho0=1.0, lid=None,

@@ -17,6 +17,7 @@
  *   - omega from nu by Eq. viscosity2, nu = (1/omega - 1/2)/3;
  *   - half-way link-wise walls, Eq. ACM2.0cccbb2, with the moving-wall term of
  *     Eq. ACM2.0ccccbb (Section 2.6, rules of the 2D cavity in Section 2.6.1);
+ *   - a passive scalar advected and diffused by Eq. ACM2.0t (lwo_step_scalar);
  *   - a separate relaxation frequency omega_p for the pressure update (Section
  *     2.2, item 3), periodic domains (lwo_step_nu_p);
  *   - external forcing, Eq. force, with a constant acceleration or a per-node
@@ -353,6 +354,71 @@ int lwo_step_nu_p(int Q, int nx, int ny, int nz, double nu, double nu_p, const d
                   double *uy, double *uz, int nthreads) {
     return run_steps(Q, nx, ny, nz, nu, nu_p, LWO_PERIODIC, 1.0, NULL, force, gx, gy, gz, nsteps, d, ux, uy, uz,
                      nthreads);
+}
+
+/* ---------------------------------------------------------------------------
+ * Passive scalar (Appendix "Asymptotic analysis for energy equation", Eq. ACM2.0t):
+ *   g_i(x,t+1) = g_i^(e)(x-c_i,t) + 2(omega_t-1)/omega_t [g_i^(e,e)(x,t) - g_i^(e,e)(x-c_i,t)]
+ * with T = sum_i g_i advected by the flow velocity u(x,t) and diffused with
+ * alpha = (1/omega_t - 1/2)/3 (Eq. diffusivity2). The equilibrium satisfies the
+ * stated moments sum g^(e) = T, sum c g^(e) = T u, sum c c g^(e) = u u + T/3 I:
+ *   g_i^(e)(T,u) = w_i [T (1 + 3 c_i.u) + 9/2 (c_i.u)^2 - 3/2 |u|^2],
+ * and g^(e,e) is its even part in u (Eq. feqe).
+ * ------------------------------------------------------------------------- */
+static double geq(const lwo_lattice *L, int i, double T, const double u[3]) {
+    const double e = L->c[i][0] * u[0] + L->c[i][1] * u[1] + L->c[i][2] * u[2];
+    const double q = u[0] * u[0] + u[1] * u[1] + u[2] * u[2];
+    return L->w[i] * (T * (1.0 + 3.0 * e) + 4.5 * e * e - 1.5 * q);
+}
+static double geqe(const lwo_lattice *L, int i, double T, const double u[3]) {
+    const double mu[3] = {-u[0], -u[1], -u[2]};
+    return 0.5 * (geq(L, i, T, u) + geq(L, i, T, mu)); /* Eq. feqe */
+}
+
+/* Advance (d, u) by Eq. ACM2.0 and the scalar T by Eq. ACM2.0t (with u at the
+ * time level t of each step), nsteps times, on a periodic domain; alpha > 0. */
+int lwo_step_scalar(int Q, int nx, int ny, int nz, double nu, double alpha, long nsteps, double *d,
+                    double *ux, double *uy, double *uz, double *T, int nthreads) {
+    lwo_lattice L;
+    lwo_geom G;
+    if (make_lattice(Q, &L)) return -1;
+    if (make_geom(&L, nx, ny, nz, LWO_PERIODIC, &G)) return -2;
+    if (!(alpha > 0.0) || !T) return -4;
+    const long N = (long)nx * ny * nz;
+    const double omega_t = omega_of_nu(alpha); /* same relation as nu(omega) */
+    const double at = 2.0 * (omega_t - 1.0) / omega_t;
+    double *Tn = (double *)malloc(sizeof(double) * N);
+    if (!Tn) return -6;
+    set_threads(nthreads);
+    for (long t = 0; t < nsteps; ++t) {
+#pragma omp parallel for collapse(2) schedule(static)
+        for (int z = 0; z < nz; ++z)
+            for (int y = 0; y < ny; ++y)
+                for (int xx = 0; xx < nx; ++xx) {
+                    const int x[3] = {xx, y, z};
+                    const long k = ((long)z * ny + y) * nx + xx;
+                    double u[3];
+                    load_u(ux, uy, uz, k, u);
+                    double acc = 0.0;
+                    for (int i = 0; i < L.Q; ++i) {
+                        int above;
+                        const long s = source_of(&G, x, L.c[i], &above);
+                        double us[3];
+                        load_u(ux, uy, uz, s, us);
+                        acc += geq(&L, i, T[s], us) + at * (geqe(&L, i, T[k], u) - geqe(&L, i, T[s], us));
+                    }
+                    Tn[k] = acc;
+                }
+        /* the flow moves on with the same step */
+        const int rc = lwo_step(Q, nx, ny, nz, nu, LWO_PERIODIC, 1.0, NULL, NULL, 1, d, ux, uy, uz, nthreads);
+        if (rc) {
+            free(Tn);
+            return rc;
+        }
+        memcpy(T, Tn, sizeof(double) * N);
+    }
+    free(Tn);
+    return 0;
 }
 
 int lwo_lattice_tables(int Q, int *c, double *w, int *bb) {
