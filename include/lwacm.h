@@ -116,12 +116,20 @@ enum {
                                      values computed once per node and exchanged in
                                      shared memory. Single D2Q9 contexts: the shape of
                                      kernel 6. Any time; lwacm_autotune picks one. */
-    LWACM_OPT_NU_P = 14           /* viscosity nu_p of the pressure (density) update,
+    LWACM_OPT_NU_P = 14,          /* viscosity nu_p of the pressure (density) update,
                                      i.e. omega_p of Section 2.2 item 3 (Eq. FDcompact c
                                      relaxed with omega_p, momentum with omega): in (0,
                                      1/6], or 0 = nu (default). Single periodic domains
                                      only (LWACM_E_UNSUPPORTED otherwise); runs on the
                                      generic kernel; the adjoint refuses nu_p != nu. */
+    LWACM_OPT_SCALAR_ALPHA = 15   /* > 0: carry a passive scalar T (Eq. ACM2.0t, the
+                                     thermal LW-ACM of Appendix "Asymptotic analysis for
+                                     energy equation") with diffusivity alpha in (0, 1/6]
+                                     (alpha = (1/omega_t - 1/2)/3, Eq. diffusivity2),
+                                     advected by the flow velocity at each step's time
+                                     level; 0 = none (default). Before lwacm_bind (it
+                                     adds one field to the workspace); single periodic
+                                     domains only; runs on the generic kernel. */
 };
 
 /* Create a single-domain context.
@@ -186,6 +194,15 @@ lwacm_status lwacm_set_fields(lwacm_ctx *ctx, const void *d, const void *ux, con
  * Errors: LWACM_E_STATE (nothing reserved, or not bound), LWACM_E_ARG. */
 lwacm_status lwacm_set_force_field(lwacm_ctx *ctx, const void *gx, const void *gy, const void *gz,
                                    int dtype, int where);
+
+/* The passive scalar T of LWACM_OPT_SCALAR_ALPHA: copy nx*ny*nz values of type
+ * dtype (LWACM_F32 / LWACM_F64) in from, or out to, the device or the host (where),
+ * rounded to the storage type on the way in. lwacm_set_fields sets the scalar to
+ * zero, so call lwacm_set_scalar after it. Stream-ordered; lwacm_get_scalar
+ * synchronises when where == LWACM_HOST. Errors: LWACM_E_STATE (no scalar, not
+ * bound, or fields not set), LWACM_E_ARG. */
+lwacm_status lwacm_set_scalar(lwacm_ctx *ctx, const void *T, int dtype, int where);
+lwacm_status lwacm_get_scalar(lwacm_ctx *ctx, void *T, int dtype, int where);
 
 /* Advance the state by n >= 0 time steps of Eq. ACM2.0 (plus the wall pass of
  * Eqs. ACM2.0cccbb2 / ACM2.0ccccbb and the forcing of Eq. force when enabled).

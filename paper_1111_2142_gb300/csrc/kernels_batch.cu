@@ -54,6 +54,8 @@ __device__ __forceinline__ void tile_update(const T *__restrict__ in, T *__restr
     p.has_force = 0;
     p.gfield = nullptr;
     p.sdelta = 0.f;
+    p.scalar = 0;
+    p.at = 0.f;
     p.lid_axis = 0;
     p.err = nullptr;
     for (int c = 0; c < 3; ++c) {
@@ -416,7 +418,7 @@ bool batch_shape_supported(int Q, int storage, int k) {
 }
 
 bool tiles2d_supported(int Q, int storage, const StepParams &p) {
-    return Q == 9 && p.nz == 1 && !p.has_force && !p.gfield && p.sdelta == 0.f &&
+    return Q == 9 && p.nz == 1 && !p.has_force && !p.gfield && p.sdelta == 0.f && !p.scalar &&
            (storage == STORE_F32 || storage == STORE_BF16 || storage == STORE_F16);
 }
 

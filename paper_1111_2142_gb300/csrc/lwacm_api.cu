@@ -28,6 +28,8 @@ inline int esize(int storage) { return storage == LWACM_F32 ? 4 : 2; }
 struct lwacm_ctx {
     int Q = 0, D = 0, nx = 0, ny = 0, nz = 0, bc = 0, nf = 0;
     double nu = 0, nu_p = 0;  // nu_p: viscosity of the pressure update (0: nu)
+    double alpha = 0;         // diffusivity of the passive scalar (0: no scalar)
+    int nsc = 0;              // scalar fields stored after the flow fields (0 or 1)
     long long N = 0, Nal = 0;
     double lid[3] = {0, 0, 0}, force[3] = {0, 0, 0}, rho0 = 1.0;
     int storage = LWACM_F32;
@@ -97,7 +99,7 @@ void layout(lwacm_ctx *c) {
     size_t off = 0;
     for (int b = 0; b < 2; ++b) {
         c->off_buf[b] = off;
-        off = align_up(off + fbytes * c->nf, kAlign);
+        off = align_up(off + fbytes * (c->nf + c->nsc), kAlign);
     }
     c->off_stage = off;
     off = align_up(off + (size_t)c->Nal * 8, kAlign);
@@ -143,6 +145,8 @@ StepParams params(const lwacm_ctx *c) {
     p.has_force = (c->force[0] != 0 || c->force[1] != 0 || c->force[2] != 0) ? 1 : 0;
     p.gfield = (c->ff_active && c->ws) ? (const float *)(c->ws + c->off_ff) : nullptr;
     p.sdelta = c->nu_p > 0 ? (float)(18.0 * (c->nu_p - c->nu)) : 0.f;
+    p.scalar = c->nsc;
+    p.at = (float)(1.0 - 6.0 * c->alpha);  // a_t = 2(omega_t - 1)/omega_t, alpha = (1/omega_t - 1/2)/3
     p.err = c->ws ? (int *)(c->ws + c->off_err) : nullptr;
     p.walled[0] = p.walled[1] = p.walled[2] = 0;
     p.lid_axis = c->D - 1;
@@ -409,7 +413,7 @@ lwacm_status apply_cand(lwacm_ctx *c, const Cand &k) {
 
 // the rest state (all fields zero) in buffer 0, marked as set
 lwacm_status tune_zero_state(lwacm_ctx *c) {
-    CK(c, cudaMemsetAsync(bufp(c, 0), 0, field_bytes(c) * c->nf, c->stream), "zero state");
+    CK(c, cudaMemsetAsync(bufp(c, 0), 0, field_bytes(c) * (c->nf + c->nsc), c->stream), "zero state");
     c->cur = 0;
     c->has_fields = true;
     c->steps = 0;
@@ -591,6 +595,18 @@ lwacm_status lwacm_set_option(lwacm_ctx *c, int key, double v) {
             c->batch_mode = m;
             break;
         }
+        case LWACM_OPT_SCALAR_ALPHA: {
+            if (c->nbatch) return fail(c, LWACM_E_UNSUPPORTED, "no scalar in batched contexts");
+            if (c->bound) return fail(c, LWACM_E_STATE, "the scalar is set up before lwacm_bind");
+            if (v != 0 && !(v > 0.0 && v <= 1.0 / 6.0 + 1e-15))
+                return fail(c, LWACM_E_RANGE, "alpha must be in (0, 1/6] (or 0: no scalar)");
+            if (v != 0 && c->bc != LWACM_BC_PERIODIC)
+                return fail(c, LWACM_E_UNSUPPORTED, "the scalar is for periodic domains");
+            c->alpha = v;
+            c->nsc = v != 0 ? 1 : 0;
+            layout(c);
+            break;
+        }
         case LWACM_OPT_NU_P: {
             if (c->nbatch) return fail(c, LWACM_E_UNSUPPORTED, "no omega_p in batched contexts");
             if (v != 0 && !(v > 0.0 && v <= 1.0 / 6.0 + 1e-15))
@@ -698,6 +714,8 @@ lwacm_status lwacm_set_fields(lwacm_ctx *c, const void *d, const void *ux, const
         }
         CK(c, launch_convert_in(c->storage, dtype, dsrc, fd, c->N, c->stream), "convert in");
     }
+    if (c->nsc)  // the scalar starts at zero until lwacm_set_scalar
+        CK(c, cudaMemsetAsync(dst + (size_t)c->nf * field_bytes(c), 0, field_bytes(c), c->stream), "zero scalar");
     c->has_fields = true;
     c->steps = 0;
     return LWACM_OK;
@@ -829,6 +847,49 @@ lwacm_status lwacm_get_fields(lwacm_ctx *c, void *d, void *ux, void *uy, void *u
     return LWACM_OK;
 }
 
+lwacm_status lwacm_set_scalar(lwacm_ctx *c, const void *T, int dtype, int where) {
+    lwacm_status s = ready(c, true);
+    if (s != LWACM_OK) return s;
+    if (!c->nsc) return fail(c, LWACM_E_STATE, "no scalar (LWACM_OPT_SCALAR_ALPHA before bind)");
+    if (!T) return fail(c, LWACM_E_ARG, "null scalar");
+    if (dtype != LWACM_F32 && dtype != LWACM_F64) return fail(c, LWACM_E_ARG, "dtype must be F32 or F64");
+    if (where != LWACM_DEVICE && where != LWACM_HOST) return fail(c, LWACM_E_ARG, "bad location");
+    char *fd = (char *)bufp(c, c->cur) + (size_t)c->nf * field_bytes(c);
+    const size_t nbytes = (size_t)c->N * (dtype == LWACM_F64 ? 8 : 4);
+    if (where == LWACM_HOST && dtype == LWACM_F32 && c->storage == LWACM_F32) {
+        CK(c, cudaMemcpyAsync(fd, T, nbytes, cudaMemcpyHostToDevice, c->stream), "H2D");
+        return LWACM_OK;
+    }
+    const void *src = T;
+    if (where == LWACM_HOST) {
+        CK(c, cudaMemcpyAsync(c->ws + c->off_stage, T, nbytes, cudaMemcpyHostToDevice, c->stream), "H2D stage");
+        src = c->ws + c->off_stage;
+    }
+    CK(c, launch_convert_in(c->storage, dtype, src, fd, c->N, c->stream), "convert in");
+    return LWACM_OK;
+}
+
+lwacm_status lwacm_get_scalar(lwacm_ctx *c, void *T, int dtype, int where) {
+    lwacm_status s = ready(c, true);
+    if (s != LWACM_OK) return s;
+    if (!c->nsc) return fail(c, LWACM_E_STATE, "no scalar (LWACM_OPT_SCALAR_ALPHA before bind)");
+    if (!T) return fail(c, LWACM_E_ARG, "null scalar");
+    if (dtype != LWACM_F32 && dtype != LWACM_F64) return fail(c, LWACM_E_ARG, "dtype must be F32 or F64");
+    if (where != LWACM_DEVICE && where != LWACM_HOST) return fail(c, LWACM_E_ARG, "bad location");
+    const char *fs = (const char *)bufp(c, c->cur) + (size_t)c->nf * field_bytes(c);
+    const size_t nbytes = (size_t)c->N * (dtype == LWACM_F64 ? 8 : 4);
+    if (where == LWACM_HOST && dtype == LWACM_F32 && c->storage == LWACM_F32) {
+        CK(c, cudaMemcpyAsync(T, fs, nbytes, cudaMemcpyDeviceToHost, c->stream), "D2H");
+    } else {
+        void *ddst = where == LWACM_HOST ? (void *)(c->ws + c->off_stage) : T;
+        CK(c, launch_convert_out(c->storage, dtype, fs, ddst, c->N, c->stream), "convert out");
+        if (where == LWACM_HOST)
+            CK(c, cudaMemcpyAsync(T, ddst, nbytes, cudaMemcpyDeviceToHost, c->stream), "D2H stage");
+    }
+    if (where == LWACM_HOST) CK(c, cudaStreamSynchronize(c->stream), "sync");
+    return LWACM_OK;
+}
+
 lwacm_status lwacm_diagnostics(lwacm_ctx *c, double out[8]) {
     lwacm_status s = ready(c, true);
     if (s != LWACM_OK) return s;
@@ -863,6 +924,7 @@ lwacm_status lwacm_forward_record(lwacm_ctx *c, long long T, int stride, void *w
         return fail(c, LWACM_E_UNSUPPORTED, "the adjoint needs one periodic domain with FP32 storage");
     if (c->ff_active) return fail(c, LWACM_E_UNSUPPORTED, "the adjoint does not take a force field");
     if (c->nu_p > 0 && c->nu_p != c->nu) return fail(c, LWACM_E_UNSUPPORTED, "the adjoint needs omega_p = omega");
+    if (c->nsc) return fail(c, LWACM_E_UNSUPPORTED, "the adjoint does not carry the scalar");
     const AdjLayout L = adj_layout(c, T, stride);
     if (bytes < L.bytes) return fail(c, LWACM_E_NOMEM, "adjoint workspace smaller than lwacm_adjoint_workspace_bytes");
     c->adj = (char *)ws;

@@ -90,6 +90,8 @@ struct StepParams {
     int has_force;
     const float *gfield;  // per-node g of Eq. force (D FP32 fields, stride fstride) or null
     float sdelta;         // 18 (nu_p - nu): pressure update relaxed with omega_p (0: omega_p = omega)
+    int scalar;           // 1: a passive scalar T is stored after the flow fields (Eq. ACM2.0t)
+    float at;             // 1 - 6 alpha = 2(omega_t - 1)/omega_t of the scalar
     int walled[3];      // 1 = half-way walls on both ends of this axis
     int lid_axis;       // axis whose top wall moves with the lid velocity
     int *err;           // device error word (bounded waits that gave up set it)

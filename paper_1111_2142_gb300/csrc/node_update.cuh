@@ -9,8 +9,12 @@ namespace lwacm {
 // Full update of one node (x,y,z). With WALLS, sources beyond a walled face are
 // replaced by the bounce-back rule; without, every axis wraps (periodic).
 // With NUP the density sums its link values with s_p = 18 nu_p in place of s
-// (omega_p of Section 2.2, item 3: only the pressure update changes).
-template <int Q, bool WALLS, bool NUP = false, typename T>
+// (omega_p of Section 2.2, item 3: only the pressure update changes). With SC a
+// passive scalar T (the field after the flow fields) is advanced by Eq. ACM2.0t
+// with the velocity at time t:
+//   T+(x) = a_t T(x) + sum_i w_i [(1 - a_t)(T + 9/2 e^2 - 3/2 |u|^2) + 3 T e](x - c_i),
+// the own node's even parts summing to a_t T(x) (sum_i w_i (9/2 e^2 - 3/2 |u|^2) = 0).
+template <int Q, bool WALLS, bool NUP = false, bool SC = false, typename T>
 __device__ __forceinline__ void node_update(const T *__restrict__ in, T *__restrict__ out,
                                             const StepParams &p, int x, int y, int z) {
     using L = Lat<Q>;
@@ -21,7 +25,9 @@ __device__ __forceinline__ void node_update(const T *__restrict__ in, T *__restr
     const float uz = (Q == 19) ? ldf(Win + k) : 0.f;
     const float rx = 1.f + dx;
     const float qx = fmaf(ux, ux, fmaf(uy, uy, uz * uz));
-    float dd = 0.f, jx = 0.f, jy = 0.f, jz = 0.f, dsp = 0.f;
+    float dd = 0.f, jx = 0.f, jy = 0.f, jz = 0.f, dsp = 0.f, ts = 0.f;
+    const T *Tin = in + (Q == 19 ? 4 : 3) * p.fstride;
+    const float omt = 1.f - p.at;
 #pragma unroll
     for (int i = 0; i < Q; ++i) {
         const int cx = L::c(i, 0), cy = L::c(i, 1), cz = L::c(i, 2);
@@ -47,6 +53,11 @@ __device__ __forceinline__ void node_update(const T *__restrict__ in, T *__restr
             const float q = fmaf(us, us, fmaf(vs, vs, ws * ws));
             g = link_g(L::w(i), ds, 1.f + ds, e, q, p.s);
             if (NUP) dsp = fmaf(L::w(i) * (1.f + ds), e, dsp);  // sum of w rho e
+            if (SC) {
+                const float tsrc = ldf(Tin + s);
+                const float even = tsrc + fmaf(4.5f * e, e, -1.5f * q);
+                ts = fmaf(L::w(i), fmaf(omt, even, 3.f * tsrc * e), ts);
+            }
         } else {
             // Eq. ACM2.0cccbb2 + Eq. ACM2.0ccccbb: own outgoing BB(i) value, reflected
             const float e = -(cx * ux + cy * uy + cz * uz);
@@ -80,6 +91,7 @@ __device__ __forceinline__ void node_update(const T *__restrict__ in, T *__restr
     stf(out + p.fstride + k, jx / rn);
     stf(out + 2 * p.fstride + k, jy / rn);
     if (Q == 19) stf(out + 3 * p.fstride + k, jz / rn);
+    if (SC) stf(out + (Q == 19 ? 4 : 3) * p.fstride + k, fmaf(p.at, ldf(Tin + k), ts));
 }
 
 }  // namespace lwacm

@@ -23,6 +23,7 @@ DEVICE, HOST = 0, 1
 OPT_LID_X, OPT_LID_Y, OPT_LID_Z, OPT_FORCE_X, OPT_FORCE_Y, OPT_FORCE_Z = range(6)
 OPT_RHO0, OPT_STORAGE, OPT_GRAPH_CHUNK, OPT_KERNEL = 6, 7, 8, 9
 OPT_BATCH_MODE, OPT_TEST_WITHHOLD, OPT_FORCE_FIELD, OPT_BATCH_TILE, OPT_NU_P = 10, 11, 12, 13, 14
+OPT_SCALAR_ALPHA = 15
 # 2D tile shapes of the D2Q9 batched kernel (LWACM_OPT_BATCH_TILE 1..6); 0 = 1D runs
 BATCH_TILE_SHAPES = {0: None, 1: (30, 6), 2: (30, 14), 3: (62, 6), 4: (30, 30), 5: (62, 14), 6: (126, 6)}
 
@@ -72,6 +73,8 @@ def load():
         "lwacm_selftest_reciprocal": [vp, vp, ll, vp],
         "lwacm_set_force_field": [vp, vp, vp, vp, i, i],
         "lwacm_autotune": [vp, ctypes.c_char_p, i, ctypes.c_char_p, ctypes.c_size_t],
+        "lwacm_set_scalar": [vp, vp, i, i],
+        "lwacm_get_scalar": [vp, vp, i, i],
     }
     for name, args in sig.items():
         fn = getattr(lib, name)
@@ -111,7 +114,7 @@ class Lwacm:
 
     def __init__(self, lattice, nx, ny, nz=1, nu=0.01, bc=PERIODIC, *, storage=F32, lid=None,
                  force=None, rho0=None, kernel=0, graph_chunk=None, device=None, stream=None,
-                 force_field=False):
+                 force_field=False, scalar_alpha=None):
         lib = load()
         self.lattice, self.nx, self.ny, self.nz = int(lattice), int(nx), int(ny), int(nz)
         self.nu, self.bc = float(nu), int(bc)
@@ -121,8 +124,12 @@ class Lwacm:
                               ctypes.byref(h))
         if st != OK:
             raise LwacmError(st, "lwacm_create")
-        self._setup(lib, h, storage, lid, force, rho0, kernel, graph_chunk, device, stream,
-                    {OPT_FORCE_FIELD: 1} if force_field else {})
+        extra = {}
+        if force_field:
+            extra[OPT_FORCE_FIELD] = 1
+        if scalar_alpha:
+            extra[OPT_SCALAR_ALPHA] = scalar_alpha
+        self._setup(lib, h, storage, lid, force, rho0, kernel, graph_chunk, device, stream, extra)
 
     def _setup(self, lib, h, storage, lid, force, rho0, kernel, graph_chunk, device, stream,
                extra):
@@ -237,6 +244,32 @@ class Lwacm:
         else:
             for a in keep:  # the copy runs on the library's stream
                 a.record_stream(self.stream)
+
+    def set_scalar(self, T):
+        """The passive scalar (needs scalar_alpha at construction; after set_fields):
+        a numpy array (host, FP64) or a torch tensor (CUDA or host, FP32/FP64)."""
+        torch = _torch()
+        if isinstance(T, np.ndarray):
+            keep = np.ascontiguousarray(T, dtype=np.float64).reshape(-1)
+            dtype, where = F64, HOST
+        else:
+            keep = T.contiguous().reshape(-1)
+            dtype = {torch.float32: F32, torch.float64: F64}[keep.dtype]
+            where = DEVICE if keep.is_cuda else HOST
+        assert (keep.size if isinstance(keep, np.ndarray) else keep.numel()) == self.n_nodes
+        self._check(self._lib.lwacm_set_scalar(self._h, _ptr(keep), dtype, where))
+        if where == HOST:
+            self._hold = keep
+            self.sync()
+            self._hold = None
+        else:
+            keep.record_stream(self.stream)
+
+    def get_scalar(self):
+        """The passive scalar as an FP64 numpy array of the domain's shape."""
+        out = np.empty(self.n_nodes, dtype=np.float64)
+        self._check(self._lib.lwacm_get_scalar(self._h, out.ctypes.data, F64, HOST))
+        return out.reshape(self.shape)
 
     def autotune(self, cache=None, steps=0):
         """lwacm_autotune: time the candidate kernel configurations and keep the

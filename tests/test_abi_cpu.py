@@ -195,3 +195,20 @@ def test_nu_p_option(lib):
     st, hc = _create(lib, 9, 16, 16, 1, 0.02, 1)
     assert lib.lwacm_set_option(hc, lw.OPT_NU_P, 0.1) == lw.E_UNSUPPORTED
     lib.lwacm_destroy(hc)
+
+
+def test_scalar_option(lib):
+    from paper_1111_2142_gb300 import lwacm as lw
+    st, h = _create(lib, 9, 16, 12, 1, 0.02, 0)
+    n0 = ctypes.c_size_t()
+    assert lib.lwacm_workspace_bytes(h, ctypes.byref(n0)) == lw.OK
+    assert lib.lwacm_set_option(h, lw.OPT_SCALAR_ALPHA, 0.3) == lw.E_RANGE
+    assert lib.lwacm_set_option(h, lw.OPT_SCALAR_ALPHA, 0.05) == lw.OK
+    n1 = ctypes.c_size_t()
+    assert lib.lwacm_workspace_bytes(h, ctypes.byref(n1)) == lw.OK
+    assert n1.value >= n0.value + 2 * 16 * 12 * 4  # one more field in each buffer
+    assert lib.lwacm_set_scalar(h, ctypes.c_void_p(16), lw.F32, lw.DEVICE) == lw.E_STATE  # not bound
+    lib.lwacm_destroy(h)
+    st, hc = _create(lib, 9, 16, 16, 1, 0.02, 1)
+    assert lib.lwacm_set_option(hc, lw.OPT_SCALAR_ALPHA, 0.05) == lw.E_UNSUPPORTED
+    lib.lwacm_destroy(hc)
