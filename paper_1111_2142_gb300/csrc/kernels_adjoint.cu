@@ -44,71 +44,102 @@ __global__ void __launch_bounds__(256) k_adj_prep(const float *__restrict__ sn, 
     }
 }
 
-// lambda at t from (Dbar, Jbar) gathered at the downwind neighbours and the state at t
+// lambda at t from (Dbar, Jbar) gathered at the downwind neighbours and the state
+// at t, with the (Dbar, Jbar) fields staged in shared memory: a CTA of
+// 32 x 8 threads takes an x-y tile of the domain and marches along z through a run
+// of planes, keeping the planes z-1, z, z+1 of the tile plus a one-node frame in a
+// ring of three shared-memory slots (one plane loaded per step of the march).
+constexpr int ATX = 32, ATY = 8, AZC = 16;
+constexpr int AW = ATX + 2, AH = ATY + 2, APL = AW * AH;
+
 template <int Q>
-__global__ void __launch_bounds__(256) k_adj_gather(const float *__restrict__ st, const float *__restrict__ dj,
-                                                    float *__restrict__ lam_out, StepParams p,
-                                                    double *__restrict__ nu_partial) {
+__global__ void __launch_bounds__(ATX *ATY) k_adj_gather_tiled(const float *__restrict__ st,
+                                                               const float *__restrict__ dj,
+                                                               float *__restrict__ lam_out, StepParams p, int ntx,
+                                                               int nty, int nzc, double *__restrict__ nu_partial) {
     using L = Lat<Q>;
+    constexpr int NF = Q == 19 ? 4 : 3;
+    __shared__ float ring[3][NF][APL];
+    const int tid = (int)threadIdx.x, tx = tid % ATX, ty = tid / ATX;
+    const long long plane = (long long)p.nx * p.ny;
     double nu_acc = 0.0;
-    for (long long k = (long long)blockIdx.x * blockDim.x + threadIdx.x; k < p.N;
-         k += (long long)gridDim.x * blockDim.x) {
-        const int x = (int)(k % p.nx);
-        const long long r = k / p.nx;
-        const int y = (int)(r % p.ny);
-        const int z = (int)(r / p.ny);
-        const float d = st[k], u = st[p.fstride + k], v = st[2 * p.fstride + k];
-        const float w = Q == 19 ? st[3 * p.fstride + k] : 0.f;
-        const float rho = 1.f + d;
-        const float q = fmaf(u, u, fmaf(v, v, w * w));
-        float ld = 0.f, lu = 0.f, lv = 0.f, lw = 0.f, ln = 0.f;
+    const long long nitems = (long long)ntx * nty * nzc;
+    for (long long item = blockIdx.x; item < nitems; item += gridDim.x) {
+        const int bx = (int)(item % ntx), by = (int)((item / ntx) % nty), bz = (int)(item / ((long long)ntx * nty));
+        const int x0 = bx * ATX, y0 = by * ATY, za = bz * AZC;
+        const int zb = za + AZC < p.nz ? za + AZC : p.nz;
+        auto load = [&](int z) {  // plane z (periodic) of the tile + frame into its ring slot
+            int zl = z % p.nz;
+            if (zl < 0) zl += p.nz;
+            const int slot = ((z % 3) + 3) % 3;
+            for (int e = tid; e < APL; e += ATX * ATY) {
+                int gx = (x0 + e % AW - 1) % p.nx, gy = (y0 + e / AW - 1) % p.ny;
+                if (gx < 0) gx += p.nx;
+                if (gy < 0) gy += p.ny;
+                const long long k = (long long)zl * plane + (long long)gy * p.nx + gx;
 #pragma unroll
-        for (int i = 0; i < Q; ++i) {
-            const int cx = L::c(i, 0), cy = L::c(i, 1), cz = L::c(i, 2);
-            int rx = x + cx, ry = y + cy, rz = z + cz;
-            rx = rx < 0 ? rx + p.nx : (rx >= p.nx ? rx - p.nx : rx);
-            ry = ry < 0 ? ry + p.ny : (ry >= p.ny ? ry - p.ny : ry);
-            rz = rz < 0 ? rz + p.nz : (rz >= p.nz ? rz - p.nz : rz);
-            const long long kr = ((long long)rz * p.ny + ry) * p.nx + rx;
-            float gb = __ldg(dj + kr);  // gbar_i = Dbar + c_i . Jbar at y + c_i
-            if (cx) gb = fmaf((float)cx, __ldg(dj + p.fstride + kr), gb);
-            if (cy) gb = fmaf((float)cy, __ldg(dj + 2 * p.fstride + kr), gb);
-            if (Q == 19 && cz) gb = fmaf((float)cz, __ldg(dj + 3 * p.fstride + kr), gb);
-            const float e = cx * u + cy * v + cz * w;
-            const float wg = L::w(i) * gb;
-            // dg/dd = w [1 + s e + 9/2 e^2 - 3/2 q]
-            ld = fmaf(wg, 1.f + fmaf(e, fmaf(4.5f, e, p.s), -1.5f * q), ld);
-            // dg/du = w rho [s c + 9 e c - 3 u]
-            const float cc = rho * (p.s + 9.f * e);
-            const float m3 = -3.f * rho;
-            lu = fmaf(wg, fmaf(cc, (float)cx, m3 * u), lu);
-            lv = fmaf(wg, fmaf(cc, (float)cy, m3 * v), lv);
-            if (Q == 19) lw = fmaf(wg, fmaf(cc, (float)cz, m3 * w), lw);
-            ln = fmaf(wg, rho * e, ln);  // dg/ds = w rho e; ds/dnu = 18
+                for (int f = 0; f < NF; ++f) ring[slot][f][e] = __ldg(dj + f * p.fstride + k);
+            }
+        };
+        __syncthreads();  // the previous item's last reads are done
+        load(za - 1);
+        load(za);
+        for (int z = za; z < zb; ++z) {
+            load(z + 1);
+            __syncthreads();
+            const int x = x0 + tx, y = y0 + ty;
+            if (x < p.nx && y < p.ny) {
+                const long long k = (long long)z * plane + (long long)y * p.nx + x;
+                const float d = st[k], u = st[p.fstride + k], v = st[2 * p.fstride + k];
+                const float w = Q == 19 ? st[3 * p.fstride + k] : 0.f;
+                const float rho = 1.f + d;
+                const float q = fmaf(u, u, fmaf(v, v, w * w));
+                float ld = 0.f, lu = 0.f, lv = 0.f, lw = 0.f, ln = 0.f;
+#pragma unroll
+                for (int i = 0; i < Q; ++i) {
+                    const int cx = L::c(i, 0), cy = L::c(i, 1), cz = L::c(i, 2);
+                    const int slot = (((z + cz) % 3) + 3) % 3;
+                    const int e = (ty + 1 + cy) * AW + tx + 1 + cx;
+                    float gb = ring[slot][0][e];  // gbar_i = Dbar + c_i . Jbar at y + c_i
+                    if (cx) gb = fmaf((float)cx, ring[slot][1][e], gb);
+                    if (cy) gb = fmaf((float)cy, ring[slot][2][e], gb);
+                    if (Q == 19 && cz) gb = fmaf((float)cz, ring[slot][3][e], gb);
+                    const float ee = cx * u + cy * v + cz * w;
+                    const float wg = L::w(i) * gb;
+                    ld = fmaf(wg, 1.f + fmaf(ee, fmaf(4.5f, ee, p.s), -1.5f * q), ld);
+                    const float cc = rho * (p.s + 9.f * ee);
+                    const float m3 = -3.f * rho;
+                    lu = fmaf(wg, fmaf(cc, (float)cx, m3 * u), lu);
+                    lv = fmaf(wg, fmaf(cc, (float)cy, m3 * v), lv);
+                    if (Q == 19) lw = fmaf(wg, fmaf(cc, (float)cz, m3 * w), lw);
+                    ln = fmaf(wg, rho * ee, ln);
+                }
+                const int own = (ty + 1) * AW + tx + 1, os = ((z % 3) + 3) % 3;
+                const float jx = ring[os][1][own], jy = ring[os][2][own];
+                const float jz = Q == 19 ? ring[os][3][own] : 0.f;
+                const float ju = u * jx + v * jy + w * jz;
+                ld = fmaf(p.a, ju, ld);
+                if (p.has_force) ld += p.force[0] * jx + p.force[1] * jy + p.force[2] * jz;
+                lu = fmaf(p.a * rho, jx, lu);
+                lv = fmaf(p.a * rho, jy, lv);
+                lw = fmaf(p.a * rho, jz, lw);
+                lam_out[k] = ld;
+                lam_out[p.fstride + k] = lu;
+                lam_out[2 * p.fstride + k] = lv;
+                if (Q == 19) lam_out[3 * p.fstride + k] = lw;
+                nu_acc += 18.0 * (double)ln - 6.0 * (double)rho * (double)ju;
+            }
+            __syncthreads();  // slot (z - 1) % 3 is reloaded next
         }
-        const float jx = __ldg(dj + p.fstride + k), jy = __ldg(dj + 2 * p.fstride + k);
-        const float jz = Q == 19 ? __ldg(dj + 3 * p.fstride + k) : 0.f;
-        const float ju = u * jx + v * jy + w * jz;
-        // post-combine a rho u (and forcing rho G): d/dd and d/du
-        ld = fmaf(p.a, ju, ld);
-        if (p.has_force) ld += p.force[0] * jx + p.force[1] * jy + p.force[2] * jz;
-        lu = fmaf(p.a * rho, jx, lu);
-        lv = fmaf(p.a * rho, jy, lv);
-        lw = fmaf(p.a * rho, jz, lw);
-        lam_out[k] = ld;
-        lam_out[p.fstride + k] = lu;
-        lam_out[2 * p.fstride + k] = lv;
-        if (Q == 19) lam_out[3 * p.fstride + k] = lw;
-        nu_acc += 18.0 * (double)ln - 6.0 * (double)rho * (double)ju;
     }
-    __shared__ double sh[256];
-    sh[threadIdx.x] = nu_acc;
+    __shared__ double sh[ATX * ATY];
+    sh[tid] = nu_acc;
     __syncthreads();
-    for (int off = blockDim.x / 2; off > 0; off >>= 1) {
-        if (threadIdx.x < off) sh[threadIdx.x] += sh[threadIdx.x + off];
+    for (int off = ATX * ATY / 2; off > 0; off >>= 1) {
+        if (tid < off) sh[tid] += sh[tid + off];
         __syncthreads();
     }
-    if (threadIdx.x == 0) nu_partial[blockIdx.x] = sh[0];
+    if (tid == 0) nu_partial[blockIdx.x] = sh[0];
 }
 
 // total += sum of the partials, in a fixed order
@@ -132,14 +163,19 @@ int adjoint_partials() { return kAdjBlocks; }
 cudaError_t launch_adjoint_step(int Q, const float *state_t, const float *state_t1, const float *lam_t1,
                                 float *dj, float *lam_t, const StepParams &p, double *nu_partial,
                                 double *nu_total, cudaStream_t st) {
+    // tiled gather: x-y tiles of 32 x 8, z-runs of 16 planes; every CTA writes one
+    // partial (the grid never exceeds the partials buffer)
+    const int ntx = (p.nx + ATX - 1) / ATX, nty = (p.ny + ATY - 1) / ATY, nzc = (p.nz + AZC - 1) / AZC;
+    const long long items = (long long)ntx * nty * nzc;
+    const int grid = (int)(items < kAdjBlocks ? items : kAdjBlocks);
     if (Q == 9) {
         k_adj_prep<9><<<kAdjBlocks, 256, 0, st>>>(state_t1, lam_t1, dj, p.fstride, p.N);
-        k_adj_gather<9><<<kAdjBlocks, 256, 0, st>>>(state_t, dj, lam_t, p, nu_partial);
+        k_adj_gather_tiled<9><<<grid, ATX * ATY, 0, st>>>(state_t, dj, lam_t, p, ntx, nty, nzc, nu_partial);
     } else {
         k_adj_prep<19><<<kAdjBlocks, 256, 0, st>>>(state_t1, lam_t1, dj, p.fstride, p.N);
-        k_adj_gather<19><<<kAdjBlocks, 256, 0, st>>>(state_t, dj, lam_t, p, nu_partial);
+        k_adj_gather_tiled<19><<<grid, ATX * ATY, 0, st>>>(state_t, dj, lam_t, p, ntx, nty, nzc, nu_partial);
     }
-    k_adj_nu_sum<<<1, 256, 0, st>>>(nu_partial, kAdjBlocks, nu_total);
+    k_adj_nu_sum<<<1, 256, 0, st>>>(nu_partial, grid, nu_total);
     return cudaGetLastError();
 }
 
