@@ -94,26 +94,45 @@ __global__ void __launch_bounds__(ATX *ATY) k_adj_gather_tiled(const float *__re
                 const float w = Q == 19 ? st[3 * p.fstride + k] : 0.f;
                 const float rho = 1.f + d;
                 const float q = fmaf(u, u, fmaf(v, v, w * w));
-                float ld = 0.f, lu = 0.f, lv = 0.f, lw = 0.f, ln = 0.f;
+                // weighted moments of gbar_i = Dbar + c_i . Jbar over the links:
+                //   G0 = sum w gbar, G1 = sum w c gbar, G2 = sum w c c gbar, so that
+                //   sum_i gbar_i dg_i/dd = (1 - 3/2 q) G0 + s u.G1 + 9/2 u.G2.u,
+                //   sum_i gbar_i dg_i/du = rho (s G1 + 9 G2.u - 3 u G0),
+                //   sum_i gbar_i dg_i/ds = rho u.G1
+                float g0 = 0.f, g1x = 0.f, g1y = 0.f, g1z = 0.f;
+                float gxx = 0.f, gyy = 0.f, gzz = 0.f, gxy = 0.f, gxz = 0.f, gyz = 0.f;
 #pragma unroll
                 for (int i = 0; i < Q; ++i) {
                     const int cx = L::c(i, 0), cy = L::c(i, 1), cz = L::c(i, 2);
+                    const float wi = L::w(i);
                     const int slot = (((z + cz) % 3) + 3) % 3;
                     const int e = (ty + 1 + cy) * AW + tx + 1 + cx;
-                    float gb = ring[slot][0][e];  // gbar_i = Dbar + c_i . Jbar at y + c_i
+                    float gb = ring[slot][0][e];
                     if (cx) gb = fmaf((float)cx, ring[slot][1][e], gb);
                     if (cy) gb = fmaf((float)cy, ring[slot][2][e], gb);
                     if (Q == 19 && cz) gb = fmaf((float)cz, ring[slot][3][e], gb);
-                    const float ee = cx * u + cy * v + cz * w;
-                    const float wg = L::w(i) * gb;
-                    ld = fmaf(wg, 1.f + fmaf(ee, fmaf(4.5f, ee, p.s), -1.5f * q), ld);
-                    const float cc = rho * (p.s + 9.f * ee);
-                    const float m3 = -3.f * rho;
-                    lu = fmaf(wg, fmaf(cc, (float)cx, m3 * u), lu);
-                    lv = fmaf(wg, fmaf(cc, (float)cy, m3 * v), lv);
-                    if (Q == 19) lw = fmaf(wg, fmaf(cc, (float)cz, m3 * w), lw);
-                    ln = fmaf(wg, rho * ee, ln);
+                    g0 = fmaf(wi, gb, g0);
+                    if (cx) g1x = fmaf(wi * cx, gb, g1x);
+                    if (cy) g1y = fmaf(wi * cy, gb, g1y);
+                    if (cz) g1z = fmaf(wi * cz, gb, g1z);
+                    if (cx) gxx = fmaf(wi, gb, gxx);
+                    if (cy) gyy = fmaf(wi, gb, gyy);
+                    if (cz) gzz = fmaf(wi, gb, gzz);
+                    if (cx && cy) gxy = fmaf(wi * cx * cy, gb, gxy);
+                    if (cx && cz) gxz = fmaf(wi * cx * cz, gb, gxz);
+                    if (cy && cz) gyz = fmaf(wi * cy * cz, gb, gyz);
                 }
+                const float hx = fmaf(gxx, u, fmaf(gxy, v, gxz * w));  // G2 . u
+                const float hy = fmaf(gxy, u, fmaf(gyy, v, gyz * w));
+                const float hz = fmaf(gxz, u, fmaf(gyz, v, gzz * w));
+                const float uG1 = fmaf(u, g1x, fmaf(v, g1y, w * g1z));
+                const float uG2u = fmaf(u, hx, fmaf(v, hy, w * hz));
+                float ld = fmaf(4.5f, uG2u, fmaf(p.s, uG1, g0 * fmaf(-1.5f, q, 1.f)));
+                const float m3 = -3.f * g0;
+                float lu = rho * fmaf(p.s, g1x, fmaf(9.f, hx, m3 * u));
+                float lv = rho * fmaf(p.s, g1y, fmaf(9.f, hy, m3 * v));
+                float lw = Q == 19 ? rho * fmaf(p.s, g1z, fmaf(9.f, hz, m3 * w)) : 0.f;
+                const float ln = rho * uG1;
                 const int own = (ty + 1) * AW + tx + 1, os = ((z % 3) + 3) % 3;
                 const float jx = ring[os][1][own], jy = ring[os][2][own];
                 const float jz = Q == 19 ? ring[os][3][own] : 0.f;
