@@ -48,7 +48,8 @@ __global__ void __launch_bounds__(256) k_adj_prep(const float *__restrict__ sn, 
 // at t, with the (Dbar, Jbar) fields staged in shared memory: a CTA of
 // 32 x 8 threads takes an x-y tile of the domain and marches along z through a run
 // of planes, keeping the planes z-1, z, z+1 of the tile plus a one-node frame in a
-// ring of three shared-memory slots (one plane loaded per step of the march).
+// ring of four shared-memory slots, the plane z+2 arriving by asynchronous copies
+// while the plane z is computed.
 constexpr int ATX = 32, ATY = 8, AZC = 16;
 constexpr int AW = ATX + 2, AH = ATY + 2, APL = AW * AH;
 
@@ -59,7 +60,7 @@ __global__ void __launch_bounds__(ATX *ATY) k_adj_gather_tiled(const float *__re
                                                                int nty, int nzc, double *__restrict__ nu_partial) {
     using L = Lat<Q>;
     constexpr int NF = Q == 19 ? 4 : 3;
-    __shared__ float ring[3][NF][APL];
+    __shared__ float ring[4][NF][APL];
     const int tid = (int)threadIdx.x, tx = tid % ATX, ty = tid / ATX;
     const long long plane = (long long)p.nx * p.ny;
     double nu_acc = 0.0;
@@ -68,24 +69,37 @@ __global__ void __launch_bounds__(ATX *ATY) k_adj_gather_tiled(const float *__re
         const int bx = (int)(item % ntx), by = (int)((item / ntx) % nty), bz = (int)(item / ((long long)ntx * nty));
         const int x0 = bx * ATX, y0 = by * ATY, za = bz * AZC;
         const int zb = za + AZC < p.nz ? za + AZC : p.nz;
-        auto load = [&](int z) {  // plane z (periodic) of the tile + frame into its ring slot
+        // asynchronous copy of plane z (periodic) of the tile + frame into ring slot z % 4
+        auto issue = [&](int z) {
             int zl = z % p.nz;
             if (zl < 0) zl += p.nz;
-            const int slot = ((z % 3) + 3) % 3;
+            const int slot = ((z % 4) + 4) % 4;
             for (int e = tid; e < APL; e += ATX * ATY) {
                 int gx = (x0 + e % AW - 1) % p.nx, gy = (y0 + e / AW - 1) % p.ny;
                 if (gx < 0) gx += p.nx;
                 if (gy < 0) gy += p.ny;
                 const long long k = (long long)zl * plane + (long long)gy * p.nx + gx;
 #pragma unroll
-                for (int f = 0; f < NF; ++f) ring[slot][f][e] = __ldg(dj + f * p.fstride + k);
+                for (int f = 0; f < NF; ++f) {
+                    const unsigned dst = (unsigned)__cvta_generic_to_shared(&ring[slot][f][e]);
+                    asm volatile("cp.async.ca.shared.global [%0], [%1], 4;" ::"r"(dst), "l"(dj + f * p.fstride + k)
+                                 : "memory");
+                }
             }
+            asm volatile("cp.async.commit_group;" ::: "memory");
         };
         __syncthreads();  // the previous item's last reads are done
-        load(za - 1);
-        load(za);
+        issue(za - 1);
+        issue(za);
+        issue(za + 1);
         for (int z = za; z < zb; ++z) {
-            load(z + 1);
+            // planes z-1, z, z+1 complete (z+2 may still be in flight)
+            if (z + 2 <= zb) {
+                issue(z + 2);
+                asm volatile("cp.async.wait_group 1;" ::: "memory");
+            } else {
+                asm volatile("cp.async.wait_group 0;" ::: "memory");
+            }
             __syncthreads();
             const int x = x0 + tx, y = y0 + ty;
             if (x < p.nx && y < p.ny) {
@@ -105,7 +119,7 @@ __global__ void __launch_bounds__(ATX *ATY) k_adj_gather_tiled(const float *__re
                 for (int i = 0; i < Q; ++i) {
                     const int cx = L::c(i, 0), cy = L::c(i, 1), cz = L::c(i, 2);
                     const float wi = L::w(i);
-                    const int slot = (((z + cz) % 3) + 3) % 3;
+                    const int slot = (((z + cz) % 4) + 4) % 4;
                     const int e = (ty + 1 + cy) * AW + tx + 1 + cx;
                     float gb = ring[slot][0][e];
                     if (cx) gb = fmaf((float)cx, ring[slot][1][e], gb);
@@ -133,7 +147,7 @@ __global__ void __launch_bounds__(ATX *ATY) k_adj_gather_tiled(const float *__re
                 float lv = rho * fmaf(p.s, g1y, fmaf(9.f, hy, m3 * v));
                 float lw = Q == 19 ? rho * fmaf(p.s, g1z, fmaf(9.f, hz, m3 * w)) : 0.f;
                 const float ln = rho * uG1;
-                const int own = (ty + 1) * AW + tx + 1, os = ((z % 3) + 3) % 3;
+                const int own = (ty + 1) * AW + tx + 1, os = ((z % 4) + 4) % 4;
                 const float jx = ring[os][1][own], jy = ring[os][2][own];
                 const float jz = Q == 19 ? ring[os][3][own] : 0.f;
                 const float ju = u * jx + v * jy + w * jz;
@@ -148,7 +162,7 @@ __global__ void __launch_bounds__(ATX *ATY) k_adj_gather_tiled(const float *__re
                 if (Q == 19) lam_out[3 * p.fstride + k] = lw;
                 nu_acc += 18.0 * (double)ln - 6.0 * (double)rho * (double)ju;
             }
-            __syncthreads();  // slot (z - 1) % 3 is reloaded next
+            __syncthreads();  // slot (z - 1) % 4 is refilled next
         }
     }
     __shared__ double sh[ATX * ATY];
