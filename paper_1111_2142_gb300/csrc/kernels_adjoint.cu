@@ -63,31 +63,44 @@ __global__ void __launch_bounds__(ATX *ATY) k_adj_gather_tiled(const float *__re
     __shared__ float ring[4][NF][APL];
     const int tid = (int)threadIdx.x, tx = tid % ATX, ty = tid / ATX;
     const long long plane = (long long)p.nx * p.ny;
-    double nu_acc = 0.0;
+    double nu_acc = 0.0;  // FP64 over items; FP32 within an item's run of planes
     const long long nitems = (long long)ntx * nty * nzc;
     for (long long item = blockIdx.x; item < nitems; item += gridDim.x) {
         const int bx = (int)(item % ntx), by = (int)((item / ntx) % nty), bz = (int)(item / ((long long)ntx * nty));
         const int x0 = bx * ATX, y0 = by * ATY, za = bz * AZC;
         const int zb = za + AZC < p.nz ? za + AZC : p.nz;
+        // in-plane offsets of this thread's (at most two) tile + frame elements,
+        // wrapped periodically once per item
+        constexpr int NE = (APL + ATX * ATY - 1) / (ATX * ATY);
+        long long off2[NE];
+#pragma unroll
+        for (int r = 0; r < NE; ++r) {
+            const int e = tid + r * ATX * ATY;
+            int gx = (x0 + e % AW - 1) % p.nx, gy = (y0 + e / AW - 1) % p.ny;
+            if (gx < 0) gx += p.nx;
+            if (gy < 0) gy += p.ny;
+            off2[r] = (long long)gy * p.nx + gx;
+        }
         // asynchronous copy of plane z (periodic) of the tile + frame into ring slot z % 4
         auto issue = [&](int z) {
-            int zl = z % p.nz;
-            if (zl < 0) zl += p.nz;
-            const int slot = ((z % 4) + 4) % 4;
-            for (int e = tid; e < APL; e += ATX * ATY) {
-                int gx = (x0 + e % AW - 1) % p.nx, gy = (y0 + e / AW - 1) % p.ny;
-                if (gx < 0) gx += p.nx;
-                if (gy < 0) gy += p.ny;
-                const long long k = (long long)zl * plane + (long long)gy * p.nx + gx;
+            const int zl = z < 0 ? z + p.nz : (z >= p.nz ? z - p.nz : z);
+            const int slot = z & 3;
 #pragma unroll
-                for (int f = 0; f < NF; ++f) {
-                    const unsigned dst = (unsigned)__cvta_generic_to_shared(&ring[slot][f][e]);
-                    asm volatile("cp.async.ca.shared.global [%0], [%1], 4;" ::"r"(dst), "l"(dj + f * p.fstride + k)
-                                 : "memory");
+            for (int r = 0; r < NE; ++r) {
+                const int e = tid + r * ATX * ATY;
+                if (e < APL) {
+                    const float *src = dj + (long long)zl * plane + off2[r];
+#pragma unroll
+                    for (int f = 0; f < NF; ++f) {
+                        const unsigned dst = (unsigned)__cvta_generic_to_shared(&ring[slot][f][e]);
+                        asm volatile("cp.async.ca.shared.global [%0], [%1], 4;" ::"r"(dst), "l"(src + f * p.fstride)
+                                     : "memory");
+                    }
                 }
             }
             asm volatile("cp.async.commit_group;" ::: "memory");
         };
+        float nu_run = 0.f;
         __syncthreads();  // the previous item's last reads are done
         issue(za - 1);
         issue(za);
@@ -119,7 +132,7 @@ __global__ void __launch_bounds__(ATX *ATY) k_adj_gather_tiled(const float *__re
                 for (int i = 0; i < Q; ++i) {
                     const int cx = L::c(i, 0), cy = L::c(i, 1), cz = L::c(i, 2);
                     const float wi = L::w(i);
-                    const int slot = (((z + cz) % 4) + 4) % 4;
+                    const int slot = (z + cz) & 3;
                     const int e = (ty + 1 + cy) * AW + tx + 1 + cx;
                     float gb = ring[slot][0][e];
                     if (cx) gb = fmaf((float)cx, ring[slot][1][e], gb);
@@ -147,7 +160,7 @@ __global__ void __launch_bounds__(ATX *ATY) k_adj_gather_tiled(const float *__re
                 float lv = rho * fmaf(p.s, g1y, fmaf(9.f, hy, m3 * v));
                 float lw = Q == 19 ? rho * fmaf(p.s, g1z, fmaf(9.f, hz, m3 * w)) : 0.f;
                 const float ln = rho * uG1;
-                const int own = (ty + 1) * AW + tx + 1, os = ((z % 4) + 4) % 4;
+                const int own = (ty + 1) * AW + tx + 1, os = z & 3;
                 const float jx = ring[os][1][own], jy = ring[os][2][own];
                 const float jz = Q == 19 ? ring[os][3][own] : 0.f;
                 const float ju = u * jx + v * jy + w * jz;
@@ -160,10 +173,11 @@ __global__ void __launch_bounds__(ATX *ATY) k_adj_gather_tiled(const float *__re
                 lam_out[p.fstride + k] = lu;
                 lam_out[2 * p.fstride + k] = lv;
                 if (Q == 19) lam_out[3 * p.fstride + k] = lw;
-                nu_acc += 18.0 * (double)ln - 6.0 * (double)rho * (double)ju;
+                nu_run += fmaf(18.f, ln, -6.f * rho * ju);
             }
             __syncthreads();  // slot (z - 1) % 4 is refilled next
         }
+        nu_acc += (double)nu_run;
     }
     __shared__ double sh[ATX * ATY];
     sh[tid] = nu_acc;
