@@ -362,3 +362,39 @@ def test_nu_p_matches_oracle(lw, Q, shape):
     eu, ed = errs(got, ref, 0.05)
     print(f"nu_p Q{Q} {shape}: du/U={eu:.2e} dd/d={ed:.2e}")
     assert eu < 1e-5 and ed < 1e-4
+
+
+def test_large_domain_sampled_nodes(lw):
+    """A domain of 537M nodes (256 x 2048 x 1024, D3Q19 FP32; the fourth field
+    starts beyond 2^31 elements, so every 64-bit offset is exercised), one step on
+    the half-row kernel, checked at 300 sampled nodes: a node's new state depends
+    only on its 3 x 3 x 3 neighbourhood, so the oracle stepping that neighbourhood
+    as a periodic 3 x 3 x 3 box gives the node's exact value at its centre."""
+    import torch
+    nx, ny, nz = 256, 2048, 1024
+    g = torch.Generator(device="cuda").manual_seed(5)
+    shape = (nz, ny, nx)
+    d = (torch.rand(shape, generator=g, device="cuda") - 0.5) * 0.02
+    u = [(torch.rand(shape, generator=g, device="cuda") - 0.5) * 0.1 for _ in range(3)]
+    sim = lw.Lwacm(lw.D3Q19, nx, ny, nz, 0.02)
+    assert sim.kernel_name.startswith("half")
+    sim.set_fields(d, *u)
+    sim.step(1)
+    out = sim.fields()  # zero-copy views of the new state
+    rng = np.random.default_rng(6)
+    pts = [(int(rng.integers(nz)), int(rng.integers(ny)), int(rng.integers(nx))) for _ in range(296)]
+    pts += [(0, 0, 0), (nz - 1, ny - 1, nx - 1), (nz - 1, 0, nx - 1), (0, ny - 1, 0)]
+    worst = 0.0
+    src = [t for t in (d, *u)]
+    for (z, y, x) in pts:
+        zi = [(z + k) % nz for k in (-1, 0, 1)]
+        yi = [(y + k) % ny for k in (-1, 0, 1)]
+        xi = [(x + k) % nx for k in (-1, 0, 1)]
+        patch = [f[zi][:, yi][:, :, xi].double().cpu().numpy() for f in src]
+        ref = oracle.step(19, *patch, nu=0.02, nsteps=1)
+        got = [float(o[z, y, x]) for o in out]
+        worst = max(worst, max(abs(gv - float(r[1, 1, 1])) for gv, r in zip(got[1:], ref[1:])) / 0.05)
+        assert abs(got[0] - float(ref[0][1, 1, 1])) < 1e-6
+    print(f"537M-node domain: 300 sampled nodes, max |du| / U = {worst:.2e}")
+    assert worst < 1e-6
+    sim.close()
