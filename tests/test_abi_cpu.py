@@ -212,3 +212,12 @@ def test_scalar_option(lib):
     st, hc = _create(lib, 9, 16, 16, 1, 0.02, 1)
     assert lib.lwacm_set_option(hc, lw.OPT_SCALAR_ALPHA, 0.05) == lw.E_UNSUPPORTED
     lib.lwacm_destroy(hc)
+
+
+def test_missing_library_fails_loudly(monkeypatch, tmp_path):
+    """No CPU fallback: without the built library the binding raises."""
+    from paper_1111_2142_gb300 import lwacm as lw
+    monkeypatch.setattr(lw, "_lib", None)
+    monkeypatch.setattr(lw, "LIB_PATH", str(tmp_path / "liblwacm.so"))
+    with pytest.raises(RuntimeError, match="no CPU fallback"):
+        lw.load()
