@@ -398,3 +398,37 @@ def test_large_domain_sampled_nodes(lw):
     print(f"537M-node domain: 300 sampled nodes, max |du| / U = {worst:.2e}")
     assert worst < 1e-6
     sim.close()
+
+
+def _poisoned_step(lw, sim, nf):
+    """Fill the write buffer with NaN bytes, step once, return the new state: a
+    node the kernels fail to write shows up as NaN."""
+    esize = 4 if sim.storage == lw.F32 else 2
+    nal = (sim.n_nodes + 63) // 64 * 64
+    off1 = (nal * esize * nf + 255) // 256 * 256
+    sim.sync()
+    sim.workspace[off1:off1 + nal * esize * nf].fill_(0xFF)
+    sim.step(1)
+    return sim.get_fields()
+
+
+@pytest.mark.parametrize("case", [
+    (19, (5, 16, 256), 0, 5, 0), (19, (7, 24, 128), 0, 5, 1), (19, (3, 8, 256), 0, 2, 0), (19, (4, 16, 128), 0, 3, 0),
+    (19, (9, 11, 13), 0, 1, 0), (19, (6, 7, 5), 1, 1, 0), (9, (37, 41), 0, 6, 0), (9, (33, 30), 1, 6, 0),
+    (9, (19, 23), 2, 6, 2), (9, (19, 23), 1, 1, 0)])
+def test_every_node_is_written(lw, case):
+    """Ping-pong poisoning: every kernel, boundary and storage type writes every
+    node of the output buffer (no NaN survives one step)."""
+    Q, shape, bc, kernel, storage = case
+    f = inputs.smooth_random(shape, seed=41, u_amp=0.03, d_amp=0.01)
+    nz = 1 if Q == 9 else shape[0]
+    ny, nx = shape[-2], shape[-1]
+    lid = None if bc != 1 else ((0.05, 0.0) if Q == 9 else (0.05, 0.0, 0.0))
+    sim = lw.Lwacm(Q, nx, ny, nz, 0.02, bc, lid=lid, storage=storage)
+    sim.set_option(lw.OPT_KERNEL, kernel)
+    sim.set_fields(*f)
+    got = _poisoned_step(lw, sim, 3 if Q == 9 else 4)
+    name = sim.kernel_name
+    sim.close()
+    for g in got:
+        assert np.all(np.isfinite(g)), (name, case)
