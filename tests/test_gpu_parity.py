@@ -432,3 +432,32 @@ def test_every_node_is_written(lw, case):
     sim.close()
     for g in got:
         assert np.all(np.isfinite(g)), (name, case)
+
+
+@pytest.mark.parametrize("kernel", [0, 1])
+def test_slab_with_ghost_planes_on_the_gpu(lw, kernel):
+    """The single-domain decomposition path on one GPU (shard.SlabHalo with one
+    rank: ghosts refreshed by local plane copies through the zero-copy field
+    views): the owned planes of a slab of nz + 2 planes, stepped and refreshed
+    every step, equal the undivided periodic domain."""
+    import torch
+    from paper_1111_2142_gb300.shard import SlabHalo
+    nx, ny, nz, T = 256, 16, 9, 12
+    f = inputs.smooth_random((nz, ny, nx), seed=19, u_amp=0.04, d_amp=0.01)
+    ref_sim = lw.Lwacm(lw.D3Q19, nx, ny, nz, 0.02, kernel=kernel)
+    ref_sim.set_fields(*f)
+    ref_sim.step(T)
+    ref = ref_sim.get_fields()
+    ref_sim.close()
+    h = SlabHalo(nz, 0, 1)
+    slab = [np.concatenate([g[-1:], g, g[:1]], axis=0) for g in f]
+    sim = lw.Lwacm(lw.D3Q19, nx, ny, nz + 2, 0.02, kernel=kernel)
+    sim.set_fields(*slab)
+    for _ in range(T):
+        sim.step(1)
+        h.exchange(list(sim.fields()))
+    got = sim.get_fields()
+    name = sim.kernel_name
+    sim.close()
+    for g_, r in zip(got, ref):
+        assert float(np.max(np.abs(g_[1:nz + 1] - r))) < 1e-6, name

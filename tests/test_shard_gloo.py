@@ -7,7 +7,7 @@ import numpy as np
 import pytest
 
 from paper_1111_2142_gb300 import inputs
-from paper_1111_2142_gb300.shard import aggregate_throughput, partition
+from paper_1111_2142_gb300.shard import SlabHalo, aggregate_throughput, partition, slabs
 
 
 def test_partition_covers_and_balances():
@@ -88,3 +88,67 @@ def test_two_gloo_ranks_shard_the_ensemble():
         ref = oracle.step(9, d["d"], d["ux"], d["uy"], nu=d["nu"], nsteps=4, nthreads=1)
         for a, r in zip(res[b], ref):
             assert np.array_equal(np.asarray(a), r)
+
+
+def test_slabs_cover_every_plane():
+    for nz, ws in ((7, 3), (16, 4), (5, 5), (9, 1)):
+        s = slabs(nz, ws)
+        assert s[0][0] == 0 and s[-1][1] == nz
+        assert all(a[1] == b[0] for a, b in zip(s, s[1:]))
+        assert max(b - a for a, b in s) - min(b - a for a, b in s) <= 1
+    with pytest.raises(ValueError):
+        slabs(3, 4)
+
+
+def _slab_main(rank, ws, port, q, shape, T):
+    import torch.distributed as dist
+    os.environ.update(MASTER_ADDR="127.0.0.1", MASTER_PORT=str(port))
+    dist.init_process_group("gloo", rank=rank, world_size=ws)
+    try:
+        import oracle
+        nz = shape[0]
+        f = inputs.smooth_random(shape, seed=11, u_amp=0.05, d_amp=0.01)
+        h = SlabHalo(nz, rank, ws)
+        # owned planes plus ghosts, filled by one exchange
+        sl = [np.zeros((h.n + 2,) + shape[1:]) for _ in f]
+        for s_, g in zip(sl, f):
+            s_[1:h.n + 1] = g[h.z0:h.z1]
+        h.exchange(sl)
+        for _ in range(T):
+            sl = list(oracle.step(19, *sl, nu=0.02, nsteps=1, nthreads=1))
+            h.exchange(sl)
+        gathered = [None] * ws
+        dist.all_gather_object(gathered, (h.z0, h.z1, [h.interior(s_).tolist() for s_ in sl]))
+        if rank == 0:
+            q.put(gathered)
+    finally:
+        dist.destroy_process_group()
+
+
+@pytest.mark.parametrize("ws,shape", [(2, (6, 5, 7)), (3, (7, 4, 6))])
+def test_slab_halo_exchange_reproduces_the_single_domain(ws, shape):
+    """A periodic D3Q19 domain split along z over gloo ranks, each stepping its
+    slab with one ghost plane per side and exchanging ghosts after every step,
+    equals the undivided run bit for bit."""
+    import multiprocessing as mp
+    import oracle
+    from paper_1111_2142_gb300.shard import SlabHalo  # noqa: F401  (spawned ranks import it)
+    oracle.build()
+    T = 5
+    ctx = mp.get_context("spawn")
+    q = ctx.Queue()
+    port = _free_port()
+    procs = [ctx.Process(target=_slab_main, args=(r, ws, port, q, shape, T)) for r in range(ws)]
+    for p in procs:
+        p.start()
+    try:
+        gathered = q.get(timeout=120)
+    finally:
+        for p in procs:
+            p.join(timeout=60)
+    assert all(p.exitcode == 0 for p in procs)
+    f = inputs.smooth_random(shape, seed=11, u_amp=0.05, d_amp=0.01)
+    ref = oracle.step(19, *f, nu=0.02, nsteps=T, nthreads=1)
+    for z0, z1, parts in gathered:
+        for part, r in zip(parts, ref):
+            assert np.array_equal(np.asarray(part), r[z0:z1])
