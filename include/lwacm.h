@@ -236,9 +236,11 @@ lwacm_status lwacm_diagnostics(lwacm_ctx *ctx, double out[8]);
 /* ---- Adjoint (reverse-mode derivative of T steps) -----------------------------
  * The derivative of a scalar loss L of the state after T steps with respect to
  * the initial state (d, u) and to nu, by the chain rule through the moment form
- * of Eq. ACM2.0 (nu enters through a = 1 - 6 nu, Eq. ACM2.0nu, and the 18 nu of
- * the pre-combined values). Periodic domains with FP32 storage (and optional
- * forcing); other setups return LWACM_E_UNSUPPORTED. Memory is the caller's:
+ * of Eq. ACM2.0 (nu enters through a = 1 - 6 nu, Eq. ACM2.0nu, the 18 nu of the
+ * pre-combined values and the 36 nu rho0 of the moving-wall term). One domain with
+ * FP32 storage, any boundary (the wall rule of Eqs. ACM2.0cccbb2 / ACM2.0ccccbb is
+ * differentiated too), optional constant forcing; a force field, omega_p != omega
+ * or a passive scalar return LWACM_E_UNSUPPORTED. Memory is the caller's:
  * ceil(T/S) checkpoints of the state plus S+1 segment states and three lambda
  * states, S = stride (0 = ceil(sqrt(T))). */
 

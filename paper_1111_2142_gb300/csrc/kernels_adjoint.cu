@@ -1,5 +1,5 @@
-// Adjoint (reverse-mode derivative) of one LW-ACM step in the moment form, for
-// periodic domains with optional forcing.
+// Adjoint (reverse-mode derivative) of one LW-ACM step in the moment form, with
+// optional forcing and link-wise walls.
 //
 // Forward step (see lwacm_core.cuh), per receiver x and link i with source
 // y = x - c_i, e = c_i . u(y), q = |u(y)|^2, rho = 1 + d:
@@ -53,7 +53,10 @@ __global__ void __launch_bounds__(256) k_adj_prep(const float *__restrict__ sn, 
 constexpr int ATX = 32, ATY = 8, AZC = 16;
 constexpr int AW = ATX + 2, AH = ATY + 2, APL = AW * AH;
 
-template <int Q>
+// With WALLS, a link whose receiver x + c lies beyond a walled face is the value the
+// node itself takes for the bounced link -c (Eq. ACM2.0cccbb2): gbar = Dbar - c.Jbar
+// of the node; the moving-wall term of Eq. ACM2.0ccccbb adds its nu-derivative.
+template <int Q, bool WALLS>
 __global__ void __launch_bounds__(ATX *ATY) k_adj_gather_tiled(const float *__restrict__ st,
                                                                const float *__restrict__ dj,
                                                                float *__restrict__ lam_out, StepParams p, int ntx,
@@ -128,6 +131,7 @@ __global__ void __launch_bounds__(ATX *ATY) k_adj_gather_tiled(const float *__re
                 //   sum_i gbar_i dg_i/ds = rho u.G1
                 float g0 = 0.f, g1x = 0.f, g1y = 0.f, g1z = 0.f;
                 float gxx = 0.f, gyy = 0.f, gzz = 0.f, gxy = 0.f, gxz = 0.f, gyz = 0.f;
+                float nu_wall = 0.f;  // sum over lid links of gbar * d(wall term)/dnu
 #pragma unroll
                 for (int i = 0; i < Q; ++i) {
                     const int cx = L::c(i, 0), cy = L::c(i, 1), cz = L::c(i, 2);
@@ -138,6 +142,27 @@ __global__ void __launch_bounds__(ATX *ATY) k_adj_gather_tiled(const float *__re
                     if (cx) gb = fmaf((float)cx, ring[slot][1][e], gb);
                     if (cy) gb = fmaf((float)cy, ring[slot][2][e], gb);
                     if (Q == 19 && cz) gb = fmaf((float)cz, ring[slot][3][e], gb);
+                    if (WALLS && i > 0) {
+                        const int xr = x + cx, yr = y + cy, zr = z + cz;
+                        const bool out = (p.walled[0] && (xr < 0 || xr >= p.nx)) ||
+                                         (p.walled[1] && (yr < 0 || yr >= p.ny)) ||
+                                         (Q == 19 && p.walled[2] && (zr < 0 || zr >= p.nz));
+                        if (out) {
+                            const int os0 = z & 3, own0 = (ty + 1) * AW + tx + 1;
+                            float b = ring[os0][0][own0];
+                            if (cx) b = fmaf((float)-cx, ring[os0][1][own0], b);
+                            if (cy) b = fmaf((float)-cy, ring[os0][2][own0], b);
+                            if (Q == 19 && cz) b = fmaf((float)-cz, ring[os0][3][own0], b);
+                            gb = b;
+                            const int rl = p.lid_axis == 0 ? xr : (p.lid_axis == 1 ? yr : zr);
+                            const int nl = p.lid_axis == 0 ? p.nx : (p.lid_axis == 1 ? p.ny : p.nz);
+                            if (rl >= nl) {
+                                // wall term w (36 nu rho0)(-c.u_w) of the bounced link
+                                const float cu = cx * p.lid[0] + cy * p.lid[1] + cz * p.lid[2];
+                                nu_wall = fmaf(gb, -wi * cu, nu_wall);
+                            }
+                        }
+                    }
                     g0 = fmaf(wi, gb, g0);
                     if (cx) g1x = fmaf(wi * cx, gb, g1x);
                     if (cy) g1y = fmaf(wi * cy, gb, g1y);
@@ -174,6 +199,7 @@ __global__ void __launch_bounds__(ATX *ATY) k_adj_gather_tiled(const float *__re
                 lam_out[2 * p.fstride + k] = lv;
                 if (Q == 19) lam_out[3 * p.fstride + k] = lw;
                 nu_run += fmaf(18.f, ln, -6.f * rho * ju);
+                if (WALLS) nu_run = fmaf(18.f * p.wallc / p.s, nu_wall, nu_run);  // 36 rho0 = wallc / nu
             }
             __syncthreads();  // slot (z - 1) % 4 is refilled next
         }
@@ -215,12 +241,21 @@ cudaError_t launch_adjoint_step(int Q, const float *state_t, const float *state_
     const int ntx = (p.nx + ATX - 1) / ATX, nty = (p.ny + ATY - 1) / ATY, nzc = (p.nz + AZC - 1) / AZC;
     const long long items = (long long)ntx * nty * nzc;
     const int grid = (int)(items < kAdjBlocks ? items : kAdjBlocks);
+    const bool walls = p.walled[0] || p.walled[1] || p.walled[2];
     if (Q == 9) {
         k_adj_prep<9><<<kAdjBlocks, 256, 0, st>>>(state_t1, lam_t1, dj, p.fstride, p.N);
-        k_adj_gather_tiled<9><<<grid, ATX * ATY, 0, st>>>(state_t, dj, lam_t, p, ntx, nty, nzc, nu_partial);
+        if (walls)
+            k_adj_gather_tiled<9, true><<<grid, ATX * ATY, 0, st>>>(state_t, dj, lam_t, p, ntx, nty, nzc, nu_partial);
+        else
+            k_adj_gather_tiled<9, false><<<grid, ATX * ATY, 0, st>>>(state_t, dj, lam_t, p, ntx, nty, nzc, nu_partial);
     } else {
         k_adj_prep<19><<<kAdjBlocks, 256, 0, st>>>(state_t1, lam_t1, dj, p.fstride, p.N);
-        k_adj_gather_tiled<19><<<grid, ATX * ATY, 0, st>>>(state_t, dj, lam_t, p, ntx, nty, nzc, nu_partial);
+        if (walls)
+            k_adj_gather_tiled<19, true><<<grid, ATX * ATY, 0, st>>>(state_t, dj, lam_t, p, ntx, nty, nzc,
+                                                                     nu_partial);
+        else
+            k_adj_gather_tiled<19, false><<<grid, ATX * ATY, 0, st>>>(state_t, dj, lam_t, p, ntx, nty, nzc,
+                                                                      nu_partial);
     }
     k_adj_nu_sum<<<1, 256, 0, st>>>(nu_partial, grid, nu_total);
     return cudaGetLastError();

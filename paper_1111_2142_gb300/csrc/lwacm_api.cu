@@ -920,8 +920,8 @@ lwacm_status lwacm_forward_record(lwacm_ctx *c, long long T, int stride, void *w
     if (s != LWACM_OK) return s;
     if (T < 0 || stride < 0 || !ws) return fail(c, LWACM_E_ARG, "T >= 0, stride >= 0, workspace required");
     if (((uintptr_t)ws) % kAlign) return fail(c, LWACM_E_ARG, "adjoint workspace not 256-byte aligned");
-    if (c->storage != LWACM_F32 || c->bc != LWACM_BC_PERIODIC || c->nbatch)
-        return fail(c, LWACM_E_UNSUPPORTED, "the adjoint needs one periodic domain with FP32 storage");
+    if (c->storage != LWACM_F32 || c->nbatch)
+        return fail(c, LWACM_E_UNSUPPORTED, "the adjoint needs one domain with FP32 storage");
     if (c->ff_active) return fail(c, LWACM_E_UNSUPPORTED, "the adjoint does not take a force field");
     if (c->nu_p > 0 && c->nu_p != c->nu) return fail(c, LWACM_E_UNSUPPORTED, "the adjoint needs omega_p = omega");
     if (c->nsc) return fail(c, LWACM_E_UNSUPPORTED, "the adjoint does not carry the scalar");

@@ -25,11 +25,11 @@ def lw():
     return lwacm
 
 
-def gpu_grad(lw, Q, f, target, nu, T, stride=0, force=None):
+def gpu_grad(lw, Q, f, target, nu, T, stride=0, force=None, bc=0, lid=None):
     import torch
     shape = f[0].shape
     nz = 1 if Q == 9 else shape[0]
-    sim = lw.Lwacm(Q, shape[-1], shape[-2], nz, nu, force=force)
+    sim = lw.Lwacm(Q, shape[-1], shape[-2], nz, nu, bc, force=force, lid=lid)
     sim.set_fields(*f)
     sim.forward_record(T, stride)
     out = sim.get_fields()
@@ -57,6 +57,27 @@ def test_adjoint_matches_fp64_oracle(lw, Q, shape, force):
     scale = max(float(np.max(np.abs(x))) for x in rg)
     err = max(float(np.max(np.abs(a - b))) for a, b in zip(g, rg)) / scale
     print(f"adjoint Q{Q} {shape} force={force}: max|dg|/max|g| = {err:.2e}, dnu rel = "
+          f"{abs(gnu - rnu) / abs(rnu):.2e}")
+    assert err < 1e-5
+    assert abs(gnu - rnu) <= 1e-4 * abs(rnu)
+
+
+@pytest.mark.parametrize("Q,shape,bc,lid", [(9, (16, 20), 1, (0.05, 0.0)), (9, (12, 14), 2, (0.03, 0.0)),
+                                           (19, (6, 8, 10), 1, (0.04, 0.02, 0.0)), (9, (11, 13), 1, None)])
+def test_adjoint_with_walls_matches_fp64_oracle(lw, Q, shape, bc, lid):
+    """The adjoint through the link-wise wall rule (bounce-back of Eq. ACM2.0cccbb2
+    and the moving-wall term of Eq. ACM2.0ccccbb, whose nu-dependence enters dL/dnu):
+    cavity with a lid, channel with a moving wall, a resting cavity."""
+    T, nu = 6, 0.03
+    st = inputs.smooth_random(shape, seed=53, u_amp=0.05, d_amp=0.01)
+    tgt = inputs.smooth_random(shape, seed=54, u_amp=0.05)[1:]
+    lid3 = None if lid is None else tuple(lid) + (0.0,) * (3 - len(lid))
+    loss, g, gnu = gpu_grad(lw, Q, st, tgt, nu, T, bc=bc, lid=lid)
+    rl, rg, rnu = oracle.grad(Q, st, tgt, nu=nu, T=T, bc=bc, lid=lid3)
+    assert abs(loss - rl) <= 1e-5 * rl
+    scale = max(float(np.max(np.abs(x))) for x in rg)
+    err = max(float(np.max(np.abs(a - b))) for a, b in zip(g, rg)) / scale
+    print(f"adjoint walls Q{Q} {shape} bc={bc} lid={lid}: max|dg|/max|g| = {err:.2e}, dnu rel = "
           f"{abs(gnu - rnu) / abs(rnu):.2e}")
     assert err < 1e-5
     assert abs(gnu - rnu) <= 1e-4 * abs(rnu)
