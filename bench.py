@@ -150,7 +150,8 @@ def run_reference(args):
     dt = time.perf_counter() - t0
     v = args.steps * n ** 3 / dt / 1e9
     cores = oracle.max_threads()
-    line = {"impl": "reference", "metric": METRIC, "value": v, "unit": "GLUPS", "n_gpus": 0,
+    # the oracle runs on the host cores of rank 0; n_gpus echoes the launch
+    line = {"impl": "reference", "metric": METRIC, "value": v, "unit": "GLUPS", "n_gpus": args.gpus,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": dt / args.steps * 1e3,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
             "data": "synthetic", "config": {"workload": WORKLOAD + " (FP64 oracle)"},
