@@ -23,6 +23,7 @@
 // moments (post-combining, Eq. ACM2.0b(c)).
 #include <cooperative_groups.h>
 
+#include "dev_cache.h"
 #include "launch.h"
 #include "lwacm_core.cuh"
 #include "node_update.cuh"
@@ -260,18 +261,16 @@ __global__ void __launch_bounds__((TW + 2) * (TH + 2)) k_batch_tiles_persistent(
     }
 }
 
-// occupancy-limited grid of a kernel: CTAs per SM x SMs, cached per kernel
+// occupancy-limited grid of a kernel: CTAs per SM x SMs, cached per kernel and
+// device (-1 when it cannot be determined)
 template <typename K>
-static int max_grid(K kern, int threads, int *cache) {
-    if (*cache == 0) {
-        int dev = 0, sms = 0, per = 0;
-        if (cudaGetDevice(&dev) != cudaSuccess ||
-            cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess ||
-            cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, kern, threads, 0) != cudaSuccess)
-            return 0;
-        *cache = per * sms;
-    }
-    return *cache;
+static int max_grid(K kern, int threads, DevSlots &cache) {
+    return per_device(cache, [&] {
+        int per = 0;
+        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, kern, threads, 0) != cudaSuccess || per < 1)
+            return -1;
+        return per * device_sms();
+    });
 }
 
 template <int TW, int TH, typename T>
@@ -279,15 +278,15 @@ cudaError_t tiles_t(const void *in, void *out, void *b0, void *b1, const BatchPa
                     int parity, bool persistent, cudaStream_t st) {
     constexpr int NT = (TW + 2) * (TH + 2);
     if (!persistent) {
-        static int cap = 0;
-        const int g = max_grid(k_batch_tiles<TW, TH, T>, NT, &cap);
+        static DevSlots cap;
+        const int g = max_grid(k_batch_tiles<TW, TH, T>, NT, cap);
         if (g < 1) return cudaErrorNotSupported;
         const long long grid = bp.ntiles < 4LL * g ? bp.ntiles : 4LL * g;
         k_batch_tiles<TW, TH, T><<<(unsigned)grid, NT, 0, st>>>((const T *)in, (T *)out, bp);
         return cudaGetLastError();
     }
-    static int cap = 0;
-    const int g = max_grid(k_batch_tiles_persistent<TW, TH, T>, NT, &cap);
+    static DevSlots cap;
+    const int g = max_grid(k_batch_tiles_persistent<TW, TH, T>, NT, cap);
     if (g < 1) return cudaErrorNotSupported;
     const long long grid = bp.ntiles < g ? bp.ntiles : g;
     T *p0 = (T *)b0, *p1 = (T *)b1;
@@ -324,8 +323,8 @@ cudaError_t tiles_storage(int storage, const void *in, void *out, void *b0, void
 template <int TW, int TH, typename T, bool WALLS>
 cudaError_t single_w(const void *in, void *out, const StepParams &p, const Walls2 &wl, cudaStream_t st) {
     constexpr int NT = (TW + 2) * (TH + 2);
-    static int cap = 0;
-    const int g = max_grid(k_d2q9_tiles<TW, TH, T, WALLS>, NT, &cap);
+    static DevSlots cap;
+    const int g = max_grid(k_d2q9_tiles<TW, TH, T, WALLS>, NT, cap);
     if (g < 1) return cudaErrorNotSupported;
     const int tilesx = (p.nx + TW - 1) / TW;
     const long long ntiles = (long long)tilesx * ((p.ny + TH - 1) / TH);
@@ -364,18 +363,9 @@ cudaError_t single_dispatch(int shape, const void *in, void *out, const StepPara
 template <int Q, typename T>
 cudaError_t persistent_t(void *b0, void *b1, const BatchParams &bp, long long nsteps, int parity,
                          cudaStream_t st) {
-    static int max_ctas = 0;
-    if (max_ctas == 0) {
-        int dev = 0, sms = 0, per = 0;
-        cudaError_t e = cudaGetDevice(&dev);
-        if (e != cudaSuccess) return e;
-        e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-        if (e != cudaSuccess) return e;
-        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_batch_persistent<Q, T>, kTile, 0);
-        if (e != cudaSuccess) return e;
-        max_ctas = per * sms;
-        if (max_ctas < 1) return cudaErrorNotSupported;
-    }
+    static DevSlots cap;
+    const int max_ctas = max_grid(k_batch_persistent<Q, T>, kTile, cap);
+    if (max_ctas < 1) return cudaErrorNotSupported;
     const long long grid = bp.ntiles < max_ctas ? bp.ntiles : max_ctas;
     T *p0 = (T *)b0, *p1 = (T *)b1;
     BatchParams q = bp;
@@ -386,14 +376,7 @@ cudaError_t persistent_t(void *b0, void *b1, const BatchParams &bp, long long ns
 
 template <typename T>
 cudaError_t step_t(int Q, const void *in, void *out, const BatchParams &bp, cudaStream_t st) {
-    static int sms = 0;
-    if (sms == 0) {
-        int dev = 0;
-        if (cudaGetDevice(&dev) != cudaSuccess ||
-            cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
-            sms = 152;
-    }
-    const long long cap = (long long)sms * 8;
+    const long long cap = (long long)device_sms() * 8;
     const unsigned grid = (unsigned)(bp.ntiles < cap ? bp.ntiles : cap);
     if (Q == 9)
         k_batch_step<9, T><<<grid, kTile, 0, st>>>((const T *)in, (T *)out, bp);

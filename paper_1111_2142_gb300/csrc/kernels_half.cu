@@ -20,6 +20,7 @@
 // warps share an SM.
 #include <stdint.h>
 
+#include "dev_cache.h"
 #include "launch.h"
 #include "lwacm_core.cuh"
 #include "tile_common.cuh"
@@ -558,26 +559,23 @@ __global__ void __launch_bounds__(HG<NH>::NTH, 2 / NH) k_d3q19_half(const T *__r
     }
 }
 
+// per device: opt in to the shared-memory size; persistent grid = CTAs per SM x
+// SMs (-1 when a CTA does not fit)
 template <int NH, typename T>
 cudaError_t prepare(int *ctas) {
-    static int state = 0, nctas = 0;
-    if (state == 0) {
-        cudaError_t e = cudaFuncSetAttribute(k_d3q19_half<NH, T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                             (int)HG<NH, T>::BYTES);
-        if (e != cudaSuccess) return e;
-        int nb = 0, dev = 0, sms = 0;
-        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_d3q19_half<NH, T>, HG<NH, T>::NTH,
-                                                          HG<NH, T>::BYTES);
-        if (e != cudaSuccess) return e;
-        e = cudaGetDevice(&dev);
-        if (e != cudaSuccess) return e;
-        e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-        if (e != cudaSuccess) return e;
-        state = nb >= 1 ? 1 : -1;
-        nctas = nb * sms;
-    }
-    if (ctas) *ctas = nctas;
-    return state == 1 ? cudaSuccess : cudaErrorNotSupported;
+    static DevSlots slots;
+    const int n = per_device(slots, [] {
+        if (cudaFuncSetAttribute(k_d3q19_half<NH, T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)HG<NH, T>::BYTES) != cudaSuccess)
+            return -1;
+        int nb = 0;
+        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_d3q19_half<NH, T>, HG<NH, T>::NTH,
+                                                          HG<NH, T>::BYTES) != cudaSuccess || nb < 1)
+            return -1;
+        return nb * device_sms();
+    });
+    if (ctas) *ctas = n;
+    return n > 0 ? cudaSuccess : cudaErrorNotSupported;
 }
 
 int half_chunk_planes(int ycols, int nz, int ctas) {

@@ -26,6 +26,7 @@
 // waits (bounded) for its own copies in flight and exits.
 #include <stdint.h>
 
+#include "dev_cache.h"
 #include "launch.h"
 #include "lwacm_core.cuh"
 #include "tile_common.cuh"
@@ -426,23 +427,20 @@ __global__ void __launch_bounds__(NTHREADS, 1)
 
 template <int VX>
 static cudaError_t prepare_vx(int *ctas) {
-    static int state = 0, nctas = 0;
-    if (state == 0) {
-        cudaError_t e = cudaFuncSetAttribute(k_d3q19_tiled<VX>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                             (int)Geo<VX>::BYTES);
-        if (e != cudaSuccess) return e;
-        int nb = 0, dev = 0, sms = 0;
-        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_d3q19_tiled<VX>, NTHREADS, Geo<VX>::BYTES);
-        if (e != cudaSuccess) return e;
-        e = cudaGetDevice(&dev);
-        if (e != cudaSuccess) return e;
-        e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-        if (e != cudaSuccess) return e;
-        state = nb >= 1 ? 1 : -1;
-        nctas = nb * sms;
-    }
-    if (ctas) *ctas = nctas;
-    return state == 1 ? cudaSuccess : cudaErrorNotSupported;
+    static DevSlots slots;
+    const int n = per_device(slots, [] {
+        if (cudaFuncSetAttribute(k_d3q19_tiled<VX>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)Geo<VX>::BYTES) != cudaSuccess)
+            return -1;
+        int nb = 0;
+        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_d3q19_tiled<VX>, NTHREADS, Geo<VX>::BYTES) !=
+                cudaSuccess ||
+            nb < 1)
+            return -1;
+        return nb * device_sms();
+    });
+    if (ctas) *ctas = n;
+    return n > 0 ? cudaSuccess : cudaErrorNotSupported;
 }
 
 // Planes per chunk: minimise the per-CTA critical path, i.e. the number of items

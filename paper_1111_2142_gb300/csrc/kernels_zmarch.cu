@@ -19,6 +19,7 @@
 // (Eq. ACM2.0b(c): + a rho u), divided by rho (moments, Section 2.1) and stored.
 // The next plane's fields are loaded into registers while the current plane's
 // exchange and stores proceed.
+#include "dev_cache.h"
 #include "launch.h"
 #include "lwacm_core.cuh"
 
@@ -357,15 +358,7 @@ __global__ void __launch_bounds__(NTHREADS, 1) k_d3q19_zmarch(const float *__res
 int chunk_for(const StepParams &p) {
     // CTAs = (ny/8) x ceil(nz/zc): aim for a whole number of waves at one CTA
     // per SM with chunks of >= 8 planes.
-    static int sms = 0;
-    if (sms == 0) {
-        int dev = 0, n = 0;
-        if (cudaGetDevice(&dev) == cudaSuccess &&
-            cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev) == cudaSuccess && n > 0)
-            sms = n;
-        else
-            sms = 152;
-    }
+    const int sms = device_sms();
     const int ycta = p.ny / ROWS;
     int best = p.nz, best_score = -1;
     for (int zc = 8; zc <= p.nz; ++zc) {
@@ -387,16 +380,17 @@ int chunk_for(const StepParams &p) {
 // check that one CTA fits on an SM (registers + shared memory).
 template <int VX>
 static cudaError_t prepare_vx() {
-    static int state = 0;  // 0 unknown, 1 ok, -1 does not fit
-    if (state == 0) {
-        cudaError_t e = cudaFuncSetAttribute(k_d3q19_zmarch<VX>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                             (int)Geo<VX>::BYTES);
-        if (e != cudaSuccess) return e;
+    static DevSlots slots;  // per device: 1 ok, -1 does not fit
+    const int state = per_device(slots, [] {
+        if (cudaFuncSetAttribute(k_d3q19_zmarch<VX>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)Geo<VX>::BYTES) != cudaSuccess)
+            return -1;
         int nb = 0;
-        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_d3q19_zmarch<VX>, NTHREADS, Geo<VX>::BYTES);
-        if (e != cudaSuccess) return e;
-        state = nb >= 1 ? 1 : -1;
-    }
+        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_d3q19_zmarch<VX>, NTHREADS, Geo<VX>::BYTES) !=
+            cudaSuccess)
+            return -1;
+        return nb >= 1 ? 1 : -1;
+    });
     return state == 1 ? cudaSuccess : cudaErrorNotSupported;
 }
 
