@@ -446,6 +446,38 @@ def run_gpu(args):
     return 0
 
 
+def run_case(name, steps):
+    """One variant workload, stepped without timing (a target for profilers)."""
+    import torch
+    from paper_1111_2142_gb300 import inputs
+    from paper_1111_2142_gb300 import lwacm as lw
+    if name == "adjoint":  # D3Q19 128^3: recorded forward + backward over `steps` steps
+        n3 = 128
+        fa = inputs.random_divfree_3d(n3, n3, n3, rms=0.03, kmax=8, seed=2)
+        sim = lw.Lwacm(lw.D3Q19, n3, n3, n3, 0.01)
+        sim.set_fields(*fa)
+        sim.forward_record(steps)
+        lam = [torch.zeros((n3, n3, n3), device="cuda")] + [
+            torch.tensor(a, dtype=torch.float32, device="cuda") for a in fa[1:]]
+        sim.backward(lam)
+    elif name == "ensemble":  # 256 D2Q9 domains (seed 1), 2D tiles 30x14
+        doms = inputs.ensemble_2d(256, seed=1)
+        sim = lw.LwacmBatch(lw.D2Q9, [(d["nx"], d["ny"]) for d in doms], [d["nu"] for d in doms], tile=2)
+        sim.set_domains([(d["d"], d["ux"], d["uy"]) for d in doms])
+        sim.step(steps)
+    elif name == "cavity":  # D2Q9 1024^2 lid-driven cavity, Re 1000, from rest
+        z = torch.zeros((1024, 1024), dtype=torch.float32, device="cuda")
+        sim = lw.Lwacm(lw.D2Q9, 1024, 1024, 1, 0.1024, lw.CAVITY, lid=(0.1, 0.0))
+        sim.set_fields(z, z, z)
+        sim.step(steps)
+    else:
+        raise SystemExit(f"unknown case {name}")
+    sim.sync()
+    sim.close()
+    print(json.dumps({"case": name, "steps": steps, "done": True}))
+    return 0
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -458,6 +490,8 @@ def main():
     ap.add_argument("--cpu-steps", type=int, default=40)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-variants", action="store_true")
+    ap.add_argument("--profile-case", choices=["adjoint", "ensemble", "cavity"],
+                    help="run one variant workload for --steps steps without timing (for profilers)")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3
@@ -465,6 +499,8 @@ def main():
         return run_reference(args)
     import __graft_entry__
     __graft_entry__.build()
+    if args.profile_case:
+        return run_case(args.profile_case, args.steps)
     return run_gpu(args)
 
 
