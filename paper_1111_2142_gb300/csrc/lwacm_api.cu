@@ -11,6 +11,8 @@
 #include <string>
 #include <vector>
 
+#include <nvtx3/nvToolsExt.h>
+
 #include "../../include/lwacm.h"
 #include "launch.h"
 #include "lwacm_core.cuh"
@@ -18,6 +20,12 @@
 using namespace lwacm;
 
 namespace {
+
+// NVTX range around an entry point (a no-op unless a profiler is attached)
+struct Range {
+    explicit Range(const char *name) { nvtxRangePushA(name); }
+    ~Range() { nvtxRangePop(); }
+};
 
 constexpr size_t kAlign = 256;
 inline size_t align_up(size_t v, size_t a) { return (v + a - 1) / a * a; }
@@ -689,6 +697,7 @@ lwacm_status lwacm_bind(lwacm_ctx *c, void *ws, size_t bytes, void *stream) {
 
 lwacm_status lwacm_set_fields(lwacm_ctx *c, const void *d, const void *ux, const void *uy,
                               const void *uz, int dtype, int where) {
+    const Range range("lwacm_set_fields");
     lwacm_status s = ready(c, false);
     if (s != LWACM_OK) return s;
     if (!d || !ux || !uy || (c->Q == 19 && !uz) || (c->Q == 9 && uz))
@@ -767,6 +776,7 @@ lwacm_status lwacm_set_force_field(lwacm_ctx *c, const void *gx, const void *gy,
 }
 
 lwacm_status lwacm_step(lwacm_ctx *c, long long n) {
+    const Range range("lwacm_step");
     lwacm_status s = ready(c, true);
     if (s != LWACM_OK) return s;
     if (n < 0) return fail(c, LWACM_E_ARG, "negative step count");
@@ -823,6 +833,7 @@ lwacm_status lwacm_fields(lwacm_ctx *c, void **d, void **ux, void **uy, void **u
 
 lwacm_status lwacm_get_fields(lwacm_ctx *c, void *d, void *ux, void *uy, void *uz, int dtype,
                               int where) {
+    const Range range("lwacm_get_fields");
     lwacm_status s = ready(c, true);
     if (s != LWACM_OK) return s;
     if (!d || !ux || !uy || (c->Q == 19 && !uz))
@@ -891,6 +902,7 @@ lwacm_status lwacm_get_scalar(lwacm_ctx *c, void *T, int dtype, int where) {
 }
 
 lwacm_status lwacm_diagnostics(lwacm_ctx *c, double out[8]) {
+    const Range range("lwacm_diagnostics");
     lwacm_status s = ready(c, true);
     if (s != LWACM_OK) return s;
     if (!out) return fail(c, LWACM_E_ARG, "null output");
@@ -916,6 +928,7 @@ lwacm_status lwacm_adjoint_workspace_bytes(const lwacm_ctx *c, long long T, int 
 }
 
 lwacm_status lwacm_forward_record(lwacm_ctx *c, long long T, int stride, void *ws, size_t bytes) {
+    const Range range("lwacm_forward_record");
     lwacm_status s = ready(c, true);
     if (s != LWACM_OK) return s;
     if (T < 0 || stride < 0 || !ws) return fail(c, LWACM_E_ARG, "T >= 0, stride >= 0, workspace required");
@@ -948,6 +961,7 @@ lwacm_status lwacm_forward_record(lwacm_ctx *c, long long T, int stride, void *w
 lwacm_status lwacm_backward(lwacm_ctx *c, const void *ld, const void *lux, const void *luy,
                             const void *luz, int dtype, void *gd, void *gux, void *guy, void *guz,
                             double *g_nu) {
+    const Range range("lwacm_backward");
     lwacm_status s = ready(c, false);
     if (s != LWACM_OK) return s;
     if (c->rec_T < 0 || !c->adj) return fail(c, LWACM_E_STATE, "no recorded run (call lwacm_forward_record)");
@@ -1021,6 +1035,7 @@ lwacm_status lwacm_sync(lwacm_ctx *c) {
 
 lwacm_status lwacm_autotune(lwacm_ctx *c, const char *cache_path, int trial_steps, char *report,
                             size_t report_bytes) {
+    const Range range("lwacm_autotune");
     lwacm_status s = ready(c, false);
     if (s != LWACM_OK) return s;
     if (c->has_fields)
