@@ -70,7 +70,7 @@ def _build_locked(srcs, verbose, extra):
         objs = list(ex.map(compile_one, srcs))
     tmp = LIB + f".tmp{os.getpid()}"
     cmd = [nvcc, "-shared", "-gencode", "arch=compute_103a,code=sm_103a", "-o", tmp, *objs,
-           "-Xcompiler", "-fPIC"]
+           "-Xcompiler", "-fPIC", "-ldl"]  # -ldl: the NVTX header loads a profiler's hooks on demand
     r = subprocess.run(cmd, capture_output=True, text=True)
     if r.returncode != 0:
         raise RuntimeError(f"link failed:\n{r.stdout}\n{r.stderr}")
