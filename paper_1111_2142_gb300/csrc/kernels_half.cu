@@ -10,14 +10,13 @@
 // registers: 16 warps per SM instead of 8.
 //
 // The two halves of a row meet at x = 127|128 and, periodically, at x = 255|0. A
-// shuffle cannot cross them, so the values that must (the boundary lane's in-row
-// links and the x-shifted row-crossing diagonals) are written to a small edge
-// buffer in phase A and added by the partner half's boundary lane after the
-// barrier.
+// shuffle cannot cross them, so each half's boundary lanes (0 and 31) recompute
+// the link values they take from their neighbour node in the other half (in-row
+// links and the x-shifted row-crossing diagonals) from that node's staged fields:
+// the halves exchange nothing.
 //
 // nx = 128 uses the same code with one warp per row (NH = 1): the warp's shuffles
-// wrap x periodically by themselves, there is no edge buffer, and two CTAs of 8
-// warps share an SM.
+// wrap x periodically by themselves, and two CTAs of 8 warps share an SM.
 #include <stdint.h>
 
 #include "dev_cache.h"
@@ -32,12 +31,9 @@ using namespace tile;
 
 constexpr int VXH = 4;                 // nodes per lane
 constexpr int HALF = 128;              // nodes per warp row segment
-// edge values per staged row and half: in-row c = (1,0,cz) from lane 31 (3),
-// -c from lane 0 (3), and the four shifted diagonals of the row-crossing send
-constexpr int E_INP = 0, E_INM = 3, E_UP1 = 6, E_UP2 = 7, E_DN1 = 8, E_DN2 = 9, NEDGE = 12;
 
 // NH warps share a row of nx = 128 NH nodes (NH = 1: one warp per row, its lanes
-// wrap periodically by themselves; NH = 2: two halves with the edge exchange).
+// wrap periodically by themselves; NH = 2: two halves, see above).
 // T: storage type of the fields (FP32, or BF16 / FP16 widened to FP32 on load).
 template <int NH, typename T = float>
 struct HG {
@@ -47,9 +43,7 @@ struct HG {
     static constexpr int XDIR = NSLOT * XSLOT;
     static constexpr int XBUF = 2 * XDIR;        // floats
     static constexpr int STAGE = 4 * TROWS * RL;  // elements of T
-    static constexpr int EBUF = NH == 2 ? TROWS * 2 * NEDGE : 0;
-    static constexpr size_t BYTES =
-        (2 * (size_t)XBUF + 2 * (size_t)EBUF) * 4 + 2 * (size_t)STAGE * sizeof(T) + 64;
+    static constexpr size_t BYTES = 2 * (size_t)XBUF * 4 + 2 * (size_t)STAGE * sizeof(T) + 64;
     static constexpr uint32_t TX = STAGE * sizeof(T);
 };
 
@@ -60,13 +54,10 @@ struct HG {
 using F2 = float2;
 __device__ __forceinline__ F2 b2(float v) { return make_float2(v, v); }
 __device__ __forceinline__ F2 add2(F2 a, F2 b) { return __fadd2_rn(a, b); }
-__device__ __forceinline__ F2 sub2(F2 a, F2 b) { return __fadd2_rn(a, make_float2(-b.x, -b.y)); }
+__device__ __forceinline__ F2 sub2(F2 a, F2 b) { return __ffma2_rn(b, make_float2(-1.f, -1.f), a); }
 __device__ __forceinline__ F2 mul2(F2 a, F2 b) { return __fmul2_rn(a, b); }
 __device__ __forceinline__ F2 fma2(F2 a, F2 b, F2 c) { return __ffma2_rn(a, b, c); }
-__device__ __forceinline__ F2 neg2(F2 a) { return make_float2(-a.x, -a.y); }
-
-// node i of a lane inside a pair array
-__device__ __forceinline__ float ndv(const F2 (&v)[2], int i) { return (i & 1) ? v[i >> 1].y : v[i >> 1].x; }
+__device__ __forceinline__ F2 neg2(F2 a) { return __fmul2_rn(a, make_float2(-1.f, -1.f)); }
 
 // per-node constants of the moment form (see tile_common.cuh, NodeConst), per pair
 struct NC2 {
@@ -106,6 +97,38 @@ __device__ __forceinline__ void pair2(const NC2 &nc, int j, F2 e, bool diag, F2 
     gm = make_float2(fmaf(-A.x, e.x, cx), fmaf(-A.y, e.y, cy));
 }
 
+// The boundary neighbour of a half row (NH = 2): lanes 0-15 take node x0 - 1 (the
+// one lane 0 receives from), lanes 16-31 node x0 + 128 (lane 31's), both wrapped
+// periodically. sA = +A for lanes 0-15 and -A for lanes 16-31, so that one value
+// c + sA e serves lane 0 (the link towards +x) and lane 31 (towards -x).
+struct NbC {
+    float U, V, W, K1, sA1, B1, K2, sA2, B2;
+};
+__device__ __forceinline__ float ld1(const float *p) { return *p; }
+__device__ __forceinline__ float ld1(const __nv_bfloat16 *p) { return __bfloat162float(*p); }
+__device__ __forceinline__ float ld1(const __half *p) { return __half2float(*p); }
+
+template <typename T>
+__device__ __forceinline__ NbC nb_consts(const T *row, int rstride, int nbx, float sgn, float s18) {
+    NbC c;
+    const float d = ld1(row + nbx);
+    c.U = ld1(row + rstride + nbx);
+    c.V = ld1(row + 2 * rstride + nbx);
+    c.W = ld1(row + 3 * rstride + nbx);
+    const float rho = 1.f + d;
+    const float K = fmaf(-1.5f * rho, fmaf(c.U, c.U, fmaf(c.V, c.V, c.W * c.W)), d);
+    const float sr = sgn * rho * s18;
+    c.K1 = K * (1.f / 18.f);
+    c.sA1 = sr;
+    c.B1 = rho * 0.25f;
+    c.K2 = K * (1.f / 36.f);
+    c.sA2 = 0.5f * sr;
+    c.B2 = rho * 0.125f;
+    return c;
+}
+// K + B e^2 + sA e
+__device__ __forceinline__ float nb_val(float K, float sA, float B, float e) { return fmaf(sA, e, fmaf(B * e, e, K)); }
+
 // c.u of the five pairs with c_y = +1: c = (0,1,0), (1,1,0), (-1,1,0), (0,1,1), (0,1,-1)
 __device__ __forceinline__ F2 ye2(const NC2 &nc, int k, int j) {
     return k == 0 ? nc.V[j]
@@ -137,30 +160,17 @@ __device__ __forceinline__ void ld_slot2(const float *slot, F2 (&o)[2], int lane
     o[1] = make_float2(t.z, t.w);
 }
 
-// deposit one node's link value g of c = (cx, cy, cz) into a receiver's (d, jx, jy, jz)
-// (as dep() in tile_common.cuh; c_z = +1 arrivals skip jz)
-__device__ __forceinline__ float &ac(F2 (&a)[2][4], int i, int c) {
-    return (i & 1) ? a[i >> 1][c].y : a[i >> 1][c].x;
-}
-__device__ __forceinline__ void dep1(F2 (&a)[2][4], int i, float g, int cx, int cy, int cz) {
-    ac(a, i, 0) += g;
-    if (cx > 0) ac(a, i, 1) += g;
-    if (cx < 0) ac(a, i, 1) -= g;
-    if (cy > 0) ac(a, i, 2) += g;
-    if (cy < 0) ac(a, i, 2) -= g;
-    if (cz < 0) ac(a, i, 3) -= g;
-}
-
 // Row-crossing values of one half row, computed once per link pair and sent to
 // the receivers above (up, c_y = +1; when UP) and below (down, c_y = -1; when DN),
 // four values per receiver x and direction as in kernels_tiled.cu:
 //   slot 0: sum of the three c_z = 0 links (d, +-jy), slot 1: their x-momentum,
 //   slot 2: the c_z = +1 link, slot 3: the c_z = -1 link.
-// The boundary lanes leave out the x-shifted diagonal that would cross into the
-// other half and record their own boundary value in `edge`.
+// With NH = 2 the boundary lanes take the x-shifted diagonal that crosses from the
+// other half from the neighbour's values nb1 (c = (1,1,0) at lane 0, (-1,-1,0) at
+// lane 31) and nb2 (c = (1,-1,0) at lane 0, (-1,1,0) at lane 31).
 template <int NH, int MODE>
 __device__ __forceinline__ void send_rows(const NC2 &nc, float *ubase, float *dbase, bool UP, bool DN,
-                                          float *edge, int lane) {
+                                          float nb1, float nb2, int lane) {
     constexpr int XSLOT = HG<NH>::XSLOT;
     const bool l0 = lane == 0 && NH == 2, l31 = lane == 31 && NH == 2;
     if (MODE == MID) {
@@ -172,14 +182,12 @@ __device__ __forceinline__ void send_rows(const NC2 &nc, float *ubase, float *db
 #pragma unroll
             for (int j = 0; j < 2; ++j) pair2(nc, j, ye2(nc, 1, j), true, gp[j], gm[j]);
             if (UP) {
-                if (NH == 2) st_shared_if(edge + E_UP1, gp[1].y, l31);
                 shift2(gp, 1, lane);
-                gp[0].x = l0 ? 0.f : gp[0].x;
+                gp[0].x = l0 ? nb1 : gp[0].x;
             }
             if (DN) {
-                if (NH == 2) st_shared_if(edge + E_DN1, gm[0].x, l0);
                 shift2(gm, -1, lane);
-                gm[1].y = l31 ? 0.f : gm[1].y;
+                gm[1].y = l31 ? nb1 : gm[1].y;
             }
 #pragma unroll
             for (int j = 0; j < 2; ++j) {
@@ -194,14 +202,12 @@ __device__ __forceinline__ void send_rows(const NC2 &nc, float *ubase, float *db
 #pragma unroll
             for (int j = 0; j < 2; ++j) pair2(nc, j, ye2(nc, 2, j), true, gp[j], gm[j]);
             if (UP) {
-                if (NH == 2) st_shared_if(edge + E_UP2, gp[0].x, l0);
                 shift2(gp, -1, lane);
-                gp[1].y = l31 ? 0.f : gp[1].y;
+                gp[1].y = l31 ? nb2 : gp[1].y;
             }
             if (DN) {
-                if (NH == 2) st_shared_if(edge + E_DN2, gm[1].y, l31);
                 shift2(gm, 1, lane);
-                gm[0].x = l0 ? 0.f : gm[0].x;
+                gm[0].x = l0 ? nb2 : gm[0].x;
             }
 #pragma unroll
             for (int j = 0; j < 2; ++j) {
@@ -250,15 +256,19 @@ __device__ __forceinline__ constexpr bool need_m(int mode, int cz) {
 using Acc = F2[3][2][4];  // [plane behind / current / ahead][node pair][d, jx, jy, jz]
 
 template <int NH, int MODE, typename T>
-__device__ __forceinline__ void phase_a(Acc &acc, const T *stg, float *xbuf, float *ebuf, const TiledParams &p,
-                                        int lane, int row, int half) {
+__device__ __forceinline__ void phase_a(Acc &acc, const T *stg, float *xbuf, const TiledParams &p, int lane,
+                                        int row, int half) {
     constexpr int PM = 0, P0 = 1, PP = 2;
     constexpr int RL = HG<NH>::RL, XDIR = HG<NH>::XDIR;
     float *up = xbuf + half * HALF, *dn = xbuf + XDIR + half * HALF;
     {
         NC2 nc;
         node_consts2(nc, stg + (row + 1) * RL + half * HALF, TROWS * RL, lane, p.s18);
-        float *edge = NH == 2 ? ebuf + ((row + 1) * 2 + half) * NEDGE : nullptr;
+        // NH = 2: the boundary neighbour's constants (unused for NH = 1)
+        const int nbx = lane < 16 ? (half * HALF + RL - 1) % RL : (half * HALF + HALF) % RL;
+        const float sgn = lane < 16 ? 1.f : -1.f;
+        NbC nb{};
+        if (NH == 2) nb = nb_consts(stg + (row + 1) * RL, TROWS * RL, nbx, sgn, p.s18);
 #pragma unroll
         for (int j = 0; j < 2; ++j) {
             F2 gp, gm;
@@ -287,107 +297,96 @@ __device__ __forceinline__ void phase_a(Acc &acc, const T *stg, float *xbuf, flo
                 const F2 e = cz == 0 ? nc.U[j] : (cz > 0 ? add2(nc.U[j], nc.W[j]) : sub2(nc.U[j], nc.W[j]));
                 pair2(nc, j, e, cz != 0, gp[j], gm[j]);
             }
+            // in-row deposits as packed pairs of receivers: for +c the receivers
+            // (0,1 | 2,3) take the values of nodes (-1,0 | 1,2), for -c those of
+            // nodes (1,2 | 3,4); nodes -1 and 4 are the neighbouring lanes'
+            // NH = 2: lane 0's +c value and lane 31's -c value from the neighbour
+            const float nbv = NH == 2 ? nb_val(cz ? nb.K2 : nb.K1, cz ? nb.sA2 : nb.sA1, cz ? nb.B2 : nb.B1,
+                                               cz == 0 ? nb.U : (cz > 0 ? nb.U + nb.W : nb.U - nb.W))
+                                      : 0.f;
             if (np) {  // c = (1,0,cz): node i feeds node i+1
-#pragma unroll
-                for (int i = 0; i + 1 < VXH; ++i) dep1(acc[pl<PM, P0, PP>(cz)], i + 1, ndv(gp, i), 1, 0, cz);
                 const float eP = gp[1].y;
-                if (NH == 2) st_shared_if(edge + E_INP + cz + 1, eP, lane == 31);  // for the other half's lane 0
                 float rP = __shfl_sync(FULL, eP, (lane + 31) & 31);
-                if (NH == 2) rP = lane == 0 ? 0.f : rP;  // lane 0's comes from the other half (phase B)
-                dep1(acc[pl<PM, P0, PP>(cz)], 0, rP, 1, 0, cz);
-            }
-            if (nm) {  // -c: node i feeds node i-1
-                // for cz = -1 this is the first x-momentum of the plane ahead
+                if (NH == 2) rP = lane == 0 ? nbv : rP;
+                const F2 R[2] = {make_float2(rP, gp[0].x), make_float2(gp[0].y, gp[1].x)};
+                F2(&a)[2][4] = acc[pl<PM, P0, PP>(cz)];
 #pragma unroll
-                for (int i = 1; i < VXH; ++i) {
-                    if (cz < 0) {
-                        ac(acc[PP], i - 1, 0) += ndv(gm, i);
-                        ac(acc[PP], i - 1, 1) = -ndv(gm, i);
-                    } else {
-                        dep1(acc[pl<PM, P0, PP>(-cz)], i - 1, ndv(gm, i), -1, 0, -cz);
-                    }
+                for (int j = 0; j < 2; ++j) {
+                    a[j][0] = add2(a[j][0], R[j]);
+                    a[j][1] = add2(a[j][1], R[j]);
+                    if (cz < 0) a[j][3] = sub2(a[j][3], R[j]);
                 }
+            }
+            if (nm) {  // -c = (-1,0,-cz): node i feeds node i-1
                 const float eM = gm[0].x;
-                if (NH == 2) st_shared_if(edge + E_INM + cz + 1, eM, lane == 0);  // for the other half's lane 31
                 float rM = __shfl_sync(FULL, eM, (lane + 1) & 31);
-                if (NH == 2) rM = lane == 31 ? 0.f : rM;
-                if (cz < 0) {
-                    ac(acc[PP], VXH - 1, 0) += rM;
-                    ac(acc[PP], VXH - 1, 1) = -rM;
+                if (NH == 2) rM = lane == 31 ? nbv : rM;
+                const F2 L[2] = {make_float2(gm[0].y, gm[1].x), make_float2(gm[1].y, rM)};
+                if (cz < 0) {  // -c = (-1,0,1): first x-momentum of the plane ahead
+#pragma unroll
+                    for (int j = 0; j < 2; ++j) {
+                        acc[PP][j][0] = add2(acc[PP][j][0], L[j]);
+                        acc[PP][j][1] = neg2(L[j]);
+                    }
                 } else {
-                    dep1(acc[pl<PM, P0, PP>(-cz)], VXH - 1, rM, -1, 0, -cz);
+                    F2(&a)[2][4] = acc[pl<PM, P0, PP>(-cz)];
+#pragma unroll
+                    for (int j = 0; j < 2; ++j) {
+                        a[j][0] = add2(a[j][0], L[j]);
+                        a[j][1] = sub2(a[j][1], L[j]);
+                        if (cz > 0) a[j][3] = sub2(a[j][3], L[j]);
+                    }
                 }
             }
         }
-        send_rows<NH, MODE>(nc, up + (row + 1) * RL, dn + (row - 1) * RL, row + 1 < ROWS, row > 0, edge, lane);
+        const float nb1 = NH == 2 && MODE == MID ? nb_val(nb.K2, nb.sA2, nb.B2, nb.U + nb.V) : 0.f;
+        const float nb2 = NH == 2 && MODE == MID ? nb_val(nb.K2, -nb.sA2, nb.B2, nb.V - nb.U) : 0.f;
+        send_rows<NH, MODE>(nc, up + (row + 1) * RL, dn + (row - 1) * RL, row + 1 < ROWS, row > 0, nb1, nb2, lane);
     }
-    if (row == 0) {  // bottom halo row y0-1 (staged row 0) feeds row 0
+    if (row == 0 || row == ROWS - 1) {  // halo rows: y0-1 (staged row 0) feeds row 0, y0+8 (staged 9) row 7
+        const int sr = row == 0 ? 0 : TROWS - 1;
         NC2 hc;
-        node_consts2(hc, stg + half * HALF, TROWS * RL, lane, p.s18);
-        send_rows<NH, MODE>(hc, up, nullptr, true, false, NH == 2 ? ebuf + half * NEDGE : nullptr, lane);
-    } else if (row == ROWS - 1) {  // top halo row y0+8 (staged row 9) feeds row 7
-        NC2 hc;
-        node_consts2(hc, stg + (TROWS - 1) * RL + half * HALF, TROWS * RL, lane, p.s18);
-        send_rows<NH, MODE>(hc, nullptr, dn + (ROWS - 1) * RL, false, true,
-                            NH == 2 ? ebuf + ((TROWS - 1) * 2 + half) * NEDGE : nullptr, lane);
+        node_consts2(hc, stg + sr * RL + half * HALF, TROWS * RL, lane, p.s18);
+        float nb1 = 0.f, nb2 = 0.f;
+        if (NH == 2 && MODE == MID) {
+            const int nbx = lane < 16 ? (half * HALF + RL - 1) % RL : (half * HALF + HALF) % RL;
+            const NbC hb = nb_consts(stg + sr * RL, TROWS * RL, nbx, lane < 16 ? 1.f : -1.f, p.s18);
+            nb1 = nb_val(hb.K2, hb.sA2, hb.B2, hb.U + hb.V);
+            nb2 = nb_val(hb.K2, -hb.sA2, hb.B2, hb.V - hb.U);
+        }
+        if (row == 0)
+            send_rows<NH, MODE>(hc, up, nullptr, true, false, nb1, nb2, lane);
+        else
+            send_rows<NH, MODE>(hc, nullptr, dn + (ROWS - 1) * RL, false, true, nb1, nb2, lane);
     }
 }
 
 template <int NH, int MODE, typename T>
-__device__ __forceinline__ void phase_b(Acc &acc, const float *xbuf, const float *ebuf, T *out,
-                                        const TiledParams &p, int lane, int row, int half, int col, int zfin) {
+__device__ __forceinline__ void phase_b(Acc &acc, const float *xbuf, T *out, const TiledParams &p, int lane,
+                                        int row, int half, int col, int zfin) {
     constexpr int PM = 0, P0 = 1, PP = 2;
     constexpr int RL = HG<NH>::RL, XDIR = HG<NH>::XDIR, XSLOT = HG<NH>::XSLOT;
     const float *up = xbuf + row * RL + half * HALF, *dn = xbuf + XDIR + row * RL + half * HALF;
-    const int ph = 1 - half;
-    const float *e_own = ebuf + ((row + 1) * 2 + ph) * NEDGE;  // partner half, same row
-    const float *e_up = ebuf + (row * 2 + ph) * NEDGE;         // partner half, row below
-    const float *e_dn = ebuf + ((row + 2) * 2 + ph) * NEDGE;   // partner half, row above
     F2 o[2];
     if (MODE == MID) {
-        const float u1 = NH == 2 ? e_up[E_UP1] : 0.f, u2 = NH == 2 ? e_up[E_UP2] : 0.f;
-        const float d1 = NH == 2 ? e_dn[E_DN1] : 0.f, d2 = NH == 2 ? e_dn[E_DN2] : 0.f;
-        const bool l0 = lane == 0 && NH == 2, l31 = lane == 31 && NH == 2;
         ld_slot2(up, o, lane);  // from below, c_z = 0: d, +jy
-        o[0].x += l0 ? u1 : 0.f;
-        o[1].y += l31 ? u2 : 0.f;
 #pragma unroll
         for (int j = 0; j < 2; ++j) {
             acc[P0][j][0] = add2(acc[P0][j][0], o[j]);
             acc[P0][j][2] = add2(acc[P0][j][2], o[j]);
         }
         ld_slot2(up + XSLOT, o, lane);
-        o[0].x += l0 ? u1 : 0.f;
-        o[1].y -= l31 ? u2 : 0.f;
 #pragma unroll
         for (int j = 0; j < 2; ++j) acc[P0][j][1] = add2(acc[P0][j][1], o[j]);
         ld_slot2(dn, o, lane);  // from above, c_z = 0: d, -jy
-        o[1].y += l31 ? d1 : 0.f;
-        o[0].x += l0 ? d2 : 0.f;
 #pragma unroll
         for (int j = 0; j < 2; ++j) {
             acc[P0][j][0] = add2(acc[P0][j][0], o[j]);
             acc[P0][j][2] = sub2(acc[P0][j][2], o[j]);
         }
         ld_slot2(dn + XSLOT, o, lane);
-        o[1].y -= l31 ? d1 : 0.f;
-        o[0].x += l0 ? d2 : 0.f;
 #pragma unroll
         for (int j = 0; j < 2; ++j) acc[P0][j][1] = add2(acc[P0][j][1], o[j]);
-    }
-    // in-row values from the other half's boundary lanes
-    if (NH == 2) {
-#pragma unroll
-        for (int cz = -1; cz <= 1; ++cz) {
-            if (need_p(MODE, cz)) {
-                const float v = e_own[E_INP + cz + 1];
-                dep1(acc[pl<PM, P0, PP>(cz)], 0, lane == 0 ? v : 0.f, 1, 0, cz);
-            }
-            if (need_m(MODE, cz)) {
-                const float v = e_own[E_INM + cz + 1];
-                dep1(acc[pl<PM, P0, PP>(-cz)], VXH - 1, lane == 31 ? v : 0.f, -1, 0, -cz);
-            }
-        }
     }
     if (MODE != LAST) {  // c_z = +1 arrivals for the plane ahead (jz implied by d)
         ld_slot2(up + 2 * XSLOT, o, lane);
@@ -481,17 +480,18 @@ __device__ __forceinline__ void rotate(Acc &acc) {
 template <int NH, typename T>
 __global__ void __launch_bounds__(HG<NH>::NTH, 2 / NH) k_d3q19_half(const T *__restrict__ in,
                                                                    T *__restrict__ out, TiledParams p) {
-    constexpr int XBUF = HG<NH, T>::XBUF, STAGE = HG<NH, T>::STAGE, EBUF = HG<NH, T>::EBUF;
+    constexpr int XBUF = HG<NH, T>::XBUF, STAGE = HG<NH, T>::STAGE;
     extern __shared__ float4 smem4[];
     float *xs = reinterpret_cast<float *>(smem4);
     T *stg = reinterpret_cast<T *>(xs + 2 * XBUF);
-    float *eb = reinterpret_cast<float *>(stg + 2 * STAGE);
-    uint64_t *bars = reinterpret_cast<uint64_t *>(eb + 2 * EBUF);
+    uint64_t *bars = reinterpret_cast<uint64_t *>(stg + 2 * STAGE);
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const int row = NH == 2 ? warp >> 1 : warp, half = NH == 2 ? (warp & 1) : 0;
     if ((int)blockIdx.x >= p.nitems) return;  // uniform per CTA
 
+    __shared__ int failed;
     if (threadIdx.x == 0) {
+        failed = 0;
         mbar_init(&bars[0], 1);
         mbar_init(&bars[1], 1);
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
@@ -519,19 +519,20 @@ __global__ void __launch_bounds__(HG<NH>::NTH, 2 / NH) k_d3q19_half(const T *__r
         const int s = tc & 1;
         const T *stage = stg + s * STAGE;
         float *xbuf = xs + s * XBUF;
-        float *ebuf = eb + s * EBUF;
         const bool ok = mbar_wait(&bars[s], (uint32_t)((tc >> 1) & 1));
         const int mode = it.mode();
         if (ok) {
             if (mode == MID) {
-                phase_a<NH, MID>(acc, stage, xbuf, ebuf, p, lane, row, half);
+                phase_a<NH, MID>(acc, stage, xbuf, p, lane, row, half);
             } else if (mode == FIRST) {
-                phase_a<NH, FIRST>(acc, stage, xbuf, ebuf, p, lane, row, half);
+                phase_a<NH, FIRST>(acc, stage, xbuf, p, lane, row, half);
             } else {
-                phase_a<NH, LAST>(acc, stage, xbuf, ebuf, p, lane, row, half);
+                phase_a<NH, LAST>(acc, stage, xbuf, p, lane, row, half);
             }
         }
-        if (__syncthreads_or(ok ? 0 : 1)) {
+        if (!ok) failed = 1;  // a wait that gave up, seen by every thread after the barrier
+        __syncthreads();
+        if (failed) {
             if (threadIdx.x == 0) {
                 atomicExch(p.err, 1);
                 for (int t = tc + 1; t < issued; ++t) mbar_wait(&bars[t & 1], (uint32_t)((t >> 1) & 1));
@@ -547,13 +548,13 @@ __global__ void __launch_bounds__(HG<NH>::NTH, 2 / NH) k_d3q19_half(const T *__r
             pf.next();
         }
         if (mode == MID) {
-            phase_b<NH, MID>(acc, xbuf, ebuf, out, p, lane, row, half, it.col, it.pz > it.za ? it.pz - 1 : -1);
+            phase_b<NH, MID>(acc, xbuf, out, p, lane, row, half, it.col, it.pz > it.za ? it.pz - 1 : -1);
             rotate(acc);
         } else if (mode == FIRST) {
-            phase_b<NH, FIRST>(acc, xbuf, ebuf, out, p, lane, row, half, it.col, -1);
+            phase_b<NH, FIRST>(acc, xbuf, out, p, lane, row, half, it.col, -1);
             rotate(acc);
         } else {
-            phase_b<NH, LAST>(acc, xbuf, ebuf, out, p, lane, row, half, it.col, it.zb - 1);
+            phase_b<NH, LAST>(acc, xbuf, out, p, lane, row, half, it.col, it.zb - 1);
         }
         it.next();
     }

@@ -347,7 +347,9 @@ __global__ void __launch_bounds__(NTHREADS, 1)
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     if ((int)blockIdx.x >= p.nitems) return;  // uniform per CTA
 
+    __shared__ int failed;
     if (threadIdx.x == 0) {
+        failed = 0;
         mbar_init(&bars[0], 1);
         mbar_init(&bars[1], 1);
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
@@ -386,7 +388,9 @@ __global__ void __launch_bounds__(NTHREADS, 1)
             else
                 phase_a<VX, LAST, 0, 1, 2>(acc, stage, xbuf, p, lane, warp);
         }
-        if (__syncthreads_or(ok ? 0 : 1)) {
+        if (!ok) failed = 1;  // a wait that gave up, seen by every thread after the barrier
+        __syncthreads();
+        if (failed) {
             // a copy never arrived: flag it, let the copies in flight land, stop
             if (threadIdx.x == 0) {
                 atomicExch(p.err, 1);

@@ -64,14 +64,6 @@ __device__ __forceinline__ void bulk_g2s(void *dst, const void *src, uint32_t by
         : "memory");
 }
 
-// store v to a shared-memory float only where p holds, without a branch
-__device__ __forceinline__ void st_shared_if(float *addr, float v, bool p) {
-    asm volatile(
-        "{\n .reg .pred q;\n setp.ne.u32 q, %2, 0;\n @q st.shared.f32 [%0], %1;\n}\n" ::"r"(sa(addr)),
-        "f"(v), "r"((unsigned)p)
-        : "memory");
-}
-
 // 1/x: hardware approximation refined by one Newton-Raphson step
 // (r <- r + r (1 - x r)), accurate to about an ulp for the densities here.
 __device__ __forceinline__ float rcp_nr(float x) {
