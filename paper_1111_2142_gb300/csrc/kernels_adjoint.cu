@@ -15,8 +15,14 @@
 //     lambda_u(y) = sum_i gbar_i w_i rho(y) [s c_i + 9 e c_i - 3 u(y)] + a rho(y) Jbar(y)
 //     dL/dnu     += sum_y [ sum_i gbar_i 18 w_i rho(y) e  - 6 rho(y) u(y).Jbar(y) ]
 // (s = 18 nu and a = 1 - 6 nu carry all of the nu-dependence, Eq. ACM2.0nu). The
-// dL/dnu sum is accumulated in FP64: per-block partials, then one block adds them
-// in a fixed order to a running total (deterministic).
+// dL/dnu sum is accumulated in FP64: per-block partials, then the block that
+// finishes last adds them in a fixed order to a running total (deterministic).
+//
+// (Dbar, Jbar) of a step are pointwise in lambda+ and the state at t+1, which are
+// the lambda and the state of the step before it in the backward sweep: the gather
+// of step t writes (Dbar, Jbar) for step t-1 straight from its lambda_t and the
+// state at t it already holds, so only the first step of the sweep runs the
+// separate prep pass and only the last one writes lambda.
 #include "launch.h"
 #include "lwacm_core.cuh"
 
@@ -56,11 +62,14 @@ constexpr int AW = ATX + 2, AH = ATY + 2, APL = AW * AH;
 // With WALLS, a link whose receiver x + c lies beyond a walled face is the value the
 // node itself takes for the bounced link -c (Eq. ACM2.0cccbb2): gbar = Dbar - c.Jbar
 // of the node; the moving-wall term of Eq. ACM2.0ccccbb adds its nu-derivative.
-template <int Q, bool WALLS>
+// NEXT: write (Dbar, Jbar) of the next step of the sweep to `out` instead of lambda.
+template <int Q, bool WALLS, bool NEXT>
 __global__ void __launch_bounds__(ATX *ATY) k_adj_gather_tiled(const float *__restrict__ st,
                                                                const float *__restrict__ dj,
-                                                               float *__restrict__ lam_out, StepParams p, int ntx,
-                                                               int nty, int nzc, double *__restrict__ nu_partial) {
+                                                               float *__restrict__ out, StepParams p, int ntx,
+                                                               int nty, int nzc, double *__restrict__ nu_partial,
+                                                               unsigned *__restrict__ done,
+                                                               double *__restrict__ nu_total) {
     using L = Lat<Q>;
     constexpr int NF = Q == 19 ? 4 : 3;
     __shared__ float ring[4][NF][APL];
@@ -194,10 +203,18 @@ __global__ void __launch_bounds__(ATX *ATY) k_adj_gather_tiled(const float *__re
                 lu = fmaf(p.a * rho, jx, lu);
                 lv = fmaf(p.a * rho, jy, lv);
                 lw = fmaf(p.a * rho, jz, lw);
-                lam_out[k] = ld;
-                lam_out[p.fstride + k] = lu;
-                lam_out[2 * p.fstride + k] = lv;
-                if (Q == 19) lam_out[3 * p.fstride + k] = lw;
+                if (NEXT) {  // the prep of the next step: this node's state at t is its state at t+1
+                    const float inv = 1.f / rho;
+                    out[k] = ld - (lu * u + lv * v + lw * w) * inv;
+                    out[p.fstride + k] = lu * inv;
+                    out[2 * p.fstride + k] = lv * inv;
+                    if (Q == 19) out[3 * p.fstride + k] = lw * inv;
+                } else {
+                    out[k] = ld;
+                    out[p.fstride + k] = lu;
+                    out[2 * p.fstride + k] = lv;
+                    if (Q == 19) out[3 * p.fstride + k] = lw;
+                }
                 nu_run += fmaf(18.f, ln, -6.f * rho * ju);
                 if (WALLS) nu_run = fmaf(18.f * p.wallc / p.s, nu_wall, nu_run);  // 36 rho0 = wallc / nu
             }
@@ -212,52 +229,68 @@ __global__ void __launch_bounds__(ATX *ATY) k_adj_gather_tiled(const float *__re
         if (tid < off) sh[tid] += sh[tid + off];
         __syncthreads();
     }
-    if (tid == 0) nu_partial[blockIdx.x] = sh[0];
-}
-
-// total += sum of the partials, in a fixed order
-__global__ void k_adj_nu_sum(const double *__restrict__ partial, int n, double *__restrict__ total) {
-    __shared__ double sh[256];
-    double a = 0.0;
-    for (int b = threadIdx.x; b < n; b += blockDim.x) a += partial[b];
-    sh[threadIdx.x] = a;
+    // the block that finishes last adds the partials in a fixed order
+    __shared__ bool last;
+    if (tid == 0) {
+        nu_partial[blockIdx.x] = sh[0];
+        __threadfence();
+        last = atomicAdd(done, 1u) == gridDim.x - 1;
+    }
     __syncthreads();
-    for (int off = blockDim.x / 2; off > 0; off >>= 1) {
-        if (threadIdx.x < off) sh[threadIdx.x] += sh[threadIdx.x + off];
+    if (!last) return;
+    double a = 0.0;
+    for (int b = tid; b < (int)gridDim.x; b += ATX * ATY) a += __ldcg(nu_partial + b);
+    sh[tid] = a;
+    __syncthreads();
+    for (int off = ATX * ATY / 2; off > 0; off >>= 1) {
+        if (tid < off) sh[tid] += sh[tid + off];
         __syncthreads();
     }
-    if (threadIdx.x == 0) *total += sh[0];
+    if (tid == 0) {
+        *nu_total += sh[0];
+        *done = 0u;  // ready for the next step (stream-ordered)
+    }
 }
 
 }  // namespace
 
 int adjoint_partials() { return kAdjBlocks; }
 
+template <int Q, bool WALLS>
+static void gather(bool next, int grid, const float *state_t, const float *dj, float *out, const StepParams &p,
+                   int ntx, int nty, int nzc, double *part, unsigned *done, double *total, cudaStream_t st) {
+    if (next)
+        k_adj_gather_tiled<Q, WALLS, true>
+            <<<grid, ATX * ATY, 0, st>>>(state_t, dj, out, p, ntx, nty, nzc, part, done, total);
+    else
+        k_adj_gather_tiled<Q, WALLS, false>
+            <<<grid, ATX * ATY, 0, st>>>(state_t, dj, out, p, ntx, nty, nzc, part, done, total);
+}
+
 cudaError_t launch_adjoint_step(int Q, const float *state_t, const float *state_t1, const float *lam_t1,
-                                float *dj, float *lam_t, const StepParams &p, double *nu_partial,
-                                double *nu_total, cudaStream_t st) {
+                                float *dj, float *dj_next, float *lam_t, const StepParams &p, double *nu_partial,
+                                unsigned *done, double *nu_total, cudaStream_t st) {
     // tiled gather: x-y tiles of 32 x 8, z-runs of 16 planes; every CTA writes one
     // partial (the grid never exceeds the partials buffer)
     const int ntx = (p.nx + ATX - 1) / ATX, nty = (p.ny + ATY - 1) / ATY, nzc = (p.nz + AZC - 1) / AZC;
     const long long items = (long long)ntx * nty * nzc;
     const int grid = (int)(items < kAdjBlocks ? items : kAdjBlocks);
     const bool walls = p.walled[0] || p.walled[1] || p.walled[2];
+    const bool next = dj_next != nullptr;
+    float *out = next ? dj_next : lam_t;
     if (Q == 9) {
-        k_adj_prep<9><<<kAdjBlocks, 256, 0, st>>>(state_t1, lam_t1, dj, p.fstride, p.N);
+        if (lam_t1) k_adj_prep<9><<<kAdjBlocks, 256, 0, st>>>(state_t1, lam_t1, dj, p.fstride, p.N);
         if (walls)
-            k_adj_gather_tiled<9, true><<<grid, ATX * ATY, 0, st>>>(state_t, dj, lam_t, p, ntx, nty, nzc, nu_partial);
+            gather<9, true>(next, grid, state_t, dj, out, p, ntx, nty, nzc, nu_partial, done, nu_total, st);
         else
-            k_adj_gather_tiled<9, false><<<grid, ATX * ATY, 0, st>>>(state_t, dj, lam_t, p, ntx, nty, nzc, nu_partial);
+            gather<9, false>(next, grid, state_t, dj, out, p, ntx, nty, nzc, nu_partial, done, nu_total, st);
     } else {
-        k_adj_prep<19><<<kAdjBlocks, 256, 0, st>>>(state_t1, lam_t1, dj, p.fstride, p.N);
+        if (lam_t1) k_adj_prep<19><<<kAdjBlocks, 256, 0, st>>>(state_t1, lam_t1, dj, p.fstride, p.N);
         if (walls)
-            k_adj_gather_tiled<19, true><<<grid, ATX * ATY, 0, st>>>(state_t, dj, lam_t, p, ntx, nty, nzc,
-                                                                     nu_partial);
+            gather<19, true>(next, grid, state_t, dj, out, p, ntx, nty, nzc, nu_partial, done, nu_total, st);
         else
-            k_adj_gather_tiled<19, false><<<grid, ATX * ATY, 0, st>>>(state_t, dj, lam_t, p, ntx, nty, nzc,
-                                                                      nu_partial);
+            gather<19, false>(next, grid, state_t, dj, out, p, ntx, nty, nzc, nu_partial, done, nu_total, st);
     }
-    k_adj_nu_sum<<<1, 256, 0, st>>>(nu_partial, grid, nu_total);
     return cudaGetLastError();
 }
 

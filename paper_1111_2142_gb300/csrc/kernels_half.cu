@@ -487,6 +487,8 @@ __global__ void __launch_bounds__(HG<NH>::NTH, 2 / NH) k_d3q19_half(const T *__r
     uint64_t *bars = reinterpret_cast<uint64_t *>(stg + 2 * STAGE);
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const int row = NH == 2 ? warp >> 1 : warp, half = NH == 2 ? (warp & 1) : 0;
+    // the thread that issues the copies: in row 1, which has no halo row to send
+    const bool producer = threadIdx.x == (NH == 2 ? 64 : 32);
     if ((int)blockIdx.x >= p.nitems) return;  // uniform per CTA
 
     __shared__ int failed;
@@ -502,7 +504,7 @@ __global__ void __launch_bounds__(HG<NH>::NTH, 2 / NH) k_d3q19_half(const T *__r
     TaskIter pf = it;
     int issued = 0;
     for (int k = 0; k < 2 && pf.valid(); ++k) {
-        if (threadIdx.x == 0) issue_plane<NH, T>(in, p, pf.col, pf.pz, stg + k * STAGE, &bars[k]);
+        if (producer) issue_plane<NH, T>(in, p, pf.col, pf.pz, stg + k * STAGE, &bars[k]);
         ++issued;
         pf.next();
     }
@@ -533,14 +535,14 @@ __global__ void __launch_bounds__(HG<NH>::NTH, 2 / NH) k_d3q19_half(const T *__r
         if (!ok) failed = 1;  // a wait that gave up, seen by every thread after the barrier
         __syncthreads();
         if (failed) {
-            if (threadIdx.x == 0) {
+            if (producer) {
                 atomicExch(p.err, 1);
                 for (int t = tc + 1; t < issued; ++t) mbar_wait(&bars[t & 1], (uint32_t)((t >> 1) & 1));
             }
             return;
         }
         if (pf.valid()) {
-            if (threadIdx.x == 0) {
+            if (producer) {
                 asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
                 issue_plane<NH, T>(in, p, pf.col, pf.pz, stg + s * STAGE, &bars[s]);
             }

@@ -35,12 +35,15 @@ cudaError_t launch_step_tiled(int Q, int storage, const void *in, void *out, con
                               cudaStream_t st);
 const char *tiled_name(int Q);
 
-// Adjoint of one step (periodic; kernels_adjoint.cu): lambda_t from lambda_t1, the
-// states at t and t+1; dj is scratch for (Dbar, Jbar); adds dL/dnu to *nu_total.
+// Adjoint of one step (kernels_adjoint.cu) from the states at t and t+1 and
+// (Dbar, Jbar) in dj; adds dL/dnu to *nu_total. With lam_t1 (the first step of a
+// sweep), dj is first formed from lambda_t1 and the state at t+1. With dj_next, the
+// step writes (Dbar, Jbar) of the next step (t-1) there; otherwise lambda_t to
+// lam_t. `done` is a zeroed counter the step leaves zeroed.
 int adjoint_partials();
 cudaError_t launch_adjoint_step(int Q, const float *state_t, const float *state_t1, const float *lam_t1,
-                                float *dj, float *lam_t, const StepParams &p, double *nu_partial,
-                                double *nu_total, cudaStream_t st);
+                                float *dj, float *dj_next, float *lam_t, const StepParams &p, double *nu_partial,
+                                unsigned *done, double *nu_total, cudaStream_t st);
 
 // Batched independent periodic domains packed in one set of field arrays
 // (kernels_batch.cu). A tile is batch_tile() consecutive nodes of one domain.

@@ -285,8 +285,8 @@ cudaError_t enqueue_step(lwacm_ctx *c, int cur, cudaStream_t st) {
     return step_between(c, bufp(c, cur), bufp(c, 1 - cur), st);
 }
 
-// adjoint workspace: K checkpoints, S+1 segment states, 2 lambda states, (Dbar, Jbar),
-// dL/dnu partials and total
+// adjoint workspace: K checkpoints, S+1 segment states, 2 lambda / (Dbar, Jbar)
+// states, one more (Dbar, Jbar) state, dL/dnu partials, total and block counter
 struct AdjLayout {
     long long K = 0;
     int S = 0;
@@ -973,13 +973,15 @@ lwacm_status lwacm_backward(lwacm_ctx *c, const void *ld, const void *lux, const
     const size_t sb = (size_t)c->Nal * 4 * c->nf;
     const size_t fb = (size_t)c->Nal * 4;
     char *A = c->adj;
-    float *lam[2] = {(float *)(A + L.lam), (float *)(A + L.lam + L.state)};
-    float *dj = (float *)(A + L.dj);
+    // lambda in and out in lam0; (Dbar, Jbar) alternate between the other two
+    float *lam0 = (float *)(A + L.lam);
+    float *dj[2] = {(float *)(A + L.lam + L.state), (float *)(A + L.dj)};
     double *part = (double *)(A + L.part), *total = (double *)(A + L.total);
+    unsigned *done = (unsigned *)(A + L.total + 8);
     const void *lin[4] = {ld, lux, luy, luz};
     for (int f = 0; f < c->nf; ++f)
-        CK(c, launch_convert_in(STORE_F32, dtype, lin[f], (char *)lam[0] + f * fb, c->N, c->stream), "lambda in");
-    CK(c, cudaMemsetAsync(total, 0, sizeof(double), c->stream), "clear dnu");
+        CK(c, launch_convert_in(STORE_F32, dtype, lin[f], (char *)lam0 + f * fb, c->N, c->stream), "lambda in");
+    CK(c, cudaMemsetAsync(total, 0, 16, c->stream), "clear dnu");
     const StepParams p = params(c);
     int cur = 0;
     for (long long k = L.K - 1; k >= 0; --k) {
@@ -991,9 +993,10 @@ lwacm_status lwacm_backward(lwacm_ctx *c, const void *ld, const void *lux, const
         for (long long j = 0; j < len; ++j)
             CK(c, step_between(c, seg + j * L.state, seg + (j + 1) * L.state, c->stream), "segment recompute");
         for (long long j = len - 1; j >= 0; --j) {
+            const bool first = k == L.K - 1 && j == len - 1, last = k == 0 && j == 0;
             CK(c, launch_adjoint_step(c->Q, (const float *)(seg + j * L.state),
-                                      (const float *)(seg + (j + 1) * L.state), lam[cur], dj, lam[1 - cur], p,
-                                      part, total, c->stream),
+                                      (const float *)(seg + (j + 1) * L.state), first ? lam0 : nullptr, dj[cur],
+                                      last ? nullptr : dj[1 - cur], lam0, p, part, done, total, c->stream),
                "adjoint step");
             cur ^= 1;
         }
@@ -1001,11 +1004,11 @@ lwacm_status lwacm_backward(lwacm_ctx *c, const void *ld, const void *lux, const
     void *gout[4] = {gd, gux, guy, guz};
     for (int f = 0; f < c->nf; ++f) {
         if (dtype == LWACM_F32)
-            CK(c, cudaMemcpyAsync(gout[f], (char *)lam[cur] + f * fb, (size_t)c->N * 4, cudaMemcpyDeviceToDevice,
+            CK(c, cudaMemcpyAsync(gout[f], (char *)lam0 + f * fb, (size_t)c->N * 4, cudaMemcpyDeviceToDevice,
                                   c->stream),
                "gradient out");
         else
-            CK(c, launch_convert_out(STORE_F32, LWACM_F64, (char *)lam[cur] + f * fb, gout[f], c->N, c->stream),
+            CK(c, launch_convert_out(STORE_F32, LWACM_F64, (char *)lam0 + f * fb, gout[f], c->N, c->stream),
                "gradient out");
     }
     double h = 0.0;
