@@ -29,7 +29,7 @@
 namespace lwacm {
 namespace {
 
-constexpr int kAdjBlocks = 152 * 4;
+constexpr int kAdjBlocks = 152 * 6;
 
 // (Dbar, Jbar) from lambda+ and the state at t+1: four FP32 fields (three in 2D)
 template <int Q>
@@ -54,10 +54,12 @@ __global__ void __launch_bounds__(256) k_adj_prep(const float *__restrict__ sn, 
 // at t, with the (Dbar, Jbar) fields staged in shared memory: a CTA of
 // 32 x 8 threads takes an x-y tile of the domain and marches along z through a run
 // of planes, keeping the planes z-1, z, z+1 of the tile plus a one-node frame in a
-// ring of four shared-memory slots, the plane z+2 arriving by asynchronous copies
-// while the plane z is computed.
-constexpr int ATX = 32, ATY = 8, AZC = 16;
-constexpr int AW = ATX + 2, AH = ATY + 2, APL = AW * AH;
+// ring of five shared-memory slots, the plane z+2 arriving by asynchronous copies
+// while the plane z is computed (five slots: the slot a copy refills was last read
+// two planes earlier, so one barrier per plane orders it). The state at t of the
+// plane z+1 is loaded into registers while the plane z is computed.
+constexpr int ATX = 32, ATY = 8, AZC = 8;
+constexpr int AW = ATX + 2, AH = ATY + 2, APL = AW * AH, NSL = 5;
 
 // With WALLS, a link whose receiver x + c lies beyond a walled face is the value the
 // node itself takes for the bounced link -c (Eq. ACM2.0cccbb2): gbar = Dbar - c.Jbar
@@ -72,7 +74,7 @@ __global__ void __launch_bounds__(ATX *ATY) k_adj_gather_tiled(const float *__re
                                                                double *__restrict__ nu_total) {
     using L = Lat<Q>;
     constexpr int NF = Q == 19 ? 4 : 3;
-    __shared__ float ring[4][NF][APL];
+    __shared__ float ring[NSL][NF][APL];
     const int tid = (int)threadIdx.x, tx = tid % ATX, ty = tid / ATX;
     const long long plane = (long long)p.nx * p.ny;
     double nu_acc = 0.0;  // FP64 over items; FP32 within an item's run of planes
@@ -93,10 +95,12 @@ __global__ void __launch_bounds__(ATX *ATY) k_adj_gather_tiled(const float *__re
             if (gy < 0) gy += p.ny;
             off2[r] = (long long)gy * p.nx + gx;
         }
-        // asynchronous copy of plane z (periodic) of the tile + frame into ring slot z % 4
+        // asynchronous copy of plane z (periodic) of the tile + frame into ring slot
+        // (z - za + 1) % NSL
+        auto slot_of = [&](int z) { return (z - za + 1) % NSL; };
         auto issue = [&](int z) {
             const int zl = z < 0 ? z + p.nz : (z >= p.nz ? z - p.nz : z);
-            const int slot = z & 3;
+            const int slot = slot_of(z);
 #pragma unroll
             for (int r = 0; r < NE; ++r) {
                 const int e = tid + r * ATX * ATY;
@@ -113,6 +117,18 @@ __global__ void __launch_bounds__(ATX *ATY) k_adj_gather_tiled(const float *__re
             asm volatile("cp.async.commit_group;" ::: "memory");
         };
         float nu_run = 0.f;
+        const int x = x0 + tx, y = y0 + ty;
+        const bool inside = x < p.nx && y < p.ny;
+        const long long k0 = (long long)y * p.nx + x;
+        // the state at t of plane za (then prefetched one plane ahead)
+        float d = 0.f, u = 0.f, v = 0.f, w = 0.f;
+        if (inside) {
+            const long long k = (long long)za * plane + k0;
+            d = st[k];
+            u = st[p.fstride + k];
+            v = st[2 * p.fstride + k];
+            if (Q == 19) w = st[3 * p.fstride + k];
+        }
         __syncthreads();  // the previous item's last reads are done
         issue(za - 1);
         issue(za);
@@ -126,11 +142,17 @@ __global__ void __launch_bounds__(ATX *ATY) k_adj_gather_tiled(const float *__re
                 asm volatile("cp.async.wait_group 0;" ::: "memory");
             }
             __syncthreads();
-            const int x = x0 + tx, y = y0 + ty;
-            if (x < p.nx && y < p.ny) {
-                const long long k = (long long)z * plane + (long long)y * p.nx + x;
-                const float d = st[k], u = st[p.fstride + k], v = st[2 * p.fstride + k];
-                const float w = Q == 19 ? st[3 * p.fstride + k] : 0.f;
+            float dn = 0.f, un = 0.f, vn = 0.f, wn = 0.f;
+            if (inside && z + 1 < zb) {
+                const long long k = (long long)(z + 1) * plane + k0;
+                dn = st[k];
+                un = st[p.fstride + k];
+                vn = st[2 * p.fstride + k];
+                if (Q == 19) wn = st[3 * p.fstride + k];
+            }
+            const int sm = slot_of(z - 1), s0 = slot_of(z), sp = slot_of(z + 1);
+            if (inside) {
+                const long long k = (long long)z * plane + k0;
                 const float rho = 1.f + d;
                 const float q = fmaf(u, u, fmaf(v, v, w * w));
                 // weighted moments of gbar_i = Dbar + c_i . Jbar over the links:
@@ -145,7 +167,7 @@ __global__ void __launch_bounds__(ATX *ATY) k_adj_gather_tiled(const float *__re
                 for (int i = 0; i < Q; ++i) {
                     const int cx = L::c(i, 0), cy = L::c(i, 1), cz = L::c(i, 2);
                     const float wi = L::w(i);
-                    const int slot = (z + cz) & 3;
+                    const int slot = cz < 0 ? sm : (cz > 0 ? sp : s0);
                     const int e = (ty + 1 + cy) * AW + tx + 1 + cx;
                     float gb = ring[slot][0][e];
                     if (cx) gb = fmaf((float)cx, ring[slot][1][e], gb);
@@ -157,7 +179,7 @@ __global__ void __launch_bounds__(ATX *ATY) k_adj_gather_tiled(const float *__re
                                          (p.walled[1] && (yr < 0 || yr >= p.ny)) ||
                                          (Q == 19 && p.walled[2] && (zr < 0 || zr >= p.nz));
                         if (out) {
-                            const int os0 = z & 3, own0 = (ty + 1) * AW + tx + 1;
+                            const int os0 = s0, own0 = (ty + 1) * AW + tx + 1;
                             float b = ring[os0][0][own0];
                             if (cx) b = fmaf((float)-cx, ring[os0][1][own0], b);
                             if (cy) b = fmaf((float)-cy, ring[os0][2][own0], b);
@@ -194,7 +216,7 @@ __global__ void __launch_bounds__(ATX *ATY) k_adj_gather_tiled(const float *__re
                 float lv = rho * fmaf(p.s, g1y, fmaf(9.f, hy, m3 * v));
                 float lw = Q == 19 ? rho * fmaf(p.s, g1z, fmaf(9.f, hz, m3 * w)) : 0.f;
                 const float ln = rho * uG1;
-                const int own = (ty + 1) * AW + tx + 1, os = z & 3;
+                const int own = (ty + 1) * AW + tx + 1, os = s0;
                 const float jx = ring[os][1][own], jy = ring[os][2][own];
                 const float jz = Q == 19 ? ring[os][3][own] : 0.f;
                 const float ju = u * jx + v * jy + w * jz;
@@ -218,7 +240,10 @@ __global__ void __launch_bounds__(ATX *ATY) k_adj_gather_tiled(const float *__re
                 nu_run += fmaf(18.f, ln, -6.f * rho * ju);
                 if (WALLS) nu_run = fmaf(18.f * p.wallc / p.s, nu_wall, nu_run);  // 36 rho0 = wallc / nu
             }
-            __syncthreads();  // slot (z - 1) % 4 is refilled next
+            d = dn;
+            u = un;
+            v = vn;
+            w = wn;
         }
         nu_acc += (double)nu_run;
     }
