@@ -223,6 +223,17 @@ lwacm_status lwacm_fields(lwacm_ctx *ctx, void **d, void **ux, void **uy, void *
 lwacm_status lwacm_get_fields(lwacm_ctx *ctx, void *d, void *ux, void *uy, void *uz, int dtype,
                               int where);
 
+/* As lwacm_get_fields, but only enqueued: with where == LWACM_HOST the copies
+ * are in flight when the call returns, and the host arrays hold the state once
+ * the bound stream has reached them (lwacm_sync, or a synchronisation of that
+ * stream). Host arrays must be page-locked for the copies to overlap other work,
+ * and must stay allocated and untouched until then. Lets a caller stream
+ * independent problems through several contexts on several streams, one
+ * problem's copy back overlapping the next one's copy in. Same arguments and
+ * errors as lwacm_get_fields. */
+lwacm_status lwacm_get_fields_async(lwacm_ctx *ctx, void *d, void *ux, void *uy, void *uz, int dtype,
+                                    int where);
+
 /* FP64 global quantities of the current state (Eq. global.quantities):
  *   out[0] = sum d (mass minus the node count), out[1..3] = sum rho u_a,
  *   out[4] = 0.5 sum rho |u|^2, out[5] = max |u|, out[6] = 0.5 sum (ux+uy)^2,

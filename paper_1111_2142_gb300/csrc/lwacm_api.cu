@@ -831,9 +831,8 @@ lwacm_status lwacm_fields(lwacm_ctx *c, void **d, void **ux, void **uy, void **u
     return LWACM_OK;
 }
 
-lwacm_status lwacm_get_fields(lwacm_ctx *c, void *d, void *ux, void *uy, void *uz, int dtype,
-                              int where) {
-    const Range range("lwacm_get_fields");
+static lwacm_status get_fields(lwacm_ctx *c, void *d, void *ux, void *uy, void *uz, int dtype, int where,
+                               bool sync) {
     lwacm_status s = ready(c, true);
     if (s != LWACM_OK) return s;
     if (!d || !ux || !uy || (c->Q == 19 && !uz))
@@ -854,8 +853,20 @@ lwacm_status lwacm_get_fields(lwacm_ctx *c, void *d, void *ux, void *uy, void *u
         if (where == LWACM_HOST)
             CK(c, cudaMemcpyAsync(dst[f], ddst, nbytes, cudaMemcpyDeviceToHost, c->stream), "D2H stage");
     }
-    if (where == LWACM_HOST) CK(c, cudaStreamSynchronize(c->stream), "sync");
+    if (where == LWACM_HOST && sync) CK(c, cudaStreamSynchronize(c->stream), "sync");
     return LWACM_OK;
+}
+
+lwacm_status lwacm_get_fields(lwacm_ctx *c, void *d, void *ux, void *uy, void *uz, int dtype,
+                              int where) {
+    const Range range("lwacm_get_fields");
+    return get_fields(c, d, ux, uy, uz, dtype, where, true);
+}
+
+lwacm_status lwacm_get_fields_async(lwacm_ctx *c, void *d, void *ux, void *uy, void *uz, int dtype,
+                                    int where) {
+    const Range range("lwacm_get_fields_async");
+    return get_fields(c, d, ux, uy, uz, dtype, where, false);
 }
 
 lwacm_status lwacm_set_scalar(lwacm_ctx *c, const void *T, int dtype, int where) {

@@ -60,6 +60,7 @@ def load():
         "lwacm_step": [vp, ll],
         "lwacm_fields": [vp, P(vp), P(vp), P(vp), P(vp), P(i), P(ll)],
         "lwacm_get_fields": [vp, vp, vp, vp, vp, i, i],
+        "lwacm_get_fields_async": [vp, vp, vp, vp, vp, i, i],
         "lwacm_diagnostics": [vp, P(d)],
         "lwacm_step_count": [vp, P(ll)],
         "lwacm_sync": [vp],
@@ -311,6 +312,19 @@ class Lwacm:
             code = F64 if first.dtype == torch.float64 else F32
         ptrs = [_ptr(o) for o in outs] + [None] * (4 - len(outs))
         self._check(self._lib.lwacm_get_fields(self._h, *ptrs, code, where))
+
+    def get_fields_async(self, outs, where=HOST):
+        """As get_fields_into, only enqueued on this context's stream
+        (lwacm_get_fields_async): host arrays (page-locked for overlap) hold the
+        state once the stream has reached the copies (sync())."""
+        torch = _torch()
+        first = outs[0]
+        if isinstance(first, np.ndarray):
+            code = F64 if first.dtype == np.float64 else F32
+        else:
+            code = F64 if first.dtype == torch.float64 else F32
+        ptrs = [_ptr(o) for o in outs] + [None] * (4 - len(outs))
+        self._check(self._lib.lwacm_get_fields_async(self._h, *ptrs, code, where))
 
     def fields(self):
         """Zero-copy torch views of the current state (storage dtype)."""

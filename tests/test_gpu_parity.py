@@ -322,6 +322,35 @@ def test_roundtrip_and_zero_steps(lw):
     sim.close()
 
 
+def test_get_fields_async_two_contexts(lw):
+    """Two independent problems stepped in turn on two contexts (two streams), the
+    state copied back with the enqueue-only call into pinned host memory: after a
+    device synchronisation each host copy equals that problem's synchronous
+    read-back, and the second problem matches the FP64 oracle."""
+    import torch
+    fa = inputs.smooth_random((6, 8, 12), seed=21)
+    fb = inputs.smooth_random((6, 8, 12), seed=22)
+    sims = [lw.Lwacm(19, 12, 8, 6, 0.02), lw.Lwacm(19, 12, 8, 6, 0.02, stream=torch.cuda.Stream())]
+    outs = [[torch.empty((6, 8, 12), dtype=torch.float32).pin_memory() for _ in range(4)] for _ in sims]
+    for s, f in zip(sims, (fa, fb)):
+        s.set_fields(*f)
+    for k in range(6):
+        s = sims[k % 2]
+        s.step(1)
+        s.get_fields_async(outs[k % 2], lw.HOST)
+    torch.cuda.synchronize()
+    for s, o in zip(sims, outs):
+        ref = s.get_fields(np.float32)
+        for a, b in zip(o, ref):
+            assert np.array_equal(a.numpy(), b)
+        assert s.step_count() == 3
+    eu, ed = errs([o.numpy().astype(np.float64) for o in outs[1]], oracle.step(19, *fb, nu=0.02, nsteps=3),
+                  float(np.max(np.abs(fb[1]))))
+    assert eu < 1e-5 and ed < 1e-4, (eu, ed)
+    for s in sims:
+        s.close()
+
+
 def test_nonfinite_is_reported(lw):
     d, u, v = inputs.smooth_random((8, 8), seed=11)
     d = d.copy()
