@@ -186,6 +186,26 @@ def gtg_force(n: int, t: float):
     return eps ** 3 * np.sin(a) * np.cos(b) * amp, -eps ** 3 * np.cos(a) * np.sin(b) * amp
 
 
+def minion_brown(n: int, u_lat: float = 0.04, k: float = 80.0, delta: float = 0.05):
+    """Perturbed double shear layer of Section 3.2 (Minion & Brown) on the periodic
+    unit square, n x n nodes at x_i = i / n: u = U tanh(k (y - 1/4)) for y <= 1/2,
+    U tanh(k (3/4 - y)) above, v = U delta sin(2 pi (x + 1/4)), with the unit speed
+    U = u_lat in lattice units (the Mach number Ma of the paper's runs) and d = 0.
+    Returns (d, ux, uy) of shape (n, n)."""
+    x = np.arange(n) / n
+    X, Y = np.meshgrid(x, x, indexing="xy")
+    ux = np.where(Y <= 0.5, np.tanh(k * (Y - 0.25)), np.tanh(k * (0.75 - Y))) * u_lat
+    uy = u_lat * delta * np.sin(2.0 * np.pi * (X + 0.25))
+    return np.zeros((n, n)), ux, uy
+
+
+def minion_brown_lattice(n: int, u_lat: float = 0.04, re: float = 1.0e4):
+    """Lattice viscosity and the number of steps to t = 1 for the shear layer: with
+    dx = 1/n and a unit speed of u_lat lattice units, dt = u_lat / n, so
+    nu = (1/Re) dt / dx^2 = u_lat n / Re and t = 1 takes n / u_lat steps."""
+    return u_lat * n / re, int(round(n / u_lat))
+
+
 def gtg_steps(n: int, t_end: float = 60.0) -> int:
     """Number of steps of size eps^2 nearest to t_end."""
     eps = 2.0 * np.pi / n

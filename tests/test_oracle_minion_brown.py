@@ -1,0 +1,74 @@
+"""Robustness run of Section 3.2 (Minion & Brown flow) on the FP64 oracle: the
+perturbed double shear layer, k = 80, delta = 0.05, Re = 10^4 on a 128 x 128 grid
+with a unit speed of 0.04 lattice units (Ma = 0.04), to t = 1 (3200 steps).
+
+What the section states and these tests check:
+  * LW-ACM is stable for this under-resolved flow (the run stays finite and the
+    velocity bounded);
+  * the plain scheme satisfies the divergence-free condition poorly (its
+    pseudo-compressibility coefficient eps^2/nu is 0.61), and relaxing the pressure
+    with the fictitious viscosity nu_p = 170 nu (Section 2.2, item 3) lowers it
+    to eps^2/nu_p = 0.0036, so the velocity divergence drops.
+The paper's figures (vorticity contours) hold no printed values, so the check is
+on these stated properties, not on numbers."""
+import numpy as np
+import pytest
+
+import oracle
+from paper_1111_2142_gb300 import inputs
+
+N, U = 128, 0.04
+
+
+def divergence(ux, uy):
+    """Central-difference divergence in lattice units (periodic)."""
+    return 0.5 * (np.roll(ux, -1, 1) - np.roll(ux, 1, 1) + np.roll(uy, -1, 0) - np.roll(uy, 1, 0))
+
+
+@pytest.fixture(scope="module")
+def runs():
+    nu, steps = inputs.minion_brown_lattice(N, U)
+    f = inputs.minion_brown(N, U)
+    plain = oracle.step(9, *f, nu=nu, nsteps=steps)
+    with_nu_p = oracle.step_nu_p(9, *f, nu=nu, nu_p=170.0 * nu, nsteps=steps)
+    return nu, steps, plain, with_nu_p
+
+
+def test_lattice_parameters():
+    nu, steps = inputs.minion_brown_lattice(N, U)
+    assert steps == 3200
+    assert nu == pytest.approx(5.12e-4)
+    # eps^2/nu of the section, with eps = 1/N and nu = 1/Re in physical units
+    assert (1.0 / N) ** 2 / 1e-4 == pytest.approx(0.61, abs=0.005)
+    assert (1.0 / N) ** 2 / (170e-4) == pytest.approx(0.0036, abs=0.0001)
+    assert 1.0 <= 2.0 / (6.0 * nu + 1.0) < 2.0  # omega in the stable range of Section 2.3
+
+
+def test_initial_state():
+    d, ux, uy = inputs.minion_brown(N, U)
+    assert np.all(d == 0.0)
+    assert np.max(np.abs(ux)) <= U and np.max(np.abs(uy)) == pytest.approx(0.05 * U, rel=1e-3)
+    assert abs(float(np.mean(divergence(ux, uy)))) < 1e-15  # u depends on y only, v on x only: div u = 0
+    assert np.max(np.abs(divergence(ux, uy))) < 1e-15
+
+
+def test_stable_to_t1(runs):
+    _, _, plain, with_nu_p = runs
+    for s in (plain, with_nu_p):
+        assert all(np.all(np.isfinite(a)) for a in s)
+        assert max(np.max(np.abs(s[1])), np.max(np.abs(s[2]))) < 2.0 * U
+
+
+def test_nu_p_reduces_the_divergence(runs):
+    _, _, plain, with_nu_p = runs
+    dp, dn = divergence(plain[1], plain[2]), divergence(with_nu_p[1], with_nu_p[2])
+    assert np.mean(np.abs(dp)) > 3.0 * np.mean(np.abs(dn))
+    assert np.max(np.abs(dp)) > 3.0 * np.max(np.abs(dn))
+
+
+def test_shear_layers_roll_up(runs):
+    """By t = 1 the perturbation has grown: v is no longer the single initial mode."""
+    _, _, plain, with_nu_p = runs
+    _, _, uy0 = inputs.minion_brown(N, U)
+    for s in (plain, with_nu_p):
+        assert np.max(np.abs(s[2])) > 5.0 * np.max(np.abs(uy0))
