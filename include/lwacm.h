@@ -122,7 +122,7 @@ enum {
                                      1/6], or 0 = nu (default). Single periodic domains
                                      only (LWACM_E_UNSUPPORTED otherwise); runs on the
                                      generic kernel; the adjoint refuses nu_p != nu. */
-    LWACM_OPT_SCALAR_ALPHA = 15   /* > 0: carry a passive scalar T (Eq. ACM2.0t, the
+    LWACM_OPT_SCALAR_ALPHA = 15,  /* > 0: carry a passive scalar T (Eq. ACM2.0t, the
                                      thermal LW-ACM of Appendix "Asymptotic analysis for
                                      energy equation") with diffusivity alpha in (0, 1/6]
                                      (alpha = (1/omega_t - 1/2)/3, Eq. diffusivity2),
@@ -130,6 +130,25 @@ enum {
                                      level; 0 = none (default). Before lwacm_bind (it
                                      adds one field to the workspace); single periodic
                                      domains only; runs on the generic kernel. */
+    LWACM_OPT_BULK_GAMMA = 16     /* gamma in (-1, 1), 0 = off (default): the bulk-
+                                     viscosity variant of Appendix "Computing derivatives
+                                     locally", Eq. quasi-equilibrium2. The equilibrium of
+                                     Eq. ACM2.0 becomes f^(e) plus the change of the
+                                     product-form quasi-equilibrium (Eqs.
+                                     d2q9_equilibrium_gen, quasi-equilibrium) when its
+                                     trace moves from Tr^(e) = 2/3 + |u|^2 to Tr^(e) +
+                                     gamma (Tr^(+) - Tr^(e)), Tr^(+) the trace of
+                                     sum_i c_i c_i f_i over rho of the node's last update,
+                                     carried as the field Tr^(+) - Tr^(e)
+                                     (lwacm_get_trace; lwacm_set_fields sets it to zero).
+                                     On a linear longitudinal wave
+                                     of wave number k the extra damping per step is
+                                     nu gamma k^2 / (1 - gamma) (bulk viscosity raised by
+                                     2 rho0 nu gamma / (1 - gamma)); shear waves are
+                                     unchanged. Before lwacm_bind (one more field);
+                                     periodic D2Q9 domains only, neither with the scalar
+                                     nor with LWACM_OPT_NU_P (LWACM_E_UNSUPPORTED); runs
+                                     on the generic kernel. */
 };
 
 /* Create a single-domain context.
@@ -203,6 +222,12 @@ lwacm_status lwacm_set_force_field(lwacm_ctx *ctx, const void *gx, const void *g
  * bound, or fields not set), LWACM_E_ARG. */
 lwacm_status lwacm_set_scalar(lwacm_ctx *ctx, const void *T, int dtype, int where);
 lwacm_status lwacm_get_scalar(lwacm_ctx *ctx, void *T, int dtype, int where);
+
+/* The trace deviation Tr^(+) - Tr^(e) of LWACM_OPT_BULK_GAMMA (nx*ny values, as
+ * lwacm_get_scalar): Tr^(+) the trace of sum_i c_i c_i f_i over rho of each node's
+ * last update, Tr^(e) = 2/3 + |u|^2 of the current state. LWACM_E_STATE without
+ * the variant. */
+lwacm_status lwacm_get_trace(lwacm_ctx *ctx, void *T, int dtype, int where);
 
 /* Advance the state by n >= 0 time steps of Eq. ACM2.0 (plus the wall pass of
  * Eqs. ACM2.0cccbb2 / ACM2.0ccccbb and the forcing of Eq. force when enabled).

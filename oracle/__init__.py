@@ -64,6 +64,8 @@ def _load():
         lib.lwo_step_force_field.argtypes = [i, i, i, i, d, i, d, P, P, P, P, l, P, P, P, P, i]
         lib.lwo_step_scalar.argtypes = [i, i, i, i, d, d, l, P, P, P, P, P, i]
         lib.lwo_step_nu_p.argtypes = [i, i, i, i, d, d, P, P, P, P, l, P, P, P, P, i]
+        lib.lwo_step_bulk.argtypes = [i, i, d, d, l, P, P, P, P, i]
+        lib.lwo_feq_star.argtypes = [d, P, d, d, P]
         lib.lwo_lattice_tables.argtypes = [i, IP, P, IP]
         lib.lwo_equilibria.argtypes = [i, d, P, P, P]
         lib.lwo_bgk_init.argtypes = [i, i, i, i, P, P, P, P, P]
@@ -177,6 +179,33 @@ def step_scalar(Q, d, ux, uy, uz=None, *, T, nu, alpha, nsteps=1, nthreads=0):
     if rc != 0:
         raise ValueError(f"oracle scalar step failed: {rc}")
     return (d, ux, uy, T) if Q == 9 else (d, ux, uy, uz, T)
+
+
+def step_bulk(d, ux, uy, tr=None, *, nu, gamma, nsteps=1, nthreads=0):
+    """D2Q9, periodic: Eq. ACM2.0 with the quasi-equilibrium f^(e*) of Eq.
+    quasi-equilibrium2 (bulk viscosity xi = 2 rho0 nu (1 + 2 gamma)); tr is the
+    normalised trace Tr^(+) of the last update (default Tr^(e) = 2/3 + |u|^2).
+    Returns (d, ux, uy, tr)."""
+    lib = _load()
+    d, ux, uy = _f64(d), _f64(ux), _f64(uy)
+    tr = 2.0 / 3.0 + ux * ux + uy * uy if tr is None else _f64(tr)
+    ny, nx = d.shape[-2], d.shape[-1]
+    rc = lib.lwo_step_bulk(nx, ny, float(nu), float(gamma), int(nsteps), _p(d), _p(ux), _p(uy), _p(tr),
+                           int(nthreads))
+    if rc != 0:
+        raise ValueError(f"oracle bulk step failed: {rc}")
+    return d, ux, uy, tr
+
+
+def feq_star(rho, u, tr_plus, gamma):
+    """The nine values f^(e*)_i (oracle link order) at one node."""
+    lib = _load()
+    f = np.zeros(9)
+    uu = np.array([u[0], u[1]], dtype=np.float64)
+    rc = lib.lwo_feq_star(float(rho), _p(uu), float(tr_plus), float(gamma), _p(f))
+    if rc != 0:
+        raise ValueError(f"oracle feq_star failed: {rc}")
+    return f
 
 
 def step_force_field(Q, d, ux, uy, uz=None, *, nu, g, bc=PERIODIC, nsteps=1, rho0=1.0, lid=None,

@@ -20,6 +20,10 @@
  *   - a passive scalar advected and diffused by Eq. ACM2.0t (lwo_step_scalar);
  *   - a separate relaxation frequency omega_p for the pressure update (Section
  *     2.2, item 3), periodic domains (lwo_step_nu_p);
+ *   - the bulk-viscosity variant of Appendix "Computing derivatives locally"
+ *     (Eq. quasi-equilibrium2 with the quasi-equilibrium of Eq. quasi-equilibrium
+ *     and the product form of Eq. d2q9_equilibrium_gen), D2Q9, periodic
+ *     (lwo_step_bulk);
  *   - external forcing, Eq. force, with a constant acceleration or a per-node
  *     field g(x) (lwo_step_force_field; a time-dependent g is applied by one call
  *     per step);
@@ -418,6 +422,106 @@ int lwo_step_scalar(int Q, int nx, int ny, int nz, double nu, double alpha, long
         memcpy(T, Tn, sizeof(double) * N);
     }
     free(Tn);
+    return 0;
+}
+
+/* -------------------------------------------------------------------------
+ * Bulk viscosity (Appendix "Computing derivatives locally"), D2Q9 only.
+ * Eq. d2q9_equilibrium_gen: f^(g)_i(Pxx, Pyy) = rho phi_x(c_ix) phi_y(c_iy) with
+ * phi_x(0) = 1 - Pxx, phi_x(+-1) = (Pxx +- u)/2 and likewise for y (the listed
+ * rows written as one product, independent of the link order).
+ * Eq. quasi-equilibrium: f^(qe)(rho, u, Tr) = f^(g)((Tr + u^2 - v^2)/2, (Tr - u^2 + v^2)/2).
+ * Eq. quasi-equilibrium2 replaces f^(e) in Eq. ACM2.0 by the quasi-equilibrium at
+ * Tr* = Tr^(e) + gamma (Tr^(+) - Tr^(e)), Tr^(e) = 2/3 + |u|^2, Tr^(+) the trace of
+ * sum_i c_i c_i f_i of the updated populations over rho. Reading (the printed
+ * f^(g) equals f^(e) only up to third-order terms): the increment is added to
+ * f^(e),
+ *   f^(e*)_i = f^(e)_i + f^(qe)_i(rho, u, Tr*) - f^(qe)_i(rho, u, Tr^(e)),
+ * which has the second moment of Eq. second-quasi-equilibrium2 exactly and is
+ * f^(e) itself when gamma = 0 or Tr^(+) = Tr^(e). The odd part is taken from its
+ * definition, (f(rho, u) - f(rho, -u))/2, as for f^(e).
+ * ------------------------------------------------------------------------- */
+static double fg(int cx, int cy, double rho, double u, double v, double pxx, double pyy) {
+    const double px = cx == 0 ? 1.0 - pxx : 0.5 * (pxx + cx * u);
+    const double py = cy == 0 ? 1.0 - pyy : 0.5 * (pyy + cy * v);
+    return rho * px * py;
+}
+static double fqe(int cx, int cy, double rho, double u, double v, double tr) {
+    return fg(cx, cy, rho, u, v, 0.5 * (tr + u * u - v * v), 0.5 * (tr - u * u + v * v));
+}
+static double feq_star(const lwo_lattice *L, int i, double rho, const double u[3], double tr_plus,
+                       double gamma) {
+    const double tre = 2.0 / 3.0 + u[0] * u[0] + u[1] * u[1];
+    const double trs = tre + gamma * (tr_plus - tre);
+    const int cx = L->c[i][0], cy = L->c[i][1];
+    return feq(L, i, rho, u) + fqe(cx, cy, rho, u[0], u[1], trs) - fqe(cx, cy, rho, u[0], u[1], tre);
+}
+static double feq_star_o(const lwo_lattice *L, int i, double rho, const double u[3], double tr_plus,
+                         double gamma) {
+    const double mu[3] = {-u[0], -u[1], -u[2]};
+    return 0.5 * (feq_star(L, i, rho, u, tr_plus, gamma) - feq_star(L, i, rho, mu, tr_plus, gamma));
+}
+
+/* f^(e*) of one node (Q = 9 values), for the tests of Eq. second-quasi-equilibrium2 */
+int lwo_feq_star(double rho, const double *u, double tr_plus, double gamma, double *f) {
+    lwo_lattice L;
+    if (make_lattice(9, &L)) return -1;
+    const double uu[3] = {u[0], u[1], 0.0};
+    for (int i = 0; i < 9; ++i) f[i] = feq_star(&L, i, rho, uu, tr_plus, gamma);
+    return 0;
+}
+
+/* Advance (d, u, Tr) of a periodic D2Q9 domain by Eq. ACM2.0 with f^(e*) in place
+ * of f^(e), nsteps times. Tr holds Tr^(+) of the last update (the caller starts it
+ * at Tr^(e) = 2/3 + |u|^2, which makes the first step the standard one). */
+int lwo_step_bulk(int nx, int ny, double nu, double gamma, long nsteps, double *d, double *ux, double *uy,
+                  double *tr, int nthreads) {
+    lwo_lattice L;
+    lwo_geom G;
+    if (make_lattice(9, &L)) return -1;
+    if (make_geom(&L, nx, ny, 1, LWO_PERIODIC, &G)) return -2;
+    if (!(nu > 0.0) || nu > 1.0 / 6.0) return -3;
+    if (!tr) return -4;
+    const long N = (long)nx * ny;
+    const double omega = omega_of_nu(nu);
+    const double a = 2.0 * (omega - 1.0) / omega;
+    double *buf = (double *)malloc(sizeof(double) * 4 * N);
+    if (!buf) return -6;
+    double *dn = buf, *un = buf + N, *vn = buf + 2 * N, *tn = buf + 3 * N;
+    set_threads(nthreads);
+    for (long t = 0; t < nsteps; ++t) {
+#pragma omp parallel for schedule(static)
+        for (int y = 0; y < ny; ++y)
+            for (int xx = 0; xx < nx; ++xx) {
+                const int x[3] = {xx, y, 0};
+                const long k = (long)y * nx + xx;
+                const double rk = 1.0 + d[k];
+                const double uk[3] = {ux[k], uy[k], 0.0};
+                double m0 = 0.0, m1 = 0.0, m2 = 0.0, m3 = 0.0;
+                for (int i = 0; i < 9; ++i) {
+                    int above;
+                    const long s = source_of(&G, x, L.c[i], &above);
+                    const double rs = 1.0 + d[s];
+                    const double us[3] = {ux[s], uy[s], 0.0};
+                    const double fi = feq_star(&L, i, rs, us, tr[s], gamma) +
+                                      a * (feq_star_o(&L, i, rk, uk, tr[k], gamma) -
+                                           feq_star_o(&L, i, rs, us, tr[s], gamma));
+                    m0 += fi;
+                    m1 += L.c[i][0] * fi;
+                    m2 += L.c[i][1] * fi;
+                    m3 += (L.c[i][0] * L.c[i][0] + L.c[i][1] * L.c[i][1]) * fi;
+                }
+                dn[k] = m0 - 1.0;
+                un[k] = m1 / m0;
+                vn[k] = m2 / m0;
+                tn[k] = m3 / m0;
+            }
+        memcpy(d, dn, sizeof(double) * N);
+        memcpy(ux, un, sizeof(double) * N);
+        memcpy(uy, vn, sizeof(double) * N);
+        memcpy(tr, tn, sizeof(double) * N);
+    }
+    free(buf);
     return 0;
 }
 

@@ -56,6 +56,8 @@ __device__ __forceinline__ void tile_update(const T *__restrict__ in, T *__restr
     p.gfield = nullptr;
     p.sdelta = 0.f;
     p.scalar = 0;
+    p.bulk = 0;
+    p.gamma = 0.f;
     p.at = 0.f;
     p.lid_axis = 0;
     p.err = nullptr;
@@ -401,7 +403,7 @@ bool batch_shape_supported(int Q, int storage, int k) {
 }
 
 bool tiles2d_supported(int Q, int storage, const StepParams &p) {
-    return Q == 9 && p.nz == 1 && !p.has_force && !p.gfield && p.sdelta == 0.f && !p.scalar &&
+    return Q == 9 && p.nz == 1 && !p.has_force && !p.gfield && p.sdelta == 0.f && !p.scalar && !p.bulk &&
            (storage == STORE_F32 || storage == STORE_BF16 || storage == STORE_F16);
 }
 

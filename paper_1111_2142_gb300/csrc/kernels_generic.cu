@@ -11,7 +11,7 @@
 
 namespace lwacm {
 
-template <int Q, typename T, bool NUP, bool SC>
+template <int Q, typename T, bool NUP, bool SC, bool BULK = false>
 __global__ void __launch_bounds__(256) k_step_generic(const T *__restrict__ in,
                                                       T *__restrict__ out, StepParams p) {
     const long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x;
@@ -20,7 +20,7 @@ __global__ void __launch_bounds__(256) k_step_generic(const T *__restrict__ in,
     const long long r = idx / p.nx;
     const int y = (int)(r % p.ny);
     const int z = (int)(r / p.ny);
-    node_update<Q, false, NUP, SC>(in, out, p, x, y, z);
+    node_update<Q, false, NUP, SC, BULK>(in, out, p, x, y, z);
 }
 
 // Boundary nodes of a walled domain, enumerated without gaps.
@@ -186,7 +186,7 @@ template <typename T>
 cudaError_t launch_step_generic_t(int Q, const void *in, void *out, const StepParams &p,
                                   cudaStream_t st) {
     const unsigned nb = blocks_for(p.N, 256);
-    const int v = (p.sdelta != 0.f ? 1 : 0) + (p.scalar ? 2 : 0);
+    const int v = (p.sdelta != 0.f ? 1 : 0) + (p.scalar ? 2 : 0) + (p.bulk ? 4 : 0);
     const T *i0 = (const T *)in;
     T *o0 = (T *)out;
     if (Q == 9) {
@@ -194,7 +194,9 @@ cudaError_t launch_step_generic_t(int Q, const void *in, void *out, const StepPa
             case 0: k_step_generic<9, T, false, false><<<nb, 256, 0, st>>>(i0, o0, p); break;
             case 1: k_step_generic<9, T, true, false><<<nb, 256, 0, st>>>(i0, o0, p); break;
             case 2: k_step_generic<9, T, false, true><<<nb, 256, 0, st>>>(i0, o0, p); break;
-            default: k_step_generic<9, T, true, true><<<nb, 256, 0, st>>>(i0, o0, p); break;
+            case 3: k_step_generic<9, T, true, true><<<nb, 256, 0, st>>>(i0, o0, p); break;
+            case 4: k_step_generic<9, T, false, false, true><<<nb, 256, 0, st>>>(i0, o0, p); break;
+            default: return cudaErrorInvalidValue;  // the trace goes with neither omega_p nor the scalar
         }
     } else {
         switch (v) {

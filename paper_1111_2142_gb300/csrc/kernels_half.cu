@@ -612,7 +612,7 @@ static cudaError_t prepare_storage(int storage) {
 bool half_supported(int Q, int storage, const StepParams &p) {
     if (Q != 19 || p.bc != BC_PERIODIC) return false;
     if (storage != STORE_F32 && storage != STORE_BF16 && storage != STORE_F16) return false;
-    if (p.has_force || p.gfield || p.sdelta != 0.f || p.scalar) return false;  // plain scheme only
+    if (p.has_force || p.gfield || p.sdelta != 0.f || p.scalar || p.bulk) return false;  // plain scheme only
     if ((p.nx != 128 && p.nx != 256) || p.ny % ROWS != 0 || p.ny < ROWS || p.nz < 1) return false;
     if (p.fstride % 8 != 0 || !p.err) return false;  // 16-byte field starts for 2-byte storage
     int dev = 0;

@@ -37,7 +37,9 @@ struct lwacm_ctx {
     int Q = 0, D = 0, nx = 0, ny = 0, nz = 0, bc = 0, nf = 0;
     double nu = 0, nu_p = 0;  // nu_p: viscosity of the pressure update (0: nu)
     double alpha = 0;         // diffusivity of the passive scalar (0: no scalar)
-    int nsc = 0;              // scalar fields stored after the flow fields (0 or 1)
+    double gamma = 0;         // D2Q9 bulk-viscosity variant (Appendix "Computing derivatives locally")
+    bool bulk = false;        // the variant is on: Tr+ - Tr^(e) is the field after the flow fields
+    int nsc = 0;              // fields stored after the flow fields: the scalar or the trace (0 or 1)
     long long N = 0, Nal = 0;
     double lid[3] = {0, 0, 0}, force[3] = {0, 0, 0}, rho0 = 1.0;
     int storage = LWACM_F32;
@@ -153,8 +155,10 @@ StepParams params(const lwacm_ctx *c) {
     p.has_force = (c->force[0] != 0 || c->force[1] != 0 || c->force[2] != 0) ? 1 : 0;
     p.gfield = (c->ff_active && c->ws) ? (const float *)(c->ws + c->off_ff) : nullptr;
     p.sdelta = c->nu_p > 0 ? (float)(18.0 * (c->nu_p - c->nu)) : 0.f;
-    p.scalar = c->nsc;
+    p.scalar = c->alpha != 0 ? 1 : 0;
     p.at = (float)(1.0 - 6.0 * c->alpha);  // a_t = 2(omega_t - 1)/omega_t, alpha = (1/omega_t - 1/2)/3
+    p.bulk = c->bulk ? 1 : 0;
+    p.gamma = (float)c->gamma;
     p.err = c->ws ? (int *)(c->ws + c->off_err) : nullptr;
     p.walled[0] = p.walled[1] = p.walled[2] = 0;
     p.lid_axis = c->D - 1;
@@ -610,8 +614,23 @@ lwacm_status lwacm_set_option(lwacm_ctx *c, int key, double v) {
                 return fail(c, LWACM_E_RANGE, "alpha must be in (0, 1/6] (or 0: no scalar)");
             if (v != 0 && c->bc != LWACM_BC_PERIODIC)
                 return fail(c, LWACM_E_UNSUPPORTED, "the scalar is for periodic domains");
+            if (v != 0 && c->bulk) return fail(c, LWACM_E_UNSUPPORTED, "not with the bulk-viscosity variant");
             c->alpha = v;
             c->nsc = v != 0 ? 1 : 0;
+            layout(c);
+            break;
+        }
+        case LWACM_OPT_BULK_GAMMA: {
+            if (c->nbatch) return fail(c, LWACM_E_UNSUPPORTED, "no bulk-viscosity variant in batched contexts");
+            if (c->bound) return fail(c, LWACM_E_STATE, "the bulk-viscosity variant is set up before lwacm_bind");
+            if (!(v > -1.0 && v < 1.0)) return fail(c, LWACM_E_RANGE, "gamma must be in (-1, 1)");
+            if (v != 0 && (c->Q != 9 || c->bc != LWACM_BC_PERIODIC))
+                return fail(c, LWACM_E_UNSUPPORTED, "the bulk-viscosity variant is for periodic D2Q9 domains");
+            if (v != 0 && c->alpha != 0) return fail(c, LWACM_E_UNSUPPORTED, "not with the passive scalar");
+            if (v != 0 && c->nu_p > 0) return fail(c, LWACM_E_UNSUPPORTED, "not with omega_p");
+            c->gamma = v;
+            c->bulk = v != 0;
+            c->nsc = c->bulk ? 1 : 0;
             layout(c);
             break;
         }
@@ -621,6 +640,7 @@ lwacm_status lwacm_set_option(lwacm_ctx *c, int key, double v) {
                 return fail(c, LWACM_E_RANGE, "nu_p must be in (0, 1/6] (or 0: same as nu)");
             if (v != 0 && c->bc != LWACM_BC_PERIODIC)
                 return fail(c, LWACM_E_UNSUPPORTED, "omega_p is for periodic domains");
+            if (v != 0 && c->bulk) return fail(c, LWACM_E_UNSUPPORTED, "not with the bulk-viscosity variant");
             c->nu_p = v;
             break;
         }
@@ -723,8 +743,9 @@ lwacm_status lwacm_set_fields(lwacm_ctx *c, const void *d, const void *ux, const
         }
         CK(c, launch_convert_in(c->storage, dtype, dsrc, fd, c->N, c->stream), "convert in");
     }
-    if (c->nsc)  // the scalar starts at zero until lwacm_set_scalar
-        CK(c, cudaMemsetAsync(dst + (size_t)c->nf * field_bytes(c), 0, field_bytes(c), c->stream), "zero scalar");
+    // the scalar starts at zero until lwacm_set_scalar; the trace deviation of the
+    // bulk-viscosity variant at zero (Tr^(+) = Tr^(e): the first step is the standard one)
+    if (c->nsc) CK(c, cudaMemsetAsync(dst + (size_t)c->nf * field_bytes(c), 0, field_bytes(c), c->stream), "zero extra");
     c->has_fields = true;
     c->steps = 0;
     return LWACM_OK;
@@ -872,7 +893,7 @@ lwacm_status lwacm_get_fields_async(lwacm_ctx *c, void *d, void *ux, void *uy, v
 lwacm_status lwacm_set_scalar(lwacm_ctx *c, const void *T, int dtype, int where) {
     lwacm_status s = ready(c, true);
     if (s != LWACM_OK) return s;
-    if (!c->nsc) return fail(c, LWACM_E_STATE, "no scalar (LWACM_OPT_SCALAR_ALPHA before bind)");
+    if (c->alpha == 0) return fail(c, LWACM_E_STATE, "no scalar (LWACM_OPT_SCALAR_ALPHA before bind)");
     if (!T) return fail(c, LWACM_E_ARG, "null scalar");
     if (dtype != LWACM_F32 && dtype != LWACM_F64) return fail(c, LWACM_E_ARG, "dtype must be F32 or F64");
     if (where != LWACM_DEVICE && where != LWACM_HOST) return fail(c, LWACM_E_ARG, "bad location");
@@ -891,11 +912,8 @@ lwacm_status lwacm_set_scalar(lwacm_ctx *c, const void *T, int dtype, int where)
     return LWACM_OK;
 }
 
-lwacm_status lwacm_get_scalar(lwacm_ctx *c, void *T, int dtype, int where) {
-    lwacm_status s = ready(c, true);
-    if (s != LWACM_OK) return s;
-    if (!c->nsc) return fail(c, LWACM_E_STATE, "no scalar (LWACM_OPT_SCALAR_ALPHA before bind)");
-    if (!T) return fail(c, LWACM_E_ARG, "null scalar");
+static lwacm_status get_extra(lwacm_ctx *c, void *T, int dtype, int where) {
+    if (!T) return fail(c, LWACM_E_ARG, "null output");
     if (dtype != LWACM_F32 && dtype != LWACM_F64) return fail(c, LWACM_E_ARG, "dtype must be F32 or F64");
     if (where != LWACM_DEVICE && where != LWACM_HOST) return fail(c, LWACM_E_ARG, "bad location");
     const char *fs = (const char *)bufp(c, c->cur) + (size_t)c->nf * field_bytes(c);
@@ -910,6 +928,20 @@ lwacm_status lwacm_get_scalar(lwacm_ctx *c, void *T, int dtype, int where) {
     }
     if (where == LWACM_HOST) CK(c, cudaStreamSynchronize(c->stream), "sync");
     return LWACM_OK;
+}
+
+lwacm_status lwacm_get_scalar(lwacm_ctx *c, void *T, int dtype, int where) {
+    lwacm_status s = ready(c, true);
+    if (s != LWACM_OK) return s;
+    if (c->alpha == 0) return fail(c, LWACM_E_STATE, "no scalar (LWACM_OPT_SCALAR_ALPHA before bind)");
+    return get_extra(c, T, dtype, where);
+}
+
+lwacm_status lwacm_get_trace(lwacm_ctx *c, void *T, int dtype, int where) {
+    lwacm_status s = ready(c, true);
+    if (s != LWACM_OK) return s;
+    if (!c->bulk) return fail(c, LWACM_E_STATE, "no bulk-viscosity variant (LWACM_OPT_BULK_GAMMA before bind)");
+    return get_extra(c, T, dtype, where);
 }
 
 lwacm_status lwacm_diagnostics(lwacm_ctx *c, double out[8]) {

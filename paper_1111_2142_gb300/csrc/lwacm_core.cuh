@@ -92,6 +92,8 @@ struct StepParams {
     float sdelta;         // 18 (nu_p - nu): pressure update relaxed with omega_p (0: omega_p = omega)
     int scalar;           // 1: a passive scalar T is stored after the flow fields (Eq. ACM2.0t)
     float at;             // 1 - 6 alpha = 2(omega_t - 1)/omega_t of the scalar
+    int bulk;             // 1: D2Q9 bulk-viscosity variant, the trace Tr+ stored after the flow fields
+    float gamma;          // its gamma (Appendix "Computing derivatives locally")
     int walled[3];      // 1 = half-way walls on both ends of this axis
     int lid_axis;       // axis whose top wall moves with the lid velocity
     int *err;           // device error word (bounded waits that gave up set it)

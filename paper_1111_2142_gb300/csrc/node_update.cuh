@@ -14,7 +14,20 @@ namespace lwacm {
 // with the velocity at time t:
 //   T+(x) = a_t T(x) + sum_i w_i [(1 - a_t)(T + 9/2 e^2 - 3/2 |u|^2) + 3 T e](x - c_i),
 // the own node's even parts summing to a_t T(x) (sum_i w_i (9/2 e^2 - 3/2 |u|^2) = 0).
-template <int Q, bool WALLS, bool NUP = false, bool SC = false, typename T>
+// With BULK (D2Q9, periodic) the source's equilibrium is f^(e*) of Appendix
+// "Computing derivatives locally" (Eq. quasi-equilibrium2): f^(e) plus the change of
+// the product-form quasi-equilibrium (Eqs. d2q9_equilibrium_gen, quasi-equilibrium)
+// when its trace moves from Tr^(e) = 2/3 + |u|^2 to Tr^(e) + gamma (Tr^(+) - Tr^(e)),
+// Tr^(+) the trace of the source's last update, stored as the deviation
+// Tr^(+) - Tr^(e) (like d = rho - 1: no O(1) constant in single precision). Per
+// link the increment is
+//   Df = rho [h (ax B + ay A) + ax ay h^2],  h = gamma (Tr^(+) - Tr^(e)) / 2,
+// with A = 1 - Pxx (c_x = 0) or (Pxx + c_x u)/2, ax = -1 or 1/2 (B, ay likewise in
+// y), Pxx = 1/3 + u^2, Pyy = 1/3 + v^2; it is pre-combined like f^(e), Df - a Df^o,
+// with its odd part Df^o = rho h (ax c_y v/2 + ay c_x u/2). The post-combine term
+// adds nothing to the trace and sum_i (|c_i|^2 - 2/3) w_i = 0, so
+// Tr^(+) - Tr^(e) = sum_i (|c_i|^2 - 2/3) g_i / rho+ - |u+|^2.
+template <int Q, bool WALLS, bool NUP = false, bool SC = false, bool BULK = false, typename T>
 __device__ __forceinline__ void node_update(const T *__restrict__ in, T *__restrict__ out,
                                             const StepParams &p, int x, int y, int z) {
     using L = Lat<Q>;
@@ -25,7 +38,7 @@ __device__ __forceinline__ void node_update(const T *__restrict__ in, T *__restr
     const float uz = (Q == 19) ? ldf(Win + k) : 0.f;
     const float rx = 1.f + dx;
     const float qx = fmaf(ux, ux, fmaf(uy, uy, uz * uz));
-    float dd = 0.f, jx = 0.f, jy = 0.f, jz = 0.f, dsp = 0.f, ts = 0.f;
+    float dd = 0.f, jx = 0.f, jy = 0.f, jz = 0.f, dsp = 0.f, ts = 0.f, trs = 0.f;
     const T *Tin = in + (Q == 19 ? 4 : 3) * p.fstride;
     const float omt = 1.f - p.at;
 #pragma unroll
@@ -58,6 +71,17 @@ __device__ __forceinline__ void node_update(const T *__restrict__ in, T *__restr
                 const float even = tsrc + fmaf(4.5f * e, e, -1.5f * q);
                 ts = fmaf(L::w(i), fmaf(omt, even, 3.f * tsrc * e), ts);
             }
+            if (BULK) {
+                const float pxx = fmaf(us, us, 1.f / 3.f), pyy = fmaf(vs, vs, 1.f / 3.f);
+                const float h = 0.5f * p.gamma * ldf(Tin + s);
+                const float A = cx == 0 ? 1.f - pxx : 0.5f * fmaf((float)cx, us, pxx);
+                const float B = cy == 0 ? 1.f - pyy : 0.5f * fmaf((float)cy, vs, pyy);
+                const float ax = cx == 0 ? -1.f : 0.5f, ay = cy == 0 ? -1.f : 0.5f;
+                const float rs = 1.f + ds;
+                const float df = rs * h * fmaf(ax * ay, h, fmaf(ax, B, ay * A));
+                const float dfo = rs * h * (0.5f * fmaf(ax * cy, vs, ay * cx * us));
+                g += fmaf(-p.a, dfo, df);
+            }
         } else {
             // Eq. ACM2.0cccbb2 + Eq. ACM2.0ccccbb: own outgoing BB(i) value, reflected
             const float e = -(cx * ux + cy * uy + cz * uz);
@@ -68,6 +92,7 @@ __device__ __forceinline__ void node_update(const T *__restrict__ in, T *__restr
             }
         }
         dd += g;
+        if (BULK) trs = fmaf((float)(cx * cx + cy * cy) - 2.f / 3.f, g, trs);
         if (cx) jx += cx > 0 ? g : -g;
         if (cy) jy += cy > 0 ? g : -g;
         if (cz) jz += cz > 0 ? g : -g;
@@ -87,11 +112,13 @@ __device__ __forceinline__ void node_update(const T *__restrict__ in, T *__restr
         if (Q == 19) jz = fmaf(rx, __ldg(p.gfield + 2 * p.fstride + k), jz);
     }
     const float rn = 1.f + dd;
+    const float uxn = jx / rn, uyn = jy / rn;
     stf(out + k, dd);
-    stf(out + p.fstride + k, jx / rn);
-    stf(out + 2 * p.fstride + k, jy / rn);
+    stf(out + p.fstride + k, uxn);
+    stf(out + 2 * p.fstride + k, uyn);
     if (Q == 19) stf(out + 3 * p.fstride + k, jz / rn);
     if (SC) stf(out + (Q == 19 ? 4 : 3) * p.fstride + k, fmaf(p.at, ldf(Tin + k), ts));
+    if (BULK) stf(out + 3 * p.fstride + k, trs / rn - fmaf(uxn, uxn, uyn * uyn));
 }
 
 }  // namespace lwacm

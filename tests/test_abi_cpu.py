@@ -214,6 +214,35 @@ def test_scalar_option(lib):
     lib.lwacm_destroy(hc)
 
 
+def test_bulk_gamma_option(lib):
+    """LWACM_OPT_BULK_GAMMA: range, one more field, periodic D2Q9 only, exclusive
+    with the scalar and with omega_p, before bind; lwacm_get_trace needs it."""
+    from paper_1111_2142_gb300 import lwacm as lw
+    st, h = _create(lib, 9, 16, 12, 1, 0.02, 0)
+    n0 = ctypes.c_size_t()
+    assert lib.lwacm_workspace_bytes(h, ctypes.byref(n0)) == lw.OK
+    assert lib.lwacm_get_trace(h, ctypes.c_void_p(16), lw.F32, lw.DEVICE) == lw.E_STATE  # not bound
+    for bad in (1.0, -1.0, 2.5):
+        assert lib.lwacm_set_option(h, lw.OPT_BULK_GAMMA, bad) == lw.E_RANGE
+    assert lib.lwacm_set_option(h, lw.OPT_BULK_GAMMA, 0.4) == lw.OK
+    n1 = ctypes.c_size_t()
+    assert lib.lwacm_workspace_bytes(h, ctypes.byref(n1)) == lw.OK
+    assert n1.value >= n0.value + 2 * 16 * 12 * 4  # the trace field in each buffer
+    assert lib.lwacm_set_option(h, lw.OPT_SCALAR_ALPHA, 0.05) == lw.E_UNSUPPORTED
+    assert lib.lwacm_set_option(h, lw.OPT_NU_P, 0.1) == lw.E_UNSUPPORTED
+    assert lib.lwacm_set_option(h, lw.OPT_BULK_GAMMA, 0.0) == lw.OK  # off again
+    n2 = ctypes.c_size_t()
+    assert lib.lwacm_workspace_bytes(h, ctypes.byref(n2)) == lw.OK and n2.value == n0.value
+    assert lib.lwacm_set_option(h, lw.OPT_SCALAR_ALPHA, 0.05) == lw.OK
+    assert lib.lwacm_set_option(h, lw.OPT_BULK_GAMMA, 0.4) == lw.E_UNSUPPORTED
+    lib.lwacm_destroy(h)
+    for args in ((19, 8, 8, 8, 0.02, 0), (9, 16, 16, 1, 0.02, 1)):  # D3Q19; a cavity
+        st, hb = _create(lib, *args)
+        assert st == lw.OK
+        assert lib.lwacm_set_option(hb, lw.OPT_BULK_GAMMA, 0.4) == lw.E_UNSUPPORTED
+        lib.lwacm_destroy(hb)
+
+
 def test_missing_library_fails_loudly(monkeypatch, tmp_path):
     """No CPU fallback: without the built library the binding raises."""
     from paper_1111_2142_gb300 import lwacm as lw
