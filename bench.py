@@ -8,9 +8,9 @@ One bench "step" is one LW-ACM time step over the whole 256^3 lattice
   e2e        the same metric through the C ABI with host buffers: each step
              copies the fields of one 256^3 problem in from pinned host memory
              (lwacm_set_fields), advances it one step and copies the fields back
-             (lwacm_get_fields_async); consecutive steps alternate between two
-             contexts on two streams (two independent problems), so that one
-             problem's copy back overlaps the next one's copy in;
+             (lwacm_get_fields_async); consecutive steps rotate over three
+             contexts on three streams (three independent problems), so that one
+             problem's copy back overlaps the next ones' copies in;
   roofline   the dominant kernel (the interior update) against the measured HBM
              copy bandwidth: 32 algorithmic bytes per node (4 FP32 fields read
              once, written once);
@@ -386,25 +386,26 @@ def run_gpu(args):
         fp32_tflops, fp32_ms = None, None
     fp32_achieved = FLOPS_PER_NODE * N / (ms_step * 1e-3) / 1e12
 
-    # end-to-end through the C ABI with pinned host buffers: two independent
-    # problems on two contexts (two streams), one step each in turn
+    # end-to-end through the C ABI with pinned host buffers: three independent
+    # problems on three contexts (three streams), one step each in turn
     e2e_steps = max(3, min(args.e2e_steps, args.steps))
-    sim2 = lw.Lwacm(lw.D3Q19, n, n, n, NU, graph_chunk=args.graph_chunk, kernel=args.kernel,
-                    stream=torch.cuda.Stream())
-    e2e_sims = [sim, sim2]
+    extra = [lw.Lwacm(lw.D3Q19, n, n, n, NU, graph_chunk=args.graph_chunk, kernel=args.kernel,
+                      stream=torch.cuda.Stream()) for _ in range(2)]
+    e2e_sims = [sim] + extra
+    ns = len(e2e_sims)
     host_in = [[torch.from_numpy(a.astype(np.float32)).pin_memory() for a in f] for _ in e2e_sims]
     host_out = [[torch.empty_like(h).pin_memory() for h in hi] for hi in host_in]
     ptr_in = [[h.data_ptr() for h in hi] for hi in host_in]
     lib = lw.load()
 
     def e2e_step(k):
-        s = e2e_sims[k % 2]
-        s._check(lib.lwacm_set_fields(s._h, *ptr_in[k % 2], lw.F32, lw.HOST))
+        s = e2e_sims[k % ns]
+        s._check(lib.lwacm_set_fields(s._h, *ptr_in[k % ns], lw.F32, lw.HOST))
         s._check(lib.lwacm_step(s._h, 1))
-        s.get_fields_async(host_out[k % 2], lw.HOST)
+        s.get_fields_async(host_out[k % ns], lw.HOST)
 
-    e2e_step(0)
-    e2e_step(1)
+    for k in range(ns):
+        e2e_step(k)
     barrier()
     torch.cuda.synchronize()
     t0 = time.perf_counter()
@@ -414,7 +415,8 @@ def run_gpu(args):
     barrier()
     e2e_units, e2e_s = aggregate_throughput(e2e_steps * N, time.perf_counter() - t0, device="cuda")
     e2e_glups = e2e_units / e2e_s / 1e9
-    sim2.close()
+    for s in extra:
+        s.close()
     field_bytes = 4 * N * 4
 
     line = {
@@ -436,7 +438,7 @@ def run_gpu(args):
                               "peak_source": "measured: FMA-chain kernel (lwacm_measure_fp32_peak)"}},
         "e2e": {"value": e2e_glups, "unit": "GLUPS", "h2d_bytes_per_step": field_bytes,
                 "d2h_bytes_per_step": field_bytes, "steps": e2e_steps,
-                "pipeline": "2 independent problems on 2 contexts/streams, one step each in turn"},
+                "pipeline": "3 independent problems on 3 contexts/streams, one step each in turn"},
         "gpu_launches": args.steps,
         "clocks": clocks,
         "check": {"mass": diag["mass"], "ke": diag["ke"], "finite": diag["finite"]},
