@@ -29,6 +29,7 @@ import os
 import statistics
 import subprocess
 import sys
+import tempfile
 import time
 
 ROOT = os.path.dirname(os.path.abspath(__file__))
@@ -69,7 +70,9 @@ class ClockSampler:
     def __init__(self, gpu_index):
         self.gpu = gpu_index
         self.proc = None
-        self.path = os.path.join(ROOT, "gpurun_out", f"clocks_bench_{os.getpid()}.csv")
+        # the raw samples go to a scratch file; the JSON line carries their summary
+        self.path = os.path.join(os.environ.get("LWACM_CLOCKS_DIR", tempfile.gettempdir()),
+                                 f"lwacm_clocks_{os.getpid()}.csv")
 
     def __enter__(self):
         try:
