@@ -4,7 +4,8 @@ Only the test-suite, ``__graft_entry__.smoke()`` and the CPU-baseline leg of
 ``bench.py`` may import this package. It is the plain, slow reference the CUDA
 library is checked against and shares no code with it. The arithmetic lives in
 ``lwacm_oracle.c`` (populations form of Eq. ACM2.0, walls of Eqs. ACM2.0cccbb2 /
-ACM2.0ccccbb, forcing of Eq. force, the BGK comparator, the Appendix-C
+ACM2.0ccccbb, forcing of Eq. force, omega_p, the passive scalar, the
+bulk-viscosity quasi-equilibrium, the BGK comparator, the Appendix-C
 finite-difference formulas and the reverse-mode adjoint); this module only
 marshals numpy arrays and adds FP64 diagnostics sums (Eq. global.quantities,
 Eq. 3Dmomenta).
@@ -66,6 +67,7 @@ def _load():
         lib.lwo_step_nu_p.argtypes = [i, i, i, i, d, d, P, P, P, P, l, P, P, P, P, i]
         lib.lwo_step_bulk.argtypes = [i, i, d, d, l, P, P, P, P, i]
         lib.lwo_feq_star.argtypes = [d, P, d, d, P]
+        lib.lwo_fqe.argtypes = [d, P, d, P]
         lib.lwo_lattice_tables.argtypes = [i, IP, P, IP]
         lib.lwo_equilibria.argtypes = [i, d, P, P, P]
         lib.lwo_bgk_init.argtypes = [i, i, i, i, P, P, P, P, P]
@@ -182,10 +184,10 @@ def step_scalar(Q, d, ux, uy, uz=None, *, T, nu, alpha, nsteps=1, nthreads=0):
 
 
 def step_bulk(d, ux, uy, tr=None, *, nu, gamma, nsteps=1, nthreads=0):
-    """D2Q9, periodic: Eq. ACM2.0 with the quasi-equilibrium f^(e*) of Eq.
-    quasi-equilibrium2 (bulk viscosity xi = 2 rho0 nu (1 + 2 gamma)); tr is the
-    normalised trace Tr^(+) of the last update (default Tr^(e) = 2/3 + |u|^2).
-    Returns (d, ux, uy, tr)."""
+    """D2Q9, periodic: Eq. ACM2.0 with the modified equilibrium f^(e*) of Eq.
+    quasi-equilibrium2 (the reading is in lwacm_oracle.c; it raises the bulk
+    viscosity by 2 rho0 nu gamma / (1 - gamma)); tr is the normalised trace Tr^(+)
+    of the last update (default Tr^(e) = 2/3 + |u|^2). Returns (d, ux, uy, tr)."""
     lib = _load()
     d, ux, uy = _f64(d), _f64(ux), _f64(uy)
     tr = 2.0 / 3.0 + ux * ux + uy * uy if tr is None else _f64(tr)
@@ -205,6 +207,18 @@ def feq_star(rho, u, tr_plus, gamma):
     rc = lib.lwo_feq_star(float(rho), _p(uu), float(tr_plus), float(gamma), _p(f))
     if rc != 0:
         raise ValueError(f"oracle feq_star failed: {rc}")
+    return f
+
+
+def fqe(rho, u, tr):
+    """The nine values of the quasi-equilibrium f^(qe)(rho, u, Tr) (Eq.
+    quasi-equilibrium, oracle link order) at one node."""
+    lib = _load()
+    f = np.zeros(9)
+    uu = np.array([u[0], u[1]], dtype=np.float64)
+    rc = lib.lwo_fqe(float(rho), _p(uu), float(tr), _p(f))
+    if rc != 0:
+        raise ValueError(f"oracle fqe failed: {rc}")
     return f
 
 

@@ -462,6 +462,14 @@ static double feq_star_o(const lwo_lattice *L, int i, double rho, const double u
     return 0.5 * (feq_star(L, i, rho, u, tr_plus, gamma) - feq_star(L, i, rho, mu, tr_plus, gamma));
 }
 
+/* f^(qe)(rho, u, Tr) of one node (Q = 9 values, Eq. quasi-equilibrium) */
+int lwo_fqe(double rho, const double *u, double tr, double *f) {
+    lwo_lattice L;
+    if (make_lattice(9, &L)) return -1;
+    for (int i = 0; i < 9; ++i) f[i] = fqe(L.c[i][0], L.c[i][1], rho, u[0], u[1], tr);
+    return 0;
+}
+
 /* f^(e*) of one node (Q = 9 values), for the tests of Eq. second-quasi-equilibrium2 */
 int lwo_feq_star(double rho, const double *u, double tr_plus, double gamma, double *f) {
     lwo_lattice L;

@@ -55,6 +55,30 @@ def test_second_moment_of_the_modified_equilibrium():
         assert np.max(np.abs(oracle.feq_star(rho, u, tre, g) - fe)) < 1e-15
 
 
+def test_quasi_equilibrium_at_tr_e_is_feq_to_third_order():
+    """Appendix "Equilibrium distribution functions": the product form at
+    Pxx = 1/3 + u^2, Pyy = 1/3 + v^2 (Eq. quasi-equilibrium at Tr = Tr^(e)) is f^(e)
+    when third-order terms are neglected: its moments up to the second equal f^(e)'s
+    exactly, and the difference shrinks as |u|^3."""
+    c = oracle.lattice(9)[0][:, :2].astype(float)
+    rng = np.random.default_rng(5)
+    direction = rng.standard_normal(2)
+    diffs = []
+    for amp in (0.04, 0.02, 0.01):
+        u = amp * direction
+        rho = 1.02
+        f = oracle.fqe(rho, u, 2.0 / 3.0 + u @ u)
+        fe, _ = oracle.equilibria(9, rho, [u[0], u[1], 0.0])
+        assert abs(f.sum() - rho) < 1e-15
+        assert np.max(np.abs(f @ c - rho * u)) < 1e-15
+        pi = np.einsum("i,ia,ib->ab", f, c, c)
+        assert np.max(np.abs(pi - rho * (np.outer(u, u) + np.eye(2) / 3.0))) < 1e-15
+        diffs.append(float(np.max(np.abs(f - fe))))
+    assert diffs[0] > 1e-8  # not f^(e) itself
+    for a, b in zip(diffs, diffs[1:]):
+        assert a / b == pytest.approx(8.0, rel=0.05)
+
+
 def _smooth_divergent(n, amp, k):
     x = np.arange(n)
     X, Y = np.meshgrid(x, x)
