@@ -66,10 +66,18 @@ __device__ __forceinline__ void tile_update(const T *__restrict__ in, T *__restr
         p.force[c] = 0.f;
         p.walled[c] = 0;
     }
-    const int x = (int)(local % dm.nx);
-    const long long r = local / dm.nx;
-    const int y = (int)(r % dm.ny);
-    const int z = (int)(r / dm.ny);
+    int x, y, z;
+    if (dm.n <= 0x7fffffffLL) {  // 32-bit index arithmetic (a 64-bit division costs several times more)
+        const unsigned i = (unsigned)local, nx = (unsigned)dm.nx, r = i / nx;
+        x = (int)(i - r * nx);
+        y = (int)(r % (unsigned)dm.ny);
+        z = (int)(r / (unsigned)dm.ny);
+    } else {
+        x = (int)(local % dm.nx);
+        const long long r = local / dm.nx;
+        y = (int)(r % dm.ny);
+        z = (int)(r / dm.ny);
+    }
     node_update<Q, false>(in + dm.off, out + dm.off, p, x, y, z);
 }
 
@@ -97,11 +105,21 @@ __device__ __forceinline__ void tile2_core(const T *__restrict__ in, T *__restri
                                            float (*G)[(TW + 2) * (TH + 2)], const Walls2 &wl = Walls2{}) {
     constexpr int W = TW + 2;
     const int tx = threadIdx.x % W, ty = threadIdx.x / W;
+    // periodic wrap of the frame (x0 + tx - 1 lies in [-1, x0 + TW], below 2 nx
+    // whenever nx > TW; smaller domains take the modulo)
     int x = x0 + tx - 1, y = y0 + ty - 1;
-    x %= nx;
-    if (x < 0) x += nx;
-    y %= ny;
-    if (y < 0) y += ny;
+    if (nx > TW) {
+        x = x < 0 ? x + nx : (x >= nx ? x - nx : x);
+    } else {
+        x %= nx;
+        if (x < 0) x += nx;
+    }
+    if (ny > TH) {
+        y = y < 0 ? y + ny : (y >= ny ? y - ny : y);
+    } else {
+        y %= ny;
+        if (y < 0) y += ny;
+    }
     const long long k = base + (long long)y * nx + x;
     const float d = ldf(in + k), u = ldf(in + fstride + k), v = ldf(in + 2 * fstride + k);
     const float rho = 1.f + d;

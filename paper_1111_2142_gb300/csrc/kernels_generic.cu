@@ -16,10 +16,18 @@ __global__ void __launch_bounds__(256) k_step_generic(const T *__restrict__ in,
                                                       T *__restrict__ out, StepParams p) {
     const long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     if (idx >= p.N) return;
-    const int x = (int)(idx % p.nx);
-    const long long r = idx / p.nx;
-    const int y = (int)(r % p.ny);
-    const int z = (int)(r / p.ny);
+    int x, y, z;
+    if (p.N <= 0x7fffffffLL) {  // 32-bit index arithmetic (a 64-bit division costs several times more)
+        const unsigned i = (unsigned)idx, nx = (unsigned)p.nx, r = i / nx;
+        x = (int)(i - r * nx);
+        y = (int)(r % (unsigned)p.ny);
+        z = (int)(r / (unsigned)p.ny);
+    } else {
+        x = (int)(idx % p.nx);
+        const long long r = idx / p.nx;
+        y = (int)(r % p.ny);
+        z = (int)(r / p.ny);
+    }
     node_update<Q, false, NUP, SC, BULK>(in, out, p, x, y, z);
 }
 
