@@ -200,9 +200,11 @@ __global__ void __launch_bounds__((TW + 2) * (TH + 2)) k_d2q9_tiles(const T *__r
                                                                    int nx, int ny, long long fstride, float s,
                                                                    float a, int tilesx, long long ntiles, Walls2 wl) {
     __shared__ float G[8][(TW + 2) * (TH + 2)];
-    for (long long t = blockIdx.x; t < ntiles; t += gridDim.x)
-        tile2_core<TW, TH, T, WALLS>(in, out, 0, nx, ny, fstride, s, a, (int)(t % tilesx) * TW,
-                                     (int)(t / tilesx) * TH, G, wl);
+    for (long long t = blockIdx.x; t < ntiles; t += gridDim.x) {
+        const unsigned tu = (unsigned)t, ty = tu / (unsigned)tilesx;  // fewer than 2^32 tiles
+        tile2_core<TW, TH, T, WALLS>(in, out, 0, nx, ny, fstride, s, a, (int)(tu - ty * (unsigned)tilesx) * TW,
+                                     (int)ty * TH, G, wl);
+    }
 }
 
 template <int TW, int TH, typename T>
