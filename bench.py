@@ -315,6 +315,64 @@ def variants(hbm):
     out["tgv_d2q9_64"] = {"value": glups(64 ** 2, 6400, ms), "unit": "GLUPS",
                           "kernel": sim.kernel_name, "l2_resident": True}
     sim.close()
+    out["next_rows"] = next_rows(hbm, glups)
+    return out
+
+
+def next_rows(hbm, glups):
+    """The variants beyond the plain scheme, each on a workload larger than L2 (HBM
+    fractions against the bytes each node moves per step), plus the Section 3.2
+    shear layer at its own 128^2 size: the 3D diagonally driven cavity (walls), the
+    forced Taylor-Green vortex (a per-node force field), omega_p, the bulk-viscosity
+    variant and the passive scalar."""
+    import torch
+    from paper_1111_2142_gb300 import inputs
+    from paper_1111_2142_gb300 import lwacm as lw
+    out = {}
+
+    def timed(name, sim, fields, steps, nodes, bpn, extra=None):
+        sim.set_fields(*fields)
+        if extra:
+            extra(sim)
+        sim.step(8)
+        ms = _events_ms(sim.stream, lambda: sim.step(steps))
+        g = glups(nodes, steps, ms)
+        out[name] = {"value": g, "unit": "GLUPS", "kernel": sim.kernel_name, "hbm_frac": bpn * g / hbm,
+                     "bytes_per_node": bpn}
+        sim.close()
+        torch.cuda.empty_cache()
+
+    n3 = 256
+    z3 = torch.zeros((n3, n3, n3), dtype=torch.float32, device="cuda")
+    lid = (2 ** 0.5 / 20, 2 ** 0.5 / 20, 0.0)
+    timed("cavity3d_d3q19_256", lw.Lwacm(lw.D3Q19, n3, n3, n3, 0.01, lw.CAVITY, lid=lid), (z3, z3, z3, z3),
+          100, n3 ** 3, 32)
+    f3 = inputs.tgv3d(n3, u0=U0)
+    t3 = torch.cos(2 * torch.pi * torch.arange(n3, device="cuda") / n3).expand(n3, n3, n3).contiguous()
+    timed("scalar_d3q19_256", lw.Lwacm(lw.D3Q19, n3, n3, n3, NU, scalar_alpha=0.01), f3, 100, n3 ** 3, 40,
+          extra=lambda s: s.set_scalar(t3))
+    del z3, t3
+    n2 = 4096
+    f2 = inputs.gtg_state(n2, 0.0)
+    gx, gy = inputs.gtg_force(n2, 0.0)
+    timed("forced_tgv_d2q9_4096", lw.Lwacm(lw.D2Q9, n2, n2, 1, inputs.GTG_NU, force_field=True), f2, 200,
+          n2 ** 2, 32, extra=lambda s: s.set_force_field(gx, gy))
+    sim = lw.Lwacm(lw.D2Q9, n2, n2, 1, 0.01)
+    sim.set_option(lw.OPT_NU_P, 0.1)
+    timed("nu_p_d2q9_4096", sim, f2, 200, n2 ** 2, 24)
+    timed("bulk_d2q9_4096", lw.Lwacm(lw.D2Q9, n2, n2, 1, 0.01, bulk_gamma=0.4), f2, 200, n2 ** 2, 32)
+    # Section 3.2 shear layer, 128^2 to t = 1 (3200 steps): plain and nu_p = 170 nu (L2-resident)
+    nu, steps = inputs.minion_brown_lattice(128)
+    fm = inputs.minion_brown(128)
+    for name, nu_p in (("shear_layer_d2q9_128", None), ("shear_layer_nu_p_d2q9_128", 170 * nu)):
+        sim = lw.Lwacm(lw.D2Q9, 128, 128, 1, nu)
+        if nu_p:
+            sim.set_option(lw.OPT_NU_P, nu_p)
+        sim.set_fields(*fm)
+        ms = _events_ms(sim.stream, lambda: sim.step(steps))
+        out[name] = {"value": glups(128 ** 2, steps, ms), "unit": "GLUPS", "kernel": sim.kernel_name,
+                     "ms_to_t1": ms, "l2_resident": True}
+        sim.close()
     return out
 
 

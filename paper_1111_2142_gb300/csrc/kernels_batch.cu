@@ -95,6 +95,15 @@ struct Walls2 {
     float lidx, lidy;  // lid velocity
 };
 
+// forcing of a single D2Q9 domain (Eq. force): rho(x,t) (g + g(x)) added to j, with a
+// constant acceleration g and an optional per-node field g(x) (two FP32 fields)
+struct Force2 {
+    int on = 0;
+    float gx = 0.f, gy = 0.f;
+    const float *field = nullptr;
+    long long fstride = 0;
+};
+
 // one TW x TH tile (plus frame) of a D2Q9 domain whose node (0,0) is at packed
 // index base; s, a: 18 nu and 1 - 6 nu of the domain. Without WALLS every axis is
 // periodic; with WALLS a link whose source lies beyond a walled face takes the
@@ -102,7 +111,8 @@ struct Walls2 {
 template <int TW, int TH, typename T, bool WALLS = false>
 __device__ __forceinline__ void tile2_core(const T *__restrict__ in, T *__restrict__ out, long long base, int nx,
                                            int ny, long long fstride, float s, float a, int x0, int y0,
-                                           float (*G)[(TW + 2) * (TH + 2)], const Walls2 &wl = Walls2{}) {
+                                           float (*G)[(TW + 2) * (TH + 2)], const Walls2 &wl = Walls2{},
+                                           const Force2 &fc = Force2{}) {
     constexpr int W = TW + 2;
     const int tx = threadIdx.x % W, ty = threadIdx.x / W;
     // periodic wrap of the frame (x0 + tx - 1 lies in [-1, x0 + TW], below 2 nx
@@ -176,8 +186,17 @@ __device__ __forceinline__ void tile2_core(const T *__restrict__ in, T *__restri
         }
         const float dd = fmaf(4.f / 9.f, K, ((g1 + g2) + (g3 + g4)) + ((g5 + g6) + (g7 + g8)));
         const float ar = a * rho;
-        const float jx = fmaf(ar, u, (g1 - g2) + ((g5 - g6) + (g7 - g8)));
-        const float jy = fmaf(ar, v, (g3 - g4) + ((g5 - g6) - (g7 - g8)));
+        float jx = fmaf(ar, u, (g1 - g2) + ((g5 - g6) + (g7 - g8)));
+        float jy = fmaf(ar, v, (g3 - g4) + ((g5 - g6) - (g7 - g8)));
+        if (fc.on) {  // Eq. force: the odd part of f^(e)(rho(x,t), g) adds rho g to j
+            jx = fmaf(rho, fc.gx, jx);
+            jy = fmaf(rho, fc.gy, jy);
+            if (fc.field) {
+                const long long kf = (long long)yi * nx + xi;
+                jx = fmaf(rho, __ldg(fc.field + kf), jx);
+                jy = fmaf(rho, __ldg(fc.field + fc.fstride + kf), jy);
+            }
+        }
         const float rn = 1.f + dd;
         stf(out + k, dd);
         stf(out + fstride + k, jx / rn);
@@ -198,12 +217,13 @@ __device__ __forceinline__ void tile2_update(const T *__restrict__ in, T *__rest
 template <int TW, int TH, typename T, bool WALLS>
 __global__ void __launch_bounds__((TW + 2) * (TH + 2)) k_d2q9_tiles(const T *__restrict__ in, T *__restrict__ out,
                                                                    int nx, int ny, long long fstride, float s,
-                                                                   float a, int tilesx, long long ntiles, Walls2 wl) {
+                                                                   float a, int tilesx, long long ntiles, Walls2 wl,
+                                                                   Force2 fc) {
     __shared__ float G[8][(TW + 2) * (TH + 2)];
     for (long long t = blockIdx.x; t < ntiles; t += gridDim.x) {
         const unsigned tu = (unsigned)t, ty = tu / (unsigned)tilesx;  // fewer than 2^32 tiles
         tile2_core<TW, TH, T, WALLS>(in, out, 0, nx, ny, fstride, s, a, (int)(tu - ty * (unsigned)tilesx) * TW,
-                                     (int)ty * TH, G, wl);
+                                     (int)ty * TH, G, wl, fc);
     }
 }
 
@@ -351,8 +371,14 @@ cudaError_t single_w(const void *in, void *out, const StepParams &p, const Walls
     const int tilesx = (p.nx + TW - 1) / TW;
     const long long ntiles = (long long)tilesx * ((p.ny + TH - 1) / TH);
     const long long grid = ntiles < 4LL * g ? ntiles : 4LL * g;
+    Force2 fc;
+    fc.on = p.has_force || p.gfield;
+    fc.gx = p.has_force ? p.force[0] : 0.f;
+    fc.gy = p.has_force ? p.force[1] : 0.f;
+    fc.field = p.gfield;
+    fc.fstride = p.fstride;
     k_d2q9_tiles<TW, TH, T, WALLS><<<(unsigned)grid, NT, 0, st>>>((const T *)in, (T *)out, p.nx, p.ny, p.fstride,
-                                                                 p.s, p.a, tilesx, ntiles, wl);
+                                                                 p.s, p.a, tilesx, ntiles, wl, fc);
     return cudaGetLastError();
 }
 
@@ -423,7 +449,7 @@ bool batch_shape_supported(int Q, int storage, int k) {
 }
 
 bool tiles2d_supported(int Q, int storage, const StepParams &p) {
-    return Q == 9 && p.nz == 1 && !p.has_force && !p.gfield && p.sdelta == 0.f && !p.scalar && !p.bulk &&
+    return Q == 9 && p.nz == 1 && p.sdelta == 0.f && !p.scalar && !p.bulk &&
            (storage == STORE_F32 || storage == STORE_BF16 || storage == STORE_F16);
 }
 

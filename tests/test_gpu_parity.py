@@ -159,12 +159,13 @@ def test_cavity_3d(lw, shape):
     assert eu < 1e-5 and ed < 1e-4
 
 
+@pytest.mark.parametrize("kernel", KERNELS)
 @pytest.mark.parametrize("Q,shape", [(9, (12, 20)), (19, (6, 12, 10))])
-def test_channel_force(lw, Q, shape):
+def test_channel_force(lw, Q, shape, kernel):
     g = (1e-5, 0.0, 0.0)
     f = inputs.smooth_random(shape, seed=7, u_amp=0.01, d_amp=0.002)
     got, _ = run_gpu(lw, Q, f, 0.05, 200, bc=lw.CHANNEL, force=g[: (2 if Q == 9 else 3)],
-                     lid=(0.01, 0.0, 0.0)[: (2 if Q == 9 else 3)])
+                     lid=(0.01, 0.0, 0.0)[: (2 if Q == 9 else 3)], kernel=kernel)
     ref = oracle.step(Q, *f, nu=0.05, bc=oracle.CHANNEL, force=g, lid=(0.01, 0, 0), nsteps=200)
     eu, ed = errs(got, ref, 0.01)
     print(f"channel Q{Q} {shape}: du/U={eu:.2e} dd/d={ed:.2e}")
