@@ -11,12 +11,26 @@
 
 namespace lwacm {
 
+// Blocks of 32 x 8 nodes in an x-y plane when plane_blocks(p) (blockIdx = (x tile,
+// y tile, z)), so that the y-neighbours of a block are mostly its own rows; else
+// runs of 256 consecutive nodes.
+__host__ __device__ inline bool plane_blocks(const StepParams &p) {
+    return p.nx >= 32 && p.ny <= 8 * 65535 && p.nz <= 65535;
+}
 template <int Q, typename T, bool NUP, bool SC, bool BULK = false>
 __global__ void __launch_bounds__(256) k_step_generic(const T *__restrict__ in,
                                                       T *__restrict__ out, StepParams p) {
+    int x, y, z;
+    if (plane_blocks(p)) {
+        x = (int)(blockIdx.x * 32 + (threadIdx.x & 31));
+        y = (int)(blockIdx.y * 8 + (threadIdx.x >> 5));
+        z = (int)blockIdx.z;
+        if (x >= p.nx || y >= p.ny) return;
+        node_update<Q, false, NUP, SC, BULK>(in, out, p, x, y, z);
+        return;
+    }
     const long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     if (idx >= p.N) return;
-    int x, y, z;
     if (p.N <= 0x7fffffffLL) {  // 32-bit index arithmetic (a 64-bit division costs several times more)
         const unsigned i = (unsigned)idx, nx = (unsigned)p.nx, r = i / nx;
         x = (int)(i - r * nx);
@@ -193,7 +207,9 @@ static inline unsigned blocks_for(long long n, int tpb) { return (unsigned)((n +
 template <typename T>
 cudaError_t launch_step_generic_t(int Q, const void *in, void *out, const StepParams &p,
                                   cudaStream_t st) {
-    const unsigned nb = blocks_for(p.N, 256);
+    const dim3 nb = plane_blocks(p)
+                        ? dim3((unsigned)((p.nx + 31) / 32), (unsigned)((p.ny + 7) / 8), (unsigned)p.nz)
+                        : dim3(blocks_for(p.N, 256));
     const int v = (p.sdelta != 0.f ? 1 : 0) + (p.scalar ? 2 : 0) + (p.bulk ? 4 : 0);
     const T *i0 = (const T *)in;
     T *o0 = (T *)out;
