@@ -22,9 +22,11 @@ __global__ void __launch_bounds__(256) k_step_generic(const T *__restrict__ in,
                                                       T *__restrict__ out, StepParams p) {
     int x, y, z;
     if (plane_blocks(p)) {
+        constexpr int BY = 8, BZ = 1;  // 32 x BY x BZ nodes per block (32 x 4 x 2 measured no faster in 3D)
         x = (int)(blockIdx.x * 32 + (threadIdx.x & 31));
-        y = (int)(blockIdx.y * 8 + (threadIdx.x >> 5));
-        z = (int)blockIdx.z;
+        y = (int)(blockIdx.y * BY + ((threadIdx.x >> 5) % BY));
+        z = (int)(blockIdx.z * BZ + (threadIdx.x >> 5) / BY);
+        if (z >= p.nz) return;
         if (x >= p.nx || y >= p.ny) return;
         node_update<Q, false, NUP, SC, BULK>(in, out, p, x, y, z);
         return;
@@ -207,9 +209,10 @@ static inline unsigned blocks_for(long long n, int tpb) { return (unsigned)((n +
 template <typename T>
 cudaError_t launch_step_generic_t(int Q, const void *in, void *out, const StepParams &p,
                                   cudaStream_t st) {
-    const dim3 nb = plane_blocks(p)
-                        ? dim3((unsigned)((p.nx + 31) / 32), (unsigned)((p.ny + 7) / 8), (unsigned)p.nz)
-                        : dim3(blocks_for(p.N, 256));
+    const int by = 8, bz = 1;
+    const dim3 nb = plane_blocks(p) ? dim3((unsigned)((p.nx + 31) / 32), (unsigned)((p.ny + by - 1) / by),
+                                           (unsigned)((p.nz + bz - 1) / bz))
+                                    : dim3(blocks_for(p.N, 256));
     const int v = (p.sdelta != 0.f ? 1 : 0) + (p.scalar ? 2 : 0) + (p.bulk ? 4 : 0);
     const T *i0 = (const T *)in;
     T *o0 = (T *)out;
