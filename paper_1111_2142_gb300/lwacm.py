@@ -189,8 +189,15 @@ class Lwacm:
 
     def close(self):
         if getattr(self, "_h", None):
+            # work still enqueued on the stream may read the workspace or write the
+            # destinations of enqueue-only read-backs: let it finish first
+            try:
+                self.stream.synchronize()
+            except Exception:
+                pass
             self._lib.lwacm_destroy(self._h)
             self._h = None
+            self._pending = []
 
     def __del__(self):
         try:
@@ -297,6 +304,7 @@ class Lwacm:
 
     def sync(self):
         self._check(self._lib.lwacm_sync(self._h))
+        self._pending = []  # the enqueued read-backs have landed
 
     def step_count(self):
         v = ctypes.c_longlong()
@@ -335,6 +343,8 @@ class Lwacm:
             code = F64 if first.dtype == torch.float64 else F32
         ptrs = [_ptr(o) for o in outs] + [None] * (4 - len(outs))
         self._check(self._lib.lwacm_get_fields_async(self._h, *ptrs, code, where))
+        # the destinations must outlive the copies: held until sync() or close()
+        self._pending = getattr(self, "_pending", []) + [list(outs)]
 
     def fields(self):
         """Zero-copy torch views of the current state (storage dtype)."""
