@@ -94,9 +94,10 @@ enum {
                               forcing, nx in {128, 256} and ny % 8 == 0; 2 and 3 need FP32
                               storage, 5 takes FP32, BF16 and FP16: LWACM_E_UNSUPPORTED
                               otherwise); 6 = D2Q9 2D-tile kernel (any boundary, walls
-                              applied in the kernel, no forcing; tile shape from LWACM_OPT_BATCH_TILE, 30x14 when
-                              0). The automatic choice takes 5, else 3, else 2, else 6,
-                              else 1. */
+                              and forcing applied in the kernel, not with omega_p, the
+                              scalar or the bulk-viscosity variant; tile shape from
+                              LWACM_OPT_BATCH_TILE, 30x14 when 0). The automatic choice
+                              takes 5, else 3, else 2, else 6, else 1. */
     LWACM_OPT_BATCH_MODE = 10, /* batched contexts: 0 = one launch per step, replayed
                                   from CUDA graphs (default); 1 = one persistent
                                   cooperative launch per lwacm_step call, with a
@@ -206,9 +207,9 @@ lwacm_status lwacm_set_fields(lwacm_ctx *ctx, const void *d, const void *ux, con
  * the next call. The step adds rho(x,t) g(x) to the momentum, on top of any
  * constant LWACM_OPT_FORCE_* vector. All three pointers NULL switches the field
  * off. Stream-ordered on the bound stream (host buffers must stay valid until
- * the stream reaches this point; FP32 host arrays should be pinned). The row-tiled
- * kernels have no forcing term, so a context with forcing runs the generic
- * kernel. The adjoint (lwacm_forward_record) refuses a context whose field is on
+ * the stream reaches this point; FP32 host arrays should be pinned). The D3Q19
+ * row-tiled kernels have no forcing term, so a D3Q19 context with forcing runs
+ * the generic kernel; D2Q9 runs the 2D-tile kernel, which adds it. The adjoint (lwacm_forward_record) refuses a context whose field is on
  * (LWACM_E_UNSUPPORTED).
  * Errors: LWACM_E_STATE (nothing reserved, or not bound), LWACM_E_ARG. */
 lwacm_status lwacm_set_force_field(lwacm_ctx *ctx, const void *gx, const void *gy, const void *gz,
