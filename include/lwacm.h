@@ -147,9 +147,10 @@ enum {
                                      nu gamma k^2 / (1 - gamma) (bulk viscosity raised by
                                      2 rho0 nu gamma / (1 - gamma)); shear waves are
                                      unchanged. Before lwacm_bind (one more field);
-                                     periodic D2Q9 domains only, neither with the scalar
-                                     nor with LWACM_OPT_NU_P (LWACM_E_UNSUPPORTED); runs
-                                     on the generic kernel. */
+                                     periodic D2Q9 domains only, not with the scalar
+                                     (LWACM_E_UNSUPPORTED). With LWACM_OPT_NU_P the density
+                                     is relaxed with omega_p and the momentum and the
+                                     trace with omega. Runs on the generic kernel. */
 };
 
 /* Create a single-domain context.

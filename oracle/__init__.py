@@ -65,7 +65,7 @@ def _load():
         lib.lwo_step_force_field.argtypes = [i, i, i, i, d, i, d, P, P, P, P, l, P, P, P, P, i]
         lib.lwo_step_scalar.argtypes = [i, i, i, i, d, d, l, P, P, P, P, P, i]
         lib.lwo_step_nu_p.argtypes = [i, i, i, i, d, d, P, P, P, P, l, P, P, P, P, i]
-        lib.lwo_step_bulk.argtypes = [i, i, d, d, l, P, P, P, P, i]
+        lib.lwo_step_bulk.argtypes = [i, i, d, d, d, l, P, P, P, P, i]
         lib.lwo_feq_star.argtypes = [d, P, d, d, P]
         lib.lwo_fqe.argtypes = [d, P, d, P]
         lib.lwo_lattice_tables.argtypes = [i, IP, P, IP]
@@ -183,16 +183,17 @@ def step_scalar(Q, d, ux, uy, uz=None, *, T, nu, alpha, nsteps=1, nthreads=0):
     return (d, ux, uy, T) if Q == 9 else (d, ux, uy, uz, T)
 
 
-def step_bulk(d, ux, uy, tr=None, *, nu, gamma, nsteps=1, nthreads=0):
+def step_bulk(d, ux, uy, tr=None, *, nu, gamma, nu_p=None, nsteps=1, nthreads=0):
     """D2Q9, periodic: Eq. ACM2.0 with the modified equilibrium f^(e*) of Eq.
     quasi-equilibrium2 (the reading is in lwacm_oracle.c; it raises the bulk
     viscosity by 2 rho0 nu gamma / (1 - gamma)); tr is the normalised trace Tr^(+)
-    of the last update (default Tr^(e) = 2/3 + |u|^2). Returns (d, ux, uy, tr)."""
+    of the last update (default Tr^(e) = 2/3 + |u|^2); nu_p: with omega_p as well
+    (the density relaxed with nu_p). Returns (d, ux, uy, tr)."""
     lib = _load()
     d, ux, uy = _f64(d), _f64(ux), _f64(uy)
     tr = 2.0 / 3.0 + ux * ux + uy * uy if tr is None else _f64(tr)
     ny, nx = d.shape[-2], d.shape[-1]
-    rc = lib.lwo_step_bulk(nx, ny, float(nu), float(gamma), int(nsteps), _p(d), _p(ux), _p(uy), _p(tr),
+    rc = lib.lwo_step_bulk(nx, ny, float(nu), float(nu_p or 0.0), float(gamma), int(nsteps), _p(d), _p(ux), _p(uy), _p(tr),
                            int(nthreads))
     if rc != 0:
         raise ValueError(f"oracle bulk step failed: {rc}")

@@ -481,9 +481,14 @@ int lwo_feq_star(double rho, const double *u, double tr_plus, double gamma, doub
 
 /* Advance (d, u, Tr) of a periodic D2Q9 domain by Eq. ACM2.0 with f^(e*) in place
  * of f^(e), nsteps times. Tr holds Tr^(+) of the last update (the caller starts it
- * at Tr^(e) = 2/3 + |u|^2, which makes the first step the standard one). */
-int lwo_step_bulk(int nx, int ny, double nu, double gamma, long nsteps, double *d, double *ux, double *uy,
-                  double *tr, int nthreads) {
+ * at Tr^(e) = 2/3 + |u|^2, which makes the first step the standard one). nu_p > 0:
+ * with omega_p as well (Section 2.2 item 3; both together are the runs of Fig.
+ * minion2): the density sums populations built with a_p, the momentum and the
+ * trace those built with a; u is over the new density, Tr^(+) over the zeroth
+ * moment of the populations it is the trace of (the updated distribution, built
+ * with a), which is the new density when nu_p = nu. */
+int lwo_step_bulk(int nx, int ny, double nu, double nu_p, double gamma, long nsteps, double *d, double *ux,
+                  double *uy, double *tr, int nthreads) {
     lwo_lattice L;
     lwo_geom G;
     if (make_lattice(9, &L)) return -1;
@@ -491,8 +496,11 @@ int lwo_step_bulk(int nx, int ny, double nu, double gamma, long nsteps, double *
     if (!(nu > 0.0) || nu > 1.0 / 6.0) return -3;
     if (!tr) return -4;
     const long N = (long)nx * ny;
+    if (nu_p < 0.0 || nu_p > 1.0 / 6.0) return -3;
     const double omega = omega_of_nu(nu);
     const double a = 2.0 * (omega - 1.0) / omega;
+    const double omega_p = nu_p > 0.0 ? omega_of_nu(nu_p) : omega;
+    const double ap = 2.0 * (omega_p - 1.0) / omega_p;
     double *buf = (double *)malloc(sizeof(double) * 4 * N);
     if (!buf) return -6;
     double *dn = buf, *un = buf + N, *vn = buf + 2 * N, *tn = buf + 3 * N;
@@ -505,16 +513,17 @@ int lwo_step_bulk(int nx, int ny, double nu, double gamma, long nsteps, double *
                 const long k = (long)y * nx + xx;
                 const double rk = 1.0 + d[k];
                 const double uk[3] = {ux[k], uy[k], 0.0};
-                double m0 = 0.0, m1 = 0.0, m2 = 0.0, m3 = 0.0;
+                double m0 = 0.0, m1 = 0.0, m2 = 0.0, m3 = 0.0, m0a = 0.0;
                 for (int i = 0; i < 9; ++i) {
                     int above;
                     const long s = source_of(&G, x, L.c[i], &above);
                     const double rs = 1.0 + d[s];
                     const double us[3] = {ux[s], uy[s], 0.0};
-                    const double fi = feq_star(&L, i, rs, us, tr[s], gamma) +
-                                      a * (feq_star_o(&L, i, rk, uk, tr[k], gamma) -
-                                           feq_star_o(&L, i, rs, us, tr[s], gamma));
-                    m0 += fi;
+                    const double fe = feq_star(&L, i, rs, us, tr[s], gamma);
+                    const double fo = feq_star_o(&L, i, rk, uk, tr[k], gamma) - feq_star_o(&L, i, rs, us, tr[s], gamma);
+                    const double fi = fe + a * fo;
+                    m0 += fe + ap * fo;
+                    m0a += fi;
                     m1 += L.c[i][0] * fi;
                     m2 += L.c[i][1] * fi;
                     m3 += (L.c[i][0] * L.c[i][0] + L.c[i][1] * L.c[i][1]) * fi;
@@ -522,7 +531,7 @@ int lwo_step_bulk(int nx, int ny, double nu, double gamma, long nsteps, double *
                 dn[k] = m0 - 1.0;
                 un[k] = m1 / m0;
                 vn[k] = m2 / m0;
-                tn[k] = m3 / m0;
+                tn[k] = m3 / m0a;
             }
         memcpy(d, dn, sizeof(double) * N);
         memcpy(ux, un, sizeof(double) * N);

@@ -223,7 +223,8 @@ cudaError_t launch_step_generic_t(int Q, const void *in, void *out, const StepPa
             case 2: k_step_generic<9, T, false, true><<<nb, 256, 0, st>>>(i0, o0, p); break;
             case 3: k_step_generic<9, T, true, true><<<nb, 256, 0, st>>>(i0, o0, p); break;
             case 4: k_step_generic<9, T, false, false, true><<<nb, 256, 0, st>>>(i0, o0, p); break;
-            default: return cudaErrorInvalidValue;  // the trace goes with neither omega_p nor the scalar
+            case 5: k_step_generic<9, T, true, false, true><<<nb, 256, 0, st>>>(i0, o0, p); break;
+            default: return cudaErrorInvalidValue;  // the scalar and the trace share one field
         }
     } else {
         switch (v) {

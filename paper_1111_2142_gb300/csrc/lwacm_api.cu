@@ -627,7 +627,6 @@ lwacm_status lwacm_set_option(lwacm_ctx *c, int key, double v) {
             if (v != 0 && (c->Q != 9 || c->bc != LWACM_BC_PERIODIC))
                 return fail(c, LWACM_E_UNSUPPORTED, "the bulk-viscosity variant is for periodic D2Q9 domains");
             if (v != 0 && c->alpha != 0) return fail(c, LWACM_E_UNSUPPORTED, "not with the passive scalar");
-            if (v != 0 && c->nu_p > 0) return fail(c, LWACM_E_UNSUPPORTED, "not with omega_p");
             c->gamma = v;
             c->bulk = v != 0;
             c->nsc = c->bulk ? 1 : 0;
@@ -640,7 +639,6 @@ lwacm_status lwacm_set_option(lwacm_ctx *c, int key, double v) {
                 return fail(c, LWACM_E_RANGE, "nu_p must be in (0, 1/6] (or 0: same as nu)");
             if (v != 0 && c->bc != LWACM_BC_PERIODIC)
                 return fail(c, LWACM_E_UNSUPPORTED, "omega_p is for periodic domains");
-            if (v != 0 && c->bulk) return fail(c, LWACM_E_UNSUPPORTED, "not with the bulk-viscosity variant");
             c->nu_p = v;
             break;
         }

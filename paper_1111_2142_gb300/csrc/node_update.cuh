@@ -26,7 +26,10 @@ namespace lwacm {
 // y), Pxx = 1/3 + u^2, Pyy = 1/3 + v^2; it is pre-combined like f^(e), Df - a Df^o,
 // with its odd part Df^o = rho h (ax c_y v/2 + ay c_x u/2). The post-combine term
 // adds nothing to the trace and sum_i (|c_i|^2 - 2/3) w_i = 0, so
-// Tr^(+) - Tr^(e) = sum_i (|c_i|^2 - 2/3) g_i / rho+ - |u+|^2.
+// Tr^(+) - Tr^(e) = sum_i (|c_i|^2 - 2/3) g_i / rho_a - |u+|^2, rho_a the zeroth
+// moment of the updated distribution (the new density unless NUP). With NUP as
+// well the density pre-combines the increment with a_p: (a - a_p) sum_i Df^o_i =
+// (sdelta/3) sum_i Df^o_i more; the momentum and the trace keep a.
 template <int Q, bool WALLS, bool NUP = false, bool SC = false, bool BULK = false, typename T>
 __device__ __forceinline__ void node_update(const T *__restrict__ in, T *__restrict__ out,
                                             const StepParams &p, int x, int y, int z) {
@@ -38,7 +41,7 @@ __device__ __forceinline__ void node_update(const T *__restrict__ in, T *__restr
     const float uz = (Q == 19) ? ldf(Win + k) : 0.f;
     const float rx = 1.f + dx;
     const float qx = fmaf(ux, ux, fmaf(uy, uy, uz * uz));
-    float dd = 0.f, jx = 0.f, jy = 0.f, jz = 0.f, dsp = 0.f, ts = 0.f, trs = 0.f;
+    float dd = 0.f, jx = 0.f, jy = 0.f, jz = 0.f, dsp = 0.f, ts = 0.f, trs = 0.f, dfos = 0.f;
     const T *Tin = in + (Q == 19 ? 4 : 3) * p.fstride;
     const float omt = 1.f - p.at;
 #pragma unroll
@@ -81,6 +84,7 @@ __device__ __forceinline__ void node_update(const T *__restrict__ in, T *__restr
                 const float df = rs * h * fmaf(ax * ay, h, fmaf(ax, B, ay * A));
                 const float dfo = rs * h * (0.5f * fmaf(ax * cy, vs, ay * cx * us));
                 g += fmaf(-p.a, dfo, df);
+                if (NUP) dfos += dfo;
             }
         } else {
             // Eq. ACM2.0cccbb2 + Eq. ACM2.0ccccbb: own outgoing BB(i) value, reflected
@@ -97,7 +101,9 @@ __device__ __forceinline__ void node_update(const T *__restrict__ in, T *__restr
         if (cy) jy += cy > 0 ? g : -g;
         if (cz) jz += cz > 0 ? g : -g;
     }
+    const float rna = 1.f + dd;  // zeroth moment of the distribution built with a
     if (NUP) dd = fmaf(p.sdelta, dsp, dd);
+    if (NUP && BULK) dd = fmaf(p.sdelta * (1.f / 3.f), dfos, dd);
     jx = fmaf(p.a * rx, ux, jx);
     jy = fmaf(p.a * rx, uy, jy);
     jz = fmaf(p.a * rx, uz, jz);
@@ -118,7 +124,7 @@ __device__ __forceinline__ void node_update(const T *__restrict__ in, T *__restr
     stf(out + 2 * p.fstride + k, uyn);
     if (Q == 19) stf(out + 3 * p.fstride + k, jz / rn);
     if (SC) stf(out + (Q == 19 ? 4 : 3) * p.fstride + k, fmaf(p.at, ldf(Tin + k), ts));
-    if (BULK) stf(out + 3 * p.fstride + k, trs / rn - fmaf(uxn, uxn, uyn * uyn));
+    if (BULK) stf(out + 3 * p.fstride + k, trs / rna - fmaf(uxn, uxn, uyn * uyn));
 }
 
 }  // namespace lwacm

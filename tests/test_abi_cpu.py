@@ -216,7 +216,7 @@ def test_scalar_option(lib):
 
 def test_bulk_gamma_option(lib):
     """LWACM_OPT_BULK_GAMMA: range, one more field, periodic D2Q9 only, exclusive
-    with the scalar and with omega_p, before bind; lwacm_get_trace needs it."""
+    with the scalar (not with omega_p), before bind; lwacm_get_trace needs it."""
     from paper_1111_2142_gb300 import lwacm as lw
     st, h = _create(lib, 9, 16, 12, 1, 0.02, 0)
     n0 = ctypes.c_size_t()
@@ -229,7 +229,8 @@ def test_bulk_gamma_option(lib):
     assert lib.lwacm_workspace_bytes(h, ctypes.byref(n1)) == lw.OK
     assert n1.value >= n0.value + 2 * 16 * 12 * 4  # the trace field in each buffer
     assert lib.lwacm_set_option(h, lw.OPT_SCALAR_ALPHA, 0.05) == lw.E_UNSUPPORTED
-    assert lib.lwacm_set_option(h, lw.OPT_NU_P, 0.1) == lw.E_UNSUPPORTED
+    assert lib.lwacm_set_option(h, lw.OPT_NU_P, 0.1) == lw.OK  # both improvements of Section 3.2
+    assert lib.lwacm_set_option(h, lw.OPT_NU_P, 0.0) == lw.OK
     assert lib.lwacm_set_option(h, lw.OPT_BULK_GAMMA, 0.0) == lw.OK  # off again
     n2 = ctypes.c_size_t()
     assert lib.lwacm_workspace_bytes(h, ctypes.byref(n2)) == lw.OK and n2.value == n0.value

@@ -23,9 +23,11 @@ def lw():
     return lwacm
 
 
-def _run(lw, fields, nu, gamma, steps):
+def _run(lw, fields, nu, gamma, steps, nu_p=None):
     ny, nx = fields[0].shape
     sim = lw.Lwacm(9, nx, ny, 1, nu, bulk_gamma=gamma)
+    if nu_p:
+        sim.set_option(lw.OPT_NU_P, nu_p)
     assert sim.kernel_name.startswith("generic")
     sim.set_fields(*fields)
     tr0 = sim.get_trace()
@@ -53,6 +55,19 @@ def test_bulk_matches_oracle(lw, gamma, shape):
     # gamma acts: the plain scheme differs by far more than the tolerance
     plain = oracle.step(9, *f, nu=0.02, nsteps=200)
     assert max(float(np.max(np.abs(a - b))) for a, b in zip(plain[1:], ref[1:3])) / u_scale > 1e-3
+
+
+def test_bulk_with_omega_p_matches_oracle(lw):
+    """Both improvements of Section 3.2 (omega_p and gamma) on one context."""
+    f = inputs.smooth_random((40, 48), seed=33, u_amp=0.05, d_amp=0.01)
+    got, tr, _ = _run(lw, f, 0.02, 0.4, 200, nu_p=0.1)
+    ref = oracle.step_bulk(*f, nu=0.02, nu_p=0.1, gamma=0.4, nsteps=200)
+    eu = max(float(np.max(np.abs(g - r))) for g, r in zip(got[1:], ref[1:3])) / 0.05
+    ed = float(np.max(np.abs(got[0] - ref[0]))) / max(float(np.max(np.abs(ref[0]))), 3 * 0.05 ** 2)
+    dev = ref[3] - (2.0 / 3.0 + ref[1] ** 2 + ref[2] ** 2)
+    et = float(np.max(np.abs(tr - dev))) / float(np.max(np.abs(dev)))
+    print(f"bulk + nu_p: du/U={eu:.2e} dd/d={ed:.2e} dTr/Tr_scale={et:.2e}")
+    assert eu < 1e-5 and ed < 1e-4 and et < 1e-3
 
 
 def test_longitudinal_wave_matches_oracle(lw):

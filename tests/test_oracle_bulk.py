@@ -36,6 +36,22 @@ def test_gamma_zero_is_the_standard_step():
     assert max(float(np.max(np.abs(x - y))) for x, y in zip(a, c[:3])) > 1e-5  # gamma acts
 
 
+def test_with_omega_p_reduces_to_each_variant():
+    """Both improvements of Section 3.2 together (omega_p for the density, the
+    modified equilibrium everywhere): gamma = 0 is the omega_p step and nu_p = nu
+    the bulk-viscosity step, to rounding; with both on, the result differs from each."""
+    f = inputs.smooth_random((24, 20), seed=3)
+    a = oracle.step_nu_p(9, *f, nu=0.02, nu_p=0.1, nsteps=20)
+    b = oracle.step_bulk(*f, nu=0.02, nu_p=0.1, gamma=0.0, nsteps=20)
+    assert max(float(np.max(np.abs(x - y))) for x, y in zip(a, b[:3])) < 1e-14
+    c = oracle.step_bulk(*f, nu=0.02, gamma=0.4, nsteps=20)
+    e = oracle.step_bulk(*f, nu=0.02, nu_p=0.02, gamma=0.4, nsteps=20)
+    assert max(float(np.max(np.abs(x - y))) for x, y in zip(c, e)) < 1e-14
+    g = oracle.step_bulk(*f, nu=0.02, nu_p=0.1, gamma=0.4, nsteps=20)
+    assert max(float(np.max(np.abs(x - y))) for x, y in zip(c[:3], g[:3])) > 1e-4
+    assert max(float(np.max(np.abs(x - y))) for x, y in zip(a, g[:3])) > 1e-5
+
+
 def test_second_moment_of_the_modified_equilibrium():
     c = oracle.lattice(9)[0][:, :2].astype(float)
     rng = np.random.default_rng(0)

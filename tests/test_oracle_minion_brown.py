@@ -34,6 +34,18 @@ def runs():
     return nu, steps, plain, with_nu_p
 
 
+def test_both_improvements_stable():
+    """Fig. minion2's run: nu_p = 170 nu and gamma = 0.4 together stay stable to
+    t = 1 and keep the divergence below the plain scheme's."""
+    nu, steps = inputs.minion_brown_lattice(N, U)
+    f = inputs.minion_brown(N, U)
+    both = oracle.step_bulk(*f, nu=nu, nu_p=170.0 * nu, gamma=0.4, nsteps=steps)
+    plain = oracle.step(9, *f, nu=nu, nsteps=steps)
+    assert all(np.all(np.isfinite(a)) for a in both)
+    assert max(np.max(np.abs(both[1])), np.max(np.abs(both[2]))) < 2.0 * U
+    assert np.mean(np.abs(divergence(both[1], both[2]))) < np.mean(np.abs(divergence(plain[1], plain[2]))) / 3.0
+
+
 def test_lattice_parameters():
     nu, steps = inputs.minion_brown_lattice(N, U)
     assert steps == 3200
