@@ -364,8 +364,9 @@ def next_rows(hbm, glups):
     # Section 3.2 shear layer, 128^2 to t = 1 (3200 steps): plain and nu_p = 170 nu (L2-resident)
     nu, steps = inputs.minion_brown_lattice(128)
     fm = inputs.minion_brown(128)
-    for name, nu_p in (("shear_layer_d2q9_128", None), ("shear_layer_nu_p_d2q9_128", 170 * nu)):
-        sim = lw.Lwacm(lw.D2Q9, 128, 128, 1, nu)
+    for name, nu_p, gamma in (("shear_layer_d2q9_128", None, None), ("shear_layer_nu_p_d2q9_128", 170 * nu, None),
+                              ("shear_layer_nu_p_bulk_d2q9_128", 170 * nu, 0.4)):
+        sim = lw.Lwacm(lw.D2Q9, 128, 128, 1, nu, bulk_gamma=gamma)
         if nu_p:
             sim.set_option(lw.OPT_NU_P, nu_p)
         sim.set_fields(*fm)

@@ -34,22 +34,28 @@ def runs(lw):
     nu, steps = inputs.minion_brown_lattice(N, U)
     f = inputs.minion_brown(N, U)
     out = {}
-    for name, nu_p in (("plain", None), ("nu_p", 170.0 * nu)):
-        sim = lw.Lwacm(9, N, N, 1, nu)
+    for name, nu_p, gamma in (("plain", None, None), ("nu_p", 170.0 * nu, None), ("both", 170.0 * nu, 0.4)):
+        sim = lw.Lwacm(9, N, N, 1, nu, bulk_gamma=gamma)
         if nu_p is not None:
             sim.set_option(lw.OPT_NU_P, nu_p)
         sim.set_fields(*f)
         sim.step(steps)
         got = [a.reshape(N, N) for a in sim.get_fields()]
         sim.close()
-        ref = (oracle.step(9, *f, nu=nu, nsteps=steps) if nu_p is None
-               else oracle.step_nu_p(9, *f, nu=nu, nu_p=nu_p, nsteps=steps))
+        if gamma is not None:
+            ref = oracle.step_bulk(*f, nu=nu, nu_p=nu_p, gamma=gamma, nsteps=steps)[:3]
+        elif nu_p is None:
+            ref = oracle.step(9, *f, nu=nu, nsteps=steps)
+        else:
+            ref = oracle.step_nu_p(9, *f, nu=nu, nu_p=nu_p, nsteps=steps)
         out[name] = (got, ref)
     return out
 
 
-@pytest.mark.parametrize("name", ["plain", "nu_p"])
+@pytest.mark.parametrize("name", ["plain", "nu_p", "both"])
 def test_matches_oracle_at_t1(runs, name):
+    """Each run against the oracle; both improvements together (Fig. minion2:
+    nu_p = 170 nu and the bulk-viscosity variant with gamma = 0.4) included."""
     got, ref = runs[name]
     eu = max(float(np.max(np.abs(g - r))) for g, r in zip(got[1:], ref[1:])) / U
     print(f"shear layer {name}: max|du|/U = {eu:.2e}")
