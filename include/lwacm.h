@@ -90,8 +90,9 @@ enum {
     LWACM_OPT_KERNEL = 9,  /* interior kernel: 0 = automatic choice (default),
                               1 = generic gather kernel, 2 = D3Q19 TMA row-tiled kernel,
                               3 = D3Q19 register-prefetch z-march kernel, 5 = D3Q19 half-row
-                              TMA kernel (2, 3 and 5 need a periodic domain without
-                              forcing, nx in {128, 256} and ny % 8 == 0; 2 and 3 need FP32
+                              TMA kernel (2, 3 and 5 need the plain scheme without
+                              forcing, nx in {128, 256} and ny % 8 == 0, and run walled
+                              domains with the wall pass after them; 2 and 3 need FP32
                               storage, 5 takes FP32, BF16 and FP16: LWACM_E_UNSUPPORTED
                               otherwise); 6 = D2Q9 2D-tile kernel (any boundary, walls
                               and forcing applied in the kernel, not with omega_p, the

@@ -49,16 +49,23 @@ __global__ void __launch_bounds__(256) k_step_generic(const T *__restrict__ in,
 
 // Boundary nodes of a walled domain, enumerated without gaps.
 //   cavity 2D: the perimeter of the nx x ny rectangle;
-//   cavity 3D: the planes z = 0 and z = nz-1, then the perimeter of each inner plane;
+//   cavity 3D: the planes z = 0 and z = nz-1, then the perimeter of each inner plane
+//              (with xface_split(p): only the rows y = 0 and y = ny-1 of each inner
+//              plane; the x = 0 and x = nx-1 columns go to k_wall_xface);
 //   channel:   rows y = 0 and y = ny-1 of every z plane.
 __host__ __device__ inline long long perimeter(int nx, int ny) {
     return ny <= 1 ? nx : (nx <= 1 ? ny : 2LL * nx + 2LL * (ny - 2));
+}
+// D3Q19 cavity whose x faces have inner nodes (y in [1, ny-2], z in [1, nz-2]) and
+// an inner column beside each (nx >= 2): those nodes are updated by k_wall_xface
+__host__ __device__ inline bool xface_split(const StepParams &p, int D) {
+    return D == 3 && p.bc == BC_CAVITY && p.nx >= 2 && p.ny > 2 && p.nz > 2;
 }
 __host__ __device__ inline long long boundary_count(const StepParams &p, int D) {
     if (p.bc == BC_CHANNEL) return (p.ny <= 1 ? 1LL : 2LL) * p.nx * p.nz;
     if (D == 2) return perimeter(p.nx, p.ny);
     if (p.nz <= 2) return (long long)p.nx * p.ny * p.nz;
-    return 2LL * p.nx * p.ny + (long long)(p.nz - 2) * perimeter(p.nx, p.ny);
+    return 2LL * p.nx * p.ny + (long long)(p.nz - 2) * (xface_split(p, D) ? 2LL * p.nx : perimeter(p.nx, p.ny));
 }
 __device__ inline void perimeter_node(long long t, int nx, int ny, int &x, int &y) {
     if (ny <= 1) { x = (int)t; y = 0; return; }
@@ -100,6 +107,12 @@ __global__ void __launch_bounds__(256) k_wall_pass(const T *__restrict__ in, T *
             const long long r = t < plane ? t : t - plane;
             x = (int)(r % p.nx);
             y = (int)(r / p.nx);
+        } else if (xface_split(p, 3)) {  // rows y = 0, ny-1 of the inner planes
+            const long long r = t - 2 * plane;
+            z = 1 + (int)(r / (2LL * p.nx));
+            const int q = (int)(r % (2LL * p.nx));
+            x = q < p.nx ? q : q - p.nx;
+            y = q < p.nx ? 0 : p.ny - 1;
         } else {
             const long long per = perimeter(p.nx, p.ny);
             const long long r = t - 2 * plane;
@@ -108,6 +121,191 @@ __global__ void __launch_bounds__(256) k_wall_pass(const T *__restrict__ in, T *
         }
     }
     node_update<Q, true>(in, out, p, x, y, z);
+}
+
+// node_update<19, true> for a node of a cavity (every axis walled, so no source
+// wraps): the wall test of each link reduces to the node's face flags and the
+// source offsets to per-direction constants; same link order and arithmetic.
+template <typename T>
+__device__ __forceinline__ void cavity_node_update(const T *__restrict__ in, T *__restrict__ out,
+                                                   const StepParams &p, int x, int y, int z) {
+    using L = Lat<19>;
+    const long long plane = (long long)p.nx * p.ny;
+    const long long k = z * plane + (long long)y * p.nx + x;
+    const T *Din = in + k, *Uin = in + p.fstride + k, *Vin = in + 2 * p.fstride + k, *Win = in + 3 * p.fstride + k;
+    const bool lo0 = x == 0, lo1 = y == 0, lo2 = z == 0;
+    const bool hi0 = x == p.nx - 1, hi1 = y == p.ny - 1, hi2 = z == p.nz - 1;
+    const int la = p.lid_axis;
+    const float dx = ldf(Din), ux = ldf(Uin), uy = ldf(Vin), uz = ldf(Win);
+    const float rx = 1.f + dx;
+    const float qx = fmaf(ux, ux, fmaf(uy, uy, uz * uz));
+    float dd = 0.f, jx = 0.f, jy = 0.f, jz = 0.f;
+#pragma unroll
+    for (int i = 0; i < 19; ++i) {
+        const int cx = L::c(i, 0), cy = L::c(i, 1), cz = L::c(i, 2);
+        // the source x - c lies beyond the low face when c = +1, the high face when -1
+        const bool bx = (cx > 0 && lo0) || (cx < 0 && hi0);
+        const bool by = (cy > 0 && lo1) || (cy < 0 && hi1);
+        const bool bz = (cz > 0 && lo2) || (cz < 0 && hi2);
+        const bool outside = bx || by || bz;
+        const bool above = (la == 0 ? cx < 0 && hi0 : (la == 1 ? cy < 0 && hi1 : cz < 0 && hi2));
+        // a source beyond a wall reads the node itself (loaded already, unused)
+        const long long so = outside ? 0 : cz * plane + (long long)cy * p.nx + cx;
+        const float ds = ldf(Din - so), us = ldf(Uin - so), vs = ldf(Vin - so), ws = ldf(Win - so);
+        float g;
+        if (!outside) {
+            const float e = cx * us + cy * vs + cz * ws;
+            const float q = fmaf(us, us, fmaf(vs, vs, ws * ws));
+            g = link_g(L::w(i), ds, 1.f + ds, e, q, p.s);
+        } else {
+            // Eq. ACM2.0cccbb2 + Eq. ACM2.0ccccbb: own outgoing BB(i) value, reflected
+            const float e = -(cx * ux + cy * uy + cz * uz);
+            g = link_g(L::w(i), dx, rx, e, qx, p.s);
+            if (above) {
+                const float cu = cx * p.lid[0] + cy * p.lid[1] + cz * p.lid[2];
+                g = fmaf(L::w(i) * p.wallc, cu, g);
+            }
+        }
+        dd += g;
+        if (cx) jx += cx > 0 ? g : -g;
+        if (cy) jy += cy > 0 ? g : -g;
+        if (cz) jz += cz > 0 ? g : -g;
+    }
+    jx = fmaf(p.a * rx, ux, jx);
+    jy = fmaf(p.a * rx, uy, jy);
+    jz = fmaf(p.a * rx, uz, jz);
+    if (p.has_force) {  // Eq. force
+        jx = fmaf(rx, p.force[0], jx);
+        jy = fmaf(rx, p.force[1], jy);
+        jz = fmaf(rx, p.force[2], jz);
+    }
+    if (p.gfield) {
+        jx = fmaf(rx, __ldg(p.gfield + k), jx);
+        jy = fmaf(rx, __ldg(p.gfield + p.fstride + k), jy);
+        jz = fmaf(rx, __ldg(p.gfield + 2 * p.fstride + k), jz);
+    }
+    const float rn = 1.f + dd;
+    stf(out + k, dd);
+    stf(out + p.fstride + k, jx / rn);
+    stf(out + 2 * p.fstride + k, jy / rn);
+    stf(out + 3 * p.fstride + k, jz / rn);
+}
+
+// With xface_split(p): the boundary rows other than the inner x-face nodes, one row
+// per blockIdx.y (the ny rows of z = 0, those of z = nz-1, then y = 0 and y = ny-1
+// of each inner plane), x across the blocks: coalesced, with the row found once
+// per block in 32-bit arithmetic.
+constexpr int WR_THREADS = 128;
+__host__ __device__ inline long long wall_rows(const StepParams &p) { return 2LL * p.ny + 2LL * (p.nz - 2); }
+template <typename T>
+__global__ void __launch_bounds__(WR_THREADS) k_wall_rows(const T *__restrict__ in, T *__restrict__ out,
+                                                          StepParams p) {
+    const int x = (int)(blockIdx.x * WR_THREADS + threadIdx.x);
+    if (x >= p.nx) return;
+    const int r = (int)blockIdx.y;
+    int y, z;
+    if (r < 2 * p.ny) {
+        z = r < p.ny ? 0 : p.nz - 1;
+        y = r < p.ny ? r : r - p.ny;
+    } else {
+        const int q = r - 2 * p.ny;
+        z = 1 + (q >> 1);
+        y = (q & 1) ? p.ny - 1 : 0;
+    }
+    cavity_node_update(in, out, p, x, y, z);
+}
+
+// The inner nodes of the x = 0 and x = nx-1 faces of a D3Q19 cavity (blockIdx.z =
+// face; y in [1, ny-2], z in [1, nz-2]): one thread per node, as k_wall_pass, but
+// their sources (own and inner column, y and z within one) are first staged in
+// shared memory for a patch of XF_PY x XF_PZ nodes. With x fastest in memory, one
+// thread per face node gathering straight from global memory sends every warp load
+// to 32 rows (32 sectors) and overflows L1 with lines of which 8 bytes are used;
+// here each needed row sector is requested once per patch. The update is
+// node_update<19, true> restated for these nodes (same link order and arithmetic,
+// so the same results): only x-links can leave the box, the lid applies when it
+// moves the x = nx-1 face.
+constexpr int XF_PY = 32, XF_PZ = 8, XF_RY = XF_PY + 2, XF_RZ = XF_PZ + 2;
+template <typename T>
+__global__ void __launch_bounds__(XF_PY * XF_PZ) k_wall_xface(const T *__restrict__ in, T *__restrict__ out,
+                                                              StepParams p) {
+    using L = Lat<19>;
+    __shared__ float sm[4][XF_RZ][XF_RY][2];  // [field][z][y][own column, inner column]
+    const int face = (int)blockIdx.z;
+    const int xo = face ? p.nx - 1 : 0, xi = face ? p.nx - 2 : 1;
+    const int y0 = 1 + (int)blockIdx.x * XF_PY, z0 = 1 + (int)blockIdx.y * XF_PZ;
+    // every load of the patch issued before the first shared store (NL per thread)
+    constexpr int NR = XF_RY * XF_RZ, NE = 4 * NR * 2, NT = XF_PY * XF_PZ, NL = (NE + NT - 1) / NT;
+    float v[NL];
+#pragma unroll
+    for (int j = 0; j < NL; ++j) {
+        const int e = (int)threadIdx.x + j * NT;
+        const int col = e & 1, r = (e >> 1) % NR, f = (e >> 1) / NR;
+        const int y = y0 - 1 + r % XF_RY, z = z0 - 1 + r / XF_RY;  // >= 0: y0, z0 >= 1
+        v[j] = 0.f;
+        if (e < NE && y < p.ny && z < p.nz)
+            v[j] = ldf(in + (long long)f * p.fstride + ((long long)z * p.ny + y) * p.nx + (col ? xi : xo));
+    }
+#pragma unroll
+    for (int j = 0; j < NL; ++j) {
+        const int e = (int)threadIdx.x + j * NT;
+        if (e < NE) (&sm[0][0][0][0])[e] = v[j];  // [f][z][y][col] is e's own order
+    }
+    __syncthreads();
+    const int ty = (int)threadIdx.x % XF_PY, tz = (int)threadIdx.x / XF_PY;
+    const int y = y0 + ty, z = z0 + tz;
+    if (y > p.ny - 2 || z > p.nz - 2) return;
+    const long long k = ((long long)z * p.ny + y) * p.nx + xo;
+    const float dx = sm[0][tz + 1][ty + 1][0], ux = sm[1][tz + 1][ty + 1][0], uy = sm[2][tz + 1][ty + 1][0];
+    const float uz = sm[3][tz + 1][ty + 1][0];
+    const float rx = 1.f + dx;
+    const float qx = fmaf(ux, ux, fmaf(uy, uy, uz * uz));
+    const bool lid_face = face == 1 && p.lid_axis == 0;
+    float dd = 0.f, jx = 0.f, jy = 0.f, jz = 0.f;
+#pragma unroll
+    for (int i = 0; i < 19; ++i) {
+        const int cx = L::c(i, 0), cy = L::c(i, 1), cz = L::c(i, 2);
+        const bool outside = cx == (face ? -1 : 1);  // source x - cx beyond the wall
+        float g;
+        if (!outside) {
+            const int c = cx == 0 ? 0 : 1, yy = ty + 1 - cy, zz = tz + 1 - cz;
+            const float ds = sm[0][zz][yy][c], us = sm[1][zz][yy][c], vs = sm[2][zz][yy][c];
+            const float ws = sm[3][zz][yy][c];
+            const float e = cx * us + cy * vs + cz * ws;
+            const float q = fmaf(us, us, fmaf(vs, vs, ws * ws));
+            g = link_g(L::w(i), ds, 1.f + ds, e, q, p.s);
+        } else {
+            // Eq. ACM2.0cccbb2 + Eq. ACM2.0ccccbb: own outgoing BB(i) value, reflected
+            const float e = -(cx * ux + cy * uy + cz * uz);
+            g = link_g(L::w(i), dx, rx, e, qx, p.s);
+            if (lid_face) {
+                const float cu = cx * p.lid[0] + cy * p.lid[1] + cz * p.lid[2];
+                g = fmaf(L::w(i) * p.wallc, cu, g);
+            }
+        }
+        dd += g;
+        if (cx) jx += cx > 0 ? g : -g;
+        if (cy) jy += cy > 0 ? g : -g;
+        if (cz) jz += cz > 0 ? g : -g;
+    }
+    jx = fmaf(p.a * rx, ux, jx);
+    jy = fmaf(p.a * rx, uy, jy);
+    jz = fmaf(p.a * rx, uz, jz);
+    if (p.has_force) {  // Eq. force
+        jx = fmaf(rx, p.force[0], jx);
+        jy = fmaf(rx, p.force[1], jy);
+        jz = fmaf(rx, p.force[2], jz);
+    }
+    if (p.gfield) {
+        jx = fmaf(rx, __ldg(p.gfield + k), jx);
+        jy = fmaf(rx, __ldg(p.gfield + p.fstride + k), jy);
+        jz = fmaf(rx, __ldg(p.gfield + 2 * p.fstride + k), jz);
+    }
+    const float rn = 1.f + dd;
+    stf(out + k, dd);
+    stf(out + p.fstride + k, jx / rn);
+    stf(out + 2 * p.fstride + k, jy / rn);
+    stf(out + 3 * p.fstride + k, jz / rn);
 }
 
 // storage -> double needs the exact stored value, converted without rounding
@@ -251,10 +449,20 @@ template <typename T>
 cudaError_t launch_wall_t(int Q, const void *in, void *out, const StepParams &p, cudaStream_t st) {
     const long long nb = boundary_count(p, Q == 9 ? 2 : 3);
     if (nb <= 0) return cudaSuccess;
-    if (Q == 9)
+    if (Q == 19 && xface_split(p, 3) && wall_rows(p) <= 65535)
+        k_wall_rows<T><<<dim3((unsigned)((p.nx + WR_THREADS - 1) / WR_THREADS), (unsigned)wall_rows(p)), WR_THREADS,
+                         0, st>>>((const T *)in, (T *)out, p);
+    else if (Q == 9)
         k_wall_pass<9, T><<<blocks_for(nb, 256), 256, 0, st>>>((const T *)in, (T *)out, p, nb);
     else
         k_wall_pass<19, T><<<blocks_for(nb, 256), 256, 0, st>>>((const T *)in, (T *)out, p, nb);
+    if (Q == 19 && xface_split(p, 3)) {
+        cudaError_t e = cudaGetLastError();
+        if (e != cudaSuccess) return e;
+        const dim3 grid((unsigned)((p.ny - 2 + XF_PY - 1) / XF_PY), (unsigned)((p.nz - 2 + XF_PZ - 1) / XF_PZ), 2);
+        if (grid.y > 65535) return cudaErrorInvalidConfiguration;
+        k_wall_xface<T><<<grid, XF_PY * XF_PZ, 0, st>>>((const T *)in, (T *)out, p);
+    }
     return cudaGetLastError();
 }
 

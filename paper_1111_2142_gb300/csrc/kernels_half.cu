@@ -610,7 +610,9 @@ static cudaError_t prepare_storage(int storage) {
 }
 
 bool half_supported(int Q, int storage, const StepParams &p) {
-    if (Q != 19 || p.bc != BC_PERIODIC) return false;
+    if (Q != 19) return false;
+    // walled domains (cavity, channel): the kernel wraps every axis and the wall pass
+    // after it recomputes every boundary node, the only nodes with a source outside
     if (storage != STORE_F32 && storage != STORE_BF16 && storage != STORE_F16) return false;
     if (p.has_force || p.gfield || p.sdelta != 0.f || p.scalar || p.bulk) return false;  // plain scheme only
     if ((p.nx != 128 && p.nx != 256) || p.ny % ROWS != 0 || p.ny < ROWS || p.nz < 1) return false;

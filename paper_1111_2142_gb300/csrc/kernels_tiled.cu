@@ -470,7 +470,8 @@ int chunk_planes(int ycols, int nz, int ctas) {
 
 bool tiled_supported(int Q, int storage, const StepParams &p) {
     if (Q != 19 || storage != STORE_F32) return false;
-    if (p.bc != BC_PERIODIC) return false;
+    // walled domains (cavity, channel): the kernel wraps every axis and the wall pass
+    // after it recomputes every boundary node, the only nodes with a source outside
     if (p.has_force || p.gfield || p.sdelta != 0.f || p.scalar || p.bulk) return false;  // plain scheme only
     if (!(p.nx == 128 || p.nx == 256)) return false;
     if (p.ny % ROWS != 0 || p.ny < ROWS) return false;

@@ -57,14 +57,16 @@ __device__ __forceinline__ void node_update(const T *__restrict__ in, T *__restr
             const int nl = p.lid_axis == 0 ? p.nx : (p.lid_axis == 1 ? p.ny : p.nz);
             above = outside && sl >= nl;
         }
+        // a source beyond a wall reads the node itself (already loaded, its values go
+        // unused): no link's loads wait behind the wall test
+        sx = sx < 0 ? sx + p.nx : (sx >= p.nx ? sx - p.nx : sx);
+        sy = sy < 0 ? sy + p.ny : (sy >= p.ny ? sy - p.ny : sy);
+        sz = sz < 0 ? sz + p.nz : (sz >= p.nz ? sz - p.nz : sz);
+        const long long s = outside ? k : ((long long)sz * p.ny + sy) * p.nx + sx;
+        const float ds = ldf(Din + s), us = ldf(Uin + s), vs = ldf(Vin + s);
+        const float ws = (Q == 19) ? ldf(Win + s) : 0.f;
         float g;
         if (!outside) {
-            sx = sx < 0 ? sx + p.nx : (sx >= p.nx ? sx - p.nx : sx);
-            sy = sy < 0 ? sy + p.ny : (sy >= p.ny ? sy - p.ny : sy);
-            sz = sz < 0 ? sz + p.nz : (sz >= p.nz ? sz - p.nz : sz);
-            const long long s = ((long long)sz * p.ny + sy) * p.nx + sx;
-            const float ds = ldf(Din + s), us = ldf(Uin + s), vs = ldf(Vin + s);
-            const float ws = (Q == 19) ? ldf(Win + s) : 0.f;
             const float e = cx * us + cy * vs + cz * ws;
             const float q = fmaf(us, us, fmaf(vs, vs, ws * ws));
             g = link_g(L::w(i), ds, 1.f + ds, e, q, p.s);

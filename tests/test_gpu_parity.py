@@ -126,6 +126,43 @@ def test_d3q19_tiled_kernel(lw, kernel, shape):
     assert eu < 1e-5 and ed < 1e-4
 
 
+@pytest.mark.parametrize("kernel", [2, 3, 5])
+@pytest.mark.parametrize("bc", [1, 2])
+@pytest.mark.parametrize("shape", [(5, 8, 128), (3, 16, 256), (20, 24, 128), (2, 8, 256), (11, 72, 128)])
+def test_d3q19_tiled_kernel_walls(lw, kernel, bc, shape):
+    """The row-tiled D3Q19 kernels on walled domains: the diagonally driven cavity
+    (all six faces walled, lid on the top y face) and a channel with a moving wall
+    (walls at y = 0, ny-1; x and z periodic). The interior kernel wraps every axis
+    and the wall pass after it recomputes the boundary nodes, so the result must be
+    the oracle's walled step; shapes include nz = 2 (every node on a z face)."""
+    lid = (np.sqrt(2) / 20, np.sqrt(2) / 20, 0.0) if bc == 1 else (0.01, 0.0, 0.0)
+    f = inputs.smooth_random(shape, seed=14, u_amp=0.03, d_amp=0.005)
+    got, name = run_gpu(lw, 19, f, 0.02, 40, bc=bc, lid=lid, kernel=kernel)
+    assert name.startswith({2: "tiled", 3: "zmarch", 5: "half"}[kernel])
+    ref = oracle.step(19, *f, nu=0.02, bc=bc, lid=lid, nsteps=40)
+    eu, ed = errs(got, ref, 0.1)
+    print(f"[{name}] walls bc={bc} {shape}: du/U={eu:.2e} dd/d={ed:.2e}")
+    assert eu < 1e-5 and ed < 1e-4
+
+
+@pytest.mark.parametrize("storage", [2, 1])
+def test_half_kernel_walls_half_storage(lw, storage):
+    """The half-row kernel with BF16 / FP16 storage on the cavity: one step from a
+    state already rounded to the storage type differs from the FP64 oracle by the
+    final rounding only, boundary nodes included."""
+    shape = (6, 16, 256)
+    lid = (np.sqrt(2) / 20, np.sqrt(2) / 20, 0.0)
+    f = [round_storage(a, storage) for a in inputs.smooth_random(shape, seed=15, u_amp=0.03, d_amp=0.005)]
+    got, name = run_gpu(lw, 19, f, 0.02, 1, bc=1, lid=lid, storage=storage)
+    assert name.startswith("half")
+    ref = oracle.step(19, *f, nu=0.02, bc=1, lid=lid, nsteps=1)
+    for g, r in zip(got, ref):
+        # floors: the FP16 subnormal spacing (2^-24) and the FP32 rounding of the
+        # O(0.1) terms that cancel in values near 0, added
+        tol = 1.05 * HALF_ULP[storage] * np.abs(r) + (2.0 ** -25 if storage == 2 else 0.0) + 8 * 2.0 ** -24 * 0.1
+        assert np.all(np.abs(g - r) <= tol), (name, float(np.max(np.abs(g - r) / (np.abs(r) + 1e-30))))
+
+
 @pytest.mark.parametrize("kernel", KERNELS)
 def test_d3q19_tgv_48(lw, kernel):
     """3D Taylor-Green, u0 = 0.02, nu = 0.005 (the 256^3 workload's parameters), 300 steps."""
@@ -148,8 +185,11 @@ def test_cavity_2d(lw, shape, lid):
     assert eu < 1e-5 and ed < 1e-4
 
 
-@pytest.mark.parametrize("shape", [(9, 10, 12), (2, 3, 4)])
+@pytest.mark.parametrize("shape", [(9, 10, 12), (2, 3, 4), (5, 6, 2), (13, 40, 6), (3, 3, 3)])
 def test_cavity_3d(lw, shape):
+    """Generic kernel and wall pass on small cavities; the inner x-face nodes take the
+    staged x-face update when ny, nz > 2 and nx >= 2 (several y and z patches at
+    40 x 13, each face the other's inner column at nx = 2, one node at 3^3)."""
     lid = (np.sqrt(2) / 20, np.sqrt(2) / 20, 0.0)
     f = inputs.smooth_random(shape, seed=6, u_amp=0.03, d_amp=0.005)
     got, _ = run_gpu(lw, 19, f, 0.02, 100, bc=lw.CAVITY, lid=lid)
