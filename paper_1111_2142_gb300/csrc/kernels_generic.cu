@@ -49,23 +49,16 @@ __global__ void __launch_bounds__(256) k_step_generic(const T *__restrict__ in,
 
 // Boundary nodes of a walled domain, enumerated without gaps.
 //   cavity 2D: the perimeter of the nx x ny rectangle;
-//   cavity 3D: the planes z = 0 and z = nz-1, then the perimeter of each inner plane
-//              (with xface_split(p): only the rows y = 0 and y = ny-1 of each inner
-//              plane; the x = 0 and x = nx-1 columns go to k_wall_xface);
+//   cavity 3D: the planes z = 0 and z = nz-1, then the perimeter of each inner plane;
 //   channel:   rows y = 0 and y = ny-1 of every z plane.
 __host__ __device__ inline long long perimeter(int nx, int ny) {
     return ny <= 1 ? nx : (nx <= 1 ? ny : 2LL * nx + 2LL * (ny - 2));
-}
-// D3Q19 cavity whose x faces have inner nodes (y in [1, ny-2], z in [1, nz-2]) and
-// an inner column beside each (nx >= 2): those nodes are updated by k_wall_xface
-__host__ __device__ inline bool xface_split(const StepParams &p, int D) {
-    return D == 3 && p.bc == BC_CAVITY && p.nx >= 2 && p.ny > 2 && p.nz > 2;
 }
 __host__ __device__ inline long long boundary_count(const StepParams &p, int D) {
     if (p.bc == BC_CHANNEL) return (p.ny <= 1 ? 1LL : 2LL) * p.nx * p.nz;
     if (D == 2) return perimeter(p.nx, p.ny);
     if (p.nz <= 2) return (long long)p.nx * p.ny * p.nz;
-    return 2LL * p.nx * p.ny + (long long)(p.nz - 2) * (xface_split(p, D) ? 2LL * p.nx : perimeter(p.nx, p.ny));
+    return 2LL * p.nx * p.ny + (long long)(p.nz - 2) * perimeter(p.nx, p.ny);
 }
 __device__ inline void perimeter_node(long long t, int nx, int ny, int &x, int &y) {
     if (ny <= 1) { x = (int)t; y = 0; return; }
@@ -107,12 +100,6 @@ __global__ void __launch_bounds__(256) k_wall_pass(const T *__restrict__ in, T *
             const long long r = t < plane ? t : t - plane;
             x = (int)(r % p.nx);
             y = (int)(r / p.nx);
-        } else if (xface_split(p, 3)) {  // rows y = 0, ny-1 of the inner planes
-            const long long r = t - 2 * plane;
-            z = 1 + (int)(r / (2LL * p.nx));
-            const int q = (int)(r % (2LL * p.nx));
-            x = q < p.nx ? q : q - p.nx;
-            y = q < p.nx ? 0 : p.ny - 1;
         } else {
             const long long per = perimeter(p.nx, p.ny);
             const long long r = t - 2 * plane;
@@ -191,18 +178,21 @@ __device__ __forceinline__ void cavity_node_update(const T *__restrict__ in, T *
     stf(out + 3 * p.fstride + k, jz / rn);
 }
 
-// With xface_split(p): the boundary rows other than the inner x-face nodes, one row
-// per blockIdx.y (the ny rows of z = 0, those of z = nz-1, then y = 0 and y = ny-1
-// of each inner plane), x across the blocks: coalesced, with the row found once
-// per block in 32-bit arithmetic.
-constexpr int WR_THREADS = 128;
+// D3Q19 cavity walls in one launch (k_wall_cavity3d) when the x faces have inner
+// nodes (y in [1, ny-2], z in [1, nz-2]) with an inner column beside each (nx >= 2):
+// blocks of shared-memory staged x-face patches, then blocks of boundary rows.
+__host__ __device__ inline bool xface_split(const StepParams &p, int D) {
+    return D == 3 && p.bc == BC_CAVITY && p.nx >= 2 && p.ny > 2 && p.nz > 2;
+}
+constexpr int WC_THREADS = 256;
+
+// Boundary row r other than the inner x-face nodes (the ny rows of z = 0, those of
+// z = nz-1, then y = 0 and y = ny-1 of each inner plane), node x of it: coalesced
+// across a block, the row found once per block in 32-bit arithmetic.
 __host__ __device__ inline long long wall_rows(const StepParams &p) { return 2LL * p.ny + 2LL * (p.nz - 2); }
 template <typename T>
-__global__ void __launch_bounds__(WR_THREADS) k_wall_rows(const T *__restrict__ in, T *__restrict__ out,
-                                                          StepParams p) {
-    const int x = (int)(blockIdx.x * WR_THREADS + threadIdx.x);
-    if (x >= p.nx) return;
-    const int r = (int)blockIdx.y;
+__device__ __forceinline__ void wall_row_node(const T *__restrict__ in, T *__restrict__ out, const StepParams &p,
+                                              int r, int x) {
     int y, z;
     if (r < 2 * p.ny) {
         z = r < p.ny ? 0 : p.nz - 1;
@@ -215,8 +205,8 @@ __global__ void __launch_bounds__(WR_THREADS) k_wall_rows(const T *__restrict__ 
     cavity_node_update(in, out, p, x, y, z);
 }
 
-// The inner nodes of the x = 0 and x = nx-1 faces of a D3Q19 cavity (blockIdx.z =
-// face; y in [1, ny-2], z in [1, nz-2]): one thread per node, as k_wall_pass, but
+// The inner nodes of the x = 0 and x = nx-1 faces of a D3Q19 cavity (patch (py, pz)
+// of face `face`; y in [1, ny-2], z in [1, nz-2]): one thread per node, but
 // their sources (own and inner column, y and z within one) are first staged in
 // shared memory for a patch of XF_PY x XF_PZ nodes. With x fastest in memory, one
 // thread per face node gathering straight from global memory sends every warp load
@@ -226,16 +216,16 @@ __global__ void __launch_bounds__(WR_THREADS) k_wall_rows(const T *__restrict__ 
 // so the same results): only x-links can leave the box, the lid applies when it
 // moves the x = nx-1 face.
 constexpr int XF_PY = 32, XF_PZ = 8, XF_RY = XF_PY + 2, XF_RZ = XF_PZ + 2;
+static_assert(XF_PY * XF_PZ == WC_THREADS, "one thread per patch node");
 template <typename T>
-__global__ void __launch_bounds__(XF_PY * XF_PZ) k_wall_xface(const T *__restrict__ in, T *__restrict__ out,
-                                                              StepParams p) {
+__device__ __forceinline__ void xface_patch(const T *__restrict__ in, T *__restrict__ out, const StepParams &p,
+                                            int face, int py, int pz) {
     using L = Lat<19>;
     __shared__ float sm[4][XF_RZ][XF_RY][2];  // [field][z][y][own column, inner column]
-    const int face = (int)blockIdx.z;
     const int xo = face ? p.nx - 1 : 0, xi = face ? p.nx - 2 : 1;
-    const int y0 = 1 + (int)blockIdx.x * XF_PY, z0 = 1 + (int)blockIdx.y * XF_PZ;
+    const int y0 = 1 + py * XF_PY, z0 = 1 + pz * XF_PZ;
     // every load of the patch issued before the first shared store (NL per thread)
-    constexpr int NR = XF_RY * XF_RZ, NE = 4 * NR * 2, NT = XF_PY * XF_PZ, NL = (NE + NT - 1) / NT;
+    constexpr int NR = XF_RY * XF_RZ, NE = 4 * NR * 2, NT = WC_THREADS, NL = (NE + NT - 1) / NT;
     float v[NL];
 #pragma unroll
     for (int j = 0; j < NL; ++j) {
@@ -306,6 +296,20 @@ __global__ void __launch_bounds__(XF_PY * XF_PZ) k_wall_xface(const T *__restric
     stf(out + p.fstride + k, jx / rn);
     stf(out + 2 * p.fstride + k, jy / rn);
     stf(out + 3 * p.fstride + k, jz / rn);
+}
+
+// blocks [0, 2 npy npz): x-face patches (face, py, pz), py fastest; then bpr blocks
+// per boundary row
+template <typename T>
+__global__ void __launch_bounds__(WC_THREADS) k_wall_cavity3d(const T *__restrict__ in, T *__restrict__ out,
+                                                              StepParams p, int npy, int npz, int bpr) {
+    const int b = (int)blockIdx.x, nxf = 2 * npy * npz;
+    if (b < nxf) {
+        xface_patch(in, out, p, b / (npy * npz), b % npy, (b / npy) % npz);
+        return;
+    }
+    const int rb = b - nxf, x = (rb % bpr) * WC_THREADS + (int)threadIdx.x;
+    if (x < p.nx) wall_row_node(in, out, p, rb / bpr, x);
 }
 
 // storage -> double needs the exact stored value, converted without rounding
@@ -449,19 +453,17 @@ template <typename T>
 cudaError_t launch_wall_t(int Q, const void *in, void *out, const StepParams &p, cudaStream_t st) {
     const long long nb = boundary_count(p, Q == 9 ? 2 : 3);
     if (nb <= 0) return cudaSuccess;
-    if (Q == 19 && xface_split(p, 3) && wall_rows(p) <= 65535)
-        k_wall_rows<T><<<dim3((unsigned)((p.nx + WR_THREADS - 1) / WR_THREADS), (unsigned)wall_rows(p)), WR_THREADS,
-                         0, st>>>((const T *)in, (T *)out, p);
-    else if (Q == 9)
-        k_wall_pass<9, T><<<blocks_for(nb, 256), 256, 0, st>>>((const T *)in, (T *)out, p, nb);
-    else
-        k_wall_pass<19, T><<<blocks_for(nb, 256), 256, 0, st>>>((const T *)in, (T *)out, p, nb);
     if (Q == 19 && xface_split(p, 3)) {
-        cudaError_t e = cudaGetLastError();
-        if (e != cudaSuccess) return e;
-        const dim3 grid((unsigned)((p.ny - 2 + XF_PY - 1) / XF_PY), (unsigned)((p.nz - 2 + XF_PZ - 1) / XF_PZ), 2);
-        if (grid.y > 65535) return cudaErrorInvalidConfiguration;
-        k_wall_xface<T><<<grid, XF_PY * XF_PZ, 0, st>>>((const T *)in, (T *)out, p);
+        const long long npy = (p.ny - 2 + XF_PY - 1) / XF_PY, npz = (p.nz - 2 + XF_PZ - 1) / XF_PZ;
+        const long long bpr = (p.nx + WC_THREADS - 1) / WC_THREADS;
+        const long long blocks = 2 * npy * npz + wall_rows(p) * bpr;
+        if (blocks > 0x7fffffffLL) return cudaErrorInvalidConfiguration;
+        k_wall_cavity3d<T><<<(unsigned)blocks, WC_THREADS, 0, st>>>((const T *)in, (T *)out, p, (int)npy, (int)npz,
+                                                                    (int)bpr);
+    } else if (Q == 9) {
+        k_wall_pass<9, T><<<blocks_for(nb, 256), 256, 0, st>>>((const T *)in, (T *)out, p, nb);
+    } else {
+        k_wall_pass<19, T><<<blocks_for(nb, 256), 256, 0, st>>>((const T *)in, (T *)out, p, nb);
     }
     return cudaGetLastError();
 }
