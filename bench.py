@@ -347,6 +347,8 @@ def next_rows(hbm, glups):
     lid = (2 ** 0.5 / 20, 2 ** 0.5 / 20, 0.0)
     timed("cavity3d_d3q19_256", lw.Lwacm(lw.D3Q19, n3, n3, n3, 0.01, lw.CAVITY, lid=lid), (z3, z3, z3, z3),
           100, n3 ** 3, 32)
+    timed("cavity3d_d3q19_256_bf16", lw.Lwacm(lw.D3Q19, n3, n3, n3, 0.01, lw.CAVITY, lid=lid, storage=lw.BF16),
+          (z3, z3, z3, z3), 100, n3 ** 3, 16)
     f3 = inputs.tgv3d(n3, u0=U0)
     t3 = torch.cos(2 * torch.pi * torch.arange(n3, device="cuda") / n3).expand(n3, n3, n3).contiguous()
     timed("scalar_d3q19_256", lw.Lwacm(lw.D3Q19, n3, n3, n3, NU, scalar_alpha=0.01), f3, 100, n3 ** 3, 40,

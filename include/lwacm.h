@@ -95,8 +95,9 @@ enum {
                               domains with the wall pass after them; 2 and 3 need FP32
                               storage, 5 takes FP32, BF16 and FP16: LWACM_E_UNSUPPORTED
                               otherwise); 6 = D2Q9 2D-tile kernel (any boundary, walls
-                              and forcing applied in the kernel, not with omega_p, the
-                              scalar or the bulk-viscosity variant; tile shape from
+                              and forcing applied in the kernel, the bulk-viscosity
+                              variant on periodic domains, not with omega_p or the
+                              scalar; tile shape from
                               LWACM_OPT_BATCH_TILE, 30x14 when 0). The automatic choice
                               takes 5, else 3, else 2, else 6, else 1. */
     LWACM_OPT_BATCH_MODE = 10, /* batched contexts: 0 = one launch per step, replayed
@@ -151,7 +152,8 @@ enum {
                                      periodic D2Q9 domains only, not with the scalar
                                      (LWACM_E_UNSUPPORTED). With LWACM_OPT_NU_P the density
                                      is relaxed with omega_p and the momentum and the
-                                     trace with omega. Runs on the generic kernel. */
+                                     trace with omega. Runs on the D2Q9 2D-tile kernel
+                                     (the generic kernel with LWACM_OPT_NU_P). */
 };
 
 /* Create a single-domain context.

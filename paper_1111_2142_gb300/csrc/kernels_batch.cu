@@ -107,12 +107,20 @@ struct Force2 {
 // one TW x TH tile (plus frame) of a D2Q9 domain whose node (0,0) is at packed
 // index base; s, a: 18 nu and 1 - 6 nu of the domain. Without WALLS every axis is
 // periodic; with WALLS a link whose source lies beyond a walled face takes the
-// node's own value of the opposite link plus the moving-wall term.
-template <int TW, int TH, typename T, bool WALLS = false>
+// node's own value of the opposite link plus the moving-wall term. With BULK
+// (periodic) the source's equilibrium is the quasi-equilibrium f^(e*) of Appendix
+// "Computing derivatives locally": each source adds to its eight link values the
+// increment Df - a Df^o of its trace deviation (the fourth field, Tr^(+) - Tr^(e)),
+// with h = gamma (Tr^(+) - Tr^(e)) / 2,
+//   Df = rho [h (ax B + ay A) + ax ay h^2],  Df^o = rho h (ax c_y v + ay c_x u) / 2,
+// A = 1 - Pxx (c_x = 0) or (Pxx + c_x u)/2, ax = -1 or 1/2 (B, ay likewise in y),
+// Pxx = 1/3 + u^2, Pyy = 1/3 + v^2; the rest link's increment stays with the node;
+// the node stores Tr^(+) - Tr^(e) = sum_i (|c_i|^2 - 2/3) g_i / (1 + d+) - |u+|^2.
+template <int TW, int TH, typename T, bool WALLS = false, bool BULK = false>
 __device__ __forceinline__ void tile2_core(const T *__restrict__ in, T *__restrict__ out, long long base, int nx,
                                            int ny, long long fstride, float s, float a, int x0, int y0,
                                            float (*G)[(TW + 2) * (TH + 2)], const Walls2 &wl = Walls2{},
-                                           const Force2 &fc = Force2{}) {
+                                           const Force2 &fc = Force2{}, float gamma = 0.f) {
     constexpr int W = TW + 2;
     const int tx = threadIdx.x % W, ty = threadIdx.x / W;
     // periodic wrap of the frame (x0 + tx - 1 lies in [-1, x0 + TW], below 2 nx
@@ -135,18 +143,38 @@ __device__ __forceinline__ void tile2_core(const T *__restrict__ in, T *__restri
     const float rho = 1.f + d;
     const float K = fmaf(-1.5f * rho, fmaf(u, u, v * v), d);  // d - 3/2 rho |u|^2
     const float nu = s * (1.f / 18.f);
+    float df0 = 0.f;  // BULK: the rest link's increment
     {
         // pair (c, -c) with e = c.u: w (K + 9/2 rho e^2) +- w rho s e
         const float a9 = rho * nu * 2.f, b9 = rho * 0.5f, k9 = K * (1.f / 9.f);        // axis, w = 1/9
         const float a36 = rho * nu * 0.5f, b36 = rho * 0.125f, k36 = K * (1.f / 36.f);  // diagonal, w = 1/36
         const float e[4] = {u, v, u + v, u - v};
+        float inc[8] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+        if (BULK) {
+            const float h = 0.5f * gamma * ldf(in + 3 * fstride + k), rh = rho * h;
+            const float pxx = fmaf(u, u, 1.f / 3.f), pyy = fmaf(v, v, 1.f / 3.f);
+            // A, B per component (c = +1, -1, 0) and ax = ay = 1/2 for a moving component
+            const float Ap = 0.5f * (pxx + u), Am = 0.5f * (pxx - u), A0 = 1.f - pxx;
+            const float Bp = 0.5f * (pyy + v), Bm = 0.5f * (pyy - v), B0 = 1.f - pyy;
+            // link order (1,0) (-1,0) (0,1) (0,-1) (1,1) (-1,-1) (1,-1) (-1,1)
+            const float Al[8] = {Ap, Am, A0, A0, Ap, Am, Ap, Am}, Bl[8] = {B0, B0, Bp, Bm, Bp, Bm, Bm, Bp};
+            const int cxl[8] = {1, -1, 0, 0, 1, -1, 1, -1}, cyl[8] = {0, 0, 1, -1, 1, -1, -1, 1};
+#pragma unroll
+            for (int i = 0; i < 8; ++i) {
+                const float ax = cxl[i] ? 0.5f : -1.f, ay = cyl[i] ? 0.5f : -1.f;
+                const float df = rh * fmaf(ax * ay, h, fmaf(ax, Bl[i], ay * Al[i]));
+                const float dfo = rh * (0.5f * fmaf(ax * cyl[i], v, ay * cxl[i] * u));
+                inc[i] = fmaf(-a, dfo, df);
+            }
+            df0 = rh * (h - B0 - A0);  // ax = ay = -1, no odd part
+        }
 #pragma unroll
         for (int p = 0; p < 4; ++p) {
             const bool dg = p >= 2;
             const float cm = fmaf((dg ? b36 : b9) * e[p], e[p], dg ? k36 : k9);
             const float A = dg ? a36 : a9;
-            G[2 * p][threadIdx.x] = fmaf(A, e[p], cm);
-            G[2 * p + 1][threadIdx.x] = fmaf(-A, e[p], cm);
+            G[2 * p][threadIdx.x] = fmaf(A, e[p], cm) + inc[2 * p];
+            G[2 * p + 1][threadIdx.x] = fmaf(-A, e[p], cm) + inc[2 * p + 1];
         }
     }
     __syncthreads();
@@ -184,7 +212,8 @@ __device__ __forceinline__ void tile2_core(const T *__restrict__ in, T *__restri
                 fix(g8, 8, -1, 1);
             }
         }
-        const float dd = fmaf(4.f / 9.f, K, ((g1 + g2) + (g3 + g4)) + ((g5 + g6) + (g7 + g8)));
+        const float g0 = fmaf(4.f / 9.f, K, df0);  // rest link (df0 = 0 without BULK)
+        const float dd = g0 + (((g1 + g2) + (g3 + g4)) + ((g5 + g6) + (g7 + g8)));
         const float ar = a * rho;
         float jx = fmaf(ar, u, (g1 - g2) + ((g5 - g6) + (g7 - g8)));
         float jy = fmaf(ar, v, (g3 - g4) + ((g5 - g6) - (g7 - g8)));
@@ -198,9 +227,15 @@ __device__ __forceinline__ void tile2_core(const T *__restrict__ in, T *__restri
             }
         }
         const float rn = 1.f + dd;
+        const float uxn = jx / rn, uyn = jy / rn;
         stf(out + k, dd);
-        stf(out + fstride + k, jx / rn);
-        stf(out + 2 * fstride + k, jy / rn);
+        stf(out + fstride + k, uxn);
+        stf(out + 2 * fstride + k, uyn);
+        if (BULK) {  // |c|^2 - 2/3: rest -2/3, axis 1/3, diagonal 4/3
+            const float trs = fmaf(-2.f / 3.f, g0,
+                                   fmaf(1.f / 3.f, (g1 + g2) + (g3 + g4), (4.f / 3.f) * ((g5 + g6) + (g7 + g8))));
+            stf(out + 3 * fstride + k, trs / rn - fmaf(uxn, uxn, uyn * uyn));
+        }
     }
     __syncthreads();  // G is rewritten by the next tile
 }
@@ -214,16 +249,16 @@ __device__ __forceinline__ void tile2_update(const T *__restrict__ in, T *__rest
 }
 
 // one D2Q9 domain, walls included (no separate wall pass); tiles numbered row-major
-template <int TW, int TH, typename T, bool WALLS>
+template <int TW, int TH, typename T, bool WALLS, bool BULK>
 __global__ void __launch_bounds__((TW + 2) * (TH + 2)) k_d2q9_tiles(const T *__restrict__ in, T *__restrict__ out,
                                                                    int nx, int ny, long long fstride, float s,
                                                                    float a, int tilesx, long long ntiles, Walls2 wl,
-                                                                   Force2 fc) {
+                                                                   Force2 fc, float gamma) {
     __shared__ float G[8][(TW + 2) * (TH + 2)];
     for (long long t = blockIdx.x; t < ntiles; t += gridDim.x) {
         const unsigned tu = (unsigned)t, ty = tu / (unsigned)tilesx;  // fewer than 2^32 tiles
-        tile2_core<TW, TH, T, WALLS>(in, out, 0, nx, ny, fstride, s, a, (int)(tu - ty * (unsigned)tilesx) * TW,
-                                     (int)ty * TH, G, wl, fc);
+        tile2_core<TW, TH, T, WALLS, BULK>(in, out, 0, nx, ny, fstride, s, a,
+                                           (int)(tu - ty * (unsigned)tilesx) * TW, (int)ty * TH, G, wl, fc, gamma);
     }
 }
 
@@ -362,11 +397,11 @@ cudaError_t tiles_storage(int storage, const void *in, void *out, void *b0, void
     return cudaErrorInvalidValue;
 }
 
-template <int TW, int TH, typename T, bool WALLS>
+template <int TW, int TH, typename T, bool WALLS, bool BULK = false>
 cudaError_t single_w(const void *in, void *out, const StepParams &p, const Walls2 &wl, cudaStream_t st) {
     constexpr int NT = (TW + 2) * (TH + 2);
     static DevSlots cap;
-    const int g = max_grid(k_d2q9_tiles<TW, TH, T, WALLS>, NT, cap);
+    const int g = max_grid(k_d2q9_tiles<TW, TH, T, WALLS, BULK>, NT, cap);
     if (g < 1) return cudaErrorNotSupported;
     const int tilesx = (p.nx + TW - 1) / TW;
     const long long ntiles = (long long)tilesx * ((p.ny + TH - 1) / TH);
@@ -377,13 +412,14 @@ cudaError_t single_w(const void *in, void *out, const StepParams &p, const Walls
     fc.gy = p.has_force ? p.force[1] : 0.f;
     fc.field = p.gfield;
     fc.fstride = p.fstride;
-    k_d2q9_tiles<TW, TH, T, WALLS><<<(unsigned)grid, NT, 0, st>>>((const T *)in, (T *)out, p.nx, p.ny, p.fstride,
-                                                                 p.s, p.a, tilesx, ntiles, wl, fc);
+    k_d2q9_tiles<TW, TH, T, WALLS, BULK><<<(unsigned)grid, NT, 0, st>>>(
+        (const T *)in, (T *)out, p.nx, p.ny, p.fstride, p.s, p.a, tilesx, ntiles, wl, fc, p.gamma);
     return cudaGetLastError();
 }
 
 template <int TW, int TH, typename T>
 cudaError_t single_t(const void *in, void *out, const StepParams &p, cudaStream_t st) {
+    if (p.bulk) return single_w<TW, TH, T, false, true>(in, out, p, Walls2{}, st);  // periodic only
     if (p.bc == BC_PERIODIC) return single_w<TW, TH, T, false>(in, out, p, Walls2{}, st);
     Walls2 wl;
     wl.wx = p.walled[0];
@@ -449,7 +485,7 @@ bool batch_shape_supported(int Q, int storage, int k) {
 }
 
 bool tiles2d_supported(int Q, int storage, const StepParams &p) {
-    return Q == 9 && p.nz == 1 && p.sdelta == 0.f && !p.scalar && !p.bulk &&
+    return Q == 9 && p.nz == 1 && p.sdelta == 0.f && !p.scalar && (!p.bulk || p.bc == BC_PERIODIC) &&
            (storage == STORE_F32 || storage == STORE_BF16 || storage == STORE_F16);
 }
 

@@ -23,12 +23,18 @@ def lw():
     return lwacm
 
 
-def _run(lw, fields, nu, gamma, steps, nu_p=None):
+def _run(lw, fields, nu, gamma, steps, nu_p=None, kernel=0, tile=0):
+    """kernel 0: the automatic choice, the 2D-tile kernel (the generic kernel with
+    omega_p); 1: the generic kernel; tile: the 2D-tile shape (0: 30 x 14)."""
     ny, nx = fields[0].shape
     sim = lw.Lwacm(9, nx, ny, 1, nu, bulk_gamma=gamma)
     if nu_p:
         sim.set_option(lw.OPT_NU_P, nu_p)
-    assert sim.kernel_name.startswith("generic")
+    if tile:
+        sim.set_option(lw.OPT_BATCH_TILE, tile)
+    if kernel:
+        sim.set_option(lw.OPT_KERNEL, kernel)
+    assert sim.kernel_name.startswith("generic" if (nu_p or kernel == 1) else "tiles2d"), sim.kernel_name
     sim.set_fields(*fields)
     tr0 = sim.get_trace()
     sim.step(steps)
@@ -38,11 +44,12 @@ def _run(lw, fields, nu, gamma, steps, nu_p=None):
     return got, tr, tr0.reshape(ny, nx)
 
 
+@pytest.mark.parametrize("kernel", [0, 1])
 @pytest.mark.parametrize("gamma", [0.4, -0.3])
 @pytest.mark.parametrize("shape", [(40, 48), (17, 33)])
-def test_bulk_matches_oracle(lw, gamma, shape):
+def test_bulk_matches_oracle(lw, gamma, shape, kernel):
     f = inputs.smooth_random(shape, seed=31, u_amp=0.05, d_amp=0.01)
-    got, tr, tr0 = _run(lw, f, 0.02, gamma, 200)
+    got, tr, tr0 = _run(lw, f, 0.02, gamma, 200, kernel=kernel)
     assert np.all(tr0 == 0.0)  # starts at Tr^(e)
     ref = oracle.step_bulk(*f, nu=0.02, gamma=gamma, nsteps=200)
     u_scale = 0.05
@@ -83,3 +90,18 @@ def test_longitudinal_wave_matches_oracle(lw):
     et = float(np.max(np.abs(tr - dev))) / float(np.max(np.abs(dev)))
     print(f"longitudinal wave: du/U={eu:.2e} dTr/Tr_scale={et:.2e}")
     assert eu < 1e-5 and et < 1e-3
+
+
+@pytest.mark.parametrize("tile", [1, 2, 3, 4, 5, 6])
+def test_bulk_tile_shapes(lw, tile):
+    """Every 2D-tile shape on domains narrower and wider than the tiles (ragged
+    edges, wrap across one tile), 60 steps at gamma = 0.4, against the oracle."""
+    for shape in ((23, 37), (33, 130), (5, 7)):
+        f = inputs.smooth_random(shape, seed=35, u_amp=0.05, d_amp=0.01)
+        got, tr, _ = _run(lw, f, 0.02, 0.4, 60, tile=tile)
+        ref = oracle.step_bulk(*f, nu=0.02, gamma=0.4, nsteps=60)
+        eu = max(float(np.max(np.abs(g - r))) for g, r in zip(got[1:], ref[1:3])) / 0.05
+        ed = float(np.max(np.abs(got[0] - ref[0]))) / max(float(np.max(np.abs(ref[0]))), 3 * 0.05 ** 2)
+        dev = ref[3] - (2.0 / 3.0 + ref[1] ** 2 + ref[2] ** 2)
+        et = float(np.max(np.abs(tr - dev))) / float(np.max(np.abs(dev)))
+        assert eu < 1e-5 and ed < 1e-4 and et < 1e-3, (tile, shape, eu, ed, et)
