@@ -546,6 +546,15 @@ def run_case(name, steps):
         sim = lw.Lwacm(lw.D2Q9, 1024, 1024, 1, 0.1024, lw.CAVITY, lid=(0.1, 0.0))
         sim.set_fields(z, z, z)
         sim.step(steps)
+    elif name == "cavity3d":  # D3Q19 256^3 diagonally driven cavity from rest (half-row kernel + walls)
+        z = torch.zeros((256, 256, 256), dtype=torch.float32, device="cuda")
+        sim = lw.Lwacm(lw.D3Q19, 256, 256, 256, 0.01, lw.CAVITY, lid=(2 ** 0.5 / 20, 2 ** 0.5 / 20, 0.0))
+        sim.set_fields(z, z, z, z)
+        sim.step(steps)
+    elif name == "bulk2d":  # D2Q9 4096^2 bulk-viscosity variant, gamma 0.4 (2D tiles 30x14)
+        sim = lw.Lwacm(lw.D2Q9, 4096, 4096, 1, 0.01, bulk_gamma=0.4)
+        sim.set_fields(*inputs.gtg_state(4096, 0.0))
+        sim.step(steps)
     else:
         raise SystemExit(f"unknown case {name}")
     sim.sync()
@@ -566,7 +575,7 @@ def main():
     ap.add_argument("--cpu-steps", type=int, default=40)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-variants", action="store_true")
-    ap.add_argument("--profile-case", choices=["adjoint", "ensemble", "cavity"],
+    ap.add_argument("--profile-case", choices=["adjoint", "ensemble", "cavity", "cavity3d", "bulk2d"],
                     help="run one variant workload for --steps steps without timing (for profilers)")
     args = ap.parse_args()
     if args.warmup < 3:

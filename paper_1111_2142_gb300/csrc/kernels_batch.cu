@@ -149,32 +149,33 @@ __device__ __forceinline__ void tile2_core(const T *__restrict__ in, T *__restri
         const float a9 = rho * nu * 2.f, b9 = rho * 0.5f, k9 = K * (1.f / 9.f);        // axis, w = 1/9
         const float a36 = rho * nu * 0.5f, b36 = rho * 0.125f, k36 = K * (1.f / 36.f);  // diagonal, w = 1/36
         const float e[4] = {u, v, u + v, u - v};
-        float inc[8] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+        // BULK: Df - a Df^o of the pair (c, -c) is an even part plus an odd part
+        // proportional to e = c.u; with P = Pxx + Pyy and T = rho h (1 - a) / 4
+        //   axis:     rho h (1 - P - h) / 2  -+ 2 T e
+        //   diagonal: rho h (h + P) / 4      +- T e
+        //   rest:     rho h (h - 2 + P)
+        // (they sum to 0 in mass and momentum and to 2 rho h in the trace)
+        float cax = 0.f, cdg = 0.f, oax = 0.f, odg = 0.f;
         if (BULK) {
             const float h = 0.5f * gamma * ldf(in + 3 * fstride + k), rh = rho * h;
-            const float pxx = fmaf(u, u, 1.f / 3.f), pyy = fmaf(v, v, 1.f / 3.f);
-            // A, B per component (c = +1, -1, 0) and ax = ay = 1/2 for a moving component
-            const float Ap = 0.5f * (pxx + u), Am = 0.5f * (pxx - u), A0 = 1.f - pxx;
-            const float Bp = 0.5f * (pyy + v), Bm = 0.5f * (pyy - v), B0 = 1.f - pyy;
-            // link order (1,0) (-1,0) (0,1) (0,-1) (1,1) (-1,-1) (1,-1) (-1,1)
-            const float Al[8] = {Ap, Am, A0, A0, Ap, Am, Ap, Am}, Bl[8] = {B0, B0, Bp, Bm, Bp, Bm, Bm, Bp};
-            const int cxl[8] = {1, -1, 0, 0, 1, -1, 1, -1}, cyl[8] = {0, 0, 1, -1, 1, -1, -1, 1};
-#pragma unroll
-            for (int i = 0; i < 8; ++i) {
-                const float ax = cxl[i] ? 0.5f : -1.f, ay = cyl[i] ? 0.5f : -1.f;
-                const float df = rh * fmaf(ax * ay, h, fmaf(ax, Bl[i], ay * Al[i]));
-                const float dfo = rh * (0.5f * fmaf(ax * cyl[i], v, ay * cxl[i] * u));
-                inc[i] = fmaf(-a, dfo, df);
-            }
-            df0 = rh * (h - B0 - A0);  // ax = ay = -1, no odd part
+            const float P = fmaf(u, u, fmaf(v, v, 2.f / 3.f));
+            cax = 0.5f * rh * (1.f - P - h);
+            cdg = 0.25f * rh * (h + P);
+            odg = 0.25f * rh * (1.f - a);
+            oax = -2.f * odg;
+            df0 = rh * (h - 2.f + P);
         }
 #pragma unroll
         for (int p = 0; p < 4; ++p) {
             const bool dg = p >= 2;
-            const float cm = fmaf((dg ? b36 : b9) * e[p], e[p], dg ? k36 : k9);
-            const float A = dg ? a36 : a9;
-            G[2 * p][threadIdx.x] = fmaf(A, e[p], cm) + inc[2 * p];
-            G[2 * p + 1][threadIdx.x] = fmaf(-A, e[p], cm) + inc[2 * p + 1];
+            float cm = fmaf((dg ? b36 : b9) * e[p], e[p], dg ? k36 : k9);
+            float A = dg ? a36 : a9;
+            if (BULK) {  // (no + 0.f in the plain kernel: it would not fold away)
+                cm += dg ? cdg : cax;
+                A += dg ? odg : oax;
+            }
+            G[2 * p][threadIdx.x] = fmaf(A, e[p], cm);
+            G[2 * p + 1][threadIdx.x] = fmaf(-A, e[p], cm);
         }
     }
     __syncthreads();
@@ -212,8 +213,9 @@ __device__ __forceinline__ void tile2_core(const T *__restrict__ in, T *__restri
                 fix(g8, 8, -1, 1);
             }
         }
-        const float g0 = fmaf(4.f / 9.f, K, df0);  // rest link (df0 = 0 without BULK)
-        const float dd = g0 + (((g1 + g2) + (g3 + g4)) + ((g5 + g6) + (g7 + g8)));
+        const float s8 = ((g1 + g2) + (g3 + g4)) + ((g5 + g6) + (g7 + g8));
+        const float g0 = BULK ? fmaf(4.f / 9.f, K, df0) : 0.f;  // BULK: the rest link
+        const float dd = BULK ? g0 + s8 : fmaf(4.f / 9.f, K, s8);
         const float ar = a * rho;
         float jx = fmaf(ar, u, (g1 - g2) + ((g5 - g6) + (g7 - g8)));
         float jy = fmaf(ar, v, (g3 - g4) + ((g5 - g6) - (g7 - g8)));
