@@ -116,11 +116,16 @@ struct Force2 {
 // A = 1 - Pxx (c_x = 0) or (Pxx + c_x u)/2, ax = -1 or 1/2 (B, ay likewise in y),
 // Pxx = 1/3 + u^2, Pyy = 1/3 + v^2; the rest link's increment stays with the node;
 // the node stores Tr^(+) - Tr^(e) = sum_i (|c_i|^2 - 2/3) g_i / (1 + d+) - |u+|^2.
-template <int TW, int TH, typename T, bool WALLS = false, bool BULK = false>
+// With NUP (periodic; omega_p of Section 2.2, item 3) the density sums its link
+// values with s_p = s + sdelta: d+ gains sdelta sum_i w_i rho e_i over the upwind
+// sources; each source leaves W_p = w_p rho (c_p.u) of its four pairs in O, and the
+// node takes sum_p [W_p(x - c_p) - W_p(x + c_p)] (the -c link carries -W_p).
+template <int TW, int TH, typename T, bool WALLS = false, bool BULK = false, bool NUP = false>
 __device__ __forceinline__ void tile2_core(const T *__restrict__ in, T *__restrict__ out, long long base, int nx,
                                            int ny, long long fstride, float s, float a, int x0, int y0,
                                            float (*G)[(TW + 2) * (TH + 2)], const Walls2 &wl = Walls2{},
-                                           const Force2 &fc = Force2{}, float gamma = 0.f) {
+                                           const Force2 &fc = Force2{}, float gamma = 0.f,
+                                           float (*O)[(TW + 2) * (TH + 2)] = nullptr, float sdelta = 0.f) {
     constexpr int W = TW + 2;
     const int tx = threadIdx.x % W, ty = threadIdx.x / W;
     // periodic wrap of the frame (x0 + tx - 1 lies in [-1, x0 + TW], below 2 nx
@@ -176,6 +181,7 @@ __device__ __forceinline__ void tile2_core(const T *__restrict__ in, T *__restri
             }
             G[2 * p][threadIdx.x] = fmaf(A, e[p], cm);
             G[2 * p + 1][threadIdx.x] = fmaf(-A, e[p], cm);
+            if (NUP) O[p][threadIdx.x] = (dg ? rho * (1.f / 36.f) : rho * (1.f / 9.f)) * e[p];
         }
     }
     __syncthreads();
@@ -215,7 +221,12 @@ __device__ __forceinline__ void tile2_core(const T *__restrict__ in, T *__restri
         }
         const float s8 = ((g1 + g2) + (g3 + g4)) + ((g5 + g6) + (g7 + g8));
         const float g0 = BULK ? fmaf(4.f / 9.f, K, df0) : 0.f;  // BULK: the rest link
-        const float dd = BULK ? g0 + s8 : fmaf(4.f / 9.f, K, s8);
+        float dd = BULK ? g0 + s8 : fmaf(4.f / 9.f, K, s8);
+        if (NUP) {
+            const float dsp = (O[0][tid - 1] - O[0][tid + 1]) + (O[1][tid - W] - O[1][tid + W]) +
+                              ((O[2][tid - 1 - W] - O[2][tid + 1 + W]) + (O[3][tid - 1 + W] - O[3][tid + 1 - W]));
+            dd = fmaf(sdelta, dsp, dd);
+        }
         const float ar = a * rho;
         float jx = fmaf(ar, u, (g1 - g2) + ((g5 - g6) + (g7 - g8)));
         float jy = fmaf(ar, v, (g3 - g4) + ((g5 - g6) - (g7 - g8)));
@@ -251,16 +262,18 @@ __device__ __forceinline__ void tile2_update(const T *__restrict__ in, T *__rest
 }
 
 // one D2Q9 domain, walls included (no separate wall pass); tiles numbered row-major
-template <int TW, int TH, typename T, bool WALLS, bool BULK>
+template <int TW, int TH, typename T, bool WALLS, bool BULK, bool NUP>
 __global__ void __launch_bounds__((TW + 2) * (TH + 2)) k_d2q9_tiles(const T *__restrict__ in, T *__restrict__ out,
                                                                    int nx, int ny, long long fstride, float s,
                                                                    float a, int tilesx, long long ntiles, Walls2 wl,
-                                                                   Force2 fc, float gamma) {
+                                                                   Force2 fc, float gamma, float sdelta) {
     __shared__ float G[8][(TW + 2) * (TH + 2)];
+    __shared__ float O[NUP ? 4 : 1][(TW + 2) * (TH + 2)];
     for (long long t = blockIdx.x; t < ntiles; t += gridDim.x) {
         const unsigned tu = (unsigned)t, ty = tu / (unsigned)tilesx;  // fewer than 2^32 tiles
-        tile2_core<TW, TH, T, WALLS, BULK>(in, out, 0, nx, ny, fstride, s, a,
-                                           (int)(tu - ty * (unsigned)tilesx) * TW, (int)ty * TH, G, wl, fc, gamma);
+        tile2_core<TW, TH, T, WALLS, BULK, NUP>(in, out, 0, nx, ny, fstride, s, a,
+                                                (int)(tu - ty * (unsigned)tilesx) * TW, (int)ty * TH, G, wl, fc,
+                                                gamma, O, sdelta);
     }
 }
 
@@ -399,11 +412,11 @@ cudaError_t tiles_storage(int storage, const void *in, void *out, void *b0, void
     return cudaErrorInvalidValue;
 }
 
-template <int TW, int TH, typename T, bool WALLS, bool BULK = false>
+template <int TW, int TH, typename T, bool WALLS, bool BULK = false, bool NUP = false>
 cudaError_t single_w(const void *in, void *out, const StepParams &p, const Walls2 &wl, cudaStream_t st) {
     constexpr int NT = (TW + 2) * (TH + 2);
     static DevSlots cap;
-    const int g = max_grid(k_d2q9_tiles<TW, TH, T, WALLS, BULK>, NT, cap);
+    const int g = max_grid(k_d2q9_tiles<TW, TH, T, WALLS, BULK, NUP>, NT, cap);
     if (g < 1) return cudaErrorNotSupported;
     const int tilesx = (p.nx + TW - 1) / TW;
     const long long ntiles = (long long)tilesx * ((p.ny + TH - 1) / TH);
@@ -414,14 +427,15 @@ cudaError_t single_w(const void *in, void *out, const StepParams &p, const Walls
     fc.gy = p.has_force ? p.force[1] : 0.f;
     fc.field = p.gfield;
     fc.fstride = p.fstride;
-    k_d2q9_tiles<TW, TH, T, WALLS, BULK><<<(unsigned)grid, NT, 0, st>>>(
-        (const T *)in, (T *)out, p.nx, p.ny, p.fstride, p.s, p.a, tilesx, ntiles, wl, fc, p.gamma);
+    k_d2q9_tiles<TW, TH, T, WALLS, BULK, NUP><<<(unsigned)grid, NT, 0, st>>>(
+        (const T *)in, (T *)out, p.nx, p.ny, p.fstride, p.s, p.a, tilesx, ntiles, wl, fc, p.gamma, p.sdelta);
     return cudaGetLastError();
 }
 
 template <int TW, int TH, typename T>
 cudaError_t single_t(const void *in, void *out, const StepParams &p, cudaStream_t st) {
-    if (p.bulk) return single_w<TW, TH, T, false, true>(in, out, p, Walls2{}, st);  // periodic only
+    if (p.bulk) return single_w<TW, TH, T, false, true>(in, out, p, Walls2{}, st);         // periodic only
+    if (p.sdelta != 0.f) return single_w<TW, TH, T, false, false, true>(in, out, p, Walls2{}, st);  // periodic
     if (p.bc == BC_PERIODIC) return single_w<TW, TH, T, false>(in, out, p, Walls2{}, st);
     Walls2 wl;
     wl.wx = p.walled[0];
@@ -487,7 +501,9 @@ bool batch_shape_supported(int Q, int storage, int k) {
 }
 
 bool tiles2d_supported(int Q, int storage, const StepParams &p) {
-    return Q == 9 && p.nz == 1 && p.sdelta == 0.f && !p.scalar && (!p.bulk || p.bc == BC_PERIODIC) &&
+    // omega_p and the bulk variant: periodic, not together (the generic kernel takes both)
+    const bool variant_ok = (p.sdelta == 0.f || (!p.bulk && p.bc == BC_PERIODIC)) && (!p.bulk || p.bc == BC_PERIODIC);
+    return Q == 9 && p.nz == 1 && variant_ok && !p.scalar &&
            (storage == STORE_F32 || storage == STORE_BF16 || storage == STORE_F16);
 }
 

@@ -475,16 +475,20 @@ def test_full_size_256_thousand_steps(lw, storage):
         assert 0.97 < ratio < 1.002
 
 
+@pytest.mark.parametrize("kernel", [1, 0])
 @pytest.mark.parametrize("Q,shape", [(9, (23, 37)), (9, (64, 64)), (19, (9, 11, 13)), (19, (8, 16, 128))])
-def test_nu_p_matches_oracle(lw, Q, shape):
+def test_nu_p_matches_oracle(lw, Q, shape, kernel):
     """omega_p (LWACM_OPT_NU_P): the density sums link values built with 18 nu_p,
-    the momentum with 18 nu; runs on the generic kernel."""
+    the momentum with 18 nu; on the generic kernel (1) and on the automatic choice
+    (0: the 2D-tile kernel for D2Q9, the generic kernel for D3Q19)."""
     f = inputs.smooth_random(shape, seed=17, u_amp=0.05, d_amp=0.01)
     nz = 1 if Q == 9 else shape[0]
     ny, nx = shape[-2], shape[-1]
     sim = lw.Lwacm(Q, nx, ny, nz, 0.01)
     sim.set_option(lw.OPT_NU_P, 0.12)
-    assert sim.kernel_name.startswith("generic")
+    if kernel:
+        sim.set_option(lw.OPT_KERNEL, kernel)
+    assert sim.kernel_name.startswith("tiles2d" if (Q == 9 and kernel == 0) else "generic"), sim.kernel_name
     sim.set_fields(*f)
     sim.step(40)
     got = sim.get_fields()
@@ -493,6 +497,26 @@ def test_nu_p_matches_oracle(lw, Q, shape):
     eu, ed = errs(got, ref, 0.05)
     print(f"nu_p Q{Q} {shape}: du/U={eu:.2e} dd/d={ed:.2e}")
     assert eu < 1e-5 and ed < 1e-4
+
+
+@pytest.mark.parametrize("tile", [1, 2, 3, 4, 5, 6])
+def test_nu_p_tile_shapes(lw, tile):
+    """omega_p on every 2D-tile shape, domains narrower and wider than the tiles
+    (ragged edges, wrap across one tile), 60 steps, against the oracle."""
+    for shape in ((23, 37), (33, 130), (5, 7)):
+        f = inputs.smooth_random(shape, seed=19, u_amp=0.05, d_amp=0.01)
+        ny, nx = shape
+        sim = lw.Lwacm(9, nx, ny, 1, 0.01)
+        sim.set_option(lw.OPT_NU_P, 0.12)
+        sim.set_option(lw.OPT_BATCH_TILE, tile)
+        assert sim.kernel_name.startswith("tiles2d")
+        sim.set_fields(*f)
+        sim.step(60)
+        got = sim.get_fields()
+        sim.close()
+        ref = oracle.step_nu_p(9, *f, nu=0.01, nu_p=0.12, nsteps=60)
+        eu, ed = errs(got, ref, 0.05)
+        assert eu < 1e-5 and ed < 1e-4, (tile, shape, eu, ed)
 
 
 def test_large_domain_sampled_nodes(lw):
