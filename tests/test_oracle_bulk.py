@@ -163,3 +163,41 @@ def test_shear_wave_unchanged():
         rates.append(-np.log(np.sum(out[2][0] * np.sin(k * x)) / np.sum(v0[0] * np.sin(k * x))) / 50)
     assert rates[1] == pytest.approx(rates[0], rel=1e-7)
     assert rates[0] == pytest.approx(0.02 * k * k, rel=2e-3)  # nu k^2 of the shear wave
+
+
+def test_increment_regrouped_per_link_pair():
+    """The increment f^(e*) - f^(e) of the oracle, split per link pair (c, -c) into
+    its even and odd parts, has closed forms (the 2D-tile kernel builds them this
+    way), with h = gamma (Tr^(+) - Tr^(e)) / 2 and P = Pxx + Pyy = 2/3 + |u|^2:
+      axis:     even rho h (1 - P - h) / 2,  odd -rho h (c.u) / 2
+      diagonal: even rho h (h + P) / 4,      odd  rho h (c.u) / 4
+      rest:     rho h (h - 2 + P)
+    (the product form of Eq. d2q9_equilibrium_gen moved from Pxx, Pyy to Pxx + h,
+    Pyy + h, Eq. quasi-equilibrium). A slip in the kernel's regrouping is a slip in
+    one of these lines."""
+    c = oracle.lattice(9)[0][:, :2].astype(int)
+    opp = [int(np.flatnonzero((c == -ci).all(axis=1))[0]) for ci in c]
+    rng = np.random.default_rng(8)
+    for _ in range(200):
+        rho = 1.0 + 0.05 * rng.standard_normal()
+        u = 0.08 * rng.standard_normal(2)
+        tre = 2.0 / 3.0 + u @ u
+        trp = tre + 0.05 * rng.standard_normal()
+        g = rng.uniform(-0.9, 0.9)
+        fe, _ = oracle.equilibria(9, rho, [u[0], u[1], 0.0])
+        df = oracle.feq_star(rho, u, trp, g) - fe
+        h = 0.5 * g * (trp - tre)
+        P = 2.0 / 3.0 + u @ u
+        for i, ci in enumerate(c):
+            n2 = int(ci @ ci)
+            if n2 == 0:
+                assert abs(df[i] - rho * h * (h - 2.0 + P)) < 1e-15
+                continue
+            even, odd = 0.5 * (df[i] + df[opp[i]]), 0.5 * (df[i] - df[opp[i]])
+            e = float(ci @ u)
+            if n2 == 1:
+                assert abs(even - 0.5 * rho * h * (1.0 - P - h)) < 1e-15
+                assert abs(odd + 0.5 * rho * h * e) < 1e-15
+            else:
+                assert abs(even - 0.25 * rho * h * (h + P)) < 1e-15
+                assert abs(odd - 0.25 * rho * h * e) < 1e-15
