@@ -95,9 +95,9 @@ enum {
                               domains with the wall pass after them; 2 and 3 need FP32
                               storage, 5 takes FP32, BF16 and FP16: LWACM_E_UNSUPPORTED
                               otherwise); 6 = D2Q9 2D-tile kernel (any boundary, walls
-                              and forcing applied in the kernel; omega_p or the
-                              bulk-viscosity variant on periodic domains, not both
-                              and not the scalar; tile shape from
+                              and forcing applied in the kernel; omega_p and the
+                              bulk-viscosity variant (alone or together) on periodic
+                              domains; not the scalar; tile shape from
                               LWACM_OPT_BATCH_TILE, 30x14 when 0). The automatic choice
                               takes 5, else 3, else 2, else 6, else 1. */
     LWACM_OPT_BATCH_MODE = 10, /* batched contexts: 0 = one launch per step, replayed
@@ -124,9 +124,8 @@ enum {
                                      relaxed with omega_p, momentum with omega): in (0,
                                      1/6], or 0 = nu (default). Single periodic domains
                                      only (LWACM_E_UNSUPPORTED otherwise); runs on the
-                                     D2Q9 2D-tile kernel (without the bulk-viscosity
-                                     variant), else on the generic kernel; the adjoint
-                                     refuses nu_p != nu. */
+                                     D2Q9 2D-tile kernel, else on the generic kernel;
+                                     the adjoint refuses nu_p != nu. */
     LWACM_OPT_SCALAR_ALPHA = 15,  /* > 0: carry a passive scalar T (Eq. ACM2.0t, the
                                      thermal LW-ACM of Appendix "Asymptotic analysis for
                                      energy equation") with diffusivity alpha in (0, 1/6]
@@ -154,8 +153,7 @@ enum {
                                      periodic D2Q9 domains only, not with the scalar
                                      (LWACM_E_UNSUPPORTED). With LWACM_OPT_NU_P the density
                                      is relaxed with omega_p and the momentum and the
-                                     trace with omega. Runs on the D2Q9 2D-tile kernel
-                                     (the generic kernel with LWACM_OPT_NU_P). */
+                                     trace with omega. Runs on the D2Q9 2D-tile kernel. */
 };
 
 /* Create a single-domain context.

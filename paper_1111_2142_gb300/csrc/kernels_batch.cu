@@ -119,7 +119,13 @@ struct Force2 {
 // With NUP (periodic; omega_p of Section 2.2, item 3) the density sums its link
 // values with s_p = s + sdelta: d+ gains sdelta sum_i w_i rho e_i over the upwind
 // sources; each source leaves W_p = w_p rho (c_p.u) of its four pairs in O, and the
-// node takes sum_p [W_p(x - c_p) - W_p(x + c_p)] (the -c link carries -W_p).
+// node takes sum_p [W_p(x - c_p) - W_p(x + c_p)] (the -c link carries -W_p). With
+// BULK as well the density also takes (sdelta / 3) sum_i Df^o_i over the upwind
+// sources (it pre-combines the increment with a_p, the momentum and the trace keep
+// a): Df^o = kappa (c.u) with kappa = -rho h / 2 (axis), rho h / 4 (diagonal), so
+// W_p becomes (w_p rho + kappa_p / 3) (c_p.u); the trace is normalised by the
+// zeroth moment of the distribution built with a (the density before the sdelta
+// terms).
 template <int TW, int TH, typename T, bool WALLS = false, bool BULK = false, bool NUP = false>
 __device__ __forceinline__ void tile2_core(const T *__restrict__ in, T *__restrict__ out, long long base, int nx,
                                            int ny, long long fstride, float s, float a, int x0, int y0,
@@ -160,7 +166,7 @@ __device__ __forceinline__ void tile2_core(const T *__restrict__ in, T *__restri
         //   diagonal: rho h (h + P) / 4      +- T e
         //   rest:     rho h (h - 2 + P)
         // (they sum to 0 in mass and momentum and to 2 rho h in the trace)
-        float cax = 0.f, cdg = 0.f, oax = 0.f, odg = 0.f;
+        float cax = 0.f, cdg = 0.f, oax = 0.f, odg = 0.f, kax = 0.f, kdg = 0.f;
         if (BULK) {
             const float h = 0.5f * gamma * ldf(in + 3 * fstride + k), rh = rho * h;
             const float P = fmaf(u, u, fmaf(v, v, 2.f / 3.f));
@@ -169,6 +175,8 @@ __device__ __forceinline__ void tile2_core(const T *__restrict__ in, T *__restri
             odg = 0.25f * rh * (1.f - a);
             oax = -2.f * odg;
             df0 = rh * (h - 2.f + P);
+            kax = -0.5f * rh;
+            kdg = 0.25f * rh;
         }
 #pragma unroll
         for (int p = 0; p < 4; ++p) {
@@ -181,7 +189,9 @@ __device__ __forceinline__ void tile2_core(const T *__restrict__ in, T *__restri
             }
             G[2 * p][threadIdx.x] = fmaf(A, e[p], cm);
             G[2 * p + 1][threadIdx.x] = fmaf(-A, e[p], cm);
-            if (NUP) O[p][threadIdx.x] = (dg ? rho * (1.f / 36.f) : rho * (1.f / 9.f)) * e[p];
+            if (NUP && !BULK) O[p][threadIdx.x] = (dg ? rho * (1.f / 36.f) : rho * (1.f / 9.f)) * e[p];
+            if (NUP && BULK)
+                O[p][threadIdx.x] = fmaf(1.f / 3.f, dg ? kdg : kax, dg ? rho * (1.f / 36.f) : rho * (1.f / 9.f)) * e[p];
         }
     }
     __syncthreads();
@@ -222,6 +232,7 @@ __device__ __forceinline__ void tile2_core(const T *__restrict__ in, T *__restri
         const float s8 = ((g1 + g2) + (g3 + g4)) + ((g5 + g6) + (g7 + g8));
         const float g0 = BULK ? fmaf(4.f / 9.f, K, df0) : 0.f;  // BULK: the rest link
         float dd = BULK ? g0 + s8 : fmaf(4.f / 9.f, K, s8);
+        const float rna = 1.f + dd;  // BULK: the trace's normalisation
         if (NUP) {
             const float dsp = (O[0][tid - 1] - O[0][tid + 1]) + (O[1][tid - W] - O[1][tid + W]) +
                               ((O[2][tid - 1 - W] - O[2][tid + 1 + W]) + (O[3][tid - 1 + W] - O[3][tid + 1 - W]));
@@ -247,7 +258,7 @@ __device__ __forceinline__ void tile2_core(const T *__restrict__ in, T *__restri
         if (BULK) {  // |c|^2 - 2/3: rest -2/3, axis 1/3, diagonal 4/3
             const float trs = fmaf(-2.f / 3.f, g0,
                                    fmaf(1.f / 3.f, (g1 + g2) + (g3 + g4), (4.f / 3.f) * ((g5 + g6) + (g7 + g8))));
-            stf(out + 3 * fstride + k, trs / rn - fmaf(uxn, uxn, uyn * uyn));
+            stf(out + 3 * fstride + k, trs / rna - fmaf(uxn, uxn, uyn * uyn));
         }
     }
     __syncthreads();  // G is rewritten by the next tile
@@ -434,6 +445,7 @@ cudaError_t single_w(const void *in, void *out, const StepParams &p, const Walls
 
 template <int TW, int TH, typename T>
 cudaError_t single_t(const void *in, void *out, const StepParams &p, cudaStream_t st) {
+    if (p.bulk && p.sdelta != 0.f) return single_w<TW, TH, T, false, true, true>(in, out, p, Walls2{}, st);
     if (p.bulk) return single_w<TW, TH, T, false, true>(in, out, p, Walls2{}, st);         // periodic only
     if (p.sdelta != 0.f) return single_w<TW, TH, T, false, false, true>(in, out, p, Walls2{}, st);  // periodic
     if (p.bc == BC_PERIODIC) return single_w<TW, TH, T, false>(in, out, p, Walls2{}, st);
@@ -501,8 +513,8 @@ bool batch_shape_supported(int Q, int storage, int k) {
 }
 
 bool tiles2d_supported(int Q, int storage, const StepParams &p) {
-    // omega_p and the bulk variant: periodic, not together (the generic kernel takes both)
-    const bool variant_ok = (p.sdelta == 0.f || (!p.bulk && p.bc == BC_PERIODIC)) && (!p.bulk || p.bc == BC_PERIODIC);
+    // omega_p and the bulk variant (alone or together): periodic domains
+    const bool variant_ok = (p.sdelta == 0.f && !p.bulk) || p.bc == BC_PERIODIC;
     return Q == 9 && p.nz == 1 && variant_ok && !p.scalar &&
            (storage == STORE_F32 || storage == STORE_BF16 || storage == STORE_F16);
 }

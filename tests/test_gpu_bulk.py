@@ -24,8 +24,8 @@ def lw():
 
 
 def _run(lw, fields, nu, gamma, steps, nu_p=None, kernel=0, tile=0):
-    """kernel 0: the automatic choice, the 2D-tile kernel (the generic kernel with
-    omega_p); 1: the generic kernel; tile: the 2D-tile shape (0: 30 x 14)."""
+    """kernel 0: the automatic choice, the 2D-tile kernel; 1: the generic kernel;
+    tile: the 2D-tile shape (0: 30 x 14)."""
     ny, nx = fields[0].shape
     sim = lw.Lwacm(9, nx, ny, 1, nu, bulk_gamma=gamma)
     if nu_p:
@@ -34,7 +34,7 @@ def _run(lw, fields, nu, gamma, steps, nu_p=None, kernel=0, tile=0):
         sim.set_option(lw.OPT_BATCH_TILE, tile)
     if kernel:
         sim.set_option(lw.OPT_KERNEL, kernel)
-    assert sim.kernel_name.startswith("generic" if (nu_p or kernel == 1) else "tiles2d"), sim.kernel_name
+    assert sim.kernel_name.startswith("generic" if kernel == 1 else "tiles2d"), sim.kernel_name
     sim.set_fields(*fields)
     tr0 = sim.get_trace()
     sim.step(steps)
@@ -64,10 +64,11 @@ def test_bulk_matches_oracle(lw, gamma, shape, kernel):
     assert max(float(np.max(np.abs(a - b))) for a, b in zip(plain[1:], ref[1:3])) / u_scale > 1e-3
 
 
-def test_bulk_with_omega_p_matches_oracle(lw):
+@pytest.mark.parametrize("kernel", [0, 1])
+def test_bulk_with_omega_p_matches_oracle(lw, kernel):
     """Both improvements of Section 3.2 (omega_p and gamma) on one context."""
     f = inputs.smooth_random((40, 48), seed=33, u_amp=0.05, d_amp=0.01)
-    got, tr, _ = _run(lw, f, 0.02, 0.4, 200, nu_p=0.1)
+    got, tr, _ = _run(lw, f, 0.02, 0.4, 200, nu_p=0.1, kernel=kernel)
     ref = oracle.step_bulk(*f, nu=0.02, nu_p=0.1, gamma=0.4, nsteps=200)
     eu = max(float(np.max(np.abs(g - r))) for g, r in zip(got[1:], ref[1:3])) / 0.05
     ed = float(np.max(np.abs(got[0] - ref[0]))) / max(float(np.max(np.abs(ref[0]))), 3 * 0.05 ** 2)
@@ -93,13 +94,15 @@ def test_longitudinal_wave_matches_oracle(lw):
 
 
 @pytest.mark.parametrize("tile", [1, 2, 3, 4, 5, 6])
-def test_bulk_tile_shapes(lw, tile):
+@pytest.mark.parametrize("nu_p", [None, 0.1])
+def test_bulk_tile_shapes(lw, tile, nu_p):
     """Every 2D-tile shape on domains narrower and wider than the tiles (ragged
-    edges, wrap across one tile), 60 steps at gamma = 0.4, against the oracle."""
+    edges, wrap across one tile), 60 steps at gamma = 0.4, alone and with omega_p,
+    against the oracle."""
     for shape in ((23, 37), (33, 130), (5, 7)):
         f = inputs.smooth_random(shape, seed=35, u_amp=0.05, d_amp=0.01)
-        got, tr, _ = _run(lw, f, 0.02, 0.4, 60, tile=tile)
-        ref = oracle.step_bulk(*f, nu=0.02, gamma=0.4, nsteps=60)
+        got, tr, _ = _run(lw, f, 0.02, 0.4, 60, tile=tile, nu_p=nu_p)
+        ref = oracle.step_bulk(*f, nu=0.02, gamma=0.4, nu_p=nu_p, nsteps=60)
         eu = max(float(np.max(np.abs(g - r))) for g, r in zip(got[1:], ref[1:3])) / 0.05
         ed = float(np.max(np.abs(got[0] - ref[0]))) / max(float(np.max(np.abs(ref[0]))), 3 * 0.05 ** 2)
         dev = ref[3] - (2.0 / 3.0 + ref[1] ** 2 + ref[2] ** 2)
