@@ -251,3 +251,29 @@ def test_missing_library_fails_loudly(monkeypatch, tmp_path):
     monkeypatch.setattr(lw, "LIB_PATH", str(tmp_path / "liblwacm.so"))
     with pytest.raises(RuntimeError, match="no CPU fallback"):
         lw.load()
+
+
+def test_d2q9_variant_kernel_choice(lib):
+    """The automatic choice for a periodic D2Q9 domain (decided without a device):
+    the 2D-tile kernel for the plain scheme, omega_p, the bulk-viscosity variant
+    and both together; the generic kernel for the passive scalar and for omega_p
+    on D3Q19."""
+    from paper_1111_2142_gb300 import lwacm as lw
+    st, h = _create(lib, 9, 40, 24, 1, 0.02, 0)
+    assert st == lw.OK
+    name = lambda: lib.lwacm_kernel_name(h).decode()
+    assert name() == "tiles2d_d2q9_30x14"
+    assert lib.lwacm_set_option(h, lw.OPT_NU_P, 0.1) == lw.OK
+    assert name() == "tiles2d_d2q9_30x14"
+    assert lib.lwacm_set_option(h, lw.OPT_BULK_GAMMA, 0.4) == lw.OK
+    assert name() == "tiles2d_d2q9_30x14"  # both improvements of Section 3.2
+    assert lib.lwacm_set_option(h, lw.OPT_NU_P, 0.0) == lw.OK
+    assert name() == "tiles2d_d2q9_30x14"
+    assert lib.lwacm_set_option(h, lw.OPT_BULK_GAMMA, 0.0) == lw.OK
+    assert lib.lwacm_set_option(h, lw.OPT_SCALAR_ALPHA, 0.05) == lw.OK
+    assert name() == "generic_d2q9"
+    lib.lwacm_destroy(h)
+    st, h3 = _create(lib, 19, 16, 8, 4, 0.02, 0)
+    assert lib.lwacm_set_option(h3, lw.OPT_NU_P, 0.1) == lw.OK
+    assert lib.lwacm_kernel_name(h3).decode() == "generic_d3q19"
+    lib.lwacm_destroy(h3)
