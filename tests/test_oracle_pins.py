@@ -238,6 +238,33 @@ def test_cavity_mirror_symmetry():
     assert maxdiff(a, (F(out[0]), -F(out[1]), F(out[2]))) < 1e-15
 
 
+def test_cavity_3d_diagonal_lid_symmetries():
+    """Section 3.3.2's cubic cavity with the diagonal lid (a, a, 0) on the top z
+    face: swapping x and y (with u and v) and reflecting x with the lid's x
+    component reversed are exact symmetries of the 3D wall and lid rules, so a
+    wrong index or sign in one axis's wall treatment breaks one of them."""
+    n, a = 7, 0.05
+    f = inputs.smooth_random((n, n, n), seed=24, u_amp=0.04, d_amp=0.005)
+    out = oracle.step(19, *f, nu=0.03, bc=oracle.CAVITY, lid=(a, a, 0.0), nsteps=5)
+
+    def swap(d, ux, uy, uz):  # arrays (z, y, x): x <-> y
+        T = lambda q: np.transpose(q, (0, 2, 1))
+        return T(d), T(uy), T(ux), T(uz)
+
+    b = oracle.step(19, *swap(*f), nu=0.03, bc=oracle.CAVITY, lid=(a, a, 0.0), nsteps=5)
+    assert maxdiff(b, swap(*out)) < 1e-15
+
+    def refl(d, ux, uy, uz):  # x -> -x about the box centre
+        F = lambda q: q[:, :, ::-1]
+        return F(d), -F(ux), F(uy), F(uz)
+
+    c = oracle.step(19, *refl(*f), nu=0.03, bc=oracle.CAVITY, lid=(-a, a, 0.0), nsteps=5)
+    assert maxdiff(c, refl(*out)) < 1e-15
+    # the lid drives the flow: without it the state differs
+    r = oracle.step(19, *f, nu=0.03, bc=oracle.CAVITY, lid=(0.0, 0.0, 0.0), nsteps=5)
+    assert maxdiff(r, out) > 1e-4
+
+
 def test_d3q19_z_uniform_equals_d2q9():
     """D3Q19 weights project onto D2Q9 (1/3 + 2/18 = 4/9, 1/18 + 2/36 = 1/9, 1/36):
     on z-uniform data with u_z = 0 the two lattices give the same update."""
