@@ -539,6 +539,4 @@ cudaError_t launch_diagnostics(int storage, const void *f, long long fstride, lo
     return cudaErrorInvalidValue;
 }
 
-long long wall_node_count(const StepParams &p, int Q) { return boundary_count(p, Q == 9 ? 2 : 3); }
-
 }  // namespace lwacm

@@ -20,7 +20,6 @@ cudaError_t launch_step_generic(int Q, int storage, const void *in, void *out,
                                 const StepParams &p, cudaStream_t st);
 cudaError_t launch_wall_pass(int Q, int storage, const void *in, void *out, const StepParams &p,
                              cudaStream_t st);
-long long wall_node_count(const StepParams &p, int Q);
 cudaError_t launch_convert_in(int storage, int src_dtype, const void *src, void *dst, long long n,
                               cudaStream_t st);
 cudaError_t launch_convert_out(int storage, int dst_dtype, const void *src, void *dst, long long n,
