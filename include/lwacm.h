@@ -88,18 +88,17 @@ enum {
     LWACM_OPT_GRAPH_CHUNK = 8, /* steps per captured CUDA graph in lwacm_step (even;
                                   0 disables graphs; default 64) */
     LWACM_OPT_KERNEL = 9,  /* interior kernel: 0 = automatic choice (default),
-                              1 = generic gather kernel, 2 = D3Q19 TMA row-tiled kernel,
-                              3 = D3Q19 register-prefetch z-march kernel, 5 = D3Q19 half-row
-                              TMA kernel (2, 3 and 5 need the plain scheme without
-                              forcing, nx in {128, 256} and ny % 8 == 0, and run walled
-                              domains with the wall pass after them; 2 and 3 need FP32
-                              storage, 5 takes FP32, BF16 and FP16: LWACM_E_UNSUPPORTED
-                              otherwise); 6 = D2Q9 2D-tile kernel (any boundary, walls
+                              1 = generic gather kernel, 5 = D3Q19 half-row TMA kernel
+                              (needs the plain scheme without forcing, nx in {128, 256}
+                              and ny % 8 == 0, and runs walled domains with the wall pass
+                              after it; FP32, BF16 and FP16 storage: LWACM_E_UNSUPPORTED
+                              otherwise); 2 and 3 (earlier row-tiled kernels, superseded
+                              by 5) are retired: LWACM_E_ARG; 6 = D2Q9 2D-tile kernel (any boundary, walls
                               and forcing applied in the kernel; omega_p and the
                               bulk-viscosity variant (alone or together) on periodic
                               domains; not the scalar; tile shape from
                               LWACM_OPT_BATCH_TILE, 30x14 when 0). The automatic choice
-                              takes 5, else 3, else 2, else 6, else 1. */
+                              takes 5, else 6, else 1. */
     LWACM_OPT_BATCH_MODE = 10, /* batched contexts: 0 = one launch per step, replayed
                                   from CUDA graphs (default); 1 = one persistent
                                   cooperative launch per lwacm_step call, with a
@@ -321,8 +320,9 @@ const char *lwacm_last_error(const lwacm_ctx *ctx);
  * keep the fastest (the paper has no counterpart; Section 2.4 discusses tuning the
  * implementation to the machine). The candidates are, for a batched context, every
  * tile layout (LWACM_OPT_BATCH_TILE) the lattice allows times both launch forms
- * (LWACM_OPT_BATCH_MODE); for a single domain, every interior kernel
- * (LWACM_OPT_KERNEL 5, 3, 2, 1) that supports it. Each is timed with CUDA events over
+ * (LWACM_OPT_BATCH_MODE); for a single domain, the interior kernels
+ * (LWACM_OPT_KERNEL 5 and 1, and for D2Q9 kernel 6 in every tile shape) that
+ * support it. Each is timed with CUDA events over
  * trial_steps steps (0 = 256) after a warm-up, from the rest state, on the bound
  * stream; the call synchronises.
  *
@@ -363,8 +363,11 @@ void lwacm_destroy(lwacm_ctx *ctx);
  * of 72 KiB inside this library (held on every GPU that loads the library until
  * the process exits), which limits n to LWACM_NOALLOC_MAX_N nodes; larger n
  * returns LWACM_E_RANGE without launching anything. The first call on each
- * device looks up that array's device address (with the device current), so
- * make the first call on a device before any stream capture. All calls share
+ * device looks up that array's device address (with the device current) and
+ * keeps it for the life of the process, so make the first call on a device
+ * before any stream capture; a cudaDeviceReset() of that device unloads the
+ * library's device code and leaves the kept address stale, so do not call this
+ * entry point on a device after resetting it. All calls share
  * the array: calls whose kernels overlap on the GPU (different streams, or
  * different host threads) race on it and must be ordered by the caller. Every
  * slot a call reads is written by that same call, so no clearing is needed.

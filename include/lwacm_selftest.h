@@ -1,7 +1,7 @@
 /*
  * lwacm_selftest.h — device self-tests of numerical building blocks the LW-ACM
  * kernels use (the paper has no counterpart). They let a test check, on the
- * GPU, a device function against the hardware's correctly rounded result.
+ * GPU, a device function against the correctly rounded result.
  */
 #ifndef LWACM_SELFTEST_H
 #define LWACM_SELFTEST_H
@@ -10,14 +10,20 @@
 extern "C" {
 #endif
 
-/* out_dev[k] = the reciprocal 1/x_dev[k] exactly as the row-tiled kernels compute
- * 1/rho for u = j/rho (step a5 of the update): the hardware's approximate
- * reciprocal refined by one Newton-Raphson step, r <- r + r (1 - x r).
- * x_dev, out_dev: caller-owned device arrays of n FP32 values; n in [1, 2^31).
- * Stream-ordered on `stream` (cudaStream_t; NULL = legacy default stream), not
- * synchronised. Errors: LWACM_E_ARG (null pointer, n out of range), LWACM_E_CUDA
- * (launch failure). Return values are lwacm_status codes (lwacm.h). */
-int lwacm_selftest_reciprocal(const float *x_dev, float *out_dev, long long n, void *stream);
+/* out_dev[k] = a_dev[k] / b_dev[k] exactly as the row-tiled kernels form the
+ * velocity u = j / rho (step a5 of the update, after Eq. ACM2.0b: the moments
+ * rho u and rho, divided): the correctly rounded reciprocal of the divisor and two
+ * FMA corrections of the quotient (Markstein's method), which give the IEEE
+ * round-to-nearest quotient for every normal quotient.
+ * packed != 0: elements in pairs (2k, 2k+1) through the FP32x2 form of the
+ * half-row kernel (an odd last element through the scalar form); packed == 0:
+ * every element through the scalar form.
+ * a_dev, b_dev, out_dev: caller-owned device arrays of n FP32 values; n in
+ * [1, 2^31). Stream-ordered on `stream` (cudaStream_t; NULL = legacy default
+ * stream), not synchronised. Errors: LWACM_E_ARG (null pointer, n out of range),
+ * LWACM_E_CUDA (launch failure). Return values are lwacm_status codes (lwacm.h). */
+int lwacm_selftest_quotient(const float *a_dev, const float *b_dev, float *out_dev, long long n, int packed,
+                            void *stream);
 
 #ifdef __cplusplus
 }

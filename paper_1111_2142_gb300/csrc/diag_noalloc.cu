@@ -99,7 +99,9 @@ __global__ void __launch_bounds__(kThreads) k_final(const double *__restrict__ p
 }
 
 // Host-side device address of g_partials, looked up once per device with that
-// device current (the symbol's host-side name is not a device address).
+// device current (the symbol's host-side name is not a device address), and kept
+// until the process exits: a cudaDeviceReset() of the device would make it stale,
+// which the header states as a limit of this entry point.
 std::mutex g_mu;
 double *g_addr[kMaxDevices] = {nullptr};
 

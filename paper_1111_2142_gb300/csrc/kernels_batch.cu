@@ -51,6 +51,7 @@ __device__ __forceinline__ void tile_update(const T *__restrict__ in, T *__restr
     p.fstride = bp.fstride;
     p.s = dm.s;
     p.a = dm.a;
+    p.am1 = dm.s * (-1.f / 3.f);
     p.wallc = 0.f;
     p.has_force = 0;
     p.gfield = nullptr;
@@ -238,9 +239,9 @@ __device__ __forceinline__ void tile2_core(const T *__restrict__ in, T *__restri
                               ((O[2][tid - 1 - W] - O[2][tid + 1 + W]) + (O[3][tid - 1 + W] - O[3][tid + 1 - W]));
             dd = fmaf(sdelta, dsp, dd);
         }
-        const float ar = a * rho;
-        float jx = fmaf(ar, u, (g1 - g2) + ((g5 - g6) + (g7 - g8)));
-        float jy = fmaf(ar, v, (g3 - g4) + ((g5 - g6) - (g7 - g8)));
+        const float m = post_factor(a, d, s * (-1.f / 3.f));  // a rho u = u + m u (post_combine)
+        float jx = post_combine((g1 - g2) + ((g5 - g6) + (g7 - g8)), m, u);
+        float jy = post_combine((g3 - g4) + ((g5 - g6) - (g7 - g8)), m, v);
         if (fc.on) {  // Eq. force: the odd part of f^(e)(rho(x,t), g) adds rho g to j
             jx = fmaf(rho, fc.gx, jx);
             jy = fmaf(rho, fc.gy, jy);

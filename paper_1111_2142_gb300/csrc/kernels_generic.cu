@@ -158,9 +158,10 @@ __device__ __forceinline__ void cavity_node_update(const T *__restrict__ in, T *
         if (cy) jy += cy > 0 ? g : -g;
         if (cz) jz += cz > 0 ? g : -g;
     }
-    jx = fmaf(p.a * rx, ux, jx);
-    jy = fmaf(p.a * rx, uy, jy);
-    jz = fmaf(p.a * rx, uz, jz);
+    const float mx = post_factor(p.a, dx, p.am1);  // a rho u = u + mx u (post_combine)
+    jx = post_combine(jx, mx, ux);
+    jy = post_combine(jy, mx, uy);
+    jz = post_combine(jz, mx, uz);
     if (p.has_force) {  // Eq. force
         jx = fmaf(rx, p.force[0], jx);
         jy = fmaf(rx, p.force[1], jy);
@@ -278,9 +279,10 @@ __device__ __forceinline__ void xface_patch(const T *__restrict__ in, T *__restr
         if (cy) jy += cy > 0 ? g : -g;
         if (cz) jz += cz > 0 ? g : -g;
     }
-    jx = fmaf(p.a * rx, ux, jx);
-    jy = fmaf(p.a * rx, uy, jy);
-    jz = fmaf(p.a * rx, uz, jz);
+    const float mx = post_factor(p.a, dx, p.am1);  // a rho u = u + mx u (post_combine)
+    jx = post_combine(jx, mx, ux);
+    jy = post_combine(jy, mx, uy);
+    jz = post_combine(jz, mx, uz);
     if (p.has_force) {  // Eq. force
         jx = fmaf(rx, p.force[0], jx);
         jy = fmaf(rx, p.force[1], jy);

@@ -59,13 +59,19 @@ __device__ __forceinline__ F2 mul2(F2 a, F2 b) { return __fmul2_rn(a, b); }
 __device__ __forceinline__ F2 fma2(F2 a, F2 b, F2 c) { return __ffma2_rn(a, b, c); }
 __device__ __forceinline__ F2 neg2(F2 a) { return __fmul2_rn(a, make_float2(-1.f, -1.f)); }
 
-// per-node constants of the moment form (see tile_common.cuh, NodeConst), per pair
+// Per-node constants of the moment form, per node pair: the velocity and, with
+// K = d - 3/2 rho |u|^2, the three coefficients of a link value
+// w [d + rho (s e + 9/2 e^2 - 3/2 |u|^2)] = w K + w rho s e + w 9/2 rho e^2 (e = c.u)
+// for the axis weight w = 1/18 (K1 = K/18, A1 = rho s/18 = rho nu, B1 = rho/4) and
+// the diagonal weight 1/36 (K2, A2, B2: half of those).
 struct NC2 {
     F2 U[2], V[2], W[2], K1[2], A1[2], B1[2], K2[2], A2[2], B2[2];
+    F2 M[2];  // a d - 6 nu: a rho u = u + M u (post_combine, lwacm_core.cuh)
 };
 
 template <typename T>
-__device__ __forceinline__ void node_consts2(NC2 &nc, const T *row, int rstride, int lane, float s18) {
+__device__ __forceinline__ void node_consts2(NC2 &nc, const T *row, int rstride, int lane, float s18,
+                                             float a = 0.f, float am1 = 0.f) {
     const float4 d4 = ld4(row + lane * VXH), u4 = ld4(row + rstride + lane * VXH);
     const float4 v4 = ld4(row + 2 * rstride + lane * VXH), w4 = ld4(row + 3 * rstride + lane * VXH);
     const F2 dd[2] = {make_float2(d4.x, d4.y), make_float2(d4.z, d4.w)};
@@ -86,6 +92,7 @@ __device__ __forceinline__ void node_consts2(NC2 &nc, const T *row, int rstride,
         nc.K2[j] = mul2(K, b2(1.f / 36.f));
         nc.A2[j] = mul2(rho, b2(0.5f * s18));
         nc.B2[j] = mul2(rho, b2(0.125f));
+        nc.M[j] = fma2(b2(a), dd[j], b2(am1));
     }
 }
 
@@ -263,7 +270,7 @@ __device__ __forceinline__ void phase_a(Acc &acc, const T *stg, float *xbuf, con
     float *up = xbuf + half * HALF, *dn = xbuf + XDIR + half * HALF;
     {
         NC2 nc;
-        node_consts2(nc, stg + (row + 1) * RL + half * HALF, TROWS * RL, lane, p.s18);
+        node_consts2(nc, stg + (row + 1) * RL + half * HALF, TROWS * RL, lane, p.s18, p.a, p.am1);
         // NH = 2: the boundary neighbour's constants (unused for NH = 1)
         const int nbx = lane < 16 ? (half * HALF + RL - 1) % RL : (half * HALF + HALF) % RL;
         const float sgn = lane < 16 ? 1.f : -1.f;
@@ -276,10 +283,10 @@ __device__ __forceinline__ void phase_a(Acc &acc, const T *stg, float *xbuf, con
             if (MODE == MID) {
                 acc[P0][j][3] = acc[P0][j][0];                       // jz so far = d so far
                 acc[P0][j][0] = fma2(b2(6.f), nc.K1[j], acc[P0][j][0]);  // rest link: w_0 K = K/3
-                const F2 ar = mul2(b2(p.a_s), nc.A1[j]);             // a rho (post-combine)
-                acc[P0][j][1] = fma2(ar, nc.U[j], acc[P0][j][1]);
-                acc[P0][j][2] = fma2(ar, nc.V[j], acc[P0][j][2]);
-                acc[P0][j][3] = fma2(ar, nc.W[j], acc[P0][j][3]);
+                // post-combine a rho u = u + M u, never rounding the O(1) factor a rho
+                acc[P0][j][1] = add2(fma2(nc.M[j], nc.U[j], acc[P0][j][1]), nc.U[j]);
+                acc[P0][j][2] = add2(fma2(nc.M[j], nc.V[j], acc[P0][j][2]), nc.V[j]);
+                acc[P0][j][3] = add2(fma2(nc.M[j], nc.W[j], acc[P0][j][3]), nc.W[j]);
             }
             if (MODE != LAST) acc[PP][j][0] = gp;  // first value of the plane ahead
             if (MODE != FIRST) {
@@ -421,18 +428,12 @@ __device__ __forceinline__ void phase_b(Acc &acc, const float *xbuf, T *out, con
             const long long rowoff =
                 ((long long)zfin * p.ny + col * ROWS + row) * p.nx + half * HALF + lane * VXH;
             T *op = out + rowoff;
-            F2 r[2];
-#pragma unroll
-            for (int j = 0; j < 2; ++j) {
-                // 1/rho: hardware approximation refined by one Newton-Raphson step
-                const F2 x = add2(b2(1.f), acc[PM][j][0]);
-                const F2 r0 = make_float2(__fdividef(1.0f, x.x), __fdividef(1.0f, x.y));
-                r[j] = fma2(r0, fma2(neg2(x), r0, b2(1.f)), r0);
-            }
+            // u = j / rho, correctly rounded (tile_common.cuh, div_apply2)
+            const Div2 r[2] = {div_prep2(add2(b2(1.f), acc[PM][0][0])), div_prep2(add2(b2(1.f), acc[PM][1][0]))};
             st4(op, acc[PM][0][0].x, acc[PM][0][0].y, acc[PM][1][0].x, acc[PM][1][0].y);
 #pragma unroll
             for (int c = 1; c < 4; ++c) {
-                const F2 v0 = mul2(acc[PM][0][c], r[0]), v1 = mul2(acc[PM][1][c], r[1]);
+                const F2 v0 = div_apply2(acc[PM][0][c], r[0]), v1 = div_apply2(acc[PM][1][c], r[1]);
                 st4(op + c * p.fstride, v0.x, v0.y, v1.x, v1.y);
             }
         }
@@ -637,8 +638,8 @@ static cudaError_t launch_nh(const void *in, void *out, const StepParams &sp, cu
     p.fstride = sp.fstride;
     const double nu = (double)sp.s / 18.0;
     p.s18 = (float)nu;
-    p.c4 = (float)(1.0 / (4.0 * nu));
-    p.a_s = (float)((double)sp.a / nu);
+    p.a = sp.a;
+    p.am1 = sp.am1;
     p.err = sp.err;
     const int grid = ctas < p.nitems ? ctas : p.nitems;
     k_d3q19_half<NH, T><<<(unsigned)grid, HG<NH, T>::NTH, HG<NH, T>::BYTES, st>>>((const T *)in, (T *)out, p);

@@ -27,13 +27,6 @@ cudaError_t launch_convert_out(int storage, int dst_dtype, const void *src, void
 cudaError_t launch_diagnostics(int storage, const void *f, long long fstride, long long N,
                                int has_z, double *partial, double *out, cudaStream_t st);
 
-// Tiled interior kernels (periodic axes only). supported_* says whether a shape
-// can use them; launch_* runs one step.
-bool tiled_supported(int Q, int storage, const StepParams &p);
-cudaError_t launch_step_tiled(int Q, int storage, const void *in, void *out, const StepParams &p,
-                              cudaStream_t st);
-const char *tiled_name(int Q);
-
 // Adjoint of one step (kernels_adjoint.cu) from the states at t and t+1 and
 // (Dbar, Jbar) in dj; adds dL/dnu to *nu_total. With lam_t1 (the first step of a
 // sweep), dj is first formed from lambda_t1 and the state at t+1. With dj_next, the
@@ -96,14 +89,10 @@ struct TuneChoice {
 bool tune_cache_lookup(const char *path, const std::string &key, TuneChoice *out);
 bool tune_cache_store(const char *path, const std::string &key, const TuneChoice &ch);
 
-// Half-row TMA variant of the D3Q19 kernel (nx = 256, 16 warps per CTA).
+// Half-row TMA D3Q19 kernel (nx = 256: two warps per row, 16 warps per CTA; nx = 128:
+// one warp per row).
 bool half_supported(int Q, int storage, const StepParams &p);
 cudaError_t launch_step_half(int Q, int storage, const void *in, void *out, const StepParams &p,
                              cudaStream_t st);
-
-// Register-prefetch z-marching variant of the D3Q19 kernel (same shapes).
-bool zmarch_supported(int Q, int storage, const StepParams &p);
-cudaError_t launch_step_zmarch(int Q, int storage, const void *in, void *out, const StepParams &p,
-                               cudaStream_t st);
 
 }  // namespace lwacm

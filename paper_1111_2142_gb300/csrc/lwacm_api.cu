@@ -63,8 +63,8 @@ struct lwacm_ctx {
     cudaStream_t cap_stream = nullptr;
     cudaGraphExec_t gexec[2] = {nullptr, nullptr};
     int gchunk[2] = {0, 0};
-    int kernel = 1;  // 1 generic, 2 tiled (TMA), 3 z-march (register prefetch), 4 batch, 5 half-row TMA,
-                     // 6 D2Q9 2D tiles
+    int kernel = 1;  // 1 generic, 4 batch, 5 half-row TMA, 6 D2Q9 2D tiles (2 and 3: retired
+                     // row-tiled kernels, superseded by 5)
     std::string kname = "none";
     // batched domains (nbatch > 0): packed one after the other
     int nbatch = 0;
@@ -146,6 +146,7 @@ StepParams params(const lwacm_ctx *c) {
     // Eq. viscosity2 / Eq. ACM2.0nu: a = 2(omega-1)/omega = 1 - 6 nu; s = 3(1-a) = 18 nu
     p.s = (float)(18.0 * c->nu);
     p.a = (float)(1.0 - 6.0 * c->nu);
+    p.am1 = (float)(-6.0 * c->nu);
     // Eq. ACM2.0ccccbb: (2/omega - 1) * 2 f^(e,o)(rho0, u_w) = 6 nu * 2 * 3 w rho0 (c.u_w)
     p.wallc = (float)(36.0 * c->nu * c->rho0);
     for (int a = 0; a < 3; ++a) {
@@ -180,9 +181,8 @@ void drop_graphs(lwacm_ctx *c) {
 }
 
 // Interior kernel: the explicit choice if it supports the shape, else (automatic)
-// the register-prefetch z-march kernel (fastest measured on the 256^3 D3Q19
-// workload), then the tiled TMA kernel, then the generic gather kernel, which
-// supports everything. Returns false when an
+// the half-row TMA kernel (D3Q19), then the 2D-tile kernel (D2Q9), then the
+// generic gather kernel, which supports everything. Returns false when an
 // explicit choice is not supported. Kernels that need the device are only
 // considered once a workspace is bound.
 bool choose_kernel(lwacm_ctx *c) {
@@ -199,25 +199,19 @@ bool choose_kernel(lwacm_ctx *c) {
     }
     const StepParams p = params(c);
     const bool dev = c->bound;
-    const bool t_ok = dev && tiled_supported(c->Q, c->storage, p);
-    const bool z_ok = dev && zmarch_supported(c->Q, c->storage, p);
     const bool h_ok = dev && half_supported(c->Q, c->storage, p);
     const bool s_ok = tiles2d_supported(c->Q, c->storage, p);
     bool ok = true;
     switch (c->kernel_opt) {
         case 1: c->kernel = 1; break;
-        case 2: c->kernel = t_ok ? 2 : 1; ok = t_ok || !dev; break;
-        case 3: c->kernel = z_ok ? 3 : 1; ok = z_ok || !dev; break;
         case 5: c->kernel = h_ok ? 5 : 1; ok = h_ok || !dev; break;
         case 6: c->kernel = s_ok ? 6 : 1; ok = s_ok; break;
-        default: c->kernel = h_ok ? 5 : (z_ok ? 3 : (t_ok ? 2 : (s_ok ? 6 : 1))); break;
+        default: c->kernel = h_ok ? 5 : (s_ok ? 6 : 1); break;
     }
     static const char *gname[2] = {"generic_d2q9", "generic_d3q19"};
     static const char *sname[7] = {"tiles2d_d2q9_30x14", "tiles2d_d2q9_30x6",  "tiles2d_d2q9_30x14", "tiles2d_d2q9_62x6",
                                    "tiles2d_d2q9_30x30", "tiles2d_d2q9_62x14", "tiles2d_d2q9_126x6"};
-    c->kname = c->kernel == 2   ? tiled_name(c->Q)
-               : c->kernel == 3 ? "zmarch_d3q19"
-               : c->kernel == 5 ? "half_d3q19_tma"
+    c->kname = c->kernel == 5   ? "half_d3q19_tma"
                : c->kernel == 6 ? sname[c->batch_shape >= 0 && c->batch_shape < 7 ? c->batch_shape : 0]
                                 : gname[c->Q == 19 ? 1 : 0];
     return ok;
@@ -272,9 +266,7 @@ BatchParams batch_params(lwacm_ctx *c) {
 cudaError_t step_between(lwacm_ctx *c, const void *in, void *out, cudaStream_t st) {
     if (c->nbatch) return launch_batch_step(c->Q, c->storage, in, out, batch_params(c), st);
     const StepParams p = params(c);
-    cudaError_t e = c->kernel == 2   ? launch_step_tiled(c->Q, c->storage, in, out, p, st)
-                    : c->kernel == 3 ? launch_step_zmarch(c->Q, c->storage, in, out, p, st)
-                    : c->kernel == 5 ? launch_step_half(c->Q, c->storage, in, out, p, st)
+    cudaError_t e = c->kernel == 5   ? launch_step_half(c->Q, c->storage, in, out, p, st)
                     : c->kernel == 6 ? launch_step_tiles2d(c->Q, c->storage, c->batch_shape > 0 ? c->batch_shape : 2,
                                                            in, out, p, st)
                                      : launch_step_generic(c->Q, c->storage, in, out, p, st);
@@ -400,7 +392,7 @@ std::vector<Cand> tune_candidates(const lwacm_ctx *c) {
             if (batch_shape_supported(c->Q, c->storage, k))
                 for (int m = 0; m < 2; ++m) v.push_back(Cand{0, k, m});
     } else {
-        const int ks[4] = {5, 3, 2, 1};
+        const int ks[2] = {5, 1};
         for (int k : ks) v.push_back(Cand{k, 0, 0});
         if (c->Q == 9)
             for (int k = 1; k < batch_shapes(); ++k) v.push_back(Cand{6, k, 0});
@@ -590,7 +582,8 @@ lwacm_status lwacm_set_option(lwacm_ctx *c, int key, double v) {
         }
         case LWACM_OPT_KERNEL: {
             const int k = (int)v;
-            if (k < 0 || k > 6 || k == 4) return fail(c, LWACM_E_ARG, "kernel must be 0, 1, 2, 3, 5 or 6");
+            if (k < 0 || k > 6 || k == 4 || k == 2 || k == 3)
+                return fail(c, LWACM_E_ARG, "kernel must be 0, 1, 5 or 6");
             const int old = c->kernel_opt;
             c->kernel_opt = k;
             if (!choose_kernel(c)) {

@@ -84,6 +84,7 @@ struct StepParams {
     long long fstride;  // elements between consecutive fields of one buffer
     float s;            // 18 nu
     float a;            // 1 - 6 nu = 2(omega-1)/omega
+    float am1;          // a - 1 = -6 nu (rounded from the exact value, not from a)
     float wallc;        // 36 nu rho0 (moving-wall coefficient, times w_i c_i.u_w)
     float lid[3];       // u_w of the moving wall
     float force[3];     // g of Eq. force
@@ -98,6 +99,19 @@ struct StepParams {
     int lid_axis;       // axis whose top wall moves with the lid velocity
     int *err;           // device error word (bounded waits that gave up set it)
 };
+
+// The post-combine momentum a rho(x) u(x) of Eq. ACM2.0b(c), added to the partial
+// sum j of the streamed link values: with rho = 1 + d and a = 1 + am1 (am1 = -6 nu),
+// a rho u = u + m u where m = a d + am1 = post_factor(a, d, am1), so that
+//     j + a rho u = (j + m u) + u.
+// a rho itself is O(1): rounded to FP32, its error (up to 2^-24) depends only on the
+// low bits of d, which move by a small fraction of an ulp per step, so the error
+// keeps its sign at a node over hundreds of steps and the velocity drifts linearly
+// (6e-5 u0 after 1000 steps of the 3D Taylor-Green workload against 4e-6 in this
+// form). Here every rounded quantity is either small (m) or velocity-sized, and a
+// velocity's low bits change every step.
+__device__ __forceinline__ float post_factor(float a, float d, float am1) { return fmaf(a, d, am1); }
+__device__ __forceinline__ float post_combine(float j, float m, float u) { return fmaf(m, u, j) + u; }
 
 // g_i at a node with fields (d, u), for a link with integer velocity (cx,cy,cz)
 // and weight w; q = |u|^2.

@@ -106,9 +106,10 @@ __device__ __forceinline__ void node_update(const T *__restrict__ in, T *__restr
     const float rna = 1.f + dd;  // zeroth moment of the distribution built with a
     if (NUP) dd = fmaf(p.sdelta, dsp, dd);
     if (NUP && BULK) dd = fmaf(p.sdelta * (1.f / 3.f), dfos, dd);
-    jx = fmaf(p.a * rx, ux, jx);
-    jy = fmaf(p.a * rx, uy, jy);
-    jz = fmaf(p.a * rx, uz, jz);
+    const float mx = post_factor(p.a, dx, p.am1);  // a rho u = u + mx u (post_combine)
+    jx = post_combine(jx, mx, ux);
+    jy = post_combine(jy, mx, uy);
+    jz = post_combine(jz, mx, uz);
     if (p.has_force) {  // Eq. force: the odd part of f^(e)(rho(x,t), g) adds rho g to j
         jx = fmaf(rx, p.force[0], jx);
         jy = fmaf(rx, p.force[1], jy);

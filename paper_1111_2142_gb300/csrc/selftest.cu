@@ -8,18 +8,36 @@
 
 namespace {
 
-__global__ void k_reciprocal(const float *__restrict__ x, float *__restrict__ out, long long n) {
-    for (long long k = blockIdx.x * (long long)blockDim.x + threadIdx.x; k < n;
-         k += (long long)gridDim.x * blockDim.x)
-        out[k] = lwacm::tile::rcp_nr(x[k]);
+// packed: element pairs (2k, 2k+1) through the FP32x2 form the half-row kernel uses
+// (an odd last element through the scalar form); otherwise every element through
+// the scalar form of the other row-tiled kernels
+__global__ void k_quotient(const float *__restrict__ a, const float *__restrict__ b, float *__restrict__ out,
+                           long long n, int packed) {
+    const long long stride = (long long)gridDim.x * blockDim.x;
+    const long long t0 = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    if (packed) {
+        const long long np = n / 2;
+        for (long long k = t0; k < np; k += stride) {
+            const float2 a2 = make_float2(a[2 * k], a[2 * k + 1]);
+            const float2 b2 = make_float2(b[2 * k], b[2 * k + 1]);
+            const float2 q = lwacm::tile::div_apply2(a2, lwacm::tile::div_prep2(b2));
+            out[2 * k] = q.x;
+            out[2 * k + 1] = q.y;
+        }
+        if ((n & 1) && t0 == 0) out[n - 1] = lwacm::tile::div_apply(a[n - 1], lwacm::tile::div_prep(b[n - 1]));
+    } else {
+        for (long long k = t0; k < n; k += stride)
+            out[k] = lwacm::tile::div_apply(a[k], lwacm::tile::div_prep(b[k]));
+    }
 }
 
 }  // namespace
 
-extern "C" int lwacm_selftest_reciprocal(const float *x_dev, float *out_dev, long long n, void *stream) {
-    if (!x_dev || !out_dev || n < 1 || n >= (1LL << 31)) return LWACM_E_ARG;
+extern "C" int lwacm_selftest_quotient(const float *a_dev, const float *b_dev, float *out_dev, long long n,
+                                       int packed, void *stream) {
+    if (!a_dev || !b_dev || !out_dev || n < 1 || n >= (1LL << 31)) return LWACM_E_ARG;
     const long long blocks = (n + 255) / 256;
     const unsigned grid = (unsigned)(blocks < 4096 ? blocks : 4096);
-    k_reciprocal<<<grid, 256, 0, (cudaStream_t)stream>>>(x_dev, out_dev, n);
+    k_quotient<<<grid, 256, 0, (cudaStream_t)stream>>>(a_dev, b_dev, out_dev, n, packed ? 1 : 0);
     return cudaGetLastError() == cudaSuccess ? LWACM_OK : LWACM_E_CUDA;
 }

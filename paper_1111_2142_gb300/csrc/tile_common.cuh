@@ -1,7 +1,7 @@
-// Building blocks shared by the row-tiled D3Q19 kernels (kernels_tiled.cu,
-// kernels_half.cu): per-launch parameters, mbarrier / bulk-copy wrappers, the
-// task iterator over (y-column, z-chunk) work items, the link-value arithmetic of
-// the moment form (lwacm_core.cuh) and lane-row shifts and shared-memory slots.
+// Building blocks of the row-tiled D3Q19 kernel (kernels_half.cu) and its device
+// self-test (selftest.cu): per-launch parameters, mbarrier / bulk-copy wrappers, the
+// correctly rounded velocity quotient, the task iterator over (y-column, z-chunk)
+// work items, exchange-row slots and storage-type loads and stores.
 #pragma once
 
 #include <stdint.h>
@@ -23,8 +23,7 @@ struct TiledParams {
     int zc, nitems;      // planes per chunk, ycols * ceil(nz / zc)
     long long fstride;
     float s18;           // s / 18 = nu
-    float c4;            // 1 / (4 nu)
-    float a_s;           // a / nu
+    float a, am1;        // a = 1 - 6 nu and a - 1 = -6 nu (post_combine, lwacm_core.cuh)
     int *err;            // error word (timeout)
 };
 
@@ -64,11 +63,61 @@ __device__ __forceinline__ void bulk_g2s(void *dst, const void *src, uint32_t by
         : "memory");
 }
 
-// 1/x: hardware approximation refined by one Newton-Raphson step
-// (r <- r + r (1 - x r)), accurate to about an ulp for the densities here.
-__device__ __forceinline__ float rcp_nr(float x) {
-    float r = __fdividef(1.0f, x);
-    return fmaf(r, fmaf(-x, r, 1.0f), r);
+// ---- velocity u = j / rho (step a5: IEEE division) -------------------------------
+// The three momentum components of a node share one divisor. Each quotient is the
+// correctly rounded one (the IEEE round-to-nearest quotient j / rho), formed with
+// Markstein's FMA correction (P. W. Markstein, "Computation of elementary functions
+// on the IBM RISC System/6000 processor", IBM J. Res. Develop. 34 (1990) 111-119):
+// with y = RN(1/b), the correctly rounded reciprocal, and q within one ulp of a/b,
+// the residual r = a - b q is exact in one FMA and RN(q + r y) = RN(a/b). In brief:
+// q + r y misses a/b by (a/b - q)(b y - 1); when a/b lies within 2^-24 ulp of a
+// rounding midpoint every faithful q is about half an ulp from a/b, so the miss is
+// below half an ulp times |b y - 1| < 2^-24, less than a/b's distance to any
+// midpoint (at least 2^-24 ulp / b, as a - b m is a nonzero multiple of a fixed
+// power of two).
+// The first product q0 = RN(a y) can miss by up to about 1.5 ulps (a near 2 in its
+// binade, a/b just below the next), so a first correction q1 = RN(q0 + r0 y) brings
+// it within half an ulp plus a few 2^-24 ulp (faithful) and a second correction
+// gives the correctly rounded quotient. This holds while the residuals stay normal:
+// numerators |a| >= 2^-100 and normal quotients (a smaller momentum, far below any
+// resolved velocity, may round one unit differently in the last place). A zero
+// numerator gives +0 (the exact residual of a zero quotient is +0), where IEEE
+// division keeps the quotient's sign of zero; the two zeros compare equal, and the
+// sign of a zero velocity changes no later value of the update.
+// Why the rounding matters here: a quotient through a rounded reciprocal and a
+// product (two roundings) drifts 1.7e-5 u0 from the FP64 oracle over 1000 steps of
+// the 128^3 Taylor-Green workload, the IEEE quotient 4.7e-6 u0. The reciprocal's
+// rounding error depends only on the slowly moving density, so it keeps its sign
+// at a node over many steps (as in post_combine of lwacm_core.cuh).
+struct Div1 {
+    float b, nb, y;  // divisor, -divisor, RN(1 / divisor)
+};
+__device__ __forceinline__ Div1 div_prep(float b) {
+    Div1 d;
+    d.b = b;
+    d.nb = -b;
+    d.y = __frcp_rn(b);
+    return d;
+}
+__device__ __forceinline__ float div_apply(float a, const Div1 &d) {
+    const float q0 = a * d.y;
+    const float q1 = fmaf(fmaf(d.nb, q0, a), d.y, q0);  // faithful
+    return fmaf(fmaf(d.nb, q1, a), d.y, q1);             // correctly rounded
+}
+// the same for two nodes held as an FP32x2 pair (packed FMAs, same rounding)
+struct Div2 {
+    float2 nb, y;
+};
+__device__ __forceinline__ Div2 div_prep2(float2 b) {
+    Div2 d;
+    d.nb = make_float2(-b.x, -b.y);
+    d.y = make_float2(__frcp_rn(b.x), __frcp_rn(b.y));
+    return d;
+}
+__device__ __forceinline__ float2 div_apply2(float2 a, const Div2 &d) {
+    const float2 q0 = __fmul2_rn(a, d.y);
+    const float2 q1 = __ffma2_rn(__ffma2_rn(d.nb, q0, a), d.y, q0);
+    return __ffma2_rn(__ffma2_rn(d.nb, q1, a), d.y, q1);
 }
 
 // ---- task iteration -------------------------------------------------------------
@@ -110,31 +159,8 @@ struct TaskIter {
 // groups of all lanes are contiguous, so warp float4 accesses are conflict-free
 __device__ __forceinline__ int spos(int l, int h) { return h * 128 + l * 4; }
 
-// deposit the value g of link c = (cx,cy,cz) into a receiver's (d, jx, jy, jz).
-// Values arriving along c_z = +1 links feed the plane ahead, which receives
-// nothing else before it becomes the current plane; its jz then equals its d and
-// is copied at that point, so those deposits skip jz.
-__device__ __forceinline__ void dep(float (&a)[4], float g, int cx, int cy, int cz) {
-    a[0] += g;
-    if (cx > 0) a[1] += g;
-    if (cx < 0) a[1] -= g;
-    if (cy > 0) a[2] += g;
-    if (cy < 0) a[2] -= g;
-    if (cz < 0) a[3] -= g;
-}
-
 template <int PM, int P0, int PP>
 __device__ __forceinline__ constexpr int pl(int cz) { return cz > 0 ? PP : (cz < 0 ? PM : P0); }
-
-// per-node constants: velocity and, with K = d - 3/2 rho |u|^2, the three
-// coefficients of a link value w [d + rho (s e + 9/2 e^2 - 3/2 |u|^2)] =
-// w K + w rho s e + w 9/2 rho e^2 (e = c.u) for the axis weight w = 1/18
-// (K1 = K/18, A1 = rho s/18 = rho nu, B1 = rho/4) and the diagonal weight
-// 1/36 (K2, A2, B2: half of those).
-template <int VX>
-struct NodeConst {
-    float U[VX], V[VX], W[VX], K1[VX], A1[VX], B1[VX], K2[VX], A2[VX], B2[VX];
-};
 
 // four consecutive stored values as floats (FP32, or BF16 / FP16 storage: a
 // bfloat16 is the upper half of an FP32, so widening it is exact)
@@ -169,90 +195,6 @@ __device__ __forceinline__ void st4(__half *p, float a, float b, float c, float 
     memcpy(&r.x, &x, 4);
     memcpy(&r.y, &y, 4);
     *reinterpret_cast<uint2 *>(p) = r;
-}
-
-// row: staged field-0 row; rstride: distance (in elements) between fields in the stage
-template <int VX, typename T>
-__device__ __forceinline__ void node_consts(NodeConst<VX> &nc, const T *row, int rstride, int lane,
-                                            float s18) {
-#pragma unroll
-    for (int h = 0; h < VX / 4; ++h) {
-        const float4 d4 = ld4(row + lane * VX + 4 * h);
-        const float4 u4 = ld4(row + rstride + lane * VX + 4 * h);
-        const float4 v4 = ld4(row + 2 * rstride + lane * VX + 4 * h);
-        const float4 w4 = ld4(row + 3 * rstride + lane * VX + 4 * h);
-        const float dd[4] = {d4.x, d4.y, d4.z, d4.w}, uu[4] = {u4.x, u4.y, u4.z, u4.w};
-        const float vv[4] = {v4.x, v4.y, v4.z, v4.w}, ww[4] = {w4.x, w4.y, w4.z, w4.w};
-#pragma unroll
-        for (int j = 0; j < 4; ++j) {
-            const int i = 4 * h + j;
-            const float rho = 1.f + dd[j];
-            const float q = fmaf(uu[j], uu[j], fmaf(vv[j], vv[j], ww[j] * ww[j]));
-            const float K = fmaf(-1.5f * rho, q, dd[j]);
-            nc.U[i] = uu[j];
-            nc.V[i] = vv[j];
-            nc.W[i] = ww[j];
-            nc.K1[i] = K * (1.f / 18.f);
-            nc.A1[i] = rho * s18;
-            nc.B1[i] = 0.25f * rho;
-            nc.K2[i] = K * (1.f / 36.f);
-            nc.A2[i] = rho * (0.5f * s18);
-            nc.B2[i] = 0.125f * rho;
-        }
-    }
-}
-
-// values of the pair (c, -c) at node i (e = c.u): the even part w (K + 9/2 rho e^2)
-// plus or minus the odd part w rho s e; axis links weight 1/18, diagonals 1/36
-template <int VX>
-__device__ __forceinline__ void pair_g(const NodeConst<VX> &nc, int i, float e, bool diag, float &gp,
-                                       float &gm) {
-    const float A = diag ? nc.A2[i] : nc.A1[i];
-    const float cm = fmaf((diag ? nc.B2[i] : nc.B1[i]) * e, e, diag ? nc.K2[i] : nc.K1[i]);
-    gp = fmaf(A, e, cm);
-    gm = fmaf(-A, e, cm);
-}
-
-// the five (c, -c) pairs with c_y(c) = +1: c = (cx, 1, cz)
-template <int VX>
-__device__ __forceinline__ float ypair_e(const NodeConst<VX> &nc, int k, int i) {
-    const float u = nc.U[i], v = nc.V[i], w = nc.W[i];
-    return k == 0 ? v : (k == 1 ? u + v : (k == 2 ? v - u : (k == 3 ? v + w : v - w)));
-}
-
-// shift a lane-distributed row in place by +1 (g[x] <- g[x-1]) or -1 (g[x] <- g[x+1])
-template <int VX>
-__device__ __forceinline__ void xshift(float (&g)[VX], int dir, int lane) {
-    if (dir > 0) {
-        const float e = __shfl_sync(FULL, g[VX - 1], (lane + 31) & 31);
-#pragma unroll
-        for (int i = VX - 1; i > 0; --i) g[i] = g[i - 1];
-        g[0] = e;
-    } else if (dir < 0) {
-        const float e = __shfl_sync(FULL, g[0], (lane + 1) & 31);
-#pragma unroll
-        for (int i = 0; i < VX - 1; ++i) g[i] = g[i + 1];
-        g[VX - 1] = e;
-    }
-}
-
-template <int VX>
-__device__ __forceinline__ void st_slot(float *slot, const float (&o)[VX], int lane) {
-#pragma unroll
-    for (int h = 0; h < VX / 4; ++h)
-        *reinterpret_cast<float4 *>(slot + spos(lane, h)) =
-            make_float4(o[4 * h], o[4 * h + 1], o[4 * h + 2], o[4 * h + 3]);
-}
-template <int VX>
-__device__ __forceinline__ void ld_slot(const float *slot, float (&o)[VX], int lane) {
-#pragma unroll
-    for (int h = 0; h < VX / 4; ++h) {
-        const float4 t = *reinterpret_cast<const float4 *>(slot + spos(lane, h));
-        o[4 * h] = t.x;
-        o[4 * h + 1] = t.y;
-        o[4 * h + 2] = t.z;
-        o[4 * h + 3] = t.w;
-    }
 }
 
 }  // namespace tile

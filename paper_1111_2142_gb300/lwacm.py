@@ -71,7 +71,7 @@ def load():
         "lwacm_batch_create": [i, i, P(i), P(i), P(i), P(d), i, P(vp)],
         "lwacm_batch_offsets": [vp, P(ll)],
         "lwacm_measure_fp32_peak": [ll, vp, P(d), P(d)],
-        "lwacm_selftest_reciprocal": [vp, vp, ll, vp],
+        "lwacm_selftest_quotient": [vp, vp, vp, ll, i, vp],
         "lwacm_set_force_field": [vp, vp, vp, vp, i, i],
         "lwacm_autotune": [vp, ctypes.c_char_p, i, ctypes.c_char_p, ctypes.c_size_t],
         "lwacm_set_scalar": [vp, vp, i, i],

@@ -109,10 +109,14 @@ def test_measure_fp32_peak_validation(lib):
     assert lib.lwacm_measure_fp32_peak(16, None, ctypes.byref(tf), None) == lw.E_ARG
 
 
-def test_selftest_reciprocal_validation(lib):
+def test_selftest_quotient_validation(lib):
     from paper_1111_2142_gb300 import lwacm as lw
-    assert lib.lwacm_selftest_reciprocal(None, None, 4, None) == lw.E_ARG
-    assert lib.lwacm_selftest_reciprocal(ctypes.c_void_p(16), ctypes.c_void_p(16), 0, None) == lw.E_ARG
+    p = ctypes.c_void_p(16)
+    assert lib.lwacm_selftest_quotient(None, p, p, 4, 1, None) == lw.E_ARG
+    assert lib.lwacm_selftest_quotient(p, None, p, 4, 1, None) == lw.E_ARG
+    assert lib.lwacm_selftest_quotient(p, p, None, 4, 0, None) == lw.E_ARG
+    assert lib.lwacm_selftest_quotient(p, p, p, 0, 1, None) == lw.E_ARG
+    assert lib.lwacm_selftest_quotient(p, p, p, 1 << 31, 1, None) == lw.E_ARG
 
 
 def test_force_field_option(lib):

@@ -119,7 +119,7 @@ def test_force_field_one_step(lw, Q, shape, bc, kernel):
 
 
 def test_forcing_keeps_tiled_kernels_off(lw):
-    """The row-tiled kernels have no forcing term: a periodic 256-wide D3Q19 box
+    """The row-tiled kernel has no forcing term: a periodic 256-wide D3Q19 box
     with a constant force runs the generic kernel and matches the oracle."""
     shape = (3, 8, 256)
     f = inputs.smooth_random(shape, seed=31, u_amp=0.03, d_amp=0.01)
