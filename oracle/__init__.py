@@ -4,7 +4,8 @@ Only the test-suite, ``__graft_entry__.smoke()`` and the CPU-baseline leg of
 ``bench.py`` may import this package. It is the plain, slow reference the CUDA
 library is checked against and shares no code with it. The arithmetic lives in
 ``lwacm_oracle.c`` (populations form of Eq. ACM2.0, walls of Eqs. ACM2.0cccbb2 /
-ACM2.0ccccbb, forcing of Eq. force, omega_p, the passive scalar, the
+ACM2.0ccccbb, forcing of Eq. force, omega_p, the semi-implicit pressure update of
+Eq. FDcompact_si, the passive scalar, the
 bulk-viscosity quasi-equilibrium, the BGK comparator, the Appendix-C
 finite-difference formulas and the reverse-mode adjoint); this module only
 marshals numpy arrays and adds FP64 diagnostics sums (Eq. global.quantities,
@@ -65,6 +66,7 @@ def _load():
         lib.lwo_step_force_field.argtypes = [i, i, i, i, d, i, d, P, P, P, P, l, P, P, P, P, i]
         lib.lwo_step_scalar.argtypes = [i, i, i, i, d, d, l, P, P, P, P, P, i]
         lib.lwo_step_nu_p.argtypes = [i, i, i, i, d, d, P, P, P, P, l, P, P, P, P, i]
+        lib.lwo_step_semi_implicit.argtypes = [i, i, i, i, d, P, P, P, l, P, P, P, P, i]
         lib.lwo_step_bulk.argtypes = [i, i, d, d, d, l, P, P, P, P, i]
         lib.lwo_feq_star.argtypes = [d, P, d, d, P]
         lib.lwo_fqe.argtypes = [d, P, d, P]
@@ -166,6 +168,22 @@ def step_nu_p(Q, d, ux, uy, uz=None, *, nu, nu_p, force=None, g=None, nsteps=1, 
                            int(nsteps), _p(d), _p(ux), _p(uy), _p(uz), int(nthreads))
     if rc != 0:
         raise ValueError(f"oracle step failed: {rc}")
+    return (d, ux, uy) if Q == 9 else (d, ux, uy, uz)
+
+
+def step_semi_implicit(Q, d, ux, uy, uz=None, *, nu, g=None, nsteps=1, nthreads=0):
+    """As step() on a periodic domain, with the semi-implicit pressure update of
+    Eq. FDcompact_si (Section 2.2, item 2): the density is summed again from the
+    old density and the velocity of the explicit step. g: a per-node acceleration
+    field (gx, gy[, gz]) held fixed over the nsteps (Eq. force), or None."""
+    lib = _load()
+    d, ux, uy, uz = _f64(d), _f64(ux), _f64(uy), _f64(uz)
+    nx, ny, nz = _dims(Q, d)
+    gs = [None, None, None] if g is None else [_f64(c) for c in g] + [None] * (3 - len(g))
+    rc = lib.lwo_step_semi_implicit(Q, nx, ny, nz, float(nu), _p(gs[0]), _p(gs[1]), _p(gs[2]), int(nsteps),
+                                    _p(d), _p(ux), _p(uy), _p(uz), int(nthreads))
+    if rc != 0:
+        raise ValueError(f"oracle semi-implicit step failed: {rc}")
     return (d, ux, uy) if Q == 9 else (d, ux, uy, uz)
 
 

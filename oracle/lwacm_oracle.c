@@ -20,6 +20,8 @@
  *   - a passive scalar advected and diffused by Eq. ACM2.0t (lwo_step_scalar);
  *   - a separate relaxation frequency omega_p for the pressure update (Section
  *     2.2, item 3), periodic domains (lwo_step_nu_p);
+ *   - the semi-implicit pressure update of Eq. FDcompact_si (Section 2.2, item 2),
+ *     periodic domains (lwo_step_semi_implicit);
  *   - the bulk-viscosity variant of Appendix "Computing derivatives locally"
  *     (Eq. quasi-equilibrium2 with the quasi-equilibrium of Eq. quasi-equilibrium
  *     and the product form of Eq. d2q9_equilibrium_gen), D2Q9, periodic
@@ -358,6 +360,75 @@ int lwo_step_nu_p(int Q, int nx, int ny, int nz, double nu, double nu_p, const d
                   double *uy, double *uz, int nthreads) {
     return run_steps(Q, nx, ny, nz, nu, nu_p, LWO_PERIODIC, 1.0, NULL, force, gx, gy, gz, nsteps, d, ux, uy, uz,
                      nthreads);
+}
+
+/* Semi-implicit pressure update (Section 2.2, item 2, Eq. FDcompact_si) on a
+ * periodic domain: the density (pressure) is updated with the already updated
+ * velocity, p+ = f_p(u+, p). Reading: f_u, f_v of Eq. FDcompact a, b are functions
+ * of the state at t only, so u+ is the velocity of the explicit step (its momentum
+ * over its explicit density); the density is then the density of Eq. ACM2.0 summed
+ * again, every population built from the old density and the new velocity:
+ *   rho+(x) = sum_i f_i^(e)(rho(x-c_i), u+(x-c_i))
+ *             + a [f_i^(e,o)(rho(x), u+(x)) - f_i^(e,o)(rho(x-c_i), u+(x-c_i))].
+ * The final state is (rho+, u+). A per-node acceleration (gx, gy[, gz], or NULL)
+ * enters the momentum as in Eq. force; it leaves every density untouched, since
+ * the odd parts sum to zero. */
+int lwo_step_semi_implicit(int Q, int nx, int ny, int nz, double nu, const double *gx, const double *gy,
+                           const double *gz, long nsteps, double *d, double *ux, double *uy, double *uz,
+                           int nthreads) {
+    lwo_lattice L;
+    lwo_geom G;
+    if (make_lattice(Q, &L)) return -1;
+    if (make_geom(&L, nx, ny, nz, LWO_PERIODIC, &G)) return -2;
+    if (!(nu > 0.0)) return -4;
+    if (Q == 19 && !uz) return -5;
+    if (gx && !gy) return -3;
+    set_threads(nthreads);
+    const double omega = omega_of_nu(nu);
+    const double zero[3] = {0.0, 0.0, 0.0};
+    const long N = (long)nx * ny * nz;
+    const int nf = (Q == 19) ? 4 : 3;
+    double *buf = (double *)malloc(sizeof(double) * N * nf);
+    if (!buf) return -6;
+    double *un[3] = {buf + N, buf + 2 * N, (nf == 4) ? buf + 3 * N : NULL};
+    for (long t = 0; t < nsteps; ++t) {
+        /* the explicit step: (rho+ explicit, u+) */
+#pragma omp parallel for collapse(2) schedule(static)
+        for (int z = 0; z < nz; ++z)
+            for (int y = 0; y < ny; ++y)
+                for (int xx = 0; xx < nx; ++xx) {
+                    const int x[3] = {xx, y, z};
+                    const long k = ((long)z * ny + y) * nx + xx;
+                    double r, u[3], gk[3] = {0.0, 0.0, 0.0};
+                    if (gx) {
+                        gk[0] = gx[k];
+                        gk[1] = gy[k];
+                        gk[2] = gz ? gz[k] : 0.0;
+                    }
+                    node_update(&L, &G, omega, omega, 1.0, zero, gk, gx != NULL, x, d, ux, uy, uz, &r, u);
+                    buf[k] = r - 1.0;
+                    un[0][k] = u[0];
+                    un[1][k] = u[1];
+                    if (un[2]) un[2][k] = u[2];
+                }
+        /* the density again, from the old density and the new velocity */
+#pragma omp parallel for collapse(2) schedule(static)
+        for (int z = 0; z < nz; ++z)
+            for (int y = 0; y < ny; ++y)
+                for (int xx = 0; xx < nx; ++xx) {
+                    const int x[3] = {xx, y, z};
+                    const long k = ((long)z * ny + y) * nx + xx;
+                    double r, u[3];
+                    node_update(&L, &G, omega, omega, 1.0, zero, zero, 0, x, d, un[0], un[1], un[2], &r, u);
+                    buf[k] = r - 1.0; /* over the explicit density, which this pass does not read */
+                }
+        memcpy(d, buf, sizeof(double) * N);
+        memcpy(ux, un[0], sizeof(double) * N);
+        memcpy(uy, un[1], sizeof(double) * N);
+        if (uz) memcpy(uz, un[2], sizeof(double) * N);
+    }
+    free(buf);
+    return 0;
 }
 
 /* ---------------------------------------------------------------------------
