@@ -351,7 +351,7 @@ def next_rows(hbm, glups):
     fractions against the bytes each node moves per step), plus the Section 3.2
     shear layer at its own 128^2 size: the 3D diagonally driven cavity (walls), the
     forced Taylor-Green vortex (a per-node force field), omega_p, the bulk-viscosity
-    variant and the passive scalar."""
+    variant, the semi-implicit pressure update and the passive scalar."""
     import torch
     from paper_1111_2142_gb300 import inputs
     from paper_1111_2142_gb300 import lwacm as lw
@@ -380,6 +380,8 @@ def next_rows(hbm, glups):
     t3 = torch.cos(2 * torch.pi * torch.arange(n3, device="cuda") / n3).expand(n3, n3, n3).contiguous()
     timed("scalar_d3q19_256", lw.Lwacm(lw.D3Q19, n3, n3, n3, NU, scalar_alpha=0.01), f3, 100, n3 ** 3, 40,
           extra=lambda s: s.set_scalar(t3))
+    # a constant acceleration (Eq. force) on the 256^3 Taylor-Green workload (half-row kernel)
+    timed("forced_d3q19_256", lw.Lwacm(lw.D3Q19, n3, n3, n3, NU, force=(1e-6, 0.0, 0.0)), f3, 200, n3 ** 3, 32)
     del z3, t3
     n2 = 4096
     f2 = inputs.gtg_state(n2, 0.0)
@@ -390,6 +392,10 @@ def next_rows(hbm, glups):
     sim.set_option(lw.OPT_NU_P, 0.1)
     timed("nu_p_d2q9_4096", sim, f2, 200, n2 ** 2, 24)
     timed("bulk_d2q9_4096", lw.Lwacm(lw.D2Q9, n2, n2, 1, 0.01, bulk_gamma=0.4), f2, 200, n2 ** 2, 32)
+    # semi-implicit pressure update: the explicit step (24 B/node) plus the density pass
+    # (old density and new velocity read, new density written: 16 B/node)
+    timed("semi_implicit_d2q9_4096", lw.Lwacm(lw.D2Q9, n2, n2, 1, 0.01, semi_implicit=True), f2, 200, n2 ** 2,
+          40)
     # Section 3.2 shear layer, 128^2 to t = 1 (3200 steps): plain and nu_p = 170 nu (L2-resident)
     nu, steps = inputs.minion_brown_lattice(128)
     fm = inputs.minion_brown(128)

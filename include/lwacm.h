@@ -89,7 +89,8 @@ enum {
                                   0 disables graphs; default 64) */
     LWACM_OPT_KERNEL = 9,  /* interior kernel: 0 = automatic choice (default),
                               1 = generic gather kernel, 5 = D3Q19 half-row TMA kernel
-                              (needs the plain scheme without forcing, nx in {128, 256}
+                              (needs the plain scheme, with or without a constant
+                              acceleration but not a force field, nx in {128, 256}
                               and ny % 8 == 0, and runs walled domains with the wall pass
                               after it; FP32, BF16 and FP16 storage: LWACM_E_UNSUPPORTED
                               otherwise); 2 and 3 (earlier row-tiled kernels, superseded
@@ -133,7 +134,7 @@ enum {
                                      level; 0 = none (default). Before lwacm_bind (it
                                      adds one field to the workspace); single periodic
                                      domains only; runs on the generic kernel. */
-    LWACM_OPT_BULK_GAMMA = 16     /* gamma in (-1, 1), 0 = off (default): the bulk-
+    LWACM_OPT_BULK_GAMMA = 16,    /* gamma in (-1, 1), 0 = off (default): the bulk-
                                      viscosity variant of Appendix "Computing derivatives
                                      locally", Eq. quasi-equilibrium2. The equilibrium of
                                      Eq. ACM2.0 becomes f^(e) plus the change of the
@@ -153,6 +154,17 @@ enum {
                                      (LWACM_E_UNSUPPORTED). With LWACM_OPT_NU_P the density
                                      is relaxed with omega_p and the momentum and the
                                      trace with omega. Runs on the D2Q9 2D-tile kernel. */
+    LWACM_OPT_SEMI_IMPLICIT = 17  /* 1: semi-implicit pressure update (Section 2.2 item 2,
+                                     Eq. FDcompact_si), 0 = explicit (default). The
+                                     velocity is that of the explicit step; the density
+                                     is then summed again with every link value built
+                                     from the old density and the new velocity (one more
+                                     pass per step, after the interior kernel). Single
+                                     periodic domains, D2Q9 and D3Q19, with or without
+                                     forcing and LWACM_OPT_NU_P (the density then uses
+                                     nu_p); not with the passive scalar, the
+                                     bulk-viscosity variant or the adjoint
+                                     (LWACM_E_UNSUPPORTED). */
 };
 
 /* Create a single-domain context.

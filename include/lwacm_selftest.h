@@ -15,12 +15,15 @@ extern "C" {
  * rho u and rho, divided): the correctly rounded reciprocal of the divisor and two
  * FMA corrections of the quotient (Markstein's method), which give the IEEE
  * round-to-nearest quotient for every normal quotient.
- * packed != 0: elements in pairs (2k, 2k+1) through the FP32x2 form of the
+ * packed == 1: elements in pairs (2k, 2k+1) through the FP32x2 form of the
  * half-row kernel (an odd last element through the scalar form); packed == 0:
- * every element through the scalar form.
+ * every element through the scalar form; packed == 2: out_dev[k] = the
+ * reciprocal RN(1 / b_dev[k]) that the quotient divides with (a_dev is not read,
+ * but must be a valid pointer).
  * a_dev, b_dev, out_dev: caller-owned device arrays of n FP32 values; n in
  * [1, 2^31). Stream-ordered on `stream` (cudaStream_t; NULL = legacy default
- * stream), not synchronised. Errors: LWACM_E_ARG (null pointer, n out of range),
+ * stream), not synchronised. Errors: LWACM_E_ARG (null pointer, n out of range,
+ * packed not in {0, 1, 2}),
  * LWACM_E_CUDA (launch failure). Return values are lwacm_status codes (lwacm.h). */
 int lwacm_selftest_quotient(const float *a_dev, const float *b_dev, float *out_dev, long long n, int packed,
                             void *stream);

@@ -47,6 +47,71 @@ __global__ void __launch_bounds__(256) k_step_generic(const T *__restrict__ in,
     node_update<Q, false, NUP, SC, BULK>(in, out, p, x, y, z);
 }
 
+// Semi-implicit pressure update (Eq. FDcompact_si, Section 2.2 item 2), periodic
+// domains: after the explicit step has written (d+, u+) to `out`, the density is
+// summed again with every link value built from the old density (`in`) and the
+// new velocity, d+(x) = sum_i g_i(d(x - c_i), u+(x - c_i)) with the link values of
+// the moment form (lwacm_core.cuh; s_d = 18 nu, or 18 nu_p with omega_p). Reads
+// the old density and the new velocity, writes only the new density.
+template <int Q, typename T>
+__global__ void __launch_bounds__(256) k_semi_implicit(const T *__restrict__ in, T *__restrict__ out,
+                                                       StepParams p, float s_d) {
+    using L = Lat<Q>;
+    int x, y, z;
+    if (plane_blocks(p)) {
+        x = (int)(blockIdx.x * 32 + (threadIdx.x & 31));
+        y = (int)(blockIdx.y * 8 + (threadIdx.x >> 5));
+        z = (int)blockIdx.z;
+        if (x >= p.nx || y >= p.ny || z >= p.nz) return;
+    } else {
+        const long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+        if (idx >= p.N) return;
+        x = (int)(idx % p.nx);
+        const long long r = idx / p.nx;
+        y = (int)(r % p.ny);
+        z = (int)(r / p.ny);
+    }
+    const T *Un = out + p.fstride, *Vn = out + 2 * p.fstride, *Wn = out + 3 * p.fstride;
+    float dd = 0.f;
+#pragma unroll
+    for (int i = 0; i < Q; ++i) {
+        const int cx = L::c(i, 0), cy = L::c(i, 1), cz = L::c(i, 2);
+        int sx = x - cx, sy = y - cy, sz = z - cz;
+        sx = sx < 0 ? sx + p.nx : (sx >= p.nx ? sx - p.nx : sx);
+        sy = sy < 0 ? sy + p.ny : (sy >= p.ny ? sy - p.ny : sy);
+        sz = sz < 0 ? sz + p.nz : (sz >= p.nz ? sz - p.nz : sz);
+        const long long s = ((long long)sz * p.ny + sy) * p.nx + sx;
+        const float ds = ldf(in + s), us = ldf(Un + s), vs = ldf(Vn + s);
+        const float ws = (Q == 19) ? ldf(Wn + s) : 0.f;
+        const float e = cx * us + cy * vs + cz * ws;
+        const float q = fmaf(us, us, fmaf(vs, vs, ws * ws));
+        dd += link_g(L::w(i), ds, 1.f + ds, e, q, s_d);
+    }
+    stf(out + ((long long)z * p.ny + y) * p.nx + x, dd);
+}
+
+template <typename T>
+cudaError_t launch_semi_implicit_t(int Q, const void *in, void *out, const StepParams &p, cudaStream_t st) {
+    const dim3 nb = plane_blocks(p) ? dim3((unsigned)((p.nx + 31) / 32), (unsigned)((p.ny + 7) / 8), (unsigned)p.nz)
+                                    : dim3((unsigned)((p.N + 255) / 256));
+    const float s_d = p.s + p.sdelta;
+    if (Q == 9)
+        k_semi_implicit<9, T><<<nb, 256, 0, st>>>((const T *)in, (T *)out, p, s_d);
+    else
+        k_semi_implicit<19, T><<<nb, 256, 0, st>>>((const T *)in, (T *)out, p, s_d);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_semi_implicit(int Q, int storage, const void *in, void *out, const StepParams &p,
+                                 cudaStream_t st) {
+    switch (storage) {
+        case STORE_F32: return launch_semi_implicit_t<float>(Q, in, out, p, st);
+        case STORE_BF16: return launch_semi_implicit_t<__nv_bfloat16>(Q, in, out, p, st);
+        case STORE_F16: return launch_semi_implicit_t<__half>(Q, in, out, p, st);
+    }
+    return cudaErrorInvalidValue;
+}
+
 // Boundary nodes of a walled domain, enumerated without gaps.
 //   cavity 2D: the perimeter of the nx x ny rectangle;
 //   cavity 3D: the planes z = 0 and z = nz-1, then the perimeter of each inner plane;
@@ -456,7 +521,9 @@ cudaError_t launch_wall_t(int Q, const void *in, void *out, const StepParams &p,
     const long long nb = boundary_count(p, Q == 9 ? 2 : 3);
     if (nb <= 0) return cudaSuccess;
     if (Q == 19 && xface_split(p, 3)) {
-        const long long npy = (p.ny - 2 + XF_PY - 1) / XF_PY, npz = (p.nz - 2 + XF_PZ - 1) / XF_PZ;
+        // the inner x-face nodes in staged patches, unless the interior kernel did them
+        const long long npy = p.xfaces_done ? 0 : (p.ny - 2 + XF_PY - 1) / XF_PY;
+        const long long npz = p.xfaces_done ? 0 : (p.nz - 2 + XF_PZ - 1) / XF_PZ;
         const long long bpr = (p.nx + WC_THREADS - 1) / WC_THREADS;
         const long long blocks = 2 * npy * npz + wall_rows(p) * bpr;
         if (blocks > 0x7fffffffLL) return cudaErrorInvalidConfiguration;

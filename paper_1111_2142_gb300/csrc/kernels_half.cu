@@ -67,6 +67,7 @@ __device__ __forceinline__ F2 neg2(F2 a) { return __fmul2_rn(a, make_float2(-1.f
 struct NC2 {
     F2 U[2], V[2], W[2], K1[2], A1[2], B1[2], K2[2], A2[2], B2[2];
     F2 M[2];  // a d - 6 nu: a rho u = u + M u (post_combine, lwacm_core.cuh)
+    F2 D[2];  // d (the forced variant: rho g = g + d g)
 };
 
 template <typename T>
@@ -93,12 +94,15 @@ __device__ __forceinline__ void node_consts2(NC2 &nc, const T *row, int rstride,
         nc.A2[j] = mul2(rho, b2(0.5f * s18));
         nc.B2[j] = mul2(rho, b2(0.125f));
         nc.M[j] = fma2(b2(a), dd[j], b2(am1));
+        nc.D[j] = dd[j];
     }
 }
 
 // values of the link pair (c, -c) at the two nodes of pair j, e = c.u
 __device__ __forceinline__ void pair2(const NC2 &nc, int j, F2 e, bool diag, F2 &gp, F2 &gm) {
     const F2 A = diag ? nc.A2[j] : nc.A1[j], B = diag ? nc.B2[j] : nc.B1[j], K = diag ? nc.K2[j] : nc.K1[j];
+    // scalar on purpose: the same arithmetic as FP32x2 operations measured 3% slower
+    // (the FMA pipe, not instruction issue, is what these values contend for)
     const float cx = fmaf(B.x * e.x, e.x, K.x), cy = fmaf(B.y * e.y, e.y, K.y);
     gp = make_float2(fmaf(A.x, e.x, cx), fmaf(A.y, e.y, cy));
     gm = make_float2(fmaf(-A.x, e.x, cx), fmaf(-A.y, e.y, cy));
@@ -175,9 +179,16 @@ __device__ __forceinline__ void ld_slot2(const float *slot, F2 (&o)[2], int lane
 // With NH = 2 the boundary lanes take the x-shifted diagonal that crosses from the
 // other half from the neighbour's values nb1 (c = (1,1,0) at lane 0, (-1,-1,0) at
 // lane 31) and nb2 (c = (1,-1,0) at lane 0, (-1,1,0) at lane 31).
-template <int NH, int MODE>
+// XW (x walls: the cavity's x = 0 and x = nx-1 faces): e0 / eN mark the lane that
+// holds node x = 0 / x = nx-1. A value that would cross such a face (wrapped
+// periodically) is dropped, and for an own row (own != nullptr) the node takes
+// instead its own value of the bounced link (Eq. ACM2.0cccbb2; the moving-wall
+// term is zero: the lid is not on an x face): link (1,1,0) arriving at x = 0 is
+// replaced by the node's (-1,-1,0) value, and so on.
+template <int NH, int MODE, bool XW = false>
 __device__ __forceinline__ void send_rows(const NC2 &nc, float *ubase, float *dbase, bool UP, bool DN,
-                                          float nb1, float nb2, int lane) {
+                                          float nb1, float nb2, int lane, bool e0 = false, bool eN = false,
+                                          F2 (*own)[4] = nullptr) {
     constexpr int XSLOT = HG<NH>::XSLOT;
     const bool l0 = lane == 0 && NH == 2, l31 = lane == 31 && NH == 2;
     if (MODE == MID) {
@@ -188,13 +199,29 @@ __device__ __forceinline__ void send_rows(const NC2 &nc, float *ubase, float *db
             F2 gp[2], gm[2];
 #pragma unroll
             for (int j = 0; j < 2; ++j) pair2(nc, j, ye2(nc, 1, j), true, gp[j], gm[j]);
+            if (XW && own) {
+                if (e0) {  // (1,1,0) into x = 0 bounces: its (-1,-1,0) value
+                    const float v = gm[0].x;
+                    own[0][0].x += v;
+                    own[0][1].x += v;
+                    own[0][2].x += v;
+                }
+                if (eN) {  // (-1,-1,0) into x = nx-1 bounces: its (1,1,0) value
+                    const float v = gp[1].y;
+                    own[1][0].y += v;
+                    own[1][1].y -= v;
+                    own[1][2].y -= v;
+                }
+            }
             if (UP) {
                 shift2(gp, 1, lane);
                 gp[0].x = l0 ? nb1 : gp[0].x;
+                if (XW) gp[0].x = e0 ? 0.f : gp[0].x;
             }
             if (DN) {
                 shift2(gm, -1, lane);
                 gm[1].y = l31 ? nb1 : gm[1].y;
+                if (XW) gm[1].y = eN ? 0.f : gm[1].y;
             }
 #pragma unroll
             for (int j = 0; j < 2; ++j) {
@@ -208,13 +235,29 @@ __device__ __forceinline__ void send_rows(const NC2 &nc, float *ubase, float *db
             F2 gp[2], gm[2];
 #pragma unroll
             for (int j = 0; j < 2; ++j) pair2(nc, j, ye2(nc, 2, j), true, gp[j], gm[j]);
+            if (XW && own) {
+                if (e0) {  // (1,-1,0) into x = 0 bounces: its (-1,1,0) value
+                    const float v = gp[0].x;
+                    own[0][0].x += v;
+                    own[0][1].x += v;
+                    own[0][2].x -= v;
+                }
+                if (eN) {  // (-1,1,0) into x = nx-1 bounces: its (1,-1,0) value
+                    const float v = gm[1].y;
+                    own[1][0].y += v;
+                    own[1][1].y -= v;
+                    own[1][2].y += v;
+                }
+            }
             if (UP) {
                 shift2(gp, -1, lane);
                 gp[1].y = l31 ? nb2 : gp[1].y;
+                if (XW) gp[1].y = eN ? 0.f : gp[1].y;
             }
             if (DN) {
                 shift2(gm, 1, lane);
                 gm[0].x = l0 ? nb2 : gm[0].x;
+                if (XW) gm[0].x = e0 ? 0.f : gm[0].x;
             }
 #pragma unroll
             for (int j = 0; j < 2; ++j) {
@@ -262,10 +305,11 @@ __device__ __forceinline__ constexpr bool need_m(int mode, int cz) {
 
 using Acc = F2[3][2][4];  // [plane behind / current / ahead][node pair][d, jx, jy, jz]
 
-template <int NH, int MODE, typename T>
+template <int NH, int MODE, bool F, bool XW, typename T>
 __device__ __forceinline__ void phase_a(Acc &acc, const T *stg, float *xbuf, const TiledParams &p, int lane,
                                         int row, int half) {
     constexpr int PM = 0, P0 = 1, PP = 2;
+    const bool e0 = XW && lane == 0 && half == 0, eN = XW && lane == 31 && half == NH - 1;
     constexpr int RL = HG<NH>::RL, XDIR = HG<NH>::XDIR;
     float *up = xbuf + half * HALF, *dn = xbuf + XDIR + half * HALF;
     {
@@ -287,6 +331,11 @@ __device__ __forceinline__ void phase_a(Acc &acc, const T *stg, float *xbuf, con
                 acc[P0][j][1] = add2(fma2(nc.M[j], nc.U[j], acc[P0][j][1]), nc.U[j]);
                 acc[P0][j][2] = add2(fma2(nc.M[j], nc.V[j], acc[P0][j][2]), nc.V[j]);
                 acc[P0][j][3] = add2(fma2(nc.M[j], nc.W[j], acc[P0][j][3]), nc.W[j]);
+                if (F) {  // Eq. force: rho(x,t) g = g + d g, the odd part of f^(e)(rho, g)
+#pragma unroll
+                    for (int c = 0; c < 3; ++c)
+                        acc[P0][j][1 + c] = fma2(nc.D[j], b2(p.g[c]), add2(acc[P0][j][1 + c], b2(p.g[c])));
+                }
             }
             if (MODE != LAST) acc[PP][j][0] = gp;  // first value of the plane ahead
             if (MODE != FIRST) {
@@ -311,10 +360,25 @@ __device__ __forceinline__ void phase_a(Acc &acc, const T *stg, float *xbuf, con
             const float nbv = NH == 2 ? nb_val(cz ? nb.K2 : nb.K1, cz ? nb.sA2 : nb.sA1, cz ? nb.B2 : nb.B1,
                                                cz == 0 ? nb.U : (cz > 0 ? nb.U + nb.W : nb.U - nb.W))
                                       : 0.f;
+            if (XW && MODE == MID) {  // links crossing an x face bounce (see send_rows)
+                if (e0) {  // (1,0,cz) into x = 0: its own (-1,0,-cz) value
+                    const float v = gm[0].x;
+                    acc[P0][0][0].x += v;
+                    acc[P0][0][1].x += v;
+                    if (cz) acc[P0][0][3].x += cz * v;
+                }
+                if (eN) {  // (-1,0,-cz) into x = nx-1: its own (1,0,cz) value
+                    const float v = gp[1].y;
+                    acc[P0][1][0].y += v;
+                    acc[P0][1][1].y -= v;
+                    if (cz) acc[P0][1][3].y -= cz * v;
+                }
+            }
             if (np) {  // c = (1,0,cz): node i feeds node i+1
                 const float eP = gp[1].y;
                 float rP = __shfl_sync(FULL, eP, (lane + 31) & 31);
                 if (NH == 2) rP = lane == 0 ? nbv : rP;
+                if (XW) rP = e0 ? 0.f : rP;
                 const F2 R[2] = {make_float2(rP, gp[0].x), make_float2(gp[0].y, gp[1].x)};
                 F2(&a)[2][4] = acc[pl<PM, P0, PP>(cz)];
 #pragma unroll
@@ -328,6 +392,7 @@ __device__ __forceinline__ void phase_a(Acc &acc, const T *stg, float *xbuf, con
                 const float eM = gm[0].x;
                 float rM = __shfl_sync(FULL, eM, (lane + 1) & 31);
                 if (NH == 2) rM = lane == 31 ? nbv : rM;
+                if (XW) rM = eN ? 0.f : rM;
                 const F2 L[2] = {make_float2(gm[0].y, gm[1].x), make_float2(gm[1].y, rM)};
                 if (cz < 0) {  // -c = (-1,0,1): first x-momentum of the plane ahead
 #pragma unroll
@@ -348,7 +413,8 @@ __device__ __forceinline__ void phase_a(Acc &acc, const T *stg, float *xbuf, con
         }
         const float nb1 = NH == 2 && MODE == MID ? nb_val(nb.K2, nb.sA2, nb.B2, nb.U + nb.V) : 0.f;
         const float nb2 = NH == 2 && MODE == MID ? nb_val(nb.K2, -nb.sA2, nb.B2, nb.V - nb.U) : 0.f;
-        send_rows<NH, MODE>(nc, up + (row + 1) * RL, dn + (row - 1) * RL, row + 1 < ROWS, row > 0, nb1, nb2, lane);
+        send_rows<NH, MODE, XW>(nc, up + (row + 1) * RL, dn + (row - 1) * RL, row + 1 < ROWS, row > 0, nb1, nb2, lane,
+                                e0, eN, MODE == MID ? acc[P0] : nullptr);
     }
     if (row == 0 || row == ROWS - 1) {  // halo rows: y0-1 (staged row 0) feeds row 0, y0+8 (staged 9) row 7
         const int sr = row == 0 ? 0 : TROWS - 1;
@@ -362,9 +428,9 @@ __device__ __forceinline__ void phase_a(Acc &acc, const T *stg, float *xbuf, con
             nb2 = nb_val(hb.K2, -hb.sA2, hb.B2, hb.V - hb.U);
         }
         if (row == 0)
-            send_rows<NH, MODE>(hc, up, nullptr, true, false, nb1, nb2, lane);
+            send_rows<NH, MODE, XW>(hc, up, nullptr, true, false, nb1, nb2, lane, e0, eN);
         else
-            send_rows<NH, MODE>(hc, nullptr, dn + (ROWS - 1) * RL, false, true, nb1, nb2, lane);
+            send_rows<NH, MODE, XW>(hc, nullptr, dn + (ROWS - 1) * RL, false, true, nb1, nb2, lane, e0, eN);
     }
 }
 
@@ -478,9 +544,12 @@ __device__ __forceinline__ void rotate(Acc &acc) {
     }
 }
 
-template <int NH, typename T>
+// V: the variant, 0 = the plain scheme, 1 = with a constant acceleration (Eq. force),
+// 2 = with the x faces walled (the cavity's x = 0 and x = nx-1 faces, lid elsewhere)
+template <int NH, typename T, int V>
 __global__ void __launch_bounds__(HG<NH>::NTH, 2 / NH) k_d3q19_half(const T *__restrict__ in,
                                                                    T *__restrict__ out, TiledParams p) {
+    constexpr bool F = V == 1, XW = V == 2;
     constexpr int XBUF = HG<NH, T>::XBUF, STAGE = HG<NH, T>::STAGE;
     extern __shared__ float4 smem4[];
     float *xs = reinterpret_cast<float *>(smem4);
@@ -526,11 +595,11 @@ __global__ void __launch_bounds__(HG<NH>::NTH, 2 / NH) k_d3q19_half(const T *__r
         const int mode = it.mode();
         if (ok) {
             if (mode == MID) {
-                phase_a<NH, MID>(acc, stage, xbuf, p, lane, row, half);
+                phase_a<NH, MID, F, XW>(acc, stage, xbuf, p, lane, row, half);
             } else if (mode == FIRST) {
-                phase_a<NH, FIRST>(acc, stage, xbuf, p, lane, row, half);
+                phase_a<NH, FIRST, F, XW>(acc, stage, xbuf, p, lane, row, half);
             } else {
-                phase_a<NH, LAST>(acc, stage, xbuf, p, lane, row, half);
+                phase_a<NH, LAST, F, XW>(acc, stage, xbuf, p, lane, row, half);
             }
         }
         if (!ok) failed = 1;  // a wait that gave up, seen by every thread after the barrier
@@ -565,15 +634,15 @@ __global__ void __launch_bounds__(HG<NH>::NTH, 2 / NH) k_d3q19_half(const T *__r
 
 // per device: opt in to the shared-memory size; persistent grid = CTAs per SM x
 // SMs (-1 when a CTA does not fit)
-template <int NH, typename T>
+template <int NH, typename T, int V>
 cudaError_t prepare(int *ctas) {
     static DevSlots slots;
     const int n = per_device(slots, [] {
-        if (cudaFuncSetAttribute(k_d3q19_half<NH, T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+        if (cudaFuncSetAttribute(k_d3q19_half<NH, T, V>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                  (int)HG<NH, T>::BYTES) != cudaSuccess)
             return -1;
         int nb = 0;
-        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_d3q19_half<NH, T>, HG<NH, T>::NTH,
+        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_d3q19_half<NH, T, V>, HG<NH, T>::NTH,
                                                           HG<NH, T>::BYTES) != cudaSuccess || nb < 1)
             return -1;
         return nb * device_sms();
@@ -600,14 +669,23 @@ int half_chunk_planes(int ycols, int nz, int ctas) {
 
 }  // namespace
 
-template <int NH>
+template <int NH, int V>
 static cudaError_t prepare_storage(int storage) {
     switch (storage) {
-        case STORE_F32: return prepare<NH, float>(nullptr);
-        case STORE_BF16: return prepare<NH, __nv_bfloat16>(nullptr);
-        case STORE_F16: return prepare<NH, __half>(nullptr);
+        case STORE_F32: return prepare<NH, float, V>(nullptr);
+        case STORE_BF16: return prepare<NH, __nv_bfloat16, V>(nullptr);
+        case STORE_F16: return prepare<NH, __half, V>(nullptr);
     }
     return cudaErrorInvalidValue;
+}
+
+bool half_xwalls(const StepParams &p) { return p.walled[0] && p.lid_axis != 0; }
+
+// the kernel variant a step needs (-1: none serves it)
+static int half_variant(const StepParams &p) {
+    const bool xw = half_xwalls(p);
+    if (p.has_force && xw) return -1;
+    return xw ? 2 : (p.has_force ? 1 : 0);
 }
 
 bool half_supported(int Q, int storage, const StepParams &p) {
@@ -615,18 +693,26 @@ bool half_supported(int Q, int storage, const StepParams &p) {
     // walled domains (cavity, channel): the kernel wraps every axis and the wall pass
     // after it recomputes every boundary node, the only nodes with a source outside
     if (storage != STORE_F32 && storage != STORE_BF16 && storage != STORE_F16) return false;
-    if (p.has_force || p.gfield || p.sdelta != 0.f || p.scalar || p.bulk) return false;  // plain scheme only
+    // the plain scheme, with or without a constant acceleration (Eq. force)
+    if (p.gfield || p.sdelta != 0.f || p.scalar || p.bulk) return false;
     if ((p.nx != 128 && p.nx != 256) || p.ny % ROWS != 0 || p.ny < ROWS || p.nz < 1) return false;
     if (p.fstride % 8 != 0 || !p.err) return false;  // 16-byte field starts for 2-byte storage
     int dev = 0;
     if (cudaGetDevice(&dev) != cudaSuccess) return false;
-    return (p.nx == 256 ? prepare_storage<2>(storage) : prepare_storage<1>(storage)) == cudaSuccess;
+    const int v = half_variant(p);
+    if (v < 0) return false;
+    cudaError_t e;
+    if (p.nx == 256)
+        e = v == 0 ? prepare_storage<2, 0>(storage) : (v == 1 ? prepare_storage<2, 1>(storage) : prepare_storage<2, 2>(storage));
+    else
+        e = v == 0 ? prepare_storage<1, 0>(storage) : (v == 1 ? prepare_storage<1, 1>(storage) : prepare_storage<1, 2>(storage));
+    return e == cudaSuccess;
 }
 
-template <int NH, typename T>
+template <int NH, typename T, int V>
 static cudaError_t launch_nh(const void *in, void *out, const StepParams &sp, cudaStream_t st) {
     int ctas = 0;
-    cudaError_t e = prepare<NH, T>(&ctas);
+    cudaError_t e = prepare<NH, T, V>(&ctas);
     if (e != cudaSuccess) return e;
     TiledParams p;
     p.nx = sp.nx;
@@ -641,22 +727,30 @@ static cudaError_t launch_nh(const void *in, void *out, const StepParams &sp, cu
     p.a = sp.a;
     p.am1 = sp.am1;
     p.err = sp.err;
+    for (int c = 0; c < 3; ++c) p.g[c] = V == 1 ? sp.force[c] : 0.f;
     const int grid = ctas < p.nitems ? ctas : p.nitems;
-    k_d3q19_half<NH, T><<<(unsigned)grid, HG<NH, T>::NTH, HG<NH, T>::BYTES, st>>>((const T *)in, (T *)out, p);
+    k_d3q19_half<NH, T, V><<<(unsigned)grid, HG<NH, T>::NTH, HG<NH, T>::BYTES, st>>>((const T *)in, (T *)out, p);
     return cudaGetLastError();
+}
+
+template <int V>
+static cudaError_t launch_variant(int storage, const void *in, void *out, const StepParams &sp, cudaStream_t st) {
+    const bool w = sp.nx == 256;
+    switch (storage) {
+        case STORE_F32: return w ? launch_nh<2, float, V>(in, out, sp, st) : launch_nh<1, float, V>(in, out, sp, st);
+        case STORE_BF16:
+            return w ? launch_nh<2, __nv_bfloat16, V>(in, out, sp, st) : launch_nh<1, __nv_bfloat16, V>(in, out, sp, st);
+        case STORE_F16: return w ? launch_nh<2, __half, V>(in, out, sp, st) : launch_nh<1, __half, V>(in, out, sp, st);
+    }
+    return cudaErrorInvalidValue;
 }
 
 cudaError_t launch_step_half(int Q, int storage, const void *in, void *out, const StepParams &sp,
                              cudaStream_t st) {
     if (!half_supported(Q, storage, sp)) return cudaErrorNotSupported;
-    const bool w = sp.nx == 256;
-    switch (storage) {
-        case STORE_F32: return w ? launch_nh<2, float>(in, out, sp, st) : launch_nh<1, float>(in, out, sp, st);
-        case STORE_BF16:
-            return w ? launch_nh<2, __nv_bfloat16>(in, out, sp, st) : launch_nh<1, __nv_bfloat16>(in, out, sp, st);
-        case STORE_F16: return w ? launch_nh<2, __half>(in, out, sp, st) : launch_nh<1, __half>(in, out, sp, st);
-    }
-    return cudaErrorInvalidValue;
+    const int v = half_variant(sp);
+    return v == 0 ? launch_variant<0>(storage, in, out, sp, st)
+                  : (v == 1 ? launch_variant<1>(storage, in, out, sp, st) : launch_variant<2>(storage, in, out, sp, st));
 }
 
 }  // namespace lwacm

@@ -20,6 +20,9 @@ cudaError_t launch_step_generic(int Q, int storage, const void *in, void *out,
                                 const StepParams &p, cudaStream_t st);
 cudaError_t launch_wall_pass(int Q, int storage, const void *in, void *out, const StepParams &p,
                              cudaStream_t st);
+// semi-implicit density pass (Eq. FDcompact_si) after the explicit step in -> out
+cudaError_t launch_semi_implicit(int Q, int storage, const void *in, void *out, const StepParams &p,
+                                 cudaStream_t st);
 cudaError_t launch_convert_in(int storage, int src_dtype, const void *src, void *dst, long long n,
                               cudaStream_t st);
 cudaError_t launch_convert_out(int storage, int dst_dtype, const void *src, void *dst, long long n,
@@ -92,6 +95,9 @@ bool tune_cache_store(const char *path, const std::string &key, const TuneChoice
 // Half-row TMA D3Q19 kernel (nx = 256: two warps per row, 16 warps per CTA; nx = 128:
 // one warp per row).
 bool half_supported(int Q, int storage, const StepParams &p);
+// whether the half-row kernel applies the x-face walls itself (the wall pass then
+// leaves the inner x-face nodes alone)
+bool half_xwalls(const StepParams &p);
 cudaError_t launch_step_half(int Q, int storage, const void *in, void *out, const StepParams &p,
                              cudaStream_t st);
 

@@ -39,6 +39,7 @@ struct lwacm_ctx {
     double alpha = 0;         // diffusivity of the passive scalar (0: no scalar)
     double gamma = 0;         // D2Q9 bulk-viscosity variant (Appendix "Computing derivatives locally")
     bool bulk = false;        // the variant is on: Tr+ - Tr^(e) is the field after the flow fields
+    bool semi = false;        // semi-implicit pressure update (Eq. FDcompact_si)
     int nsc = 0;              // fields stored after the flow fields: the scalar or the trace (0 or 1)
     long long N = 0, Nal = 0;
     double lid[3] = {0, 0, 0}, force[3] = {0, 0, 0}, rho0 = 1.0;
@@ -271,8 +272,14 @@ cudaError_t step_between(lwacm_ctx *c, const void *in, void *out, cudaStream_t s
                                                            in, out, p, st)
                                      : launch_step_generic(c->Q, c->storage, in, out, p, st);
     if (e != cudaSuccess) return e;
-    // the 2D-tile kernel applies the wall rule itself
-    if (c->bc != LWACM_BC_PERIODIC && c->kernel != 6) e = launch_wall_pass(c->Q, c->storage, in, out, p, st);
+    // the 2D-tile kernel applies the wall rule itself; the half-row kernel the x-face
+    // walls of a cavity whose lid is not on an x face
+    if (c->bc != LWACM_BC_PERIODIC && c->kernel != 6) {
+        StepParams pw = p;
+        pw.xfaces_done = c->kernel == 5 && half_xwalls(p) ? 1 : 0;
+        e = launch_wall_pass(c->Q, c->storage, in, out, pw, st);
+    }
+    if (e == cudaSuccess && c->semi) e = launch_semi_implicit(c->Q, c->storage, in, out, p, st);
     return e;
 }
 
@@ -608,6 +615,7 @@ lwacm_status lwacm_set_option(lwacm_ctx *c, int key, double v) {
             if (v != 0 && c->bc != LWACM_BC_PERIODIC)
                 return fail(c, LWACM_E_UNSUPPORTED, "the scalar is for periodic domains");
             if (v != 0 && c->bulk) return fail(c, LWACM_E_UNSUPPORTED, "not with the bulk-viscosity variant");
+            if (v != 0 && c->semi) return fail(c, LWACM_E_UNSUPPORTED, "not with the semi-implicit pressure update");
             c->alpha = v;
             c->nsc = v != 0 ? 1 : 0;
             layout(c);
@@ -620,10 +628,21 @@ lwacm_status lwacm_set_option(lwacm_ctx *c, int key, double v) {
             if (v != 0 && (c->Q != 9 || c->bc != LWACM_BC_PERIODIC))
                 return fail(c, LWACM_E_UNSUPPORTED, "the bulk-viscosity variant is for periodic D2Q9 domains");
             if (v != 0 && c->alpha != 0) return fail(c, LWACM_E_UNSUPPORTED, "not with the passive scalar");
+            if (v != 0 && c->semi) return fail(c, LWACM_E_UNSUPPORTED, "not with the semi-implicit pressure update");
             c->gamma = v;
             c->bulk = v != 0;
             c->nsc = c->bulk ? 1 : 0;
             layout(c);
+            break;
+        }
+        case LWACM_OPT_SEMI_IMPLICIT: {
+            if (v != 0 && v != 1) return fail(c, LWACM_E_ARG, "semi-implicit must be 0 or 1");
+            if (v != 0 && (c->nbatch || c->bc != LWACM_BC_PERIODIC))
+                return fail(c, LWACM_E_UNSUPPORTED, "the semi-implicit pressure update is for single periodic domains");
+            if (v != 0 && (c->alpha != 0 || c->bulk))
+                return fail(c, LWACM_E_UNSUPPORTED, "not with the passive scalar or the bulk-viscosity variant");
+            c->semi = v != 0;
+            drop_graphs(c);
             break;
         }
         case LWACM_OPT_NU_P: {
@@ -971,6 +990,7 @@ lwacm_status lwacm_forward_record(lwacm_ctx *c, long long T, int stride, void *w
         return fail(c, LWACM_E_UNSUPPORTED, "the adjoint needs one domain with FP32 storage");
     if (c->ff_active) return fail(c, LWACM_E_UNSUPPORTED, "the adjoint does not take a force field");
     if (c->nu_p > 0 && c->nu_p != c->nu) return fail(c, LWACM_E_UNSUPPORTED, "the adjoint needs omega_p = omega");
+    if (c->semi) return fail(c, LWACM_E_UNSUPPORTED, "the adjoint is for the explicit update");
     if (c->nsc) return fail(c, LWACM_E_UNSUPPORTED, "the adjoint does not carry the scalar");
     const AdjLayout L = adj_layout(c, T, stride);
     if (bytes < L.bytes) return fail(c, LWACM_E_NOMEM, "adjoint workspace smaller than lwacm_adjoint_workspace_bytes");

@@ -97,6 +97,7 @@ struct StepParams {
     float gamma;          // its gamma (Appendix "Computing derivatives locally")
     int walled[3];      // 1 = half-way walls on both ends of this axis
     int lid_axis;       // axis whose top wall moves with the lid velocity
+    int xfaces_done;    // 1: the interior kernel applied the x-face walls (inner x-face nodes)
     int *err;           // device error word (bounded waits that gave up set it)
 };
 

@@ -8,14 +8,21 @@
 
 namespace {
 
-// packed: element pairs (2k, 2k+1) through the FP32x2 form the half-row kernel uses
-// (an odd last element through the scalar form); otherwise every element through
-// the scalar form of the other row-tiled kernels
+// packed 1: element pairs (2k, 2k+1) through the FP32x2 form the half-row kernel
+// uses (an odd last element through the scalar form); 2: the reciprocal of b that
+// form divides with; 0: every element through the scalar form
 __global__ void k_quotient(const float *__restrict__ a, const float *__restrict__ b, float *__restrict__ out,
                            long long n, int packed) {
     const long long stride = (long long)gridDim.x * blockDim.x;
     const long long t0 = blockIdx.x * (long long)blockDim.x + threadIdx.x;
-    if (packed) {
+    if (packed == 2) {  // the reciprocal RN(1/b) itself (a unused), FP32x2 form
+        for (long long k = t0; k < n / 2; k += stride) {
+            const float2 y = lwacm::tile::div_prep2(make_float2(b[2 * k], b[2 * k + 1])).y;
+            out[2 * k] = y.x;
+            out[2 * k + 1] = y.y;
+        }
+        if ((n & 1) && t0 == 0) out[n - 1] = lwacm::tile::rcp_rn(b[n - 1]);
+    } else if (packed) {
         const long long np = n / 2;
         for (long long k = t0; k < np; k += stride) {
             const float2 a2 = make_float2(a[2 * k], a[2 * k + 1]);
@@ -35,9 +42,9 @@ __global__ void k_quotient(const float *__restrict__ a, const float *__restrict_
 
 extern "C" int lwacm_selftest_quotient(const float *a_dev, const float *b_dev, float *out_dev, long long n,
                                        int packed, void *stream) {
-    if (!a_dev || !b_dev || !out_dev || n < 1 || n >= (1LL << 31)) return LWACM_E_ARG;
+    if (!a_dev || !b_dev || !out_dev || n < 1 || n >= (1LL << 31) || packed < 0 || packed > 2) return LWACM_E_ARG;
     const long long blocks = (n + 255) / 256;
     const unsigned grid = (unsigned)(blocks < 4096 ? blocks : 4096);
-    k_quotient<<<grid, 256, 0, (cudaStream_t)stream>>>(a_dev, b_dev, out_dev, n, packed ? 1 : 0);
+    k_quotient<<<grid, 256, 0, (cudaStream_t)stream>>>(a_dev, b_dev, out_dev, n, packed == 2 ? 2 : (packed ? 1 : 0));
     return cudaGetLastError() == cudaSuccess ? LWACM_OK : LWACM_E_CUDA;
 }

@@ -24,6 +24,7 @@ struct TiledParams {
     long long fstride;
     float s18;           // s / 18 = nu
     float a, am1;        // a = 1 - 6 nu and a - 1 = -6 nu (post_combine, lwacm_core.cuh)
+    float g[3];          // constant acceleration of Eq. force (used by the forced variant)
     int *err;            // error word (timeout)
 };
 
@@ -68,8 +69,9 @@ __device__ __forceinline__ void bulk_g2s(void *dst, const void *src, uint32_t by
 // correctly rounded one (the IEEE round-to-nearest quotient j / rho), formed with
 // Markstein's FMA correction (P. W. Markstein, "Computation of elementary functions
 // on the IBM RISC System/6000 processor", IBM J. Res. Develop. 34 (1990) 111-119):
-// with y = RN(1/b), the correctly rounded reciprocal, and q within one ulp of a/b,
-// the residual r = a - b q is exact in one FMA and RN(q + r y) = RN(a/b). In brief:
+// with y = RN(1/b), the correctly rounded reciprocal (rcp_rn below), and q within
+// one ulp of a/b, the residual r = a - b q is exact in one FMA and
+// RN(q + r y) = RN(a/b). In brief:
 // q + r y misses a/b by (a/b - q)(b y - 1); when a/b lies within 2^-24 ulp of a
 // rounding midpoint every faithful q is about half an ulp from a/b, so the miss is
 // below half an ulp times |b y - 1| < 2^-24, less than a/b's distance to any
@@ -89,14 +91,37 @@ __device__ __forceinline__ void bulk_g2s(void *dst, const void *src, uint32_t by
 // the 128^3 Taylor-Green workload, the IEEE quotient 4.7e-6 u0. The reciprocal's
 // rounding error depends only on the slowly moving density, so it keeps its sign
 // at a node over many steps (as in post_combine of lwacm_core.cuh).
+// RN(1/b) without branches, for normal b with a normal reciprocal: the hardware's
+// approximate reciprocal (relative error far below 2^-20), then two Newton-Raphson
+// steps y <- y + y (1 - b y), each an FMA residual and an FMA update. The first
+// brings y within one ulp; from there Markstein's reciprocal theorem (same paper)
+// makes the second step return RN(1/b) for every b whose significand is not all
+// ones. For those, b = (2 - 2^-23) 2^k, 1/b lies just above the midpoint between
+// 2^(-k-1) and its successor, which the step rounds to even: one ulp low. RN(1/b)
+// then has the last significand bit set, so that bit is set for them.
+__device__ __forceinline__ float rcp_approx(float b) {
+    float y;
+    asm("rcp.approx.f32 %0, %1;" : "=f"(y) : "f"(b));
+    return y;
+}
+__device__ __forceinline__ float rcp_fix(float b, float y) {
+    const unsigned ones = ((__float_as_uint(b) & 0x7fffffu) + 1u) >> 23;  // 1 iff significand all ones
+    return __uint_as_float(__float_as_uint(y) | ones);
+}
+__device__ __forceinline__ float rcp_rn(float b) {
+    float y = rcp_approx(b);
+    y = fmaf(y, fmaf(-b, y, 1.f), y);
+    y = fmaf(y, fmaf(-b, y, 1.f), y);
+    return rcp_fix(b, y);
+}
+
 struct Div1 {
-    float b, nb, y;  // divisor, -divisor, RN(1 / divisor)
+    float nb, y;  // -divisor, RN(1 / divisor)
 };
 __device__ __forceinline__ Div1 div_prep(float b) {
     Div1 d;
-    d.b = b;
     d.nb = -b;
-    d.y = __frcp_rn(b);
+    d.y = rcp_rn(b);
     return d;
 }
 __device__ __forceinline__ float div_apply(float a, const Div1 &d) {
@@ -111,7 +136,11 @@ struct Div2 {
 __device__ __forceinline__ Div2 div_prep2(float2 b) {
     Div2 d;
     d.nb = make_float2(-b.x, -b.y);
-    d.y = make_float2(__frcp_rn(b.x), __frcp_rn(b.y));
+    const float2 one = make_float2(1.f, 1.f);
+    float2 y = make_float2(rcp_approx(b.x), rcp_approx(b.y));
+    y = __ffma2_rn(y, __ffma2_rn(d.nb, y, one), y);
+    y = __ffma2_rn(y, __ffma2_rn(d.nb, y, one), y);
+    d.y = make_float2(rcp_fix(b.x, y.x), rcp_fix(b.y, y.y));
     return d;
 }
 __device__ __forceinline__ float2 div_apply2(float2 a, const Div2 &d) {

@@ -23,7 +23,7 @@ DEVICE, HOST = 0, 1
 OPT_LID_X, OPT_LID_Y, OPT_LID_Z, OPT_FORCE_X, OPT_FORCE_Y, OPT_FORCE_Z = range(6)
 OPT_RHO0, OPT_STORAGE, OPT_GRAPH_CHUNK, OPT_KERNEL = 6, 7, 8, 9
 OPT_BATCH_MODE, OPT_TEST_WITHHOLD, OPT_FORCE_FIELD, OPT_BATCH_TILE, OPT_NU_P = 10, 11, 12, 13, 14
-OPT_SCALAR_ALPHA, OPT_BULK_GAMMA = 15, 16
+OPT_SCALAR_ALPHA, OPT_BULK_GAMMA, OPT_SEMI_IMPLICIT = 15, 16, 17
 # 2D tile shapes of the D2Q9 batched kernel (LWACM_OPT_BATCH_TILE 1..6); 0 = 1D runs
 BATCH_TILE_SHAPES = {0: None, 1: (30, 6), 2: (30, 14), 3: (62, 6), 4: (30, 30), 5: (62, 14), 6: (126, 6)}
 
@@ -116,7 +116,7 @@ class Lwacm:
 
     def __init__(self, lattice, nx, ny, nz=1, nu=0.01, bc=PERIODIC, *, storage=F32, lid=None,
                  force=None, rho0=None, kernel=0, graph_chunk=None, device=None, stream=None,
-                 force_field=False, scalar_alpha=None, bulk_gamma=None):
+                 force_field=False, scalar_alpha=None, bulk_gamma=None, semi_implicit=False):
         lib = load()
         self.lattice, self.nx, self.ny, self.nz = int(lattice), int(nx), int(ny), int(nz)
         self.nu, self.bc = float(nu), int(bc)
@@ -133,6 +133,8 @@ class Lwacm:
             extra[OPT_SCALAR_ALPHA] = scalar_alpha
         if bulk_gamma:
             extra[OPT_BULK_GAMMA] = bulk_gamma
+        if semi_implicit:
+            extra[OPT_SEMI_IMPLICIT] = 1
         self._setup(lib, h, storage, lid, force, rho0, kernel, graph_chunk, device, stream, extra)
 
     def _setup(self, lib, h, storage, lid, force, rho0, kernel, graph_chunk, device, stream,

@@ -117,6 +117,8 @@ def test_selftest_quotient_validation(lib):
     assert lib.lwacm_selftest_quotient(p, p, None, 4, 0, None) == lw.E_ARG
     assert lib.lwacm_selftest_quotient(p, p, p, 0, 1, None) == lw.E_ARG
     assert lib.lwacm_selftest_quotient(p, p, p, 1 << 31, 1, None) == lw.E_ARG
+    assert lib.lwacm_selftest_quotient(p, p, p, 4, 3, None) == lw.E_ARG
+    assert lib.lwacm_selftest_quotient(p, p, p, 4, -1, None) == lw.E_ARG
 
 
 def test_force_field_option(lib):
@@ -281,3 +283,26 @@ def test_d2q9_variant_kernel_choice(lib):
     assert lib.lwacm_set_option(h3, lw.OPT_NU_P, 0.1) == lw.OK
     assert lib.lwacm_kernel_name(h3).decode() == "generic_d3q19"
     lib.lwacm_destroy(h3)
+
+
+def test_semi_implicit_option(lib):
+    """The semi-implicit pressure update (Eq. FDcompact_si) is a 0/1 option for single
+    periodic domains, exclusive with the passive scalar and the bulk-viscosity
+    variant; checked without a device."""
+    from paper_1111_2142_gb300 import lwacm as lw
+    st, h = _create(lib, 9, 40, 24, 1, 0.02, lw.PERIODIC)
+    assert st == lw.OK
+    assert lib.lwacm_set_option(h, lw.OPT_SEMI_IMPLICIT, 2.0) == lw.E_ARG
+    assert lib.lwacm_set_option(h, lw.OPT_SEMI_IMPLICIT, 1.0) == lw.OK
+    assert lib.lwacm_set_option(h, lw.OPT_SCALAR_ALPHA, 0.01) == lw.E_UNSUPPORTED
+    assert lib.lwacm_set_option(h, lw.OPT_BULK_GAMMA, 0.4) == lw.E_UNSUPPORTED
+    assert lib.lwacm_set_option(h, lw.OPT_NU_P, 0.05) == lw.OK
+    assert lib.lwacm_set_option(h, lw.OPT_SEMI_IMPLICIT, 0.0) == lw.OK
+    assert lib.lwacm_set_option(h, lw.OPT_SCALAR_ALPHA, 0.01) == lw.OK
+    assert lib.lwacm_set_option(h, lw.OPT_SEMI_IMPLICIT, 1.0) == lw.E_UNSUPPORTED
+    lib.lwacm_destroy(h)
+    for bc in (lw.CAVITY, lw.CHANNEL):
+        st, h = _create(lib, 19, 8, 8, 8, 0.02, bc)
+        assert st == lw.OK
+        assert lib.lwacm_set_option(h, lw.OPT_SEMI_IMPLICIT, 1.0) == lw.E_UNSUPPORTED
+        lib.lwacm_destroy(h)

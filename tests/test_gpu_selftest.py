@@ -45,6 +45,21 @@ def _mismatches(got, a, b):
     return np.flatnonzero(differ & ~((got == 0) & (ref == 0)))
 
 
+def test_reciprocal_every_divisor_in_half_to_two(quotient):
+    """The quotient divides with RN(1/b), the correctly rounded reciprocal (Markstein's
+    correction needs it): for every FP32 b in [1/2, 2) (2^24 values, among them the
+    all-ones significands 1 - 2^-24 and 2 - 2^-23 that the Newton step rounds low)
+    and for powers of two times them up to 2^+-60, the kernel's reciprocal equals the
+    host's IEEE 1/b bit for bit."""
+    b = _f32_range(0.5, 2.0)
+    for scale in (1.0, 2.0 ** 60, 2.0 ** -60):
+        bs = (b * np.float32(scale)).astype(np.float32)
+        got = quotient(np.ones_like(bs), bs, 2)
+        ref = np.divide(np.float32(1.0), bs, dtype=np.float32)
+        bad = np.flatnonzero(got.view(np.uint32) != ref.view(np.uint32))
+        assert bad.size == 0, (scale, bs[bad[:5]], got[bad[:5]], ref[bad[:5]])
+
+
 @pytest.mark.parametrize("packed", [1, 0])
 def test_quotient_every_divisor_in_half_to_two(quotient, packed):
     """The kernels form u = j / rho (step a5). For every FP32 divisor in [1/2, 2)
