@@ -82,6 +82,7 @@ struct lwacm_ctx {
     size_t adj_bytes = 0;
     long long rec_T = -1;
     int rec_S = 0;
+    bool rec_last_kept = false;  // the last segment's states are in the segment buffer
 };
 
 namespace {
@@ -997,12 +998,24 @@ lwacm_status lwacm_forward_record(lwacm_ctx *c, long long T, int stride, void *w
     c->adj = (char *)ws;
     c->adj_bytes = bytes;
     const size_t sb = (size_t)c->Nal * 4 * c->nf;
+    c->rec_last_kept = false;
     for (long long k = 0; k < L.K; ++k) {
-        CK(c, cudaMemcpyAsync(c->adj + L.ckpt + k * L.state, bufp(c, c->cur), sb, cudaMemcpyDeviceToDevice,
-                              c->stream),
-           "checkpoint copy");
+        char *ck = c->adj + L.ckpt + k * L.state;
+        CK(c, cudaMemcpyAsync(ck, bufp(c, c->cur), sb, cudaMemcpyDeviceToDevice, c->stream), "checkpoint copy");
         const long long n = std::min<long long>(L.S, T - k * L.S);
-        if (n > 0) {
+        if (n > 0 && k == L.K - 1) {
+            // the last segment steps through the segment buffer, whose states the
+            // backward sweep then reads without recomputing them; its last state
+            // becomes the context's current state
+            char *seg = c->adj + L.seg;
+            for (long long j = 0; j < n; ++j)
+                CK(c, step_between(c, j == 0 ? ck : seg + j * L.state, seg + (j + 1) * L.state, c->stream),
+                   "recorded step");
+            CK(c, cudaMemcpyAsync(bufp(c, c->cur), seg + n * L.state, sb, cudaMemcpyDeviceToDevice, c->stream),
+               "final state");
+            c->steps += n;
+            c->rec_last_kept = true;
+        } else if (n > 0) {
             s = lwacm_step(c, n);
             if (s != LWACM_OK) return s;
         }
@@ -1024,8 +1037,7 @@ lwacm_status lwacm_backward(lwacm_ctx *c, const void *ld, const void *lux, const
     if (dtype != LWACM_F32 && dtype != LWACM_F64) return fail(c, LWACM_E_ARG, "dtype must be F32 or F64");
     const long long T = c->rec_T;
     const AdjLayout L = adj_layout(c, T, c->rec_S);
-    const size_t sb = (size_t)c->Nal * 4 * c->nf;
-    const size_t fb = (size_t)c->Nal * 4;
+        const size_t fb = (size_t)c->Nal * 4;
     char *A = c->adj;
     // lambda in and out in lam0; (Dbar, Jbar) alternate between the other two
     float *lam0 = (float *)(A + L.lam);
@@ -1042,19 +1054,23 @@ lwacm_status lwacm_backward(lwacm_ctx *c, const void *ld, const void *lux, const
         const long long t0 = k * L.S;
         const long long len = std::min<long long>(L.S, T - t0);
         char *seg = A + L.seg;
-        CK(c, cudaMemcpyAsync(seg, A + L.ckpt + k * L.state, sb, cudaMemcpyDeviceToDevice, c->stream),
-           "segment restore");
-        for (long long j = 0; j < len; ++j)
-            CK(c, step_between(c, seg + j * L.state, seg + (j + 1) * L.state, c->stream), "segment recompute");
+        // the state at step j of the segment: the checkpoint itself for j = 0
+        char *ck = A + L.ckpt + k * L.state;
+        auto state = [&](long long j) { return j == 0 ? ck : seg + j * L.state; };
+        if (!(k == L.K - 1 && c->rec_last_kept))
+            for (long long j = 0; j < len; ++j)
+                CK(c, step_between(c, state(j), seg + (j + 1) * L.state, c->stream), "segment recompute");
         for (long long j = len - 1; j >= 0; --j) {
             const bool first = k == L.K - 1 && j == len - 1, last = k == 0 && j == 0;
-            CK(c, launch_adjoint_step(c->Q, (const float *)(seg + j * L.state),
-                                      (const float *)(seg + (j + 1) * L.state), first ? lam0 : nullptr, dj[cur],
-                                      last ? nullptr : dj[1 - cur], lam0, p, part, done, total, c->stream),
+            CK(c, launch_adjoint_step(c->Q, (const float *)state(j), (const float *)state(j + 1),
+                                      first ? lam0 : nullptr, dj[cur], last ? nullptr : dj[1 - cur], lam0, p, part,
+                                      done, total, c->stream),
                "adjoint step");
             cur ^= 1;
         }
     }
+    // a recomputed segment overwrote the kept one (a second backward recomputes it)
+    c->rec_last_kept = c->rec_last_kept && L.K == 1;
     void *gout[4] = {gd, gux, guy, guz};
     for (int f = 0; f < c->nf; ++f) {
         if (dtype == LWACM_F32)

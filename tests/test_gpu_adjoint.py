@@ -43,9 +43,14 @@ def gpu_grad(lw, Q, f, target, nu, T, stride=0, force=None, bc=0, lid=None):
     return loss, [x.cpu().numpy() for x in g], gnu
 
 
+# (8, 16, 128), (5, 8, 256), (9, 24, 128) and (4, 8, 128) with a force run the
+# row-tiled gather (128- and 256-node rows: several columns, ragged z-runs, one
+# plane's rows wrapping in y); the other shapes the tiled gather
 @pytest.mark.parametrize("Q,shape,force", [(19, (8, 10, 12), None), (9, (16, 20), None),
                                            (19, (6, 8, 10), (2e-4, -1e-4, 5e-5)),
-                                           (9, (12, 16), (1e-4, 2e-4))])
+                                           (9, (12, 16), (1e-4, 2e-4)),
+                                           (19, (8, 16, 128), None), (19, (5, 8, 256), None),
+                                           (19, (9, 24, 128), None), (19, (4, 8, 128), (2e-4, -1e-4, 5e-5))])
 def test_adjoint_matches_fp64_oracle(lw, Q, shape, force):
     T, nu = 6, 0.03
     st = inputs.smooth_random(shape, seed=51, u_amp=0.05, d_amp=0.01)
