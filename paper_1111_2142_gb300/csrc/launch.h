@@ -95,6 +95,10 @@ bool tune_cache_store(const char *path, const std::string &key, const TuneChoice
 // Half-row TMA D3Q19 kernel (nx = 256: two warps per row, 16 warps per CTA; nx = 128:
 // one warp per row).
 bool half_supported(int Q, int storage, const StepParams &p);
+// the passive scalar (Eq. ACM2.0t) on its own row-tiled D3Q19 kernel (FP32,
+// periodic, nx 128 / 256, ny % 8 == 0), run after the flow kernel on the same state
+bool scalar_rows_supported(int Q, int storage, const StepParams &p);
+cudaError_t launch_scalar_rows(const void *in, void *out, const StepParams &p, cudaStream_t st);
 // whether the half-row kernel applies the x-face walls itself (the wall pass then
 // leaves the inner x-face nodes alone)
 bool half_xwalls(const StepParams &p);

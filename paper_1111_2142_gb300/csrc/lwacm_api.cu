@@ -40,6 +40,7 @@ struct lwacm_ctx {
     double gamma = 0;         // D2Q9 bulk-viscosity variant (Appendix "Computing derivatives locally")
     bool bulk = false;        // the variant is on: Tr+ - Tr^(e) is the field after the flow fields
     bool semi = false;        // semi-implicit pressure update (Eq. FDcompact_si)
+    bool scalar_rows = false; // the passive scalar on its own row-tiled kernel after the flow kernel
     int nsc = 0;              // fields stored after the flow fields: the scalar or the trace (0 or 1)
     long long N = 0, Nal = 0;
     double lid[3] = {0, 0, 0}, force[3] = {0, 0, 0}, rho0 = 1.0;
@@ -201,7 +202,12 @@ bool choose_kernel(lwacm_ctx *c) {
     }
     const StepParams p = params(c);
     const bool dev = c->bound;
-    const bool h_ok = dev && half_supported(c->Q, c->storage, p);
+    // the passive scalar: on its own row-tiled kernel when the shape allows, the
+    // flow then on the half-row kernel; otherwise both on the generic kernel
+    c->scalar_rows = dev && p.scalar && scalar_rows_supported(c->Q, c->storage, p);
+    StepParams pf = p;
+    if (c->scalar_rows) pf.scalar = 0;
+    const bool h_ok = dev && half_supported(c->Q, c->storage, pf);
     const bool s_ok = tiles2d_supported(c->Q, c->storage, p);
     bool ok = true;
     switch (c->kernel_opt) {
@@ -213,7 +219,8 @@ bool choose_kernel(lwacm_ctx *c) {
     static const char *gname[2] = {"generic_d2q9", "generic_d3q19"};
     static const char *sname[7] = {"tiles2d_d2q9_30x14", "tiles2d_d2q9_30x6",  "tiles2d_d2q9_30x14", "tiles2d_d2q9_62x6",
                                    "tiles2d_d2q9_30x30", "tiles2d_d2q9_62x14", "tiles2d_d2q9_126x6"};
-    c->kname = c->kernel == 5   ? "half_d3q19_tma"
+    if (c->kernel != 5) c->scalar_rows = false;
+    c->kname = c->kernel == 5   ? (c->scalar_rows ? "half_d3q19_tma+scalar_rows" : "half_d3q19_tma")
                : c->kernel == 6 ? sname[c->batch_shape >= 0 && c->batch_shape < 7 ? c->batch_shape : 0]
                                 : gname[c->Q == 19 ? 1 : 0];
     return ok;
@@ -268,7 +275,9 @@ BatchParams batch_params(lwacm_ctx *c) {
 cudaError_t step_between(lwacm_ctx *c, const void *in, void *out, cudaStream_t st) {
     if (c->nbatch) return launch_batch_step(c->Q, c->storage, in, out, batch_params(c), st);
     const StepParams p = params(c);
-    cudaError_t e = c->kernel == 5   ? launch_step_half(c->Q, c->storage, in, out, p, st)
+    StepParams pf = p;
+    if (c->scalar_rows) pf.scalar = 0;  // the flow kernel leaves the scalar to its own kernel
+    cudaError_t e = c->kernel == 5   ? launch_step_half(c->Q, c->storage, in, out, pf, st)
                     : c->kernel == 6 ? launch_step_tiles2d(c->Q, c->storage, c->batch_shape > 0 ? c->batch_shape : 2,
                                                            in, out, p, st)
                                      : launch_step_generic(c->Q, c->storage, in, out, p, st);
@@ -281,6 +290,7 @@ cudaError_t step_between(lwacm_ctx *c, const void *in, void *out, cudaStream_t s
         e = launch_wall_pass(c->Q, c->storage, in, out, pw, st);
     }
     if (e == cudaSuccess && c->semi) e = launch_semi_implicit(c->Q, c->storage, in, out, p, st);
+    if (e == cudaSuccess && c->scalar_rows) e = launch_scalar_rows(in, out, p, st);
     return e;
 }
 

@@ -16,8 +16,17 @@ def lw():
     return lwacm
 
 
-@pytest.mark.parametrize("Q,shape,T", [(9, (48, 64), 150), (9, (17, 23), 60), (19, (10, 12, 14), 40)])
-def test_scalar_matches_oracle(lw, Q, shape, T):
+# D2Q9 and odd D3Q19 shapes run on the generic kernel (flow and scalar in one
+# pass); D3Q19 boxes with 128- or 256-node rows and ny % 8 == 0 run the flow on the
+# half-row kernel and the scalar on its own row-tiled kernel (several columns,
+# ragged z-chunks, one plane, y wrapping inside a column)
+@pytest.mark.parametrize("Q,shape,T,kern", [(9, (48, 64), 150, "generic"), (9, (17, 23), 60, "generic"),
+                                            (19, (10, 12, 14), 40, "generic"),
+                                            (19, (6, 16, 128), 40, "half_d3q19_tma+scalar_rows"),
+                                            (19, (5, 8, 256), 40, "half_d3q19_tma+scalar_rows"),
+                                            (19, (37, 24, 128), 30, "half_d3q19_tma+scalar_rows"),
+                                            (19, (1, 8, 256), 20, "half_d3q19_tma+scalar_rows")])
+def test_scalar_matches_oracle(lw, Q, shape, T, kern):
     """Flow and scalar together, every node against the oracle; the scalar's total
     is conserved to FP32 rounding."""
     f = inputs.smooth_random(shape, seed=31, u_amp=0.05, d_amp=0.01)
@@ -25,7 +34,7 @@ def test_scalar_matches_oracle(lw, Q, shape, T):
     nz = 1 if Q == 9 else shape[0]
     ny, nx = shape[-2], shape[-1]
     sim = lw.Lwacm(Q, nx, ny, nz, 0.02, scalar_alpha=0.03)
-    assert sim.kernel_name.startswith("generic")
+    assert sim.kernel_name.startswith(kern)
     sim.set_fields(*f)
     sim.set_scalar(T0)
     sim.step(T)
