@@ -584,6 +584,12 @@ def run_case(name, steps):
         sim = lw.Lwacm(lw.D3Q19, 256, 256, 256, 0.01, lw.CAVITY, lid=(2 ** 0.5 / 20, 2 ** 0.5 / 20, 0.0))
         sim.set_fields(z, z, z, z)
         sim.step(steps)
+    elif name == "scalar":  # D3Q19 256^3 Taylor-Green with a passive scalar (half-row + scalar row kernels)
+        n3 = 256
+        sim = lw.Lwacm(lw.D3Q19, n3, n3, n3, NU, scalar_alpha=0.01)
+        sim.set_fields(*inputs.tgv3d(n3, u0=U0))
+        sim.set_scalar(torch.cos(2 * torch.pi * torch.arange(n3, device="cuda") / n3).expand(n3, n3, n3).contiguous())
+        sim.step(steps)
     elif name == "bulk2d":  # D2Q9 4096^2 bulk-viscosity variant, gamma 0.4 (2D tiles 30x14)
         sim = lw.Lwacm(lw.D2Q9, 4096, 4096, 1, 0.01, bulk_gamma=0.4)
         sim.set_fields(*inputs.gtg_state(4096, 0.0))
@@ -608,7 +614,7 @@ def main():
     ap.add_argument("--cpu-steps", type=int, default=40)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-variants", action="store_true")
-    ap.add_argument("--profile-case", choices=["adjoint", "ensemble", "cavity", "cavity3d", "bulk2d"],
+    ap.add_argument("--profile-case", choices=["adjoint", "ensemble", "cavity", "cavity3d", "bulk2d", "scalar"],
                     help="run one variant workload for --steps steps without timing (for profilers)")
     args = ap.parse_args()
     if args.warmup < 3:
