@@ -53,39 +53,51 @@ struct ScalarParams {
     int *err;
 };
 
-// per node: the four link-value coefficients of each weight class,
-// h = K + e (B e +- O): K = w (1 - a_t)(T - 3/2 |u|^2), O = 3 w T, B uniform
+// The four nodes of a lane are held as two pairs, (0,1) and (2,3), in FP32x2
+// registers: the same operation on two nodes issues as one packed instruction (same
+// rounding). Unlike the flow kernel, this one has FMA-pipe capacity to spare, so the
+// link-pair values are packed too.
+using F2 = float2;
+__device__ __forceinline__ F2 b2(float v) { return make_float2(v, v); }
+__device__ __forceinline__ F2 add2(F2 a, F2 b) { return __fadd2_rn(a, b); }
+__device__ __forceinline__ F2 mul2(F2 a, F2 b) { return __fmul2_rn(a, b); }
+__device__ __forceinline__ F2 fma2(F2 a, F2 b, F2 c) { return __ffma2_rn(a, b, c); }
+
+// per node pair: the link-value coefficients of each weight class,
+// h = K + e (B e +- O): K = w (1 - a_t)(T - 3/2 |u|^2), O = 3 w T (nO = -O), B uniform
 struct SC {
-    float U[4], V[4], W[4], K1[4], O1[4], K2[4], O2[4], KR[4];  // KR: the rest link + a_t T
+    F2 U[2], V[2], W[2], K1[2], O1[2], nO1[2], K2[2], O2[2], nO2[2], KR[2];  // KR: the rest link + a_t T
 };
 
 __device__ __forceinline__ void s_consts(SC &c, const float *row, int rstride, int lane, const ScalarParams &p) {
     const float4 t4 = ld4(row + lane * 4), u4 = ld4(row + rstride + lane * 4);
     const float4 v4 = ld4(row + 2 * rstride + lane * 4), w4 = ld4(row + 3 * rstride + lane * 4);
-    const float tt[4] = {t4.x, t4.y, t4.z, t4.w}, uu[4] = {u4.x, u4.y, u4.z, u4.w};
-    const float vv[4] = {v4.x, v4.y, v4.z, v4.w}, ww[4] = {w4.x, w4.y, w4.z, w4.w};
+    const F2 tt[2] = {make_float2(t4.x, t4.y), make_float2(t4.z, t4.w)};
+    c.U[0] = make_float2(u4.x, u4.y);
+    c.U[1] = make_float2(u4.z, u4.w);
+    c.V[0] = make_float2(v4.x, v4.y);
+    c.V[1] = make_float2(v4.z, v4.w);
+    c.W[0] = make_float2(w4.x, w4.y);
+    c.W[1] = make_float2(w4.z, w4.w);
 #pragma unroll
-    for (int n = 0; n < 4; ++n) {
-        const float q = fmaf(uu[n], uu[n], fmaf(vv[n], vv[n], ww[n] * ww[n]));
-        const float K = p.kt * fmaf(-1.5f, q, tt[n]);  // (1 - a_t)(T - 3/2 q)
-        c.U[n] = uu[n];
-        c.V[n] = vv[n];
-        c.W[n] = ww[n];
-        c.K1[n] = K * (1.f / 18.f);
-        c.K2[n] = K * (1.f / 36.f);
-        c.O1[n] = tt[n] * (1.f / 6.f);   // 3 T / 18
-        c.O2[n] = tt[n] * (1.f / 12.f);  // 3 T / 36
-        c.KR[n] = fmaf(p.at, tt[n], K * (1.f / 3.f));
+    for (int j = 0; j < 2; ++j) {
+        const F2 q = fma2(c.U[j], c.U[j], fma2(c.V[j], c.V[j], mul2(c.W[j], c.W[j])));
+        const F2 K = mul2(b2(p.kt), fma2(b2(-1.5f), q, tt[j]));  // (1 - a_t)(T - 3/2 q)
+        c.K1[j] = mul2(K, b2(1.f / 18.f));
+        c.K2[j] = mul2(K, b2(1.f / 36.f));
+        c.O1[j] = mul2(tt[j], b2(1.f / 6.f));     // 3 T / 18
+        c.nO1[j] = mul2(tt[j], b2(-1.f / 6.f));
+        c.O2[j] = mul2(tt[j], b2(1.f / 12.f));    // 3 T / 36
+        c.nO2[j] = mul2(tt[j], b2(-1.f / 12.f));
+        c.KR[j] = fma2(b2(p.at), tt[j], mul2(K, b2(1.f / 3.f)));
     }
 }
 
-// the pair (c, -c) at node n: K + B e^2 +- O e
-__device__ __forceinline__ void s_pair(const SC &c, int n, float e, bool diag, float b1, float b2, float &hp,
-                                       float &hm) {
-    const float cm = fmaf((diag ? b2 : b1) * e, e, diag ? c.K2[n] : c.K1[n]);
-    const float O = diag ? c.O2[n] : c.O1[n];
-    hp = fmaf(O, e, cm);
-    hm = fmaf(-O, e, cm);
+// the pair (c, -c) at node pair j: K + B e^2 +- O e
+__device__ __forceinline__ void s_pair(const SC &c, int j, F2 e, bool diag, float b1, float b2v, F2 &hp, F2 &hm) {
+    const F2 cm = fma2(mul2(b2(diag ? b2v : b1), e), e, diag ? c.K2[j] : c.K1[j]);
+    hp = fma2(diag ? c.O2[j] : c.O1[j], e, cm);
+    hm = fma2(diag ? c.nO2[j] : c.nO1[j], e, cm);
 }
 
 // the boundary neighbour of a half row (NH = 2): lanes 0-15 take node x0 - 1,
@@ -109,36 +121,32 @@ __device__ __forceinline__ SN s_nb(const float *row, int rstride, int nbx, float
 __device__ __forceinline__ float s_nbv(float K, float sO, float B, float e) { return fmaf(sO, e, fmaf(B * e, e, K)); }
 
 // c.u of the five pairs with c_y = +1: (0,1,0), (1,1,0), (-1,1,0), (0,1,1), (0,1,-1)
-__device__ __forceinline__ float s_ye(const SC &c, int k, int n) {
-    const float u = c.U[n], v = c.V[n], w = c.W[n];
-    return k == 0 ? v : (k == 1 ? u + v : (k == 2 ? v - u : (k == 3 ? v + w : v - w)));
+__device__ __forceinline__ F2 s_ye(const SC &c, int k, int j) {
+    const F2 u = c.U[j], v = c.V[j], w = c.W[j];
+    return k == 0 ? v
+                  : (k == 1 ? add2(u, v)
+                            : (k == 2 ? fma2(u, b2(-1.f), v) : (k == 3 ? add2(v, w) : fma2(w, b2(-1.f), v))));
 }
 
 // shift four lane-held values by +1 (g[x] <- g[x-1]) or -1 (g[x] <- g[x+1])
-__device__ __forceinline__ void s_shift(float (&g)[4], int dir, int lane) {
+__device__ __forceinline__ void s_shift(F2 (&g)[2], int dir, int lane) {
     if (dir > 0) {
-        const float e = __shfl_sync(FULL, g[3], (lane + 31) & 31);
-        g[3] = g[2];
-        g[2] = g[1];
-        g[1] = g[0];
-        g[0] = e;
+        const float e = __shfl_sync(FULL, g[1].y, (lane + 31) & 31);
+        g[1] = make_float2(g[0].y, g[1].x);
+        g[0] = make_float2(e, g[0].x);
     } else {
-        const float e = __shfl_sync(FULL, g[0], (lane + 1) & 31);
-        g[0] = g[1];
-        g[1] = g[2];
-        g[2] = g[3];
-        g[3] = e;
+        const float e = __shfl_sync(FULL, g[0].x, (lane + 1) & 31);
+        g[0] = make_float2(g[0].y, g[1].x);
+        g[1] = make_float2(g[1].y, e);
     }
 }
-__device__ __forceinline__ void s_st(float *slot, const float (&o)[4], int lane) {
-    *reinterpret_cast<float4 *>(slot + spos(lane, 0)) = make_float4(o[0], o[1], o[2], o[3]);
+__device__ __forceinline__ void s_st(float *slot, const F2 (&o)[2], int lane) {
+    *reinterpret_cast<float4 *>(slot + spos(lane, 0)) = make_float4(o[0].x, o[0].y, o[1].x, o[1].y);
 }
-__device__ __forceinline__ void s_ld(const float *slot, float (&o)[4], int lane) {
+__device__ __forceinline__ void s_ld(const float *slot, F2 (&o)[2], int lane) {
     const float4 t = *reinterpret_cast<const float4 *>(slot + spos(lane, 0));
-    o[0] = t.x;
-    o[1] = t.y;
-    o[2] = t.z;
-    o[3] = t.w;
+    o[0] = make_float2(t.x, t.y);
+    o[1] = make_float2(t.z, t.w);
 }
 
 // The row-crossing values of one half row, sent up (c_y = +1, when UP) and down
@@ -152,50 +160,50 @@ __device__ __forceinline__ void s_send(const SC &c, const ScalarParams &p, float
     constexpr int XSLOT = SG<NH>::XSLOT;
     const bool l0 = lane == 0 && NH == 2, l31 = lane == 31 && NH == 2;
     if (MODE == MID) {
-        float u0[4], d0[4];
+        F2 u0[2], d0[2];
 #pragma unroll
-        for (int n = 0; n < 4; ++n) s_pair(c, n, s_ye(c, 0, n), false, p.b1, p.b2, u0[n], d0[n]);
+        for (int j = 0; j < 2; ++j) s_pair(c, j, s_ye(c, 0, j), false, p.b1, p.b2, u0[j], d0[j]);
 #pragma unroll
         for (int k = 1; k <= 2; ++k) {  // k = 1: (1,1,0) up x <- x-1, (-1,-1,0) down x <- x+1; k = 2 mirrored
-            float hp[4], hm[4];
+            F2 hp[2], hm[2];
 #pragma unroll
-            for (int n = 0; n < 4; ++n) s_pair(c, n, s_ye(c, k, n), true, p.b1, p.b2, hp[n], hm[n]);
+            for (int j = 0; j < 2; ++j) s_pair(c, j, s_ye(c, k, j), true, p.b1, p.b2, hp[j], hm[j]);
             if (UP) {
                 s_shift(hp, k == 1 ? 1 : -1, lane);
-                if (k == 1) hp[0] = l0 ? nb1 : hp[0];
-                else hp[3] = l31 ? nb2 : hp[3];
+                if (k == 1) hp[0].x = l0 ? nb1 : hp[0].x;
+                else hp[1].y = l31 ? nb2 : hp[1].y;
             }
             if (DN) {
                 s_shift(hm, k == 1 ? -1 : 1, lane);
-                if (k == 1) hm[3] = l31 ? nb1 : hm[3];
-                else hm[0] = l0 ? nb2 : hm[0];
+                if (k == 1) hm[1].y = l31 ? nb1 : hm[1].y;
+                else hm[0].x = l0 ? nb2 : hm[0].x;
             }
 #pragma unroll
-            for (int n = 0; n < 4; ++n) {
-                u0[n] += hp[n];
-                d0[n] += hm[n];
+            for (int j = 0; j < 2; ++j) {
+                u0[j] = add2(u0[j], hp[j]);
+                d0[j] = add2(d0[j], hm[j]);
             }
         }
         if (UP) s_st(ub, u0, lane);
         if (DN) s_st(db, d0, lane);
     }
     {  // k = 3: c = (0,1,1) up -> ahead, -c = (0,-1,-1) down -> behind
-        float hp[4], hm[4];
+        F2 hp[2], hm[2];
 #pragma unroll
-        for (int n = 0; n < 4; ++n) s_pair(c, n, s_ye(c, 3, n), true, p.b1, p.b2, hp[n], hm[n]);
+        for (int j = 0; j < 2; ++j) s_pair(c, j, s_ye(c, 3, j), true, p.b1, p.b2, hp[j], hm[j]);
         if (UP && MODE != LAST) s_st(ub + XSLOT, hp, lane);
         if (DN && MODE != FIRST) s_st(db + 2 * XSLOT, hm, lane);
     }
     {  // k = 4: c = (0,1,-1) up -> behind, -c = (0,-1,1) down -> ahead
-        float hp[4], hm[4];
+        F2 hp[2], hm[2];
 #pragma unroll
-        for (int n = 0; n < 4; ++n) s_pair(c, n, s_ye(c, 4, n), true, p.b1, p.b2, hp[n], hm[n]);
+        for (int j = 0; j < 2; ++j) s_pair(c, j, s_ye(c, 4, j), true, p.b1, p.b2, hp[j], hm[j]);
         if (UP && MODE != FIRST) s_st(ub + 2 * XSLOT, hp, lane);
         if (DN && MODE != LAST) s_st(db + XSLOT, hm, lane);
     }
 }
 
-using SAcc = float[3][4];  // [plane behind / current / ahead][node]
+using SAcc = F2[3][2];  // [plane behind / current / ahead][node pair]
 
 template <int NH, int MODE>
 __device__ __forceinline__ void s_phase_a(SAcc &acc, const float *stg, float *xbuf, const ScalarParams &p,
@@ -211,44 +219,42 @@ __device__ __forceinline__ void s_phase_a(SAcc &acc, const float *stg, float *xb
         SN nb{};
         if (NH == 2) nb = s_nb(stg + (row + 1) * RL, TROWS * RL, nbx, sgn, p);
 #pragma unroll
-        for (int n = 0; n < 4; ++n) {
-            float hp, hm;
-            s_pair(c, n, c.W[n], false, p.b1, p.b2, hp, hm);  // (0,0,+1) / (0,0,-1)
-            if (MODE == MID) acc[P0][n] += c.KR[n];             // rest link and a_t T(x)
-            if (MODE != LAST) acc[PP][n] = hp;                  // first value of the plane ahead
-            if (MODE != FIRST) acc[PM][n] += hm;
+        for (int j = 0; j < 2; ++j) {
+            F2 hp, hm;
+            s_pair(c, j, c.W[j], false, p.b1, p.b2, hp, hm);  // (0,0,+1) / (0,0,-1)
+            if (MODE == MID) acc[P0][j] = add2(acc[P0][j], c.KR[j]);  // rest link and a_t T(x)
+            if (MODE != LAST) acc[PP][j] = hp;                          // first value of the plane ahead
+            if (MODE != FIRST) acc[PM][j] = add2(acc[PM][j], hm);
         }
 #pragma unroll
         for (int cz = -1; cz <= 1; ++cz) {
             const bool np = MODE == MID || (MODE == FIRST ? cz > 0 : cz < 0);
             const bool nm = MODE == MID || (MODE == FIRST ? cz < 0 : cz > 0);
             if (!np && !nm) continue;
-            float hp[4], hm[4];
+            F2 hp[2], hm[2];
 #pragma unroll
-            for (int n = 0; n < 4; ++n) {
-                const float e = cz == 0 ? c.U[n] : (cz > 0 ? c.U[n] + c.W[n] : c.U[n] - c.W[n]);
-                s_pair(c, n, e, cz != 0, p.b1, p.b2, hp[n], hm[n]);
+            for (int j = 0; j < 2; ++j) {
+                const F2 e = cz == 0 ? c.U[j] : (cz > 0 ? add2(c.U[j], c.W[j]) : fma2(c.W[j], b2(-1.f), c.U[j]));
+                s_pair(c, j, e, cz != 0, p.b1, p.b2, hp[j], hm[j]);
             }
             const float nbv = NH == 2 ? s_nbv(cz ? nb.K2 : nb.K1, cz ? nb.sO2 : nb.sO1, cz ? p.b2 : p.b1,
                                               cz == 0 ? nb.U : (cz > 0 ? nb.U + nb.W : nb.U - nb.W))
                                       : 0.f;
             if (np) {  // c = (1,0,cz): node n feeds node n+1 in plane +cz
-                float r = __shfl_sync(FULL, hp[3], (lane + 31) & 31);
+                float r = __shfl_sync(FULL, hp[1].y, (lane + 31) & 31);
                 if (NH == 2) r = lane == 0 ? nbv : r;
-                float(&a)[4] = acc[pl<PM, P0, PP>(cz)];
-                a[0] += r;
-                a[1] += hp[0];
-                a[2] += hp[1];
-                a[3] += hp[2];
+                const F2 R[2] = {make_float2(r, hp[0].x), make_float2(hp[0].y, hp[1].x)};
+                F2(&a)[2] = acc[pl<PM, P0, PP>(cz)];
+                a[0] = add2(a[0], R[0]);
+                a[1] = add2(a[1], R[1]);
             }
             if (nm) {  // -c = (-1,0,-cz): node n feeds node n-1 in plane -cz
-                float r = __shfl_sync(FULL, hm[0], (lane + 1) & 31);
+                float r = __shfl_sync(FULL, hm[0].x, (lane + 1) & 31);
                 if (NH == 2) r = lane == 31 ? nbv : r;
-                float(&a)[4] = acc[pl<PM, P0, PP>(-cz)];
-                a[0] += hm[1];
-                a[1] += hm[2];
-                a[2] += hm[3];
-                a[3] += r;
+                const F2 Lv[2] = {make_float2(hm[0].y, hm[1].x), make_float2(hm[1].y, r)};
+                F2(&a)[2] = acc[pl<PM, P0, PP>(-cz)];
+                a[0] = add2(a[0], Lv[0]);
+                a[1] = add2(a[1], Lv[1]);
             }
         }
         const float nb1 = NH == 2 && MODE == MID ? s_nbv(nb.K2, nb.sO2, p.b2, nb.U + nb.V) : 0.f;
@@ -278,27 +284,28 @@ __device__ __forceinline__ void s_phase_b(SAcc &acc, const float *xbuf, float *t
     constexpr int PM = 0, P0 = 1, PP = 2;
     constexpr int RL = SG<NH>::RL, XDIR = SG<NH>::XDIR, XSLOT = SG<NH>::XSLOT;
     const float *up = xbuf + row * RL + half * SHALF, *dn = xbuf + XDIR + row * RL + half * SHALF;
-    float o[4], q[4];
+    F2 o[2], q[2];
     if (MODE == MID) {
         s_ld(up, o, lane);
         s_ld(dn, q, lane);
 #pragma unroll
-        for (int n = 0; n < 4; ++n) acc[P0][n] += o[n] + q[n];
+        for (int j = 0; j < 2; ++j) acc[P0][j] = add2(acc[P0][j], add2(o[j], q[j]));
     }
     if (MODE != LAST) {
         s_ld(up + XSLOT, o, lane);
         s_ld(dn + XSLOT, q, lane);
 #pragma unroll
-        for (int n = 0; n < 4; ++n) acc[PP][n] += o[n] + q[n];
+        for (int j = 0; j < 2; ++j) acc[PP][j] = add2(acc[PP][j], add2(o[j], q[j]));
     }
     if (MODE != FIRST) {
         s_ld(up + 2 * XSLOT, o, lane);
         s_ld(dn + 2 * XSLOT, q, lane);
 #pragma unroll
-        for (int n = 0; n < 4; ++n) acc[PM][n] += o[n] + q[n];
+        for (int j = 0; j < 2; ++j) acc[PM][j] = add2(acc[PM][j], add2(o[j], q[j]));
         if (zfin >= 0) {
             const long long off = ((long long)zfin * p.ny + col * ROWS + row) * p.nx + half * SHALF + lane * 4;
-            *reinterpret_cast<float4 *>(tout + off) = make_float4(acc[PM][0], acc[PM][1], acc[PM][2], acc[PM][3]);
+            *reinterpret_cast<float4 *>(tout + off) =
+                make_float4(acc[PM][0].x, acc[PM][0].y, acc[PM][1].x, acc[PM][1].y);
         }
     }
 }
@@ -365,7 +372,7 @@ __global__ void __launch_bounds__(SG<NH>::NTH, 2 / NH) k_scalar_rows(const float
 #pragma unroll
     for (int a = 0; a < 3; ++a)
 #pragma unroll
-        for (int n = 0; n < 4; ++n) acc[a][n] = 0.f;
+        for (int j = 0; j < 2; ++j) acc[a][j] = b2(0.f);
 
     for (int tc = 0; it.valid(); ++tc) {
         const int s = tc & 1;
@@ -407,9 +414,9 @@ __global__ void __launch_bounds__(SG<NH>::NTH, 2 / NH) k_scalar_rows(const float
         }
         if (mode != LAST) {  // rotate: the plane ahead starts from assignments
 #pragma unroll
-            for (int n = 0; n < 4; ++n) {
-                acc[0][n] = acc[1][n];
-                acc[1][n] = acc[2][n];
+            for (int j = 0; j < 2; ++j) {
+                acc[0][j] = acc[1][j];
+                acc[1][j] = acc[2][j];
             }
         }
         it.next();
