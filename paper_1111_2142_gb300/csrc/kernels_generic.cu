@@ -8,6 +8,7 @@
 #include "launch.h"
 #include "lwacm_core.cuh"
 #include "node_update.cuh"
+#include "tile_common.cuh"
 
 namespace lwacm {
 
@@ -178,12 +179,15 @@ __global__ void __launch_bounds__(256) k_wall_pass(const T *__restrict__ in, T *
 // node_update<19, true> for a node of a cavity (every axis walled, so no source
 // wraps): the wall test of each link reduces to the node's face flags and the
 // source offsets to per-direction constants; same link order and arithmetic.
-template <typename T>
+// I32: every element offset of the four fields fits 32-bit arithmetic (the caller
+// checks 4 fstride < 2^31); the per-direction offsets are then formed once.
+template <typename T, bool I32 = false>
 __device__ __forceinline__ void cavity_node_update(const T *__restrict__ in, T *__restrict__ out,
                                                    const StepParams &p, int x, int y, int z) {
     using L = Lat<19>;
-    const long long plane = (long long)p.nx * p.ny;
-    const long long k = z * plane + (long long)y * p.nx + x;
+    using Idx = typename std::conditional<I32, int, long long>::type;
+    const Idx plane = (Idx)p.nx * p.ny, nxi = (Idx)p.nx;
+    const Idx k = (Idx)z * plane + (Idx)y * p.nx + x;
     const T *Din = in + k, *Uin = in + p.fstride + k, *Vin = in + 2 * p.fstride + k, *Win = in + 3 * p.fstride + k;
     const bool lo0 = x == 0, lo1 = y == 0, lo2 = z == 0;
     const bool hi0 = x == p.nx - 1, hi1 = y == p.ny - 1, hi2 = z == p.nz - 1;
@@ -202,7 +206,7 @@ __device__ __forceinline__ void cavity_node_update(const T *__restrict__ in, T *
         const bool outside = bx || by || bz;
         const bool above = (la == 0 ? cx < 0 && hi0 : (la == 1 ? cy < 0 && hi1 : cz < 0 && hi2));
         // a source beyond a wall reads the node itself (loaded already, unused)
-        const long long so = outside ? 0 : cz * plane + (long long)cy * p.nx + cx;
+        const Idx so = outside ? 0 : (Idx)cz * plane + (Idx)cy * nxi + cx;
         const float ds = ldf(Din - so), us = ldf(Uin - so), vs = ldf(Vin - so), ws = ldf(Win - so);
         float g;
         if (!outside) {
@@ -237,11 +241,12 @@ __device__ __forceinline__ void cavity_node_update(const T *__restrict__ in, T *
         jy = fmaf(rx, __ldg(p.gfield + p.fstride + k), jy);
         jz = fmaf(rx, __ldg(p.gfield + 2 * p.fstride + k), jz);
     }
-    const float rn = 1.f + dd;
+    // u = j / (1 + d+), the IEEE quotient without the checked division's branch
+    const tile::Div1 r = tile::div_prep(1.f + dd);
     stf(out + k, dd);
-    stf(out + p.fstride + k, jx / rn);
-    stf(out + 2 * p.fstride + k, jy / rn);
-    stf(out + 3 * p.fstride + k, jz / rn);
+    stf(out + p.fstride + k, tile::div_apply(jx, r));
+    stf(out + 2 * p.fstride + k, tile::div_apply(jy, r));
+    stf(out + 3 * p.fstride + k, tile::div_apply(jz, r));
 }
 
 // D3Q19 cavity walls in one launch (k_wall_cavity3d) when the x faces have inner
@@ -268,7 +273,10 @@ __device__ __forceinline__ void wall_row_node(const T *__restrict__ in, T *__res
         z = 1 + (q >> 1);
         y = (q & 1) ? p.ny - 1 : 0;
     }
-    cavity_node_update(in, out, p, x, y, z);
+    if (4 * p.fstride < 0x7fffffffLL)
+        cavity_node_update<T, true>(in, out, p, x, y, z);
+    else
+        cavity_node_update<T, false>(in, out, p, x, y, z);
 }
 
 // The inner nodes of the x = 0 and x = nx-1 faces of a D3Q19 cavity (patch (py, pz)

@@ -1,13 +1,13 @@
-// Half-row variant of the TMA row-tiled D3Q19 kernel, for periodic domains with
-// nx = 256 (or 128) and ny a multiple of 8: the moment form of Eq. ACM2.0 (see
-// lwacm_core.cuh), every field read from HBM once and written once per step.
+// Half-row TMA row-tiled D3Q19 kernel, for domains with nx = 256 (or 128) and ny a
+// multiple of 8 (periodic; walled domains get the wall pass after it, the cavity's
+// x faces handled here): the moment form of Eq. ACM2.0 (see lwacm_core.cuh), every
+// field read from HBM once and written once per step.
 //
-// Same structure as kernels_tiled.cu (persistent CTAs over chunk-major
-// (y-column, z-chunk) items, TMA bulk copies of ten staged rows per plane, packed
-// row exchange through shared memory, three rotating accumulator planes), but each
-// 256-node row is shared by two warps (half h covers x = 128 h .. 128 h + 127, four
-// nodes per lane), so a CTA of 8 rows has 16 warps and each thread keeps half the
-// registers: 16 warps per SM instead of 8.
+// Persistent CTAs over chunk-major (y-column, z-chunk) items, TMA bulk copies of
+// ten staged rows per plane, packed row exchange through shared memory, three
+// rotating accumulator planes; each 256-node row is shared by two warps (half h
+// covers x = 128 h .. 128 h + 127, four nodes per lane), so a CTA of 8 rows has 16
+// warps at 125 registers per thread.
 //
 // The two halves of a row meet at x = 127|128 and, periodically, at x = 255|0. A
 // shuffle cannot cross them, so each half's boundary lanes (0 and 31) recompute
@@ -173,7 +173,7 @@ __device__ __forceinline__ void ld_slot2(const float *slot, F2 (&o)[2], int lane
 
 // Row-crossing values of one half row, computed once per link pair and sent to
 // the receivers above (up, c_y = +1; when UP) and below (down, c_y = -1; when DN),
-// four values per receiver x and direction as in kernels_tiled.cu:
+// four values per receiver x and direction:
 //   slot 0: sum of the three c_z = 0 links (d, +-jy), slot 1: their x-momentum,
 //   slot 2: the c_z = +1 link, slot 3: the c_z = -1 link.
 // With NH = 2 the boundary lanes take the x-shifted diagonal that crosses from the
@@ -187,8 +187,8 @@ __device__ __forceinline__ void ld_slot2(const float *slot, F2 (&o)[2], int lane
 // replaced by the node's (-1,-1,0) value, and so on.
 template <int NH, int MODE, bool XW = false>
 __device__ __forceinline__ void send_rows(const NC2 &nc, float *ubase, float *dbase, bool UP, bool DN,
-                                          float nb1, float nb2, int lane, bool e0 = false, bool eN = false,
-                                          F2 (*own)[4] = nullptr) {
+                                          float nb1, float nb2, int lane, bool w0 = false, bool wN = false,
+                                          bool e0 = false, bool eN = false, F2 (*own)[4] = nullptr) {
     constexpr int XSLOT = HG<NH>::XSLOT;
     const bool l0 = lane == 0 && NH == 2, l31 = lane == 31 && NH == 2;
     if (MODE == MID) {
@@ -200,13 +200,13 @@ __device__ __forceinline__ void send_rows(const NC2 &nc, float *ubase, float *db
 #pragma unroll
             for (int j = 0; j < 2; ++j) pair2(nc, j, ye2(nc, 1, j), true, gp[j], gm[j]);
             if (XW && own) {
-                if (e0) {  // (1,1,0) into x = 0 bounces: its (-1,-1,0) value
+                if (w0 && e0) {  // (1,1,0) into x = 0 bounces: its (-1,-1,0) value
                     const float v = gm[0].x;
                     own[0][0].x += v;
                     own[0][1].x += v;
                     own[0][2].x += v;
                 }
-                if (eN) {  // (-1,-1,0) into x = nx-1 bounces: its (1,1,0) value
+                if (wN && eN) {  // (-1,-1,0) into x = nx-1 bounces: its (1,1,0) value
                     const float v = gp[1].y;
                     own[1][0].y += v;
                     own[1][1].y -= v;
@@ -216,12 +216,12 @@ __device__ __forceinline__ void send_rows(const NC2 &nc, float *ubase, float *db
             if (UP) {
                 shift2(gp, 1, lane);
                 gp[0].x = l0 ? nb1 : gp[0].x;
-                if (XW) gp[0].x = e0 ? 0.f : gp[0].x;
+                if (XW && w0) gp[0].x = e0 ? 0.f : gp[0].x;
             }
             if (DN) {
                 shift2(gm, -1, lane);
                 gm[1].y = l31 ? nb1 : gm[1].y;
-                if (XW) gm[1].y = eN ? 0.f : gm[1].y;
+                if (XW && wN) gm[1].y = eN ? 0.f : gm[1].y;
             }
 #pragma unroll
             for (int j = 0; j < 2; ++j) {
@@ -236,13 +236,13 @@ __device__ __forceinline__ void send_rows(const NC2 &nc, float *ubase, float *db
 #pragma unroll
             for (int j = 0; j < 2; ++j) pair2(nc, j, ye2(nc, 2, j), true, gp[j], gm[j]);
             if (XW && own) {
-                if (e0) {  // (1,-1,0) into x = 0 bounces: its (-1,1,0) value
+                if (w0 && e0) {  // (1,-1,0) into x = 0 bounces: its (-1,1,0) value
                     const float v = gp[0].x;
                     own[0][0].x += v;
                     own[0][1].x += v;
                     own[0][2].x -= v;
                 }
-                if (eN) {  // (-1,1,0) into x = nx-1 bounces: its (1,-1,0) value
+                if (wN && eN) {  // (-1,1,0) into x = nx-1 bounces: its (1,-1,0) value
                     const float v = gm[1].y;
                     own[1][0].y += v;
                     own[1][1].y -= v;
@@ -252,12 +252,12 @@ __device__ __forceinline__ void send_rows(const NC2 &nc, float *ubase, float *db
             if (UP) {
                 shift2(gp, -1, lane);
                 gp[1].y = l31 ? nb2 : gp[1].y;
-                if (XW) gp[1].y = eN ? 0.f : gp[1].y;
+                if (XW && wN) gp[1].y = eN ? 0.f : gp[1].y;
             }
             if (DN) {
                 shift2(gm, 1, lane);
                 gm[0].x = l0 ? nb2 : gm[0].x;
-                if (XW) gm[0].x = e0 ? 0.f : gm[0].x;
+                if (XW && w0) gm[0].x = e0 ? 0.f : gm[0].x;
             }
 #pragma unroll
             for (int j = 0; j < 2; ++j) {
@@ -309,7 +309,10 @@ template <int NH, int MODE, bool F, bool XW, typename T>
 __device__ __forceinline__ void phase_a(Acc &acc, const T *stg, float *xbuf, const TiledParams &p, int lane,
                                         int row, int half) {
     constexpr int PM = 0, P0 = 1, PP = 2;
-    const bool e0 = XW && lane == 0 && half == 0, eN = XW && lane == 31 && half == NH - 1;
+    // w0 / wN: the warp holds the x = 0 / x = nx-1 end of its row (warp-uniform, so
+    // the other warps skip the face code); e0 / eN: the lane holding that node
+    const bool w0 = XW && half == 0, wN = XW && half == NH - 1;
+    const bool e0 = w0 && lane == 0, eN = wN && lane == 31;
     constexpr int RL = HG<NH>::RL, XDIR = HG<NH>::XDIR;
     float *up = xbuf + half * HALF, *dn = xbuf + XDIR + half * HALF;
     {
@@ -361,13 +364,13 @@ __device__ __forceinline__ void phase_a(Acc &acc, const T *stg, float *xbuf, con
                                                cz == 0 ? nb.U : (cz > 0 ? nb.U + nb.W : nb.U - nb.W))
                                       : 0.f;
             if (XW && MODE == MID) {  // links crossing an x face bounce (see send_rows)
-                if (e0) {  // (1,0,cz) into x = 0: its own (-1,0,-cz) value
+                if (w0 && e0) {  // (1,0,cz) into x = 0: its own (-1,0,-cz) value
                     const float v = gm[0].x;
                     acc[P0][0][0].x += v;
                     acc[P0][0][1].x += v;
                     if (cz) acc[P0][0][3].x += cz * v;
                 }
-                if (eN) {  // (-1,0,-cz) into x = nx-1: its own (1,0,cz) value
+                if (wN && eN) {  // (-1,0,-cz) into x = nx-1: its own (1,0,cz) value
                     const float v = gp[1].y;
                     acc[P0][1][0].y += v;
                     acc[P0][1][1].y -= v;
@@ -378,7 +381,7 @@ __device__ __forceinline__ void phase_a(Acc &acc, const T *stg, float *xbuf, con
                 const float eP = gp[1].y;
                 float rP = __shfl_sync(FULL, eP, (lane + 31) & 31);
                 if (NH == 2) rP = lane == 0 ? nbv : rP;
-                if (XW) rP = e0 ? 0.f : rP;
+                if (XW && w0) rP = e0 ? 0.f : rP;
                 const F2 R[2] = {make_float2(rP, gp[0].x), make_float2(gp[0].y, gp[1].x)};
                 F2(&a)[2][4] = acc[pl<PM, P0, PP>(cz)];
 #pragma unroll
@@ -392,7 +395,7 @@ __device__ __forceinline__ void phase_a(Acc &acc, const T *stg, float *xbuf, con
                 const float eM = gm[0].x;
                 float rM = __shfl_sync(FULL, eM, (lane + 1) & 31);
                 if (NH == 2) rM = lane == 31 ? nbv : rM;
-                if (XW) rM = eN ? 0.f : rM;
+                if (XW && wN) rM = eN ? 0.f : rM;
                 const F2 L[2] = {make_float2(gm[0].y, gm[1].x), make_float2(gm[1].y, rM)};
                 if (cz < 0) {  // -c = (-1,0,1): first x-momentum of the plane ahead
 #pragma unroll
@@ -414,7 +417,7 @@ __device__ __forceinline__ void phase_a(Acc &acc, const T *stg, float *xbuf, con
         const float nb1 = NH == 2 && MODE == MID ? nb_val(nb.K2, nb.sA2, nb.B2, nb.U + nb.V) : 0.f;
         const float nb2 = NH == 2 && MODE == MID ? nb_val(nb.K2, -nb.sA2, nb.B2, nb.V - nb.U) : 0.f;
         send_rows<NH, MODE, XW>(nc, up + (row + 1) * RL, dn + (row - 1) * RL, row + 1 < ROWS, row > 0, nb1, nb2, lane,
-                                e0, eN, MODE == MID ? acc[P0] : nullptr);
+                                w0, wN, e0, eN, MODE == MID ? acc[P0] : nullptr);
     }
     if (row == 0 || row == ROWS - 1) {  // halo rows: y0-1 (staged row 0) feeds row 0, y0+8 (staged 9) row 7
         const int sr = row == 0 ? 0 : TROWS - 1;
@@ -428,9 +431,9 @@ __device__ __forceinline__ void phase_a(Acc &acc, const T *stg, float *xbuf, con
             nb2 = nb_val(hb.K2, -hb.sA2, hb.B2, hb.V - hb.U);
         }
         if (row == 0)
-            send_rows<NH, MODE, XW>(hc, up, nullptr, true, false, nb1, nb2, lane, e0, eN);
+            send_rows<NH, MODE, XW>(hc, up, nullptr, true, false, nb1, nb2, lane, w0, wN, e0, eN);
         else
-            send_rows<NH, MODE, XW>(hc, nullptr, dn + (ROWS - 1) * RL, false, true, nb1, nb2, lane, e0, eN);
+            send_rows<NH, MODE, XW>(hc, nullptr, dn + (ROWS - 1) * RL, false, true, nb1, nb2, lane, w0, wN, e0, eN);
     }
 }
 
