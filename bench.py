@@ -14,7 +14,10 @@ One bench "step" is one LW-ACM time step over the whole 256^3 lattice
   roofline   the dominant kernel (the interior update) against the measured HBM
              copy bandwidth: 32 algorithmic bytes per node (4 FP32 fields read
              once, written once);
-  cpu_baseline  the FP64 oracle timed on the host cores on a bounded sample.
+  cpu_baseline  the FP64 oracle timed on the host cores on a bounded sample (1000
+             steps of the workload's vortex on 128^3);
+  accuracy   the same 1000 steps through the benchmarked kernel against the
+             oracle: per-field errors and the kinetic-energy curve.
 
 --impl reference times the FP64 oracle (the plain CPU restatement of the
 method) on the same workload, metric and unit.
@@ -120,19 +123,61 @@ class ClockSampler:
                 "reasons": reasons, "samples": len(rows)}
 
 
-def cpu_baseline(steps=40, n=N_SIDE):
-    """The FP64 oracle as it stands on the host cores: `steps` updates of the same
-    256^3 workload (a bounded sample of the GPU run's steps)."""
+ACC_SIDE, ACC_EVERY = 128, 10  # the accuracy sample: the workload's parameters on 128^3
+
+
+def cpu_baseline(steps=1000, n=ACC_SIDE, every=ACC_EVERY):
+    """The FP64 oracle as it stands on the host cores, timed on a bounded sample:
+    `steps` updates of the Taylor-Green workload (same u0, nu) on n^3, in runs of
+    `every` steps (only the updates are timed). The same run on the GPU, through
+    the benchmarked kernel from the same FP32-rounded fields, is compared with it:
+    the per-field errors after `steps` steps and the kinetic energy every `every`
+    steps (the metric's stated error), and the same for FP16 storage rounded
+    stochastically. Returns (cpu_baseline, accuracy)."""
+    import numpy as np
     import oracle
     from paper_1111_2142_gb300 import inputs
-    f = inputs.tgv3d(n, u0=U0)
-    oracle.step(19, *[a[:8] for a in f], nu=NU, nsteps=1)  # load/build outside the timing
-    t0 = time.perf_counter()
-    oracle.step(19, *f, nu=NU, nsteps=steps)
-    dt = time.perf_counter() - t0
-    return {"value": steps * n ** 3 / dt / 1e9, "unit": "GLUPS", "cores": oracle.max_threads(),
-            "kind": "oracle", "sample": f"{steps} FP64 oracle steps of the {n}^3 workload "
-            f"({dt:.1f} s)"}
+    from paper_1111_2142_gb300 import lwacm as lw
+    f32 = [a.astype(np.float32).astype(np.float64) for a in inputs.tgv3d(n, u0=U0)]
+
+    def gpu(**kw):
+        sim = lw.Lwacm(lw.D3Q19, n, n, n, NU, **kw)
+        sim.set_fields(*f32)
+        ke = [sim.diagnostics()["ke"]]
+        for _ in range(steps // every):
+            sim.step(every)
+            ke.append(sim.diagnostics()["ke"])
+        out = [a.reshape(n, n, n) for a in sim.get_fields()]
+        name = sim.kernel_name
+        sim.close()
+        return out, np.array(ke), name
+
+    got, ke_gpu, kname = gpu()
+    got16, ke16, _ = gpu(storage=lw.F16, stochastic_rounding=True)
+    oracle.step(19, *[a[:8] for a in f32], nu=NU, nsteps=1)  # load/build outside the timing
+    state = tuple(f32)
+    ke_ref = [oracle.diagnostics(*state)["ke"]]
+    dt = 0.0
+    for _ in range(steps // every):
+        t0 = time.perf_counter()
+        state = oracle.step(19, *state, nu=NU, nsteps=every)
+        dt += time.perf_counter() - t0
+        ke_ref.append(oracle.diagnostics(*state)["ke"])
+    ke_ref = np.array(ke_ref)
+    done = (steps // every) * every
+    base = {"value": done * n ** 3 / dt / 1e9, "unit": "GLUPS", "cores": oracle.max_threads(),
+            "kind": "oracle", "sample": f"{done} FP64 oracle steps of the workload's Taylor-Green vortex "
+            f"on {n}^3 ({dt:.1f} s)"}
+
+    def errs(g, ke):
+        dscale = max(float(np.max(np.abs(state[0]))), 3 * U0 ** 2)
+        return {"max_abs_du_over_u0": max(float(np.max(np.abs(a - b))) for a, b in zip(g[1:], state[1:])) / U0,
+                "max_abs_dd_over_dscale": float(np.max(np.abs(g[0] - state[0]))) / dscale,
+                "ke_curve_max_rel": float(np.max(np.abs(ke - ke_ref) / ke_ref))}
+    acc = {"workload": f"D3Q19 3D Taylor-Green {n}^3, u0={U0}, nu={NU}, {done} steps, KE every {every}",
+           "kernel": kname, "fp32": errs(got, ke_gpu), "fp16_stochastic_rounding": errs(got16, ke16),
+           "ke_ratio_oracle": float(ke_ref[-1] / ke_ref[0]), "reference": "FP64 oracle"}
+    return base, acc
 
 
 REF_SIDE = 128  # the reference arm's bounded sample: the same workload on 128^3
@@ -218,6 +263,8 @@ def variants(hbm):
     f = inputs.tgv3d(n, u0=U0)
     for name, kw, bpn in (("d3q19_256_bf16_storage", dict(storage=lw.BF16), 16),
                           ("d3q19_256_fp16_storage", dict(storage=lw.F16), 16),
+                          ("d3q19_256_fp16_stochastic_rounding", dict(storage=lw.F16, stochastic_rounding=True), 16),
+                          ("d3q19_256_bf16_stochastic_rounding", dict(storage=lw.BF16, stochastic_rounding=True), 16),
                           ("d3q19_256_generic_kernel", dict(kernel=1), 32)):
         sim = lw.Lwacm(lw.D3Q19, n, n, n, NU, **kw)
         sim.set_fields(*f)
@@ -544,7 +591,7 @@ def run_gpu(args):
         line["variants"] = variants(hbm)
     if rank == 0 and not args.no_cpu_baseline and ws == 1:
         try:
-            line["cpu_baseline"] = cpu_baseline(args.cpu_steps)
+            line["cpu_baseline"], line["accuracy"] = cpu_baseline(args.cpu_steps)
         except Exception as exc:  # the oracle is a reported baseline, not a requirement
             line["cpu_baseline"] = {"value": None, "error": str(exc)[:200]}
     if rank == 0:
@@ -611,7 +658,7 @@ def main():
     ap.add_argument("--graph-chunk", type=int, default=64)
     ap.add_argument("--kernel", type=int, default=0)
     ap.add_argument("--e2e-steps", type=int, default=20)
-    ap.add_argument("--cpu-steps", type=int, default=40)
+    ap.add_argument("--cpu-steps", type=int, default=1000)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-variants", action="store_true")
     ap.add_argument("--profile-case", choices=["adjoint", "ensemble", "cavity", "cavity3d", "bulk2d", "scalar"],

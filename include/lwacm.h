@@ -154,7 +154,7 @@ enum {
                                      (LWACM_E_UNSUPPORTED). With LWACM_OPT_NU_P the density
                                      is relaxed with omega_p and the momentum and the
                                      trace with omega. Runs on the D2Q9 2D-tile kernel. */
-    LWACM_OPT_SEMI_IMPLICIT = 17  /* 1: semi-implicit pressure update (Section 2.2 item 2,
+    LWACM_OPT_SEMI_IMPLICIT = 17, /* 1: semi-implicit pressure update (Section 2.2 item 2,
                                      Eq. FDcompact_si), 0 = explicit (default). The
                                      velocity is that of the explicit step; the density
                                      is then summed again with every link value built
@@ -165,6 +165,22 @@ enum {
                                      nu_p); not with the passive scalar, the
                                      bulk-viscosity variant or the adjoint
                                      (LWACM_E_UNSUPPORTED). */
+    LWACM_OPT_STOCHASTIC_ROUNDING = 18 /* 1: BF16 / FP16 stores rounded stochastically,
+                                     0 = to nearest (default). A value between two
+                                     neighbours of the storage type is stored as the one
+                                     further from zero with probability equal to its
+                                     distance from the nearer-to-zero one over their
+                                     spacing (16 random bits per value from a counter-
+                                     based hash of the node, the field and a step counter
+                                     kept in the workspace), so that stored values are
+                                     unbiased and a per-step change below half a storage
+                                     ulp is not lost. Single periodic D3Q19 domains with
+                                     BF16 / FP16 storage on the half-row kernel (nx 128 or
+                                     256, ny % 8 == 0), plain scheme only (no forcing,
+                                     nu_p, scalar, bulk variant or semi-implicit update);
+                                     otherwise LWACM_E_UNSUPPORTED, at set_option, bind
+                                     or step. Runs are reproducible: the counter starts at
+                                     0 at lwacm_bind. */
 };
 
 /* Create a single-domain context.

@@ -28,6 +28,15 @@ extern "C" {
 int lwacm_selftest_quotient(const float *a_dev, const float *b_dev, float *out_dev, long long n, int packed,
                             void *stream);
 
+/* out_dev[k] = x_dev[k] rounded stochastically to the storage type (LWACM_BF16 or
+ * LWACM_F16) exactly as the half-row kernel stores the density of node k in the step
+ * whose counter is `step` (LWACM_OPT_STOCHASTIC_ROUNDING), widened back to FP32
+ * (exact): one of the two storage values around x, the one further from zero with
+ * probability |x - lo| / |hi - lo|. x_dev, out_dev: caller-owned device arrays of n
+ * FP32 values, n in [1, 2^31). Stream-ordered on `stream`, not synchronised.
+ * Errors: LWACM_E_ARG (null pointer, n out of range, other storage), LWACM_E_CUDA. */
+int lwacm_selftest_round(const float *x_dev, float *out_dev, long long n, int storage, unsigned step, void *stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -249,6 +249,75 @@ __device__ __forceinline__ void cavity_node_update(const T *__restrict__ in, T *
     stf(out + 3 * p.fstride + k, tile::div_apply(jz, r));
 }
 
+// The same update for a node of a boundary row whose y and z faces are known at
+// compile time (YF, ZF: 0 none, 1 the low face, 2 the high face; 32-bit offsets):
+// a link that leaves through one of them bounces with neither a load nor a test,
+// and only the x-face links (the row's two end nodes) keep a test. Same link order
+// and arithmetic as cavity_node_update, so the same results.
+template <typename T, int YF, int ZF>
+__device__ __forceinline__ void cavity_row_update(const T *__restrict__ in, T *__restrict__ out,
+                                                  const StepParams &p, int x, int y, int z) {
+    using L = Lat<19>;
+    const int plane = p.nx * p.ny;
+    const int k = z * plane + y * p.nx + x;
+    const T *Din = in + k, *Uin = in + p.fstride + k, *Vin = in + 2 * p.fstride + k, *Win = in + 3 * p.fstride + k;
+    const bool lo0 = x == 0, hi0 = x == p.nx - 1;
+    const int la = p.lid_axis;
+    const float dx = ldf(Din), ux = ldf(Uin), uy = ldf(Vin), uz = ldf(Win);
+    const float rx = 1.f + dx;
+    const float qx = fmaf(ux, ux, fmaf(uy, uy, uz * uz));
+    float dd = 0.f, jx = 0.f, jy = 0.f, jz = 0.f;
+#pragma unroll
+    for (int i = 0; i < 19; ++i) {
+        const int cx = L::c(i, 0), cy = L::c(i, 1), cz = L::c(i, 2);
+        const bool byz = (cy > 0 && YF == 1) || (cy < 0 && YF == 2) || (cz > 0 && ZF == 1) || (cz < 0 && ZF == 2);
+        const bool bx = (cx > 0 && lo0) || (cx < 0 && hi0);
+        const bool above = la == 0 ? (cx < 0 && hi0) : (la == 1 ? (cy < 0 && YF == 2) : (cz < 0 && ZF == 2));
+        float g;
+        bool own = byz;
+        if (!byz) {
+            const int so = bx ? 0 : cz * plane + cy * p.nx + cx;
+            const float ds = ldf(Din - so), us = ldf(Uin - so), vs = ldf(Vin - so), ws = ldf(Win - so);
+            const float e = cx * us + cy * vs + cz * ws;
+            const float q = fmaf(us, us, fmaf(vs, vs, ws * ws));
+            g = link_g(L::w(i), ds, 1.f + ds, e, q, p.s);
+            own = bx;
+        }
+        if (own) {
+            // Eq. ACM2.0cccbb2 + Eq. ACM2.0ccccbb: own outgoing BB(i) value, reflected
+            const float e = -(cx * ux + cy * uy + cz * uz);
+            g = link_g(L::w(i), dx, rx, e, qx, p.s);
+            if (above) {
+                const float cu = cx * p.lid[0] + cy * p.lid[1] + cz * p.lid[2];
+                g = fmaf(L::w(i) * p.wallc, cu, g);
+            }
+        }
+        dd += g;
+        if (cx) jx += cx > 0 ? g : -g;
+        if (cy) jy += cy > 0 ? g : -g;
+        if (cz) jz += cz > 0 ? g : -g;
+    }
+    const float mx = post_factor(p.a, dx, p.am1);  // a rho u = u + mx u (post_combine)
+    jx = post_combine(jx, mx, ux);
+    jy = post_combine(jy, mx, uy);
+    jz = post_combine(jz, mx, uz);
+    if (p.has_force) {  // Eq. force
+        jx = fmaf(rx, p.force[0], jx);
+        jy = fmaf(rx, p.force[1], jy);
+        jz = fmaf(rx, p.force[2], jz);
+    }
+    if (p.gfield) {
+        jx = fmaf(rx, __ldg(p.gfield + k), jx);
+        jy = fmaf(rx, __ldg(p.gfield + p.fstride + k), jy);
+        jz = fmaf(rx, __ldg(p.gfield + 2 * p.fstride + k), jz);
+    }
+    const tile::Div1 r = tile::div_prep(1.f + dd);
+    stf(out + k, dd);
+    stf(out + p.fstride + k, tile::div_apply(jx, r));
+    stf(out + 2 * p.fstride + k, tile::div_apply(jy, r));
+    stf(out + 3 * p.fstride + k, tile::div_apply(jz, r));
+}
+
 // D3Q19 cavity walls in one launch (k_wall_cavity3d) when the x faces have inner
 // nodes (y in [1, ny-2], z in [1, nz-2]) with an inner column beside each (nx >= 2):
 // blocks of shared-memory staged x-face patches, then blocks of boundary rows.
@@ -273,10 +342,22 @@ __device__ __forceinline__ void wall_row_node(const T *__restrict__ in, T *__res
         z = 1 + (q >> 1);
         y = (q & 1) ? p.ny - 1 : 0;
     }
-    if (4 * p.fstride < 0x7fffffffLL)
-        cavity_node_update<T, true>(in, out, p, x, y, z);
-    else
+    if (4 * p.fstride >= 0x7fffffffLL) {
         cavity_node_update<T, false>(in, out, p, x, y, z);
+        return;
+    }
+    const int yf = y == 0 ? 1 : (y == p.ny - 1 ? 2 : 0), zf = z == 0 ? 1 : (z == p.nz - 1 ? 2 : 0);
+    switch (yf * 3 + zf) {  // uniform per block: one row
+        case 1: cavity_row_update<T, 0, 1>(in, out, p, x, y, z); break;
+        case 2: cavity_row_update<T, 0, 2>(in, out, p, x, y, z); break;
+        case 3: cavity_row_update<T, 1, 0>(in, out, p, x, y, z); break;
+        case 4: cavity_row_update<T, 1, 1>(in, out, p, x, y, z); break;
+        case 5: cavity_row_update<T, 1, 2>(in, out, p, x, y, z); break;
+        case 6: cavity_row_update<T, 2, 0>(in, out, p, x, y, z); break;
+        case 7: cavity_row_update<T, 2, 1>(in, out, p, x, y, z); break;
+        case 8: cavity_row_update<T, 2, 2>(in, out, p, x, y, z); break;
+        default: cavity_node_update<T, true>(in, out, p, x, y, z); break;
+    }
 }
 
 // The inner nodes of the x = 0 and x = nx-1 faces of a D3Q19 cavity (patch (py, pz)

@@ -437,9 +437,10 @@ __device__ __forceinline__ void phase_a(Acc &acc, const T *stg, float *xbuf, con
     }
 }
 
-template <int NH, int MODE, typename T>
+// SRND: BF16 / FP16 stores rounded stochastically (tile_common.cuh) with the step's key
+template <int NH, int MODE, bool SRND, typename T>
 __device__ __forceinline__ void phase_b(Acc &acc, const float *xbuf, T *out, const TiledParams &p, int lane,
-                                        int row, int half, int col, int zfin) {
+                                        int row, int half, int col, int zfin, uint32_t key) {
     constexpr int PM = 0, P0 = 1, PP = 2;
     constexpr int RL = HG<NH>::RL, XDIR = HG<NH>::XDIR, XSLOT = HG<NH>::XSLOT;
     const float *up = xbuf + row * RL + half * HALF, *dn = xbuf + XDIR + row * RL + half * HALF;
@@ -499,11 +500,31 @@ __device__ __forceinline__ void phase_b(Acc &acc, const float *xbuf, T *out, con
             T *op = out + rowoff;
             // u = j / rho, correctly rounded (tile_common.cuh, div_apply2)
             const Div2 r[2] = {div_prep2(add2(b2(1.f), acc[PM][0][0])), div_prep2(add2(b2(1.f), acc[PM][1][0]))};
-            st4(op, acc[PM][0][0].x, acc[PM][0][0].y, acc[PM][1][0].x, acc[PM][1][0].y);
+            if constexpr (SRND && sizeof(T) == 2) {
+                // random words of the lane's four nodes: h[0] for d (low) and u (high), h[1] for v and w
+                const uint32_t k0 = (uint32_t)rowoff;
+                uint32_t h[2][4];
 #pragma unroll
-            for (int c = 1; c < 4; ++c) {
-                const F2 v0 = div_apply2(acc[PM][0][c], r[0]), v1 = div_apply2(acc[PM][1][c], r[1]);
-                st4(op + c * p.fstride, v0.x, v0.y, v1.x, v1.y);
+                for (int i = 0; i < 4; ++i) {
+                    h[0][i] = sr_bits(k0 + i, 0u, key);
+                    h[1][i] = sr_bits(k0 + i, 1u, key);
+                }
+                st4_sr(op, acc[PM][0][0].x, acc[PM][0][0].y, acc[PM][1][0].x, acc[PM][1][0].y, h[0][0], h[0][1],
+                       h[0][2], h[0][3]);
+#pragma unroll
+                for (int c = 1; c < 4; ++c) {
+                    const F2 v0 = div_apply2(acc[PM][0][c], r[0]), v1 = div_apply2(acc[PM][1][c], r[1]);
+                    const int q = c >> 1, sh = (c & 1) * 16;
+                    st4_sr(op + c * p.fstride, v0.x, v0.y, v1.x, v1.y, h[q][0] >> sh, h[q][1] >> sh, h[q][2] >> sh,
+                           h[q][3] >> sh);
+                }
+            } else {
+                st4(op, acc[PM][0][0].x, acc[PM][0][0].y, acc[PM][1][0].x, acc[PM][1][0].y);
+#pragma unroll
+                for (int c = 1; c < 4; ++c) {
+                    const F2 v0 = div_apply2(acc[PM][0][c], r[0]), v1 = div_apply2(acc[PM][1][c], r[1]);
+                    st4(op + c * p.fstride, v0.x, v0.y, v1.x, v1.y);
+                }
             }
         }
     }
@@ -548,11 +569,12 @@ __device__ __forceinline__ void rotate(Acc &acc) {
 }
 
 // V: the variant, 0 = the plain scheme, 1 = with a constant acceleration (Eq. force),
-// 2 = with the x faces walled (the cavity's x = 0 and x = nx-1 faces, lid elsewhere)
+// 2 = with the x faces walled (the cavity's x = 0 and x = nx-1 faces, lid elsewhere),
+// 3 = the plain scheme with BF16 / FP16 stores rounded stochastically
 template <int NH, typename T, int V>
 __global__ void __launch_bounds__(HG<NH>::NTH, 2 / NH) k_d3q19_half(const T *__restrict__ in,
                                                                    T *__restrict__ out, TiledParams p) {
-    constexpr bool F = V == 1, XW = V == 2;
+    constexpr bool F = V == 1, XW = V == 2, SRND = V == 3;
     constexpr int XBUF = HG<NH, T>::XBUF, STAGE = HG<NH, T>::STAGE;
     extern __shared__ float4 smem4[];
     float *xs = reinterpret_cast<float *>(smem4);
@@ -582,6 +604,8 @@ __global__ void __launch_bounds__(HG<NH>::NTH, 2 / NH) k_d3q19_half(const T *__r
         pf.next();
     }
 
+    // the step's random key (the counter advances after the launch, k_sr_tick)
+    const uint32_t key = SRND ? sr_key(*p.sr_ctr) : 0u;
     Acc acc;
 #pragma unroll
     for (int a = 0; a < 3; ++a)
@@ -623,13 +647,13 @@ __global__ void __launch_bounds__(HG<NH>::NTH, 2 / NH) k_d3q19_half(const T *__r
             pf.next();
         }
         if (mode == MID) {
-            phase_b<NH, MID>(acc, xbuf, out, p, lane, row, half, it.col, it.pz > it.za ? it.pz - 1 : -1);
+            phase_b<NH, MID, SRND>(acc, xbuf, out, p, lane, row, half, it.col, it.pz > it.za ? it.pz - 1 : -1, key);
             rotate(acc);
         } else if (mode == FIRST) {
-            phase_b<NH, FIRST>(acc, xbuf, out, p, lane, row, half, it.col, -1);
+            phase_b<NH, FIRST, SRND>(acc, xbuf, out, p, lane, row, half, it.col, -1, key);
             rotate(acc);
         } else {
-            phase_b<NH, LAST>(acc, xbuf, out, p, lane, row, half, it.col, it.zb - 1);
+            phase_b<NH, LAST, SRND>(acc, xbuf, out, p, lane, row, half, it.col, it.zb - 1, key);
         }
         it.next();
     }
@@ -675,7 +699,9 @@ int half_chunk_planes(int ycols, int nz, int ctas) {
 template <int NH, int V>
 static cudaError_t prepare_storage(int storage) {
     switch (storage) {
-        case STORE_F32: return prepare<NH, float, V>(nullptr);
+        case STORE_F32:
+            if constexpr (V == 3) return cudaErrorNotSupported;  // FP32 stores round to nearest
+            else return prepare<NH, float, V>(nullptr);
         case STORE_BF16: return prepare<NH, __nv_bfloat16, V>(nullptr);
         case STORE_F16: return prepare<NH, __half, V>(nullptr);
     }
@@ -686,6 +712,8 @@ bool half_xwalls(const StepParams &p) { return p.walled[0] && p.lid_axis != 0; }
 
 // the kernel variant a step needs (-1: none serves it)
 static int half_variant(const StepParams &p) {
+    if (p.sr_ctr)  // stochastic rounding: the plain periodic scheme only
+        return (p.walled[0] || p.walled[1] || p.walled[2] || p.has_force) ? -1 : 3;
     const bool xw = half_xwalls(p);
     if (p.has_force && xw) return -1;
     return xw ? 2 : (p.has_force ? 1 : 0);
@@ -706,9 +734,15 @@ bool half_supported(int Q, int storage, const StepParams &p) {
     if (v < 0) return false;
     cudaError_t e;
     if (p.nx == 256)
-        e = v == 0 ? prepare_storage<2, 0>(storage) : (v == 1 ? prepare_storage<2, 1>(storage) : prepare_storage<2, 2>(storage));
+        e = v == 0   ? prepare_storage<2, 0>(storage)
+            : v == 1 ? prepare_storage<2, 1>(storage)
+            : v == 2 ? prepare_storage<2, 2>(storage)
+                     : prepare_storage<2, 3>(storage);
     else
-        e = v == 0 ? prepare_storage<1, 0>(storage) : (v == 1 ? prepare_storage<1, 1>(storage) : prepare_storage<1, 2>(storage));
+        e = v == 0   ? prepare_storage<1, 0>(storage)
+            : v == 1 ? prepare_storage<1, 1>(storage)
+            : v == 2 ? prepare_storage<1, 2>(storage)
+                     : prepare_storage<1, 3>(storage);
     return e == cudaSuccess;
 }
 
@@ -731,6 +765,7 @@ static cudaError_t launch_nh(const void *in, void *out, const StepParams &sp, cu
     p.am1 = sp.am1;
     p.err = sp.err;
     for (int c = 0; c < 3; ++c) p.g[c] = V == 1 ? sp.force[c] : 0.f;
+    p.sr_ctr = V == 3 ? sp.sr_ctr : nullptr;
     const int grid = ctas < p.nitems ? ctas : p.nitems;
     k_d3q19_half<NH, T, V><<<(unsigned)grid, HG<NH, T>::NTH, HG<NH, T>::BYTES, st>>>((const T *)in, (T *)out, p);
     return cudaGetLastError();
@@ -740,7 +775,9 @@ template <int V>
 static cudaError_t launch_variant(int storage, const void *in, void *out, const StepParams &sp, cudaStream_t st) {
     const bool w = sp.nx == 256;
     switch (storage) {
-        case STORE_F32: return w ? launch_nh<2, float, V>(in, out, sp, st) : launch_nh<1, float, V>(in, out, sp, st);
+        case STORE_F32:
+            if constexpr (V == 3) return cudaErrorNotSupported;
+            else return w ? launch_nh<2, float, V>(in, out, sp, st) : launch_nh<1, float, V>(in, out, sp, st);
         case STORE_BF16:
             return w ? launch_nh<2, __nv_bfloat16, V>(in, out, sp, st) : launch_nh<1, __nv_bfloat16, V>(in, out, sp, st);
         case STORE_F16: return w ? launch_nh<2, __half, V>(in, out, sp, st) : launch_nh<1, __half, V>(in, out, sp, st);
@@ -752,8 +789,19 @@ cudaError_t launch_step_half(int Q, int storage, const void *in, void *out, cons
                              cudaStream_t st) {
     if (!half_supported(Q, storage, sp)) return cudaErrorNotSupported;
     const int v = half_variant(sp);
-    return v == 0 ? launch_variant<0>(storage, in, out, sp, st)
-                  : (v == 1 ? launch_variant<1>(storage, in, out, sp, st) : launch_variant<2>(storage, in, out, sp, st));
+    return v == 0   ? launch_variant<0>(storage, in, out, sp, st)
+           : v == 1 ? launch_variant<1>(storage, in, out, sp, st)
+           : v == 2 ? launch_variant<2>(storage, in, out, sp, st)
+                    : launch_variant<3>(storage, in, out, sp, st);
+}
+
+// advance the stochastic-rounding step counter (after each step's stores)
+static __global__ void k_sr_tick(unsigned *ctr) {
+    if (threadIdx.x == 0) *ctr += 1u;
+}
+cudaError_t launch_sr_tick(unsigned *ctr, cudaStream_t st) {
+    k_sr_tick<<<1, 32, 0, st>>>(ctr);
+    return cudaGetLastError();
 }
 
 }  // namespace lwacm

@@ -102,6 +102,8 @@ cudaError_t launch_scalar_rows(const void *in, void *out, const StepParams &p, c
 // whether the half-row kernel applies the x-face walls itself (the wall pass then
 // leaves the inner x-face nodes alone)
 bool half_xwalls(const StepParams &p);
+// stochastic rounding: advance the step counter the next step's random key is drawn from
+cudaError_t launch_sr_tick(unsigned *ctr, cudaStream_t st);
 cudaError_t launch_step_half(int Q, int storage, const void *in, void *out, const StepParams &p,
                              cudaStream_t st);
 

@@ -40,6 +40,7 @@ struct lwacm_ctx {
     double gamma = 0;         // D2Q9 bulk-viscosity variant (Appendix "Computing derivatives locally")
     bool bulk = false;        // the variant is on: Tr+ - Tr^(e) is the field after the flow fields
     bool semi = false;        // semi-implicit pressure update (Eq. FDcompact_si)
+    bool sr = false;          // BF16 / FP16 stores rounded stochastically (half-row kernel)
     bool scalar_rows = false; // the passive scalar on its own row-tiled kernel after the flow kernel
     int nsc = 0;              // fields stored after the flow fields: the scalar or the trace (0 or 1)
     long long N = 0, Nal = 0;
@@ -164,6 +165,8 @@ StepParams params(const lwacm_ctx *c) {
     p.bulk = c->bulk ? 1 : 0;
     p.gamma = (float)c->gamma;
     p.err = c->ws ? (int *)(c->ws + c->off_err) : nullptr;
+    // the stochastic-rounding step counter: the word after the error word
+    p.sr_ctr = c->sr && c->ws ? (unsigned *)(c->ws + c->off_err) + 1 : nullptr;
     p.walled[0] = p.walled[1] = p.walled[2] = 0;
     p.lid_axis = c->D - 1;
     if (c->bc == LWACM_BC_CAVITY) {
@@ -210,7 +213,10 @@ bool choose_kernel(lwacm_ctx *c) {
     const bool h_ok = dev && half_supported(c->Q, c->storage, pf);
     const bool s_ok = tiles2d_supported(c->Q, c->storage, p);
     bool ok = true;
-    switch (c->kernel_opt) {
+    if (c->sr) {  // only the half-row kernel rounds stochastically: no fallback
+        c->kernel = h_ok ? 5 : 1;
+        ok = (c->kernel_opt == 0 || c->kernel_opt == 5) && (h_ok || !dev);
+    } else switch (c->kernel_opt) {
         case 1: c->kernel = 1; break;
         case 5: c->kernel = h_ok ? 5 : 1; ok = h_ok || !dev; break;
         case 6: c->kernel = s_ok ? 6 : 1; ok = s_ok; break;
@@ -289,6 +295,7 @@ cudaError_t step_between(lwacm_ctx *c, const void *in, void *out, cudaStream_t s
         pw.xfaces_done = c->kernel == 5 && half_xwalls(p) ? 1 : 0;
         e = launch_wall_pass(c->Q, c->storage, in, out, pw, st);
     }
+    if (e == cudaSuccess && p.sr_ctr && c->kernel == 5) e = launch_sr_tick(p.sr_ctr, st);
     if (e == cudaSuccess && c->semi) e = launch_semi_implicit(c->Q, c->storage, in, out, p, st);
     if (e == cudaSuccess && c->scalar_rows) e = launch_scalar_rows(in, out, p, st);
     return e;
@@ -587,6 +594,7 @@ lwacm_status lwacm_set_option(lwacm_ctx *c, int key, double v) {
             if (s != LWACM_F32 && s != LWACM_BF16 && s != LWACM_F16)
                 return fail(c, LWACM_E_ARG, "storage must be F32, BF16 or F16");
             if (c->bound) return fail(c, LWACM_E_STATE, "storage type is fixed once bound");
+            if (s == LWACM_F32 && c->sr) return fail(c, LWACM_E_UNSUPPORTED, "stochastic rounding needs BF16 or FP16 storage");
             c->storage = s;
             layout(c);
             break;
@@ -644,6 +652,18 @@ lwacm_status lwacm_set_option(lwacm_ctx *c, int key, double v) {
             c->bulk = v != 0;
             c->nsc = c->bulk ? 1 : 0;
             layout(c);
+            break;
+        }
+        case LWACM_OPT_STOCHASTIC_ROUNDING: {
+            if (v != 0 && v != 1) return fail(c, LWACM_E_ARG, "stochastic rounding must be 0 or 1");
+            if (v != 0 && (c->nbatch || c->Q != 19 || c->bc != LWACM_BC_PERIODIC))
+                return fail(c, LWACM_E_UNSUPPORTED, "stochastic rounding is for single periodic D3Q19 domains");
+            if (v != 0 && c->storage == LWACM_F32)
+                return fail(c, LWACM_E_UNSUPPORTED, "stochastic rounding needs BF16 or FP16 storage");
+            if (v != 0 && (c->semi || c->alpha != 0 || c->bulk || c->nu_p > 0 || c->ff_reserved))
+                return fail(c, LWACM_E_UNSUPPORTED, "stochastic rounding is for the plain scheme");
+            c->sr = v != 0;
+            drop_graphs(c);
             break;
         }
         case LWACM_OPT_SEMI_IMPLICIT: {
@@ -822,6 +842,8 @@ lwacm_status lwacm_step(lwacm_ctx *c, long long n) {
     lwacm_status s = ready(c, true);
     if (s != LWACM_OK) return s;
     if (n < 0) return fail(c, LWACM_E_ARG, "negative step count");
+    if (c->sr && c->kernel != 5)  // an option set later may have ruled the half-row kernel out
+        return fail(c, LWACM_E_UNSUPPORTED, "stochastic rounding needs the half-row kernel (the plain periodic scheme)");
     if (c->nbatch && c->batch_mode == 1) {
         if (n == 0) return LWACM_OK;
         CK(c, launch_batch_persistent(c->Q, c->storage, bufp(c, 0), bufp(c, 1), batch_params(c), n, c->cur,

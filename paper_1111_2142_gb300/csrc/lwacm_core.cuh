@@ -98,6 +98,7 @@ struct StepParams {
     int walled[3];      // 1 = half-way walls on both ends of this axis
     int lid_axis;       // axis whose top wall moves with the lid velocity
     int xfaces_done;    // 1: the interior kernel applied the x-face walls (inner x-face nodes)
+    unsigned *sr_ctr;   // non-null: round stores stochastically, keyed by this step counter
     int *err;           // device error word (bounded waits that gave up set it)
 };
 

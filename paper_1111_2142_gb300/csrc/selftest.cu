@@ -38,7 +38,43 @@ __global__ void k_quotient(const float *__restrict__ a, const float *__restrict_
     }
 }
 
+// stochastic rounding of x[k] as the half-row kernel stores field 0 (the density) of
+// node k in the step with counter `step`, widened back to FP32; four elements per
+// call of the kernel's store routine
+template <typename T>
+__global__ void k_round(const float *__restrict__ x, float *__restrict__ out, long long n, uint32_t key) {
+    const long long stride = (long long)gridDim.x * blockDim.x;
+    for (long long k = 4 * (blockIdx.x * (long long)blockDim.x + threadIdx.x); k < n; k += 4 * stride) {
+        float v[4];
+        uint32_t h[4];
+#pragma unroll
+        for (int i = 0; i < 4; ++i) {
+            v[i] = k + i < n ? x[k + i] : 0.f;
+            h[i] = lwacm::tile::sr_bits((uint32_t)(k + i), 0u, key);
+        }
+        __align__(8) T t[4];
+        lwacm::tile::st4_sr(t, v[0], v[1], v[2], v[3], h[0], h[1], h[2], h[3]);
+#pragma unroll
+        for (int i = 0; i < 4; ++i)
+            if (k + i < n) out[k + i] = (float)t[i];
+    }
+}
+
 }  // namespace
+
+extern "C" int lwacm_selftest_round(const float *x_dev, float *out_dev, long long n, int storage, unsigned step,
+                                    void *stream) {
+    if (!x_dev || !out_dev || n < 1 || n >= (1LL << 31) || (storage != LWACM_BF16 && storage != LWACM_F16))
+        return LWACM_E_ARG;
+    const long long blocks = (n + 1023) / 1024;
+    const unsigned grid = (unsigned)(blocks < 4096 ? blocks : 4096);
+    const uint32_t key = lwacm::tile::sr_key(step);
+    if (storage == LWACM_BF16)
+        k_round<__nv_bfloat16><<<grid, 256, 0, (cudaStream_t)stream>>>(x_dev, out_dev, n, key);
+    else
+        k_round<__half><<<grid, 256, 0, (cudaStream_t)stream>>>(x_dev, out_dev, n, key);
+    return cudaGetLastError() == cudaSuccess ? LWACM_OK : LWACM_E_CUDA;
+}
 
 extern "C" int lwacm_selftest_quotient(const float *a_dev, const float *b_dev, float *out_dev, long long n,
                                        int packed, void *stream) {

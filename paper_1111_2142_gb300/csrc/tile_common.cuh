@@ -25,6 +25,7 @@ struct TiledParams {
     float s18;           // s / 18 = nu
     float a, am1;        // a = 1 - 6 nu and a - 1 = -6 nu (post_combine, lwacm_core.cuh)
     float g[3];          // constant acceleration of Eq. force (used by the forced variant)
+    const unsigned *sr_ctr;  // stochastic rounding (BF16 / FP16 storage): the step counter
     int *err;            // error word (timeout)
 };
 
@@ -223,6 +224,61 @@ __device__ __forceinline__ void st4(__half *p, float a, float b, float c, float 
     uint2 r;
     memcpy(&r.x, &x, 4);
     memcpy(&r.y, &y, 4);
+    *reinterpret_cast<uint2 *>(p) = r;
+}
+
+// ---- stochastic rounding to BF16 / FP16 storage -----------------------------------
+// A value x between the storage type's neighbours lo and hi (|lo| <= |x| < |hi|,
+// same sign) is stored as hi with probability (x - lo) / (hi - lo), else as lo, so
+// that the stored value is x in expectation: a change per step below half a storage
+// ulp accumulates over the steps instead of being rounded away each step. The 16
+// random bits per stored value come from a counter-based generator: MurmurHash3's
+// 32-bit finalizer (A. Appleby, MurmurHash3, public domain), a bijection of 32-bit
+// words, applied to (node index, field pair) xored with a key drawn from the step
+// counter; each field takes one half of the word.
+__host__ __device__ __forceinline__ uint32_t fmix32(uint32_t h) {
+    h ^= h >> 16;
+    h *= 0x85ebca6bu;
+    h ^= h >> 13;
+    h *= 0xc2b2ae35u;
+    h ^= h >> 16;
+    return h;
+}
+__host__ __device__ __forceinline__ uint32_t sr_key(uint32_t step) { return fmix32(step ^ 0x9e3779b9u); }
+// the random word of fields 2q (low half) and 2q+1 (high half) of node k
+__device__ __forceinline__ uint32_t sr_bits(uint32_t k, uint32_t q, uint32_t key) { return fmix32(((k << 1) | q) ^ key); }
+
+// bfloat16 is the upper half of an FP32: adding r16 to the discarded half carries
+// into the kept half with probability (discarded bits) / 2^16
+__device__ __forceinline__ uint16_t sr_bf16(float x, uint32_t r16) {
+    const uint32_t b = __float_as_uint(x);
+    if ((b & 0x7f800000u) == 0x7f800000u) return __bfloat16_as_ushort(__float2bfloat16_rn(x));  // inf, NaN
+    return (uint16_t)((b + r16) >> 16);
+}
+// FP16 in its normal range (2^-14 <= |x| < 2^16): 13 significand bits are dropped,
+// so adding 13 random bits there and rounding toward zero carries into the kept
+// bits with probability (dropped bits) / 2^13. Below it the FP16 spacing is a fixed
+// 2^-24: the fraction of a spacing is formed exactly and compared with the bits.
+__device__ __forceinline__ uint16_t sr_f16(float x, uint32_t r16) {
+    const uint32_t b = __float_as_uint(x), ex = (b >> 23) & 0xffu;
+    if (ex >= 113u && ex <= 142u) return __half_as_ushort(__float2half_rz(__uint_as_float(b + (r16 & 0x1fffu))));
+    if (ex < 113u) {
+        const uint16_t lb = __half_as_ushort(__float2half_rz(x));
+        const float frac = fabsf(x - __half2float(__ushort_as_half(lb))) * 16777216.f;
+        return frac * 65536.f > (float)r16 ? (uint16_t)(lb + 1u) : lb;
+    }
+    return __half_as_ushort(__float2half_rn(x));  // beyond the FP16 range, inf, NaN
+}
+__device__ __forceinline__ uint16_t sr_round(float x, uint32_t r16, const __nv_bfloat16 *) { return sr_bf16(x, r16); }
+__device__ __forceinline__ uint16_t sr_round(float x, uint32_t r16, const __half *) { return sr_f16(x, r16); }
+
+// store four floats rounded stochastically (r: 16 random bits each, in the low half)
+template <typename T>
+__device__ __forceinline__ void st4_sr(T *p, float a, float b, float c, float d, uint32_t ra, uint32_t rb,
+                                       uint32_t rc, uint32_t rd) {
+    uint2 r;
+    r.x = (uint32_t)sr_round(a, ra & 0xffffu, p) | ((uint32_t)sr_round(b, rb & 0xffffu, p) << 16);
+    r.y = (uint32_t)sr_round(c, rc & 0xffffu, p) | ((uint32_t)sr_round(d, rd & 0xffffu, p) << 16);
     *reinterpret_cast<uint2 *>(p) = r;
 }
 

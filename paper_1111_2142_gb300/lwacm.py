@@ -24,6 +24,7 @@ OPT_LID_X, OPT_LID_Y, OPT_LID_Z, OPT_FORCE_X, OPT_FORCE_Y, OPT_FORCE_Z = range(6
 OPT_RHO0, OPT_STORAGE, OPT_GRAPH_CHUNK, OPT_KERNEL = 6, 7, 8, 9
 OPT_BATCH_MODE, OPT_TEST_WITHHOLD, OPT_FORCE_FIELD, OPT_BATCH_TILE, OPT_NU_P = 10, 11, 12, 13, 14
 OPT_SCALAR_ALPHA, OPT_BULK_GAMMA, OPT_SEMI_IMPLICIT = 15, 16, 17
+OPT_STOCHASTIC_ROUNDING = 18
 # 2D tile shapes of the D2Q9 batched kernel (LWACM_OPT_BATCH_TILE 1..6); 0 = 1D runs
 BATCH_TILE_SHAPES = {0: None, 1: (30, 6), 2: (30, 14), 3: (62, 6), 4: (30, 30), 5: (62, 14), 6: (126, 6)}
 
@@ -72,6 +73,7 @@ def load():
         "lwacm_batch_offsets": [vp, P(ll)],
         "lwacm_measure_fp32_peak": [ll, vp, P(d), P(d)],
         "lwacm_selftest_quotient": [vp, vp, vp, ll, i, vp],
+        "lwacm_selftest_round": [vp, vp, ll, i, ctypes.c_uint, vp],
         "lwacm_set_force_field": [vp, vp, vp, vp, i, i],
         "lwacm_autotune": [vp, ctypes.c_char_p, i, ctypes.c_char_p, ctypes.c_size_t],
         "lwacm_set_scalar": [vp, vp, i, i],
@@ -116,7 +118,8 @@ class Lwacm:
 
     def __init__(self, lattice, nx, ny, nz=1, nu=0.01, bc=PERIODIC, *, storage=F32, lid=None,
                  force=None, rho0=None, kernel=0, graph_chunk=None, device=None, stream=None,
-                 force_field=False, scalar_alpha=None, bulk_gamma=None, semi_implicit=False):
+                 force_field=False, scalar_alpha=None, bulk_gamma=None, semi_implicit=False,
+                 stochastic_rounding=False):
         lib = load()
         self.lattice, self.nx, self.ny, self.nz = int(lattice), int(nx), int(ny), int(nz)
         self.nu, self.bc = float(nu), int(bc)
@@ -135,6 +138,8 @@ class Lwacm:
             extra[OPT_BULK_GAMMA] = bulk_gamma
         if semi_implicit:
             extra[OPT_SEMI_IMPLICIT] = 1
+        if stochastic_rounding:
+            extra[OPT_STOCHASTIC_ROUNDING] = 1
         self._setup(lib, h, storage, lid, force, rho0, kernel, graph_chunk, device, stream, extra)
 
     def _setup(self, lib, h, storage, lid, force, rho0, kernel, graph_chunk, device, stream,

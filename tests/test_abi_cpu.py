@@ -306,3 +306,38 @@ def test_semi_implicit_option(lib):
         assert st == lw.OK
         assert lib.lwacm_set_option(h, lw.OPT_SEMI_IMPLICIT, 1.0) == lw.E_UNSUPPORTED
         lib.lwacm_destroy(h)
+
+
+def test_stochastic_rounding_option(lib):
+    """Stochastic rounding of BF16 / FP16 stores is a 0/1 option for single periodic
+    D3Q19 domains with half-width storage and the plain scheme; checked without a
+    device (the kernel choice itself is made at bind)."""
+    from paper_1111_2142_gb300 import lwacm as lw
+    st, h = _create(lib, 19, 256, 16, 8, 0.02, lw.PERIODIC)
+    assert st == lw.OK
+    assert lib.lwacm_set_option(h, lw.OPT_STOCHASTIC_ROUNDING, 2.0) == lw.E_ARG
+    assert lib.lwacm_set_option(h, lw.OPT_STOCHASTIC_ROUNDING, 1.0) == lw.E_UNSUPPORTED  # FP32 storage
+    assert lib.lwacm_set_option(h, lw.OPT_STORAGE, float(lw.F16)) == lw.OK
+    assert lib.lwacm_set_option(h, lw.OPT_STOCHASTIC_ROUNDING, 1.0) == lw.OK
+    assert lib.lwacm_set_option(h, lw.OPT_STORAGE, float(lw.F32)) == lw.E_UNSUPPORTED
+    assert lib.lwacm_set_option(h, lw.OPT_STORAGE, float(lw.BF16)) == lw.OK
+    assert lib.lwacm_set_option(h, lw.OPT_STOCHASTIC_ROUNDING, 0.0) == lw.OK
+    assert lib.lwacm_set_option(h, lw.OPT_SEMI_IMPLICIT, 1.0) == lw.OK
+    assert lib.lwacm_set_option(h, lw.OPT_STOCHASTIC_ROUNDING, 1.0) == lw.E_UNSUPPORTED
+    lib.lwacm_destroy(h)
+    for lat, bc in ((9, lw.PERIODIC), (19, lw.CAVITY), (19, lw.CHANNEL)):
+        st, h = _create(lib, lat, 256, 16, 8 if lat == 19 else 1, 0.02, bc)
+        assert st == lw.OK
+        assert lib.lwacm_set_option(h, lw.OPT_STORAGE, float(lw.BF16)) == lw.OK
+        assert lib.lwacm_set_option(h, lw.OPT_STOCHASTIC_ROUNDING, 1.0) == lw.E_UNSUPPORTED
+        lib.lwacm_destroy(h)
+
+
+def test_selftest_round_validation(lib):
+    from paper_1111_2142_gb300 import lwacm as lw
+    p = ctypes.c_void_p(16)
+    assert lib.lwacm_selftest_round(None, p, 4, lw.BF16, 0, None) == lw.E_ARG
+    assert lib.lwacm_selftest_round(p, None, 4, lw.BF16, 0, None) == lw.E_ARG
+    assert lib.lwacm_selftest_round(p, p, 0, lw.F16, 0, None) == lw.E_ARG
+    assert lib.lwacm_selftest_round(p, p, 1 << 31, lw.F16, 0, None) == lw.E_ARG
+    assert lib.lwacm_selftest_round(p, p, 4, lw.F32, 0, None) == lw.E_ARG

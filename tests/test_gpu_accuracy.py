@@ -37,32 +37,50 @@ def _rel_l2(g, r):
     return float(np.linalg.norm((g - r).ravel()) / max(np.linalg.norm(r.ravel()), 1e-300))
 
 
-@pytest.mark.parametrize("n", [128, 256])
-def test_benchmark_kernel_thousand_steps_vs_oracle(lw, n):
-    f = inputs.tgv3d(n, u0=U0)
-    f32 = [a.astype(np.float32).astype(np.float64) for a in f]  # the GPU's rounded initial state
-    sim = lw.Lwacm(lw.D3Q19, n, n, n, NU)
+_ORACLE = {}
+
+
+def _oracle_run(n):
+    """The FP64 oracle's kinetic energy every EVERY steps and its state after T steps,
+    from the FP32-rounded initial fields (computed once per size and kept)."""
+    if n not in _ORACLE:
+        f32 = [a.astype(np.float32).astype(np.float64) for a in inputs.tgv3d(n, u0=U0)]
+        state = tuple(f32)
+        ke = [oracle.diagnostics(*state)["ke"]]
+        for _ in range(T // EVERY):
+            state = oracle.step(19, *state, nu=NU, nsteps=EVERY)
+            ke.append(oracle.diagnostics(*state)["ke"])
+        _ORACLE[n] = (f32, np.array(ke), state)
+    return _ORACLE[n]
+
+
+def _gpu_run(lw, n, f32, **kw):
+    sim = lw.Lwacm(lw.D3Q19, n, n, n, NU, **kw)
     sim.set_fields(*f32)
-    ke_gpu = [sim.diagnostics()["ke"]]
+    ke = [sim.diagnostics()["ke"]]
     for _ in range(T // EVERY):
         sim.step(EVERY)
-        ke_gpu.append(sim.diagnostics()["ke"])
+        ke.append(sim.diagnostics()["ke"])
     got = [a.reshape(n, n, n) for a in sim.get_fields()]
     name = sim.kernel_name
     sim.close()
+    return got, np.array(ke), name
 
-    state = tuple(f32)
-    ke_ref = [oracle.diagnostics(*state)["ke"]]
-    for _ in range(T // EVERY):
-        state = oracle.step(19, *state, nu=NU, nsteps=EVERY)
-        ke_ref.append(oracle.diagnostics(*state)["ke"])
 
+def _errors(got, ke_gpu, state, ke_ref):
     eu = max(float(np.max(np.abs(g - r))) for g, r in zip(got[1:], state[1:])) / U0
     dscale = max(float(np.max(np.abs(state[0]))), 3 * U0 ** 2)
     ed = float(np.max(np.abs(got[0] - state[0]))) / dscale
     l2 = [_rel_l2(g, r) for g, r in zip(got, state)]
-    ke_gpu, ke_ref = np.array(ke_gpu), np.array(ke_ref)
     eke = float(np.max(np.abs(ke_gpu - ke_ref) / ke_ref))
+    return eu, ed, l2, eke
+
+
+@pytest.mark.parametrize("n", [128, 256])
+def test_benchmark_kernel_thousand_steps_vs_oracle(lw, n):
+    f32, ke_ref, state = _oracle_run(n)
+    got, ke_gpu, name = _gpu_run(lw, n, f32)
+    eu, ed, l2, eke = _errors(got, ke_gpu, state, ke_ref)
     print(f"[{name}] D3Q19 TGV {n}^3 x {T}: max|du|/u0 = {eu:.2e}, max|dd|/d = {ed:.2e}, "
           f"rel L2 (d, ux, uy, uz) = {', '.join(f'{x:.1e}' for x in l2)}, "
           f"KE curve max rel = {eke:.1e}, KE(T)/KE(0) = {ke_ref[-1] / ke_ref[0]:.6f}")
@@ -70,3 +88,34 @@ def test_benchmark_kernel_thousand_steps_vs_oracle(lw, n):
     assert eu <= 1e-5 and ed <= 1e-4
     assert eke <= 4e-5
     assert np.all(np.diff(ke_ref) < 0) and np.all(np.diff(ke_gpu) < 0)
+
+
+@pytest.mark.parametrize("n,storage", [(128, 2), (256, 2), (128, 1)])
+def test_half_storage_stochastic_rounding_thousand_steps(lw, n, storage):
+    """FP16 / BF16 storage with stochastic rounding on the same 1000-step workload.
+    Rounded to nearest, the decay stalls: the per-step change of u (3 nu k^2 u, about
+    4e-5 u per step at 128^3) is below half an FP16 ulp (2^-11 u), so most values
+    never move and the kinetic energy stays near its initial value. Rounded
+    stochastically, each stored value is unbiased, so the decay proceeds; the
+    rounding noise (a few storage ulps per value) averages out of the kinetic energy
+    over the n^3 nodes. FP16 keeps the KE curve within the FP32 run's bound (4e-5);
+    BF16 (8-bit significand, 8x the FP16 spacing) within 64x that (its noise variance
+    adds ~(ulp / u)^2 to the energy). The per-field errors against the oracle are
+    printed for the record and bounded by 16 storage spacings (of u near u0, and of
+    d relative to its scale)."""
+    f32, ke_ref, state = _oracle_run(n)
+    fmt = "FP16" if storage == 2 else "BF16"
+    got, ke_sr, name = _gpu_run(lw, n, f32, storage=storage, stochastic_rounding=True)
+    eu, ed, l2, eke = _errors(got, ke_sr, state, ke_ref)
+    _, ke_rn, _ = _gpu_run(lw, n, f32, storage=storage)
+    eke_rn = float(np.max(np.abs(ke_rn - ke_ref) / ke_ref))
+    print(f"[{name}] {fmt} stochastic D3Q19 TGV {n}^3 x {T}: max|du|/u0 = {eu:.2e}, max|dd|/d = {ed:.2e}, "
+          f"rel L2 (d, ux, uy, uz) = {', '.join(f'{x:.1e}' for x in l2)}, KE curve max rel = {eke:.1e} "
+          f"(rounded to nearest: {eke_rn:.1e}), KE(T)/KE(0) = {ke_sr[-1] / ke_sr[0]:.6f} "
+          f"(oracle {ke_ref[-1] / ke_ref[0]:.6f})")
+    assert name.startswith("half")
+    assert eke <= (4e-5 if storage == 2 else 64 * 4e-5)
+    assert eke_rn > 10 * eke
+    # storage spacing: of u near u0 (u0 = 0.02 in [2^-6, 2^-5)) and, relative, of d
+    su, rel = (2.0 ** -16, 2.0 ** -10) if storage == 2 else (2.0 ** -13, 2.0 ** -7)
+    assert eu <= 16 * su / U0 and ed <= 16 * rel

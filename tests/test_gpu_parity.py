@@ -124,14 +124,19 @@ def test_d3q19_tiled_kernel(lw, shape):
     assert eu < 1e-5 and ed < 1e-4
 
 
-@pytest.mark.parametrize("bc", [1, 2])
-@pytest.mark.parametrize("shape", [(5, 8, 128), (3, 16, 256), (20, 24, 128), (2, 8, 256), (11, 72, 128)])
+WALL_SHAPES = [(5, 8, 128), (3, 16, 256), (20, 24, 128), (2, 8, 256), (11, 72, 128), (4, 8, 256), (7, 40, 256)]
+
+
+@pytest.mark.parametrize("bc,shape", [(bc, s) for bc in (1, 2) for s in WALL_SHAPES] + [(2, (1, 16, 128))])
 def test_d3q19_tiled_kernel_walls(lw, bc, shape):
     """The row-tiled D3Q19 kernel on walled domains: the diagonally driven cavity
-    (all six faces walled, lid on the top y face) and a channel with a moving wall
-    (walls at y = 0, ny-1; x and z periodic). The interior kernel wraps every axis
-    and the wall pass after it recomputes the boundary nodes, so the result must be
-    the oracle's walled step; shapes include nz = 2 (every node on a z face)."""
+    (all six faces walled, the lid on the top z face moving along the diagonal) and a
+    channel with a moving wall (walls at y = 0, ny-1, the one at ny-1 moving; x and
+    z periodic). The kernel applies the cavity's x-face walls itself and wraps y and
+    z; the wall pass after it recomputes the other boundary nodes, so the result
+    must be the oracle's walled step. Shapes include nz = 2 (every node on a z face;
+    a cavity needs two planes, the channel runs one), one column of rows (ny = 8)
+    and runs that cross columns."""
     lid = (np.sqrt(2) / 20, np.sqrt(2) / 20, 0.0) if bc == 1 else (0.01, 0.0, 0.0)
     f = inputs.smooth_random(shape, seed=14, u_amp=0.03, d_amp=0.005)
     got, name = run_gpu(lw, 19, f, 0.02, 40, bc=bc, lid=lid, kernel=5)
@@ -139,6 +144,33 @@ def test_d3q19_tiled_kernel_walls(lw, bc, shape):
     ref = oracle.step(19, *f, nu=0.02, bc=bc, lid=lid, nsteps=40)
     eu, ed = errs(got, ref, 0.1)
     print(f"[{name}] walls bc={bc} {shape}: du/U={eu:.2e} dd/d={ed:.2e}")
+    assert eu < 1e-5 and ed < 1e-4
+
+
+@pytest.mark.parametrize("shape", [(6, 16, 128), (3, 8, 256)])
+def test_d3q19_tiled_kernel_resting_walls(lw, shape):
+    """A closed box with resting walls (no moving wall): every face bounces, no lid term."""
+    f = inputs.smooth_random(shape, seed=17, u_amp=0.03, d_amp=0.005)
+    got, name = run_gpu(lw, 19, f, 0.02, 40, bc=1, lid=(0.0, 0.0, 0.0), kernel=5)
+    assert name.startswith("half")
+    ref = oracle.step(19, *f, nu=0.02, bc=1, lid=(0.0, 0.0, 0.0), nsteps=40)
+    eu, ed = errs(got, ref, 0.03)
+    print(f"[{name}] resting box {shape}: du/U={eu:.2e} dd/d={ed:.2e}")
+    assert eu < 1e-5 and ed < 1e-4
+
+
+@pytest.mark.parametrize("shape", [(4, 16, 128), (3, 8, 256)])
+def test_d3q19_tiled_kernel_forced_channel(lw, shape):
+    """A channel driven by a constant acceleration along x (Eq. force; walls at
+    y = 0, ny-1 at rest): the forced kernel wraps every axis and the wall pass after
+    it recomputes the wall rows, forcing included."""
+    g = (2e-5, 0.0, 1e-6)
+    f = inputs.smooth_random(shape, seed=18, u_amp=0.02, d_amp=0.003)
+    got, name = run_gpu(lw, 19, f, 0.02, 40, bc=2, lid=(0.0, 0.0, 0.0), force=g, kernel=5)
+    assert name.startswith("half")
+    ref = oracle.step(19, *f, nu=0.02, bc=2, lid=(0.0, 0.0, 0.0), force=g, nsteps=40)
+    eu, ed = errs(got, ref, 0.02)
+    print(f"[{name}] forced channel {shape}: du/U={eu:.2e} dd/d={ed:.2e}")
     assert eu < 1e-5 and ed < 1e-4
 
 

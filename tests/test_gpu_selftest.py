@@ -102,3 +102,76 @@ def test_quotient_wide_range(quotient):
     for packed in (1, 0):
         bad = _mismatches(quotient(a, b, packed), a, b)
         assert bad.size == 0, (packed, a[bad[:5]], b[bad[:5]])
+
+
+# ---- stochastic rounding of BF16 / FP16 stores ---------------------------------
+
+def _neighbours(x, storage):
+    """The storage values lo (x rounded toward zero) and hi (the next one away from
+    zero) around each FP32 value x, as FP64."""
+    x = np.asarray(x, dtype=np.float32)
+    if storage == 1:  # bfloat16: the upper 16 bits of an FP32
+        b = x.view(np.uint32)
+        lo = (b & np.uint32(0xFFFF0000)).view(np.float32).astype(np.float64)
+        hi = ((b & np.uint32(0xFFFF0000)) + np.uint32(0x10000)).view(np.float32).astype(np.float64)
+        return lo, hi
+    h = x.astype(np.float16)  # to nearest, then step toward zero where it overshot
+    over = np.abs(h.astype(np.float64)) > np.abs(x.astype(np.float64))
+    h = np.where(over, np.nextafter(h, np.float16(0)), h)
+    away = np.where(np.signbit(x), np.float16(-np.inf), np.float16(np.inf))
+    return h.astype(np.float64), np.nextafter(h, away).astype(np.float64)
+
+
+@pytest.fixture(scope="module")
+def rounding():
+    import __graft_entry__
+    __graft_entry__.build()
+    import torch
+    from paper_1111_2142_gb300 import lwacm as lw
+    lib = lw.load()
+
+    def run(x, storage, step):
+        xd = torch.from_numpy(np.ascontiguousarray(x, dtype=np.float32)).cuda()
+        out = torch.empty_like(xd)
+        st = torch.cuda.current_stream()
+        assert lib.lwacm_selftest_round(ctypes.c_void_p(xd.data_ptr()), ctypes.c_void_p(out.data_ptr()), x.size,
+                                        int(storage), int(step), ctypes.c_void_p(st.cuda_stream)) == lw.OK
+        return out.cpu().numpy().astype(np.float64)
+    return run
+
+
+@pytest.mark.parametrize("storage", [1, 2])
+def test_stochastic_rounding_is_unbiased(rounding, storage):
+    """Each stored value is one of the two storage values around x, never another;
+    exact values stay; over S step keys the fraction rounded away from zero matches
+    (x - lo) / (hi - lo) for every x (binomial bound, 6 sigma plus the 2^-16
+    resolution of the random bits), and the mean of the rounding error over all
+    values and keys is zero within its standard error (round to nearest would be
+    biased by the full per-value distance to the nearer neighbour)."""
+    rng = np.random.default_rng(31)
+    n, S = 6000, 256
+    mag = 10.0 ** rng.uniform(-7 if storage == 2 else -20, 0, n)
+    x = (mag * rng.choice([-1.0, 1.0], n)).astype(np.float32)
+    x[:64] = np.float32(0.0)
+    lo, hi = _neighbours(x, storage)
+    x[64:128] = lo[64:128].astype(np.float32)  # exactly representable values
+    lo, hi = _neighbours(x, storage)
+    xd = x.astype(np.float64)
+    up = np.zeros(n)
+    err = np.zeros(n)
+    for s in range(S):
+        got = rounding(x, storage, s)
+        is_lo, is_hi = got == lo, got == hi
+        assert np.all(is_lo | is_hi), np.flatnonzero(~(is_lo | is_hi))[:5]
+        up += is_hi & ~is_lo
+        err += got - xd
+    frac = np.where(hi != lo, (xd - lo) / (hi - lo), 0.0)
+    obs = up / S
+    sig = np.sqrt(frac * (1 - frac) / S)
+    assert np.all(obs[64:128] == 0) and np.all(obs[:64] == 0)
+    assert np.all(np.abs(obs - frac) <= 6 * sig + 2.0 ** -16 + 1e-12), float(np.max(np.abs(obs - frac) - 6 * sig))
+    # mean rounding error in units of each value's spacing: zero within 5 standard errors
+    spacing = np.where(hi != lo, np.abs(hi - lo), 1.0)
+    e = (err / S) / spacing
+    se = np.sqrt(np.sum(frac * (1 - frac) / S)) / n
+    assert abs(float(np.mean(e))) <= 5 * se + 2.0 ** -16, (float(np.mean(e)), se)
