@@ -1,7 +1,8 @@
-// Half-row TMA row-tiled D3Q19 kernel, for domains with nx = 256 (or 128) and ny a
-// multiple of 8 (periodic; walled domains get the wall pass after it, the cavity's
-// x faces handled here): the moment form of Eq. ACM2.0 (see lwacm_core.cuh), every
-// field read from HBM once and written once per step.
+// Half-row TMA row-tiled D3Q19 kernel, for domains with nx = 256, 128 or any larger
+// multiple of 128 and ny a multiple of 8 (periodic; walled domains get the wall pass
+// after it, the cavity's x faces handled here for rows of 128 and 256): the moment
+// form of Eq. ACM2.0 (see lwacm_core.cuh), every field read from HBM once and
+// written once per step.
 //
 // Persistent CTAs over chunk-major (y-column, z-chunk) items, TMA bulk copies of
 // ten staged rows per plane, packed row exchange through shared memory, three
@@ -16,7 +17,10 @@
 // the halves exchange nothing.
 //
 // nx = 128 uses the same code with one warp per row (NH = 1): the warp's shuffles
-// wrap x periodically by themselves, and two CTAs of 8 warps share an SM.
+// wrap x periodically by themselves, and two CTAs of 8 warps share an SM. Longer
+// rows (NH = 0) are cut into 128-node segments, one warp each, whose boundary lanes
+// recompute their outside neighbours' link values like the halves do, from 8 extra
+// staged nodes on each side.
 #include <stdint.h>
 
 #include "dev_cache.h"
@@ -32,18 +36,34 @@ using namespace tile;
 constexpr int VXH = 4;                 // nodes per lane
 constexpr int HALF = 128;              // nodes per warp row segment
 
-// NH warps share a row of nx = 128 NH nodes (NH = 1: one warp per row, its lanes
-// wrap periodically by themselves; NH = 2: two halves, see above).
-// T: storage type of the fields (FP32, or BF16 / FP16 widened to FP32 on load).
-template <int NH, typename T = float>
-struct HG {
-    static constexpr int NTH = ROWS * NH * 32;  // threads per CTA
-    static constexpr int RL = HALF * NH;        // row length (nx)
+// Row geometry. NH = 1: one warp per row of nx = 128 nodes, its lanes wrap
+// periodically by themselves; NH = 2: two warps (halves) per row of 256, see above;
+// NH = 0: rows of nx = 128 S nodes (S >= 3) cut into S segments of 128, one warp per
+// segment and a CTA per (segment, column of rows): the staged rows carry 8 more
+// nodes on each side (x0 - 8 .. x0 + 135, wrapped), and the boundary lanes take
+// their outside neighbours from them as the halves do.
+template <int NH>
+struct HGeo {
+    static constexpr bool SEG = NH == 0;
+    static constexpr int NW = NH == 2 ? 2 : 1;      // warps per row (or segment)
+    static constexpr int NTH = ROWS * NW * 32;      // threads per CTA
+    static constexpr int MINB = NH == 2 ? 1 : 2;    // CTAs per SM
+    static constexpr int RL = HALF * NW;            // nodes of a row a CTA updates
+    static constexpr int SRL = SEG ? HALF + 16 : RL;  // staged row length
+    static constexpr int OWN = SEG ? 8 : 0;         // staged index of the first own node
+    static constexpr bool NB = NH != 1;             // boundary lanes read their outside neighbours
     static constexpr int XSLOT = ROWS * RL;
     static constexpr int XDIR = NSLOT * XSLOT;
-    static constexpr int XBUF = 2 * XDIR;        // floats
-    static constexpr int STAGE = 4 * TROWS * RL;  // elements of T
-    static constexpr size_t BYTES = 2 * (size_t)XBUF * 4 + 2 * (size_t)STAGE * sizeof(T) + 64;
+    static constexpr int XBUF = 2 * XDIR;  // floats
+    // staged indices of the neighbours lane 0 (left) and lane 31 (right) of half h take
+    __device__ static int left(int h) { return SEG ? OWN - 1 : (h * HALF + RL - 1) % RL; }
+    __device__ static int right(int h) { return SEG ? OWN + HALF : (h * HALF + HALF) % RL; }
+};
+// T: storage type of the fields (FP32, or BF16 / FP16 widened to FP32 on load).
+template <int NH, typename T = float>
+struct HG : HGeo<NH> {
+    static constexpr int STAGE = 4 * TROWS * HGeo<NH>::SRL;  // elements of T
+    static constexpr size_t BYTES = 2 * (size_t)HGeo<NH>::XBUF * 4 + 2 * (size_t)STAGE * sizeof(T) + 64;
     static constexpr uint32_t TX = STAGE * sizeof(T);
 };
 
@@ -190,7 +210,7 @@ __device__ __forceinline__ void send_rows(const NC2 &nc, float *ubase, float *db
                                           float nb1, float nb2, int lane, bool w0 = false, bool wN = false,
                                           bool e0 = false, bool eN = false, F2 (*own)[4] = nullptr) {
     constexpr int XSLOT = HG<NH>::XSLOT;
-    const bool l0 = lane == 0 && NH == 2, l31 = lane == 31 && NH == 2;
+    const bool l0 = lane == 0 && HG<NH>::NB, l31 = lane == 31 && HG<NH>::NB;
     if (MODE == MID) {
         F2 u0[2], u1[2], d0[2], d1[2];
 #pragma unroll
@@ -313,16 +333,17 @@ __device__ __forceinline__ void phase_a(Acc &acc, const T *stg, float *xbuf, con
     // the other warps skip the face code); e0 / eN: the lane holding that node
     const bool w0 = XW && half == 0, wN = XW && half == NH - 1;
     const bool e0 = w0 && lane == 0, eN = wN && lane == 31;
-    constexpr int RL = HG<NH>::RL, XDIR = HG<NH>::XDIR;
+    constexpr int RL = HG<NH>::RL, XDIR = HG<NH>::XDIR, SRL = HG<NH>::SRL, OWN = HG<NH>::OWN;
+    constexpr bool NB = HG<NH>::NB;
     float *up = xbuf + half * HALF, *dn = xbuf + XDIR + half * HALF;
     {
         NC2 nc;
-        node_consts2(nc, stg + (row + 1) * RL + half * HALF, TROWS * RL, lane, p.s18, p.a, p.am1);
-        // NH = 2: the boundary neighbour's constants (unused for NH = 1)
-        const int nbx = lane < 16 ? (half * HALF + RL - 1) % RL : (half * HALF + HALF) % RL;
+        node_consts2(nc, stg + (row + 1) * SRL + OWN + half * HALF, TROWS * SRL, lane, p.s18, p.a, p.am1);
+        // the boundary neighbour's constants (NB; unused for NH = 1)
+        const int nbx = lane < 16 ? HG<NH>::left(half) : HG<NH>::right(half);
         const float sgn = lane < 16 ? 1.f : -1.f;
         NbC nb{};
-        if (NH == 2) nb = nb_consts(stg + (row + 1) * RL, TROWS * RL, nbx, sgn, p.s18);
+        if (NB) nb = nb_consts(stg + (row + 1) * SRL, TROWS * SRL, nbx, sgn, p.s18);
 #pragma unroll
         for (int j = 0; j < 2; ++j) {
             F2 gp, gm;
@@ -360,9 +381,9 @@ __device__ __forceinline__ void phase_a(Acc &acc, const T *stg, float *xbuf, con
             // (0,1 | 2,3) take the values of nodes (-1,0 | 1,2), for -c those of
             // nodes (1,2 | 3,4); nodes -1 and 4 are the neighbouring lanes'
             // NH = 2: lane 0's +c value and lane 31's -c value from the neighbour
-            const float nbv = NH == 2 ? nb_val(cz ? nb.K2 : nb.K1, cz ? nb.sA2 : nb.sA1, cz ? nb.B2 : nb.B1,
-                                               cz == 0 ? nb.U : (cz > 0 ? nb.U + nb.W : nb.U - nb.W))
-                                      : 0.f;
+            const float nbv = NB ? nb_val(cz ? nb.K2 : nb.K1, cz ? nb.sA2 : nb.sA1, cz ? nb.B2 : nb.B1,
+                                          cz == 0 ? nb.U : (cz > 0 ? nb.U + nb.W : nb.U - nb.W))
+                                 : 0.f;
             if (XW && MODE == MID) {  // links crossing an x face bounce (see send_rows)
                 if (w0 && e0) {  // (1,0,cz) into x = 0: its own (-1,0,-cz) value
                     const float v = gm[0].x;
@@ -380,7 +401,7 @@ __device__ __forceinline__ void phase_a(Acc &acc, const T *stg, float *xbuf, con
             if (np) {  // c = (1,0,cz): node i feeds node i+1
                 const float eP = gp[1].y;
                 float rP = __shfl_sync(FULL, eP, (lane + 31) & 31);
-                if (NH == 2) rP = lane == 0 ? nbv : rP;
+                if (NB) rP = lane == 0 ? nbv : rP;
                 if (XW && w0) rP = e0 ? 0.f : rP;
                 const F2 R[2] = {make_float2(rP, gp[0].x), make_float2(gp[0].y, gp[1].x)};
                 F2(&a)[2][4] = acc[pl<PM, P0, PP>(cz)];
@@ -394,7 +415,7 @@ __device__ __forceinline__ void phase_a(Acc &acc, const T *stg, float *xbuf, con
             if (nm) {  // -c = (-1,0,-cz): node i feeds node i-1
                 const float eM = gm[0].x;
                 float rM = __shfl_sync(FULL, eM, (lane + 1) & 31);
-                if (NH == 2) rM = lane == 31 ? nbv : rM;
+                if (NB) rM = lane == 31 ? nbv : rM;
                 if (XW && wN) rM = eN ? 0.f : rM;
                 const F2 L[2] = {make_float2(gm[0].y, gm[1].x), make_float2(gm[1].y, rM)};
                 if (cz < 0) {  // -c = (-1,0,1): first x-momentum of the plane ahead
@@ -414,19 +435,19 @@ __device__ __forceinline__ void phase_a(Acc &acc, const T *stg, float *xbuf, con
                 }
             }
         }
-        const float nb1 = NH == 2 && MODE == MID ? nb_val(nb.K2, nb.sA2, nb.B2, nb.U + nb.V) : 0.f;
-        const float nb2 = NH == 2 && MODE == MID ? nb_val(nb.K2, -nb.sA2, nb.B2, nb.V - nb.U) : 0.f;
+        const float nb1 = NB && MODE == MID ? nb_val(nb.K2, nb.sA2, nb.B2, nb.U + nb.V) : 0.f;
+        const float nb2 = NB && MODE == MID ? nb_val(nb.K2, -nb.sA2, nb.B2, nb.V - nb.U) : 0.f;
         send_rows<NH, MODE, XW>(nc, up + (row + 1) * RL, dn + (row - 1) * RL, row + 1 < ROWS, row > 0, nb1, nb2, lane,
                                 w0, wN, e0, eN, MODE == MID ? acc[P0] : nullptr);
     }
     if (row == 0 || row == ROWS - 1) {  // halo rows: y0-1 (staged row 0) feeds row 0, y0+8 (staged 9) row 7
         const int sr = row == 0 ? 0 : TROWS - 1;
         NC2 hc;
-        node_consts2(hc, stg + sr * RL + half * HALF, TROWS * RL, lane, p.s18);
+        node_consts2(hc, stg + sr * SRL + OWN + half * HALF, TROWS * SRL, lane, p.s18);
         float nb1 = 0.f, nb2 = 0.f;
-        if (NH == 2 && MODE == MID) {
-            const int nbx = lane < 16 ? (half * HALF + RL - 1) % RL : (half * HALF + HALF) % RL;
-            const NbC hb = nb_consts(stg + sr * RL, TROWS * RL, nbx, lane < 16 ? 1.f : -1.f, p.s18);
+        if (NB && MODE == MID) {
+            const int nbx = lane < 16 ? HG<NH>::left(half) : HG<NH>::right(half);
+            const NbC hb = nb_consts(stg + sr * SRL, TROWS * SRL, nbx, lane < 16 ? 1.f : -1.f, p.s18);
             nb1 = nb_val(hb.K2, hb.sA2, hb.B2, hb.U + hb.V);
             nb2 = nb_val(hb.K2, -hb.sA2, hb.B2, hb.V - hb.U);
         }
@@ -440,7 +461,7 @@ __device__ __forceinline__ void phase_a(Acc &acc, const T *stg, float *xbuf, con
 // SRND: BF16 / FP16 stores rounded stochastically (tile_common.cuh) with the step's key
 template <int NH, int MODE, bool SRND, typename T>
 __device__ __forceinline__ void phase_b(Acc &acc, const float *xbuf, T *out, const TiledParams &p, int lane,
-                                        int row, int half, int col, int zfin, uint32_t key) {
+                                        int row, int half, int col, int x0, int zfin, uint32_t key) {
     constexpr int PM = 0, P0 = 1, PP = 2;
     constexpr int RL = HG<NH>::RL, XDIR = HG<NH>::XDIR, XSLOT = HG<NH>::XSLOT;
     const float *up = xbuf + row * RL + half * HALF, *dn = xbuf + XDIR + row * RL + half * HALF;
@@ -496,7 +517,7 @@ __device__ __forceinline__ void phase_b(Acc &acc, const float *xbuf, T *out, con
         }
         if (zfin >= 0) {
             const long long rowoff =
-                ((long long)zfin * p.ny + col * ROWS + row) * p.nx + half * HALF + lane * VXH;
+                ((long long)zfin * p.ny + col * ROWS + row) * p.nx + x0 + half * HALF + lane * VXH;
             T *op = out + rowoff;
             // u = j / rho, correctly rounded (tile_common.cuh, div_apply2)
             const Div2 r[2] = {div_prep2(add2(b2(1.f), acc[PM][0][0])), div_prep2(add2(b2(1.f), acc[PM][1][0]))};
@@ -530,28 +551,55 @@ __device__ __forceinline__ void phase_b(Acc &acc, const float *xbuf, T *out, con
     }
 }
 
+// The staged rows of one plane (four fields) for an item's rows, by 1-D bulk copies
+// that complete on `bar`. NH = 1, 2: one thread issues them (the whole rows, wrapped
+// in y). NH = 0: the lanes of one warp issue one staged row each (40 rows; a
+// segment at an x end of the domain takes its wrapped 8 nodes in a second copy).
 template <int NH, typename T>
 __device__ __forceinline__ void issue_plane(const T *in, const TiledParams &p, int col, int z, T *stage,
-                                            uint64_t *bar) {
-    constexpr int RL = HG<NH, T>::RL;
+                                            uint64_t *bar, int lane) {
+    constexpr int RL = HG<NH, T>::RL, SRL = HG<NH, T>::SRL;
     constexpr uint32_t TX = HG<NH, T>::TX;
     const int zl = z < 0 ? z + p.nz : (z >= p.nz ? z - p.nz : z);
-    const int y0 = col * ROWS;
     const long long plane = (long long)p.nx * p.ny;
-    mbar_expect_tx(bar, TX);
-    const uint32_t rb = (uint32_t)(RL * sizeof(T));
+    if constexpr (NH == 0) {
+        const int seg = col / p.ycols, y0 = (col - seg * p.ycols) * ROWS;
+        const int x0 = seg * HALF, last = p.nx / HALF - 1;
+        if (lane == 0) mbar_expect_tx(bar, TX);
+        __syncwarp();
+        for (int k = lane; k < 4 * TROWS; k += 32) {
+            const int f = k / TROWS, r = k - f * TROWS;
+            int y = y0 - 1 + r;
+            y = y < 0 ? y + p.ny : (y >= p.ny ? y - p.ny : y);
+            const T *src = in + f * p.fstride + (long long)zl * plane + (long long)y * p.nx;
+            T *dst = stage + (f * TROWS + r) * SRL;
+            if (seg == 0) {
+                bulk_g2s(dst, src + p.nx - 8, 8 * sizeof(T), bar);
+                bulk_g2s(dst + 8, src, (HALF + 8) * sizeof(T), bar);
+            } else if (seg == last) {
+                bulk_g2s(dst, src + x0 - 8, (HALF + 8) * sizeof(T), bar);
+                bulk_g2s(dst + HALF + 8, src, 8 * sizeof(T), bar);
+            } else {
+                bulk_g2s(dst, src + x0 - 8, SRL * sizeof(T), bar);
+            }
+        }
+    } else {
+        const int y0 = col * ROWS;
+        mbar_expect_tx(bar, TX);
+        const uint32_t rb = (uint32_t)(RL * sizeof(T));
 #pragma unroll
-    for (int f = 0; f < 4; ++f) {
-        const T *src = in + f * p.fstride + (long long)zl * plane;
-        T *dst = stage + f * TROWS * RL;
-        if (y0 >= 1 && y0 + ROWS < p.ny) {
-            bulk_g2s(dst, src + (long long)(y0 - 1) * p.nx, TROWS * rb, bar);
-        } else {
-            const int yb = y0 - 1 < 0 ? y0 - 1 + p.ny : y0 - 1;
-            const int yt = y0 + ROWS >= p.ny ? y0 + ROWS - p.ny : y0 + ROWS;
-            bulk_g2s(dst, src + (long long)yb * p.nx, rb, bar);
-            bulk_g2s(dst + RL, src + (long long)y0 * p.nx, ROWS * rb, bar);
-            bulk_g2s(dst + (TROWS - 1) * RL, src + (long long)yt * p.nx, rb, bar);
+        for (int f = 0; f < 4; ++f) {
+            const T *src = in + f * p.fstride + (long long)zl * plane;
+            T *dst = stage + f * TROWS * RL;
+            if (y0 >= 1 && y0 + ROWS < p.ny) {
+                bulk_g2s(dst, src + (long long)(y0 - 1) * p.nx, TROWS * rb, bar);
+            } else {
+                const int yb = y0 - 1 < 0 ? y0 - 1 + p.ny : y0 - 1;
+                const int yt = y0 + ROWS >= p.ny ? y0 + ROWS - p.ny : y0 + ROWS;
+                bulk_g2s(dst, src + (long long)yb * p.nx, rb, bar);
+                bulk_g2s(dst + RL, src + (long long)y0 * p.nx, ROWS * rb, bar);
+                bulk_g2s(dst + (TROWS - 1) * RL, src + (long long)yt * p.nx, rb, bar);
+            }
         }
     }
 }
@@ -572,7 +620,7 @@ __device__ __forceinline__ void rotate(Acc &acc) {
 // 2 = with the x faces walled (the cavity's x = 0 and x = nx-1 faces, lid elsewhere),
 // 3 = the plain scheme with BF16 / FP16 stores rounded stochastically
 template <int NH, typename T, int V>
-__global__ void __launch_bounds__(HG<NH>::NTH, 2 / NH) k_d3q19_half(const T *__restrict__ in,
+__global__ void __launch_bounds__(HG<NH>::NTH, HG<NH>::MINB) k_d3q19_half(const T *__restrict__ in,
                                                                    T *__restrict__ out, TiledParams p) {
     constexpr bool F = V == 1, XW = V == 2, SRND = V == 3;
     constexpr int XBUF = HG<NH, T>::XBUF, STAGE = HG<NH, T>::STAGE;
@@ -582,8 +630,10 @@ __global__ void __launch_bounds__(HG<NH>::NTH, 2 / NH) k_d3q19_half(const T *__r
     uint64_t *bars = reinterpret_cast<uint64_t *>(stg + 2 * STAGE);
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const int row = NH == 2 ? warp >> 1 : warp, half = NH == 2 ? (warp & 1) : 0;
-    // the thread that issues the copies: in row 1, which has no halo row to send
+    // the thread that issues the copies (NH = 0: its whole warp): in row 1, which has
+    // no halo row to send
     const bool producer = threadIdx.x == (NH == 2 ? 64 : 32);
+    const bool issuer = NH == 0 ? warp == 1 : producer;
     if ((int)blockIdx.x >= p.nitems) return;  // uniform per CTA
 
     __shared__ int failed;
@@ -595,11 +645,11 @@ __global__ void __launch_bounds__(HG<NH>::NTH, 2 / NH) k_d3q19_half(const T *__r
     }
     __syncthreads();
 
-    TaskIter it(blockIdx.x, p.nitems, gridDim.x, p.ycols, p.zc, p.nz);
+    TaskIter it(blockIdx.x, p.nitems, gridDim.x, p.ycols * p.segs, p.zc, p.nz);
     TaskIter pf = it;
     int issued = 0;
     for (int k = 0; k < 2 && pf.valid(); ++k) {
-        if (producer) issue_plane<NH, T>(in, p, pf.col, pf.pz, stg + k * STAGE, &bars[k]);
+        if (issuer) issue_plane<NH, T>(in, p, pf.col, pf.pz, stg + k * STAGE, &bars[k], lane);
         ++issued;
         pf.next();
     }
@@ -639,21 +689,23 @@ __global__ void __launch_bounds__(HG<NH>::NTH, 2 / NH) k_d3q19_half(const T *__r
             return;
         }
         if (pf.valid()) {
-            if (producer) {
+            if (issuer) {
                 asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-                issue_plane<NH, T>(in, p, pf.col, pf.pz, stg + s * STAGE, &bars[s]);
+                issue_plane<NH, T>(in, p, pf.col, pf.pz, stg + s * STAGE, &bars[s], lane);
             }
             ++issued;
             pf.next();
         }
+        // NH = 0: the item's column of rows and its segment
+        const int seg = HG<NH>::SEG ? it.col / p.ycols : 0, ycol = it.col - seg * p.ycols, x0 = seg * HALF;
         if (mode == MID) {
-            phase_b<NH, MID, SRND>(acc, xbuf, out, p, lane, row, half, it.col, it.pz > it.za ? it.pz - 1 : -1, key);
+            phase_b<NH, MID, SRND>(acc, xbuf, out, p, lane, row, half, ycol, x0, it.pz > it.za ? it.pz - 1 : -1, key);
             rotate(acc);
         } else if (mode == FIRST) {
-            phase_b<NH, FIRST, SRND>(acc, xbuf, out, p, lane, row, half, it.col, -1, key);
+            phase_b<NH, FIRST, SRND>(acc, xbuf, out, p, lane, row, half, ycol, x0, -1, key);
             rotate(acc);
         } else {
-            phase_b<NH, LAST, SRND>(acc, xbuf, out, p, lane, row, half, it.col, it.zb - 1, key);
+            phase_b<NH, LAST, SRND>(acc, xbuf, out, p, lane, row, half, ycol, x0, it.zb - 1, key);
         }
         it.next();
     }
@@ -698,6 +750,7 @@ int half_chunk_planes(int ycols, int nz, int ctas) {
 
 template <int NH, int V>
 static cudaError_t prepare_storage(int storage) {
+    if constexpr (NH == 0 && V == 2) return cudaErrorNotSupported;  // x walls: rows of 128 / 256 only
     switch (storage) {
         case STORE_F32:
             if constexpr (V == 3) return cudaErrorNotSupported;  // FP32 stores round to nearest
@@ -708,7 +761,12 @@ static cudaError_t prepare_storage(int storage) {
     return cudaErrorInvalidValue;
 }
 
-bool half_xwalls(const StepParams &p) { return p.walled[0] && p.lid_axis != 0; }
+// row geometry (the NH of HG) for a row of nx nodes: 2 (256), 1 (128), 0 (128 S, S >= 3)
+static int half_geometry(int nx) { return nx == 256 ? 2 : (nx == 128 ? 1 : 0); }
+
+bool half_xwalls(const StepParams &p) {
+    return p.walled[0] && p.lid_axis != 0 && half_geometry(p.nx) != 0;
+}
 
 // the kernel variant a step needs (-1: none serves it)
 static int half_variant(const StepParams &p) {
@@ -726,23 +784,26 @@ bool half_supported(int Q, int storage, const StepParams &p) {
     if (storage != STORE_F32 && storage != STORE_BF16 && storage != STORE_F16) return false;
     // the plain scheme, with or without a constant acceleration (Eq. force)
     if (p.gfield || p.sdelta != 0.f || p.scalar || p.bulk) return false;
-    if ((p.nx != 128 && p.nx != 256) || p.ny % ROWS != 0 || p.ny < ROWS || p.nz < 1) return false;
+    if (p.nx < 128 || p.nx % 128 != 0 || p.ny % ROWS != 0 || p.ny < ROWS || p.nz < 1) return false;
     if (p.fstride % 8 != 0 || !p.err) return false;  // 16-byte field starts for 2-byte storage
     int dev = 0;
     if (cudaGetDevice(&dev) != cudaSuccess) return false;
     const int v = half_variant(p);
     if (v < 0) return false;
     cudaError_t e;
-    if (p.nx == 256)
+    const int g = half_geometry(p.nx);
+    if (g == 2)
         e = v == 0   ? prepare_storage<2, 0>(storage)
             : v == 1 ? prepare_storage<2, 1>(storage)
             : v == 2 ? prepare_storage<2, 2>(storage)
                      : prepare_storage<2, 3>(storage);
-    else
+    else if (g == 1)
         e = v == 0   ? prepare_storage<1, 0>(storage)
             : v == 1 ? prepare_storage<1, 1>(storage)
             : v == 2 ? prepare_storage<1, 2>(storage)
                      : prepare_storage<1, 3>(storage);
+    else
+        e = v == 0 ? prepare_storage<0, 0>(storage) : v == 1 ? prepare_storage<0, 1>(storage) : prepare_storage<0, 3>(storage);
     return e == cudaSuccess;
 }
 
@@ -756,8 +817,9 @@ static cudaError_t launch_nh(const void *in, void *out, const StepParams &sp, cu
     p.ny = sp.ny;
     p.nz = sp.nz;
     p.ycols = sp.ny / ROWS;
-    p.zc = half_chunk_planes(p.ycols, sp.nz, ctas);
-    p.nitems = p.ycols * ((sp.nz + p.zc - 1) / p.zc);
+    p.segs = NH == 0 ? sp.nx / HALF : 1;
+    p.zc = half_chunk_planes(p.ycols * p.segs, sp.nz, ctas);
+    p.nitems = p.ycols * p.segs * ((sp.nz + p.zc - 1) / p.zc);
     p.fstride = sp.fstride;
     const double nu = (double)sp.s / 18.0;
     p.s18 = (float)nu;
@@ -771,16 +833,23 @@ static cudaError_t launch_nh(const void *in, void *out, const StepParams &sp, cu
     return cudaGetLastError();
 }
 
+template <int V, typename T>
+static cudaError_t launch_geometry(const void *in, void *out, const StepParams &sp, cudaStream_t st) {
+    const int g = half_geometry(sp.nx);
+    if (g == 2) return launch_nh<2, T, V>(in, out, sp, st);
+    if (g == 1) return launch_nh<1, T, V>(in, out, sp, st);
+    if constexpr (V == 2) return cudaErrorNotSupported;
+    else return launch_nh<0, T, V>(in, out, sp, st);
+}
+
 template <int V>
 static cudaError_t launch_variant(int storage, const void *in, void *out, const StepParams &sp, cudaStream_t st) {
-    const bool w = sp.nx == 256;
     switch (storage) {
         case STORE_F32:
             if constexpr (V == 3) return cudaErrorNotSupported;
-            else return w ? launch_nh<2, float, V>(in, out, sp, st) : launch_nh<1, float, V>(in, out, sp, st);
-        case STORE_BF16:
-            return w ? launch_nh<2, __nv_bfloat16, V>(in, out, sp, st) : launch_nh<1, __nv_bfloat16, V>(in, out, sp, st);
-        case STORE_F16: return w ? launch_nh<2, __half, V>(in, out, sp, st) : launch_nh<1, __half, V>(in, out, sp, st);
+            else return launch_geometry<V, float>(in, out, sp, st);
+        case STORE_BF16: return launch_geometry<V, __nv_bfloat16>(in, out, sp, st);
+        case STORE_F16: return launch_geometry<V, __half>(in, out, sp, st);
     }
     return cudaErrorInvalidValue;
 }

@@ -118,10 +118,12 @@ def test_force_field_one_step(lw, Q, shape, bc, kernel):
     sim.close()
 
 
-@pytest.mark.parametrize("shape,storage", [((3, 8, 256), 0), ((11, 24, 128), 0), ((6, 16, 256), 2)])
+@pytest.mark.parametrize("shape,storage", [((3, 8, 256), 0), ((11, 24, 128), 0), ((6, 16, 256), 2),
+                                           ((4, 16, 384), 0), ((3, 8, 512), 2)])
 def test_constant_force_on_the_half_kernel(lw, shape, storage):
     """A constant acceleration (Eq. force) on the half-row D3Q19 kernel (256- and
-    128-node rows, FP32 and FP16 storage), 60 steps against the oracle; with a force
+    128-node rows and rows of 128-node segments, FP32 and FP16 storage), 60 steps
+    against the oracle; with a force
     field instead, the generic kernel runs."""
     f = inputs.smooth_random(shape, seed=31, u_amp=0.03, d_amp=0.01)
     nz, ny, nx = shape

@@ -110,11 +110,13 @@ def test_d3q19_ragged(lw, kernel, shape):
 
 
 @pytest.mark.parametrize("shape", [(5, 8, 128), (3, 16, 256), (20, 24, 128), (1, 8, 128),
-                                   (2, 8, 256), (37, 8, 128), (300, 16, 128), (41, 24, 256)])
+                                   (2, 8, 256), (37, 8, 128), (300, 16, 128), (41, 24, 256),
+                                   (5, 8, 384), (3, 16, 512), (4, 8, 640), (17, 24, 384), (1, 8, 1024)])
 def test_d3q19_tiled_kernel(lw, shape):
     """The row-tiled D3Q19 kernel (half-row TMA kernel: two warps per 256-node row,
-    one per 128-node row; ny a multiple of 8), forced on; shapes cover runs that
-    cross columns, one plane, ragged chunks."""
+    one per 128-node row, one per 128-node segment of longer rows; ny a multiple of
+    8), forced on; shapes cover runs that cross columns, one plane, ragged chunks,
+    and rows of 3, 4, 5 and 8 segments (the first and last wrap in x)."""
     f = inputs.smooth_random(shape, seed=12, u_amp=0.05, d_amp=0.01)
     got, name = run_gpu(lw, 19, f, 0.01, 25, kernel=5)
     assert name.startswith("half")
@@ -124,7 +126,8 @@ def test_d3q19_tiled_kernel(lw, shape):
     assert eu < 1e-5 and ed < 1e-4
 
 
-WALL_SHAPES = [(5, 8, 128), (3, 16, 256), (20, 24, 128), (2, 8, 256), (11, 72, 128), (4, 8, 256), (7, 40, 256)]
+WALL_SHAPES = [(5, 8, 128), (3, 16, 256), (20, 24, 128), (2, 8, 256), (11, 72, 128), (4, 8, 256), (7, 40, 256),
+               (4, 16, 384)]
 
 
 @pytest.mark.parametrize("bc,shape", [(bc, s) for bc in (1, 2) for s in WALL_SHAPES] + [(2, (1, 16, 128))])
@@ -290,7 +293,7 @@ HALF_ULP = {2: 2.0 ** -11, 1: 2.0 ** -8}
 
 # (nx, ny, nz): the generic kernel (32^3) and the half-row kernel with 256- and
 # 128-node rows
-HALF_SHAPES = [(32, 32, 32), (256, 16, 8), (128, 24, 5)]
+HALF_SHAPES = [(32, 32, 32), (256, 16, 8), (128, 24, 5), (384, 16, 6)]
 
 
 def _tgv_box(shape):
@@ -313,6 +316,28 @@ def test_half_storage_one_step(lw, storage, shape):
         tol = 1.05 * HALF_ULP[storage] * np.abs(r) + max(2.0 ** -25 if storage == 2 else 0.0,
                                                          4 * 2.0 ** -24 * 0.02)
         assert np.all(np.abs(g - r) <= tol), (name, float(np.max(np.abs(g - r) / (np.abs(r) + 1e-30))))
+
+
+@pytest.mark.parametrize("shape", [(256, 16, 8), (384, 8, 4)])
+@pytest.mark.parametrize("storage", [2, 1])
+def test_stochastic_rounding_one_step(lw, storage, shape):
+    """Stochastic rounding on the half-row kernel (256-node rows and 128-node
+    segments): from the same rounded state one step stores, for every field, one of
+    the two storage values around the oracle's result, so it is within one storage
+    spacing of it (plus the FP32 rounding), and the rounding differs from
+    round-to-nearest on a sizeable share of the values."""
+    f = [round_storage(a, storage) for a in _tgv_box(shape)]
+    got, name = run_gpu(lw, 19, f, 0.005, 1, storage=storage, stochastic_rounding=True)
+    assert name.startswith("half")
+    rn, _ = run_gpu(lw, 19, f, 0.005, 1, storage=storage)
+    ref = oracle.step(19, *f, nu=0.005, nsteps=1)
+    differ = 0
+    for g, q, r in zip(got, rn, ref):
+        tol = 2.05 * HALF_ULP[storage] * np.abs(r) + max(2.0 ** -24 if storage == 2 else 0.0,
+                                                         4 * 2.0 ** -24 * 0.02)
+        assert np.all(np.abs(g - r) <= tol), (name, float(np.max(np.abs(g - r) / (np.abs(r) + 1e-30))))
+        differ += int(np.count_nonzero(g != q))
+    assert differ > 0.05 * sum(a.size for a in got)
 
 
 @pytest.mark.parametrize("shape", HALF_SHAPES)
