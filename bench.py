@@ -276,6 +276,21 @@ def variants(hbm):
                      "hbm_frac": bpn * g / hbm, "bytes_per_node": bpn}
         sim.close()
         torch.cuda.empty_cache()
+    # rows longer than 256: the half-row kernel on 128-node segments, and the generic kernel
+    sx, sy, sz = 384, 256, 256
+    fs = inputs.tgv3d(sx, u0=U0, ny=sy, nz=sz)
+    seg = {"shape": [sx, sy, sz], "unit": "GLUPS", "bytes_per_node": 32}
+    for label, kw in (("segments", {}), ("generic_kernel", dict(kernel=1))):
+        sim = lw.Lwacm(lw.D3Q19, sx, sy, sz, NU, **kw)
+        sim.set_fields(*fs)
+        sim.step(20)
+        ms = _events_ms(sim.stream, lambda: sim.step(300))
+        seg[label] = glups(sx * sy * sz, 300, ms)
+        seg[label + "_kernel"] = sim.kernel_name
+        sim.close()
+        torch.cuda.empty_cache()
+    seg["hbm_frac"] = 32 * seg["segments"] / hbm
+    out["d3q19_384x256x256"] = seg
 
     # batched ensemble: 256 D2Q9 domains (seed 1), 2000 steps
     doms = inputs.ensemble_2d(256, seed=1)
@@ -637,6 +652,10 @@ def run_case(name, steps):
         sim.set_fields(*inputs.tgv3d(n3, u0=U0))
         sim.set_scalar(torch.cos(2 * torch.pi * torch.arange(n3, device="cuda") / n3).expand(n3, n3, n3).contiguous())
         sim.step(steps)
+    elif name == "segments":  # D3Q19 384 x 256 x 128 Taylor-Green (half-row kernel on 128-node segments)
+        sim = lw.Lwacm(lw.D3Q19, 384, 256, 128, NU)
+        sim.set_fields(*inputs.tgv3d(384, u0=U0, ny=256, nz=128))
+        sim.step(steps)
     elif name == "bulk2d":  # D2Q9 4096^2 bulk-viscosity variant, gamma 0.4 (2D tiles 30x14)
         sim = lw.Lwacm(lw.D2Q9, 4096, 4096, 1, 0.01, bulk_gamma=0.4)
         sim.set_fields(*inputs.gtg_state(4096, 0.0))
@@ -661,7 +680,8 @@ def main():
     ap.add_argument("--cpu-steps", type=int, default=1000)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-variants", action="store_true")
-    ap.add_argument("--profile-case", choices=["adjoint", "ensemble", "cavity", "cavity3d", "bulk2d", "scalar"],
+    ap.add_argument("--profile-case", choices=["adjoint", "ensemble", "cavity", "cavity3d", "bulk2d", "scalar",
+                                               "segments"],
                     help="run one variant workload for --steps steps without timing (for profilers)")
     args = ap.parse_args()
     if args.warmup < 3:

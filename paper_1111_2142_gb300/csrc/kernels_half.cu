@@ -553,11 +553,15 @@ __device__ __forceinline__ void phase_b(Acc &acc, const float *xbuf, T *out, con
 
 // The staged rows of one plane (four fields) for an item's rows, by 1-D bulk copies
 // that complete on `bar`. NH = 1, 2: one thread issues them (the whole rows, wrapped
-// in y). NH = 0: the lanes of one warp issue one staged row each (40 rows; a
-// segment at an x end of the domain takes its wrapped 8 nodes in a second copy).
+// in y). NH = 0: 40 staged rows (a segment at an x end of the domain takes its
+// wrapped 8 nodes in a second copy), issued by lane 0 of rows 1-6, every sixth row
+// each (a bulk copy takes warp-uniform operands, so the lanes of one warp would
+// issue theirs one after another, and that warp would hold up the plane barrier);
+// row 1's thread also posts the expected bytes (the barrier's transaction count may
+// run below zero until it does).
 template <int NH, typename T>
 __device__ __forceinline__ void issue_plane(const T *in, const TiledParams &p, int col, int z, T *stage,
-                                            uint64_t *bar, int lane) {
+                                            uint64_t *bar, int warp) {
     constexpr int RL = HG<NH, T>::RL, SRL = HG<NH, T>::SRL;
     constexpr uint32_t TX = HG<NH, T>::TX;
     const int zl = z < 0 ? z + p.nz : (z >= p.nz ? z - p.nz : z);
@@ -565,9 +569,8 @@ __device__ __forceinline__ void issue_plane(const T *in, const TiledParams &p, i
     if constexpr (NH == 0) {
         const int seg = col / p.ycols, y0 = (col - seg * p.ycols) * ROWS;
         const int x0 = seg * HALF, last = p.nx / HALF - 1;
-        if (lane == 0) mbar_expect_tx(bar, TX);
-        __syncwarp();
-        for (int k = lane; k < 4 * TROWS; k += 32) {
+        if (warp == 1) mbar_expect_tx(bar, TX);
+        for (int k = warp - 1; k < 4 * TROWS; k += 6) {
             const int f = k / TROWS, r = k - f * TROWS;
             int y = y0 - 1 + r;
             y = y < 0 ? y + p.ny : (y >= p.ny ? y - p.ny : y);
@@ -630,10 +633,10 @@ __global__ void __launch_bounds__(HG<NH>::NTH, HG<NH>::MINB) k_d3q19_half(const 
     uint64_t *bars = reinterpret_cast<uint64_t *>(stg + 2 * STAGE);
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const int row = NH == 2 ? warp >> 1 : warp, half = NH == 2 ? (warp & 1) : 0;
-    // the thread that issues the copies (NH = 0: its whole warp): in row 1, which has
-    // no halo row to send
+    // the thread that issues the copies (NH = 0: lane 0 of rows 1 to 6, see
+    // issue_plane): in row 1, which has no halo row to send
     const bool producer = threadIdx.x == (NH == 2 ? 64 : 32);
-    const bool issuer = NH == 0 ? warp == 1 : producer;
+    const bool issuer = NH == 0 ? (lane == 0 && warp >= 1 && warp <= 6) : producer;
     if ((int)blockIdx.x >= p.nitems) return;  // uniform per CTA
 
     __shared__ int failed;
@@ -649,7 +652,7 @@ __global__ void __launch_bounds__(HG<NH>::NTH, HG<NH>::MINB) k_d3q19_half(const 
     TaskIter pf = it;
     int issued = 0;
     for (int k = 0; k < 2 && pf.valid(); ++k) {
-        if (issuer) issue_plane<NH, T>(in, p, pf.col, pf.pz, stg + k * STAGE, &bars[k], lane);
+        if (issuer) issue_plane<NH, T>(in, p, pf.col, pf.pz, stg + k * STAGE, &bars[k], warp);
         ++issued;
         pf.next();
     }
@@ -691,7 +694,7 @@ __global__ void __launch_bounds__(HG<NH>::NTH, HG<NH>::MINB) k_d3q19_half(const 
         if (pf.valid()) {
             if (issuer) {
                 asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-                issue_plane<NH, T>(in, p, pf.col, pf.pz, stg + s * STAGE, &bars[s], lane);
+                issue_plane<NH, T>(in, p, pf.col, pf.pz, stg + s * STAGE, &bars[s], warp);
             }
             ++issued;
             pf.next();
