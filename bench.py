@@ -444,6 +444,11 @@ def next_rows(hbm, glups):
           extra=lambda s: s.set_scalar(t3))
     # a constant acceleration (Eq. force) on the 256^3 Taylor-Green workload (half-row kernel)
     timed("forced_d3q19_256", lw.Lwacm(lw.D3Q19, n3, n3, n3, NU, force=(1e-6, 0.0, 0.0)), f3, 200, n3 ** 3, 32)
+    # omega_p on the 256^3 Taylor-Green workload: the density-term pass (reads the state,
+    # writes one FP32 field) and the half-row kernel (reads that field too): 52 B/node
+    sim = lw.Lwacm(lw.D3Q19, n3, n3, n3, NU)
+    sim.set_option(lw.OPT_NU_P, 0.05)
+    timed("nu_p_d3q19_256", sim, f3, 200, n3 ** 3, 52)
     del z3, t3
     n2 = 4096
     f2 = inputs.gtg_state(n2, 0.0)

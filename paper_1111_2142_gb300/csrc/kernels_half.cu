@@ -458,8 +458,9 @@ __device__ __forceinline__ void phase_a(Acc &acc, const T *stg, float *xbuf, con
     }
 }
 
-// SRND: BF16 / FP16 stores rounded stochastically (tile_common.cuh) with the step's key
-template <int NH, int MODE, bool SRND, typename T>
+// SRND: BF16 / FP16 stores rounded stochastically (tile_common.cuh) with the step's key;
+// NUPV: omega_p, the density adds sdelta P (P formed before the step by k_nup_sum)
+template <int NH, int MODE, bool SRND, bool NUPV, typename T>
 __device__ __forceinline__ void phase_b(Acc &acc, const float *xbuf, T *out, const TiledParams &p, int lane,
                                         int row, int half, int col, int x0, int zfin, uint32_t key) {
     constexpr int PM = 0, P0 = 1, PP = 2;
@@ -519,6 +520,11 @@ __device__ __forceinline__ void phase_b(Acc &acc, const float *xbuf, T *out, con
             const long long rowoff =
                 ((long long)zfin * p.ny + col * ROWS + row) * p.nx + x0 + half * HALF + lane * VXH;
             T *op = out + rowoff;
+            if constexpr (NUPV) {  // d+ = sum of the link values + sdelta P (as s_p in place of s)
+                const float4 pv = *reinterpret_cast<const float4 *>(p.pfield + rowoff);
+                acc[PM][0][0] = fma2(b2(p.sdelta), make_float2(pv.x, pv.y), acc[PM][0][0]);
+                acc[PM][1][0] = fma2(b2(p.sdelta), make_float2(pv.z, pv.w), acc[PM][1][0]);
+            }
             // u = j / rho, correctly rounded (tile_common.cuh, div_apply2)
             const Div2 r[2] = {div_prep2(add2(b2(1.f), acc[PM][0][0])), div_prep2(add2(b2(1.f), acc[PM][1][0]))};
             if constexpr (SRND && sizeof(T) == 2) {
@@ -621,11 +627,12 @@ __device__ __forceinline__ void rotate(Acc &acc) {
 
 // V: the variant, 0 = the plain scheme, 1 = with a constant acceleration (Eq. force),
 // 2 = with the x faces walled (the cavity's x = 0 and x = nx-1 faces, lid elsewhere),
-// 3 = the plain scheme with BF16 / FP16 stores rounded stochastically
+// 3 = the plain scheme with BF16 / FP16 stores rounded stochastically,
+// 4 = the pressure update relaxed with omega_p (periodic, no forcing)
 template <int NH, typename T, int V>
 __global__ void __launch_bounds__(HG<NH>::NTH, HG<NH>::MINB) k_d3q19_half(const T *__restrict__ in,
                                                                    T *__restrict__ out, TiledParams p) {
-    constexpr bool F = V == 1, XW = V == 2, SRND = V == 3;
+    constexpr bool F = V == 1, XW = V == 2, SRND = V == 3, NUPV = V == 4;
     constexpr int XBUF = HG<NH, T>::XBUF, STAGE = HG<NH, T>::STAGE;
     extern __shared__ float4 smem4[];
     float *xs = reinterpret_cast<float *>(smem4);
@@ -701,14 +708,24 @@ __global__ void __launch_bounds__(HG<NH>::NTH, HG<NH>::MINB) k_d3q19_half(const 
         }
         // NH = 0: the item's column of rows and its segment
         const int seg = HG<NH>::SEG ? it.col / p.ycols : 0, ycol = it.col - seg * p.ycols, x0 = seg * HALF;
+        if (NUPV && producer && mode == MID) {
+            // omega_p: the density terms of this source plane's rows are read when the
+            // plane is completed, next iteration; bring them into L2 now
+            const float *pr = p.pfield + ((long long)it.pz * p.ny + ycol * ROWS) * p.nx + x0;
+            if (HG<NH>::SEG) {
+                for (int r = 0; r < ROWS; ++r) prefetch_l2(pr + (long long)r * p.nx, HALF * 4);
+            } else {
+                prefetch_l2(pr, (uint32_t)(ROWS * HG<NH>::RL * 4));
+            }
+        }
         if (mode == MID) {
-            phase_b<NH, MID, SRND>(acc, xbuf, out, p, lane, row, half, ycol, x0, it.pz > it.za ? it.pz - 1 : -1, key);
+            phase_b<NH, MID, SRND, NUPV>(acc, xbuf, out, p, lane, row, half, ycol, x0, it.pz > it.za ? it.pz - 1 : -1, key);
             rotate(acc);
         } else if (mode == FIRST) {
-            phase_b<NH, FIRST, SRND>(acc, xbuf, out, p, lane, row, half, ycol, x0, -1, key);
+            phase_b<NH, FIRST, SRND, NUPV>(acc, xbuf, out, p, lane, row, half, ycol, x0, -1, key);
             rotate(acc);
         } else {
-            phase_b<NH, LAST, SRND>(acc, xbuf, out, p, lane, row, half, ycol, x0, it.zb - 1, key);
+            phase_b<NH, LAST, SRND, NUPV>(acc, xbuf, out, p, lane, row, half, ycol, x0, it.zb - 1, key);
         }
         it.next();
     }
@@ -773,8 +790,11 @@ bool half_xwalls(const StepParams &p) {
 
 // the kernel variant a step needs (-1: none serves it)
 static int half_variant(const StepParams &p) {
+    const bool walls = p.walled[0] || p.walled[1] || p.walled[2];
     if (p.sr_ctr)  // stochastic rounding: the plain periodic scheme only
-        return (p.walled[0] || p.walled[1] || p.walled[2] || p.has_force) ? -1 : 3;
+        return (walls || p.has_force || p.sdelta != 0.f) ? -1 : 3;
+    if (p.sdelta != 0.f)  // omega_p: periodic, no forcing, with its scratch field
+        return (walls || p.has_force || !p.nup_p || !nup_sum_supported(p)) ? -1 : 4;
     const bool xw = half_xwalls(p);
     if (p.has_force && xw) return -1;
     return xw ? 2 : (p.has_force ? 1 : 0);
@@ -786,7 +806,7 @@ bool half_supported(int Q, int storage, const StepParams &p) {
     // after it recomputes every boundary node, the only nodes with a source outside
     if (storage != STORE_F32 && storage != STORE_BF16 && storage != STORE_F16) return false;
     // the plain scheme, with or without a constant acceleration (Eq. force)
-    if (p.gfield || p.sdelta != 0.f || p.scalar || p.bulk) return false;
+    if (p.gfield || p.scalar || p.bulk) return false;
     if (p.nx < 128 || p.nx % 128 != 0 || p.ny % ROWS != 0 || p.ny < ROWS || p.nz < 1) return false;
     if (p.fstride % 8 != 0 || !p.err) return false;  // 16-byte field starts for 2-byte storage
     int dev = 0;
@@ -799,14 +819,19 @@ bool half_supported(int Q, int storage, const StepParams &p) {
         e = v == 0   ? prepare_storage<2, 0>(storage)
             : v == 1 ? prepare_storage<2, 1>(storage)
             : v == 2 ? prepare_storage<2, 2>(storage)
-                     : prepare_storage<2, 3>(storage);
+            : v == 3 ? prepare_storage<2, 3>(storage)
+                     : prepare_storage<2, 4>(storage);
     else if (g == 1)
         e = v == 0   ? prepare_storage<1, 0>(storage)
             : v == 1 ? prepare_storage<1, 1>(storage)
             : v == 2 ? prepare_storage<1, 2>(storage)
-                     : prepare_storage<1, 3>(storage);
+            : v == 3 ? prepare_storage<1, 3>(storage)
+                     : prepare_storage<1, 4>(storage);
     else
-        e = v == 0 ? prepare_storage<0, 0>(storage) : v == 1 ? prepare_storage<0, 1>(storage) : prepare_storage<0, 3>(storage);
+        e = v == 0   ? prepare_storage<0, 0>(storage)
+            : v == 1 ? prepare_storage<0, 1>(storage)
+            : v == 3 ? prepare_storage<0, 3>(storage)
+                     : prepare_storage<0, 4>(storage);
     return e == cudaSuccess;
 }
 
@@ -831,6 +856,8 @@ static cudaError_t launch_nh(const void *in, void *out, const StepParams &sp, cu
     p.err = sp.err;
     for (int c = 0; c < 3; ++c) p.g[c] = V == 1 ? sp.force[c] : 0.f;
     p.sr_ctr = V == 3 ? sp.sr_ctr : nullptr;
+    p.pfield = V == 4 ? sp.nup_p : nullptr;
+    p.sdelta = V == 4 ? sp.sdelta : 0.f;
     const int grid = ctas < p.nitems ? ctas : p.nitems;
     k_d3q19_half<NH, T, V><<<(unsigned)grid, HG<NH, T>::NTH, HG<NH, T>::BYTES, st>>>((const T *)in, (T *)out, p);
     return cudaGetLastError();
@@ -864,7 +891,8 @@ cudaError_t launch_step_half(int Q, int storage, const void *in, void *out, cons
     return v == 0   ? launch_variant<0>(storage, in, out, sp, st)
            : v == 1 ? launch_variant<1>(storage, in, out, sp, st)
            : v == 2 ? launch_variant<2>(storage, in, out, sp, st)
-                    : launch_variant<3>(storage, in, out, sp, st);
+           : v == 3 ? launch_variant<3>(storage, in, out, sp, st)
+                    : launch_variant<4>(storage, in, out, sp, st);
 }
 
 // advance the stochastic-rounding step counter (after each step's stores)

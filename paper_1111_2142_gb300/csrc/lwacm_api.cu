@@ -167,6 +167,9 @@ StepParams params(const lwacm_ctx *c) {
     p.err = c->ws ? (int *)(c->ws + c->off_err) : nullptr;
     // the stochastic-rounding step counter: the word after the error word
     p.sr_ctr = c->sr && c->ws ? (unsigned *)(c->ws + c->off_err) + 1 : nullptr;
+    // omega_p on the half-row kernel: the staging buffer (unused during steps) holds
+    // the density term k_nup_sum forms before each step
+    p.nup_p = p.sdelta != 0.f && c->ws ? (float *)(c->ws + c->off_stage) : nullptr;
     p.walled[0] = p.walled[1] = p.walled[2] = 0;
     p.lid_axis = c->D - 1;
     if (c->bc == LWACM_BC_CAVITY) {
@@ -226,7 +229,9 @@ bool choose_kernel(lwacm_ctx *c) {
     static const char *sname[7] = {"tiles2d_d2q9_30x14", "tiles2d_d2q9_30x6",  "tiles2d_d2q9_30x14", "tiles2d_d2q9_62x6",
                                    "tiles2d_d2q9_30x30", "tiles2d_d2q9_62x14", "tiles2d_d2q9_126x6"};
     if (c->kernel != 5) c->scalar_rows = false;
-    c->kname = c->kernel == 5   ? (c->scalar_rows ? "half_d3q19_tma+scalar_rows" : "half_d3q19_tma")
+    static const char *hname[2][2] = {{"half_d3q19_tma", "half_d3q19_tma+scalar_rows"},
+                                      {"half_d3q19_tma+nu_p_sum", "half_d3q19_tma+nu_p_sum+scalar_rows"}};
+    c->kname = c->kernel == 5   ? hname[p.sdelta != 0.f ? 1 : 0][c->scalar_rows ? 1 : 0]
                : c->kernel == 6 ? sname[c->batch_shape >= 0 && c->batch_shape < 7 ? c->batch_shape : 0]
                                 : gname[c->Q == 19 ? 1 : 0];
     return ok;
@@ -283,7 +288,10 @@ cudaError_t step_between(lwacm_ctx *c, const void *in, void *out, cudaStream_t s
     const StepParams p = params(c);
     StepParams pf = p;
     if (c->scalar_rows) pf.scalar = 0;  // the flow kernel leaves the scalar to its own kernel
-    cudaError_t e = c->kernel == 5   ? launch_step_half(c->Q, c->storage, in, out, pf, st)
+    cudaError_t e = cudaSuccess;
+    if (c->kernel == 5 && p.sdelta != 0.f) e = launch_nup_sum(c->storage, in, p.nup_p, p, st);
+    if (e != cudaSuccess) return e;
+    e = c->kernel == 5               ? launch_step_half(c->Q, c->storage, in, out, pf, st)
                     : c->kernel == 6 ? launch_step_tiles2d(c->Q, c->storage, c->batch_shape > 0 ? c->batch_shape : 2,
                                                            in, out, p, st)
                                      : launch_step_generic(c->Q, c->storage, in, out, p, st);

@@ -99,6 +99,7 @@ struct StepParams {
     int lid_axis;       // axis whose top wall moves with the lid velocity
     int xfaces_done;    // 1: the interior kernel applied the x-face walls (inner x-face nodes)
     unsigned *sr_ctr;   // non-null: round stores stochastically, keyed by this step counter
+    float *nup_p;       // omega_p on the half-row kernel: scratch for sum_i w_i c_i . J(x - c_i)
     int *err;           // device error word (bounded waits that gave up set it)
 };
 

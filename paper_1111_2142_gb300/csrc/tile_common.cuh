@@ -27,6 +27,8 @@ struct TiledParams {
     float a, am1;        // a = 1 - 6 nu and a - 1 = -6 nu (post_combine, lwacm_core.cuh)
     float g[3];          // constant acceleration of Eq. force (used by the forced variant)
     const unsigned *sr_ctr;  // stochastic rounding (BF16 / FP16 storage): the step counter
+    const float *pfield;     // omega_p: sum_i w_i c_i . J(x - c_i) per node (k_nup_sum)
+    float sdelta;            // omega_p: 18 (nu_p - nu)
     int *err;            // error word (timeout)
 };
 
@@ -57,6 +59,10 @@ __device__ __forceinline__ bool mbar_wait(uint64_t *bar, uint32_t parity) {
         if (it > 32) __nanosleep(100);
     }
     return false;
+}
+// bring `bytes` (a multiple of 16, 16-byte aligned) of global memory into L2
+__device__ __forceinline__ void prefetch_l2(const void *src, uint32_t bytes) {
+    asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(src), "r"(bytes) : "memory");
 }
 __device__ __forceinline__ void bulk_g2s(void *dst, const void *src, uint32_t bytes, uint64_t *bar) {
     asm volatile(

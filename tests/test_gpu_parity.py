@@ -534,7 +534,9 @@ def test_full_size_256_thousand_steps(lw, storage):
 def test_nu_p_matches_oracle(lw, Q, shape, kernel):
     """omega_p (LWACM_OPT_NU_P): the density sums link values built with 18 nu_p,
     the momentum with 18 nu; on the generic kernel (1) and on the automatic choice
-    (0: the 2D-tile kernel for D2Q9, the generic kernel for D3Q19)."""
+    (0: the 2D-tile kernel for D2Q9; for D3Q19 the half-row kernel with the density
+    term summed before the step when nx is a multiple of 128, else the generic
+    kernel)."""
     f = inputs.smooth_random(shape, seed=17, u_amp=0.05, d_amp=0.01)
     nz = 1 if Q == 9 else shape[0]
     ny, nx = shape[-2], shape[-1]
@@ -542,7 +544,8 @@ def test_nu_p_matches_oracle(lw, Q, shape, kernel):
     sim.set_option(lw.OPT_NU_P, 0.12)
     if kernel:
         sim.set_option(lw.OPT_KERNEL, kernel)
-    assert sim.kernel_name.startswith("tiles2d" if (Q == 9 and kernel == 0) else "generic"), sim.kernel_name
+    want = "generic" if kernel else ("tiles2d" if Q == 9 else ("half" if shape[-1] % 128 == 0 else "generic"))
+    assert sim.kernel_name.startswith(want), sim.kernel_name
     sim.set_fields(*f)
     sim.step(40)
     got = sim.get_fields()
@@ -551,6 +554,37 @@ def test_nu_p_matches_oracle(lw, Q, shape, kernel):
     eu, ed = errs(got, ref, 0.05)
     print(f"nu_p Q{Q} {shape}: du/U={eu:.2e} dd/d={ed:.2e}")
     assert eu < 1e-5 and ed < 1e-4
+
+
+@pytest.mark.parametrize("shape,storage", [((6, 16, 256), 0), ((5, 8, 128), 0), ((4, 8, 384), 0),
+                                           ((1, 8, 256), 0), ((3, 16, 256), 2), ((4, 8, 384), 1)])
+def test_nu_p_on_the_half_kernel(lw, shape, storage):
+    """omega_p on D3Q19 with nx a multiple of 128: the density term
+    sdelta sum_i w_i c_i . J(x - c_i) is summed from the state before the step and
+    the half-row kernel adds it to each node's density. FP32: 40 steps against the
+    oracle; FP16 / BF16 storage: one step from a rounded state within half a storage
+    ulp (plus the FP32 rounding)."""
+    nz, ny, nx = shape
+    f = inputs.smooth_random(shape, seed=21, u_amp=0.05, d_amp=0.01)
+    if storage:
+        f = [round_storage(a, storage) for a in f]
+    sim = lw.Lwacm(19, nx, ny, nz, 0.01, storage=storage)
+    sim.set_option(lw.OPT_NU_P, 0.12)
+    assert sim.kernel_name.startswith("half") and "nu_p" in sim.kernel_name, sim.kernel_name
+    T = 40 if storage == 0 else 1
+    sim.set_fields(*f)
+    sim.step(T)
+    got = sim.get_fields()
+    sim.close()
+    ref = oracle.step_nu_p(19, *f, nu=0.01, nu_p=0.12, nsteps=T)
+    if storage == 0:
+        eu, ed = errs(got, ref, 0.05)
+        print(f"nu_p half kernel {shape}: du/U={eu:.2e} dd/d={ed:.2e}")
+        assert eu < 1e-5 and ed < 1e-4
+    else:
+        for g, r in zip(got, ref):
+            tol = 1.05 * HALF_ULP[storage] * np.abs(r) + max(2.0 ** -25 if storage == 2 else 0.0, 8 * 2.0 ** -24 * 0.05)
+            assert np.all(np.abs(g - r) <= tol), float(np.max(np.abs(g - r) / (np.abs(r) + 1e-30)))
 
 
 @pytest.mark.parametrize("tile", [1, 2, 3, 4, 5, 6])
