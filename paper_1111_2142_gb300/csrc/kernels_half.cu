@@ -1,8 +1,10 @@
 // Half-row TMA row-tiled D3Q19 kernel, for domains with nx = 256, 128 or any larger
-// multiple of 128 and ny a multiple of 8 (periodic; walled domains get the wall pass
-// after it, the cavity's x faces handled here for rows of 128 and 256): the moment
-// form of Eq. ACM2.0 (see lwacm_core.cuh), every field read from HBM once and
-// written once per step.
+// multiple of 128 and any ny (periodic; walled domains get the wall pass after it,
+// the cavity's x faces handled here for rows of 128 and 256): the moment form of
+// Eq. ACM2.0 (see lwacm_core.cuh), every field read from HBM once and written once
+// per step. A CTA updates columns of 8 rows; when ny % 8 != 0 the last column's
+// rows beyond ny hold the rows that follow it periodically, so its first such row
+// feeds the last real row from above as a halo row would, and none of them is stored.
 //
 // Persistent CTAs over chunk-major (y-column, z-chunk) items, TMA bulk copies of
 // ten staged rows per plane, packed row exchange through shared memory, three
@@ -35,6 +37,7 @@ using namespace tile;
 
 constexpr int VXH = 4;                 // nodes per lane
 constexpr int HALF = 128;              // nodes per warp row segment
+constexpr int HALF_ROWS = 8;           // rows per column of the 256-node-row form
 
 // Row geometry. NH = 1: one warp per row of nx = 128 nodes, its lanes wrap
 // periodically by themselves; NH = 2: two warps (halves) per row of 256, see above;
@@ -45,14 +48,16 @@ constexpr int HALF = 128;              // nodes per warp row segment
 template <int NH>
 struct HGeo {
     static constexpr bool SEG = NH == 0;
+    static constexpr int RW = NH == 2 ? HALF_ROWS : ROWS;  // rows of a column (a CTA's work item)
+    static constexpr int TRW = RW + 2;              // staged rows: y0-1, y0 .. y0+RW-1, y0+RW
     static constexpr int NW = NH == 2 ? 2 : 1;      // warps per row (or segment)
-    static constexpr int NTH = ROWS * NW * 32;      // threads per CTA
-    static constexpr int MINB = NH == 2 ? 1 : 2;    // CTAs per SM
+    static constexpr int NTH = RW * NW * 32;        // threads per CTA
+    static constexpr int MINB = NH == 2 && RW == 8 ? 1 : 2;  // CTAs per SM
     static constexpr int RL = HALF * NW;            // nodes of a row a CTA updates
     static constexpr int SRL = SEG ? HALF + 16 : RL;  // staged row length
     static constexpr int OWN = SEG ? 8 : 0;         // staged index of the first own node
     static constexpr bool NB = NH != 1;             // boundary lanes read their outside neighbours
-    static constexpr int XSLOT = ROWS * RL;
+    static constexpr int XSLOT = RW * RL;
     static constexpr int XDIR = NSLOT * XSLOT;
     static constexpr int XBUF = 2 * XDIR;  // floats
     // staged indices of the neighbours lane 0 (left) and lane 31 (right) of half h take
@@ -62,7 +67,7 @@ struct HGeo {
 // T: storage type of the fields (FP32, or BF16 / FP16 widened to FP32 on load).
 template <int NH, typename T = float>
 struct HG : HGeo<NH> {
-    static constexpr int STAGE = 4 * TROWS * HGeo<NH>::SRL;  // elements of T
+    static constexpr int STAGE = 4 * HGeo<NH>::TRW * HGeo<NH>::SRL;  // elements of T
     static constexpr size_t BYTES = 2 * (size_t)HGeo<NH>::XBUF * 4 + 2 * (size_t)STAGE * sizeof(T) + 64;
     static constexpr uint32_t TX = STAGE * sizeof(T);
 };
@@ -338,12 +343,12 @@ __device__ __forceinline__ void phase_a(Acc &acc, const T *stg, float *xbuf, con
     float *up = xbuf + half * HALF, *dn = xbuf + XDIR + half * HALF;
     {
         NC2 nc;
-        node_consts2(nc, stg + (row + 1) * SRL + OWN + half * HALF, TROWS * SRL, lane, p.s18, p.a, p.am1);
+        node_consts2(nc, stg + (row + 1) * SRL + OWN + half * HALF, HGeo<NH>::TRW * SRL, lane, p.s18, p.a, p.am1);
         // the boundary neighbour's constants (NB; unused for NH = 1)
         const int nbx = lane < 16 ? HG<NH>::left(half) : HG<NH>::right(half);
         const float sgn = lane < 16 ? 1.f : -1.f;
         NbC nb{};
-        if (NB) nb = nb_consts(stg + (row + 1) * SRL, TROWS * SRL, nbx, sgn, p.s18);
+        if (NB) nb = nb_consts(stg + (row + 1) * SRL, HGeo<NH>::TRW * SRL, nbx, sgn, p.s18);
 #pragma unroll
         for (int j = 0; j < 2; ++j) {
             F2 gp, gm;
@@ -437,24 +442,25 @@ __device__ __forceinline__ void phase_a(Acc &acc, const T *stg, float *xbuf, con
         }
         const float nb1 = NB && MODE == MID ? nb_val(nb.K2, nb.sA2, nb.B2, nb.U + nb.V) : 0.f;
         const float nb2 = NB && MODE == MID ? nb_val(nb.K2, -nb.sA2, nb.B2, nb.V - nb.U) : 0.f;
-        send_rows<NH, MODE, XW>(nc, up + (row + 1) * RL, dn + (row - 1) * RL, row + 1 < ROWS, row > 0, nb1, nb2, lane,
+        send_rows<NH, MODE, XW>(nc, up + (row + 1) * RL, dn + (row - 1) * RL, row + 1 < HGeo<NH>::RW, row > 0, nb1, nb2, lane,
                                 w0, wN, e0, eN, MODE == MID ? acc[P0] : nullptr);
     }
-    if (row == 0 || row == ROWS - 1) {  // halo rows: y0-1 (staged row 0) feeds row 0, y0+8 (staged 9) row 7
-        const int sr = row == 0 ? 0 : TROWS - 1;
+    // halo rows: y0-1 (staged row 0) feeds row 0, y0+RW (staged RW+1) row RW-1
+    if (row == 0 || row == HGeo<NH>::RW - 1) {
+        const int sr = row == 0 ? 0 : HGeo<NH>::TRW - 1;
         NC2 hc;
-        node_consts2(hc, stg + sr * SRL + OWN + half * HALF, TROWS * SRL, lane, p.s18);
+        node_consts2(hc, stg + sr * SRL + OWN + half * HALF, HGeo<NH>::TRW * SRL, lane, p.s18);
         float nb1 = 0.f, nb2 = 0.f;
         if (NB && MODE == MID) {
             const int nbx = lane < 16 ? HG<NH>::left(half) : HG<NH>::right(half);
-            const NbC hb = nb_consts(stg + sr * SRL, TROWS * SRL, nbx, lane < 16 ? 1.f : -1.f, p.s18);
+            const NbC hb = nb_consts(stg + sr * SRL, HGeo<NH>::TRW * SRL, nbx, lane < 16 ? 1.f : -1.f, p.s18);
             nb1 = nb_val(hb.K2, hb.sA2, hb.B2, hb.U + hb.V);
             nb2 = nb_val(hb.K2, -hb.sA2, hb.B2, hb.V - hb.U);
         }
         if (row == 0)
             send_rows<NH, MODE, XW>(hc, up, nullptr, true, false, nb1, nb2, lane, w0, wN, e0, eN);
         else
-            send_rows<NH, MODE, XW>(hc, nullptr, dn + (ROWS - 1) * RL, false, true, nb1, nb2, lane, w0, wN, e0, eN);
+            send_rows<NH, MODE, XW>(hc, nullptr, dn + (HGeo<NH>::RW - 1) * RL, false, true, nb1, nb2, lane, w0, wN, e0, eN);
     }
 }
 
@@ -516,9 +522,11 @@ __device__ __forceinline__ void phase_b(Acc &acc, const float *xbuf, T *out, con
             acc[PM][j][2] = sub2(acc[PM][j][2], o[j]);
             acc[PM][j][3] = sub2(acc[PM][j][3], o[j]);
         }
-        if (zfin >= 0) {
+        // a short last column's rows beyond ny (they carry the wrapped rows that feed
+        // its last row from above, like a halo row) are not stored
+        if (zfin >= 0 && col * HGeo<NH>::RW + row < p.ny) {
             const long long rowoff =
-                ((long long)zfin * p.ny + col * ROWS + row) * p.nx + x0 + half * HALF + lane * VXH;
+                ((long long)zfin * p.ny + col * HGeo<NH>::RW + row) * p.nx + x0 + half * HALF + lane * VXH;
             T *op = out + rowoff;
             if constexpr (NUPV) {  // d+ = sum of the link values + sdelta P (as s_p in place of s)
                 const float4 pv = *reinterpret_cast<const float4 *>(p.pfield + rowoff);
@@ -573,15 +581,14 @@ __device__ __forceinline__ void issue_plane(const T *in, const TiledParams &p, i
     const int zl = z < 0 ? z + p.nz : (z >= p.nz ? z - p.nz : z);
     const long long plane = (long long)p.nx * p.ny;
     if constexpr (NH == 0) {
-        const int seg = col / p.ycols, y0 = (col - seg * p.ycols) * ROWS;
+        const int seg = col / p.ycols, y0 = (col - seg * p.ycols) * HGeo<NH>::RW;
         const int x0 = seg * HALF, last = p.nx / HALF - 1;
         if (warp == 1) mbar_expect_tx(bar, TX);
-        for (int k = warp - 1; k < 4 * TROWS; k += 6) {
-            const int f = k / TROWS, r = k - f * TROWS;
-            int y = y0 - 1 + r;
-            y = y < 0 ? y + p.ny : (y >= p.ny ? y - p.ny : y);
+        for (int k = warp - 1; k < 4 * HGeo<NH>::TRW; k += 6) {
+            const int f = k / HGeo<NH>::TRW, r = k - f * HGeo<NH>::TRW;
+            const int y = (y0 - 1 + r + p.ny) % p.ny;  // a remainder: rows of a short last column wrap
             const T *src = in + f * p.fstride + (long long)zl * plane + (long long)y * p.nx;
-            T *dst = stage + (f * TROWS + r) * SRL;
+            T *dst = stage + (f * HGeo<NH>::TRW + r) * SRL;
             if (seg == 0) {
                 bulk_g2s(dst, src + p.nx - 8, 8 * sizeof(T), bar);
                 bulk_g2s(dst + 8, src, (HALF + 8) * sizeof(T), bar);
@@ -593,21 +600,31 @@ __device__ __forceinline__ void issue_plane(const T *in, const TiledParams &p, i
             }
         }
     } else {
-        const int y0 = col * ROWS;
+        const int y0 = col * HGeo<NH>::RW;
         mbar_expect_tx(bar, TX);
         const uint32_t rb = (uint32_t)(RL * sizeof(T));
 #pragma unroll
         for (int f = 0; f < 4; ++f) {
             const T *src = in + f * p.fstride + (long long)zl * plane;
-            T *dst = stage + f * TROWS * RL;
-            if (y0 >= 1 && y0 + ROWS < p.ny) {
-                bulk_g2s(dst, src + (long long)(y0 - 1) * p.nx, TROWS * rb, bar);
-            } else {
+            T *dst = stage + f * HGeo<NH>::TRW * RL;
+            if (y0 >= 1 && y0 + HGeo<NH>::RW < p.ny) {
+                bulk_g2s(dst, src + (long long)(y0 - 1) * p.nx, HGeo<NH>::TRW * rb, bar);
+            } else if (y0 + HGeo<NH>::RW <= p.ny) {
                 const int yb = y0 - 1 < 0 ? y0 - 1 + p.ny : y0 - 1;
-                const int yt = y0 + ROWS >= p.ny ? y0 + ROWS - p.ny : y0 + ROWS;
+                const int yt = y0 + HGeo<NH>::RW >= p.ny ? y0 + HGeo<NH>::RW - p.ny : y0 + HGeo<NH>::RW;
                 bulk_g2s(dst, src + (long long)yb * p.nx, rb, bar);
-                bulk_g2s(dst + RL, src + (long long)y0 * p.nx, ROWS * rb, bar);
-                bulk_g2s(dst + (TROWS - 1) * RL, src + (long long)yt * p.nx, rb, bar);
+                bulk_g2s(dst + RL, src + (long long)y0 * p.nx, HGeo<NH>::RW * rb, bar);
+                bulk_g2s(dst + (HGeo<NH>::TRW - 1) * RL, src + (long long)yt * p.nx, rb, bar);
+            } else if (p.ny >= HGeo<NH>::TRW) {
+                // a short last column (ny % 8 != 0; y0 >= 8): row y0 - 1, its R rows up
+                // to ny - 1, then the rows from y = 0 that follow them periodically
+                const int R = p.ny - y0;
+                bulk_g2s(dst, src + (long long)(y0 - 1) * p.nx, rb, bar);
+                bulk_g2s(dst + RL, src + (long long)y0 * p.nx, (uint32_t)R * rb, bar);
+                bulk_g2s(dst + (R + 1) * RL, src, (uint32_t)(HGeo<NH>::TRW - 1 - R) * rb, bar);
+            } else {  // fewer than 10 rows in all: each staged row by itself, wrapped
+                for (int r = 0; r < HGeo<NH>::TRW; ++r)
+                    bulk_g2s(dst + r * RL, src + (long long)((y0 - 1 + r + p.ny) % p.ny) * p.nx, rb, bar);
             }
         }
     }
@@ -711,11 +728,11 @@ __global__ void __launch_bounds__(HG<NH>::NTH, HG<NH>::MINB) k_d3q19_half(const 
         if (NUPV && producer && mode == MID) {
             // omega_p: the density terms of this source plane's rows are read when the
             // plane is completed, next iteration; bring them into L2 now
-            const float *pr = p.pfield + ((long long)it.pz * p.ny + ycol * ROWS) * p.nx + x0;
+            const float *pr = p.pfield + ((long long)it.pz * p.ny + ycol * HGeo<NH>::RW) * p.nx + x0;
             if (HG<NH>::SEG) {
-                for (int r = 0; r < ROWS; ++r) prefetch_l2(pr + (long long)r * p.nx, HALF * 4);
+                for (int r = 0; r < HGeo<NH>::RW; ++r) prefetch_l2(pr + (long long)r * p.nx, HALF * 4);
             } else {
-                prefetch_l2(pr, (uint32_t)(ROWS * HG<NH>::RL * 4));
+                prefetch_l2(pr, (uint32_t)(HGeo<NH>::RW * HG<NH>::RL * 4));
             }
         }
         if (mode == MID) {
@@ -807,7 +824,7 @@ bool half_supported(int Q, int storage, const StepParams &p) {
     if (storage != STORE_F32 && storage != STORE_BF16 && storage != STORE_F16) return false;
     // the plain scheme, with or without a constant acceleration (Eq. force)
     if (p.gfield || p.scalar || p.bulk) return false;
-    if (p.nx < 128 || p.nx % 128 != 0 || p.ny % ROWS != 0 || p.ny < ROWS || p.nz < 1) return false;
+    if (p.nx < 128 || p.nx % 128 != 0 || p.ny < 1 || p.nz < 1) return false;
     if (p.fstride % 8 != 0 || !p.err) return false;  // 16-byte field starts for 2-byte storage
     int dev = 0;
     if (cudaGetDevice(&dev) != cudaSuccess) return false;
@@ -844,7 +861,7 @@ static cudaError_t launch_nh(const void *in, void *out, const StepParams &sp, cu
     p.nx = sp.nx;
     p.ny = sp.ny;
     p.nz = sp.nz;
-    p.ycols = sp.ny / ROWS;
+    p.ycols = (sp.ny + HGeo<NH>::RW - 1) / HGeo<NH>::RW;
     p.segs = NH == 0 ? sp.nx / HALF : 1;
     p.zc = half_chunk_planes(p.ycols * p.segs, sp.nz, ctas);
     p.nitems = p.ycols * p.segs * ((sp.nz + p.zc - 1) / p.zc);

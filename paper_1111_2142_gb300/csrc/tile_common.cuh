@@ -19,7 +19,7 @@ constexpr unsigned FULL = 0xffffffffu;
 
 struct TiledParams {
     int nx, ny, nz;
-    int ycols;           // ny / ROWS
+    int ycols;           // columns of ROWS rows: ceil(ny / ROWS)
     int segs;            // 128-node segments per row a CTA item covers one of (1: the whole row)
     int zc, nitems;      // planes per chunk, ycols * ceil(nz / zc)
     long long fstride;
