@@ -90,8 +90,10 @@ enum {
     LWACM_OPT_KERNEL = 9,  /* interior kernel: 0 = automatic choice (default),
                               1 = generic gather kernel, 5 = D3Q19 half-row TMA kernel
                               (needs the plain scheme, with or without a constant
-                              acceleration but not a force field, nx a multiple of 128
-                              and any ny, and runs walled domains with the wall pass
+                              acceleration but not a force field, nx = 128, 256 or
+                              nx >= 136 a multiple of 4 (8 for BF16 / FP16 storage)
+                              with nx % 128 == 0 or >= 8, any ny, and runs walled
+                              domains with the wall pass
                               after it; FP32, BF16 and FP16 storage: LWACM_E_UNSUPPORTED
                               otherwise); 2 and 3 (earlier row-tiled kernels, superseded
                               by 5) are retired: LWACM_E_ARG; 6 = D2Q9 2D-tile kernel (any boundary, walls
@@ -175,8 +177,8 @@ enum {
                                      kept in the workspace), so that stored values are
                                      unbiased and a per-step change below half a storage
                                      ulp is not lost. Single periodic D3Q19 domains with
-                                     BF16 / FP16 storage on the half-row kernel (nx a
-                                     multiple of 128), plain scheme only (no forcing,
+                                     BF16 / FP16 storage on the half-row kernel (nx as
+                                     for LWACM_OPT_KERNEL 5), plain scheme only (no forcing,
                                      nu_p, scalar, bulk variant or semi-implicit update);
                                      otherwise LWACM_E_UNSUPPORTED, at set_option, bind
                                      or step. Runs are reproducible: the counter starts at

@@ -41,10 +41,11 @@ constexpr int HALF_ROWS = 8;           // rows per column of the 256-node-row fo
 
 // Row geometry. NH = 1: one warp per row of nx = 128 nodes, its lanes wrap
 // periodically by themselves; NH = 2: two warps (halves) per row of 256, see above;
-// NH = 0: rows of nx = 128 S nodes (S >= 3) cut into S segments of 128, one warp per
-// segment and a CTA per (segment, column of rows): the staged rows carry 8 more
+// NH = 0: other rows (nx >= 136) cut into ceil(nx / 128) segments of 128, one warp
+// per segment and a CTA per (segment, column of rows): the staged rows carry 8 more
 // nodes on each side (x0 - 8 .. x0 + 135, wrapped), and the boundary lanes take
-// their outside neighbours from them as the halves do.
+// their outside neighbours from them as the halves do. A short last segment stages
+// the row's first nodes after its end, and its lanes there store nothing.
 template <int NH>
 struct HGeo {
     static constexpr bool SEG = NH == 0;
@@ -523,8 +524,9 @@ __device__ __forceinline__ void phase_b(Acc &acc, const float *xbuf, T *out, con
             acc[PM][j][3] = sub2(acc[PM][j][3], o[j]);
         }
         // a short last column's rows beyond ny (they carry the wrapped rows that feed
-        // its last row from above, like a halo row) are not stored
-        if (zfin >= 0 && col * HGeo<NH>::RW + row < p.ny) {
+        // its last row from above, like a halo row) are not stored, nor the nodes of a
+        // short last segment beyond nx (they carry the row's first nodes, likewise)
+        if (zfin >= 0 && col * HGeo<NH>::RW + row < p.ny && x0 + half * HALF + lane * VXH < p.nx) {
             const long long rowoff =
                 ((long long)zfin * p.ny + col * HGeo<NH>::RW + row) * p.nx + x0 + half * HALF + lane * VXH;
             T *op = out + rowoff;
@@ -582,7 +584,8 @@ __device__ __forceinline__ void issue_plane(const T *in, const TiledParams &p, i
     const long long plane = (long long)p.nx * p.ny;
     if constexpr (NH == 0) {
         const int seg = col / p.ycols, y0 = (col - seg * p.ycols) * HGeo<NH>::RW;
-        const int x0 = seg * HALF, last = p.nx / HALF - 1;
+        const int x0 = seg * HALF, last = p.segs - 1;
+        const int rn = p.nx - x0;  // nodes of this segment up to the row's end (the last may be short)
         if (warp == 1) mbar_expect_tx(bar, TX);
         for (int k = warp - 1; k < 4 * HGeo<NH>::TRW; k += 6) {
             const int f = k / HGeo<NH>::TRW, r = k - f * HGeo<NH>::TRW;
@@ -592,9 +595,9 @@ __device__ __forceinline__ void issue_plane(const T *in, const TiledParams &p, i
             if (seg == 0) {
                 bulk_g2s(dst, src + p.nx - 8, 8 * sizeof(T), bar);
                 bulk_g2s(dst + 8, src, (HALF + 8) * sizeof(T), bar);
-            } else if (seg == last) {
-                bulk_g2s(dst, src + x0 - 8, (HALF + 8) * sizeof(T), bar);
-                bulk_g2s(dst + HALF + 8, src, 8 * sizeof(T), bar);
+            } else if (seg == last) {  // to the row's end, then the row's start (wrapped)
+                bulk_g2s(dst, src + x0 - 8, (uint32_t)(rn + 8) * sizeof(T), bar);
+                bulk_g2s(dst + rn + 8, src, (uint32_t)(HALF + 8 - rn) * sizeof(T), bar);
             } else {
                 bulk_g2s(dst, src + x0 - 8, SRL * sizeof(T), bar);
             }
@@ -730,7 +733,8 @@ __global__ void __launch_bounds__(HG<NH>::NTH, HG<NH>::MINB) k_d3q19_half(const 
             // plane is completed, next iteration; bring them into L2 now
             const float *pr = p.pfield + ((long long)it.pz * p.ny + ycol * HGeo<NH>::RW) * p.nx + x0;
             if (HG<NH>::SEG) {
-                for (int r = 0; r < HGeo<NH>::RW; ++r) prefetch_l2(pr + (long long)r * p.nx, HALF * 4);
+                const int rn = p.nx - x0 < HALF ? p.nx - x0 : HALF;
+                for (int r = 0; r < HGeo<NH>::RW; ++r) prefetch_l2(pr + (long long)r * p.nx, (uint32_t)rn * 4);
             } else {
                 prefetch_l2(pr, (uint32_t)(HGeo<NH>::RW * HG<NH>::RL * 4));
             }
@@ -801,6 +805,14 @@ static cudaError_t prepare_storage(int storage) {
 // row geometry (the NH of HG) for a row of nx nodes: 2 (256), 1 (128), 0 (128 S, S >= 3)
 static int half_geometry(int nx) { return nx == 256 ? 2 : (nx == 128 ? 1 : 0); }
 
+// rows the segment form takes: at least 136 nodes (segment 0 stages 136 from the row's
+// start), a last segment of at least 8 nodes (the one before it stages 8 past its
+// end), and 16-byte row starts and copy sizes (nx a multiple of 16 bytes' worth)
+static bool segments_fit(int nx, int storage) {
+    const int q = storage == STORE_F32 ? 4 : 8;
+    return nx >= 136 && nx % q == 0 && (nx % HALF == 0 || nx % HALF >= 8);
+}
+
 bool half_xwalls(const StepParams &p) {
     return p.walled[0] && p.lid_axis != 0 && half_geometry(p.nx) != 0;
 }
@@ -824,7 +836,8 @@ bool half_supported(int Q, int storage, const StepParams &p) {
     if (storage != STORE_F32 && storage != STORE_BF16 && storage != STORE_F16) return false;
     // the plain scheme, with or without a constant acceleration (Eq. force)
     if (p.gfield || p.scalar || p.bulk) return false;
-    if (p.nx < 128 || p.nx % 128 != 0 || p.ny < 1 || p.nz < 1) return false;
+    if (p.ny < 1 || p.nz < 1) return false;
+    if (half_geometry(p.nx) == 0 && !segments_fit(p.nx, storage)) return false;
     if (p.fstride % 8 != 0 || !p.err) return false;  // 16-byte field starts for 2-byte storage
     int dev = 0;
     if (cudaGetDevice(&dev) != cudaSuccess) return false;
@@ -862,7 +875,7 @@ static cudaError_t launch_nh(const void *in, void *out, const StepParams &sp, cu
     p.ny = sp.ny;
     p.nz = sp.nz;
     p.ycols = (sp.ny + HGeo<NH>::RW - 1) / HGeo<NH>::RW;
-    p.segs = NH == 0 ? sp.nx / HALF : 1;
+    p.segs = NH == 0 ? (sp.nx + HALF - 1) / HALF : 1;
     p.zc = half_chunk_planes(p.ycols * p.segs, sp.nz, ctas);
     p.nitems = p.ycols * p.segs * ((sp.nz + p.zc - 1) / p.zc);
     p.fstride = sp.fstride;

@@ -14,8 +14,8 @@
 // P(x) = sum_a [S_a(x - e_a) - S_a(x + e_a)]. A block marches a 32 x 16 tile of an
 // x-y plane along z, J of three planes (tile plus a one-node frame, wrapped
 // periodically) in shared memory (four plane slots, one barrier per plane), the
-// loads of the plane after next in flight; the
-// rows of a last tile beyond ny are summed from wrapped rows and not stored.
+// loads of the plane after next in flight; the nodes of a last tile beyond nx or ny
+// are summed from wrapped ones and not stored.
 #include <stdint.h>
 
 #include "launch.h"
@@ -107,7 +107,7 @@ __global__ void __launch_bounds__(NTHR) k_nup_sum(const T *__restrict__ in, floa
                     J[s][2][cy + 1][cx]) * k36;
         };
         const float P = ((sx(cx - 1) - sx(cx + 1)) + (sy(cy - 1) - sy(cy + 1))) + (sz(sm) - sz(sp));
-        if (y0 + ty < p.ny) pf[(long long)z * plane + (long long)(y0 + ty) * p.nx + x0 + tx] = P;
+        if (y0 + ty < p.ny && x0 + tx < p.nx) pf[(long long)z * plane + (long long)(y0 + ty) * p.nx + x0 + tx] = P;
         __syncthreads();  // plane z + 2 is complete; slot sm is written next
         const int t = sm;
         sm = s0;
@@ -119,7 +119,8 @@ __global__ void __launch_bounds__(NTHR) k_nup_sum(const T *__restrict__ in, floa
 
 template <typename T>
 cudaError_t launch_t(const void *in, float *pf, const StepParams &p, cudaStream_t st) {
-    const int tiles_x = p.nx / NX_T, tiles_y = (p.ny + NY_T - 1) / NY_T;  // the last tile may be ragged in y
+    // the last tiles may be short in x and y
+    const int tiles_x = (p.nx + NX_T - 1) / NX_T, tiles_y = (p.ny + NY_T - 1) / NY_T;
     const long long tiles = (long long)tiles_x * tiles_y;
     const int zc = 32;  // planes per block (64 measured slower: fewer blocks in flight)
     const long long blocks = tiles * ((p.nz + zc - 1) / zc);
@@ -130,7 +131,7 @@ cudaError_t launch_t(const void *in, float *pf, const StepParams &p, cudaStream_
 
 }  // namespace
 
-bool nup_sum_supported(const StepParams &p) { return p.nx % NX_T == 0 && p.ny >= 1 && p.nz >= 1; }
+bool nup_sum_supported(const StepParams &p) { return p.nx >= 1 && p.ny >= 1 && p.nz >= 1; }
 static_assert(FX * FY <= PER * NTHR, "every frame node has a thread");
 
 cudaError_t launch_nup_sum(int storage, const void *in, float *pf, const StepParams &p, cudaStream_t st) {

@@ -103,7 +103,7 @@ cudaError_t launch_scalar_rows(const void *in, void *out, const StepParams &p, c
 // leaves the inner x-face nodes alone)
 bool half_xwalls(const StepParams &p);
 // omega_p on the half-row kernel: P(x) = sum_i w_i c_i . J(x - c_i) of the state `in`
-// (FP32, one value per node) into pf, before the step (nx % 32 == 0)
+// (FP32, one value per node) into pf, before the step
 bool nup_sum_supported(const StepParams &p);
 cudaError_t launch_nup_sum(int storage, const void *in, float *pf, const StepParams &p, cudaStream_t st);
 // stochastic rounding: advance the step counter the next step's random key is drawn from

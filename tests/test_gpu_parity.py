@@ -112,13 +112,15 @@ def test_d3q19_ragged(lw, kernel, shape):
 @pytest.mark.parametrize("shape", [(5, 8, 128), (3, 16, 256), (20, 24, 128), (1, 8, 128),
                                    (2, 8, 256), (37, 8, 128), (300, 16, 128), (41, 24, 256),
                                    (5, 8, 384), (3, 16, 512), (4, 8, 640), (17, 24, 384), (1, 8, 1024),
-                                   (5, 12, 128), (3, 20, 256), (4, 3, 384), (2, 1, 128), (6, 30, 256), (3, 7, 256)])
+                                   (5, 12, 128), (3, 20, 256), (4, 3, 384), (2, 1, 128), (6, 30, 256), (3, 7, 256),
+                                   (4, 8, 200), (3, 13, 300), (2, 8, 392), (5, 16, 136), (3, 9, 524)])
 def test_d3q19_tiled_kernel(lw, shape):
     """The row-tiled D3Q19 kernel (half-row TMA kernel: two warps per 256-node row,
     one per 128-node row, one per 128-node segment of longer rows), forced on;
     shapes cover runs that cross columns, one plane, ragged chunks, rows of 3, 4, 5
-    and 8 segments (the first and last wrap in x), and ny not a multiple of 8 (a
-    short last column; ny = 1, 3 and 7: fewer rows than one column)."""
+    and 8 segments (the first and last wrap in x), ny not a multiple of 8 (a short
+    last column; ny = 1, 3 and 7: fewer rows than one column), and nx not a multiple
+    of 128 (a short last segment of 8 to 72 nodes)."""
     f = inputs.smooth_random(shape, seed=12, u_amp=0.05, d_amp=0.01)
     got, name = run_gpu(lw, 19, f, 0.01, 25, kernel=5)
     assert name.startswith("half")
@@ -129,7 +131,7 @@ def test_d3q19_tiled_kernel(lw, shape):
 
 
 WALL_SHAPES = [(5, 8, 128), (3, 16, 256), (20, 24, 128), (2, 8, 256), (11, 72, 128), (4, 8, 256), (7, 40, 256),
-               (4, 16, 384), (4, 12, 256), (3, 5, 128)]
+               (4, 16, 384), (4, 12, 256), (3, 5, 128), (4, 8, 200)]
 
 
 @pytest.mark.parametrize("bc,shape", [(bc, s) for bc in (1, 2) for s in WALL_SHAPES] + [(2, (1, 16, 128))])
@@ -295,7 +297,7 @@ HALF_ULP = {2: 2.0 ** -11, 1: 2.0 ** -8}
 
 # (nx, ny, nz): the generic kernel (32^3) and the half-row kernel with 256- and
 # 128-node rows
-HALF_SHAPES = [(32, 32, 32), (256, 16, 8), (128, 24, 5), (384, 16, 6)]
+HALF_SHAPES = [(32, 32, 32), (256, 16, 8), (128, 24, 5), (384, 16, 6), (200, 12, 4)]
 
 
 def _tgv_box(shape):
@@ -559,7 +561,8 @@ def test_nu_p_matches_oracle(lw, Q, shape, kernel):
 
 
 @pytest.mark.parametrize("shape,storage", [((6, 16, 256), 0), ((5, 8, 128), 0), ((4, 8, 384), 0),
-                                           ((1, 8, 256), 0), ((5, 13, 256), 0), ((3, 16, 256), 2), ((4, 8, 384), 1)])
+                                           ((1, 8, 256), 0), ((5, 13, 256), 0), ((4, 10, 200), 0), ((3, 16, 256), 2),
+                                           ((4, 8, 384), 1), ((3, 8, 264), 2)])
 def test_nu_p_on_the_half_kernel(lw, shape, storage):
     """omega_p on D3Q19 with nx a multiple of 128: the density term
     sdelta sum_i w_i c_i . J(x - c_i) is summed from the state before the step and
