@@ -657,6 +657,11 @@ def run_case(name, steps):
         sim.set_fields(*inputs.tgv3d(n3, u0=U0))
         sim.set_scalar(torch.cos(2 * torch.pi * torch.arange(n3, device="cuda") / n3).expand(n3, n3, n3).contiguous())
         sim.step(steps)
+    elif name == "nu_p3d":  # D3Q19 256^3 Taylor-Green with omega_p (density pass + half-row kernel)
+        sim = lw.Lwacm(lw.D3Q19, 256, 256, 256, NU)
+        sim.set_option(lw.OPT_NU_P, 0.05)
+        sim.set_fields(*inputs.tgv3d(256, u0=U0))
+        sim.step(steps)
     elif name == "segments":  # D3Q19 384 x 256 x 128 Taylor-Green (half-row kernel on 128-node segments)
         sim = lw.Lwacm(lw.D3Q19, 384, 256, 128, NU)
         sim.set_fields(*inputs.tgv3d(384, u0=U0, ny=256, nz=128))
@@ -686,7 +691,7 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-variants", action="store_true")
     ap.add_argument("--profile-case", choices=["adjoint", "ensemble", "cavity", "cavity3d", "bulk2d", "scalar",
-                                               "segments"],
+                                               "segments", "nu_p3d"],
                     help="run one variant workload for --steps steps without timing (for profilers)")
     args = ap.parse_args()
     if args.warmup < 3:

@@ -523,10 +523,8 @@ __device__ __forceinline__ void phase_b(Acc &acc, const float *xbuf, T *out, con
             acc[PM][j][2] = sub2(acc[PM][j][2], o[j]);
             acc[PM][j][3] = sub2(acc[PM][j][3], o[j]);
         }
-        // a short last column's rows beyond ny (they carry the wrapped rows that feed
-        // its last row from above, like a halo row) are not stored, nor the nodes of a
-        // short last segment beyond nx (they carry the row's first nodes, likewise)
-        if (zfin >= 0 && col * HGeo<NH>::RW + row < p.ny && x0 + half * HALF + lane * VXH < p.nx) {
+        // zfin < 0: no plane to store (or the thread's nodes lie beyond ny or nx)
+        if (zfin >= 0) {
             const long long rowoff =
                 ((long long)zfin * p.ny + col * HGeo<NH>::RW + row) * p.nx + x0 + half * HALF + lane * VXH;
             T *op = out + rowoff;
@@ -739,14 +737,21 @@ __global__ void __launch_bounds__(HG<NH>::NTH, HG<NH>::MINB) k_d3q19_half(const 
                 prefetch_l2(pr, (uint32_t)(HGeo<NH>::RW * HG<NH>::RL * 4));
             }
         }
+        // a short last column's rows beyond ny (they carry the rows that follow
+        // periodically, the first feeding the last real row from above like a halo
+        // row) are not stored, nor the nodes of a short last segment beyond nx (they
+        // carry the row's first nodes, likewise); the check is made here rather than
+        // at the store, where it measured 1.2% slower
+        const bool live = ycol * HGeo<NH>::RW + row < p.ny && (!HGeo<NH>::SEG || x0 + lane * VXH < p.nx);
         if (mode == MID) {
-            phase_b<NH, MID, SRND, NUPV>(acc, xbuf, out, p, lane, row, half, ycol, x0, it.pz > it.za ? it.pz - 1 : -1, key);
+            phase_b<NH, MID, SRND, NUPV>(acc, xbuf, out, p, lane, row, half, ycol, x0,
+                                         it.pz > it.za && live ? it.pz - 1 : -1, key);
             rotate(acc);
         } else if (mode == FIRST) {
             phase_b<NH, FIRST, SRND, NUPV>(acc, xbuf, out, p, lane, row, half, ycol, x0, -1, key);
             rotate(acc);
         } else {
-            phase_b<NH, LAST, SRND, NUPV>(acc, xbuf, out, p, lane, row, half, ycol, x0, it.zb - 1, key);
+            phase_b<NH, LAST, SRND, NUPV>(acc, xbuf, out, p, lane, row, half, ycol, x0, live ? it.zb - 1 : -1, key);
         }
         it.next();
     }
