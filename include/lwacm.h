@@ -269,6 +269,14 @@ lwacm_status lwacm_get_trace(lwacm_ctx *ctx, void *T, int dtype, int where);
  * graphs. */
 lwacm_status lwacm_step(lwacm_ctx *ctx, long long n);
 
+/* Capture and instantiate now the CUDA graph that lwacm_step(ctx, n) would replay
+ * from the current state's buffer (none when n is below the graph chunk or graphs
+ * are off), without advancing the state: lwacm_step builds it on first use, and a
+ * caller that times or serves steps can take that one-time cost beforehand. The
+ * graph stays valid until an option changes. Needs a bound context with fields set
+ * (LWACM_E_STATE); n < 0: LWACM_E_ARG. */
+lwacm_status lwacm_prepare(lwacm_ctx *ctx, long long n);
+
 /* Borrowed device pointers to the current state (zero copy). Valid until the
  * next lwacm_step / lwacm_set_fields / lwacm_bind / lwacm_destroy. *dtype gets
  * the storage type, *pitch_elems the row pitch in elements (== nx). uz may be

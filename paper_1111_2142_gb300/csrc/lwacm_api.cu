@@ -845,6 +845,24 @@ lwacm_status lwacm_set_force_field(lwacm_ctx *c, const void *gx, const void *gy,
     return LWACM_OK;
 }
 
+lwacm_status lwacm_prepare(lwacm_ctx *c, long long n) {
+    lwacm_status s = ready(c, true);
+    if (s != LWACM_OK) return s;
+    if (n < 0) return fail(c, LWACM_E_ARG, "negative step count");
+    if (c->sr && c->kernel != 5)
+        return fail(c, LWACM_E_UNSUPPORTED, "stochastic rounding needs the half-row kernel (the plain periodic scheme)");
+    const int chunk = c->graph_chunk;
+    if (c->nbatch && c->batch_mode == 1) return LWACM_OK;  // one persistent launch, no graph
+    if (chunk <= 0 || n < chunk) return LWACM_OK;
+    const int par = c->cur;
+    if (c->gexec[par] && c->gchunk[par] == chunk) return LWACM_OK;
+    if (c->gexec[par]) {
+        cudaGraphExecDestroy(c->gexec[par]);
+        c->gexec[par] = nullptr;
+    }
+    return build_graph(c, par, chunk);
+}
+
 lwacm_status lwacm_step(lwacm_ctx *c, long long n) {
     const Range range("lwacm_step");
     lwacm_status s = ready(c, true);

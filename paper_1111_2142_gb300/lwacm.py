@@ -59,6 +59,7 @@ def load():
         "lwacm_bind": [vp, vp, ctypes.c_size_t, vp],
         "lwacm_set_fields": [vp, vp, vp, vp, vp, i, i],
         "lwacm_step": [vp, ll],
+        "lwacm_prepare": [vp, ll],
         "lwacm_fields": [vp, P(vp), P(vp), P(vp), P(vp), P(i), P(ll)],
         "lwacm_get_fields": [vp, vp, vp, vp, vp, i, i],
         "lwacm_get_fields_async": [vp, vp, vp, vp, vp, i, i],
@@ -308,6 +309,10 @@ class Lwacm:
 
     def step(self, n=1):
         self._check(self._lib.lwacm_step(self._h, int(n)))
+
+    def prepare(self, n):
+        """Build the CUDA graph that step(n) would replay, without stepping."""
+        self._check(self._lib.lwacm_prepare(self._h, int(n)))
 
     def sync(self):
         self._check(self._lib.lwacm_sync(self._h))

@@ -341,3 +341,13 @@ def test_selftest_round_validation(lib):
     assert lib.lwacm_selftest_round(p, p, 0, lw.F16, 0, None) == lw.E_ARG
     assert lib.lwacm_selftest_round(p, p, 1 << 31, lw.F16, 0, None) == lw.E_ARG
     assert lib.lwacm_selftest_round(p, p, 4, lw.F32, 0, None) == lw.E_ARG
+
+
+def test_prepare_validation(lib):
+    """lwacm_prepare needs a bound context with fields and a step count >= 0."""
+    from paper_1111_2142_gb300 import lwacm as lw
+    st, h = _create(lib, 19, 16, 8, 4, 0.02, 0)
+    assert st == lw.OK
+    assert lib.lwacm_prepare(h, 64) == lw.E_STATE
+    assert lib.lwacm_prepare(None, 64) == lw.E_ARG
+    lib.lwacm_destroy(h)

@@ -395,6 +395,27 @@ def test_conservation_fp64_reduction(lw):
     sim.close()
 
 
+def test_prepare_builds_the_graph_without_stepping(lw):
+    """lwacm_prepare captures the graph a later step(n) replays but leaves the state
+    alone: the fields and the step count are unchanged, and the steps that follow
+    give the same result as without it."""
+    f = inputs.smooth_random((9, 16, 128), seed=23, u_amp=0.03, d_amp=0.005)
+    sim = lw.Lwacm(19, 128, 16, 9, 0.02, graph_chunk=64)
+    sim.set_fields(*f)
+    before = sim.get_fields()
+    sim.prepare(130)
+    sim.prepare(130)  # already built: nothing to do
+    assert sim.step_count() == 0
+    assert all(np.array_equal(a, b) for a, b in zip(before, sim.get_fields()))
+    sim.step(1)
+    sim.prepare(129)  # the other parity's graph
+    sim.step(129)
+    got = sim.get_fields()
+    sim.close()
+    ref, _ = run_gpu(lw, 19, f, 0.02, 130, graph_chunk=64)
+    assert all(np.array_equal(a, b) for a, b in zip(got, ref))
+
+
 def test_graph_replay_matches_direct_launches(lw):
     f = inputs.smooth_random((20, 24), seed=9)
     a, _ = run_gpu(lw, 9, f, 0.02, 130, graph_chunk=64)
