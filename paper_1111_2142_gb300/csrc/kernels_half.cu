@@ -565,40 +565,61 @@ __device__ __forceinline__ void phase_b(Acc &acc, const float *xbuf, T *out, con
     }
 }
 
+// NH = 0: the bulk copies of one staged row (field f, row r) of an item, relative to
+// the plane's start: from element a, na bytes, then (x wrap) from element b, nb bytes.
+// Formed once per item by the thread that issues them, kept in shared memory.
+struct SegCopy {
+    long long a, b;
+    int na, nb;
+};
+constexpr int SEG_COPIES = 4 * (ROWS + 2);  // staged rows per plane (all four fields)
+
 // The staged rows of one plane (four fields) for an item's rows, by 1-D bulk copies
 // that complete on `bar`. NH = 1, 2: one thread issues them (the whole rows, wrapped
 // in y). NH = 0: 40 staged rows (a segment at an x end of the domain takes its
 // wrapped 8 nodes in a second copy), issued by lane 0 of rows 1-6, every sixth row
 // each (a bulk copy takes warp-uniform operands, so the lanes of one warp would
-// issue theirs one after another, and that warp would hold up the plane barrier);
-// row 1's thread also posts the expected bytes (the barrier's transaction count may
-// run below zero until it does).
+// issue theirs one after another, and that warp would hold up the plane barrier),
+// from offsets formed once per item (per plane only the plane's offset is added:
+// forming them per plane cost ~100 instructions per node); row 1's thread also posts
+// the expected bytes (the barrier's transaction count may run below zero until it
+// does).
 template <int NH, typename T>
 __device__ __forceinline__ void issue_plane(const T *in, const TiledParams &p, int col, int z, T *stage,
-                                            uint64_t *bar, int warp) {
+                                            uint64_t *bar, int warp, SegCopy *dsc = nullptr, int *dcol = nullptr) {
     constexpr int RL = HG<NH, T>::RL, SRL = HG<NH, T>::SRL;
     constexpr uint32_t TX = HG<NH, T>::TX;
     const int zl = z < 0 ? z + p.nz : (z >= p.nz ? z - p.nz : z);
     const long long plane = (long long)p.nx * p.ny;
     if constexpr (NH == 0) {
-        const int seg = col / p.ycols, y0 = (col - seg * p.ycols) * HGeo<NH>::RW;
-        const int x0 = seg * HALF, last = p.segs - 1;
-        const int rn = p.nx - x0;  // nodes of this segment up to the row's end (the last may be short)
+        static_assert(4 * HGeo<NH>::TRW == SEG_COPIES, "one descriptor per staged row");
+        const int w = warp - 1;  // this thread's rows: k = w, w + 6, ...
         if (warp == 1) mbar_expect_tx(bar, TX);
-        for (int k = warp - 1; k < 4 * HGeo<NH>::TRW; k += 6) {
-            const int f = k / HGeo<NH>::TRW, r = k - f * HGeo<NH>::TRW;
-            const int y = (y0 - 1 + r + p.ny) % p.ny;  // a remainder: rows of a short last column wrap
-            const T *src = in + f * p.fstride + (long long)zl * plane + (long long)y * p.nx;
-            T *dst = stage + (f * HGeo<NH>::TRW + r) * SRL;
-            if (seg == 0) {
-                bulk_g2s(dst, src + p.nx - 8, 8 * sizeof(T), bar);
-                bulk_g2s(dst + 8, src, (HALF + 8) * sizeof(T), bar);
-            } else if (seg == last) {  // to the row's end, then the row's start (wrapped)
-                bulk_g2s(dst, src + x0 - 8, (uint32_t)(rn + 8) * sizeof(T), bar);
-                bulk_g2s(dst + rn + 8, src, (uint32_t)(HALF + 8 - rn) * sizeof(T), bar);
-            } else {
-                bulk_g2s(dst, src + x0 - 8, SRL * sizeof(T), bar);
+        if (dcol[w] != col) {  // a new item: form its copies (the row offsets wrapped once here)
+            const int seg = col / p.ycols, y0 = (col - seg * p.ycols) * HGeo<NH>::RW;
+            const int x0 = seg * HALF, rn = p.nx - x0, last = p.segs - 1;
+            for (int k = w; k < SEG_COPIES; k += 6) {
+                const int f = k / HGeo<NH>::TRW, r = k - f * HGeo<NH>::TRW;
+                const int y = (y0 - 1 + r + p.ny) % p.ny;  // a remainder: rows of a short last column wrap
+                const long long rb = f * p.fstride + (long long)y * p.nx;
+                SegCopy d;
+                if (seg == 0) {  // the row's last 8 nodes, then its first 136
+                    d.a = rb + p.nx - 8, d.na = 8 * (int)sizeof(T), d.b = rb, d.nb = (HALF + 8) * (int)sizeof(T);
+                } else if (seg == last) {  // to the row's end, then the row's start (wrapped)
+                    d.a = rb + x0 - 8, d.na = (rn + 8) * (int)sizeof(T), d.b = rb, d.nb = (HALF + 8 - rn) * (int)sizeof(T);
+                } else {
+                    d.a = rb + x0 - 8, d.na = SRL * (int)sizeof(T), d.b = 0, d.nb = 0;
+                }
+                dsc[k] = d;
             }
+            dcol[w] = col;
+        }
+        const long long zo = (long long)zl * plane;
+        for (int k = w; k < SEG_COPIES; k += 6) {
+            const SegCopy d = dsc[k];
+            T *dst = stage + k * SRL;
+            bulk_g2s(dst, in + zo + d.a, (uint32_t)d.na, bar);
+            if (d.nb) bulk_g2s(dst + d.na / (int)sizeof(T), in + zo + d.b, (uint32_t)d.nb, bar);
         }
     } else {
         const int y0 = col * HGeo<NH>::RW;
@@ -665,6 +686,10 @@ __global__ void __launch_bounds__(HG<NH>::NTH, HG<NH>::MINB) k_d3q19_half(const 
     if ((int)blockIdx.x >= p.nitems) return;  // uniform per CTA
 
     __shared__ int failed;
+    // NH = 0: the current item's copies and, per issuing row, the item they are for
+    __shared__ SegCopy seg_dsc[NH == 0 ? SEG_COPIES : 1];
+    __shared__ int seg_col[NH == 0 ? 6 : 1];
+    if (NH == 0 && threadIdx.x < 6) seg_col[threadIdx.x] = -1;
     if (threadIdx.x == 0) {
         failed = 0;
         mbar_init(&bars[0], 1);
@@ -677,7 +702,7 @@ __global__ void __launch_bounds__(HG<NH>::NTH, HG<NH>::MINB) k_d3q19_half(const 
     TaskIter pf = it;
     int issued = 0;
     for (int k = 0; k < 2 && pf.valid(); ++k) {
-        if (issuer) issue_plane<NH, T>(in, p, pf.col, pf.pz, stg + k * STAGE, &bars[k], warp);
+        if (issuer) issue_plane<NH, T>(in, p, pf.col, pf.pz, stg + k * STAGE, &bars[k], warp, seg_dsc, seg_col);
         ++issued;
         pf.next();
     }
@@ -719,7 +744,7 @@ __global__ void __launch_bounds__(HG<NH>::NTH, HG<NH>::MINB) k_d3q19_half(const 
         if (pf.valid()) {
             if (issuer) {
                 asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-                issue_plane<NH, T>(in, p, pf.col, pf.pz, stg + s * STAGE, &bars[s], warp);
+                issue_plane<NH, T>(in, p, pf.col, pf.pz, stg + s * STAGE, &bars[s], warp, seg_dsc, seg_col);
             }
             ++issued;
             pf.next();
