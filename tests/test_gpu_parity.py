@@ -344,6 +344,28 @@ def test_stochastic_rounding_one_step(lw, storage, shape):
     assert differ > 0.05 * sum(a.size for a in got)
 
 
+def test_stochastic_rounding_with_graphs_matches_direct_launches(lw):
+    """The step counter that keys the random bits advances in the captured graphs
+    as in direct launches (its advance is part of each step), so a run replayed
+    from graphs equals the same run launched step by step, bit for bit, and two
+    steps never share their random bits (a second run from the same state, whose
+    counter goes on, rounds differently)."""
+    f = [round_storage(a, 2) for a in _tgv_box((256, 16, 8))]
+    a, _ = run_gpu(lw, 19, f, 0.005, 130, storage=2, stochastic_rounding=True, graph_chunk=64)
+    b, _ = run_gpu(lw, 19, f, 0.005, 130, storage=2, stochastic_rounding=True, graph_chunk=0)
+    for x, y in zip(a, b):
+        assert np.array_equal(x, y)
+    sim = lw.Lwacm(19, 256, 16, 8, 0.005, storage=2, stochastic_rounding=True)
+    sim.set_fields(*f)
+    sim.step(3)
+    first = sim.get_fields()
+    sim.set_fields(*f)
+    sim.step(3)
+    second = sim.get_fields()
+    sim.close()
+    assert any(not np.array_equal(x, y) for x, y in zip(first, second))
+
+
 @pytest.mark.parametrize("shape", HALF_SHAPES)
 @pytest.mark.parametrize("storage", [2, 1])
 def test_half_storage_error_vs_oracle(lw, storage, shape):
