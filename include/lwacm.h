@@ -91,7 +91,7 @@ enum {
                               1 = generic gather kernel, 5 = D3Q19 half-row TMA kernel
                               (needs the plain scheme, with or without a constant
                               acceleration but not a force field, nx = 128, 256 or
-                              nx >= 136 a multiple of 4 (8 for BF16 / FP16 storage)
+                              nx >= 72 a multiple of 4 (8 for BF16 / FP16 storage)
                               with nx % 128 == 0 or >= 8, any ny, and runs walled
                               domains with the wall pass
                               after it; FP32, BF16 and FP16 storage: LWACM_E_UNSUPPORTED

@@ -1,5 +1,5 @@
-// Half-row TMA row-tiled D3Q19 kernel, for domains with nx = 256, 128 or any larger
-// multiple of 128 and any ny (periodic; walled domains get the wall pass after it,
+// Half-row TMA row-tiled D3Q19 kernel, for domains with nx = 256, 128 or other rows
+// of at least 72 nodes (multiples of 4, see segments_fit) and any ny (periodic; walled domains get the wall pass after it,
 // the cavity's x faces handled here for rows of 128 and 256): the moment form of
 // Eq. ACM2.0 (see lwacm_core.cuh), every field read from HBM once and written once
 // per step. A CTA updates columns of 8 rows; when ny % 8 != 0 the last column's
@@ -41,7 +41,7 @@ constexpr int HALF_ROWS = 8;           // rows per column of the 256-node-row fo
 
 // Row geometry. NH = 1: one warp per row of nx = 128 nodes, its lanes wrap
 // periodically by themselves; NH = 2: two warps (halves) per row of 256, see above;
-// NH = 0: other rows (nx >= 136) cut into ceil(nx / 128) segments of 128, one warp
+// NH = 0: other rows (nx >= 72) cut into ceil(nx / 128) segments of 128, one warp
 // per segment and a CTA per (segment, column of rows): the staged rows carry 8 more
 // nodes on each side (x0 - 8 .. x0 + 135, wrapped), and the boundary lanes take
 // their outside neighbours from them as the halves do. A short last segment stages
@@ -566,8 +566,10 @@ __device__ __forceinline__ void phase_b(Acc &acc, const float *xbuf, T *out, con
 }
 
 // NH = 0: the bulk copies of one staged row (field f, row r) of an item, relative to
-// the plane's start: from element a, na bytes, then (x wrap) from element b, nb bytes.
-// Formed once per item by the thread that issues them, kept in shared memory.
+// the plane's start: from element a, na bytes, then (x wrap) from element b, nb bytes,
+// and, for a row shorter than 136 nodes (one segment), the rest of the staged row
+// from element b again (the row's start once more). Formed once per item by the
+// thread that issues them, kept in shared memory.
 struct SegCopy {
     long long a, b;
     int na, nb;
@@ -603,7 +605,9 @@ __device__ __forceinline__ void issue_plane(const T *in, const TiledParams &p, i
                 const int y = (y0 - 1 + r + p.ny) % p.ny;  // a remainder: rows of a short last column wrap
                 const long long rb = f * p.fstride + (long long)y * p.nx;
                 SegCopy d;
-                if (seg == 0) {  // the row's last 8 nodes, then its first 136
+                if (last == 0) {  // one short segment: the row's last 8 nodes, the row, its start
+                    d.a = rb + p.nx - 8, d.na = 8 * (int)sizeof(T), d.b = rb, d.nb = p.nx * (int)sizeof(T);
+                } else if (seg == 0) {  // the row's last 8 nodes, then its first 136
                     d.a = rb + p.nx - 8, d.na = 8 * (int)sizeof(T), d.b = rb, d.nb = (HALF + 8) * (int)sizeof(T);
                 } else if (seg == last) {  // to the row's end, then the row's start (wrapped)
                     d.a = rb + x0 - 8, d.na = (rn + 8) * (int)sizeof(T), d.b = rb, d.nb = (HALF + 8 - rn) * (int)sizeof(T);
@@ -615,11 +619,22 @@ __device__ __forceinline__ void issue_plane(const T *in, const TiledParams &p, i
             dcol[w] = col;
         }
         const long long zo = (long long)zl * plane;
-        for (int k = w; k < SEG_COPIES; k += 6) {
-            const SegCopy d = dsc[k];
-            T *dst = stage + k * SRL;
-            bulk_g2s(dst, in + zo + d.a, (uint32_t)d.na, bar);
-            if (d.nb) bulk_g2s(dst + d.na / (int)sizeof(T), in + zo + d.b, (uint32_t)d.nb, bar);
+        if (p.segs > 1) {
+            for (int k = w; k < SEG_COPIES; k += 6) {
+                const SegCopy d = dsc[k];
+                T *dst = stage + k * SRL;
+                bulk_g2s(dst, in + zo + d.a, (uint32_t)d.na, bar);
+                if (d.nb) bulk_g2s(dst + d.na / (int)sizeof(T), in + zo + d.b, (uint32_t)d.nb, bar);
+            }
+        } else {  // one short segment: the row's start a second time fills the staged row
+            for (int k = w; k < SEG_COPIES; k += 6) {
+                const SegCopy d = dsc[k];
+                T *dst = stage + k * SRL;
+                const int rest = SRL * (int)sizeof(T) - d.na - d.nb;
+                bulk_g2s(dst, in + zo + d.a, (uint32_t)d.na, bar);
+                bulk_g2s(dst + d.na / (int)sizeof(T), in + zo + d.b, (uint32_t)d.nb, bar);
+                bulk_g2s(dst + (d.na + d.nb) / (int)sizeof(T), in + zo + d.b, (uint32_t)rest, bar);
+            }
         }
     } else {
         const int y0 = col * HGeo<NH>::RW;
@@ -835,12 +850,13 @@ static cudaError_t prepare_storage(int storage) {
 // row geometry (the NH of HG) for a row of nx nodes: 2 (256), 1 (128), 0 (128 S, S >= 3)
 static int half_geometry(int nx) { return nx == 256 ? 2 : (nx == 128 ? 1 : 0); }
 
-// rows the segment form takes: at least 136 nodes (segment 0 stages 136 from the row's
-// start), a last segment of at least 8 nodes (the one before it stages 8 past its
-// end), and 16-byte row starts and copy sizes (nx a multiple of 16 bytes' worth)
+// rows the segment form takes: at least 72 nodes (a row of one segment is staged as
+// its last 8 nodes, itself and its first 136 - nx again: the last must fit in it), a
+// last segment of at least 8 nodes (the one before it stages 8 past its end), and
+// 16-byte row starts and copy sizes (nx a multiple of 16 bytes' worth)
 static bool segments_fit(int nx, int storage) {
     const int q = storage == STORE_F32 ? 4 : 8;
-    return nx >= 136 && nx % q == 0 && (nx % HALF == 0 || nx % HALF >= 8);
+    return nx >= 72 && nx % q == 0 && (nx % HALF == 0 || nx % HALF >= 8);
 }
 
 bool half_xwalls(const StepParams &p) {

@@ -113,14 +113,16 @@ def test_d3q19_ragged(lw, kernel, shape):
                                    (2, 8, 256), (37, 8, 128), (300, 16, 128), (41, 24, 256),
                                    (5, 8, 384), (3, 16, 512), (4, 8, 640), (17, 24, 384), (1, 8, 1024),
                                    (5, 12, 128), (3, 20, 256), (4, 3, 384), (2, 1, 128), (6, 30, 256), (3, 7, 256),
-                                   (4, 8, 200), (3, 13, 300), (2, 8, 392), (5, 16, 136), (3, 9, 524)])
+                                   (4, 8, 200), (3, 13, 300), (2, 8, 392), (5, 16, 136), (3, 9, 524),
+                                   (4, 8, 96), (3, 10, 100), (2, 8, 72), (5, 16, 124)])
 def test_d3q19_tiled_kernel(lw, shape):
     """The row-tiled D3Q19 kernel (half-row TMA kernel: two warps per 256-node row,
     one per 128-node row, one per 128-node segment of longer rows), forced on;
     shapes cover runs that cross columns, one plane, ragged chunks, rows of 3, 4, 5
     and 8 segments (the first and last wrap in x), ny not a multiple of 8 (a short
     last column; ny = 1, 3 and 7: fewer rows than one column), and nx not a multiple
-    of 128 (a short last segment of 8 to 72 nodes)."""
+    of 128 (a short last segment of 8 to 72 nodes; rows of 72 to 124 nodes, one
+    short segment that stages the row's start twice)."""
     f = inputs.smooth_random(shape, seed=12, u_amp=0.05, d_amp=0.01)
     got, name = run_gpu(lw, 19, f, 0.01, 25, kernel=5)
     assert name.startswith("half")
@@ -297,7 +299,7 @@ HALF_ULP = {2: 2.0 ** -11, 1: 2.0 ** -8}
 
 # (nx, ny, nz): the generic kernel (32^3) and the half-row kernel with 256- and
 # 128-node rows
-HALF_SHAPES = [(32, 32, 32), (256, 16, 8), (128, 24, 5), (384, 16, 6), (200, 12, 4)]
+HALF_SHAPES = [(32, 32, 32), (256, 16, 8), (128, 24, 5), (384, 16, 6), (200, 12, 4), (112, 8, 6)]
 
 
 def _tgv_box(shape):
