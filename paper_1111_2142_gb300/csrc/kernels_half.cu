@@ -713,7 +713,7 @@ __global__ void __launch_bounds__(HG<NH>::NTH, HG<NH>::MINB) k_d3q19_half(const 
     }
     __syncthreads();
 
-    TaskIter it(blockIdx.x, p.nitems, gridDim.x, p.ycols * p.segs, p.zc, p.nz);
+    TaskIter it(blockIdx.x, p.nitems, gridDim.x, p.ycols * p.segs, p.zc, p.nz, p.kcls);
     TaskIter pf = it;
     int issued = 0;
     for (int k = 0; k < 2 && pf.valid(); ++k) {
@@ -816,22 +816,6 @@ cudaError_t prepare(int *ctas) {
     return n > 0 ? cudaSuccess : cudaErrorNotSupported;
 }
 
-int half_chunk_planes(int ycols, int nz, int ctas) {
-    if (ctas < 1) ctas = 1;
-    int best = nz;
-    double best_t = 1e300;
-    for (int zc = (nz < 4 ? nz : 4); zc <= nz; ++zc) {
-        const long long items = (long long)ycols * ((nz + zc - 1) / zc);
-        const long long per = (items + ctas - 1) / ctas;
-        const double t = (double)per * (zc + 0.7);
-        if (t < best_t - 1e-9) {
-            best_t = t;
-            best = zc;
-        }
-    }
-    return best;
-}
-
 }  // namespace
 
 template <int NH, int V>
@@ -922,8 +906,10 @@ static cudaError_t launch_nh(const void *in, void *out, const StepParams &sp, cu
     p.nz = sp.nz;
     p.ycols = (sp.ny + HGeo<NH>::RW - 1) / HGeo<NH>::RW;
     p.segs = NH == 0 ? (sp.nx + HALF - 1) / HALF : 1;
-    p.zc = half_chunk_planes(p.ycols * p.segs, sp.nz, ctas);
-    p.nitems = p.ycols * p.segs * ((sp.nz + p.zc - 1) / p.zc);
+    const Schedule sc = plan_schedule(p.ycols * p.segs, sp.nz, ctas);
+    p.zc = sc.zc;
+    p.nitems = sc.nitems;
+    p.kcls = sc.kcls;
     p.fstride = sp.fstride;
     const double nu = (double)sp.s / 18.0;
     p.s18 = (float)nu;
@@ -934,8 +920,7 @@ static cudaError_t launch_nh(const void *in, void *out, const StepParams &sp, cu
     p.sr_ctr = V == 3 ? sp.sr_ctr : nullptr;
     p.pfield = V == 4 ? sp.nup_p : nullptr;
     p.sdelta = V == 4 ? sp.sdelta : 0.f;
-    const int grid = ctas < p.nitems ? ctas : p.nitems;
-    k_d3q19_half<NH, T, V><<<(unsigned)grid, HG<NH, T>::NTH, HG<NH, T>::BYTES, st>>>((const T *)in, (T *)out, p);
+    k_d3q19_half<NH, T, V><<<(unsigned)sc.grid, HG<NH, T>::NTH, HG<NH, T>::BYTES, st>>>((const T *)in, (T *)out, p);
     return cudaGetLastError();
 }
 

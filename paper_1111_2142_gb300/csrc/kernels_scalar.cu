@@ -46,7 +46,7 @@ struct SG {
 };
 
 struct ScalarParams {
-    int nx, ny, nz, ycols, zc, nitems;
+    int nx, ny, nz, ycols, zc, nitems, kcls;  // the schedule (TaskIter, tile_common.cuh)
     long long fstride;
     float at, b1, b2;  // a_t; (1 - a_t) 9/2 w for w = 1/18 and 1/36
     float kt;          // 1 - a_t
@@ -360,7 +360,7 @@ __global__ void __launch_bounds__(SG<NH>::NTH, 2 / NH) k_scalar_rows(const float
     }
     __syncthreads();
 
-    TaskIter it(blockIdx.x, p.nitems, gridDim.x, p.ycols, p.zc, p.nz);
+    TaskIter it(blockIdx.x, p.nitems, gridDim.x, p.ycols, p.zc, p.nz, p.kcls);
     TaskIter pf = it;
     int issued = 0;
     for (int k = 0; k < 2 && pf.valid(); ++k) {
@@ -439,20 +439,6 @@ int scalar_ctas() {
     });
 }
 
-int scalar_chunk_planes(int ycols, int nz, int ctas) {
-    int best = nz;
-    double best_t = 1e300;
-    for (int zc = (nz < 4 ? nz : 4); zc <= nz; ++zc) {
-        const long long items = (long long)ycols * ((nz + zc - 1) / zc);
-        const double t = (double)((items + ctas - 1) / ctas) * (zc + 0.7);
-        if (t < best_t - 1e-9) {
-            best_t = t;
-            best = zc;
-        }
-    }
-    return best;
-}
-
 }  // namespace
 
 bool scalar_rows_supported(int Q, int storage, const StepParams &p) {
@@ -471,16 +457,17 @@ static cudaError_t launch_scalar_nh(const void *in, void *out, const StepParams 
     p.ny = sp.ny;
     p.nz = sp.nz;
     p.ycols = sp.ny / ROWS;
-    p.zc = scalar_chunk_planes(p.ycols, sp.nz, ctas);
-    p.nitems = p.ycols * ((sp.nz + p.zc - 1) / p.zc);
+    const Schedule sc = plan_schedule(p.ycols, sp.nz, ctas);
+    p.zc = sc.zc;
+    p.nitems = sc.nitems;
+    p.kcls = sc.kcls;
     p.fstride = sp.fstride;
     p.at = sp.at;
     p.kt = 1.f - sp.at;
     p.b1 = p.kt * (4.5f / 18.f);
     p.b2 = p.kt * (4.5f / 36.f);
     p.err = sp.err;
-    const int grid = ctas < p.nitems ? ctas : p.nitems;
-    k_scalar_rows<NH><<<(unsigned)grid, SG<NH>::NTH, SG<NH>::BYTES, st>>>((const float *)in, (float *)out, p);
+    k_scalar_rows<NH><<<(unsigned)sc.grid, SG<NH>::NTH, SG<NH>::BYTES, st>>>((const float *)in, (float *)out, p);
     return cudaGetLastError();
 }
 

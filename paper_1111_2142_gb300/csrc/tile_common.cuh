@@ -21,7 +21,8 @@ struct TiledParams {
     int nx, ny, nz;
     int ycols;           // columns of ROWS rows: ceil(ny / ROWS)
     int segs;            // 128-node segments per row a CTA item covers one of (1: the whole row)
-    int zc, nitems;      // planes per chunk, ycols * ceil(nz / zc)
+    int zc, nitems;      // planes per chunk, ycols * ceil(nz / zc); zc = 0: equal runs (TaskIter)
+    int kcls;            // equal runs: y-neighbouring columns lie kcls apart in the run order
     long long fstride;
     float s18;           // s / 18 = nu
     float a, am1;        // a = 1 - 6 nu and a - 1 = -6 nu (post_combine, lwacm_core.cuh)
@@ -158,39 +159,138 @@ __device__ __forceinline__ float2 div_apply2(float2 a, const Div2 &d) {
 }
 
 // ---- task iteration -------------------------------------------------------------
-// Work items are (column, z-chunk) pairs, numbered chunk-major (item = chunk * ycols
-// + col) so that the CTAs working on neighbouring columns march through the same
-// planes together and share their halo rows in L2. CTA b takes items b, b + G,
-// b + 2G, ... (G = grid size). An item is a run [za, zb) of planes of one column,
-// processed as source planes za-1 (FIRST), za .. zb-1 (MID), zb (LAST).
+// An item is a run [za, zb) of planes of one column, processed as source planes
+// za-1 (FIRST), za .. zb-1 (MID), zb (LAST). Two schedules:
+// * chunks (zc > 0): items are (column, z-chunk of zc planes) pairs, numbered
+//   chunk-major (item = chunk * ycols + col) so that the CTAs working on
+//   neighbouring columns march through the same planes together and share their
+//   halo rows in L2; CTA b takes items b, b + G, b + 2G, ... (G = grid size).
+// * ranges (zc == 0): the columns' planes laid end to end (W = ycols nz planes) are
+//   cut into G equal runs, CTA b taking planes [b W / G, (b+1) W / G): one or two
+//   items (more when a run is longer than a column), the column changing inside a
+//   run. Columns follow each other in an order where y-neighbours lie kcls apart:
+//   kcls = ycols / gcd(ycols, G) columns hold exactly an integer number of runs, so
+//   a column and the one kcls after it start their runs at the same planes, and
+//   their CTAs pass each plane together as with chunks.
 enum { FIRST = 0, MID = 1, LAST = 2 };
 
 struct TaskIter {
     int item, nitems, stride, ycols, zc, nz;
+    // chunks: the item's column and chunk, and the steps of both per item (no
+    // division once started)
+    int ch, dcol, dch;
+    // runs: the next plane of the run and its end; the column's place in the run
+    // order (class r, index q in the class) and the columns per class
+    long long lin, lend;
+    int r, q, kcls, per;
     int col, za, zb, pz;
+    __device__ TaskIter(int first, int nitems_, int stride_, int ycols_, int zc_, int nz_, int kcls_ = 1)
+        : item(first), nitems(nitems_), stride(stride_), ycols(ycols_), zc(zc_), nz(nz_), kcls(kcls_) {
+        col = za = zb = pz = ch = dcol = dch = r = q = per = 0;
+        lin = lend = 0;
+        if (zc > 0) {
+            dcol = stride % ycols;
+            dch = stride / ycols;
+            col = item % ycols;
+            ch = item / ycols;
+        } else {
+            const long long w = (long long)ycols * nz;
+            lin = w * first / stride;
+            lend = w * (first + 1) / stride;
+            const int s = (int)(lin / nz);
+            za = (int)(lin - (long long)s * nz);
+            per = ycols / kcls;
+            r = s % kcls;
+            q = s / kcls;
+        }
+        if (valid()) start_run();
+    }
     __device__ void start_run() {
-        col = item % ycols;
-        const int ch = item / ycols;
-        za = ch * zc;
-        zb = za + zc < nz ? za + zc : nz;
+        if (zc > 0) {
+            za = ch * zc;
+            zb = za + zc < nz ? za + zc : nz;
+        } else {
+            const long long left = lend - lin;
+            zb = left < nz - za ? za + (int)left : nz;
+            col = r * per + q;
+        }
         pz = za - 1;
     }
-    __device__ TaskIter(int first, int nitems_, int stride_, int ycols_, int zc_, int nz_)
-        : item(first), nitems(nitems_), stride(stride_), ycols(ycols_), zc(zc_), nz(nz_) {
-        col = za = zb = pz = 0;
-        if (item < nitems) start_run();
-    }
-    __device__ bool valid() const { return item < nitems; }
+    __device__ bool valid() const { return zc > 0 ? item < nitems : lin < lend; }
     __device__ int mode() const { return pz < za ? FIRST : (pz < zb ? MID : LAST); }
     __device__ void next() {
         if (pz < zb) {
             ++pz;
-        } else {
+        } else if (zc > 0) {
             item += stride;
+            col += dcol;
+            ch += dch;
+            if (col >= ycols) {
+                col -= ycols;
+                ++ch;
+            }
             if (item < nitems) start_run();
+        } else {
+            lin += zb - za;
+            za = 0;  // a run goes on at the start of the next column
+            if (++r == kcls) {
+                r = 0;
+                ++q;
+            }
+            if (lin < lend) start_run();
         }
     }
 };
+
+// The schedule of a step (TaskIter), chosen on the host: cost model = the busiest CTA's planes plus 0.7
+// of a plane per item (its FIRST and LAST source planes, each partly computed).
+struct Schedule {
+    int zc, nitems, kcls, grid;
+};
+// chunks of zc planes: the zc with the least cost
+inline Schedule chunk_schedule(int cols, int nz, int ctas, double *cost) {
+    if (ctas < 1) ctas = 1;
+    int best = nz;
+    double best_t = 1e300;
+    for (int zc = (nz < 4 ? nz : 4); zc <= nz; ++zc) {
+        const long long items = (long long)cols * ((nz + zc - 1) / zc);
+        const long long per = (items + ctas - 1) / ctas;
+        const double t = (double)per * (zc + 0.7);
+        if (t < best_t - 1e-9) {
+            best_t = t;
+            best = zc;
+        }
+    }
+    *cost = best_t;
+    const int nitems = cols * ((nz + best - 1) / best);
+    return Schedule{best, nitems, 1, ctas < nitems ? ctas : nitems};
+}
+// equal runs over the columns laid end to end
+inline Schedule run_schedule(int cols, int nz, int ctas, double *cost) {
+    const long long w = (long long)cols * nz;
+    const int g = (int)(w < ctas ? w : ctas);
+    double worst = 0.0;
+    for (int b = 0; b < g; ++b) {
+        const long long l0 = w * b / g, l1 = w * (b + 1) / g;
+        const long long items = (l1 - 1) / nz - l0 / nz + 1;
+        const double t = (double)(l1 - l0) + 0.7 * (double)items;
+        worst = t > worst ? t : worst;
+    }
+    *cost = worst;
+    int a = cols, c = g;  // kcls = cols / gcd(cols, g)
+    while (c) {
+        const int t = a % c;
+        a = c;
+        c = t;
+    }
+    return Schedule{0, g, cols / a, g};
+}
+inline Schedule plan_schedule(int cols, int nz, int ctas) {
+    double tc = 0.0, tr = 0.0;
+    const Schedule c = chunk_schedule(cols, nz, ctas, &tc);
+    const Schedule r = run_schedule(cols, nz, ctas < 1 ? 1 : ctas, &tr);
+    return tr < tc - 1e-9 ? r : c;
+}
 
 // position of node group h (4 nodes) of lane l inside an exchange row: the 4-float
 // groups of all lanes are contiguous, so warp float4 accesses are conflict-free

@@ -114,11 +114,14 @@ def test_d3q19_ragged(lw, kernel, shape):
                                    (5, 8, 384), (3, 16, 512), (4, 8, 640), (17, 24, 384), (1, 8, 1024),
                                    (5, 12, 128), (3, 20, 256), (4, 3, 384), (2, 1, 128), (6, 30, 256), (3, 7, 256),
                                    (4, 8, 200), (3, 13, 300), (2, 8, 392), (5, 16, 136), (3, 9, 524),
-                                   (4, 8, 96), (3, 10, 100), (2, 8, 72), (5, 16, 124)])
+                                   (4, 8, 96), (3, 10, 100), (2, 8, 72), (5, 16, 124),
+                                   (100, 24, 256), (80, 16, 384), (3, 2440, 128), (1, 8000, 128)])
 def test_d3q19_tiled_kernel(lw, shape):
     """The row-tiled D3Q19 kernel (half-row TMA kernel: two warps per 256-node row,
     one per 128-node row, one per 128-node segment of longer rows), forced on;
-    shapes cover runs that cross columns, one plane, ragged chunks, rows of 3, 4, 5
+    shapes cover both schedules (equal runs that cross columns, with y-neighbouring
+    columns three apart in the run order, and runs longer than a column; chunks, a
+    CTA taking several), one plane, ragged chunks, rows of 3, 4, 5
     and 8 segments (the first and last wrap in x), ny not a multiple of 8 (a short
     last column; ny = 1, 3 and 7: fewer rows than one column), and nx not a multiple
     of 128 (a short last segment of 8 to 72 nodes; rows of 72 to 124 nodes, one
@@ -133,7 +136,7 @@ def test_d3q19_tiled_kernel(lw, shape):
 
 
 WALL_SHAPES = [(5, 8, 128), (3, 16, 256), (20, 24, 128), (2, 8, 256), (11, 72, 128), (4, 8, 256), (7, 40, 256),
-               (4, 16, 384), (4, 12, 256), (3, 5, 128), (4, 8, 200)]
+               (4, 16, 384), (4, 12, 256), (3, 5, 128), (4, 8, 200), (100, 24, 256)]
 
 
 @pytest.mark.parametrize("bc,shape", [(bc, s) for bc in (1, 2) for s in WALL_SHAPES] + [(2, (1, 16, 128))])

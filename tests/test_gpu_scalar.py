@@ -19,13 +19,16 @@ def lw():
 # D2Q9 and odd D3Q19 shapes run on the generic kernel (flow and scalar in one
 # pass); D3Q19 boxes with 128- or 256-node rows and ny % 8 == 0 run the flow on the
 # half-row kernel and the scalar on its own row-tiled kernel (several columns,
-# ragged z-chunks, one plane, y wrapping inside a column)
+# ragged z-chunks, one plane, y wrapping inside a column, equal runs that cross
+# columns: 7 and 9 columns, none a divisor of the grid)
 @pytest.mark.parametrize("Q,shape,T,kern", [(9, (48, 64), 150, "generic"), (9, (17, 23), 60, "generic"),
                                             (19, (10, 12, 14), 40, "generic"),
                                             (19, (6, 16, 128), 40, "half_d3q19_tma+scalar_rows"),
                                             (19, (5, 8, 256), 40, "half_d3q19_tma+scalar_rows"),
                                             (19, (37, 24, 128), 30, "half_d3q19_tma+scalar_rows"),
-                                            (19, (1, 8, 256), 20, "half_d3q19_tma+scalar_rows")])
+                                            (19, (1, 8, 256), 20, "half_d3q19_tma+scalar_rows"),
+                                            (19, (90, 56, 128), 20, "half_d3q19_tma+scalar_rows"),
+                                            (19, (70, 72, 256), 20, "half_d3q19_tma+scalar_rows")])
 def test_scalar_matches_oracle(lw, Q, shape, T, kern):
     """Flow and scalar together, every node against the oracle; the scalar's total
     is conserved to FP32 rounding."""
