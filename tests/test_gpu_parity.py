@@ -610,11 +610,13 @@ def test_nu_p_matches_oracle(lw, Q, shape, kernel):
 
 @pytest.mark.parametrize("shape,storage", [((6, 16, 256), 0), ((5, 8, 128), 0), ((4, 8, 384), 0),
                                            ((1, 8, 256), 0), ((5, 13, 256), 0), ((4, 10, 200), 0), ((3, 16, 256), 2),
-                                           ((4, 8, 384), 1), ((3, 8, 264), 2)])
+                                           ((4, 8, 384), 1), ((3, 8, 264), 2), ((70, 40, 256), 0),
+                                           ((2, 8, 128), 0)])
 def test_nu_p_on_the_half_kernel(lw, shape, storage):
     """omega_p on D3Q19 with nx a multiple of 128: the density term
     sdelta sum_i w_i c_i . J(x - c_i) is summed from the state before the step and
-    the half-row kernel adds it to each node's density. FP32: 40 steps against the
+    the half-row kernel adds it to each node's density (shapes with several tiles of
+    the summing pass in x, y and z, ragged ones, and one or two planes). FP32: 40 steps against the
     oracle; FP16 / BF16 storage: one step from a rounded state within half a storage
     ulp (plus the FP32 rounding)."""
     nz, ny, nx = shape
