@@ -699,6 +699,11 @@ __global__ void __launch_bounds__(HG<NH>::NTH, HG<NH>::MINB) k_d3q19_half(const 
     const bool producer = threadIdx.x == (NH == 2 ? 64 : 32);
     const bool issuer = NH == 0 ? (lane == 0 && warp >= 1 && warp <= 6) : producer;
     if ((int)blockIdx.x >= p.nitems) return;  // uniform per CTA
+    // programmatic dependent launch: the next step's kernel may be scheduled now; its
+    // CTAs take an SM as one of this grid's leaves it and set up their shared memory
+    // while the rest run, then wait (griddepcontrol.wait below) for this grid to
+    // complete before they touch global memory
+    asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
 
     __shared__ int failed;
     // NH = 0: the current item's copies and, per issuing row, the item they are for
@@ -712,6 +717,9 @@ __global__ void __launch_bounds__(HG<NH>::NTH, HG<NH>::MINB) k_d3q19_half(const 
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
     __syncthreads();
+    // the grid before this one in the stream (launched with programmatic stream
+    // serialization: a no-op otherwise) has completed and its writes are visible
+    asm volatile("griddepcontrol.wait;" ::: "memory");
 
     TaskIter it(blockIdx.x, p.nitems, gridDim.x, p.ycols * p.segs, p.zc, p.nz, p.kcls);
     TaskIter pf = it;
@@ -920,8 +928,20 @@ static cudaError_t launch_nh(const void *in, void *out, const StepParams &sp, cu
     p.sr_ctr = V == 3 ? sp.sr_ctr : nullptr;
     p.pfield = V == 4 ? sp.nup_p : nullptr;
     p.sdelta = V == 4 ? sp.sdelta : 0.f;
-    k_d3q19_half<NH, T, V><<<(unsigned)sc.grid, HG<NH, T>::NTH, HG<NH, T>::BYTES, st>>>((const T *)in, (T *)out, p);
-    return cudaGetLastError();
+    // launched with programmatic stream serialization: its CTAs may start before the
+    // previous kernel in the stream has finished and wait for it in the kernel (+0.5%
+    // on 256^3, +2% on 128^3, where the gap between steps weighs more)
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3((unsigned)sc.grid);
+    cfg.blockDim = dim3(HG<NH, T>::NTH);
+    cfg.dynamicSmemBytes = HG<NH, T>::BYTES;
+    cfg.stream = st;
+    cudaLaunchAttribute at[1];
+    at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    at[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = at;
+    cfg.numAttrs = 1;
+    return cudaLaunchKernelEx(&cfg, k_d3q19_half<NH, T, V>, (const T *)in, (T *)out, p);
 }
 
 template <int V, typename T>
