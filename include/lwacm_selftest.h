@@ -1,7 +1,8 @@
 /*
- * lwacm_selftest.h — device self-tests of numerical building blocks the LW-ACM
- * kernels use (the paper has no counterpart). They let a test check, on the
- * GPU, a device function against the correctly rounded result.
+ * lwacm_selftest.h — self-tests of building blocks the LW-ACM kernels use (the
+ * paper has no counterpart). They let a test check, on the GPU, a device function
+ * against the correctly rounded result, and, on the host, the work schedule the
+ * row-tiled kernels follow.
  */
 #ifndef LWACM_SELFTEST_H
 #define LWACM_SELFTEST_H
@@ -36,6 +37,21 @@ int lwacm_selftest_quotient(const float *a_dev, const float *b_dev, float *out_d
  * FP32 values, n in [1, 2^31). Stream-ordered on `stream`, not synchronised.
  * Errors: LWACM_E_ARG (null pointer, n out of range, other storage), LWACM_E_CUDA. */
 int lwacm_selftest_round(const float *x_dev, float *out_dev, long long n, int storage, unsigned step, void *stream);
+
+/* The work schedule of one step of the row-tiled kernels (the D3Q19 half-row kernel
+ * and the scalar kernel), host only (no GPU needed): `cols` columns of rows (times
+ * the 128-node segments of a row, where a row has several) and nz planes on `ctas`
+ * resident CTAs. Writes *grid (CTAs launched), *zc (planes per chunk; 0 = equal
+ * runs: the columns' planes laid end to end, one run per CTA, y-neighbouring columns
+ * kcls apart in the run order) and *kcls, and, CTA by CTA in launch order, each
+ * item a CTA takes in the order it takes them, as four ints (CTA, column, za, zb):
+ * the planes [za, zb) of that column (the kernel reads source planes za-1 .. zb).
+ * *count = the number of items; only the first `cap` are written to items (4 cap
+ * ints, caller-owned host memory; may be NULL when cap = 0).
+ * Errors: LWACM_E_ARG (cols, nz or ctas < 1, cols * nz >= 2^31, a null output
+ * pointer, cap < 0, items NULL with cap > 0). */
+int lwacm_selftest_schedule(int cols, int nz, int ctas, int *grid, int *zc, int *kcls, int *items, long long cap,
+                            long long *count);
 
 #ifdef __cplusplus
 }

@@ -1,4 +1,5 @@
-// Device self-tests of the kernels' numerical building blocks.
+// Self-tests of the kernels' numerical building blocks (device) and of the
+// row-tiled kernels' work schedule (host).
 #include <cuda_runtime.h>
 #include <stdint.h>
 
@@ -83,4 +84,33 @@ extern "C" int lwacm_selftest_quotient(const float *a_dev, const float *b_dev, f
     const unsigned grid = (unsigned)(blocks < 4096 ? blocks : 4096);
     k_quotient<<<grid, 256, 0, (cudaStream_t)stream>>>(a_dev, b_dev, out_dev, n, packed == 2 ? 2 : (packed ? 1 : 0));
     return cudaGetLastError() == cudaSuccess ? LWACM_OK : LWACM_E_CUDA;
+}
+
+extern "C" int lwacm_selftest_schedule(int cols, int nz, int ctas, int *grid, int *zc, int *kcls, int *items,
+                                       long long cap, long long *count) {
+    if (cols < 1 || nz < 1 || ctas < 1 || (long long)cols * nz >= (1LL << 31) || !grid || !zc || !kcls || !count ||
+        cap < 0 || (cap > 0 && !items))
+        return LWACM_E_ARG;
+    const lwacm::tile::Schedule sc = lwacm::tile::plan_schedule(cols, nz, ctas);
+    *grid = sc.grid;
+    *zc = sc.zc;
+    *kcls = sc.kcls;
+    long long n = 0;
+    for (int b = 0; b < sc.grid && b < sc.nitems; ++b) {  // CTAs b >= nitems return at once
+        lwacm::tile::TaskIter it(b, sc.nitems, sc.grid, cols, sc.zc, nz, sc.kcls);
+        while (it.valid()) {
+            if (n < cap) {
+                items[4 * n] = b;
+                items[4 * n + 1] = it.col;
+                items[4 * n + 2] = it.za;
+                items[4 * n + 3] = it.zb;
+            }
+            ++n;
+            do {  // through the item's source planes, as the kernel steps, to the next item
+                it.next();
+            } while (it.valid() && it.pz != it.za - 1);
+        }
+    }
+    *count = n;
+    return LWACM_OK;
 }

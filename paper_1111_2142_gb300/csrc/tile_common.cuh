@@ -184,7 +184,7 @@ struct TaskIter {
     long long lin, lend;
     int r, q, kcls, per;
     int col, za, zb, pz;
-    __device__ TaskIter(int first, int nitems_, int stride_, int ycols_, int zc_, int nz_, int kcls_ = 1)
+    __host__ __device__ TaskIter(int first, int nitems_, int stride_, int ycols_, int zc_, int nz_, int kcls_ = 1)
         : item(first), nitems(nitems_), stride(stride_), ycols(ycols_), zc(zc_), nz(nz_), kcls(kcls_) {
         col = za = zb = pz = ch = dcol = dch = r = q = per = 0;
         lin = lend = 0;
@@ -205,7 +205,7 @@ struct TaskIter {
         }
         if (valid()) start_run();
     }
-    __device__ void start_run() {
+    __host__ __device__ void start_run() {
         if (zc > 0) {
             za = ch * zc;
             zb = za + zc < nz ? za + zc : nz;
@@ -216,9 +216,9 @@ struct TaskIter {
         }
         pz = za - 1;
     }
-    __device__ bool valid() const { return zc > 0 ? item < nitems : lin < lend; }
-    __device__ int mode() const { return pz < za ? FIRST : (pz < zb ? MID : LAST); }
-    __device__ void next() {
+    __host__ __device__ bool valid() const { return zc > 0 ? item < nitems : lin < lend; }
+    __host__ __device__ int mode() const { return pz < za ? FIRST : (pz < zb ? MID : LAST); }
+    __host__ __device__ void next() {
         if (pz < zb) {
             ++pz;
         } else if (zc > 0) {

@@ -75,6 +75,7 @@ def load():
         "lwacm_measure_fp32_peak": [ll, vp, P(d), P(d)],
         "lwacm_selftest_quotient": [vp, vp, vp, ll, i, vp],
         "lwacm_selftest_round": [vp, vp, ll, i, ctypes.c_uint, vp],
+        "lwacm_selftest_schedule": [i, i, i, vp, vp, vp, vp, ll, vp],
         "lwacm_set_force_field": [vp, vp, vp, vp, i, i],
         "lwacm_autotune": [vp, ctypes.c_char_p, i, ctypes.c_char_p, ctypes.c_size_t],
         "lwacm_set_scalar": [vp, vp, i, i],
