@@ -6,11 +6,12 @@
 // rows beyond ny hold the rows that follow it periodically, so its first such row
 // feeds the last real row from above as a halo row would, and none of them is stored.
 //
-// Persistent CTAs over chunk-major (y-column, z-chunk) items, TMA bulk copies of
-// ten staged rows per plane, packed row exchange through shared memory, three
-// rotating accumulator planes; each 256-node row is shared by two warps (half h
-// covers x = 128 h .. 128 h + 127, four nodes per lane), so a CTA of 8 rows has 16
-// warps at 125 registers per thread.
+// Persistent CTAs over (y-column, run of planes) items, scheduled as equal runs or
+// z-chunks (TaskIter and plan_schedule in tile_common.cuh), TMA bulk copies of ten
+// staged rows per plane, packed row exchange through shared memory, three rotating
+// accumulator planes; each 256-node row is shared by two warps (half h covers
+// x = 128 h .. 128 h + 127, four nodes per lane), so a CTA of 8 rows has 16 warps
+// at up to 128 registers per thread.
 //
 // The two halves of a row meet at x = 127|128 and, periodically, at x = 255|0. A
 // shuffle cannot cross them, so each half's boundary lanes (0 and 31) recompute

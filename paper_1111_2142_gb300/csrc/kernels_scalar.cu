@@ -10,7 +10,7 @@
 // summed over i; a_t = 1 - 6 alpha; the even part of g^(e) sums to T at a node).
 //
 // Same organisation as the half-row flow kernel (kernels_half.cu): persistent CTAs
-// over (8-row column, z-chunk) items, the rows of (T, u, v, w) a plane needs staged
+// over (8-row column, run of planes) items with the same schedule, the rows of (T, u, v, w) a plane needs staged
 // by 1-D bulk copies (two stages), each source node computing its link values once
 // per link pair (c, -c) and depositing them: along x inside a lane or by warp
 // shuffle (the two halves of a 256-node row recompute the few values they take from

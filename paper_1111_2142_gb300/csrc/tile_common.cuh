@@ -1,7 +1,8 @@
-// Building blocks of the row-tiled D3Q19 kernel (kernels_half.cu) and its device
-// self-test (selftest.cu): per-launch parameters, mbarrier / bulk-copy wrappers, the
-// correctly rounded velocity quotient, the task iterator over (y-column, z-chunk)
-// work items, exchange-row slots and storage-type loads and stores.
+// Building blocks of the row-tiled D3Q19 kernels (kernels_half.cu, kernels_scalar.cu)
+// and their self-tests (selftest.cu): per-launch parameters, mbarrier / bulk-copy
+// wrappers, the correctly rounded velocity quotient, the work schedule (planned on
+// the host, iterated on the device and on the host) over (y-column, run of planes)
+// items, exchange-row slots and storage-type loads and stores.
 #pragma once
 
 #include <stdint.h>
@@ -165,7 +166,7 @@ __device__ __forceinline__ float2 div_apply2(float2 a, const Div2 &d) {
 //   chunk-major (item = chunk * ycols + col) so that the CTAs working on
 //   neighbouring columns march through the same planes together and share their
 //   halo rows in L2; CTA b takes items b, b + G, b + 2G, ... (G = grid size).
-// * ranges (zc == 0): the columns' planes laid end to end (W = ycols nz planes) are
+// * equal runs (zc == 0): the columns' planes laid end to end (W = ycols nz planes) are
 //   cut into G equal runs, CTA b taking planes [b W / G, (b+1) W / G): one or two
 //   items (more when a run is longer than a column), the column changing inside a
 //   run. Columns follow each other in an order where y-neighbours lie kcls apart:
